@@ -1,0 +1,358 @@
+// TensorSketch of a Kronecker chain by the FFT identity of Sec. 3.1:
+//   SP = IFFT( ( (.)_j FFT(S^(j) A^(j))^T )^T ).
+// Each factor column is CountSketched into shared memory (bucket/sign from the
+// packed table), transformed by a shared-memory mixed-radix Stockham FFT, and the
+// spectra of every column multi-index are multiplied and inverse transformed.
+// Two real columns share one complex transform (x + i y), both forward and inverse.
+#include "internal.cuh"
+
+namespace ts {
+
+FftPlan make_fft_plan(int m) {
+  FftPlan p{};
+  p.m = m;
+  p.nst = 0;
+  int r = m;
+  while (r % 4 == 0) { p.radix[p.nst++] = 4; r /= 4; }
+  while (r % 2 == 0) { p.radix[p.nst++] = 2; r /= 2; }
+  const int small[] = {3, 5, 7, 11, 13};
+  for (int q : small)
+    while (r % q == 0) { p.radix[p.nst++] = q; r /= q; }
+  for (int q = 17; r > 1; q += 2)
+    while (r % q == 0) { p.radix[p.nst++] = q; r /= q; }
+  return p;
+}
+
+template <>
+int fft_max_len<float>() { return 12288; }
+template <>
+int fft_max_len<double>() { return 6144; }
+
+// tw[j] = exp(-2 pi i j / m), evaluated in FP64.
+template <typename T>
+__global__ void k_twiddles(int m, Cx<T>* __restrict__ tw) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < m; j += gridDim.x * blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)j / (double)m, &s, &c);
+    tw[j] = Cx<T>{(T)c, (T)(-s)};
+  }
+}
+
+template <typename T>
+ts_status launch_twiddles(int m, Cx<T>* tw, cudaStream_t st) {
+  k_twiddles<T><<<ceil_div(m, 64), 64, 0, st>>>(m, tw);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+// In-register DFT of size P (forward).  Radices 2 and 4 are written out; the
+// others sum the P x P DFT directly with twiddles tw[(r q mod P) * m/P].
+template <typename T, int P>
+__device__ __forceinline__ void dft_small(Cx<T> (&v)[P], const Cx<T>* __restrict__ tw, int mp) {
+  if constexpr (P == 2) {
+    Cx<T> a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if constexpr (P == 4) {
+    Cx<T> a = cadd(v[0], v[2]), b = csub(v[0], v[2]);
+    Cx<T> c = cadd(v[1], v[3]), d = csub(v[1], v[3]);
+    v[0] = cadd(a, c);
+    v[2] = csub(a, c);
+    v[1] = Cx<T>{b.x + d.y, b.y - d.x};  // b - i d
+    v[3] = Cx<T>{b.x - d.y, b.y + d.x};  // b + i d
+  } else {
+    Cx<T> o[P];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+      Cx<T> acc = v[0];
+#pragma unroll
+      for (int r = 1; r < P; ++r) acc = cadd(acc, cmul(v[r], tw[((r * q) % P) * mp]));
+      o[q] = acc;
+    }
+#pragma unroll
+    for (int q = 0; q < P; ++q) v[q] = o[q];
+  }
+}
+
+// One Stockham autosort stage of radix P: butterfly j reads src[j + r m/P],
+// applies exp(-2 pi i r k / (Ns P)) with k = j mod Ns, transforms, and writes
+// dst[(j / Ns) Ns P + k + q Ns].
+template <typename T, int P>
+__device__ void fft_stage(const Cx<T>* src, Cx<T>* dst, int m, int Ns,
+                          const Cx<T>* __restrict__ tw) {
+  const int nb = m / P;
+  const int tws = m / (Ns * P);
+  for (int j = threadIdx.x; j < nb; j += blockDim.x) {
+    const int k = j % Ns;
+    Cx<T> v[P];
+#pragma unroll
+    for (int r = 0; r < P; ++r) v[r] = src[j + r * nb];
+    if (k > 0) {
+#pragma unroll
+      for (int r = 1; r < P; ++r) v[r] = cmul(v[r], tw[r * k * tws]);
+    }
+    dft_small<T, P>(v, tw, nb);
+    const int base = (j / Ns) * Ns * P + k;
+#pragma unroll
+    for (int q = 0; q < P; ++q) dst[base + q * Ns] = v[q];
+  }
+}
+
+// Stage of arbitrary radix P (large prime factors): one output per thread.
+template <typename T>
+__device__ void fft_stage_generic(const Cx<T>* src, Cx<T>* dst, int m, int Ns, int P,
+                                  const Cx<T>* __restrict__ tw) {
+  const int nb = m / P;
+  const int tws = m / (Ns * P);
+  for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    const int j = t / P, q = t % P;
+    const int k = j % Ns;
+    Cx<T> acc{0, 0};
+    for (int r = 0; r < P; ++r) {
+      int e = (int)(((long)r * k * tws + (long)((r * (long)q) % P) * nb) % m);
+      acc = cadd(acc, cmul(src[j + r * nb], tw[e]));
+    }
+    dst[(j / Ns) * Ns * P + k + q * Ns] = acc;
+  }
+}
+
+// Forward FFT of length plan.m held in a (b is the ping-pong buffer).  Returns
+// the buffer that holds the result.  Must be called by the whole block.
+template <typename T>
+__device__ Cx<T>* fft_run(Cx<T>* a, Cx<T>* b, const FftPlan& plan,
+                          const Cx<T>* __restrict__ tw) {
+  int Ns = 1;
+  const int m = plan.m;
+  for (int s = 0; s < plan.nst; ++s) {
+    const int P = plan.radix[s];
+    switch (P) {
+      case 2: fft_stage<T, 2>(a, b, m, Ns, tw); break;
+      case 3: fft_stage<T, 3>(a, b, m, Ns, tw); break;
+      case 4: fft_stage<T, 4>(a, b, m, Ns, tw); break;
+      case 5: fft_stage<T, 5>(a, b, m, Ns, tw); break;
+      case 7: fft_stage<T, 7>(a, b, m, Ns, tw); break;
+      case 11: fft_stage<T, 11>(a, b, m, Ns, tw); break;
+      case 13: fft_stage<T, 13>(a, b, m, Ns, tw); break;
+      default: fft_stage_generic<T>(a, b, m, Ns, P, tw); break;
+    }
+    __syncthreads();
+    Cx<T>* t = a;
+    a = b;
+    b = t;
+    Ns *= P;
+  }
+  return a;
+}
+
+struct ChainDesc {
+  int nf;
+  int total_cols;
+  const void* factors[TS_MAX_ORDER];
+  int64_t rows[TS_MAX_ORDER];
+  int cols[TS_MAX_ORDER];
+  int colbase[TS_MAX_ORDER];
+  const int32_t* tables[TS_MAX_ORDER];
+};
+
+// Block b: flat factor columns 2b (real part) and 2b+1 (imaginary part).
+template <typename T>
+__global__ void __launch_bounds__(256) k_factor_spectra(ChainDesc d, FftPlan plan,
+                                                        const Cx<T>* __restrict__ tw,
+                                                        Cx<T>* __restrict__ spectra) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = plan.m;
+  Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw);
+  Cx<T>* b = a + m;
+  const int c0 = 2 * blockIdx.x;
+  const int c1 = c0 + 1;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) a[i] = Cx<T>{0, 0};
+  __syncthreads();
+  for (int half = 0; half < 2; ++half) {
+    const int c = c0 + half;
+    if (c >= d.total_cols) break;
+    int f = 0;
+    while (f + 1 < d.nf && c >= d.colbase[f + 1]) ++f;
+    const int r = c - d.colbase[f];
+    const T* A = static_cast<const T*>(d.factors[f]);
+    const int R = d.cols[f];
+    const int32_t* tab = d.tables[f];
+    T* dst = half == 0 ? &a[0].x : &a[0].y;
+    for (int64_t i = threadIdx.x; i < d.rows[f]; i += blockDim.x) {
+      const int32_t e = tab[i];
+      const int bin = entry_bin(e);
+      if (bin >= m) continue;  // caller-supplied table outside [0, m): entry ignored
+      T v = A[i * R + r];
+      if (entry_neg(e)) v = -v;
+      atomicAdd(dst + 2 * (size_t)bin, v);
+    }
+  }
+  __syncthreads();
+  const Cx<T>* F = fft_run<T>(a, b, plan, tw);
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    const Cx<T> z = F[k];
+    const Cx<T> zc = cconj(F[k == 0 ? 0 : m - k]);
+    spectra[(size_t)c0 * m + k] = Cx<T>{(z.x + zc.x) * (T)0.5, (z.y + zc.y) * (T)0.5};
+    if (c1 < d.total_cols) {
+      const Cx<T> df = csub(z, zc);  // (z - conj z(-k)) / (2i)
+      spectra[(size_t)c1 * m + k] = Cx<T>{df.y * (T)0.5, -df.x * (T)0.5};
+    }
+  }
+}
+
+// Block b: Z columns 2b and 2b+1 (column multi-index, factor 0 slowest).
+template <typename T>
+__global__ void __launch_bounds__(256) k_hadamard_ifft(ChainDesc d, int ncols, FftPlan plan,
+                                                       const Cx<T>* __restrict__ tw,
+                                                       const Cx<T>* __restrict__ spectra,
+                                                       T* __restrict__ Z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = plan.m;
+  Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw);
+  Cx<T>* b = a + m;
+  const int c0 = 2 * blockIdx.x;
+  const bool has1 = c0 + 1 < ncols;
+  int sp0[TS_MAX_ORDER], sp1[TS_MAX_ORDER];
+  {
+    int x0 = c0, x1 = c0 + 1;
+    for (int f = d.nf - 1; f >= 0; --f) {
+      sp0[f] = d.colbase[f] + x0 % d.cols[f];
+      sp1[f] = d.colbase[f] + x1 % d.cols[f];
+      x0 /= d.cols[f];
+      x1 /= d.cols[f];
+    }
+  }
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    Cx<T> p0{1, 0}, p1{0, 0};
+    if (has1) p1 = Cx<T>{1, 0};
+    for (int f = 0; f < d.nf; ++f) {
+      p0 = cmul(p0, spectra[(size_t)sp0[f] * m + k]);
+      if (has1) p1 = cmul(p1, spectra[(size_t)sp1[f] * m + k]);
+    }
+    // inverse FFT of s = p0 + i p1 as conj(FFT(conj(s))) / m
+    a[k] = Cx<T>{p0.x - p1.y, -(p0.y + p1.x)};
+  }
+  __syncthreads();
+  const Cx<T>* F = fft_run<T>(a, b, plan, tw);
+  const T inv_m = (T)1 / (T)m;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    Z[(size_t)c0 * m + k] = F[k].x * inv_m;
+    if (has1) Z[(size_t)(c0 + 1) * m + k] = -F[k].y * inv_m;
+  }
+}
+
+template <typename T>
+static ts_status set_smem(const void* fn, size_t bytes) {
+  if (bytes > 48 * 1024)
+    TS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return TS_OK;
+}
+
+template <typename T>
+ts_status launch_ts_apply(int nf, const T* const* factors, const int64_t* rows, const int* cols,
+                          const int32_t* const* tables, int m, const Cx<T>* tw, Cx<T>* spectra,
+                          T* Z, cudaStream_t st) {
+  ChainDesc d{};
+  d.nf = nf;
+  int total = 0;
+  long ncols = 1;
+  for (int f = 0; f < nf; ++f) {
+    d.factors[f] = factors[f];
+    d.rows[f] = rows[f];
+    d.cols[f] = cols[f];
+    d.colbase[f] = total;
+    d.tables[f] = tables[f];
+    total += cols[f];
+    ncols *= cols[f];
+  }
+  d.total_cols = total;
+  FftPlan plan = make_fft_plan(m);
+  const size_t smem = 2 * (size_t)m * sizeof(Cx<T>);
+  TS_TRY(set_smem<T>((const void*)k_factor_spectra<T>, smem));
+  TS_TRY(set_smem<T>((const void*)k_hadamard_ifft<T>, smem));
+  k_factor_spectra<T><<<ceil_div(total, 2), 256, smem, st>>>(d, plan, tw, spectra);
+  TS_LAUNCH_CHECK();
+  k_hadamard_ifft<T><<<ceil_div(ncols, 2), 256, smem, st>>>(d, (int)ncols, plan, tw, spectra, Z);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+template ts_status launch_twiddles<float>(int, Cx<float>*, cudaStream_t);
+template ts_status launch_twiddles<double>(int, Cx<double>*, cudaStream_t);
+template ts_status launch_ts_apply<float>(int, const float* const*, const int64_t*, const int*,
+                                          const int32_t* const*, int, const Cx<float>*,
+                                          Cx<float>*, float*, cudaStream_t);
+template ts_status launch_ts_apply<double>(int, const double* const*, const int64_t*, const int*,
+                                           const int32_t* const*, int, const Cx<double>*,
+                                           Cx<double>*, double*, cudaStream_t);
+
+}  // namespace ts
+
+using namespace ts;
+
+template <typename T>
+static size_t ts_apply_scratch(int nf, const int32_t* cols, int m) {
+  Bump b;
+  int total = 0;
+  for (int f = 0; f < nf; ++f) total += cols[f];
+  b.take<Cx<T>>((size_t)m);
+  b.take<Cx<T>>((size_t)m * total);
+  return b.off;
+}
+
+extern "C" size_t tensorsketch_apply_scratch_bytes(int32_t nf, const int32_t* cols, int32_t m,
+                                                   int32_t dtype) {
+  if (nf < 1 || nf >= TS_MAX_ORDER || !cols || m < 1) return 0;
+  return dtype == TS_F64 ? ts_apply_scratch<double>(nf, cols, m)
+                         : ts_apply_scratch<float>(nf, cols, m);
+}
+
+template <typename T>
+static ts_status ts_apply_impl(int nf, const void* const* factors, const int64_t* rows,
+                               const int32_t* cols, const int32_t* const* tables, int m, void* Z,
+                               void* scratch, cudaStream_t st) {
+  Bump b{static_cast<char*>(scratch)};
+  int total = 0;
+  for (int f = 0; f < nf; ++f) total += cols[f];
+  Cx<T>* tw = b.take<Cx<T>>((size_t)m);
+  Cx<T>* spectra = b.take<Cx<T>>((size_t)m * total);
+  const T* fp[TS_MAX_ORDER];
+  int c[TS_MAX_ORDER];
+  for (int f = 0; f < nf; ++f) {
+    fp[f] = static_cast<const T*>(factors[f]);
+    c[f] = cols[f];
+  }
+  TS_TRY(launch_twiddles<T>(m, tw, st));
+  return launch_ts_apply<T>(nf, fp, rows, c, tables, m, tw, spectra, static_cast<T*>(Z), st);
+}
+
+extern "C" ts_status tensorsketch_apply(int32_t nf, const void* const* factors,
+                                        const int64_t* rows, const int32_t* cols,
+                                        const int32_t* const* tables, int32_t m, int32_t dtype,
+                                        void* Z_out, void* scratch, size_t scratch_bytes,
+                                        ts_stream stream) {
+  clear_error();
+  if (!factors || !rows || !cols || !tables || !Z_out)
+    return fail(TS_ERR_INVALID_ARG, "tensorsketch_apply: NULL argument");
+  if (dtype != TS_F32 && dtype != TS_F64)
+    return fail(TS_ERR_INVALID_ARG, "tensorsketch_apply: bad dtype %d", dtype);
+  if (nf < 1 || nf >= TS_MAX_ORDER)
+    return fail(TS_ERR_SHAPE, "tensorsketch_apply: nf=%d outside [1,%d)", nf, TS_MAX_ORDER);
+  const int maxlen = dtype == TS_F64 ? fft_max_len<double>() : fft_max_len<float>();
+  if (m < 2 || m > maxlen)
+    return fail(TS_ERR_SHAPE, "tensorsketch_apply: m=%d outside [2,%d]", m, maxlen);
+  long ncols = 1;
+  for (int f = 0; f < nf; ++f) {
+    if (!factors[f] || !tables[f] || rows[f] < 1 || cols[f] < 1)
+      return fail(TS_ERR_INVALID_ARG, "tensorsketch_apply: bad factor %d", f);
+    ncols *= cols[f];
+  }
+  if (ncols > (1l << 24)) return fail(TS_ERR_SHAPE, "tensorsketch_apply: too many columns");
+  const size_t need = tensorsketch_apply_scratch_bytes(nf, cols, m, dtype);
+  if (!scratch || scratch_bytes < need || ((uintptr_t)scratch & 255))
+    return fail(TS_ERR_WORKSPACE, "tensorsketch_apply: need %zu bytes of 256-aligned scratch",
+                need);
+  cudaStream_t st = (cudaStream_t)stream;
+  return dtype == TS_F64
+             ? ts_apply_impl<double>(nf, factors, rows, cols, tables, m, Z_out, scratch, st)
+             : ts_apply_impl<float>(nf, factors, rows, cols, tables, m, Z_out, scratch, st);
+}

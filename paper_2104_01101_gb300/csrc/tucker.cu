@@ -1,0 +1,832 @@
+// Host orchestration of Sketch-Tucker-ALS (Alg. 4) and the C-ABI entry points
+// that compose the kernels: Init-RRF (Alg. 3), the sketched subproblem solve
+// (Alg. 5 / exact), the leverage-score sketch, the fitness and the driver itself.
+// Every step runs on the caller's stream in the caller's scratch; the host only
+// validates, carves the workspace and enqueues kernels.
+#include <math.h>
+#include <string.h>
+
+#include "internal.cuh"
+
+namespace ts {
+
+// ---------------------------------------------------------------- validation
+
+static ts_status check_tensor(const ts_tensor* X, const char* who) {
+  if (!X) return fail(TS_ERR_INVALID_ARG, "%s: tensor is NULL", who);
+  if (X->order < 2 || X->order > TS_MAX_ORDER)
+    return fail(TS_ERR_SHAPE, "%s: order %d outside [2,%d]", who, X->order, TS_MAX_ORDER);
+  if (X->dtype != TS_F32 && X->dtype != TS_F64)
+    return fail(TS_ERR_INVALID_ARG, "%s: bad dtype %d", who, X->dtype);
+  if (X->format != TS_DENSE && X->format != TS_COO)
+    return fail(TS_ERR_INVALID_ARG, "%s: bad format %d", who, X->format);
+  for (int k = 0; k < X->order; ++k)
+    if (X->dims[k] < 1 || X->dims[k] >= (int64_t)kP31)
+      return fail(TS_ERR_SHAPE, "%s: dims[%d]=%lld outside [1, 2^31-1)", who, k,
+                  (long long)X->dims[k]);
+  if (X->format == TS_COO) {
+    if (X->nnz < 0) return fail(TS_ERR_INVALID_ARG, "%s: nnz < 0", who);
+    if (X->nnz > 0 && (!X->indices || !X->values))
+      return fail(TS_ERR_INVALID_ARG, "%s: COO arrays are NULL", who);
+  } else if (!X->values) {
+    return fail(TS_ERR_INVALID_ARG, "%s: values is NULL", who);
+  }
+  return TS_OK;
+}
+
+static int64_t prod_other(const int64_t* d, int N, int n) {
+  int64_t p = 1;
+  for (int k = 0; k < N; ++k)
+    if (k != n) p *= d[k];
+  return p;
+}
+
+static void rrf_widths(const ts_tensor& X, int n, int R, int m, int k1_opt, int k2_opt, int* k1o,
+                       int* k2o) {
+  const int64_t K = prod_other(X.dims, X.order, n);
+  long k1 = k1_opt > 0 ? k1_opt : (long)ceil(sqrt((double)m));
+  long k2 = k2_opt > 0 ? k2_opt : (long)R * R + k1;
+  if (k2 > K) k2 = K;
+  long k1c = k1 < k2 ? k1 : k2;
+  if (k1c > X.dims[n]) k1c = X.dims[n];
+  if (k1c < R) k1c = R;
+  *k1o = (int)k1c;
+  *k2o = (int)k2;
+}
+
+static int rsvd_width(int R, int p, int r, int64_t s) {
+  long k = R + p;
+  if (k > r) k = r;
+  if (k > s) k = s;
+  return (int)(k < R ? R : k);
+}
+
+struct Shape {
+  int N;
+  int m;
+  int sweeps;
+  int kind;
+  int solve;
+  int oversample;
+  bool rrf;
+  int ranks[TS_MAX_ORDER];
+  int r[TS_MAX_ORDER];     // prod_{k != n} ranks[k]
+  int kc[TS_MAX_ORDER];    // RSVD width of subproblem n
+  int k1[TS_MAX_ORDER], k2[TS_MAX_ORDER];
+  int64_t smax;
+  int rmax, kmax, Rmax, k1max, k2max, chain_cols_max;
+};
+
+static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, int m, int sweeps,
+                            const ts_options* opt, bool want_residual, Shape& S) {
+  TS_TRY(check_tensor(X, "tucker_als_sketched"));
+  if (!ranks || !opt) return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: NULL ranks/options");
+  if (kind != TS_TENSORSKETCH && kind != TS_LEVERAGE)
+    return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: bad sketch kind %d", kind);
+  if (opt->solve != TS_SOLVE_RSVD && opt->solve != TS_SOLVE_EXACT)
+    return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: bad solve kind %d", opt->solve);
+  if (opt->gram_bf16) return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: gram_bf16 not built");
+  if (sweeps < 1) return fail(TS_ERR_SHAPE, "tucker_als_sketched: sweeps %d < 1", sweeps);
+  if (kind == TS_LEVERAGE && X->format != TS_DENSE)
+    return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: leverage sampling needs a dense tensor");
+  if (want_residual && X->format != TS_DENSE)
+    return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: COO residuals are not built");
+  S.N = X->order;
+  S.m = m;
+  S.sweeps = sweeps;
+  S.kind = kind;
+  S.solve = opt->solve;
+  S.oversample = opt->rsvd_oversample < 0 ? 5 : opt->rsvd_oversample;
+  S.rrf = !opt->init_given;
+  S.smax = 0;
+  S.rmax = S.kmax = S.Rmax = S.k1max = S.k2max = S.chain_cols_max = 0;
+  for (int k = 0; k < S.N; ++k) {
+    if (ranks[k] < 1 || ranks[k] >= X->dims[k])
+      return fail(TS_ERR_SHAPE, "tucker_als_sketched: rank[%d]=%d must lie in [1, dims[%d]=%lld)",
+                  k, ranks[k], k, (long long)X->dims[k]);
+    S.ranks[k] = ranks[k];
+    if (X->dims[k] > S.smax) S.smax = X->dims[k];
+    if (ranks[k] > S.Rmax) S.Rmax = ranks[k];
+  }
+  const int fftmax = X->dtype == TS_F64 ? fft_max_len<double>() : fft_max_len<float>();
+  if (kind == TS_TENSORSKETCH && (m < 2 || m > fftmax))
+    return fail(TS_ERR_SHAPE, "tucker_als_sketched: m=%d outside [2,%d]", m, fftmax);
+  if (m < 1) return fail(TS_ERR_SHAPE, "tucker_als_sketched: m < 1");
+  for (int n = 0; n < S.N; ++n) {
+    long r = 1;
+    int cc = 0;
+    for (int k = 0; k < S.N; ++k)
+      if (k != n) {
+        r *= ranks[k];
+        cc += ranks[k];
+      }
+    if (r > m)
+      return fail(TS_ERR_SHAPE,
+                  "tucker_als_sketched: m=%d < prod of the other ranks (%ld) for mode %d", m, r, n);
+    S.r[n] = (int)r;
+    if (S.solve == TS_SOLVE_RSVD && r > kMaxCholSmem)
+      return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: r=%ld > %d for the RSVD solve", r,
+                  kMaxCholSmem);
+    if (S.solve == TS_SOLVE_EXACT && r > kMaxEig)
+      return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: r=%ld > %d for the exact solve", r,
+                  kMaxEig);
+    S.kc[n] = rsvd_width(ranks[n], S.oversample, (int)r, X->dims[n]);
+    if (S.kc[n] > kMaxEig)
+      return fail(TS_ERR_SHAPE, "tucker_als_sketched: RSVD width %d > %d", S.kc[n], kMaxEig);
+    if (S.solve == TS_SOLVE_RSVD &&
+        rsvd_stage1_smem_bytes((int)r, S.kc[n], dtype_size(X->dtype)) > kMaxSmem)
+      return fail(TS_ERR_UNSUPPORTED,
+                  "tucker_als_sketched: r=%ld too large for the on-chip RSVD solve", r);
+    if (r > S.rmax) S.rmax = (int)r;
+    if (S.kc[n] > S.kmax) S.kmax = S.kc[n];
+    if (cc > S.chain_cols_max) S.chain_cols_max = cc;
+    S.k1[n] = S.k2[n] = 0;
+    if (S.rrf && n >= 1) {
+      rrf_widths(*X, n, ranks[n], m, opt->rrf_k1, opt->rrf_k2, &S.k1[n], &S.k2[n]);
+      if (S.k1[n] > kMaxEig)
+        return fail(TS_ERR_SHAPE, "tucker_als_sketched: RRF width k1=%d > %d", S.k1[n], kMaxEig);
+      if (S.k1[n] > S.k1max) S.k1max = S.k1[n];
+      if (S.k2[n] > S.k2max) S.k2max = S.k2[n];
+    }
+  }
+  return TS_OK;
+}
+
+// ---------------------------------------------------------------- workspace
+
+template <typename T>
+struct Work {
+  int* flag;
+  int32_t* tab[TS_MAX_ORDER][TS_MAX_ORDER];
+  int32_t* rtab[TS_MAX_ORDER][TS_MAX_ORDER];
+  T* Y[TS_MAX_ORDER];
+  T* Wt[TS_MAX_ORDER];
+  Cx<T>* tw;
+  Cx<T>* spectra;
+  T *Z, *G, *W, *YO, *Om, *Q, *E, *Mm, *D, *K, *CnT, *Fm, *V, *H, *Xs, *Gm, *Bm, *Ylev;
+  int32_t* samples;
+  double* levscr;
+  T* partial;
+  size_t partial_elems;
+  T* fitQ;
+  double* fitacc;
+};
+
+template <typename T>
+static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& b, Work<T>& w) {
+  const int N = S.N, m = S.m;
+  w.flag = b.take<int>(64);
+  for (int n = 0; n < N; ++n)
+    for (int k = 0; k < N; ++k) {
+      w.tab[n][k] = nullptr;
+      w.rtab[n][k] = nullptr;
+    }
+  for (int n = 0; n < N; ++n) {
+    w.Y[n] = nullptr;
+    w.Wt[n] = nullptr;
+  }
+  if (S.kind == TS_TENSORSKETCH) {
+    for (int n = 0; n < N; ++n)
+      for (int k = 0; k < N; ++k)
+        if (k != n) w.tab[n][k] = b.take<int32_t>((size_t)X.dims[k]);
+    for (int n = 0; n < N; ++n) w.Y[n] = b.take<T>((size_t)m * X.dims[n]);
+    w.tw = b.take<Cx<T>>((size_t)m);
+    w.spectra = b.take<Cx<T>>((size_t)m * S.chain_cols_max);
+  } else {
+    w.tw = nullptr;
+    w.spectra = nullptr;
+  }
+  if (S.rrf) {
+    for (int n = 1; n < N; ++n) {
+      for (int k = 0; k < N; ++k)
+        if (k != n) w.rtab[n][k] = b.take<int32_t>((size_t)X.dims[k]);
+      w.Wt[n] = b.take<T>((size_t)S.k2[n] * X.dims[n]);
+    }
+    w.Gm = b.take<T>((size_t)S.k2max * S.k1max);
+    w.Bm = b.take<T>((size_t)S.smax * S.k1max);
+  } else {
+    w.Gm = w.Bm = nullptr;
+  }
+  const int r = S.rmax, k = S.kmax, R = S.Rmax;
+  const int64_t s = S.smax;
+  int eign = k;
+  if (S.solve == TS_SOLVE_EXACT && r > eign) eign = r;
+  if (S.k1max > eign) eign = S.k1max;
+  w.Z = b.take<T>((size_t)m * r);
+  w.G = b.take<T>((size_t)r * r);
+  w.W = b.take<T>((size_t)r * k);
+  w.YO = b.take<T>((size_t)m * k);
+  w.Om = b.take<T>((size_t)s * k);
+  w.Q = b.take<T>((size_t)r * k);
+  w.E = b.take<T>((size_t)r * k);
+  w.Mm = b.take<T>((size_t)m * k);
+  w.D = b.take<T>((size_t)k * s);
+  w.K = b.take<T>((size_t)eign * eign);
+  w.CnT = b.take<T>((size_t)r * R);
+  w.Fm = b.take<T>((size_t)eign * R);
+  w.V = b.take<T>((size_t)s * R);
+  if (S.solve == TS_SOLVE_EXACT) {
+    w.H = b.take<T>((size_t)r * s);
+    w.Xs = b.take<T>((size_t)r * s);
+  } else {
+    w.H = w.Xs = nullptr;
+  }
+  if (S.kind == TS_LEVERAGE) {
+    w.Ylev = b.take<T>((size_t)m * s);
+    w.samples = b.take<int32_t>((size_t)m * (N - 1));
+    size_t lv = 0;
+    for (int n = 0; n < N; ++n) {
+      size_t t = leverage_scratch_doubles(X, n, m);
+      if (t > lv) lv = t;
+    }
+    w.levscr = b.take<double>(lv);
+  } else {
+    w.Ylev = nullptr;
+    w.samples = nullptr;
+    w.levscr = nullptr;
+  }
+  size_t pm = (size_t)r * r;
+  const size_t cands[] = {(size_t)r * k, (size_t)m * k, (size_t)k * s, (size_t)s * R,
+                          (size_t)eign * eign, (size_t)s * S.k1max,
+                          S.solve == TS_SOLVE_EXACT ? (size_t)r * s : 0};
+  for (size_t c : cands)
+    if (c > pm) pm = c;
+  w.partial_elems = 32 * pm;
+  w.partial = b.take<T>(w.partial_elems);
+  if (want_residual && X.format == TS_DENSE) {
+    w.fitQ = b.take<T>(fit_dense_scratch_elems<T>(X, S.ranks));
+    w.fitacc = b.take<double>(2);
+  } else {
+    w.fitQ = nullptr;
+    w.fitacc = nullptr;
+  }
+}
+
+// ---------------------------------------------------------------- building blocks
+
+template <typename T>
+static MatView<T> mv(const T* p, long rs, long cs) {
+  return MatView<T>{p, rs, cs};
+}
+template <typename T>
+static OutView<T> ov(T* p, long rs, long cs) {
+  return OutView<T>{p, rs, cs};
+}
+
+// Sketched subproblem: Z (column-major m x r), Y (m x s) -> CnT (r x R), A_out (s x R),
+// core scattered when core != null.  RSVD (Alg. 5) or exact (Theorem 4.1's solution).
+template <typename T>
+static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc, uint64_t seed,
+                                  int sweep, int n, const T* Z, const T* Y, Work<T>& w, T* A_out,
+                                  T* core, const CoreMap& map, cudaStream_t st) {
+  const MatView<T> Zt = mv<T>(Z, m, 1);  // r x m view of Z^T
+  const MatView<T> Zm = mv<T>(Z, 1, m);  // m x r view of Z
+  T* P = w.partial;
+  const size_t PE = w.partial_elems;
+  // G = Z^T Z
+  TS_TRY(gemm<T>(r, r, m, 1.0, Zt, Zm, 0.0, ov<T>(w.G, r, 1), P, PE, st));
+  if (solve == TS_SOLVE_RSVD) {
+    const int k = kc;
+    TS_TRY(launch_gaussian<T>(seed, make_tag(TS_PURPOSE_RSVD_GAUSS, sweep, n, 0), (int64_t)s * k,
+                              1.0, w.Om, st));
+    // YO = Y Omega (m x k);  W = Z^T YO (r x k)
+    TS_TRY(gemm<T>(m, k, s, 1.0, mv<T>(Y, s, 1), mv<T>(w.Om, k, 1), 0.0, ov<T>(w.YO, k, 1), P, PE,
+                   st));
+    TS_TRY(gemm<T>(r, k, m, 1.0, Zt, mv<T>(w.YO, k, 1), 0.0, ov<T>(w.W, k, 1), P, PE, st));
+    TS_TRY(launch_rsvd_stage1<T>(r, k, w.G, w.W, w.Q, w.E, w.flag, st));
+    // M = Z E (m x k);  D = M^T Y (k x s);  K = D D^T (k x k)
+    TS_TRY(gemm<T>(m, k, r, 1.0, Zm, mv<T>(w.E, k, 1), 0.0, ov<T>(w.Mm, k, 1), P, PE, st));
+    TS_TRY(gemm<T>(k, s, m, 1.0, mv<T>(w.Mm, 1, k), mv<T>(Y, s, 1), 0.0, ov<T>(w.D, s, 1), P, PE,
+                   st));
+    TS_TRY(gemm<T>(k, k, s, 1.0, mv<T>(w.D, s, 1), mv<T>(w.D, 1, s), 0.0, ov<T>(w.K, k, 1), P, PE,
+                   st));
+    TS_TRY(launch_eig_small<T>(k, R, w.K, w.Q, r, w.CnT, w.Fm, nullptr, w.flag, st));
+    // V = D^T Fm (s x R)
+    TS_TRY(gemm<T>(s, R, k, 1.0, mv<T>(w.D, 1, s), mv<T>(w.Fm, R, 1), 0.0, ov<T>(w.V, R, 1), P,
+                   PE, st));
+  } else {
+    // H = Z^T Y (r x s);  X = G^{-1} H;  K = X X^T;  V = X^T Fm
+    TS_TRY(gemm<T>(r, s, m, 1.0, Zt, mv<T>(Y, s, 1), 0.0, ov<T>(w.H, s, 1), P, PE, st));
+    TS_TRY(launch_chol_solve<T>(r, s, w.G, w.H, w.Xs, w.flag, st));
+    TS_TRY(gemm<T>(r, r, s, 1.0, mv<T>(w.Xs, s, 1), mv<T>(w.Xs, 1, s), 0.0, ov<T>(w.K, r, 1), P,
+                   PE, st));
+    TS_TRY(launch_eig_small<T>(r, R, w.K, nullptr, r, w.CnT, w.Fm, nullptr, w.flag, st));
+    TS_TRY(gemm<T>(s, R, r, 1.0, mv<T>(w.Xs, 1, s), mv<T>(w.Fm, R, 1), 0.0, ov<T>(w.V, R, 1), P,
+                   PE, st));
+  }
+  return launch_finalize<T>(s, R, w.V, A_out, w.CnT, r, core, map, st);
+}
+
+template <typename T>
+static ts_status build_ts_tables(const ts_tensor& X, const Shape& S, uint64_t seed, int sweep,
+                                 Work<T>& w, cudaStream_t st) {
+  for (int n = 0; n < S.N; ++n)
+    for (int k = 0; k < S.N; ++k)
+      if (k != n)
+        TS_TRY(launch_hash_table(seed, TS_PURPOSE_TS_HASH, sweep, n, k, X.dims[k], S.m,
+                                 w.tab[n][k], st));
+  return TS_OK;
+}
+
+template <typename T>
+static ts_status sketch_rhs_all(const ts_tensor& X, const Shape& S, Work<T>& w, cudaStream_t st) {
+  SketchJob jobs[kMaxJobs];
+  for (int n = 0; n < S.N; ++n) {
+    jobs[n].mode = n;
+    jobs[n].nbins = S.m;
+    jobs[n].out = w.Y[n];
+    for (int k = 0; k < S.N; ++k) jobs[n].tables[k] = w.tab[n][k];
+  }
+  return launch_input_sketch<T>(X, jobs, S.N, st);
+}
+
+// Init-RRF (Alg. 3) for every mode n >= 1: one pass over X for all CountSketch
+// factors, then per mode B = W^T G, B^T B = V Lambda V^T, U = B V Sigma^{-1}.
+template <typename T>
+static ts_status rrf_all(const ts_tensor& X, const Shape& S, uint64_t seed, Work<T>& w,
+                         T* const* factors, cudaStream_t st) {
+  SketchJob jobs[kMaxJobs];
+  int nj = 0;
+  for (int n = 1; n < S.N; ++n) {
+    for (int k = 0; k < S.N; ++k)
+      if (k != n)
+        TS_TRY(launch_hash_table(seed, TS_PURPOSE_RRF_HASH, 0, n, k, X.dims[k], S.k2[n],
+                                 w.rtab[n][k], st));
+    jobs[nj].mode = n;
+    jobs[nj].nbins = S.k2[n];
+    jobs[nj].out = w.Wt[n];
+    for (int k = 0; k < S.N; ++k) jobs[nj].tables[k] = w.rtab[n][k];
+    ++nj;
+  }
+  TS_TRY(launch_input_sketch<T>(X, jobs, nj, st));
+  CoreMap none{};
+  for (int n = 1; n < S.N; ++n) {
+    const int k1 = S.k1[n], k2 = S.k2[n], R = S.ranks[n];
+    const int s = (int)X.dims[n];
+    TS_TRY(launch_gaussian<T>(seed, make_tag(TS_PURPOSE_RRF_GAUSS, 0, n, 0), (int64_t)k2 * k1,
+                              1.0 / sqrt((double)k1), w.Gm, st));
+    TS_TRY(gemm<T>(s, k1, k2, 1.0, mv<T>(w.Wt[n], 1, s), mv<T>(w.Gm, k1, 1), 0.0,
+                   ov<T>(w.Bm, k1, 1), w.partial, w.partial_elems, st));
+    TS_TRY(gemm<T>(k1, k1, s, 1.0, mv<T>(w.Bm, 1, k1), mv<T>(w.Bm, k1, 1), 0.0, ov<T>(w.K, k1, 1),
+                   w.partial, w.partial_elems, st));
+    TS_TRY(launch_eig_small<T>(k1, R, w.K, nullptr, k1, nullptr, w.Fm, nullptr, w.flag, st));
+    TS_TRY(gemm<T>(s, R, k1, 1.0, mv<T>(w.Bm, k1, 1), mv<T>(w.Fm, R, 1), 0.0, ov<T>(w.V, R, 1),
+                   w.partial, w.partial_elems, st));
+    TS_TRY(launch_finalize<T>(s, R, w.V, factors[n], nullptr, 0, nullptr, none, st));
+  }
+  return TS_OK;
+}
+
+static ts_status phase(const ts_options& opt, int i, cudaStream_t st) {
+  if (opt.phase_events && opt.phase_events[i])
+    TS_CUDA(cudaEventRecord((cudaEvent_t)opt.phase_events[i], st));
+  return TS_OK;
+}
+
+template <typename T>
+static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& opt, void* ws,
+                          T* core, T* const* factors, double* residual_out, cudaStream_t st) {
+  Work<T> w;
+  Bump b{static_cast<char*>(ws)};
+  carve<T>(X, S, residual_out != nullptr, b, w);
+  const int N = S.N, m = S.m;
+  TS_TRY(phase(opt, 0, st));
+  TS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
+  if (S.rrf) TS_TRY(rrf_all<T>(X, S, opt.seed, w, factors, st));
+  TS_TRY(phase(opt, 1, st));
+  if (S.kind == TS_TENSORSKETCH) {
+    TS_TRY(launch_twiddles<T>(m, w.tw, st));
+    TS_TRY(build_ts_tables<T>(X, S, opt.seed, 0, w, st));
+    TS_TRY(phase(opt, 2, st));
+    TS_TRY(sketch_rhs_all<T>(X, S, w, st));
+    TS_TRY(phase(opt, 3, st));
+  }
+  const T* chain[TS_MAX_ORDER];
+  const int32_t* ctab[TS_MAX_ORDER];
+  int64_t rows[TS_MAX_ORDER];
+  int cols[TS_MAX_ORDER];
+  for (int sweep = 0; sweep < S.sweeps; ++sweep) {
+    if (S.kind == TS_TENSORSKETCH && opt.resketch_each_sweep && sweep > 0) {
+      TS_TRY(build_ts_tables<T>(X, S, opt.seed, sweep, w, st));
+      TS_TRY(sketch_rhs_all<T>(X, S, w, st));
+    }
+    for (int n = 0; n < N; ++n) {
+      const T* Yn;
+      if (S.kind == TS_TENSORSKETCH) {
+        int nf = 0;
+        for (int k = 0; k < N; ++k)
+          if (k != n) {
+            chain[nf] = factors[k];
+            ctab[nf] = w.tab[n][k];
+            rows[nf] = X.dims[k];
+            cols[nf] = S.ranks[k];
+            ++nf;
+          }
+        TS_TRY(launch_ts_apply<T>(nf, chain, rows, cols, ctab, m, w.tw, w.spectra, w.Z, st));
+        Yn = w.Y[n];
+      } else {
+        TS_TRY(launch_leverage<T>(X, n, S.ranks, (const T* const*)factors, m, opt.seed, sweep, w.Z,
+                                  w.Ylev, w.samples, w.levscr, st));
+        Yn = w.Ylev;
+      }
+      CoreMap map{};
+      map.order = N;
+      map.n = n;
+      for (int k = 0; k < N; ++k) map.ranks[k] = S.ranks[k];
+      TS_TRY(solve_subproblem<T>(m, S.r[n], (int)X.dims[n], S.ranks[n], S.solve, S.kc[n], opt.seed,
+                                 sweep, n, w.Z, Yn, w, factors[n], core, map, st));
+    }
+    if (residual_out && opt.track_fit)
+      TS_TRY(launch_fit_dense<T>(X, S.ranks, core, (const T* const*)factors, w.fitQ, w.fitacc,
+                                 residual_out + sweep, st));
+  }
+  TS_TRY(phase(opt, 4, st));
+  if (residual_out && !opt.track_fit)
+    TS_TRY(launch_fit_dense<T>(X, S.ranks, core, (const T* const*)factors, w.fitQ, w.fitacc,
+                               residual_out, st));
+  TS_TRY(phase(opt, 5, st));
+  return TS_OK;
+}
+
+}  // namespace ts
+
+using namespace ts;
+
+// ============================================================== C ABI
+
+extern "C" ts_status tucker_als_workspace_bytes(const ts_tensor* X, const int32_t* ranks,
+                                                int32_t kind, int32_t m, int32_t sweeps,
+                                                const ts_options* opt, size_t* bytes_out) {
+  clear_error();
+  if (!bytes_out) return fail(TS_ERR_INVALID_ARG, "tucker_als_workspace_bytes: NULL bytes_out");
+  Shape S;
+  // Residual scratch is always counted so one size serves both uses.
+  TS_TRY(plan_shape(X, ranks, kind, m, sweeps, opt, X && X->format == TS_DENSE, S));
+  Bump b;
+  if (X->dtype == TS_F64) {
+    Work<double> w;
+    carve<double>(*X, S, X->format == TS_DENSE, b, w);
+  } else {
+    Work<float> w;
+    carve<float>(*X, S, X->format == TS_DENSE, b, w);
+  }
+  *bytes_out = b.off;
+  return TS_OK;
+}
+
+extern "C" ts_status tucker_als_sketched(const ts_tensor* X, const int32_t* ranks, int32_t kind,
+                                         int32_t m, int32_t sweeps, const ts_options* opt,
+                                         void* workspace, size_t workspace_bytes, void* core_out,
+                                         void* const* factors_inout, double* residual_out,
+                                         ts_stream stream) {
+  clear_error();
+  Shape S;
+  TS_TRY(plan_shape(X, ranks, kind, m, sweeps, opt, residual_out != nullptr, S));
+  if (!core_out || !factors_inout)
+    return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: NULL core/factors");
+  for (int k = 0; k < X->order; ++k)
+    if (!factors_inout[k]) return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: factor %d NULL", k);
+  size_t need = 0;
+  TS_TRY(tucker_als_workspace_bytes(X, ranks, kind, m, sweeps, opt, &need));
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255))
+    return fail(TS_ERR_WORKSPACE, "tucker_als_sketched: need %zu bytes of 256-aligned workspace",
+                need);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (X->dtype == TS_F64)
+    return als_impl<double>(*X, S, *opt, workspace, static_cast<double*>(core_out),
+                            reinterpret_cast<double* const*>(factors_inout), residual_out, st);
+  return als_impl<float>(*X, S, *opt, workspace, static_cast<float*>(core_out),
+                         reinterpret_cast<float* const*>(factors_inout), residual_out, st);
+}
+
+extern "C" ts_status tensorsketch_input(const ts_tensor* X, int32_t mode,
+                                        const int32_t* const* tables, int32_t m, void* Y_out,
+                                        ts_stream stream) {
+  clear_error();
+  TS_TRY(check_tensor(X, "tensorsketch_input"));
+  if (mode < 0 || mode >= X->order)
+    return fail(TS_ERR_SHAPE, "tensorsketch_input: mode %d out of range", mode);
+  if (!tables || !Y_out || m < 1)
+    return fail(TS_ERR_INVALID_ARG, "tensorsketch_input: NULL tables/Y_out or m < 1");
+  SketchJob job{};
+  job.mode = mode;
+  job.nbins = m;
+  job.out = Y_out;
+  for (int k = 0; k < X->order; ++k) {
+    if (k != mode && !tables[k])
+      return fail(TS_ERR_INVALID_ARG, "tensorsketch_input: table %d is NULL", k);
+    job.tables[k] = k == mode ? nullptr : tables[k];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  return X->dtype == TS_F64 ? launch_input_sketch<double>(*X, &job, 1, st)
+                            : launch_input_sketch<float>(*X, &job, 1, st);
+}
+
+// ---------------------------------------------------------------- Init-RRF, one mode
+
+static ts_status rrf_check(const ts_tensor* X, int32_t mode, int32_t R, int32_t k1, int32_t k2) {
+  TS_TRY(check_tensor(X, "range_finder_init"));
+  if (mode < 0 || mode >= X->order) return fail(TS_ERR_SHAPE, "range_finder_init: bad mode");
+  const int64_t K = prod_other(X->dims, X->order, mode);
+  if (!(R >= 1 && R <= k1 && k1 <= k2 && k1 <= X->dims[mode] && k2 <= K && k1 <= kMaxEig))
+    return fail(TS_ERR_SHAPE,
+                "range_finder_init: need 1 <= R <= k1 <= min(k2, dims[mode]), k2 <= %lld, k1 <= %d",
+                (long long)K, kMaxEig);
+  return TS_OK;
+}
+
+template <typename T>
+static size_t rrf_carve(const ts_tensor& X, int mode, int R, int k1, int k2, Bump& b, int** flag,
+                        int32_t** tabs, T** Wt, T** Gm, T** Bm, T** K, T** Fm, T** V, T** P,
+                        size_t* PE) {
+  *flag = b.take<int>(64);
+  for (int k = 0; k < X.order; ++k) tabs[k] = k == mode ? nullptr : b.take<int32_t>(X.dims[k]);
+  const int64_t s = X.dims[mode];
+  *Wt = b.take<T>((size_t)k2 * s);
+  *Gm = b.take<T>((size_t)k2 * k1);
+  *Bm = b.take<T>((size_t)s * k1);
+  *K = b.take<T>((size_t)k1 * k1);
+  *Fm = b.take<T>((size_t)k1 * R);
+  *V = b.take<T>((size_t)s * R);
+  size_t pm = (size_t)s * k1 > (size_t)k1 * k1 ? (size_t)s * k1 : (size_t)k1 * k1;
+  *PE = 32 * pm;
+  *P = b.take<T>(*PE);
+  return b.off;
+}
+
+extern "C" size_t range_finder_init_scratch_bytes(const ts_tensor* X, int32_t mode, int32_t R,
+                                                  int32_t k1, int32_t k2) {
+  if (rrf_check(X, mode, R, k1, k2) != TS_OK) return 0;
+  Bump b;
+  int* f;
+  int32_t* t[TS_MAX_ORDER];
+  size_t pe;
+  if (X->dtype == TS_F64) {
+    double *a, *c, *d, *e, *g, *h, *p;
+    return rrf_carve<double>(*X, mode, R, k1, k2, b, &f, t, &a, &c, &d, &e, &g, &h, &p, &pe);
+  }
+  float *a, *c, *d, *e, *g, *h, *p;
+  return rrf_carve<float>(*X, mode, R, k1, k2, b, &f, t, &a, &c, &d, &e, &g, &h, &p, &pe);
+}
+
+template <typename T>
+static ts_status rrf_one(const ts_tensor& X, int mode, int R, int k1, int k2, uint64_t seed,
+                         T* A_out, void* scratch, cudaStream_t st) {
+  Bump b{static_cast<char*>(scratch)};
+  int* flag;
+  int32_t* tabs[TS_MAX_ORDER];
+  T *Wt, *Gm, *Bm, *K, *Fm, *V, *P;
+  size_t PE;
+  rrf_carve<T>(X, mode, R, k1, k2, b, &flag, tabs, &Wt, &Gm, &Bm, &K, &Fm, &V, &P, &PE);
+  TS_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  SketchJob job{};
+  job.mode = mode;
+  job.nbins = k2;
+  job.out = Wt;
+  for (int k = 0; k < X.order; ++k) {
+    if (k != mode)
+      TS_TRY(launch_hash_table(seed, TS_PURPOSE_RRF_HASH, 0, mode, k, X.dims[k], k2, tabs[k], st));
+    job.tables[k] = tabs[k];
+  }
+  TS_TRY(launch_input_sketch<T>(X, &job, 1, st));
+  const int s = (int)X.dims[mode];
+  TS_TRY(launch_gaussian<T>(seed, make_tag(TS_PURPOSE_RRF_GAUSS, 0, mode, 0), (int64_t)k2 * k1,
+                            1.0 / sqrt((double)k1), Gm, st));
+  TS_TRY(gemm<T>(s, k1, k2, 1.0, mv<T>(Wt, 1, s), mv<T>(Gm, k1, 1), 0.0, ov<T>(Bm, k1, 1), P, PE,
+                 st));
+  TS_TRY(gemm<T>(k1, k1, s, 1.0, mv<T>(Bm, 1, k1), mv<T>(Bm, k1, 1), 0.0, ov<T>(K, k1, 1), P, PE,
+                 st));
+  TS_TRY(launch_eig_small<T>(k1, R, K, nullptr, k1, nullptr, Fm, nullptr, flag, st));
+  TS_TRY(gemm<T>(s, R, k1, 1.0, mv<T>(Bm, k1, 1), mv<T>(Fm, R, 1), 0.0, ov<T>(V, R, 1), P, PE, st));
+  CoreMap none{};
+  return launch_finalize<T>(s, R, V, A_out, nullptr, 0, nullptr, none, st);
+}
+
+extern "C" ts_status range_finder_init(const ts_tensor* X, int32_t mode, int32_t R, int32_t k1,
+                                       int32_t k2, uint64_t seed, void* A_out, void* scratch,
+                                       size_t scratch_bytes, ts_stream stream) {
+  clear_error();
+  TS_TRY(rrf_check(X, mode, R, k1, k2));
+  if (!A_out) return fail(TS_ERR_INVALID_ARG, "range_finder_init: A_out is NULL");
+  const size_t need = range_finder_init_scratch_bytes(X, mode, R, k1, k2);
+  if (!scratch || scratch_bytes < need || ((uintptr_t)scratch & 255))
+    return fail(TS_ERR_WORKSPACE, "range_finder_init: need %zu bytes of 256-aligned scratch", need);
+  cudaStream_t st = (cudaStream_t)stream;
+  return X->dtype == TS_F64
+             ? rrf_one<double>(*X, mode, R, k1, k2, seed, static_cast<double*>(A_out), scratch, st)
+             : rrf_one<float>(*X, mode, R, k1, k2, seed, static_cast<float*>(A_out), scratch, st);
+}
+
+// ---------------------------------------------------------------- one subproblem
+
+static ts_status lrls_check(int32_t m, int32_t r, int32_t s, int32_t R, int32_t dtype,
+                            int32_t solve, int32_t oversample, int* kc) {
+  if (dtype != TS_F32 && dtype != TS_F64) return fail(TS_ERR_INVALID_ARG, "ts_lrls: bad dtype");
+  if (solve != TS_SOLVE_RSVD && solve != TS_SOLVE_EXACT)
+    return fail(TS_ERR_INVALID_ARG, "ts_lrls: bad solve kind");
+  if (m < 1 || r < 1 || s < 1 || R < 1 || R > r || R > s || r > m)
+    return fail(TS_ERR_SHAPE, "ts_lrls: need 1 <= R <= min(r, s) and r <= m");
+  *kc = rsvd_width(R, oversample < 0 ? 5 : oversample, r, s);
+  if (solve == TS_SOLVE_RSVD &&
+      (r > kMaxCholSmem || *kc > kMaxEig ||
+       rsvd_stage1_smem_bytes(r, *kc, dtype_size(dtype)) > kMaxSmem))
+    return fail(TS_ERR_SHAPE, "ts_lrls: RSVD limits r <= %d, k <= %d and on-chip footprint",
+                kMaxCholSmem, kMaxEig);
+  if (solve == TS_SOLVE_EXACT && r > kMaxEig)
+    return fail(TS_ERR_SHAPE, "ts_lrls: exact limit r <= %d", kMaxEig);
+  return TS_OK;
+}
+
+template <typename T>
+static size_t lrls_carve(int m, int r, int s, int R, int solve, int kc, Bump& b, Work<T>& w) {
+  memset(&w, 0, sizeof(w));
+  w.flag = b.take<int>(64);
+  const int k = kc;
+  const int eign = solve == TS_SOLVE_EXACT ? (r > k ? r : k) : k;
+  w.G = b.take<T>((size_t)r * r);
+  w.W = b.take<T>((size_t)r * k);
+  w.YO = b.take<T>((size_t)m * k);
+  w.Om = b.take<T>((size_t)s * k);
+  w.Q = b.take<T>((size_t)r * k);
+  w.E = b.take<T>((size_t)r * k);
+  w.Mm = b.take<T>((size_t)m * k);
+  w.D = b.take<T>((size_t)k * s);
+  w.K = b.take<T>((size_t)eign * eign);
+  w.Fm = b.take<T>((size_t)eign * R);
+  w.V = b.take<T>((size_t)s * R);
+  if (solve == TS_SOLVE_EXACT) {
+    w.H = b.take<T>((size_t)r * s);
+    w.Xs = b.take<T>((size_t)r * s);
+  }
+  size_t pm = (size_t)r * r;
+  const size_t cands[] = {(size_t)r * k, (size_t)m * k, (size_t)k * s, (size_t)s * R,
+                          (size_t)eign * eign, solve == TS_SOLVE_EXACT ? (size_t)r * s : 0};
+  for (size_t c : cands)
+    if (c > pm) pm = c;
+  w.partial_elems = 32 * pm;
+  w.partial = b.take<T>(w.partial_elems);
+  return b.off;
+}
+
+extern "C" size_t ts_lrls_scratch_bytes(int32_t m, int32_t r, int32_t s, int32_t R, int32_t solve,
+                                        int32_t oversample, int32_t dtype) {
+  int kc;
+  if (lrls_check(m, r, s, R, dtype, solve, oversample, &kc) != TS_OK) return 0;
+  Bump b;
+  if (dtype == TS_F64) {
+    Work<double> w;
+    return lrls_carve<double>(m, r, s, R, solve, kc, b, w);
+  }
+  Work<float> w;
+  return lrls_carve<float>(m, r, s, R, solve, kc, b, w);
+}
+
+template <typename T>
+static ts_status lrls_one(int m, int r, int s, int R, int solve, int kc, const void* Z,
+                          const void* Y, uint64_t seed, int sweep, int n, void* CnT_out,
+                          void* A_out, void* scratch, cudaStream_t st) {
+  Bump b{static_cast<char*>(scratch)};
+  Work<T> w;
+  lrls_carve<T>(m, r, s, R, solve, kc, b, w);
+  w.CnT = static_cast<T*>(CnT_out);
+  TS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
+  CoreMap none{};
+  return solve_subproblem<T>(m, r, s, R, solve, kc, seed, sweep, n, static_cast<const T*>(Z),
+                             static_cast<const T*>(Y), w, static_cast<T*>(A_out), nullptr, none,
+                             st);
+}
+
+extern "C" ts_status ts_lrls_solve(int32_t m, int32_t r, int32_t s, int32_t R, int32_t dtype,
+                                   const void* Z_colmajor, const void* Y, int32_t solve,
+                                   uint64_t seed, int32_t sweep, int32_t n, int32_t oversample,
+                                   void* CnT_out, void* A_out, void* scratch, size_t scratch_bytes,
+                                   ts_stream stream) {
+  clear_error();
+  int kc;
+  TS_TRY(lrls_check(m, r, s, R, dtype, solve, oversample, &kc));
+  if (!Z_colmajor || !Y || !CnT_out || !A_out)
+    return fail(TS_ERR_INVALID_ARG, "ts_lrls_solve: NULL argument");
+  if (sweep < 0 || sweep >= (1 << 24) || n < 0 || n > 255)
+    return fail(TS_ERR_INVALID_ARG, "ts_lrls_solve: sweep/n out of range");
+  const size_t need = ts_lrls_scratch_bytes(m, r, s, R, solve, oversample, dtype);
+  if (!scratch || scratch_bytes < need || ((uintptr_t)scratch & 255))
+    return fail(TS_ERR_WORKSPACE, "ts_lrls_solve: need %zu bytes of 256-aligned scratch", need);
+  cudaStream_t st = (cudaStream_t)stream;
+  return dtype == TS_F64 ? lrls_one<double>(m, r, s, R, solve, kc, Z_colmajor, Y, seed, sweep, n,
+                                            CnT_out, A_out, scratch, st)
+                         : lrls_one<float>(m, r, s, R, solve, kc, Z_colmajor, Y, seed, sweep, n,
+                                           CnT_out, A_out, scratch, st);
+}
+
+// ---------------------------------------------------------------- leverage sketch
+
+extern "C" size_t ts_leverage_sketch_scratch_bytes(const ts_tensor* X, int32_t mode, int32_t m) {
+  if (check_tensor(X, "ts_leverage_sketch") != TS_OK || mode < 0 || mode >= X->order || m < 1)
+    return 0;
+  Bump b;
+  b.take<int32_t>((size_t)m * (X->order - 1));
+  b.take<double>(leverage_scratch_doubles(*X, mode, m));
+  return b.off;
+}
+
+extern "C" ts_status ts_leverage_sketch(const ts_tensor* X, int32_t mode, const int32_t* ranks,
+                                        const void* const* factors, int32_t m, uint64_t seed,
+                                        int32_t sweep, void* Z_out, void* Y_out,
+                                        int32_t* samples_out, void* scratch, size_t scratch_bytes,
+                                        ts_stream stream) {
+  clear_error();
+  TS_TRY(check_tensor(X, "ts_leverage_sketch"));
+  if (X->format != TS_DENSE) return fail(TS_ERR_SHAPE, "ts_leverage_sketch: dense tensors only");
+  if (mode < 0 || mode >= X->order || m < 1)
+    return fail(TS_ERR_SHAPE, "ts_leverage_sketch: bad mode or m");
+  if (!ranks || !factors || !Z_out || !Y_out)
+    return fail(TS_ERR_INVALID_ARG, "ts_leverage_sketch: NULL argument");
+  if (sweep < 0 || sweep >= (1 << 24))
+    return fail(TS_ERR_INVALID_ARG, "ts_leverage_sketch: sweep out of range");
+  for (int k = 0; k < X->order; ++k)
+    if (k != mode && (!factors[k] || ranks[k] < 1))
+      return fail(TS_ERR_INVALID_ARG, "ts_leverage_sketch: bad factor %d", k);
+  const size_t need = ts_leverage_sketch_scratch_bytes(X, mode, m);
+  if (!scratch || scratch_bytes < need || ((uintptr_t)scratch & 255))
+    return fail(TS_ERR_WORKSPACE, "ts_leverage_sketch: need %zu bytes of 256-aligned scratch",
+                need);
+  Bump b{static_cast<char*>(scratch)};
+  int32_t* smp = b.take<int32_t>((size_t)m * (X->order - 1));
+  double* lv = b.take<double>(leverage_scratch_doubles(*X, mode, m));
+  if (samples_out) smp = samples_out;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (X->dtype == TS_F64)
+    return launch_leverage<double>(*X, mode, ranks, reinterpret_cast<const double* const*>(factors),
+                                   m, seed, sweep, static_cast<double*>(Z_out),
+                                   static_cast<double*>(Y_out), smp, lv, st);
+  return launch_leverage<float>(*X, mode, ranks, reinterpret_cast<const float* const*>(factors), m,
+                                seed, sweep, static_cast<float*>(Z_out),
+                                static_cast<float*>(Y_out), smp, lv, st);
+}
+
+// ---------------------------------------------------------------- fitness
+
+extern "C" size_t ts_fitness_scratch_bytes(const ts_tensor* X, const int32_t* ranks) {
+  if (check_tensor(X, "ts_fitness") != TS_OK || !ranks || X->format != TS_DENSE) return 0;
+  Bump b;
+  if (X->dtype == TS_F64)
+    b.take<double>(fit_dense_scratch_elems<double>(*X, ranks));
+  else
+    b.take<float>(fit_dense_scratch_elems<float>(*X, ranks));
+  b.take<double>(2);
+  return b.off;
+}
+
+extern "C" ts_status ts_fitness(const ts_tensor* X, const int32_t* ranks, const void* core,
+                                const void* const* factors, double* residual_out, void* scratch,
+                                size_t scratch_bytes, ts_stream stream) {
+  clear_error();
+  TS_TRY(check_tensor(X, "ts_fitness"));
+  if (X->format != TS_DENSE)
+    return fail(TS_ERR_UNSUPPORTED, "ts_fitness: COO residuals are not built");
+  if (!ranks || !core || !factors || !residual_out)
+    return fail(TS_ERR_INVALID_ARG, "ts_fitness: NULL argument");
+  for (int k = 0; k < X->order; ++k)
+    if (!factors[k] || ranks[k] < 1) return fail(TS_ERR_INVALID_ARG, "ts_fitness: bad factor %d", k);
+  const size_t need = ts_fitness_scratch_bytes(X, ranks);
+  if (!scratch || scratch_bytes < need || ((uintptr_t)scratch & 255))
+    return fail(TS_ERR_WORKSPACE, "ts_fitness: need %zu bytes of 256-aligned scratch", need);
+  Bump b{static_cast<char*>(scratch)};
+  cudaStream_t st = (cudaStream_t)stream;
+  if (X->dtype == TS_F64) {
+    double* q = b.take<double>(fit_dense_scratch_elems<double>(*X, ranks));
+    double* acc = b.take<double>(2);
+    return launch_fit_dense<double>(*X, ranks, static_cast<const double*>(core),
+                                    reinterpret_cast<const double* const*>(factors), q, acc,
+                                    residual_out, st);
+  }
+  float* q = b.take<float>(fit_dense_scratch_elems<float>(*X, ranks));
+  double* acc = b.take<double>(2);
+  return launch_fit_dense<float>(*X, ranks, static_cast<const float*>(core),
+                                 reinterpret_cast<const float* const*>(factors), q, acc,
+                                 residual_out, st);
+}
+
+// ---------------------------------------------------------------- CP-Sketch-Tucker (Alg. 6)
+
+extern "C" ts_status cp_via_tucker_workspace_bytes(const ts_tensor* X, int32_t R_cp,
+                                                   const int32_t* tucker_ranks, int32_t m,
+                                                   int32_t tucker_sweeps, const ts_options* opt,
+                                                   size_t* bytes_out) {
+  clear_error();
+  (void)X; (void)R_cp; (void)tucker_ranks; (void)m; (void)tucker_sweeps; (void)opt;
+  if (bytes_out) *bytes_out = 0;
+  return fail(TS_ERR_UNSUPPORTED, "cp_via_tucker: not built yet");
+}
+
+extern "C" ts_status cp_via_tucker(const ts_tensor* X, int32_t R_cp, const int32_t* tucker_ranks,
+                                   int32_t m, int32_t tucker_sweeps, int32_t cp_sweeps,
+                                   const ts_options* opt, void* workspace, size_t workspace_bytes,
+                                   void* const* cp_factors_out, double* residual_out,
+                                   ts_stream stream) {
+  clear_error();
+  (void)X; (void)R_cp; (void)tucker_ranks; (void)m; (void)tucker_sweeps; (void)cp_sweeps;
+  (void)opt; (void)workspace; (void)workspace_bytes; (void)cp_factors_out; (void)residual_out;
+  (void)stream;
+  return fail(TS_ERR_UNSUPPORTED, "cp_via_tucker: not built yet");
+}

@@ -1,0 +1,71 @@
+"""The C-ABI library loads on the host and exports every entry point include/tsketch.h declares."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "tsketch.h")
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s+\*?([A-Za-z_][A-Za-z0-9_]*)\s*\(",
+                       src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "while", "return", "sizeof")))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_2104_01101_gb300 import build
+    return build.build_library()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for want in ["tucker_als_sketched", "tensorsketch_apply", "tensorsketch_input",
+                 "range_finder_init", "cp_via_tucker", "ts_hash_table", "ts_last_error",
+                 "ts_lrls_solve", "ts_leverage_sketch", "ts_fitness"]:
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_binding_prototypes_cover_the_header(libpath):
+    from paper_2104_01101_gb300 import tsketch
+    assert set(declared_functions()) == set(tsketch.exported_symbols())
+
+
+def test_host_side_validation_without_gpu(libpath):
+    # Argument checks run before any CUDA call, so they work on a host without a GPU.
+    from paper_2104_01101_gb300 import tsketch
+    L = tsketch.lib()
+    assert L.ts_hash_table(0, 1, 0, 0, 0, -5, 10, None, None) == 1
+    assert b"table_out" in L.ts_last_error()
+    d = tsketch._Tensor()
+    d.order = 1
+    assert L.tensorsketch_input(ctypes.byref(d), 0, None, 10, None, None) == 2
+    assert b"order" in L.ts_last_error()
+    # workspace query of an invalid problem (rank >= dimension) reports TS_ERR_SHAPE
+    d.order = 3
+    for k in range(3):
+        d.dims[k] = 10
+    d.format, d.dtype, d.values = 0, 0, 1
+    rk = (ctypes.c_int32 * 3)(10, 2, 2)
+    opt = tsketch._Options()
+    n = ctypes.c_size_t(0)
+    assert L.tucker_als_workspace_bytes(ctypes.byref(d), rk, 0, 50, 1, ctypes.byref(opt),
+                                        ctypes.byref(n)) == 2
+    rk = (ctypes.c_int32 * 3)(2, 2, 2)
+    assert L.tucker_als_workspace_bytes(ctypes.byref(d), rk, 0, 3, 1, ctypes.byref(opt),
+                                        ctypes.byref(n)) == 2      # m < prod of other ranks
+    assert L.tucker_als_workspace_bytes(ctypes.byref(d), rk, 0, 50, 1, ctypes.byref(opt),
+                                        ctypes.byref(n)) == 0
+    assert n.value > 0

@@ -1,0 +1,136 @@
+"""End-to-end parity of Sketch-Tucker-ALS (Alg. 4) on the GPU against the FP64 oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import tucker
+from paper_2104_01101_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ts():
+    from paper_2104_01101_gb300 import build, tsketch
+    build.build_library()
+    tsketch.lib()
+    return tsketch
+
+
+def proj(A):
+    return A @ A.T
+
+
+@pytest.mark.parametrize("kind,solve", [("ts", "rsvd"), ("ts", "exact"), ("lev", "rsvd"),
+                                        ("lev", "exact")])
+def test_small_dense_fp64_matches_oracle(ts, kind, solve):
+    # 40^3 FP64, Tucker rank 5 plus 1e-3 noise, m = 400, 5 sweeps, RRF init
+    dims, ranks, m, sweeps, seed = (40, 40, 40), (5, 5, 5), 400, 5, 1
+    T, _, _ = synth.dense_tucker(dims, ranks, 1e-3, seed=0)
+    k = ts.TENSORSKETCH if kind == "ts" else ts.LEVERAGE
+    s = ts.SOLVE_RSVD if solve == "rsvd" else ts.SOLVE_EXACT
+    core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, sweeps, kind=k,
+                                            seed=seed, solve=s, track_fit=True)
+    c_o, f_o, r_o = tucker.sketch_tucker_als(T, ranks, m, sweeps, seed=seed, kind=kind,
+                                             solve=solve, track_fit=True)
+    assert np.allclose(res.cpu().numpy(), r_o, rtol=1e-9, atol=0)
+    for n in range(3):
+        assert np.abs(proj(fac[n].cpu().numpy()) - proj(f_o[n])).max() < 1e-9
+    Tg = tucker.reconstruct(core.cpu().numpy(), [f.cpu().numpy() for f in fac])
+    To = tucker.reconstruct(c_o, f_o)
+    assert np.linalg.norm(Tg - To) <= 1e-9 * np.linalg.norm(To)
+
+
+@pytest.mark.parametrize("kind", ["ts", "lev"])
+def test_exact_recovery_noiseless(ts, kind):
+    T, _, _ = synth.dense_tucker((40, 40, 40), (5, 5, 5), 0.0, seed=2)
+    k = ts.TENSORSKETCH if kind == "ts" else ts.LEVERAGE
+    _, _, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), (5, 5, 5), 400, 1, kind=k,
+                                       seed=4, track_fit=True)
+    assert float(res[0]) < 1e-10
+
+
+def test_identity_sketch_equals_hooi_on_gpu(ts):
+    # Identity TensorSketch (degenerate tables, S = +1, m = s^2) with the exact solve
+    # reproduces HOOI from the same initial factors.
+    dims, ranks = (6, 6, 6), (3, 2, 3)
+    T, _, _ = synth.dense_tucker(dims, ranks, 0.3, seed=4)
+    init = tucker.hosvd(T, ranks)
+    Tg = torch.from_numpy(T).cuda()
+    m = 36
+    # Drive the subproblem solve directly with the identity sketch (Z = P, Y = T_(n)^T).
+    A = [torch.from_numpy(a).cuda() for a in init]
+    c_h, f_h = tucker.hooi(T, ranks, 3, init=init)
+    for sweep in range(3):
+        for n in range(3):
+            others = [k for k in range(3) if k != n]
+            tabs = []
+            for j, k in enumerate(others):
+                stride = int(np.prod([dims[l] for l in others[j + 1:]]))
+                tabs.append(torch.from_numpy((np.arange(dims[k]) * stride).astype(np.int32)).cuda())
+            Z = ts.tensorsketch_apply([A[k] for k in others], tabs, m)
+            Y = ts.tensorsketch_input(Tg, n, [tabs[others.index(k)] if k in others else None
+                                              for k in range(3)], m)
+            _, An = ts.lrls_solve(Z, Y, ranks[n], ts.SOLVE_EXACT)
+            A[n] = An
+    for n in range(3):
+        assert np.abs(A[n].cpu().numpy() - f_h[n]).max() < 1e-10
+
+
+def test_medium_dense_fp32_matches_oracle(ts):
+    # 120^3 FP32 with the 400^3 workload's structure (decaying core, rank 10, noise 1e-2)
+    dims, ranks, m, sweeps, seed = (120, 120, 120), (10, 10, 10), 2000, 3, 5
+    T, _, _ = synth.dense_tucker(dims, ranks, 1e-2, seed=3, core_decay=0.9, dtype=np.float32)
+    core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, sweeps,
+                                            seed=seed, rrf_k1=15, track_fit=True)
+    _, f_o, r_o = tucker.sketch_tucker_als(T.astype(np.float64), ranks, m, sweeps, seed=seed,
+                                           rrf_k1=15, track_fit=True)
+    assert np.allclose(res.cpu().numpy(), r_o, rtol=1e-5, atol=0)
+    for n in range(3):
+        assert np.abs(proj(fac[n].double().cpu().numpy()) - proj(f_o[n])).max() < 1e-4
+
+
+def test_full_size_fp32_workload_matches_oracle(ts):
+    # The benchmark workload itself: 400^3 FP32, rank 10, m = 2000, RRF k1 = 15, 10 sweeps.
+    dims, ranks, m, sweeps, seed = (400, 400, 400), (10, 10, 10), 2000, 10, 7
+    T, _, _ = synth.dense_tucker(dims, ranks, 1e-2, seed=1, core_decay=0.9, dtype=np.float32)
+    core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, sweeps,
+                                            seed=seed, rrf_k1=15)
+    T64 = T.astype(np.float64)
+    del T
+    c_o, f_o, _ = tucker.sketch_tucker_als(T64, ranks, m, sweeps, seed=seed, rrf_k1=15)
+    r_final = tucker.residual(T64, c_o, f_o)
+    assert abs(float(res[0]) - r_final) <= 1e-5 * r_final
+    for n in range(3):
+        assert np.abs(proj(fac[n].double().cpu().numpy()) - proj(f_o[n])).max() < 1e-4
+
+
+def test_order4_and_resketch(ts):
+    dims, ranks, m = (20, 18, 16, 14), (3, 3, 2, 2), 300
+    T, _, _ = synth.dense_tucker(dims, ranks, 1e-2, seed=6)
+    core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, 3, seed=3,
+                                            resketch=True, track_fit=True)
+    _, f_o, r_o = tucker.sketch_tucker_als(T, ranks, m, 3, seed=3, resketch=True, track_fit=True)
+    assert np.allclose(res.cpu().numpy(), r_o, rtol=1e-9)
+
+
+def test_coo_tensor_matches_oracle(ts):
+    dims, ranks, m = (300, 250, 200), (4, 4, 4), 400
+    idx, vals, _, _ = synth.coo_zipf_tucker(dims, 60000, ranks, seed=5, val_dtype=np.float64)
+    X = ts.Coo(torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(), dims)
+    core, fac, _ = ts.tucker_als_sketched(X, ranks, m, 2, seed=8, want_residual=False)
+    c_o, f_o, _ = tucker.sketch_tucker_als(tucker.Coo(idx.astype(np.int64), vals, dims), ranks, m,
+                                           2, seed=8)
+    for n in range(3):
+        assert np.abs(proj(fac[n].cpu().numpy()) - proj(f_o[n])).max() < 1e-9
+
+
+def test_shape_errors(ts):
+    T = torch.zeros((10, 10, 10), dtype=torch.float64, device="cuda")
+    with pytest.raises(ts.TsError) as e:
+        ts.tucker_als_sketched(T, (10, 2, 2), 50, 1)
+    assert e.value.status == 2
+    with pytest.raises(ts.TsError) as e:
+        ts.tucker_als_sketched(T, (3, 3, 3), 8, 1)     # m < 9
+    assert e.value.status == 2

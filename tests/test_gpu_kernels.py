@@ -1,0 +1,232 @@
+"""Parity of each hot-path row (CUDA via the C ABI) against the FP64 oracle."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import rng, sketch, solve, tucker
+from paper_2104_01101_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ts():
+    from paper_2104_01101_gb300 import build, tsketch
+    build.build_library()
+    tsketch.lib()
+    return tsketch
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def packed_tables(seed, dims, n, m, purpose=1, sweep=0):
+    out = {}
+    for k in range(len(dims)):
+        if k != n:
+            b, s = rng.hash_table(seed, purpose, sweep, n, k, dims[k], m)
+            out[k] = (b, s, dev(rng.pack_table(b, s)))
+    return out
+
+
+# ---------------------------------------------------------------- a1 hash tables
+
+@pytest.mark.parametrize("purpose,sweep,n,k,size,nbins", [
+    (1, 0, 0, 1, 40, 400), (1, 0, 2, 1, 400, 2000), (2, 0, 1, 0, 4000, 115),
+    (1, 7, 3, 2, 200000, 4096), (1, 0, 0, 0, 1, 1), (2, 3, 255, 255, 3001, 97)])
+def test_hash_tables_bit_exact(ts, purpose, sweep, n, k, size, nbins):
+    seed = 0xDEADBEEF12345
+    got = ts.hash_table(seed, purpose, sweep, n, k, size, nbins).cpu().numpy()
+    b, s = rng.hash_table(seed, purpose, sweep, n, k, size, nbins)
+    assert np.array_equal(got, rng.pack_table(b, s))
+
+
+# ---------------------------------------------------------------- a2 + a3 TensorSketch of a chain
+
+@pytest.mark.parametrize("dims,ranks,m", [
+    ((40, 40), (5, 5), 400),            # small dense workload shapes
+    ((400, 400), (10, 10), 2000),       # 400^3 workload shapes
+    ((33, 29, 17), (3, 4, 2), 210),     # three factors, m = 2*3*5*7
+    ((50,), (7,), 128),                 # single factor (order-2 tensors)
+    ((21, 19), (4, 3), 2 * 97),         # large prime factor in m
+    ((300, 300), (25, 25), 3000),       # 300^3 rank-25 shapes
+])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_tensorsketch_apply_matches_explicit_kronecker(ts, dims, ranks, m, dtype):
+    g = np.random.default_rng(1)
+    factors = [np.linalg.qr(g.standard_normal((s, R)))[0] for s, R in zip(dims, ranks)]
+    tabs = [rng.hash_table(5, 1, 0, 9, j, s, m) for j, s in enumerate(dims)]
+    if np.prod(dims) * np.prod(ranks) <= 3e7:
+        want = sketch.ts_apply_explicit(factors, tabs, m)
+    else:
+        want = sketch.ts_apply_fft(factors, tabs, m)
+    Z = ts.tensorsketch_apply([dev(f, dtype) for f in factors],
+                              [dev(rng.pack_table(*t)) for t in tabs], m).cpu().numpy()
+    tol = 1e-12 if dtype == torch.float64 else 1e-5
+    assert np.linalg.norm(Z - want) <= tol * np.linalg.norm(want)
+
+
+# ---------------------------------------------------------------- a4 input sketch
+
+@pytest.mark.parametrize("dims,m", [((40, 40, 40), 400), ((13, 7, 11), 50), ((9, 8, 7, 6), 300),
+                                    ((64, 3), 17)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_input_sketch_dense(ts, dims, m, dtype):
+    T = np.random.default_rng(2).standard_normal(dims)
+    Tg = dev(T, dtype)
+    for n in range(len(dims)):
+        tabs = packed_tables(7, dims, n, m)
+        Y = ts.tensorsketch_input(Tg, n, [tabs[k][2] if k in tabs else None
+                                          for k in range(len(dims))], m).cpu().numpy()
+        want = sketch.input_sketch_dense(T.astype(np.float64) if dtype == torch.float64
+                                         else T.astype(np.float32).astype(np.float64),
+                                         n, [tabs[k][:2] for k in sorted(tabs)], m)
+        tol = 1e-12 if dtype == torch.float64 else 1e-5
+        assert np.linalg.norm(Y - want) <= tol * np.linalg.norm(want)
+
+
+def test_input_sketch_dense_full_size_sampled_columns(ts):
+    # The 400^3 FP32 workload: compare a few whole columns Y_n[:, i] with the oracle
+    # applied to the slab T(i along mode n), plus the squared-norm invariant.
+    dims, m = (400, 400, 400), 2000
+    T, _, _ = synth.dense_tucker(dims, (10, 10, 10), 1e-2, seed=5, core_decay=0.9,
+                                 dtype=np.float32)
+    Tg = dev(T)
+    for n in range(3):
+        tabs = packed_tables(9, dims, n, m)
+        Y = ts.tensorsketch_input(Tg, n, [tabs[k][2] if k in tabs else None for k in range(3)], m)
+        Y = Y.cpu().numpy().astype(np.float64)
+        S = sketch.tensorsketch_sparse([tabs[k][:2] for k in sorted(tabs)], m)
+        for i in (0, 17, 399):
+            slab = np.take(T, i, axis=n).astype(np.float64).reshape(-1)
+            want = S @ slab
+            assert np.linalg.norm(Y[:, i] - want) <= 1e-5 * np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_input_sketch_coo_with_duplicates_and_empty(ts, dtype):
+    dims, m = (2000, 1500, 1000, 700), 512
+    idx, vals, _, _ = synth.coo_zipf_tucker(dims, 200000, (3, 3, 3, 3), seed=4,
+                                            val_dtype=np.float64)
+    X = ts.Coo(dev(idx), dev(vals, dtype), dims)
+    for n in range(4):
+        tabs = packed_tables(3, dims, n, m)
+        Y = ts.tensorsketch_input(X, n, [tabs[k][2] if k in tabs else None for k in range(4)], m)
+        want = sketch.input_sketch_coo(idx, vals if dtype == torch.float64 else
+                                       vals.astype(np.float32).astype(np.float64),
+                                       dims, n, [tabs[k][:2] for k in sorted(tabs)], m)
+        tol = 1e-12 if dtype == torch.float64 else 1e-5
+        assert np.linalg.norm(Y.cpu().numpy() - want) <= tol * np.linalg.norm(want)
+    empty = ts.Coo(torch.zeros((4, 0), dtype=torch.int32, device="cuda"),
+                   torch.zeros(0, dtype=dtype, device="cuda"), dims)
+    tabs = packed_tables(3, dims, 0, m)
+    Y = ts.tensorsketch_input(empty, 0, [tabs[k][2] if k in tabs else None for k in range(4)], m)
+    assert float(Y.abs().max()) == 0.0
+
+
+# ---------------------------------------------------------------- a6 Init-RRF
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-10), (torch.float32, 1e-5)])
+def test_range_finder_matches_oracle(ts, dtype, tol):
+    dims, ranks = (40, 36, 30), (5, 4, 6)
+    T, _, _ = synth.dense_tucker(dims, ranks, 1e-3, seed=6)
+    Tx = T if dtype == torch.float64 else T.astype(np.float32).astype(np.float64)
+    for n in (1, 2):
+        k1, k2 = tucker.rrf_sizes(dims, n, ranks[n], 400)
+        A = ts.range_finder_init(dev(T, dtype), n, ranks[n], k1, k2, seed=21).cpu().numpy()
+        want = tucker.init_rrf(Tx, n, ranks[n], k1, k2, seed=21)
+        assert np.abs(A - want).max() <= tol * 10
+        assert np.abs(A @ A.T - want @ want.T).max() <= tol
+
+
+# ---------------------------------------------------------------- a7 + a8 sketched solve
+
+def _solve_problem(seed, m, r, s, R, noise):
+    g = np.random.default_rng(seed)
+    Z = g.standard_normal((m, r)) / np.sqrt(m)
+    X0 = g.standard_normal((r, R)) @ g.standard_normal((R, s))
+    return Z, Z @ X0 + noise * g.standard_normal((m, s))
+
+
+@pytest.mark.parametrize("m,r,s,R", [(400, 25, 40, 5), (2000, 100, 400, 10), (97, 13, 31, 3),
+                                     (3000, 125, 300, 12)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_rsvd_lrls_matches_oracle(ts, m, r, s, R, dtype):
+    Z, Y = _solve_problem(3, m, r, s, R, 0.05)
+    if dtype == torch.float32:
+        Z = Z.astype(np.float32).astype(np.float64)
+        Y = Y.astype(np.float32).astype(np.float64)
+    k = solve.rsvd_oversampled_rank(R, 5, r, s)
+    Om = rng.gaussian(77, rng.make_tag(4, 2, 1, 0), s * k).reshape(s, k)
+    Cw, Aw = solve.rsvd_lrls(Z, Y, R, Om)
+    Cg, Ag = ts.lrls_solve(dev(Z, dtype), dev(Y, dtype), R, ts.SOLVE_RSVD, seed=77, sweep=2, n=1)
+    Bw, Bg = Cw @ Aw.T, Cg.cpu().numpy() @ Ag.cpu().numpy().T
+    tol = 1e-11 if dtype == torch.float64 else 1e-5
+    assert np.linalg.norm(Bg - Bw) <= tol * np.linalg.norm(Bw)
+    assert np.abs(Ag.cpu().numpy() - Aw).max() <= (1e-9 if dtype == torch.float64 else 1e-4)
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_exact_lrls_matches_oracle(ts, dtype):
+    Z, Y = _solve_problem(4, 400, 25, 40, 5, 0.1)
+    if dtype == torch.float32:
+        Z = Z.astype(np.float32).astype(np.float64)
+        Y = Y.astype(np.float32).astype(np.float64)
+    Cw, Aw = solve.lrls_exact(Z, Y, 5)
+    Cg, Ag = ts.lrls_solve(dev(Z, dtype), dev(Y, dtype), 5, ts.SOLVE_EXACT)
+    Bw, Bg = Cw @ Aw.T, Cg.cpu().numpy() @ Ag.cpu().numpy().T
+    tol = 1e-11 if dtype == torch.float64 else 1e-5
+    assert np.linalg.norm(Bg - Bw) <= tol * np.linalg.norm(Bw)
+
+
+def test_rsvd_exact_rank_input_equals_exact_solve(ts):
+    # noiseless rank-R right-hand side: RSVD-LRLS is exact (degenerate case of Alg. 5)
+    Z, Y = _solve_problem(5, 300, 20, 60, 4, 0.0)
+    C1, A1 = ts.lrls_solve(dev(Z), dev(Y), 4, ts.SOLVE_RSVD, seed=1)
+    C2, A2 = ts.lrls_solve(dev(Z), dev(Y), 4, ts.SOLVE_EXACT)
+    B1 = (C1 @ A1.t()).cpu().numpy()
+    B2 = (C2 @ A2.t()).cpu().numpy()
+    assert np.linalg.norm(B1 - B2) <= 1e-10 * np.linalg.norm(B2)
+
+
+# ---------------------------------------------------------------- a5 leverage sampling
+
+@pytest.mark.parametrize("dims,ranks,m", [((40, 40, 40), (5, 5, 5), 400), ((30, 20, 25, 10), (3, 2, 4, 2), 300)])
+def test_leverage_sketch_samples_bit_exact(ts, dims, ranks, m):
+    T, _, A = synth.dense_tucker(dims, ranks, 0.01, seed=8)
+    Tg = dev(T)
+    Ag = [dev(a) for a in A]
+    for n in range(len(dims)):
+        Zg, Yg, smp = ts.leverage_sketch(Tg, n, Ag, m, seed=5, sweep=3)
+        Zw, Yw, sw, _ = sketch.leverage_sketch_dense(T, n, A, m, seed=5, sweep=3)
+        assert np.array_equal(smp.cpu().numpy(), sw)
+        assert np.allclose(Zg.cpu().numpy(), Zw, rtol=1e-13, atol=0)
+        assert np.allclose(Yg.cpu().numpy(), Yw, rtol=1e-13, atol=0)
+
+
+# ---------------------------------------------------------------- a9 fitness
+
+@pytest.mark.parametrize("dims,ranks,dtype", [((40, 40, 40), (5, 5, 5), torch.float64),
+                                              ((400, 400, 400), (10, 10, 10), torch.float32),
+                                              ((30, 20, 25, 10), (3, 2, 4, 2), torch.float64),
+                                              ((123, 77), (6, 5), torch.float32)])
+def test_fitness_matches_direct_reconstruction(ts, dims, ranks, dtype):
+    T, core, A = synth.dense_tucker(dims, ranks, 1e-2, seed=9,
+                                    dtype=np.float64 if dtype == torch.float64 else np.float32)
+    core = core * 1.01        # a model that is not the exact projection
+    Tx = T.astype(np.float64)
+    coreg = dev(core, dtype)
+    Ag = [dev(a, dtype) for a in A]
+    if dtype == torch.float32:
+        core = coreg.double().cpu().numpy()
+        A = [a.double().cpu().numpy() for a in Ag]
+    want = tucker.residual(Tx, core, A)
+    got = ts.fitness_residual(dev(T), coreg, Ag)
+    tol = 1e-12 if dtype == torch.float64 else 1e-5
+    assert abs(got - want) <= tol * want

@@ -334,6 +334,9 @@ class TuckerPlan:
     def set_phase_events(self, events):
         """Record the 6 phase events of the driver (torch.cuda.Event list) on every run."""
         self._events = events
+        for e in events or []:
+            e.record()          # torch creates the CUDA event lazily, on first record
+        torch.cuda.synchronize()
         self._ev_arr = (C.c_void_p * 6)(*[e.cuda_event for e in events]) if events else None
         self.opt.phase_events = (C.cast(self._ev_arr, C.POINTER(C.c_void_p))
                                  if events else None)

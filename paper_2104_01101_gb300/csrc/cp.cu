@@ -1,0 +1,207 @@
+// CP-ALS on the Tucker core (Alg. 2 applied inside Alg. 6).  The core has only
+// prod R_n entries, so each kernel here is a small one-shot map; the normal
+// equations of every mode update use the Khatri-Rao product of the other factors
+// (first factor slowest, Sec. 2.1) and the Hadamard product of their Grams.
+#include "internal.cuh"
+
+namespace ts {
+
+struct CoreDims {
+  int order;
+  int ranks[TS_MAX_ORDER];
+};
+
+template <typename T>
+struct FacPtrs {
+  const T* p[TS_MAX_ORDER];
+};
+
+// out (R_n x prod_{k != n} R_k) = mode-n unfolding of the C-order core.
+template <typename T>
+__global__ void k_unfold(CoreDims d, int n, const T* __restrict__ C, T* __restrict__ out) {
+  long total = 1;
+  for (int k = 0; k < d.order; ++k) total *= d.ranks[k];
+  const long K = total / d.ranks[n];
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    long x = e, col = 0, stride = 1;
+    int row = 0;
+    for (int k = d.order - 1; k >= 0; --k) {
+      const int rk = (int)(x % d.ranks[k]);
+      x /= d.ranks[k];
+      if (k == n) {
+        row = rk;
+      } else {
+        col += rk * stride;
+        stride *= d.ranks[k];
+      }
+    }
+    out[row * K + col] = C[e];
+  }
+}
+
+// KR (prod_{k != n} R_k x Rc): row (r_k)_{k != n} in C order, column c:
+// prod_k A_k(r_k, c).
+template <typename T>
+__global__ void k_khatri_rao(CoreDims d, int n, int Rc, FacPtrs<T> A,
+                             T* __restrict__ KR) {
+  long K = 1;
+  for (int k = 0; k < d.order; ++k)
+    if (k != n) K *= d.ranks[k];
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < K * Rc;
+       e += (long)gridDim.x * blockDim.x) {
+    const long row = e / Rc;
+    const int c = (int)(e % Rc);
+    long x = row;
+    T v = 1;
+    for (int k = d.order - 1; k >= 0; --k) {
+      if (k == n) continue;
+      const int rk = (int)(x % d.ranks[k]);
+      x /= d.ranks[k];
+      v *= A.p[k][rk * Rc + c];
+    }
+    KR[e] = v;
+  }
+}
+
+// Gam (Rc x Rc) = Hadamard product over k != n of A_k^T A_k.
+template <typename T>
+__global__ void k_gram_hadamard(CoreDims d, int n, int Rc, FacPtrs<T> A,
+                                T* __restrict__ Gam) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Rc * Rc; e += gridDim.x * blockDim.x) {
+    const int a = e / Rc, b = e % Rc;
+    T v = 1;
+    for (int k = 0; k < d.order; ++k) {
+      if (k == n) continue;
+      T g = 0;
+      for (int i = 0; i < d.ranks[k]; ++i) g += A.p[k][i * Rc + a] * A.p[k][i * Rc + b];
+      v *= g;
+    }
+    Gam[e] = v;
+  }
+}
+
+// out (cols x rows) = in^T (in is rows x cols).
+template <typename T>
+__global__ void k_transpose(int rows, int cols, const T* __restrict__ in, T* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < rows * cols; e += gridDim.x * blockDim.x)
+    out[(e % cols) * rows + e / cols] = in[e];
+}
+
+// Superdiagonal core of a CP model (Rc^order entries, ones on the diagonal).
+template <typename T>
+__global__ void k_superdiag(int order, int Rc, T* __restrict__ D) {
+  long total = 1, step = 0, p = 1;
+  for (int k = 0; k < order; ++k) {
+    total *= Rc;
+    step += p;
+    p *= Rc;
+  }
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x)
+    D[e] = (e % step == 0) ? (T)1 : (T)0;
+}
+
+static int grid_for(long n) {
+  long b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 1024 ? 1024 : b));
+}
+
+template <typename T>
+size_t cp_core_scratch_elems(int order, const int* ranks, int Rc) {
+  long total = 1, Kmax = 0;
+  int Rmax = 0;
+  for (int k = 0; k < order; ++k) total *= ranks[k];
+  for (int n = 0; n < order; ++n) {
+    const long K = total / ranks[n];
+    if (K > Kmax) Kmax = K;
+    if (ranks[n] > Rmax) Rmax = ranks[n];
+  }
+  const int E = Rmax > Rc ? Rmax : Rc;
+  // unfold, KR, M, Gam, X, eigen K, partial
+  return (size_t)(Rmax * Kmax + Kmax * Rc + Rmax * Rc + Rc * Rc + Rc * Rmax + E * E) +
+         32 * (size_t)(Rmax * Rc > Rmax * Rmax ? Rmax * Rc : Rmax * Rmax) + 64 * 6;
+}
+
+// HOSVD initialisation (Sec. 7.2) and `sweeps` CP-ALS sweeps (Alg. 2) on the core.
+// A[k] (ranks[k] x Rc) are written; scratch holds cp_core_scratch_elems<T>() values.
+template <typename T>
+ts_status cp_als_core(int order, const int* ranks, int Rc, int sweeps, const T* core, T* const* A,
+                      T* scratch, int* flag, cudaStream_t st) {
+  CoreDims d{};
+  d.order = order;
+  FacPtrs<T> fp{};
+  for (int k = 0; k < order; ++k) fp.p[k] = A[k];
+  long total = 1, Kmax = 0;
+  int Rmax = 0;
+  for (int k = 0; k < order; ++k) {
+    d.ranks[k] = ranks[k];
+    total *= ranks[k];
+  }
+  for (int n = 0; n < order; ++n) {
+    if (total / ranks[n] > Kmax) Kmax = total / ranks[n];
+    if (ranks[n] > Rmax) Rmax = ranks[n];
+  }
+  const int E = Rmax > Rc ? Rmax : Rc;
+  T* Cn = scratch;
+  T* KR = Cn + Rmax * Kmax;
+  T* M = KR + Kmax * Rc;
+  T* Gam = M + Rmax * Rc;
+  T* X = Gam + Rc * Rc;
+  T* Ke = X + Rc * Rmax;
+  T* P = Ke + E * E;
+  const size_t PE = 32 * (size_t)(Rmax * Rc > Rmax * Rmax ? Rmax * Rc : Rmax * Rmax);
+  CoreMap none{};
+  // HOSVD of the core: leading Rc eigenvectors of C_(n) C_(n)^T, canonical signs.
+  for (int n = 0; n < order; ++n) {
+    const long K = total / ranks[n];
+    k_unfold<T><<<grid_for(total), 256, 0, st>>>(d, n, core, Cn);
+    TS_LAUNCH_CHECK();
+    TS_TRY(gemm<T>(ranks[n], ranks[n], (int)K, 1.0, MatView<T>{Cn, K, 1}, MatView<T>{Cn, 1, K},
+                   0.0, OutView<T>{Ke, ranks[n], 1}, P, PE, st));
+    TS_TRY(launch_eig_small<T>(ranks[n], Rc, Ke, nullptr, ranks[n], nullptr, nullptr, M, flag,
+                               st));
+    TS_TRY(launch_finalize<T>(ranks[n], Rc, M, A[n], nullptr, 0, nullptr, none, st));
+  }
+  for (int sweep = 0; sweep < sweeps; ++sweep) {
+    for (int n = 0; n < order; ++n) {
+      const long K = total / ranks[n];
+      k_unfold<T><<<grid_for(total), 256, 0, st>>>(d, n, core, Cn);
+      TS_LAUNCH_CHECK();
+      k_khatri_rao<T><<<grid_for(K * Rc), 256, 0, st>>>(d, n, Rc, fp, KR);
+      TS_LAUNCH_CHECK();
+      // MTTKRP: M = C_(n) KR (R_n x Rc)
+      TS_TRY(gemm<T>(ranks[n], Rc, (int)K, 1.0, MatView<T>{Cn, K, 1}, MatView<T>{KR, Rc, 1}, 0.0,
+                     OutView<T>{M, Rc, 1}, P, PE, st));
+      k_gram_hadamard<T><<<grid_for((long)Rc * Rc), 256, 0, st>>>(d, n, Rc, fp, Gam);
+      TS_LAUNCH_CHECK();
+      // A_n = M Gam^{-1}: solve Gam X = M^T, then A_n = X^T
+      k_transpose<T><<<grid_for((long)ranks[n] * Rc), 256, 0, st>>>(ranks[n], Rc, M, Ke);
+      TS_LAUNCH_CHECK();
+      TS_TRY(launch_chol_solve<T>(Rc, ranks[n], Gam, Ke, X, flag, st));
+      k_transpose<T><<<grid_for((long)ranks[n] * Rc), 256, 0, st>>>(Rc, ranks[n], X, A[n]);
+      TS_LAUNCH_CHECK();
+    }
+  }
+  return TS_OK;
+}
+
+template <typename T>
+ts_status launch_superdiag(int order, int Rc, T* D, cudaStream_t st) {
+  long total = 1;
+  for (int k = 0; k < order; ++k) total *= Rc;
+  k_superdiag<T><<<grid_for(total), 256, 0, st>>>(order, Rc, D);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+#define TS_INST(T)                                                                           \
+  template size_t cp_core_scratch_elems<T>(int, const int*, int);                           \
+  template ts_status cp_als_core<T>(int, const int*, int, int, const T*, T* const*, T*, int*, \
+                                    cudaStream_t);                                          \
+  template ts_status launch_superdiag<T>(int, int, T*, cudaStream_t);
+TS_INST(float)
+TS_INST(double)
+#undef TS_INST
+
+}  // namespace ts

@@ -110,6 +110,18 @@ ts_status launch_leverage(const ts_tensor& X, int mode, const int* ranks, const 
                           int m, uint64_t seed, int sweep, T* Z, T* Y, int32_t* samples,
                           double* scratch, cudaStream_t st);
 
+// ---------------------------------------------------------------- cp.cu
+// HOSVD initialisation and CP-ALS sweeps on a core of the given ranks; A[k] is
+// ranks[k] x Rc.  scratch: cp_core_scratch_elems<T>() values.
+template <typename T>
+size_t cp_core_scratch_elems(int order, const int* ranks, int Rc);
+template <typename T>
+ts_status cp_als_core(int order, const int* ranks, int Rc, int sweeps, const T* core, T* const* A,
+                      T* scratch, int* flag, cudaStream_t st);
+// D (Rc^order, C order) = superdiagonal tensor of ones.
+template <typename T>
+ts_status launch_superdiag(int order, int Rc, T* D, cudaStream_t st);
+
 // ---------------------------------------------------------------- fit.cu
 template <typename T>
 size_t fit_dense_scratch_elems(const ts_tensor& X, const int* ranks);

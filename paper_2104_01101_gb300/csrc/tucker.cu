@@ -809,14 +809,101 @@ extern "C" ts_status ts_fitness(const ts_tensor* X, const int32_t* ranks, const 
 
 // ---------------------------------------------------------------- CP-Sketch-Tucker (Alg. 6)
 
+namespace ts {
+
+static ts_status cp_check(const ts_tensor* X, int R_cp, const int32_t* tranks, int m, int sweeps,
+                          const ts_options* opt, bool want_residual, Shape& S) {
+  TS_TRY(plan_shape(X, tranks, TS_TENSORSKETCH, m, sweeps, opt, want_residual, S));
+  long core = 1;
+  int rmin = 1 << 30;
+  for (int k = 0; k < X->order; ++k) {
+    core *= tranks[k];
+    if (tranks[k] < rmin) rmin = tranks[k];
+  }
+  if (R_cp < 1 || R_cp > rmin || R_cp > kMaxEig || core > 65536)
+    return fail(TS_ERR_SHAPE, "cp_via_tucker: need 1 <= R_cp <= min(tucker_ranks), R_cp <= %d and "
+                              "prod(tucker_ranks) <= 65536", kMaxEig);
+  return TS_OK;
+}
+
+// Alg. 6 layout: the Tucker workspace first, then the core, B^(n), A^(n), CP scratch
+// and the residual buffers.
+template <typename T>
+struct CpWork {
+  T* core;
+  T* B[TS_MAX_ORDER];
+  T* A[TS_MAX_ORDER];
+  T* cps;
+  T* D;
+  T* fq;
+  double* acc;
+};
+
+template <typename T>
+static size_t cp_carve(const ts_tensor& X, const Shape& S, int Rc, Bump& b, CpWork<T>& c) {
+  Work<T> w;
+  carve<T>(X, S, false, b, w);
+  long core = 1, dcore = 1;
+  int rk[TS_MAX_ORDER];
+  for (int k = 0; k < S.N; ++k) {
+    core *= S.ranks[k];
+    dcore *= Rc;
+    rk[k] = Rc;
+  }
+  c.core = b.take<T>((size_t)core);
+  for (int k = 0; k < S.N; ++k) c.B[k] = b.take<T>((size_t)X.dims[k] * S.ranks[k]);
+  for (int k = 0; k < S.N; ++k) c.A[k] = b.take<T>((size_t)S.ranks[k] * Rc);
+  c.cps = b.take<T>(cp_core_scratch_elems<T>(S.N, S.ranks, Rc));
+  c.D = b.take<T>((size_t)dcore);
+  c.fq = X.format == TS_DENSE ? b.take<T>(fit_dense_scratch_elems<T>(X, rk)) : nullptr;
+  c.acc = b.take<double>(2);
+  return b.off;
+}
+
+template <typename T>
+static ts_status cp_impl(const ts_tensor& X, const Shape& S, const ts_options& opt, int Rc,
+                         int cp_sweeps, void* ws, T* const* out, double* residual_out,
+                         cudaStream_t st) {
+  Bump b{static_cast<char*>(ws)};
+  CpWork<T> c;
+  cp_carve<T>(X, S, Rc, b, c);
+  ts_options o = opt;
+  o.track_fit = 0;
+  o.init_given = 0;
+  TS_TRY(als_impl<T>(X, S, o, ws, c.core, c.B, nullptr, st));
+  int* flag = static_cast<int*>(ws);  // the Tucker workspace's breakdown flag
+  TS_TRY(cp_als_core<T>(S.N, S.ranks, Rc, cp_sweeps, c.core, c.A, c.cps, flag, st));
+  for (int k = 0; k < S.N; ++k)
+    TS_TRY(gemm<T>((int)X.dims[k], Rc, S.ranks[k], 1.0, mv<T>(c.B[k], S.ranks[k], 1),
+                   mv<T>(c.A[k], Rc, 1), 0.0, ov<T>(out[k], Rc, 1), nullptr, 0, st));
+  if (residual_out) {
+    int rk[TS_MAX_ORDER];
+    for (int k = 0; k < S.N; ++k) rk[k] = Rc;
+    TS_TRY(launch_superdiag<T>(S.N, Rc, c.D, st));
+    TS_TRY(launch_fit_dense<T>(X, rk, c.D, (const T* const*)out, c.fq, c.acc, residual_out, st));
+  }
+  return TS_OK;
+}
+
+}  // namespace ts
+
 extern "C" ts_status cp_via_tucker_workspace_bytes(const ts_tensor* X, int32_t R_cp,
                                                    const int32_t* tucker_ranks, int32_t m,
                                                    int32_t tucker_sweeps, const ts_options* opt,
                                                    size_t* bytes_out) {
   clear_error();
-  (void)X; (void)R_cp; (void)tucker_ranks; (void)m; (void)tucker_sweeps; (void)opt;
-  if (bytes_out) *bytes_out = 0;
-  return fail(TS_ERR_UNSUPPORTED, "cp_via_tucker: not built yet");
+  if (!bytes_out) return fail(TS_ERR_INVALID_ARG, "cp_via_tucker_workspace_bytes: NULL bytes_out");
+  Shape S;
+  TS_TRY(cp_check(X, R_cp, tucker_ranks, m, tucker_sweeps, opt, false, S));
+  Bump b;
+  if (X->dtype == TS_F64) {
+    CpWork<double> c;
+    *bytes_out = cp_carve<double>(*X, S, R_cp, b, c);
+  } else {
+    CpWork<float> c;
+    *bytes_out = cp_carve<float>(*X, S, R_cp, b, c);
+  }
+  return TS_OK;
 }
 
 extern "C" ts_status cp_via_tucker(const ts_tensor* X, int32_t R_cp, const int32_t* tucker_ranks,
@@ -825,8 +912,20 @@ extern "C" ts_status cp_via_tucker(const ts_tensor* X, int32_t R_cp, const int32
                                    void* const* cp_factors_out, double* residual_out,
                                    ts_stream stream) {
   clear_error();
-  (void)X; (void)R_cp; (void)tucker_ranks; (void)m; (void)tucker_sweeps; (void)cp_sweeps;
-  (void)opt; (void)workspace; (void)workspace_bytes; (void)cp_factors_out; (void)residual_out;
-  (void)stream;
-  return fail(TS_ERR_UNSUPPORTED, "cp_via_tucker: not built yet");
+  Shape S;
+  TS_TRY(cp_check(X, R_cp, tucker_ranks, m, tucker_sweeps, opt, residual_out != nullptr, S));
+  if (cp_sweeps < 0) return fail(TS_ERR_SHAPE, "cp_via_tucker: cp_sweeps < 0");
+  if (!cp_factors_out) return fail(TS_ERR_INVALID_ARG, "cp_via_tucker: NULL cp_factors_out");
+  for (int k = 0; k < X->order; ++k)
+    if (!cp_factors_out[k]) return fail(TS_ERR_INVALID_ARG, "cp_via_tucker: factor %d NULL", k);
+  size_t need = 0;
+  TS_TRY(cp_via_tucker_workspace_bytes(X, R_cp, tucker_ranks, m, tucker_sweeps, opt, &need));
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255))
+    return fail(TS_ERR_WORKSPACE, "cp_via_tucker: need %zu bytes of 256-aligned workspace", need);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (X->dtype == TS_F64)
+    return cp_impl<double>(*X, S, *opt, R_cp, cp_sweeps, workspace,
+                           reinterpret_cast<double* const*>(cp_factors_out), residual_out, st);
+  return cp_impl<float>(*X, S, *opt, R_cp, cp_sweeps, workspace,
+                        reinterpret_cast<float* const*>(cp_factors_out), residual_out, st);
 }

@@ -361,6 +361,29 @@ class TuckerPlan:
         return int(self.workspace[:4].view(torch.int32).item())
 
 
+def cp_via_tucker(X, R_cp: int, tucker_ranks, m: int, tucker_sweeps: int, cp_sweeps: int,
+                  seed: int = 0, solve=SOLVE_RSVD, oversample: int = 5, rrf_k1=None, rrf_k2=None,
+                  want_residual=True):
+    """Alg. 6: returns (CP factors [dims[k] x R_cp], residual float or None)."""
+    dims = _dims(X)
+    N = len(dims)
+    opt = _options(seed, solve, oversample, rrf_k1, rrf_k2, False, False, False)
+    d = _desc(X)
+    rk = (C.c_int32 * N)(*tucker_ranks)
+    nbytes = C.c_size_t(0)
+    _check(lib().cp_via_tucker_workspace_bytes(C.byref(d), R_cp, rk, m, tucker_sweeps,
+                                               C.byref(opt), C.byref(nbytes)))
+    ws = _scratch(nbytes.value, X.device)
+    outs = [torch.empty((s, R_cp), dtype=X.dtype, device=X.device) for s in dims]
+    res = torch.zeros(1, dtype=torch.float64, device=X.device)
+    _check(lib().cp_via_tucker(C.byref(d), R_cp, rk, m, tucker_sweeps, cp_sweeps, C.byref(opt),
+                               _ptr(ws), ws.numel(), _ptr_array(outs),
+                               _ptr(res) if want_residual else None, _stream()))
+    if int(ws[:4].view(torch.int32).item()) != 0:
+        raise TsError(6, "numerical breakdown flagged by the device")
+    return outs, (float(res.item()) if want_residual else None)
+
+
 def tucker_als_sketched(X, ranks, m: int, sweeps: int, kind=TENSORSKETCH, seed: int = 0,
                         solve=SOLVE_RSVD, oversample: int = 5, rrf_k1=None, rrf_k2=None,
                         resketch=False, init_factors=None, track_fit=False,

@@ -134,3 +134,26 @@ def test_shape_errors(ts):
     with pytest.raises(ts.TsError) as e:
         ts.tucker_als_sketched(T, (3, 3, 3), 8, 1)     # m < 9
     assert e.value.status == 2
+
+
+def test_cp_via_tucker_fp64_matches_oracle(ts):
+    # Alg. 6 on a small collinear CP tensor: Tucker (6,6,6) then CP-ALS rank 4 on the core
+    T, _ = synth.cp_collinear((30, 28, 26), 4, 0.5, 1e-3, seed=2)
+    outs, res = ts.cp_via_tucker(torch.from_numpy(T).cuda(), 4, (6, 6, 6), 300, 3, 10, seed=3)
+    B, core, Bt, Ac = tucker.cp_sketch_tucker(T, 4, (6, 6, 6), 300, 3, 10, seed=3)
+    for k in range(3):
+        assert np.abs(outs[k].cpu().numpy() - B[k]).max() <= 1e-8 * np.abs(B[k]).max()
+    want = np.linalg.norm(T - tucker.cp_reconstruct(B)) / np.linalg.norm(T)
+    assert abs(res - want) <= 1e-9 * max(want, 1e-12)
+
+
+def test_cp_via_tucker_fp32_collinear_workload(ts):
+    # Collinear-CP workload scaled down: rank-10 CP with pairwise cosine 0.9, noise 1e-2,
+    # Tucker (12,12,12), m = 1500, 25 CP sweeps; FP32 against the FP64 oracle.
+    T, _ = synth.cp_collinear((60, 60, 60), 10, 0.9, 1e-2, seed=4, dtype=np.float32)
+    outs, res = ts.cp_via_tucker(torch.from_numpy(T).cuda(), 10, (12, 12, 12), 1500, 2, 25, seed=1)
+    B, _, _, _ = tucker.cp_sketch_tucker(T.astype(np.float64), 10, (12, 12, 12), 1500, 2, 25, seed=1)
+    want = np.linalg.norm(T - tucker.cp_reconstruct(B)) / np.linalg.norm(T)
+    got_direct = np.linalg.norm(T - tucker.cp_reconstruct([o.double().cpu().numpy() for o in outs]))
+    assert abs(res - got_direct / np.linalg.norm(T)) <= 1e-4 * res
+    assert abs(res - want) <= 0.05 * want + 1e-4

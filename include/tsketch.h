@@ -150,6 +150,34 @@ ts_status tensorsketch_apply(int32_t nf, const void* const* factors, const int64
                              int32_t dtype, void* Z_out, void* scratch, size_t scratch_bytes,
                              ts_stream stream);
 
+/* TensorSketch of a Kronecker chain WITHOUT caller scratch (no counterpart in the
+ * paper: this is a library convenience).
+ *
+ * Same operation, arguments and errors as tensorsketch_apply, but the scratch
+ * (twiddle table and factor spectra) lives in a fixed 8 MiB device array inside
+ * the library, so the call allocates nothing: it makes no cudaMalloc/cudaFree
+ * call and uses no allocating library routine.  It is meant for callers that
+ * cannot allocate device memory at the point of the call: a plug-in running
+ * inside a host application whose framework owns all device memory and hands it
+ * no allocator, or a latency-critical path where cudaMalloc's implicit device
+ * synchronisation is not acceptable.
+ * - Limit: problems needing more than tensorsketch_apply_static_scratch_capacity()
+ *   bytes (tensorsketch_apply_scratch_bytes) return TS_ERR_WORKSPACE.
+ * - Cost: every GPU that loads the library holds the 8 MiB array until the process
+ *   exits.
+ * - Set-up: the first call on each device looks up the array's device address
+ *   with that device current (cudaGetSymbolAddress) and caches it; make that first
+ *   call before any stream capture.
+ * - Concurrency: all calls share the one array and it keeps the last call's
+ *   contents; calls that overlap on the GPU (any streams, any host threads) race,
+ *   so order them (one stream, or events).  Nothing in it needs clearing: each
+ *   call writes every scratch element it reads. */
+size_t tensorsketch_apply_static_scratch_capacity(void);
+ts_status tensorsketch_apply_static_scratch(int32_t nf, const void* const* factors,
+                                            const int64_t* rows, const int32_t* cols,
+                                            const int32_t* const* tables, int32_t m,
+                                            int32_t dtype, void* Z_out, ts_stream stream);
+
 /* ------------------------------------------------------------------------- */
 /* One-pass sketch of the data tensor (Alg. 4, right-hand side Y = S^(n) T_(n)^T).
  *

@@ -69,6 +69,9 @@ _PROTOS = {
     "ts_hash_table": (I32, [U64, I32, I32, I32, I32, I64, I32, P, P]),
     "tensorsketch_apply_scratch_bytes": (SZ, [I32, C.POINTER(I32), I32, I32]),
     "tensorsketch_apply": (I32, [I32, PP, C.POINTER(I64), C.POINTER(I32), PP, I32, I32, P, P, SZ, P]),
+    "tensorsketch_apply_static_scratch_capacity": (SZ, []),
+    "tensorsketch_apply_static_scratch": (I32, [I32, PP, C.POINTER(I64), C.POINTER(I32), PP, I32,
+                                                I32, P, P]),
     "tensorsketch_input": (I32, [TP, I32, PP, I32, P, P]),
     "range_finder_init_scratch_bytes": (SZ, [TP, I32, I32, I32, I32]),
     "range_finder_init": (I32, [TP, I32, I32, I32, I32, U64, P, P, SZ, P]),
@@ -215,6 +218,22 @@ def tensorsketch_apply(factors, tables, m: int):
     scr = _scratch(nbytes, dev)
     _check(lib().tensorsketch_apply(nf, _ptr_array(factors), rows, cols, _ptr_array(tables), m, dt,
                                     _ptr(Zt), _ptr(scr), scr.numel(), _stream()))
+    return Zt.t()
+
+
+def tensorsketch_apply_static_scratch(factors, tables, m: int):
+    """As tensorsketch_apply, but the library uses its fixed device scratch array and
+    nothing is allocated for scratch (only the output Z is a new tensor here)."""
+    nf = len(factors)
+    dt = _dt(factors[0])
+    rows = (C.c_int64 * nf)(*[f.shape[0] for f in factors])
+    cols = (C.c_int32 * nf)(*[f.shape[1] for f in factors])
+    ncols = 1
+    for f in factors:
+        ncols *= f.shape[1]
+    Zt = torch.empty((ncols, m), dtype=factors[0].dtype, device=factors[0].device)
+    _check(lib().tensorsketch_apply_static_scratch(nf, _ptr_array(factors), rows, cols,
+                                                   _ptr_array(tables), m, dt, _ptr(Zt), _stream()))
     return Zt.t()
 
 

@@ -150,39 +150,70 @@ def run_ours(args, rank, world):
     T = make_input()
     Tg = torch.from_numpy(T).to(dev)
     Th = torch.from_numpy(T).pin_memory()
-    plan = ts.TuckerPlan(Tg, RANKS, M, SWEEPS, seed=SEED, rrf_k1=RRF_K1)
-    events = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
-    plan.set_phase_events(events)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # 256 MB > L2
-    stream = torch.cuda.current_stream()
 
     def barrier():
         if world > 1:
             dist.barrier()
 
-    for _ in range(args.warmup):
-        plan.run(Tg)
-    torch.cuda.synchronize()
-    if plan.numeric_flag():
-        raise RuntimeError("numerical breakdown flagged during warm-up")
-
-    step_ms, sketch_ms, sweeps_ms, rrf_ms = [], [], [], []
-    l0 = ts.kernel_launches()
-    barrier()
-    torch.cuda.synchronize()
-    with Clocks(dev.index) as clk:
-        for _ in range(args.steps):
-            flush.zero_()
+    def time_form(solve_fp64):
+        """K timed decompositions of one form.  Each step replays the captured graph and
+        is bracketed by CUDA events on the launching stream; the phase breakdown comes
+        from K more, uncaptured runs whose phase events the library records."""
+        plan = ts.TuckerPlan(Tg, RANKS, M, SWEEPS, seed=SEED, rrf_k1=RRF_K1,
+                             solve_fp64=solve_fp64, use_graph=True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(args.warmup):
             plan.run(Tg)
-            torch.cuda.synchronize()
-            step_ms.append(events[0].elapsed_time(events[5]))
-            rrf_ms.append(events[0].elapsed_time(events[1]))
-            sketch_ms.append(events[2].elapsed_time(events[3]))
-            sweeps_ms.append(events[3].elapsed_time(events[4]))
+        torch.cuda.synchronize()
+        if plan.numeric_flag():
+            raise RuntimeError("numerical breakdown flagged during warm-up")
+        rec = {"step": [], "rrf": [], "sketch": [], "sweeps": []}
         barrier()
         torch.cuda.synchronize()
-    launches = (ts.kernel_launches() - l0) // max(args.steps, 1) * args.steps
-    residual = float(plan.residuals[0].item())
+        with Clocks(dev.index) as clk:
+            for _ in range(args.steps):
+                flush.zero_()
+                e0.record()
+                plan.run(Tg)
+                e1.record()
+                torch.cuda.synchronize()
+                rec["step"].append(e0.elapsed_time(e1))
+            barrier()
+            torch.cuda.synchronize()
+        rec["clocks"] = clk.summary()
+        rec["residual"] = float(plan.residuals[0].item())
+        rec["plan"] = plan
+        direct = ts.TuckerPlan(Tg, RANKS, M, SWEEPS, seed=SEED, rrf_k1=RRF_K1,
+                               solve_fp64=solve_fp64)
+        events = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        direct.set_phase_events(events)
+        direct.run(Tg)
+        for _ in range(args.steps):
+            flush.zero_()
+            l0 = ts.kernel_launches()
+            direct.run(Tg)
+            torch.cuda.synchronize()
+            rec["launches"] = ts.kernel_launches() - l0
+            rec["direct_step"] = rec.get("direct_step", []) + [events[0].elapsed_time(events[5])]
+            rec["rrf"].append(events[0].elapsed_time(events[1]))
+            rec["sketch"].append(events[2].elapsed_time(events[3]))
+            rec["sweeps"].append(events[3].elapsed_time(events[4]))
+        return rec
+
+    forms = {"plain FP32": time_form(False), "FP32 + FP64 QR/SVD": time_form(True)}
+    # chosen form: the fastest whose final residual is within 1e-3 (absolute) of plain FP32
+    base_res = forms["plain FP32"]["residual"]
+    ok = {k: v for k, v in forms.items() if abs(v["residual"] - base_res) <= 1e-3}
+    chosen = min(ok, key=lambda k: statistics.mean(ok[k]["step"]))
+    R = forms[chosen]
+    plan = R["plan"]
+    step_ms, rrf_ms, sketch_ms, sweeps_ms = R["step"], R["rrf"], R["sketch"], R["sweeps"]
+    clk_summary = R["clocks"]
+    residual = R["residual"]
+    # kernels per timed region: a replay launches the captured kernels without host
+    # calls, so count those of one uncaptured decomposition of the same form
+    launches = R["launches"] * args.steps
 
     # End to end through the same public API: pinned host tensor in, residual and the
     # model (core + factors) out, every step.
@@ -216,10 +247,15 @@ def run_ours(args, rank, world):
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": "plain FP32",
+        "config": {"workload": WORKLOAD, "form": chosen,
                    "flush": "256 MB L2 flush between steps; tensor 256 MB > L2",
-                   "parallelism": f"replicas x{world}"},
+                   "parallelism": f"replicas x{world}", "graph": "captured once, replayed"},
         "residual": residual,
+        "forms": {k: {"sweeps_per_s": SWEEPS * 1e3 / statistics.mean(v["step"]),
+                      "ms_per_step": statistics.mean(v["step"]),
+                      "ms_per_step_uncaptured": statistics.mean(v["direct_step"]),
+                      "residual": v["residual"]}
+                  for k, v in forms.items()},
         "phases_ms": {"init_rrf": statistics.mean(rrf_ms), "input_sketch": sk,
                       "sweeps": statistics.mean(sweeps_ms)},
         "input_sketch_gbs": achieved,
@@ -230,7 +266,7 @@ def run_ours(args, rank, world):
         "e2e": {"value": world * SWEEPS * 1e3 / e2e, "unit": "sweeps/s",
                 "h2d_bytes_per_step": int(T.nbytes), "d2h_bytes_per_step": int(out_bytes)},
         "gpu_launches": int(launches),
-        "clocks": clk.summary(),
+        "clocks": clk_summary,
     }
     if not args.no_cpu_baseline:
         T64 = T.astype(np.float64)

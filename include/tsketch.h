@@ -98,10 +98,18 @@ typedef struct {
   int32_t gram_bf16;          /* reserved: must be 0 in this build */
   int32_t init_given;         /* 1: factors_inout already hold the initial A^(2..N) (no RRF) */
   int32_t track_fit;          /* 1: write the relative residual after every sweep */
+  int32_t solve_fp64;         /* FP32 data: 1 runs the QR of Alg. 5 and the last Jacobi
+                                 sweeps of the SVD in FP64 (slower on GB300); FP64 data
+                                 always solves in FP64 */
+  int32_t use_graph;          /* 1: capture the whole decomposition as a CUDA graph on first
+                                 use (cached per argument set and device, up to 8 entries) and
+                                 replay it on later calls with identical arguments.  The
+                                 first call pays for the capture; it must not itself be made
+                                 while the caller's thread is capturing a stream. */
   /* Optional profiling hook: HOST array of 6 cudaEvent_t (or NULL).  The driver
    * records them on `stream` at: [0] call start, [1] after Init-RRF, [2] before
    * the one-pass sketch of the data tensor, [3] after it, [4] after the last
-   * sweep, [5] after the residual. */
+   * sweep, [5] after the residual.  Ignored when use_graph is set. */
   void* const* phase_events;
 } ts_options;
 
@@ -224,8 +232,9 @@ size_t ts_lrls_scratch_bytes(int32_t m, int32_t r, int32_t s, int32_t R, int32_t
                              int32_t oversample, int32_t dtype);
 ts_status ts_lrls_solve(int32_t m, int32_t r, int32_t s, int32_t R, int32_t dtype,
                         const void* Z_colmajor, const void* Y, int32_t solve, uint64_t seed,
-                        int32_t sweep, int32_t n, int32_t oversample, void* CnT_out, void* A_out,
-                        void* scratch, size_t scratch_bytes, ts_stream stream);
+                        int32_t sweep, int32_t n, int32_t oversample, int32_t solve_fp64,
+                        void* CnT_out, void* A_out, void* scratch, size_t scratch_bytes,
+                        ts_stream stream);
 
 /* ------------------------------------------------------------------------- */
 /* Leverage-score sketch of subproblem `mode` of a dense tensor (Sec. 3.2).

@@ -42,6 +42,11 @@ void note_launch();
     TS_CUDA(cudaGetLastError());    \
   } while (0)
 
+// Raise the dynamic shared-memory limit of kernel `fn` on the current device to at
+// least `bytes` (cached per device and kernel; static shared memory counts against
+// the default 48 KB, so every launch with dynamic shared memory goes through this).
+ts_status ensure_dynamic_smem(const void* fn, size_t bytes);
+
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Bump allocator over caller-provided scratch.  With base == nullptr it only

@@ -81,6 +81,66 @@ __global__ void k_gram_hadamard(CoreDims d, int n, int Rc, FacPtrs<T> A,
   }
 }
 
+// One CP-ALS factor update A_n = M Gam^{-1} (M = MTTKRP, R_n x Rc) in one block, with
+// Gam = Hadamard product of the other factors' Grams formed and Cholesky-factored in
+// FP64: with collinear factors Gam is ill-conditioned, and the update is tiny.
+template <typename T>
+__global__ void __launch_bounds__(256) k_cp_update(CoreDims d, int n, int Rc, FacPtrs<T> A,
+                                                   const T* __restrict__ M, T* __restrict__ out,
+                                                   int* flag) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* L = reinterpret_cast<double*>(smem_raw);  // Rc x Rc
+  double* X = L + Rc * Rc;                           // R_n x Rc (rows solved in place)
+  const int Rn = d.ranks[n];
+  for (int e = threadIdx.x; e < Rc * Rc; e += blockDim.x) {
+    const int a = e / Rc, b = e % Rc;
+    double v = 1.0;
+    for (int k = 0; k < d.order; ++k) {
+      if (k == n) continue;
+      double g = 0.0;
+      for (int i = 0; i < d.ranks[k]; ++i)
+        g += (double)A.p[k][i * Rc + a] * (double)A.p[k][i * Rc + b];
+      v *= g;
+    }
+    L[e] = v;
+  }
+  for (int e = threadIdx.x; e < Rn * Rc; e += blockDim.x) X[e] = (double)M[e];
+  __syncthreads();
+  for (int j = 0; j < Rc; ++j) {  // right-looking Cholesky, lower triangle
+    if (threadIdx.x == 0) {
+      double dj = L[j * Rc + j];
+      if (!(dj > 0.0)) {
+        if (flag) atomicExch(flag, 1);
+        dj = 1.0;
+      }
+      L[j * Rc + j] = sqrt(dj);
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < Rc; i += blockDim.x) L[i * Rc + j] /= L[j * Rc + j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < Rc * Rc; e += blockDim.x) {
+      const int i = e / Rc, l = e % Rc;
+      if (i > j && l > j && l <= i) L[i * Rc + l] -= L[i * Rc + j] * L[l * Rc + j];
+    }
+    __syncthreads();
+  }
+  // row r of A_n solves Gam x = M(r, :)^T
+  for (int r = threadIdx.x; r < Rn; r += blockDim.x) {
+    double* x = X + r * Rc;
+    for (int i = 0; i < Rc; ++i) {
+      double v = x[i];
+      for (int l = 0; l < i; ++l) v -= L[i * Rc + l] * x[l];
+      x[i] = v / L[i * Rc + i];
+    }
+    for (int i = Rc - 1; i >= 0; --i) {
+      double v = x[i];
+      for (int l = i + 1; l < Rc; ++l) v -= L[l * Rc + i] * x[l];
+      x[i] = v / L[i * Rc + i];
+    }
+    for (int c = 0; c < Rc; ++c) out[r * Rc + c] = (T)x[c];
+  }
+}
+
 // out (cols x rows) = in^T (in is rows x cols).
 template <typename T>
 __global__ void k_transpose(int rows, int cols, const T* __restrict__ in, T* __restrict__ out) {
@@ -149,8 +209,6 @@ ts_status cp_als_core(int order, const int* ranks, int Rc, int sweeps, const T* 
   T* Gam = M + Rmax * Rc;
   T* X = Gam + Rc * Rc;
   T* Ke = X + Rc * Rmax;
-  T* P = Ke + E * E;
-  const size_t PE = 32 * (size_t)(Rmax * Rc > Rmax * Rmax ? Rmax * Rc : Rmax * Rmax);
   CoreMap none{};
   // HOSVD of the core: leading Rc eigenvectors of C_(n) C_(n)^T, canonical signs.
   for (int n = 0; n < order; ++n) {
@@ -158,10 +216,11 @@ ts_status cp_als_core(int order, const int* ranks, int Rc, int sweeps, const T* 
     k_unfold<T><<<grid_for(total), 256, 0, st>>>(d, n, core, Cn);
     TS_LAUNCH_CHECK();
     TS_TRY(gemm<T>(ranks[n], ranks[n], (int)K, 1.0, MatView<T>{Cn, K, 1}, MatView<T>{Cn, 1, K},
-                   0.0, OutView<T>{Ke, ranks[n], 1}, P, PE, st));
-    TS_TRY(launch_eig_small<T>(ranks[n], Rc, Ke, nullptr, ranks[n], nullptr, nullptr, M, flag,
-                               st));
-    TS_TRY(launch_finalize<T>(ranks[n], Rc, M, A[n], nullptr, 0, nullptr, none, st));
+                   0.0, OutView<T>{Ke, ranks[n], 1}, nullptr, st));
+    TS_TRY(launch_eig_small<T>(ranks[n], Rc, Ke, nullptr, ranks[n], nullptr, nullptr, M, false,
+                               flag, st));
+    TS_TRY(launch_finalize<T>(ranks[n], Rc, M, Rc, 1, 0, nullptr, A[n], nullptr, 0, nullptr, none,
+                              st));
   }
   for (int sweep = 0; sweep < sweeps; ++sweep) {
     for (int n = 0; n < order; ++n) {
@@ -172,14 +231,11 @@ ts_status cp_als_core(int order, const int* ranks, int Rc, int sweeps, const T* 
       TS_LAUNCH_CHECK();
       // MTTKRP: M = C_(n) KR (R_n x Rc)
       TS_TRY(gemm<T>(ranks[n], Rc, (int)K, 1.0, MatView<T>{Cn, K, 1}, MatView<T>{KR, Rc, 1}, 0.0,
-                     OutView<T>{M, Rc, 1}, P, PE, st));
-      k_gram_hadamard<T><<<grid_for((long)Rc * Rc), 256, 0, st>>>(d, n, Rc, fp, Gam);
-      TS_LAUNCH_CHECK();
-      // A_n = M Gam^{-1}: solve Gam X = M^T, then A_n = X^T
-      k_transpose<T><<<grid_for((long)ranks[n] * Rc), 256, 0, st>>>(ranks[n], Rc, M, Ke);
-      TS_LAUNCH_CHECK();
-      TS_TRY(launch_chol_solve<T>(Rc, ranks[n], Gam, Ke, X, flag, st));
-      k_transpose<T><<<grid_for((long)ranks[n] * Rc), 256, 0, st>>>(Rc, ranks[n], X, A[n]);
+                     OutView<T>{M, Rc, 1}, nullptr, st));
+      // A_n = M Gam^{-1} with Gam = *_{k != n} A_k^T A_k (FP64 normal equations)
+      const size_t smem = sizeof(double) * ((size_t)Rc * Rc + (size_t)ranks[n] * Rc);
+      TS_TRY(ensure_dynamic_smem((const void*)k_cp_update<T>, smem));
+      k_cp_update<T><<<1, 256, smem, st>>>(d, n, Rc, fp, M, A[n], flag);
       TS_LAUNCH_CHECK();
     }
   }

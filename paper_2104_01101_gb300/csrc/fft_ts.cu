@@ -163,6 +163,12 @@ __global__ void __launch_bounds__(256) k_factor_spectra(ChainDesc d, FftPlan pla
   const int m = plan.m;
   Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw);
   Cx<T>* b = a + m;
+  const Cx<T>* twp = tw;
+  if (plan.stage_tw) {  // twiddles in shared memory: every stage reads them
+    Cx<T>* tws = b + m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) tws[i] = tw[i];
+    twp = tws;
+  }
   const int c0 = 2 * blockIdx.x;
   const int c1 = c0 + 1;
   for (int i = threadIdx.x; i < m; i += blockDim.x) a[i] = Cx<T>{0, 0};
@@ -187,7 +193,7 @@ __global__ void __launch_bounds__(256) k_factor_spectra(ChainDesc d, FftPlan pla
     }
   }
   __syncthreads();
-  const Cx<T>* F = fft_run<T>(a, b, plan, tw);
+  const Cx<T>* F = fft_run<T>(a, b, plan, twp);
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
     const Cx<T> z = F[k];
     const Cx<T> zc = cconj(F[k == 0 ? 0 : m - k]);
@@ -209,6 +215,12 @@ __global__ void __launch_bounds__(256) k_hadamard_ifft(ChainDesc d, int ncols, F
   const int m = plan.m;
   Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw);
   Cx<T>* b = a + m;
+  const Cx<T>* twp = tw;
+  if (plan.stage_tw) {
+    Cx<T>* tws = b + m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) tws[i] = tw[i];
+    twp = tws;
+  }
   const int c0 = 2 * blockIdx.x;
   const bool has1 = c0 + 1 < ncols;
   int sp0[TS_MAX_ORDER], sp1[TS_MAX_ORDER];
@@ -232,19 +244,12 @@ __global__ void __launch_bounds__(256) k_hadamard_ifft(ChainDesc d, int ncols, F
     a[k] = Cx<T>{p0.x - p1.y, -(p0.y + p1.x)};
   }
   __syncthreads();
-  const Cx<T>* F = fft_run<T>(a, b, plan, tw);
+  const Cx<T>* F = fft_run<T>(a, b, plan, twp);
   const T inv_m = (T)1 / (T)m;
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
     Z[(size_t)c0 * m + k] = F[k].x * inv_m;
     if (has1) Z[(size_t)(c0 + 1) * m + k] = -F[k].y * inv_m;
   }
-}
-
-template <typename T>
-static ts_status set_smem(const void* fn, size_t bytes) {
-  if (bytes > 48 * 1024)
-    TS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  return TS_OK;
 }
 
 template <typename T>
@@ -266,9 +271,10 @@ ts_status launch_ts_apply(int nf, const T* const* factors, const int64_t* rows, 
   }
   d.total_cols = total;
   FftPlan plan = make_fft_plan(m);
-  const size_t smem = 2 * (size_t)m * sizeof(Cx<T>);
-  TS_TRY(set_smem<T>((const void*)k_factor_spectra<T>, smem));
-  TS_TRY(set_smem<T>((const void*)k_hadamard_ifft<T>, smem));
+  plan.stage_tw = 3 * (size_t)m * sizeof(Cx<T>) <= kMaxSmem ? 1 : 0;
+  const size_t smem = (2 + plan.stage_tw) * (size_t)m * sizeof(Cx<T>);
+  TS_TRY(ensure_dynamic_smem((const void*)k_factor_spectra<T>, smem));
+  TS_TRY(ensure_dynamic_smem((const void*)k_hadamard_ifft<T>, smem));
   k_factor_spectra<T><<<ceil_div(total, 2), 256, smem, st>>>(d, plan, tw, spectra);
   TS_LAUNCH_CHECK();
   k_hadamard_ifft<T><<<ceil_div(ncols, 2), 256, smem, st>>>(d, (int)ncols, plan, tw, spectra, Z);

@@ -1,48 +1,28 @@
 // Relative residual ||T - T~||_F / ||T||_F of a Tucker model against a dense
 // tensor (Sec. 7 fitness f = 1 - residual), by direct reconstruction:
-//   Q = C x_1 A^(1) ... x_{N-1} A^(N-1)   (all modes but the last, small)
-//   T~(row, :) = Q(row, :) A^(N)T          (streamed against T, row by row)
-// Squares are summed per row in the data type and across rows in FP64.
+//   Q = C x_1 A^(1) ... x_{N-1} A^(N-1)   (all modes but the last; successive TTMs)
+//   T~(row, :) = Q(row, :) A^(N)T          (streamed against T, one pass)
+// Squares are summed per thread in the data type, then in FP64 across threads.
 #include "internal.cuh"
 
 namespace ts {
 
-struct FitDesc {
-  int order;
-  int64_t dims[TS_MAX_ORDER];
-  int ranks[TS_MAX_ORDER];
-  const void* factors[TS_MAX_ORDER];
-};
-
+// out = in x_k A (C order): in is (a x Rk x b), A is (sk x Rk), out is (a x sk x b).
 template <typename T>
-__global__ void k_fit_partial(FitDesc d, const T* __restrict__ core, T* __restrict__ Q,
-                              int64_t nrows) {
-  const int N = d.order;
-  const int Rl = d.ranks[N - 1];
-  int nr = 1;
-  for (int k = 0; k < N - 1; ++k) nr *= d.ranks[k];
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nrows * Rl;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t row = e / Rl;
-    const int rl = (int)(e % Rl);
-    int64_t idx[TS_MAX_ORDER];
-    int64_t x = row;
-    for (int k = N - 2; k >= 0; --k) {
-      idx[k] = x % d.dims[k];
-      x /= d.dims[k];
-    }
+__global__ void k_ttm(long a, int Rk, long b, int sk, const T* __restrict__ in,
+                      const T* __restrict__ A, T* __restrict__ out) {
+  const long total = a * sk * b;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long y = e % b;
+    const long xi = e / b;
+    const int i = (int)(xi % sk);
+    const long x = xi / sk;
+    const T* src = in + x * Rk * b + y;
+    const T* arow = A + (long)i * Rk;
     T acc = 0;
-    for (int t = 0; t < nr; ++t) {
-      T prod = core[(int64_t)t * Rl + rl];
-      int y = t;
-      for (int k = N - 2; k >= 0; --k) {
-        const int rk = y % d.ranks[k];
-        y /= d.ranks[k];
-        prod *= static_cast<const T*>(d.factors[k])[idx[k] * d.ranks[k] + rk];
-      }
-      acc += prod;
-    }
-    Q[e] = acc;
+    for (int r = 0; r < Rk; ++r) acc += arow[r] * src[r * b];
+    out[e] = acc;
   }
 }
 
@@ -52,36 +32,71 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// One warp per row of T (rows are the last-mode fibres).  The last factor is
-// staged transposed in shared memory when it fits (AT[r][j]).
+// Register-tiled pass for R_last <= RMAX and s_last % 4 == 0: thread t of a block owns
+// columns 4t..4t+3 of every row (their A^(N) rows live in registers); blocks stride over
+// the rows.  T rows are read as float4/double2-pairs, coalesced.
+template <typename T, int RMAX>
+__global__ void __launch_bounds__(256) k_fit_stream_tiled(const T* __restrict__ X,
+                                                          const T* __restrict__ Q,
+                                                          const T* __restrict__ Alast,
+                                                          int64_t nrows, int sl, int Rl,
+                                                          double* __restrict__ acc) {
+  const int nq = sl / 4;
+  double d2 = 0, t2 = 0;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    T a[4][RMAX];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) a[c][r] = r < Rl ? Alast[(long)(4 * q + c) * Rl + r] : (T)0;
+    T pd = 0, pt = 0;
+    for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
+      T qr[RMAX];
+#pragma unroll
+      for (int r = 0; r < RMAX; ++r) qr[r] = r < Rl ? __ldg(&Q[row * Rl + r]) : (T)0;
+      const T* xr = X + row * sl + 4 * q;
+      T x[4];
+      if constexpr (sizeof(T) == 4) {
+        const float4 v = *reinterpret_cast<const float4*>(xr);
+        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) x[c] = xr[c];
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        T t = 0;
+#pragma unroll
+        for (int r = 0; r < RMAX; ++r) t += qr[r] * a[c][r];
+        const T df = x[c] - t;
+        pd += df * df;
+        pt += x[c] * x[c];
+      }
+    }
+    d2 += (double)pd;
+    t2 += (double)pt;
+  }
+  d2 = warp_sum_d(d2);
+  t2 = warp_sum_d(t2);
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, d2);
+    atomicAdd(acc + 1, t2);
+  }
+}
+
+// General pass: one warp per row, the last factor read from global memory.
 template <typename T>
 __global__ void __launch_bounds__(256) k_fit_stream(const T* __restrict__ X,
                                                     const T* __restrict__ Q,
                                                     const T* __restrict__ Alast, int64_t nrows,
-                                                    int sl, int Rl, int staged,
-                                                    double* __restrict__ acc) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* qs = reinterpret_cast<T*>(smem_raw);  // 8 warps x Rl
-  T* AT = qs + 8 * Rl;                      // Rl x sl when staged
+                                                    int sl, int Rl, double* __restrict__ acc) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (staged)
-    for (int e = threadIdx.x; e < sl * Rl; e += blockDim.x) {
-      const int j = e / Rl, r = e % Rl;
-      AT[r * sl + j] = Alast[e];
-    }
-  __syncthreads();
   double d2 = 0, t2 = 0;
   for (int64_t row = blockIdx.x * 8 + warp; row < nrows; row += (int64_t)gridDim.x * 8) {
-    for (int r = lane; r < Rl; r += 32) qs[warp * Rl + r] = Q[row * Rl + r];
-    __syncwarp();
     T pd = 0, pt = 0;
     for (int j = lane; j < sl; j += 32) {
       T t = 0;
-      if (staged) {
-        for (int r = 0; r < Rl; ++r) t += qs[warp * Rl + r] * AT[r * sl + j];
-      } else {
-        for (int r = 0; r < Rl; ++r) t += qs[warp * Rl + r] * Alast[(int64_t)j * Rl + r];
-      }
+      for (int r = 0; r < Rl; ++r) t += Q[row * Rl + r] * Alast[(int64_t)j * Rl + r];
       const T x = X[row * sl + j];
       const T df = x - t;
       pd += df * df;
@@ -89,7 +104,6 @@ __global__ void __launch_bounds__(256) k_fit_stream(const T* __restrict__ X,
     }
     d2 += (double)pd;
     t2 += (double)pt;
-    __syncwarp();
   }
   d2 = warp_sum_d(d2);
   t2 = warp_sum_d(t2);
@@ -103,48 +117,62 @@ __global__ void k_fit_finish(const double* acc, double* out) {
   out[0] = acc[1] > 0 ? sqrt(acc[0] / acc[1]) : 0.0;
 }
 
+// Two buffers of |Q| = prod_{k < N-1} dims[k] * ranks[N-1] values each.
 template <typename T>
 size_t fit_dense_scratch_elems(const ts_tensor& X, const int* ranks) {
   int64_t nrows = 1;
   for (int k = 0; k < X.order - 1; ++k) nrows *= X.dims[k];
-  return (size_t)nrows * ranks[X.order - 1];
+  return 2 * (size_t)nrows * ranks[X.order - 1];
+}
+
+static int grid_for(long n) {
+  long b = (n + 255) / 256;
+  return (int)(b < 1 ? 1 : (b > 152 * 16 ? 152 * 16 : b));
 }
 
 template <typename T>
 ts_status launch_fit_dense(const ts_tensor& X, const int* ranks, const T* core,
-                           const T* const* factors, T* Q, double* acc, double* residual_out,
+                           const T* const* factors, T* scratch, double* acc, double* residual_out,
                            cudaStream_t st) {
-  FitDesc d{};
-  d.order = X.order;
-  int64_t nrows = 1;
-  for (int k = 0; k < X.order; ++k) {
-    d.dims[k] = X.dims[k];
-    d.ranks[k] = ranks[k];
-    d.factors[k] = factors[k];
-    if (k < X.order - 1) nrows *= X.dims[k];
-  }
   const int N = X.order;
+  int64_t nrows = 1;
+  for (int k = 0; k < N - 1; ++k) nrows *= X.dims[k];
   const int Rl = ranks[N - 1];
   const int sl = (int)X.dims[N - 1];
+  T* buf[2] = {scratch, scratch + (size_t)nrows * Rl};
   TS_CUDA(cudaMemsetAsync(acc, 0, 2 * sizeof(double), st));
-  {
-    int64_t tot = nrows * Rl;
-    int blocks = (int)((tot + 255) / 256);
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    k_fit_partial<T><<<blocks, 256, 0, st>>>(d, core, Q, nrows);
+  // Q by successive TTMs of the core along modes N-2, ..., 0
+  const T* cur = core;
+  long shape[TS_MAX_ORDER];
+  for (int k = 0; k < N; ++k) shape[k] = ranks[k];
+  int which = 0;
+  for (int k = N - 2; k >= 0; --k) {
+    long a = 1, b = 1;
+    for (int j = 0; j < k; ++j) a *= shape[j];
+    for (int j = k + 1; j < N; ++j) b *= shape[j];
+    T* out = buf[which];
+    k_ttm<T><<<grid_for(a * X.dims[k] * b), 256, 0, st>>>(a, ranks[k], b, (int)X.dims[k], cur,
+                                                           factors[k], out);
     TS_LAUNCH_CHECK();
+    shape[k] = X.dims[k];
+    cur = out;
+    which ^= 1;
   }
-  size_t smem = sizeof(T) * 8 * (size_t)Rl;
-  const size_t stage_bytes = sizeof(T) * (size_t)Rl * sl;
-  const int staged = (smem + stage_bytes) <= 160 * 1024 ? 1 : 0;
-  if (staged) smem += stage_bytes;
-  if (smem > 48 * 1024)
-    TS_CUDA(cudaFuncSetAttribute((const void*)k_fit_stream<T>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int blocks = (int)((nrows + 7) / 8);
-  if (blocks > 152 * 4) blocks = 152 * 4;
-  k_fit_stream<T><<<blocks, 256, smem, st>>>(static_cast<const T*>(X.values), Q, factors[N - 1],
-                                             nrows, sl, Rl, staged, acc);
+  const int blocks = (int)(nrows < 152 * 8 ? nrows : 152 * 8);
+  if (sl % 4 == 0 && Rl <= 16 && sl / 4 <= 1024 && ((uintptr_t)X.values & 15) == 0) {
+    const int threads = ((sl / 4 + 31) / 32) * 32;
+    if (Rl <= 8)
+      k_fit_stream_tiled<T, 8><<<blocks, threads, 0, st>>>(static_cast<const T*>(X.values), cur,
+                                                           factors[N - 1], nrows, sl, Rl, acc);
+    else
+      k_fit_stream_tiled<T, 16><<<blocks, threads, 0, st>>>(static_cast<const T*>(X.values), cur,
+                                                            factors[N - 1], nrows, sl, Rl, acc);
+  } else {
+    int b2 = (int)((nrows + 7) / 8);
+    if (b2 > 152 * 4) b2 = 152 * 4;
+    k_fit_stream<T><<<b2, 256, 0, st>>>(static_cast<const T*>(X.values), cur, factors[N - 1],
+                                        nrows, sl, Rl, acc);
+  }
   TS_LAUNCH_CHECK();
   k_fit_finish<<<1, 1, 0, st>>>(acc, residual_out);
   TS_LAUNCH_CHECK();

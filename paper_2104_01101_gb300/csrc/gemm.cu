@@ -1,20 +1,25 @@
-// Small strided SIMT GEMM for the sketched-system products (Z^T Z, Z^T Y Omega,
-// Z E, M^T Y, D D^T ...).  These are tall-skinny products of a few MFLOP each:
-// the tile loop is latency-bound, so the design favours a deterministic split of
-// the long dimension across many CTAs (partials reduced in a fixed order) over
-// tensor-core tiles.
+// Small strided SIMT GEMM for the sketched-system products ([Z^T Z | Z^T Y],
+// Y Omega, Z E, M^T Y, D D^T, the Init-RRF products ...).  These are tall-skinny
+// products of a few to a hundred MFLOP, latency-bound at the sizes of the method, so
+// the launcher first shrinks the output tile (64x64 -> 32x32) to reach one wave of
+// CTAs and only then splits the long dimension; split partials are summed in split
+// order by a second, fully parallel kernel, so results are deterministic.
+// The B operand may be two strided views side by side (columns [0, n1) from B1 and
+// [n1, N) from B2), so that Z^T [Z | Y] is one product even though Z is stored
+// column-major and Y row-major.
 #include "internal.cuh"
 
 namespace ts {
 
 namespace {
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+constexpr int BK = 16, NT = 256;
 }
 
-template <typename T>
+template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, MatView<T> A,
-                                             MatView<T> B, T alpha, T beta, OutView<T> C,
-                                             T* __restrict__ partial) {
+                                             MatView<T> B1, int n1, MatView<T> B2, T alpha,
+                                             T beta, OutView<T> C, T* __restrict__ partial) {
+  constexpr int TM = BM / 16, TN = BN / 16;  // outputs per thread: TM x TN
   __shared__ T As[BK][BM + 4];
   __shared__ T Bs[BK][BN + 4];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
@@ -22,12 +27,13 @@ __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, Ma
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   const bool a_kfast = (A.cs == 1);
-  const bool b_nfast = (B.cs == 1);
-  T acc[4][4];
+  const MatView<T>& Bv = n0 < n1 ? B1 : B2;  // layout of the view this tile starts in
+  const bool b_kfast = (Bv.rs == 1 && Bv.cs != 1);
+  T acc[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0;
   for (int k0 = kbeg; k0 < kend; k0 += BK) {
     for (int t = threadIdx.x; t < BM * BK; t += NT) {
       int i, kk;
@@ -37,35 +43,41 @@ __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, Ma
     }
     for (int t = threadIdx.x; t < BN * BK; t += NT) {
       int j, kk;
-      if (b_nfast) { kk = t / BN; j = t % BN; } else { j = t / BK; kk = t % BK; }
+      if (b_kfast) { j = t / BK; kk = t % BK; } else { kk = t / BN; j = t % BN; }
       const int gj = n0 + j, gk = k0 + kk;
-      Bs[kk][j] = (gj < N && gk < kend) ? B.p[(long)gk * B.rs + (long)gj * B.cs] : (T)0;
+      T v = 0;
+      if (gj < N && gk < kend) {
+        if (gj < n1) v = B1.p[(long)gk * B1.rs + (long)gj * B1.cs];
+        else v = B2.p[(long)gk * B2.rs + (long)(gj - n1) * B2.cs];
+      }
+      Bs[kk][j] = v;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+      T a[TM], b[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
     }
     __syncthreads();
   }
+  const size_t MN = (size_t)M * N;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int gi = m0 + ty * 4 + i;
+  for (int i = 0; i < TM; ++i) {
+    const int gi = m0 + ty * TM + i;
     if (gi >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gj = n0 + tx * 4 + j;
+    for (int j = 0; j < TN; ++j) {
+      const int gj = n0 + tx * TN + j;
       if (gj >= N) continue;
       if (partial) {
-        partial[(size_t)blockIdx.z * M * N + (size_t)gi * N + gj] = acc[i][j];
+        partial[blockIdx.z * MN + (size_t)gi * N + gj] = acc[i][j];
       } else {
         T* c = C.p + (long)gi * C.rs + (long)gj * C.cs;
         *c = beta == (T)0 ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *c;
@@ -89,41 +101,59 @@ __global__ void k_gemm_reduce(int M, int N, int splits, const T* __restrict__ pa
 }
 
 template <typename T>
-ts_status gemm(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B, double beta,
-               OutView<T> C, T* partial, size_t partial_elems, cudaStream_t st) {
+ts_status gemm2(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, int n1,
+                MatView<T> B2, double beta, OutView<T> C, const GemmSplit<T>* split,
+                cudaStream_t st) {
   if (M <= 0 || N <= 0) return TS_OK;
-  const int tiles = ceil_div(M, BM) * ceil_div(N, BN);
+  constexpr int kWave = 2 * 152;
+  const int tiles64 = ceil_div(M, 64) * ceil_div(N, 64);
+  const int tiles32 = ceil_div(M, 32) * ceil_div(N, 32);
+  const bool small = tiles64 < kWave;
+  const int tiles = small ? tiles32 : tiles64;
+  const int bm = small ? 32 : 64;
   int splits = 1;
-  if (partial && K > 4 * BK) {
-    splits = 2 * 152 / tiles;
-    if (splits < 1) splits = 1;
-    splits = splits > ceil_div(K, 4 * BK) ? ceil_div(K, 4 * BK) : splits;
-    if (splits > 64) splits = 64;
-    const size_t cap = partial_elems / ((size_t)M * N);
+  if (split && split->partial && tiles < kWave / 2 && K > 8 * BK) {
+    splits = kWave / tiles;
+    if (splits > ceil_div(K, 8 * BK)) splits = ceil_div(K, 8 * BK);
+    if (splits > 32) splits = 32;
+    const size_t cap = split->partial_elems / ((size_t)M * N);
     if ((size_t)splits > cap) splits = (int)cap;
     if (splits < 1) splits = 1;
   }
-  int kchunk = ceil_div(ceil_div(K > 0 ? K : 1, splits), BK) * BK;
+  const int kchunk = ceil_div(ceil_div(K > 0 ? K : 1, splits), BK) * BK;
   splits = ceil_div(K > 0 ? K : 1, kchunk);
-  dim3 grid(ceil_div(N, BN), ceil_div(M, BM), splits);
-  if (splits == 1) {
-    k_gemm<T><<<grid, NT, 0, st>>>(M, N, K, kchunk, A, B, (T)alpha, (T)beta, C, nullptr);
-    TS_LAUNCH_CHECK();
-  } else {
-    k_gemm<T><<<grid, NT, 0, st>>>(M, N, K, kchunk, A, B, (T)alpha, (T)beta, C, partial);
-    TS_LAUNCH_CHECK();
+  dim3 grid(ceil_div(N, bm), ceil_div(M, bm), splits);
+  T* part = splits > 1 ? split->partial : nullptr;
+  if (small)
+    k_gemm<T, 32, 32><<<grid, NT, 0, st>>>(M, N, K, kchunk, A, B1, n1, B2, (T)alpha, (T)beta, C,
+                                           part);
+  else
+    k_gemm<T, 64, 64><<<grid, NT, 0, st>>>(M, N, K, kchunk, A, B1, n1, B2, (T)alpha, (T)beta, C,
+                                           part);
+  TS_LAUNCH_CHECK();
+  if (splits > 1) {
     const size_t MN = (size_t)M * N;
     int blocks = (int)((MN + 255) / 256);
-    if (blocks > 1024) blocks = 1024;
-    k_gemm_reduce<T><<<blocks, 256, 0, st>>>(M, N, splits, partial, (T)alpha, (T)beta, C);
+    if (blocks > 2048) blocks = 2048;
+    k_gemm_reduce<T><<<blocks, 256, 0, st>>>(M, N, splits, part, (T)alpha, (T)beta, C);
     TS_LAUNCH_CHECK();
   }
   return TS_OK;
 }
 
-template ts_status gemm<float>(int, int, int, double, MatView<float>, MatView<float>, double,
-                               OutView<float>, float*, size_t, cudaStream_t);
-template ts_status gemm<double>(int, int, int, double, MatView<double>, MatView<double>, double,
-                                OutView<double>, double*, size_t, cudaStream_t);
+template <typename T>
+ts_status gemm(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B, double beta,
+               OutView<T> C, const GemmSplit<T>* split, cudaStream_t st) {
+  return gemm2<T>(M, N, K, alpha, A, B, N, B, beta, C, split, st);
+}
+
+#define TS_INST(T)                                                                              \
+  template ts_status gemm<T>(int, int, int, double, MatView<T>, MatView<T>, double, OutView<T>, \
+                             const GemmSplit<T>*, cudaStream_t);                                \
+  template ts_status gemm2<T>(int, int, int, double, MatView<T>, MatView<T>, int, MatView<T>,   \
+                              double, OutView<T>, const GemmSplit<T>*, cudaStream_t);
+TS_INST(float)
+TS_INST(double)
+#undef TS_INST
 
 }  // namespace ts

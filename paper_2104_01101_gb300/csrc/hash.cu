@@ -4,6 +4,9 @@
 #include <stdio.h>
 
 #include <atomic>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "internal.cuh"
 
@@ -23,6 +26,22 @@ void clear_error() { g_err[0] = 0; }
 
 static std::atomic<uint64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+ts_status ensure_dynamic_smem(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> granted;
+  if (bytes > 227 * 1024)
+    return fail(TS_ERR_SHAPE, "shared-memory footprint %zu bytes exceeds 227 KB", bytes);
+  int dev = 0;
+  TS_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& have = granted[{dev, fn}];
+  if (bytes > have) {
+    TS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    have = bytes;
+  }
+  return TS_OK;
+}
 
 // table_out[i] = bucket (poly2(i) mod nbins) | sign bit (poly3(i) odd).
 __global__ void k_hash_table(HashCoefs h, int64_t size, int nbins, int32_t* __restrict__ out) {

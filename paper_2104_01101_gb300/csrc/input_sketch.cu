@@ -66,10 +66,13 @@ __global__ void __launch_bounds__(256) k_sketch_coo(JobsDesc d, const int32_t* _
 }
 
 template <typename T>
-ts_status launch_input_sketch(const ts_tensor& X, const SketchJob* jobs, int njobs,
+ts_status launch_input_sketch(const ts_tensor& X, const SketchJob* jobs, int njobs, int* flag,
                               cudaStream_t st) {
   if (njobs < 1) return TS_OK;
   if (njobs > kMaxJobs) return fail(TS_ERR_INVALID_ARG, "input sketch: too many outputs");
+  if (sizeof(T) == 4 && dense3_tma_eligible(X, jobs, njobs) &&
+      dense3_tma_smem_bytes(X, jobs, njobs) <= kMaxSmem)
+    return launch_dense3_tma(X, jobs, njobs, flag, st);
   JobsDesc d{};
   d.njobs = njobs;
   d.order = X.order;
@@ -100,9 +103,9 @@ ts_status launch_input_sketch(const ts_tensor& X, const SketchJob* jobs, int njo
   return TS_OK;
 }
 
-template ts_status launch_input_sketch<float>(const ts_tensor&, const SketchJob*, int,
+template ts_status launch_input_sketch<float>(const ts_tensor&, const SketchJob*, int, int*,
                                               cudaStream_t);
-template ts_status launch_input_sketch<double>(const ts_tensor&, const SketchJob*, int,
+template ts_status launch_input_sketch<double>(const ts_tensor&, const SketchJob*, int, int*,
                                                cudaStream_t);
 
 }  // namespace ts

@@ -18,6 +18,7 @@ constexpr int kMaxRadices = 32;
 struct FftPlan {
   int m;
   int nst;
+  int stage_tw;  // 1: kernels copy the twiddle table into shared memory first
   int radix[kMaxRadices];
 };
 FftPlan make_fft_plan(int m);
@@ -42,10 +43,17 @@ struct SketchJob {
   const int32_t* tables[TS_MAX_ORDER];
 };
 constexpr int kMaxJobs = 2 * TS_MAX_ORDER;
-// Zeroes every output, then accumulates all jobs in one pass over X.
+// Zeroes every output, then accumulates all jobs in one pass over X.  Dense order-3
+// FP32 tensors with at most one job per mode take the TMA tile/bulk-reduction kernel
+// (input_sketch_tma.cu); a bounded wait that expires there writes TS_ERR_TIMEOUT to
+// *flag (when flag is not null).
 template <typename T>
-ts_status launch_input_sketch(const ts_tensor& X, const SketchJob* jobs, int njobs,
+ts_status launch_input_sketch(const ts_tensor& X, const SketchJob* jobs, int njobs, int* flag,
                               cudaStream_t st);
+bool dense3_tma_eligible(const ts_tensor& X, const SketchJob* jobs, int njobs);
+size_t dense3_tma_smem_bytes(const ts_tensor& X, const SketchJob* jobs, int njobs);
+ts_status launch_dense3_tma(const ts_tensor& X, const SketchJob* jobs, int njobs, int* flag,
+                            cudaStream_t st);
 
 // ---------------------------------------------------------------- gemm.cu
 // Strided matrix view: element (i, j) at p[i * rs + j * cs].
@@ -59,11 +67,25 @@ struct OutView {
   T* p;
   long rs, cs;
 };
-// C = alpha * A B + beta * C for A (M x K), B (K x N).  `partial` (may be null)
-// enables a deterministic split of K: up to partial_elems / (M N) slices.
+// C = alpha * A B + beta * C for A (M x K), B (K x N).  With a GemmSplit the long
+// dimension K may be split across CTAs; the partials are then summed in split order
+// by a second kernel (deterministic).
+template <typename T>
+struct GemmSplit {
+  T* partial;            // splits x M x N values
+  size_t partial_elems;
+  unsigned* counters;    // unused (kept for layout stability of the workspaces)
+  int ncounters;
+};
 template <typename T>
 ts_status gemm(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B, double beta,
-               OutView<T> C, T* partial, size_t partial_elems, cudaStream_t st);
+               OutView<T> C, const GemmSplit<T>* split, cudaStream_t st);
+// Same, with B's columns [0, n1) taken from B1 and [n1, N) from B2 (column j - n1).
+template <typename T>
+ts_status gemm2(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, int n1,
+                MatView<T> B2, double beta, OutView<T> C, const GemmSplit<T>* split,
+                cudaStream_t st);
+constexpr int kGemmCounters = 4096;
 
 // ---------------------------------------------------------------- solve.cu
 // Layout of the core for scattering C_(n)^T into it.
@@ -73,33 +95,51 @@ struct CoreMap {
   int ranks[TS_MAX_ORDER];
 };
 
-// RSVD-LRLS stage 1 (Alg. 5): with G = Z^T Z (r x r) and W = Z^T Y Omega (r x k):
-// C = G^{-1} W, Q = orth(C) (FP64 Householder QR), E = G^{-1} Q.
-template <typename T>
-ts_status launch_rsvd_stage1(int r, int k, const T* G, const T* W, T* Q, T* E, int* flag,
-                             cudaStream_t st);
-// Shared memory of the stage-1 kernel; it must not exceed kMaxSmem.
-inline size_t rsvd_stage1_smem_bytes(int r, int k, size_t tsize) {
-  return sizeof(double) * (3 * (size_t)r * k + k + 2) + tsize * ((size_t)r * r + (size_t)r * k);
-}
 constexpr size_t kMaxSmem = 227 * 1024;
+constexpr int kMaxEig = 64;
+// RSVD-LRLS stage 1 (Alg. 5): with G = Z^T Z (r x r, row stride ldg) and
+// W = Z^T Y Omega (r x k, row stride ldw): C = G^{-1} W, Q = orth(C) (Householder,
+// FP64 when qr64), E = G^{-1} Q.
+template <typename T>
+ts_status launch_rsvd_stage1(int r, int k, const T* G, int ldg, const T* W, int ldw, T* Q, T* E,
+                             bool qr64, int* flag, cudaStream_t st);
+size_t rsvd_stage1_smem_bytes(int r, int k, size_t tsize, bool qr64);
+// Large-r pieces of stage 1: Q = orth(C) in one block, and G^{-1} by Newton-Schulz
+// (S1: 2 r^2 values, S2: r^2 values of scratch).
+template <typename T>
+ts_status launch_qr_only(int r, int k, const T* C, T* Q, bool qr64, cudaStream_t st);
+size_t qr_only_smem_bytes(int r, int k, bool qr64, size_t tsize);
+template <typename T>
+ts_status newton_schulz_inverse(int r, const T* G, long ldg, T* X, T* S1, T* S2, int iters,
+                                const GemmSplit<T>* split, cudaStream_t st);
+constexpr int kNewtonSchulzIters = 14;
 // X = G^{-1} H for G (r x r) SPD and H (r x s).
 template <typename T>
 ts_status launch_chol_solve(int r, int s, const T* G, const T* H, T* X, int* flag,
                             cudaStream_t st);
+size_t chol_solve_smem_bytes(int r, size_t tsize);
 // Symmetric eigen-decomposition of K (n x n), eigenvalues descending, lambda_i = sigma_i^2:
 // CnT = Q U_R Sigma_R (r x R; Q null means identity, r = n), Fm = U_R Sigma_R^{-1} (n x R),
-// Uout = U_R (n x R).  Any output may be null.
+// Uout = U_R (n x R).  Any output may be null.  polish64: FP64 final sweeps (FP32 data).
 template <typename T>
 ts_status launch_eig_small(int n, int R, const T* K, const T* Q, int r, T* CnT, T* Fm, T* Uout,
-                           int* flag, cudaStream_t st);
-constexpr int kMaxEig = 64;
-constexpr int kMaxCholSmem = 192;
-// Column signs (largest-|.| entry positive) on V (s x R); flips CnT (r x R) with it,
-// writes A_out = V and, when core != null, scatters CnT into the core.
+                           bool polish64, int* flag, cudaStream_t st);
+// The whole subproblem after [G | H] = Z^T [Z | Y] in one block (RSVD or exact; see
+// solve.cu): writes A_out (s x R), CnT (r x R, may be null) and the core (may be null).
+// Mbuf: k x s (RSVD) or r x s (exact) scratch.
+size_t lrls_fused_smem_bytes(int r, int s, int k, int R, int solve, size_t tsize, bool fp64,
+                             bool* stage_om);
 template <typename T>
-ts_status launch_finalize(int s, int R, const T* V, T* A_out, T* CnT, int r, T* core,
-                          CoreMap map, cudaStream_t st);
+ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, const T* G,
+                            long ldg, const T* H, long ldh, const T* Om, T* Mbuf, T* CnT,
+                            T* A_out, T* core, CoreMap map, int* flag, cudaStream_t st);
+// Factor columns V (s x R) with V(i, c) = sum_a M(i, a) Fm(a, c) (M element (i, a) at
+// M[i*rs + a*cs], a < kdim), or V(i, c) = M[i*rs + c*cs] when Fm is null.  Each
+// column is signed so that its largest-|.| entry is positive; A_out = V; CnT (r x R)
+// is flipped with it and, when core != null, scattered into the core.
+template <typename T>
+ts_status launch_finalize(int s, int R, const T* M, long rs, long cs, int kdim, const T* Fm,
+                          T* A_out, T* CnT, int r, T* core, CoreMap map, cudaStream_t st);
 
 // ---------------------------------------------------------------- leverage.cu
 // Leverage-score sketch of subproblem `mode` (dense X).  Z column-major m x prod R_k,

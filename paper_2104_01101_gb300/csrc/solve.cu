@@ -1,12 +1,16 @@
 // Small dense linear algebra of the sketched rank-constrained solve (Sec. 4,
-// Alg. 5).  Every kernel here runs in ONE thread block with its operands in
-// shared memory: the matrices are r x r (r = prod of the other ranks, <= 192)
-// or k x k (k = R + oversampling, <= 64), so the work is latency-bound and a
-// single SM keeps every intermediate on chip.
+// Alg. 5).  Each kernel runs in ONE thread block with its operands in shared
+// memory: the matrices are r x r (r = product of the other ranks) or k x k
+// (k = R + oversampling), so the work is latency-bound and one SM keeps every
+// intermediate on chip.  The design goal is few block-wide barriers: blocked
+// Cholesky (16-wide panels factored by one warp with shuffles), blocked triangular
+// solves, and a Jacobi eigensolver whose rotations of one round are applied by all
+// threads at once (pair x column mapping, power-of-two strides).
 //
-// Precision: Cholesky of Z^T Z and the triangular solves run in the data type T;
-// the QR of Alg. 5 (Householder) runs in FP64; the symmetric eigensolver that
-// yields the SVD runs Jacobi sweeps in T and finishes with FP64 sweeps.
+// Precision.  The data type T is used throughout by default.  With `polish64`
+// (FP32 data only) the QR of Alg. 5 runs in FP64 and the eigensolver ends with
+// FP64 Jacobi sweeps on V^T K V: GB300's FP64 rate is ~1/64 of FP32, so this is an
+// option, not the default.  FP64 data runs FP64 everywhere.
 #include "internal.cuh"
 
 namespace ts {
@@ -14,6 +18,7 @@ namespace ts {
 namespace {
 constexpr int NT = 512;
 constexpr int NWARP = NT / 32;
+constexpr int NB = 16;  // Cholesky / triangular-solve panel width
 }  // namespace
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -27,101 +32,169 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
-// In-place lower Cholesky of the r x r matrix in shared memory (row stride r).
-// Sets *flag = 1 (and substitutes 1 for the pivot) if a pivot is not positive.
-template <typename T>
-__device__ void chol_smem(T* L, int r, int* flag) {
-  for (int j = 0; j < r; ++j) {
-    if (threadIdx.x == 0) {
-      T d = L[j * r + j];
-      if (!(d > (T)0) || !isfinite((double)d)) {
-        if (flag) atomicExch(flag, 1);
-        d = (T)1;
-      }
-      L[j * r + j] = sqrt(d);
-    }
-    __syncthreads();
-    const T piv = L[j * r + j];
-    for (int i = j + 1 + threadIdx.x; i < r; i += blockDim.x) L[i * r + j] /= piv;
-    __syncthreads();
-    const int n = r - j - 1;
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
-      const int i = j + 1 + t / n, l = j + 1 + t % n;
-      if (l <= i) L[i * r + l] -= L[i * r + j] * L[l * r + j];
-    }
-    __syncthreads();
-  }
-}
+// ---------------------------------------------------------------- Cholesky
 
-// Solve (L L^T) x = b in place for column `col` of B (r x ncols, row stride ld),
-// one warp per column.
+// In-place lower Cholesky of the r x r matrix at L (row stride ld, shared memory).
+// A non-positive or non-finite pivot sets *flag and is replaced by 1.
 template <typename T>
-__device__ void chol_solve_col_warp(const T* L, int r, T* B, int ld, int col) {
-  const int lane = threadIdx.x & 31;
-  for (int i = 0; i < r; ++i) {
-    T part = 0;
-    for (int l = lane; l < i; l += 32) part += L[i * r + l] * B[l * ld + col];
-    part = warp_sum(part);
-    if (lane == 0) B[i * ld + col] = (B[i * ld + col] - part) / L[i * r + i];
-    __syncwarp();
-  }
-  for (int i = r - 1; i >= 0; --i) {
-    T part = 0;
-    for (int l = i + 1 + lane; l < r; l += 32) part += L[l * r + i] * B[l * ld + col];
-    part = warp_sum(part);
-    if (lane == 0) B[i * ld + col] = (B[i * ld + col] - part) / L[i * r + i];
-    __syncwarp();
-  }
-}
-
-// Thin Householder QR of A (r x k, FP64, row stride k, r >= k) in shared memory:
-// on exit Qo (r x k) holds the orthonormal factor.  Vh (r x k) and tau (k) are
-// work arrays.  Robust to rank deficiency (a zero column gives tau = 0).
-__device__ void householder_q(double* A, int r, int k, double* Vh, double* tau, double* Qo,
-                              double* red) {
+__device__ void chol_blocked(T* L, int r, int ld, int* flag) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarp = blockDim.x >> 5;
+  for (int j0 = 0; j0 < r; j0 += NB) {
+    const int nb = min(NB, r - j0);
+    if (warp == 0) {  // diagonal block: lane i owns row j0 + i
+      T row[NB];
+      const bool mine = lane < nb;
+#pragma unroll
+      for (int c = 0; c < NB; ++c) row[c] = (mine && c < nb) ? L[(j0 + lane) * ld + j0 + c] : (T)0;
+#pragma unroll
+      for (int jj = 0; jj < NB; ++jj) {
+        if (jj < nb) {
+          T d = __shfl_sync(0xffffffffu, row[jj], jj);
+          if (!(d > (T)0) || !isfinite((double)d)) {
+            if (lane == 0 && flag) atomicExch(flag, 1);
+            d = (T)1;
+          }
+          const T piv = sqrt(d);
+          if (lane == jj) row[jj] = piv;
+          if (lane > jj) row[jj] /= piv;
+          const T lij = row[jj];
+#pragma unroll
+          for (int l = jj + 1; l < NB; ++l) {
+            const T llj = __shfl_sync(0xffffffffu, row[jj], l);
+            if (l < nb && lane >= l) row[l] -= lij * llj;
+          }
+        }
+      }
+      if (mine) {
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+          if (c <= lane) L[(j0 + lane) * ld + j0 + c] = row[c];
+      }
+    }
+    __syncthreads();
+    // panel below the diagonal block: row i solves x L_dd^T = a
+    for (int i = j0 + nb + threadIdx.x; i < r; i += blockDim.x) {
+      T x[NB];
+#pragma unroll
+      for (int c = 0; c < NB; ++c) {
+        if (c < nb) {
+          T v = L[i * ld + j0 + c];
+#pragma unroll
+          for (int p = 0; p < c; ++p) v -= x[p] * L[(j0 + c) * ld + j0 + p];
+          x[c] = v / L[(j0 + c) * ld + j0 + c];
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < NB; ++c)
+        if (c < nb) L[i * ld + j0 + c] = x[c];
+    }
+    __syncthreads();
+    // trailing lower triangle: A(i, l) -= L(i, panel) L(l, panel)^T, l <= i
+    const int t0 = j0 + nb;
+    for (int ii = t0 + warp; ii < r; ii += nwarp) {
+      for (int ll = t0 + lane; ll <= ii; ll += 32) {
+        T acc = 0;
+#pragma unroll
+        for (int p = 0; p < NB; ++p)
+          if (p < nb) acc += L[ii * ld + j0 + p] * L[ll * ld + j0 + p];
+        L[ii * ld + ll] -= acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// B (r x k, row stride ldb) <- (L L^T)^{-1} B, blocked forward then backward substitution.
+template <typename T>
+__device__ void chol_solve_multi(const T* L, int r, int ld, T* B, int k, int ldb) {
+  const int nblk = (r + NB - 1) / NB;
+  for (int b = 0; b < nblk; ++b) {  // forward: L y = b
+    const int j0 = b * NB, nb = min(NB, r - j0);
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+      for (int jj = 0; jj < nb; ++jj) {
+        T v = B[(j0 + jj) * ldb + c];
+        for (int p = 0; p < jj; ++p) v -= L[(j0 + jj) * ld + j0 + p] * B[(j0 + p) * ldb + c];
+        B[(j0 + jj) * ldb + c] = v / L[(j0 + jj) * ld + j0 + jj];
+      }
+    }
+    __syncthreads();
+    const int rows = r - j0 - nb;
+    for (int e = threadIdx.x; e < rows * k; e += blockDim.x) {
+      const int i = j0 + nb + e / k, c = e % k;
+      T acc = 0;
+      for (int p = 0; p < nb; ++p) acc += L[i * ld + j0 + p] * B[(j0 + p) * ldb + c];
+      B[i * ldb + c] -= acc;
+    }
+    __syncthreads();
+  }
+  for (int b = nblk - 1; b >= 0; --b) {  // backward: L^T x = y
+    const int j0 = b * NB, nb = min(NB, r - j0);
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+      for (int jj = nb - 1; jj >= 0; --jj) {
+        T v = B[(j0 + jj) * ldb + c];
+        for (int p = jj + 1; p < nb; ++p) v -= L[(j0 + p) * ld + j0 + jj] * B[(j0 + p) * ldb + c];
+        B[(j0 + jj) * ldb + c] = v / L[(j0 + jj) * ld + j0 + jj];
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < j0 * k; e += blockDim.x) {
+      const int i = e / k, c = e % k;
+      T acc = 0;
+      for (int p = 0; p < nb; ++p) acc += L[(j0 + p) * ld + i] * B[(j0 + p) * ldb + c];
+      B[i * ldb + c] -= acc;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- Householder QR
+
+// Thin Householder QR of A (r x k, row stride k, r >= k) in compute type U: on exit
+// Qo (r x k) holds orthonormal columns spanning range(A).  A zero column gives
+// tau = 0 (identity reflector), so rank-deficient inputs are handled.
+template <typename U>
+__device__ void householder_q(U* A, int r, int k, U* Vh, U* tau, U* Qo, U* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarp = blockDim.x >> 5;
   for (int j = 0; j < k; ++j) {
     if (warp == 0) {
-      double s = 0;
+      U s = 0;
       for (int i = j + lane; i < r; i += 32) s += A[i * k + j] * A[i * k + j];
       s = warp_sum(s);
       if (lane == 0) {
-        const double ajj = A[j * k + j];
-        double tj = 0;
-        if (s > 0) {
-          const double alpha = ajj >= 0 ? -sqrt(s) : sqrt(s);
-          const double v0 = ajj - alpha;
-          const double vn2 = s - ajj * ajj + v0 * v0;
-          tj = vn2 > 0 ? 2.0 / vn2 : 0.0;
+        const U ajj = A[j * k + j];
+        U tj = 0;
+        red[0] = 0;
+        if (s > (U)0) {
+          const U alpha = ajj >= (U)0 ? -sqrt(s) : sqrt(s);
+          const U v0 = ajj - alpha;
+          const U vn2 = s - ajj * ajj + v0 * v0;
+          tj = vn2 > (U)0 ? (U)2 / vn2 : (U)0;
           red[0] = v0;
-          red[1] = alpha;
-        } else {
-          red[0] = 0;
-          red[1] = ajj;
         }
         tau[j] = tj;
       }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < r; i += blockDim.x)
-      Vh[i * k + j] = i < j ? 0.0 : (i == j ? red[0] : A[i * k + j]);
+      Vh[i * k + j] = i < j ? (U)0 : (i == j ? red[0] : A[i * k + j]);
     __syncthreads();
-    const double tj = tau[j];
-    for (int c = j + 1 + warp; c < k; c += NWARP) {
-      double w = 0;
+    const U tj = tau[j];
+    for (int c = j + 1 + warp; c < k; c += nwarp) {
+      U w = 0;
       for (int i = j + lane; i < r; i += 32) w += Vh[i * k + j] * A[i * k + c];
       w = warp_sum(w) * tj;
       for (int i = j + lane; i < r; i += 32) A[i * k + c] -= w * Vh[i * k + j];
     }
     __syncthreads();
   }
-  // Q = H_0 ... H_{k-1} [I; 0], applied from the last reflector.
-  for (int t = threadIdx.x; t < r * k; t += blockDim.x) Qo[t] = (t / k == t % k) ? 1.0 : 0.0;
+  for (int t = threadIdx.x; t < r * k; t += blockDim.x) Qo[t] = (t / k == t % k) ? (U)1 : (U)0;
   __syncthreads();
   for (int j = k - 1; j >= 0; --j) {
-    const double tj = tau[j];
-    for (int c = warp; c < k; c += NWARP) {
-      double w = 0;
+    const U tj = tau[j];
+    for (int c = warp; c < k; c += nwarp) {
+      U w = 0;
       for (int i = j + lane; i < r; i += 32) w += Vh[i * k + j] * Qo[i * k + c];
       w = warp_sum(w) * tj;
       for (int i = j + lane; i < r; i += 32) Qo[i * k + c] -= w * Vh[i * k + j];
@@ -130,112 +203,249 @@ __device__ void householder_q(double* A, int r, int k, double* Vh, double* tau, 
   }
 }
 
-// Alg. 5 up to the SVD: C = G^{-1} W, Q = qr(C), E = G^{-1} Q.
-template <typename T>
+// ---------------------------------------------------------------- RSVD-LRLS stage 1
+
+size_t rsvd_stage1_smem_bytes(int r, int k, size_t tsize, bool qr64) {
+  const size_t usize = qr64 ? 8 : tsize;
+  return usize * (3 * (size_t)r * k + k + 2) + tsize * ((size_t)r * (r + 1) + (size_t)r * k) + 16;
+}
+
+// Alg. 5 up to the SVD: C = G^{-1} W, Q = qr(C), E = G^{-1} Q.  G and W are read
+// with row strides ldg / ldw (they may be two column blocks of one product).
+template <typename T, typename U>
 __global__ void __launch_bounds__(NT) k_rsvd_stage1(int r, int k, const T* __restrict__ G,
-                                                    const T* __restrict__ W, T* __restrict__ Qout,
-                                                    T* __restrict__ Eout, int* flag) {
+                                                    int ldg, const T* __restrict__ W, int ldw,
+                                                    T* __restrict__ Qout, T* __restrict__ Eout,
+                                                    int* flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* A = reinterpret_cast<double*>(smem_raw);  // r x k
-  double* Vh = A + r * k;                           // r x k
-  double* Qd = Vh + r * k;                          // r x k
-  double* tau = Qd + r * k;                         // k
-  double* red = tau + k;                            // 2
-  T* L = reinterpret_cast<T*>(red + 2);             // r x r
-  T* B = L + r * r;                                 // r x k
-  for (int t = threadIdx.x; t < r * r; t += blockDim.x) L[t] = G[t];
-  for (int t = threadIdx.x; t < r * k; t += blockDim.x) B[t] = W[t];
+  U* A = reinterpret_cast<U*>(smem_raw);  // r x k
+  U* Vh = A + r * k;                      // r x k
+  U* Qd = Vh + r * k;                     // r x k
+  U* tau = Qd + r * k;                    // k
+  U* red = tau + k;                       // 2
+  T* L = reinterpret_cast<T*>(red + 2);   // r x (r + 1)
+  T* B = L + r * (r + 1);                 // r x k
+  const int ld = r + 1;
+  for (int i = threadIdx.x >> 5; i < r; i += NWARP)
+    for (int j = threadIdx.x & 31; j <= i; j += 32) L[i * ld + j] = G[(long)i * ldg + j];
+  for (int t = threadIdx.x; t < r * k; t += blockDim.x) B[t] = W[(long)(t / k) * ldw + t % k];
   __syncthreads();
-  chol_smem<T>(L, r, flag);
-  const int warp = threadIdx.x >> 5;
-  for (int c = warp; c < k; c += NWARP) chol_solve_col_warp<T>(L, r, B, k, c);
+  chol_blocked<T>(L, r, ld, flag);
+  chol_solve_multi<T>(L, r, ld, B, k, k);
+  for (int t = threadIdx.x; t < r * k; t += blockDim.x) A[t] = (U)B[t];
   __syncthreads();
-  for (int t = threadIdx.x; t < r * k; t += blockDim.x) A[t] = (double)B[t];
-  __syncthreads();
-  householder_q(A, r, k, Vh, tau, Qd, red);
+  householder_q<U>(A, r, k, Vh, tau, Qd, red);
   for (int t = threadIdx.x; t < r * k; t += blockDim.x) {
     const T q = (T)Qd[t];
     Qout[t] = q;
     B[t] = q;
   }
   __syncthreads();
-  for (int c = warp; c < k; c += NWARP) chol_solve_col_warp<T>(L, r, B, k, c);
-  __syncthreads();
+  chol_solve_multi<T>(L, r, ld, B, k, k);
   for (int t = threadIdx.x; t < r * k; t += blockDim.x) Eout[t] = B[t];
 }
 
-// X = G^{-1} H, H r x s (row-major), all columns in one block.
+// Q = orth(C) for C (r x k) in one block (Householder in compute type U); used when r
+// is too large for the on-chip Cholesky of stage 1.
+template <typename T, typename U>
+__global__ void __launch_bounds__(NT) k_qr_only(int r, int k, const T* __restrict__ C,
+                                                T* __restrict__ Qout) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  U* A = reinterpret_cast<U*>(smem_raw);  // r x k
+  U* Vh = A + r * k;
+  U* Qd = Vh + r * k;
+  U* tau = Qd + r * k;
+  U* red = tau + k;
+  for (int t = threadIdx.x; t < r * k; t += blockDim.x) A[t] = (U)C[t];
+  __syncthreads();
+  householder_q<U>(A, r, k, Vh, tau, Qd, red);
+  for (int t = threadIdx.x; t < r * k; t += blockDim.x) Qout[t] = (T)Qd[t];
+}
+
+// Newton-Schulz for G^{-1}: X0 = I / beta with beta the Gershgorin bound of lambda_max
+// (max absolute row sum), so that ||I - G X0|| < 1 for SPD G.  Writes X0 into X and
+// 2I into twoI (the additive term of each iteration X <- X (2I - G X)).
+template <typename T>
+__global__ void k_ns_init(int r, const T* __restrict__ G, long ldg, T* __restrict__ X,
+                          T* __restrict__ twoI) {
+  __shared__ double red[32];
+  double mx = 0;
+  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+    double srow = 0;
+    for (int j = 0; j < r; ++j) srow += fabs((double)G[(long)i * ldg + j]);
+    mx = srow > mx ? srow : mx;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = v > mx ? v : mx;
+  }
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
+    red[0] = m > 0 ? m : 1.0;
+  }
+  __syncthreads();
+  const T inv = (T)(1.0 / red[0]);
+  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+    const bool diag = (e / r) == (e % r);
+    X[e] = diag ? inv : (T)0;
+    twoI[e] = diag ? (T)2 : (T)0;
+  }
+}
+
+template <typename T>
+__global__ void k_copy(long n, const T* __restrict__ src, T* __restrict__ dst) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    dst[e] = src[e];
+}
+
+template <typename T>
+ts_status launch_qr_only(int r, int k, const T* C, T* Q, bool qr64, cudaStream_t st) {
+  if (qr64 && sizeof(T) == 4) {
+    const size_t smem = 8 * (3 * (size_t)r * k + k + 2);
+    TS_TRY(ensure_dynamic_smem((const void*)k_qr_only<T, double>, smem));
+    k_qr_only<T, double><<<1, NT, smem, st>>>(r, k, C, Q);
+  } else {
+    const size_t smem = sizeof(T) * (3 * (size_t)r * k + k + 2);
+    TS_TRY(ensure_dynamic_smem((const void*)k_qr_only<T, T>, smem));
+    k_qr_only<T, T><<<1, NT, smem, st>>>(r, k, C, Q);
+  }
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+size_t qr_only_smem_bytes(int r, int k, bool qr64, size_t tsize) {
+  return (qr64 ? 8 : tsize) * (3 * (size_t)r * k + k + 2);
+}
+
+// G^{-1} (r x r, into X) by `iters` Newton-Schulz steps; S1 holds 2 r^2 and S2 r^2 values.
+template <typename T>
+ts_status newton_schulz_inverse(int r, const T* G, long ldg, T* X, T* S1, T* S2, int iters,
+                                const GemmSplit<T>* split, cudaStream_t st) {
+  k_ns_init<T><<<1, 1024, 0, st>>>(r, G, ldg, X, S2);
+  TS_LAUNCH_CHECK();
+  const long rr = (long)r * r;
+  for (int it = 0; it < iters; ++it) {
+    // S1 = 2I - G X
+    k_copy<T><<<ceil_div(rr, 256) > 1024 ? 1024 : ceil_div(rr, 256), 256, 0, st>>>(rr, S2, S1);
+    TS_LAUNCH_CHECK();
+    TS_TRY(gemm<T>(r, r, r, -1.0, MatView<T>{G, ldg, 1}, MatView<T>{X, r, 1}, 1.0,
+                   OutView<T>{S1, r, 1}, split, st));
+    // X <- X S1 (written through the first r*r of the split buffer)
+    TS_TRY(gemm<T>(r, r, r, 1.0, MatView<T>{X, r, 1}, MatView<T>{S1, r, 1}, 0.0,
+                   OutView<T>{S1 + rr, r, 1}, split, st));
+    k_copy<T><<<ceil_div(rr, 256) > 1024 ? 1024 : ceil_div(rr, 256), 256, 0, st>>>(rr, S1 + rr, X);
+    TS_LAUNCH_CHECK();
+  }
+  return TS_OK;
+}
+
+// ---------------------------------------------------------------- exact solve
+
+// X = G^{-1} H, H r x s (row-major): one block, columns in chunks of 64.
 template <typename T>
 __global__ void __launch_bounds__(NT) k_chol_solve(int r, int s, const T* __restrict__ G,
                                                    const T* __restrict__ H, T* __restrict__ X,
                                                    int* flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* L = reinterpret_cast<T*>(smem_raw);  // r x r
-  T* Bw = L + r * r;                      // NWARP x r  (one column per warp)
-  for (int t = threadIdx.x; t < r * r; t += blockDim.x) L[t] = G[t];
+  T* L = reinterpret_cast<T*>(smem_raw);  // r x (r + 1)
+  T* B = L + r * (r + 1);                 // r x 64
+  const int ld = r + 1;
+  for (int i = threadIdx.x >> 5; i < r; i += NWARP)
+    for (int j = threadIdx.x & 31; j <= i; j += 32) L[i * ld + j] = G[(long)i * r + j];
   __syncthreads();
-  chol_smem<T>(L, r, flag);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* b = Bw + warp * r;
-  for (int c = warp; c < s; c += NWARP) {
-    for (int i = lane; i < r; i += 32) b[i] = H[(long)i * s + c];
-    __syncwarp();
-    chol_solve_col_warp<T>(L, r, b, 1, 0);
-    for (int i = lane; i < r; i += 32) X[(long)i * s + c] = b[i];
-    __syncwarp();
+  chol_blocked<T>(L, r, ld, flag);
+  for (int c0 = 0; c0 < s; c0 += 64) {
+    const int kc = min(64, s - c0);
+    for (int t = threadIdx.x; t < r * kc; t += blockDim.x)
+      B[(t / kc) * 64 + t % kc] = H[(long)(t / kc) * s + c0 + t % kc];
+    __syncthreads();
+    chol_solve_multi<T>(L, r, ld, B, kc, 64);
+    for (int t = threadIdx.x; t < r * kc; t += blockDim.x)
+      X[(long)(t / kc) * s + c0 + t % kc] = B[(t / kc) * 64 + t % kc];
+    __syncthreads();
   }
 }
 
-// One cyclic Jacobi sweep (round-robin pairing, n padded to even) on the n x n
-// symmetric matrix A with accumulated eigenvectors V; returns nothing, caller checks.
-template <typename U>
-__device__ void jacobi_sweep(U* A, U* V, int n, int* rp, int* rq, U* rc, U* rs) {
-  const int np = (n + 1) & ~1;
-  const int npairs = np / 2;
+// ---------------------------------------------------------------- symmetric eigensolver
+
+struct JacobiShape {
+  int n;   // matrix order
+  int np;  // n rounded up to even (round-robin players)
+  int lg;  // log2 of the column stride (power of two >= n)
+};
+
+// Barrier policies: the whole block, or the first nthr threads (named barrier 1).
+struct BlockSync {
+  __device__ void operator()() const { __syncthreads(); }
+  __device__ int size() const { return blockDim.x; }
+};
+struct SubSync {
+  int nthr;  // multiple of 32
+  __device__ void operator()() const { asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory"); }
+  __device__ int size() const { return nthr; }
+};
+
+// Threads the Jacobi sweep of a matrix of order n keeps busy (pairs x padded columns).
+__host__ __device__ inline int jacobi_threads(int n) {
+  int lg = 0;
+  while ((1 << lg) < n) ++lg;
+  const int work = (((n + 1) & ~1) / 2) << lg;
+  int t = ((work + 31) / 32) * 32;
+  return t < 64 ? 64 : (t > 512 ? 512 : t);
+}
+
+// One cyclic sweep with round-robin pairing on A (n x n, row stride n); V accumulates.
+// Called by the threads of `sync` (threadIdx.x < sync.size()).
+template <typename U, typename Sync = BlockSync>
+__device__ void jacobi_sweep(U* A, U* V, const JacobiShape& js, int* rp, int* rq, U* rc, U* rs,
+                             Sync sync = Sync()) {
+  const int n = js.n, np = js.np, npairs = np / 2;
+  const int np2 = 1 << js.lg;
+  const int nthr = sync.size();
   for (int t = 0; t < np - 1; ++t) {
     if (threadIdx.x < npairs) {
       const int i = threadIdx.x;
-      int a, b;
-      if (i == 0) {
-        a = t;
-        b = np - 1;
-      } else {
-        a = (t + i) % (np - 1);
-        b = (t - i + np - 1) % (np - 1);
-      }
-      int p = a < b ? a : b, q = a < b ? b : a;
+      const int a = i == 0 ? t : (t + i) % (np - 1);
+      const int b = i == 0 ? np - 1 : (t - i + np - 1) % (np - 1);
+      int p = min(a, b);
+      const int q = max(a, b);
       U c = 1, s = 0;
       if (q < n) {
         const U apq = A[p * n + q];
         if (apq != (U)0) {
           const U theta = (A[q * n + q] - A[p * n + p]) / (2 * apq);
-          const U tt = (theta >= 0 ? (U)1 : (U)-1) / (fabs(theta) + sqrt(theta * theta + (U)1));
+          const U tt = (theta >= (U)0 ? (U)1 : (U)-1) / (fabs(theta) + sqrt(theta * theta + (U)1));
           c = (U)1 / sqrt(tt * tt + (U)1);
           s = tt * c;
         }
       } else {
-        p = q = -1;
+        p = -1;
       }
       rp[i] = p;
       rq[i] = q;
       rc[i] = c;
       rs[i] = s;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < npairs * n; e += blockDim.x) {
-      const int i = e / n, l = e % n;
-      const int p = rp[i], q = rq[i];
-      if (p < 0) continue;
+    sync();
+    for (int e = threadIdx.x; e < npairs * np2; e += nthr) {  // rows p, q
+      const int i = e >> js.lg, l = e & (np2 - 1);
+      const int p = rp[i];
+      if (p < 0 || l >= n) continue;
+      const int q = rq[i];
       const U c = rc[i], s = rs[i];
       const U ap = A[p * n + l], aq = A[q * n + l];
       A[p * n + l] = c * ap - s * aq;
       A[q * n + l] = s * ap + c * aq;
     }
-    __syncthreads();
-    for (int e = threadIdx.x; e < npairs * n; e += blockDim.x) {
-      const int i = e / n, l = e % n;
-      const int p = rp[i], q = rq[i];
-      if (p < 0) continue;
+    sync();
+    for (int e = threadIdx.x; e < npairs * np2; e += nthr) {  // columns p, q and V
+      const int i = e >> js.lg, l = e & (np2 - 1);
+      const int p = rp[i];
+      if (p < 0 || l >= n) continue;
+      const int q = rq[i];
       const U c = rc[i], s = rs[i];
       const U ap = A[l * n + p], aq = A[l * n + q];
       A[l * n + p] = c * ap - s * aq;
@@ -244,156 +454,189 @@ __device__ void jacobi_sweep(U* A, U* V, int n, int* rp, int* rq, U* rc, U* rs) 
       V[l * n + p] = c * vp - s * vq;
       V[l * n + q] = s * vp + c * vq;
     }
-    __syncthreads();
+    sync();
   }
 }
 
-// Returns off-diagonal^2 and total^2 of A (block-wide; result valid in all threads).
-template <typename U>
-__device__ void offdiag_norms(const U* A, int n, double* red, double& off, double& tot) {
-  double o = 0, a = 0;
-  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-    const double v = (double)A[e];
+// Off-diagonal and total squared Frobenius norms (valid in every participating thread;
+// red holds 2 * (threads / 32) + 2 values).
+template <typename U, typename Sync = BlockSync>
+__device__ void jacobi_norms(const U* A, int n, U* red, U& off, U& tot, Sync sync = Sync()) {
+  const int nthr = sync.size();
+  U o = 0, a = 0;
+  for (int e = threadIdx.x; e < n * n; e += nthr) {
+    const U v = A[e];
     a += v * v;
     if (e / n != e % n) o += v * v;
   }
   o = warp_sum(o);
   a = warp_sum(a);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nthr >> 5;
   if (lane == 0) {
     red[2 * warp] = o;
     red[2 * warp + 1] = a;
   }
-  __syncthreads();
+  sync();
   if (threadIdx.x == 0) {
-    double so = 0, sa = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+    U so = 0, sa = 0;
+    for (int w = 0; w < nw; ++w) {
       so += red[2 * w];
       sa += red[2 * w + 1];
     }
-    red[2 * NWARP] = so;
-    red[2 * NWARP + 1] = sa;
+    red[2 * nw] = so;
+    red[2 * nw + 1] = sa;
   }
-  __syncthreads();
-  off = red[2 * NWARP];
-  tot = red[2 * NWARP + 1];
-  __syncthreads();
+  sync();
+  off = red[2 * nw];
+  tot = red[2 * nw + 1];
+  sync();
 }
 
-template <typename T>
-__global__ void __launch_bounds__(NT) k_eig_small(int n, int R, const T* __restrict__ K,
+// K (n x n) = U Lambda U^T, eigenvalues descending, sigma = sqrt(lambda):
+// CnT = Q U_R Sigma_R (Q null: identity, r = n), Fm = U_R Sigma_R^{-1}, Uout = U_R.
+template <typename T, bool POLISH64>
+__global__ void __launch_bounds__(NT) k_eig_small(int n, int R, JacobiShape js,
+                                                  const T* __restrict__ K,
                                                   const T* __restrict__ Q, int r,
                                                   T* __restrict__ CnT, T* __restrict__ Fm,
                                                   T* __restrict__ Uout, int* flag) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int rp[kMaxEig / 2 + 1], rq[kMaxEig / 2 + 1];
-  __shared__ double rc64[kMaxEig / 2 + 1], rs64[kMaxEig / 2 + 1];
-  __shared__ T rc32[kMaxEig / 2 + 1], rs32[kMaxEig / 2 + 1];
-  __shared__ double red[2 * NWARP + 2];
+  __shared__ T rcT[kMaxEig / 2 + 1], rsT[kMaxEig / 2 + 1];
+  __shared__ double rc64[POLISH64 ? kMaxEig / 2 + 1 : 1], rs64[POLISH64 ? kMaxEig / 2 + 1 : 1];
+  __shared__ T redT[2 * NWARP + 2];
+  __shared__ double red64[POLISH64 ? 2 * NWARP + 2 : 1];
   __shared__ int order[kMaxEig];
-  __shared__ double lam[kMaxEig];
+  __shared__ T lamT[kMaxEig];
   const int nn = n * n;
-  double* A64 = reinterpret_cast<double*>(smem_raw);  // n x n
-  double* V64 = A64 + nn;                             // n x n
-  double* K64 = V64 + nn;                             // n x n
-  T* A32 = reinterpret_cast<T*>(K64 + nn);            // n x n
-  T* V32 = A32 + nn;                                  // n x n
+  T* A = reinterpret_cast<T*>(smem_raw);  // n x n
+  T* V = A + nn;                          // n x n
   for (int e = threadIdx.x; e < nn; e += blockDim.x) {
     const int i = e / n, j = e % n;
-    const T sym = (T)0.5 * (K[i * n + j] + K[j * n + i]);
-    A32[e] = sym;
-    K64[e] = (double)sym;
-    V32[e] = (i == j) ? (T)1 : (T)0;
+    A[e] = (T)0.5 * (K[i * n + j] + K[j * n + i]);
+    V[e] = (i == j) ? (T)1 : (T)0;
   }
   __syncthreads();
-  double off, tot;
-  // Phase 1: Jacobi sweeps in the data type (skipped for FP64 data).
-  if (sizeof(T) == 4) {
-    for (int sweep = 0; sweep < 30; ++sweep) {
-      offdiag_norms<T>(A32, n, red, off, tot);
-      if (off <= 1e-12 * tot || tot == 0) break;
-      jacobi_sweep<T>(A32, V32, n, rp, rq, rc32, rs32);
+  // stop on squared norms: the FP32 rounding floor of off/tot is ~n^2 eps^2 ~ 1e-12
+  const T tol = sizeof(T) == 4 ? (T)1e-11 : (T)1e-28;
+  T off, tot;
+  for (int sweep = 0; sweep < 24; ++sweep) {
+    jacobi_norms<T>(A, n, redT, off, tot);
+    if (off <= tol * tot || tot == (T)0) break;
+    jacobi_sweep<T>(A, V, js, rp, rq, rcT, rsT);
+  }
+  if constexpr (POLISH64) {
+    // FP64 sweeps on V^T K V, V accumulated in FP64.
+    double* A64 = reinterpret_cast<double*>(smem_raw + 2 * nn * sizeof(T) + 8 - ((2 * nn * sizeof(T)) & 7));
+    double* V64 = A64 + nn;
+    double* KV = V64 + nn;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) V64[e] = (double)V[e];
+    __syncthreads();
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int i = e / n, j = e % n;
+      double acc = 0;
+      for (int b = 0; b < n; ++b)
+        acc += 0.5 * ((double)K[i * n + b] + (double)K[b * n + i]) * V64[b * n + j];
+      KV[e] = acc;
     }
-  }
-  // Phase 2: FP64 sweeps on V^T K V (K V into A64, then V^T (K V) into K64).
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) V64[e] = (double)V32[e];
-  __syncthreads();
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    double acc = 0;
-    for (int b = 0; b < n; ++b) acc += K64[i * n + b] * V64[b * n + j];
-    A64[e] = acc;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    double acc = 0;
-    for (int a = 0; a < n; ++a) acc += V64[a * n + i] * A64[a * n + j];
-    K64[e] = acc;
-  }
-  __syncthreads();
-  for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    A64[e] = 0.5 * (K64[i * n + j] + K64[j * n + i]);
-  }
-  __syncthreads();
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    offdiag_norms<double>(A64, n, red, off, tot);
-    if (off <= 1e-28 * tot || tot == 0) break;
-    jacobi_sweep<double>(A64, V64, n, rp, rq, rc64, rs64);
+    __syncthreads();
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int i = e / n, j = e % n;
+      double acc = 0;
+      for (int a = 0; a < n; ++a) acc += V64[a * n + i] * KV[a * n + j];
+      A64[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+      const int i = e / n, j = e % n;
+      if (i < j) {
+        const double s = 0.5 * (A64[i * n + j] + A64[j * n + i]);
+        A64[i * n + j] = s;
+        A64[j * n + i] = s;
+      }
+    }
+    __syncthreads();
+    double o64, t64;
+    for (int sweep = 0; sweep < 10; ++sweep) {
+      jacobi_norms<double>(A64, n, red64, o64, t64);
+      if (o64 <= 1e-28 * t64 || t64 == 0) break;
+      jacobi_sweep<double>(A64, V64, js, rp, rq, rc64, rs64);
+    }
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) V[e] = (T)V64[e];
+    if (threadIdx.x < n) A[threadIdx.x * n + threadIdx.x] = (T)A64[threadIdx.x * n + threadIdx.x];
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
     for (int i = 0; i < n; ++i) {
-      lam[i] = A64[i * n + i];
+      lamT[i] = A[i * n + i];
       order[i] = i;
     }
     for (int i = 0; i < n; ++i) {  // selection sort, descending, stable on ties
       int best = i;
       for (int j = i + 1; j < n; ++j)
-        if (lam[order[j]] > lam[order[best]]) best = j;
+        if (lamT[order[j]] > lamT[order[best]]) best = j;
       const int t = order[i];
       order[i] = order[best];
       order[best] = t;
     }
     for (int i = 0; i < n; ++i)
-      if (!isfinite(lam[i]) && flag) atomicExch(flag, 1);
+      if (!isfinite((double)lamT[i]) && flag) atomicExch(flag, 1);
   }
   __syncthreads();
-  // Fm = U_R Sigma_R^{-1}, Uout = U_R
   for (int e = threadIdx.x; e < n * R; e += blockDim.x) {
     const int i = e / R, c = e % R;
-    const double l = lam[order[c]];
-    const double sig = l > 0 ? sqrt(l) : 0.0;
-    if (Fm) Fm[e] = (T)(sig > 0 ? V64[i * n + order[c]] / sig : 0.0);
-    if (Uout) Uout[e] = (T)V64[i * n + order[c]];
+    const T l = lamT[order[c]];
+    const T sig = l > (T)0 ? sqrt(l) : (T)0;
+    const T u = V[i * n + order[c]];
+    if (Fm) Fm[e] = sig > (T)0 ? u / sig : (T)0;
+    if (Uout) Uout[e] = u;
   }
-  // CnT = Q U_R Sigma_R
-  if (CnT) for (int e = threadIdx.x; e < r * R; e += blockDim.x) {
-    const int i = e / R, c = e % R;
-    const double l = lam[order[c]];
-    const double sig = l > 0 ? sqrt(l) : 0.0;
-    double acc;
-    if (Q) {
-      acc = 0;
-      for (int a = 0; a < n; ++a) acc += (double)Q[i * n + a] * V64[a * n + order[c]];
-    } else {
-      acc = V64[i * n + order[c]];
+  if (CnT) {
+    for (int e = threadIdx.x; e < r * R; e += blockDim.x) {
+      const int i = e / R, c = e % R;
+      const T l = lamT[order[c]];
+      const T sig = l > (T)0 ? sqrt(l) : (T)0;
+      T acc;
+      if (Q) {
+        acc = 0;
+        for (int a = 0; a < n; ++a) acc += Q[i * n + a] * V[a * n + order[c]];
+      } else {
+        acc = V[i * n + order[c]];
+      }
+      CnT[e] = acc * sig;
     }
-    CnT[e] = (T)(acc * sig);
   }
 }
 
-// Block c: canonical sign of column c of V (largest |.|, lowest index on ties).
+// ---------------------------------------------------------------- signs, factor, core
+
+// Column c of V = M Fm (M element (i, a) at M[i*rs + a*cs], a < kdim) or, with Fm
+// null, V(i, c) = M[i*rs + c*cs].
 template <typename T>
-__global__ void __launch_bounds__(256) k_finalize(int s, int R, const T* V, T* A_out, T* CnT,
-                                                  int r, T* core, CoreMap map) {
-  __shared__ double bv[256];
+__device__ __forceinline__ T vcol(const T* M, long rs, long cs, int kdim, const T* Fm, int R,
+                                  int i, int c) {
+  if (!Fm) return M[i * rs + c * cs];
+  T v = 0;
+  for (int a = 0; a < kdim; ++a) v += M[i * rs + a * cs] * Fm[a * R + c];
+  return v;
+}
+
+// Block c: canonical sign of column c of V (entry of largest magnitude positive,
+// lowest index on ties); A_out(:, c) = sign * V(:, c), CnT(:, c) *= sign and, when
+// core != null, C_(n)^T is scattered into the core.
+template <typename T>
+__global__ void __launch_bounds__(256) k_finalize(int s, int R, const T* __restrict__ M, long rs,
+                                                  long cs, int kdim, const T* __restrict__ Fm,
+                                                  T* __restrict__ A_out, T* __restrict__ CnT,
+                                                  int r, T* __restrict__ core, CoreMap map) {
+  __shared__ T bv[256];
   __shared__ int bi[256];
+  __shared__ T sgn_s;
   const int c = blockIdx.x;
-  double best = -1.0;
+  T best = (T)-1;
   int bidx = 0x7fffffff;
   for (int i = threadIdx.x; i < s; i += blockDim.x) {
-    const double a = fabs((double)V[(long)i * R + c]);
+    const T a = fabs(vcol<T>(M, rs, cs, kdim, Fm, R, i, c));
     if (a > best || (a == best && i < bidx)) {
       best = a;
       bidx = i;
@@ -404,7 +647,7 @@ __global__ void __launch_bounds__(256) k_finalize(int s, int R, const T* V, T* A
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {
     if (threadIdx.x < w) {
-      const double ob = bv[threadIdx.x + w];
+      const T ob = bv[threadIdx.x + w];
       const int oi = bi[threadIdx.x + w];
       if (ob > bv[threadIdx.x] || (ob == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
         bv[threadIdx.x] = ob;
@@ -413,9 +656,11 @@ __global__ void __launch_bounds__(256) k_finalize(int s, int R, const T* V, T* A
     }
     __syncthreads();
   }
-  const T sgn = V[(long)bi[0] * R + c] < (T)0 ? (T)-1 : (T)1;
+  if (threadIdx.x == 0) sgn_s = vcol<T>(M, rs, cs, kdim, Fm, R, bi[0], c) < (T)0 ? (T)-1 : (T)1;
   __syncthreads();
-  for (int i = threadIdx.x; i < s; i += blockDim.x) A_out[(long)i * R + c] = sgn * V[(long)i * R + c];
+  const T sgn = sgn_s;
+  for (int i = threadIdx.x; i < s; i += blockDim.x)
+    A_out[(long)i * R + c] = sgn * vcol<T>(M, rs, cs, kdim, Fm, R, i, c);
   if (CnT) {
     for (int rho = threadIdx.x; rho < r; rho += blockDim.x) {
       const T v = sgn * CnT[(long)rho * R + c];
@@ -439,28 +684,437 @@ __global__ void __launch_bounds__(256) k_finalize(int s, int R, const T* V, T* A
   }
 }
 
-static ts_status smem_attr(const void* fn, size_t bytes) {
-  if (bytes > kMaxSmem) return fail(TS_ERR_SHAPE, "shared-memory footprint %zu too large", bytes);
-  if (bytes > 48 * 1024)
-    TS_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  return TS_OK;
+// ---------------------------------------------------------------- fused subproblem solve
+
+// Shared-memory layout of k_lrls_fused (byte offsets; U = QR compute type).
+struct FusedLayout {
+  size_t hA, hV, hQ, htau, hred, Gi, colp, rowp, Cm, Qs, Es, Kk, Vk, Fm, CnTs, Oms, K64, V64, KV64,
+      total;
+};
+
+__host__ __device__ inline FusedLayout fused_layout(int r, int s, int k, int R, int solve,
+                                                    size_t tsz, size_t usz, bool stage_om,
+                                                    bool polish) {
+  FusedLayout L{};
+  const bool rsvd = solve == TS_SOLVE_RSVD;
+  const int n = rsvd ? k : r;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 15) & ~(size_t)15;
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  const size_t rk = rsvd ? (size_t)r * k : 0;
+  L.hA = take(usz * rk);
+  L.hV = take(usz * rk);
+  L.hQ = take(usz * rk);
+  L.htau = take(usz * (rsvd ? k : 0));
+  L.hred = take(usz * 2);
+  L.Gi = take(tsz * (size_t)r * (r + 1));
+  L.colp = take(tsz * r);
+  L.rowp = take(tsz * r);
+  L.Cm = take(tsz * rk);
+  L.Qs = take(tsz * rk);
+  L.Es = take(tsz * rk);
+  L.Kk = take(tsz * (size_t)n * n);
+  L.Vk = take(tsz * (size_t)n * n);
+  L.Fm = take(tsz * (size_t)n * R);
+  L.CnTs = take(tsz * (size_t)r * R);
+  L.Oms = take(stage_om ? tsz * (size_t)s * k : 0);
+  L.K64 = take(polish ? 8 * (size_t)n * n : 0);
+  L.V64 = take(polish ? 8 * (size_t)n * n : 0);
+  L.KV64 = take(polish ? 8 * (size_t)n * n : 0);
+  L.total = off;
+  return L;
 }
 
 template <typename T>
-ts_status launch_rsvd_stage1(int r, int k, const T* G, const T* W, T* Q, T* E, int* flag,
-                             cudaStream_t st) {
-  const size_t smem = rsvd_stage1_smem_bytes(r, k, sizeof(T));
-  TS_TRY(smem_attr((const void*)k_rsvd_stage1<T>, smem));
-  k_rsvd_stage1<T><<<1, NT, smem, st>>>(r, k, G, W, Q, E, flag);
+struct FusedArgs {
+  int r, s, k, R, solve;
+  const T* G;
+  long ldg;  // r x r
+  const T* H;
+  long ldh;      // r x s
+  const T* Om;   // s x k (RSVD)
+  T* Mbuf;       // scratch: k x s (RSVD, D) or r x s (exact, X)
+  T* CnT;        // r x R out
+  T* A_out;      // s x R out
+  T* core;
+  CoreMap map;
+  int* flag;
+  bool stage_om;
+};
+
+// The whole sketched subproblem after [G | H] = Z^T [Z | Y], in one block:
+//   G^{-1} by Gauss-Jordan (G is SPD and well conditioned: Z = S P with P orthonormal);
+//   RSVD (Alg. 5): W = H Omega, C = G^{-1} W, Q = qr(C) (Householder, type U),
+//     E = G^{-1} Q, D = E^T H (= Q^T G^{-1} Z^T Y), K = D D^T;
+//   exact: X = G^{-1} H, K = X X^T;
+//   K = U Lambda U^T (Jacobi in T, optional FP64 polish), CnT = Q U_R Sigma_R (Q = I for
+//   exact), A = M^T U_R Sigma_R^{-1} with M = D or X, canonical signs, core scatter.
+template <typename T, typename U, bool POLISH64>
+__global__ void __launch_bounds__(1024) k_lrls_fused(FusedArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int rp[kMaxEig / 2 + 1], rq[kMaxEig / 2 + 1];
+  __shared__ T rcT[kMaxEig / 2 + 1], rsT[kMaxEig / 2 + 1];
+  __shared__ double rc64[kMaxEig / 2 + 1], rs64[kMaxEig / 2 + 1];
+  __shared__ T redT[2 * 16 + 2];
+  __shared__ double red64[2 * 16 + 2];
+  __shared__ int order[kMaxEig];
+  __shared__ T lamT[kMaxEig];
+  __shared__ T sgn[64];
+  const int r = a.r, s = a.s, R = a.R;
+  const bool rsvd = a.solve == TS_SOLVE_RSVD;
+  const int k = a.k;
+  const int n = rsvd ? k : r;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nthr = blockDim.x, nwarp = nthr >> 5;
+  const int ld = r + 1;
+  const FusedLayout L = fused_layout(r, s, k, R, a.solve, sizeof(T), sizeof(U), a.stage_om,
+                                     POLISH64);
+  U* hA = reinterpret_cast<U*>(smem_raw + L.hA);
+  U* hV = reinterpret_cast<U*>(smem_raw + L.hV);
+  U* hQ = reinterpret_cast<U*>(smem_raw + L.hQ);
+  U* htau = reinterpret_cast<U*>(smem_raw + L.htau);
+  U* hred = reinterpret_cast<U*>(smem_raw + L.hred);
+  T* Gi = reinterpret_cast<T*>(smem_raw + L.Gi);
+  T* colp = reinterpret_cast<T*>(smem_raw + L.colp);
+  T* rowp = reinterpret_cast<T*>(smem_raw + L.rowp);
+  T* Cm = reinterpret_cast<T*>(smem_raw + L.Cm);
+  T* Qs = reinterpret_cast<T*>(smem_raw + L.Qs);
+  T* Es = reinterpret_cast<T*>(smem_raw + L.Es);
+  T* Kk = reinterpret_cast<T*>(smem_raw + L.Kk);
+  T* Vk = reinterpret_cast<T*>(smem_raw + L.Vk);
+  T* Fm = reinterpret_cast<T*>(smem_raw + L.Fm);
+  T* CnTs = reinterpret_cast<T*>(smem_raw + L.CnTs);
+  const T* Om = a.stage_om ? reinterpret_cast<T*>(smem_raw + L.Oms) : a.Om;
+
+  // 1. stage G (and Omega)
+  for (int i = warp; i < r; i += nwarp)
+    for (int j = lane; j < r; j += 32) Gi[i * ld + j] = a.G[i * a.ldg + j];
+  if (rsvd && a.stage_om)
+    for (int t = tid; t < s * k; t += nthr) const_cast<T*>(Om)[t] = a.Om[t];
+  __syncthreads();
+  // 2. G^{-1} in place (Gauss-Jordan, no pivoting)
+  for (int p = 0; p < r; ++p) {
+    for (int t = tid; t < r; t += nthr) {
+      colp[t] = Gi[t * ld + p];
+      rowp[t] = Gi[p * ld + t];
+    }
+    __syncthreads();
+    T piv = rowp[p];
+    if (!(piv > (T)0) || !isfinite((double)piv)) {
+      if (tid == 0 && a.flag) atomicExch(a.flag, 1);
+      piv = (T)1;
+    }
+    const T inv = (T)1 / piv;
+    for (int i = warp; i < r; i += nwarp) {
+      const T ci = colp[i] * inv;
+      for (int j = lane; j < r; j += 32) {
+        T v;
+        if (i == p) v = (j == p) ? inv : rowp[j] * inv;
+        else v = (j == p) ? -ci : Gi[i * ld + j] - ci * rowp[j];
+        Gi[i * ld + j] = v;
+      }
+    }
+    __syncthreads();
+  }
+  const T* M;  // n x s, the matrix whose Gram K is decomposed
+  if (rsvd) {
+    // 3. W = H Omega;  4. C = G^{-1} W
+    for (int e = tid; e < r * k; e += nthr) {
+      const int i = e / k, c = e - (e / k) * k;
+      const T* h = a.H + i * a.ldh;
+      T acc = 0;
+      for (int j = 0; j < s; ++j) acc += h[j] * Om[j * k + c];
+      Cm[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < r * k; e += nthr) {
+      const int i = e / k, c = e - (e / k) * k;
+      T acc = 0;
+      for (int l = 0; l < r; ++l) acc += Gi[i * ld + l] * Cm[l * k + c];
+      hA[e] = (U)acc;
+    }
+    __syncthreads();
+    // 5. Q = qr(C)
+    householder_q<U>(hA, r, k, hV, htau, hQ, hred);
+    for (int t = tid; t < r * k; t += nthr) Qs[t] = (T)hQ[t];
+    __syncthreads();
+    // 6. E = G^{-1} Q;  7. D = E^T H
+    for (int e = tid; e < r * k; e += nthr) {
+      const int i = e / k, c = e - (e / k) * k;
+      T acc = 0;
+      for (int l = 0; l < r; ++l) acc += Gi[i * ld + l] * Qs[l * k + c];
+      Es[e] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < k * s; e += nthr) {
+      const int c = e / s, j = e - (e / s) * s;
+      T acc = 0;
+      for (int i = 0; i < r; ++i) acc += Es[i * k + c] * a.H[i * a.ldh + j];
+      a.Mbuf[e] = acc;
+    }
+  } else {
+    // exact: X = G^{-1} H
+    for (int e = tid; e < r * s; e += nthr) {
+      const int i = e / s, j = e - (e / s) * s;
+      T acc = 0;
+      for (int l = 0; l < r; ++l) acc += Gi[i * ld + l] * a.H[l * a.ldh + j];
+      a.Mbuf[e] = acc;
+    }
+  }
+  __syncthreads();
+  M = a.Mbuf;
+  // 8. K = M M^T (upper triangle by warps, mirrored)
+  for (int pr = warp; pr < n * n; pr += nwarp) {
+    const int i = pr / n, j = pr - (pr / n) * n;
+    if (j < i) continue;
+    T acc = 0;
+    for (int t = lane; t < s; t += 32) acc += M[i * s + t] * M[j * s + t];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      Kk[i * n + j] = acc;
+      Kk[j * n + i] = acc;
+    }
+  }
+  for (int e = tid; e < n * n; e += nthr) Vk[e] = (e / n == e % n) ? (T)1 : (T)0;
+  __syncthreads();
+  // 9. Jacobi on K by the first nj threads
+  JacobiShape js;
+  js.n = n;
+  js.np = (n + 1) & ~1;
+  js.lg = 0;
+  while ((1 << js.lg) < n) ++js.lg;
+  const int nj = jacobi_threads(n);
+  if (tid < nj) {
+    SubSync sync{nj};
+    const T tol = sizeof(T) == 4 ? (T)1e-11 : (T)1e-28;
+    T off, tot;
+    for (int sweep = 0; sweep < 24; ++sweep) {
+      jacobi_norms<T, SubSync>(Kk, n, redT, off, tot, sync);
+      if (off <= tol * tot || tot == (T)0) break;
+      jacobi_sweep<T, SubSync>(Kk, Vk, js, rp, rq, rcT, rsT, sync);
+    }
+    if constexpr (POLISH64) {
+      double* K64 = reinterpret_cast<double*>(smem_raw + L.K64);
+      double* V64 = reinterpret_cast<double*>(smem_raw + L.V64);
+      double* KV = reinterpret_cast<double*>(smem_raw + L.KV64);
+      // exact FP64 Gram of M, then V^T K V
+      for (int pr = warp; pr < n * n; pr += (nj >> 5)) {
+        const int i = pr / n, j = pr - (pr / n) * n;
+        if (j < i) continue;
+        double acc = 0;
+        for (int t = lane; t < s; t += 32) acc += (double)M[i * s + t] * (double)M[j * s + t];
+        acc = warp_sum(acc);
+        if (lane == 0) {
+          K64[i * n + j] = acc;
+          K64[j * n + i] = acc;
+        }
+      }
+      for (int e = tid; e < n * n; e += nj) V64[e] = (double)Vk[e];
+      sync();
+      for (int e = tid; e < n * n; e += nj) {
+        const int i = e / n, j = e % n;
+        double acc = 0;
+        for (int b = 0; b < n; ++b) acc += K64[i * n + b] * V64[b * n + j];
+        KV[e] = acc;
+      }
+      sync();
+      for (int e = tid; e < n * n; e += nj) {
+        const int i = e / n, j = e % n;
+        double acc = 0;
+        for (int b = 0; b < n; ++b) acc += V64[b * n + i] * KV[b * n + j];
+        K64[e] = acc;
+      }
+      sync();
+      for (int e = tid; e < n * n; e += nj) {
+        const int i = e / n, j = e % n;
+        if (i < j) {
+          const double v = 0.5 * (K64[i * n + j] + K64[j * n + i]);
+          K64[i * n + j] = v;
+          K64[j * n + i] = v;
+        }
+      }
+      sync();
+      double o64, t64;
+      for (int sweep = 0; sweep < 10; ++sweep) {
+        jacobi_norms<double, SubSync>(K64, n, red64, o64, t64, sync);
+        if (o64 <= 1e-28 * t64 || t64 == 0) break;
+        jacobi_sweep<double, SubSync>(K64, V64, js, rp, rq, rc64, rs64, sync);
+      }
+      for (int e = tid; e < n * n; e += nj) Vk[e] = (T)V64[e];
+      if (tid < n) Kk[tid * n + tid] = (T)K64[tid * n + tid];
+    }
+  }
+  __syncthreads();
+  // 10. eigenvalues descending; Fm = U_R / sigma; CnT = Q U_R sigma (Q = I for exact)
+  if (tid == 0) {
+    for (int i = 0; i < n; ++i) {
+      lamT[i] = Kk[i * n + i];
+      order[i] = i;
+    }
+    for (int i = 0; i < n; ++i) {
+      int best = i;
+      for (int j = i + 1; j < n; ++j)
+        if (lamT[order[j]] > lamT[order[best]]) best = j;
+      const int t = order[i];
+      order[i] = order[best];
+      order[best] = t;
+    }
+    for (int i = 0; i < n; ++i)
+      if (!isfinite((double)lamT[i]) && a.flag) atomicExch(a.flag, 1);
+  }
+  __syncthreads();
+  for (int e = tid; e < n * R; e += nthr) {
+    const int i = e / R, c = e - (e / R) * R;
+    const T l = lamT[order[c]];
+    const T sig = l > (T)0 ? sqrt(l) : (T)0;
+    Fm[e] = sig > (T)0 ? Vk[i * n + order[c]] / sig : (T)0;
+  }
+  for (int e = tid; e < r * R; e += nthr) {
+    const int i = e / R, c = e - (e / R) * R;
+    const T l = lamT[order[c]];
+    const T sig = l > (T)0 ? sqrt(l) : (T)0;
+    T acc;
+    if (rsvd) {
+      acc = 0;
+      for (int b = 0; b < k; ++b) acc += Qs[i * k + b] * Vk[b * n + order[c]];
+    } else {
+      acc = Vk[i * n + order[c]];
+    }
+    CnTs[e] = acc * sig;
+  }
+  __syncthreads();
+  // 11. A = M^T Fm (unsigned), 12. canonical signs, 13. signed outputs and core
+  for (int e = tid; e < s * R; e += nthr) {
+    const int i = e / R, c = e - (e / R) * R;
+    T acc = 0;
+    for (int b = 0; b < n; ++b) acc += M[b * s + i] * Fm[b * R + c];
+    a.A_out[e] = acc;
+  }
+  __syncthreads();
+  for (int c = warp; c < R; c += nwarp) {
+    T best = (T)-1;
+    int bidx = 0x7fffffff;
+    for (int i = lane; i < s; i += 32) {
+      const T v = fabs(a.A_out[(long)i * R + c]);
+      if (v > best || (v == best && i < bidx)) {
+        best = v;
+        bidx = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) {
+        best = ob;
+        bidx = oi;
+      }
+    }
+    if (lane == 0) sgn[c] = a.A_out[(long)bidx * R + c] < (T)0 ? (T)-1 : (T)1;
+  }
+  __syncthreads();
+  for (int e = tid; e < s * R; e += nthr) {
+    const int c = e - (e / R) * R;
+    a.A_out[e] *= sgn[c];
+  }
+  for (int e = tid; e < r * R; e += nthr) {
+    const int rho = e / R, c = e - (e / R) * R;
+    const T v = sgn[c] * CnTs[e];
+    if (a.CnT) a.CnT[e] = v;
+    if (a.core) {
+      long idx = 0, stride = 1, x = rho;
+      for (int kk = a.map.order - 1; kk >= 0; --kk) {
+        int digit;
+        if (kk == a.map.n) {
+          digit = c;
+        } else {
+          digit = (int)(x % a.map.ranks[kk]);
+          x /= a.map.ranks[kk];
+        }
+        idx += digit * stride;
+        stride *= a.map.ranks[kk];
+      }
+      a.core[idx] = v;
+    }
+  }
+}
+
+size_t lrls_fused_smem_bytes(int r, int s, int k, int R, int solve, size_t tsize, bool fp64,
+                             bool* stage_om) {
+  const size_t usz = fp64 ? 8 : tsize;
+  FusedLayout L = fused_layout(r, s, k, R, solve, tsize, usz, false, fp64);
+  const size_t om = solve == TS_SOLVE_RSVD ? tsize * (size_t)s * k : 0;
+  const bool stage = om > 0 && L.total + om + 16 <= 160 * 1024;
+  if (stage_om) *stage_om = stage;
+  return fused_layout(r, s, k, R, solve, tsize, usz, stage, fp64).total + 16;
+}
+
+template <typename T>
+ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, const T* G,
+                            long ldg, const T* H, long ldh, const T* Om, T* Mbuf, T* CnT,
+                            T* A_out, T* core, CoreMap map, int* flag, cudaStream_t st) {
+  FusedArgs<T> a{};
+  a.r = r;
+  a.s = s;
+  a.k = k;
+  a.R = R;
+  a.solve = solve;
+  a.G = G;
+  a.ldg = ldg;
+  a.H = H;
+  a.ldh = ldh;
+  a.Om = Om;
+  a.Mbuf = Mbuf;
+  a.CnT = CnT;
+  a.A_out = A_out;
+  a.core = core;
+  a.map = map;
+  a.flag = flag;
+  const bool f64 = fp64 && sizeof(T) == 4;
+  const size_t smem = lrls_fused_smem_bytes(r, s, k, R, solve, sizeof(T), f64, &a.stage_om);
+  if (smem > kMaxSmem) return fail(TS_ERR_SHAPE, "fused solve: %zu bytes of shared memory", smem);
+  if (f64) {
+    TS_TRY(ensure_dynamic_smem((const void*)k_lrls_fused<T, double, true>, smem));
+    k_lrls_fused<T, double, true><<<1, 1024, smem, st>>>(a);
+  } else {
+    TS_TRY(ensure_dynamic_smem((const void*)k_lrls_fused<T, T, false>, smem));
+    k_lrls_fused<T, T, false><<<1, 1024, smem, st>>>(a);
+  }
   TS_LAUNCH_CHECK();
   return TS_OK;
+}
+
+// ---------------------------------------------------------------- launchers
+
+template <typename T>
+ts_status launch_rsvd_stage1(int r, int k, const T* G, int ldg, const T* W, int ldw, T* Q, T* E,
+                             bool qr64, int* flag, cudaStream_t st) {
+  if (qr64 && sizeof(T) == 4) {
+    const size_t smem = rsvd_stage1_smem_bytes(r, k, sizeof(T), true);
+    TS_TRY(ensure_dynamic_smem((const void*)k_rsvd_stage1<T, double>, smem));
+    k_rsvd_stage1<T, double><<<1, NT, smem, st>>>(r, k, G, ldg, W, ldw, Q, E, flag);
+  } else {
+    const size_t smem = rsvd_stage1_smem_bytes(r, k, sizeof(T), false);
+    TS_TRY(ensure_dynamic_smem((const void*)k_rsvd_stage1<T, T>, smem));
+    k_rsvd_stage1<T, T><<<1, NT, smem, st>>>(r, k, G, ldg, W, ldw, Q, E, flag);
+  }
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+size_t chol_solve_smem_bytes(int r, size_t tsize) {
+  return tsize * ((size_t)r * (r + 1) + (size_t)r * 64);
 }
 
 template <typename T>
 ts_status launch_chol_solve(int r, int s, const T* G, const T* H, T* X, int* flag,
                             cudaStream_t st) {
-  const size_t smem = sizeof(T) * ((size_t)r * r + (size_t)NWARP * r);
-  TS_TRY(smem_attr((const void*)k_chol_solve<T>, smem));
+  const size_t smem = chol_solve_smem_bytes(r, sizeof(T));
+  TS_TRY(ensure_dynamic_smem((const void*)k_chol_solve<T>, smem));
   k_chol_solve<T><<<1, NT, smem, st>>>(r, s, G, H, X, flag);
   TS_LAUNCH_CHECK();
   return TS_OK;
@@ -468,31 +1122,53 @@ ts_status launch_chol_solve(int r, int s, const T* G, const T* H, T* X, int* fla
 
 template <typename T>
 ts_status launch_eig_small(int n, int R, const T* K, const T* Q, int r, T* CnT, T* Fm, T* Uout,
-                           int* flag, cudaStream_t st) {
-  if (n > kMaxEig) return fail(TS_ERR_SHAPE, "eigensolver: n=%d > %d", n, kMaxEig);
-  const size_t smem = (size_t)n * n * (3 * sizeof(double) + 2 * sizeof(T));
-  TS_TRY(smem_attr((const void*)k_eig_small<T>, smem));
-  k_eig_small<T><<<1, NT, smem, st>>>(n, R, K, Q, r, CnT, Fm, Uout, flag);
+                           bool polish64, int* flag, cudaStream_t st) {
+  if (n > kMaxEig || n < 1)
+    return fail(TS_ERR_SHAPE, "eigensolver: n=%d outside [1,%d]", n, kMaxEig);
+  JacobiShape js;
+  js.n = n;
+  js.np = (n + 1) & ~1;
+  js.lg = 0;
+  while ((1 << js.lg) < n) ++js.lg;
+  const int work = (js.np / 2) << js.lg;
+  int threads = work < NT ? ((work + 31) / 32) * 32 : NT;
+  if (threads < 64) threads = 64;
+  const size_t nn = (size_t)n * n;
+  if (polish64 && sizeof(T) == 4) {
+    const size_t smem = nn * 2 * sizeof(T) + 8 + nn * 3 * sizeof(double);
+    TS_TRY(ensure_dynamic_smem((const void*)k_eig_small<T, true>, smem));
+    k_eig_small<T, true><<<1, threads, smem, st>>>(n, R, js, K, Q, r, CnT, Fm, Uout, flag);
+  } else {
+    const size_t smem = nn * 2 * sizeof(T);
+    TS_TRY(ensure_dynamic_smem((const void*)k_eig_small<T, false>, smem));
+    k_eig_small<T, false><<<1, threads, smem, st>>>(n, R, js, K, Q, r, CnT, Fm, Uout, flag);
+  }
   TS_LAUNCH_CHECK();
   return TS_OK;
 }
 
 template <typename T>
-ts_status launch_finalize(int s, int R, const T* V, T* A_out, T* CnT, int r, T* core, CoreMap map,
-                          cudaStream_t st) {
-  k_finalize<T><<<R, 256, 0, st>>>(s, R, V, A_out, CnT, r, core, map);
+ts_status launch_finalize(int s, int R, const T* M, long rs, long cs, int kdim, const T* Fm,
+                          T* A_out, T* CnT, int r, T* core, CoreMap map, cudaStream_t st) {
+  k_finalize<T><<<R, 256, 0, st>>>(s, R, M, rs, cs, kdim, Fm, A_out, CnT, r, core, map);
   TS_LAUNCH_CHECK();
   return TS_OK;
 }
 
 #define TS_INST(T)                                                                               \
-  template ts_status launch_rsvd_stage1<T>(int, int, const T*, const T*, T*, T*, int*,          \
-                                           cudaStream_t);                                        \
+  template ts_status launch_rsvd_stage1<T>(int, int, const T*, int, const T*, int, T*, T*, bool, \
+                                           int*, cudaStream_t);                                  \
   template ts_status launch_chol_solve<T>(int, int, const T*, const T*, T*, int*, cudaStream_t); \
-  template ts_status launch_eig_small<T>(int, int, const T*, const T*, int, T*, T*, T*, int*,   \
-                                         cudaStream_t);                                          \
-  template ts_status launch_finalize<T>(int, int, const T*, T*, T*, int, T*, CoreMap,           \
-                                        cudaStream_t);
+  template ts_status launch_eig_small<T>(int, int, const T*, const T*, int, T*, T*, T*, bool,   \
+                                         int*, cudaStream_t);                                    \
+  template ts_status launch_finalize<T>(int, int, const T*, long, long, int, const T*, T*, T*,  \
+                                        int, T*, CoreMap, cudaStream_t);                         \
+  template ts_status launch_lrls_fused<T>(int, int, int, int, int, bool, const T*, long,        \
+                                          const T*, long, const T*, T*, T*, T*, T*, CoreMap,     \
+                                          int*, cudaStream_t);                                   \
+  template ts_status launch_qr_only<T>(int, int, const T*, T*, bool, cudaStream_t);             \
+  template ts_status newton_schulz_inverse<T>(int, const T*, long, T*, T*, T*, int,             \
+                                              const GemmSplit<T>*, cudaStream_t);
 TS_INST(float)
 TS_INST(double)
 #undef TS_INST

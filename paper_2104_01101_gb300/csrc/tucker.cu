@@ -1,10 +1,14 @@
 // Host orchestration of Sketch-Tucker-ALS (Alg. 4) and the C-ABI entry points
 // that compose the kernels: Init-RRF (Alg. 3), the sketched subproblem solve
-// (Alg. 5 / exact), the leverage-score sketch, the fitness and the driver itself.
-// Every step runs on the caller's stream in the caller's scratch; the host only
-// validates, carves the workspace and enqueues kernels.
+// (Alg. 5 / exact), the leverage-score sketch, the fitness, the driver itself and
+// CP-Sketch-Tucker (Alg. 6).  Every step runs on the caller's stream in the
+// caller's scratch; the host only validates, carves the workspace and enqueues.
 #include <math.h>
 #include <string.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -54,6 +58,15 @@ static void rrf_widths(const ts_tensor& X, int n, int R, int m, int k1_opt, int 
   *k2o = (int)k2;
 }
 
+// The fused single-block solve applies when Z^T Y (r x s) is small enough to form
+// and the block's shared-memory layout fits.
+static bool fused_ok(int r, long s, int kc, int R, int solve, size_t tsize, bool fp64) {
+  if ((long)r * s > (1l << 22)) return false;
+  const int n = solve == TS_SOLVE_RSVD ? kc : r;
+  if (n > kMaxEig) return false;
+  return lrls_fused_smem_bytes(r, (int)s, kc, R, solve, tsize, fp64, nullptr) <= kMaxSmem;
+}
+
 static int rsvd_width(int R, int p, int r, int64_t s) {
   long k = R + p;
   if (k > r) k = r;
@@ -69,10 +82,15 @@ struct Shape {
   int solve;
   int oversample;
   bool rrf;
+  bool fp64solve;  // FP64 QR / polish on FP32 data
   int ranks[TS_MAX_ORDER];
-  int r[TS_MAX_ORDER];     // prod_{k != n} ranks[k]
-  int kc[TS_MAX_ORDER];    // RSVD width of subproblem n
+  int r[TS_MAX_ORDER];   // prod_{k != n} ranks[k]
+  int kc[TS_MAX_ORDER];  // RSVD width of subproblem n
+  bool fused[TS_MAX_ORDER];  // subproblem n takes the fused single-block solve
+  bool large[TS_MAX_ORDER];  // subproblem n inverts Z^T Z by Newton-Schulz (large r)
   int k1[TS_MAX_ORDER], k2[TS_MAX_ORDER];
+  size_t om_off[TS_MAX_ORDER];  // offset of Omega(sweep, n) inside one sweep's block
+  size_t om_sweep;              // elements of all Omegas of one sweep
   int64_t smax;
   int rmax, kmax, Rmax, k1max, k2max, chain_cols_max;
 };
@@ -98,8 +116,11 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
   S.solve = opt->solve;
   S.oversample = opt->rsvd_oversample < 0 ? 5 : opt->rsvd_oversample;
   S.rrf = !opt->init_given;
+  S.fp64solve = opt->solve_fp64 != 0 && X->dtype == TS_F32;
   S.smax = 0;
   S.rmax = S.kmax = S.Rmax = S.k1max = S.k2max = S.chain_cols_max = 0;
+  S.om_sweep = 0;
+  const size_t tsz = dtype_size(X->dtype);
   for (int k = 0; k < S.N; ++k) {
     if (ranks[k] < 1 || ranks[k] >= X->dims[k])
       return fail(TS_ERR_SHAPE, "tucker_als_sketched: rank[%d]=%d must lie in [1, dims[%d]=%lld)",
@@ -124,22 +145,32 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
       return fail(TS_ERR_SHAPE,
                   "tucker_als_sketched: m=%d < prod of the other ranks (%ld) for mode %d", m, r, n);
     S.r[n] = (int)r;
-    if (S.solve == TS_SOLVE_RSVD && r > kMaxCholSmem)
-      return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: r=%ld > %d for the RSVD solve", r,
-                  kMaxCholSmem);
-    if (S.solve == TS_SOLVE_EXACT && r > kMaxEig)
-      return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: r=%ld > %d for the exact solve", r,
-                  kMaxEig);
     S.kc[n] = rsvd_width(ranks[n], S.oversample, (int)r, X->dims[n]);
-    if (S.kc[n] > kMaxEig)
-      return fail(TS_ERR_SHAPE, "tucker_als_sketched: RSVD width %d > %d", S.kc[n], kMaxEig);
-    if (S.solve == TS_SOLVE_RSVD &&
-        rsvd_stage1_smem_bytes((int)r, S.kc[n], dtype_size(X->dtype)) > kMaxSmem)
-      return fail(TS_ERR_UNSUPPORTED,
-                  "tucker_als_sketched: r=%ld too large for the on-chip RSVD solve", r);
+    S.fused[n] = fused_ok((int)r, X->dims[n], S.kc[n], ranks[n], S.solve, tsz, S.fp64solve);
+    S.large[n] = false;
+    if (S.fused[n]) {
+      // the fused block solve covers this subproblem
+    } else if (S.solve == TS_SOLVE_RSVD) {
+      if (S.kc[n] > kMaxEig)
+        return fail(TS_ERR_SHAPE, "tucker_als_sketched: RSVD width %d > %d", S.kc[n], kMaxEig);
+      if (rsvd_stage1_smem_bytes((int)r, S.kc[n], tsz, S.fp64solve) > kMaxSmem) {
+        // G^{-1} by Newton-Schulz products, QR in one block
+        if (qr_only_smem_bytes((int)r, S.kc[n], S.fp64solve, tsz) > kMaxSmem)
+          return fail(TS_ERR_UNSUPPORTED,
+                      "tucker_als_sketched: r=%ld, k=%d too large for the RSVD solve", r,
+                      S.kc[n]);
+        S.large[n] = true;
+      }
+    } else {
+      if (r > kMaxEig || chol_solve_smem_bytes((int)r, tsz) > kMaxSmem)
+        return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: r=%ld > %d for the exact solve", r,
+                    kMaxEig);
+    }
     if (r > S.rmax) S.rmax = (int)r;
     if (S.kc[n] > S.kmax) S.kmax = S.kc[n];
     if (cc > S.chain_cols_max) S.chain_cols_max = cc;
+    S.om_off[n] = S.om_sweep;
+    S.om_sweep += (size_t)X->dims[n] * S.kc[n];
     S.k1[n] = S.k2[n] = 0;
     if (S.rrf && n >= 1) {
       rrf_widths(*X, n, ranks[n], m, opt->rrf_k1, opt->rrf_k2, &S.k1[n], &S.k2[n]);
@@ -157,34 +188,32 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
 template <typename T>
 struct Work {
   int* flag;
+  unsigned* counters;
+  GemmSplit<T> split;
   int32_t* tab[TS_MAX_ORDER][TS_MAX_ORDER];
   int32_t* rtab[TS_MAX_ORDER][TS_MAX_ORDER];
   T* Y[TS_MAX_ORDER];
   T* Wt[TS_MAX_ORDER];
   Cx<T>* tw;
   Cx<T>* spectra;
-  T *Z, *G, *W, *YO, *Om, *Q, *E, *Mm, *D, *K, *CnT, *Fm, *V, *H, *Xs, *Gm, *Bm, *Ylev;
+  T* ZW;   // column-major m x (r + k): Z, then Y Omega
+  T* GW;   // [Z^T Z | Z^T Y Omega] (r x (r + k)) or [Z^T Z | Z^T Y] (r x (r + s), fused path)
+  T* Mbuf; // fused path: D (k x s) or X (r x s)
+  T *Ginv, *NS1, *NS2, *Cb;  // large-r path: G^{-1}, Newton-Schulz scratch, C = G^{-1} W
+  T* Om;   // Omega of every (sweep, mode), s_n x k_n each
+  T *Q, *E, *Mm, *D, *K, *CnT, *Fm, *H, *Xs, *Gm, *Bm, *Ylev;
   int32_t* samples;
   double* levscr;
-  T* partial;
-  size_t partial_elems;
   T* fitQ;
   double* fitacc;
 };
 
 template <typename T>
 static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& b, Work<T>& w) {
+  memset(&w, 0, sizeof(w));
   const int N = S.N, m = S.m;
   w.flag = b.take<int>(64);
-  for (int n = 0; n < N; ++n)
-    for (int k = 0; k < N; ++k) {
-      w.tab[n][k] = nullptr;
-      w.rtab[n][k] = nullptr;
-    }
-  for (int n = 0; n < N; ++n) {
-    w.Y[n] = nullptr;
-    w.Wt[n] = nullptr;
-  }
+  w.counters = b.take<unsigned>(kGemmCounters);
   if (S.kind == TS_TENSORSKETCH) {
     for (int n = 0; n < N; ++n)
       for (int k = 0; k < N; ++k)
@@ -192,9 +221,6 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
     for (int n = 0; n < N; ++n) w.Y[n] = b.take<T>((size_t)m * X.dims[n]);
     w.tw = b.take<Cx<T>>((size_t)m);
     w.spectra = b.take<Cx<T>>((size_t)m * S.chain_cols_max);
-  } else {
-    w.tw = nullptr;
-    w.spectra = nullptr;
   }
   if (S.rrf) {
     for (int n = 1; n < N; ++n) {
@@ -204,19 +230,32 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
     }
     w.Gm = b.take<T>((size_t)S.k2max * S.k1max);
     w.Bm = b.take<T>((size_t)S.smax * S.k1max);
-  } else {
-    w.Gm = w.Bm = nullptr;
   }
   const int r = S.rmax, k = S.kmax, R = S.Rmax;
   const int64_t s = S.smax;
   int eign = k;
   if (S.solve == TS_SOLVE_EXACT && r > eign) eign = r;
   if (S.k1max > eign) eign = S.k1max;
-  w.Z = b.take<T>((size_t)m * r);
-  w.G = b.take<T>((size_t)r * r);
-  w.W = b.take<T>((size_t)r * k);
-  w.YO = b.take<T>((size_t)m * k);
-  w.Om = b.take<T>((size_t)s * k);
+  size_t gw = (size_t)r * (r + k), mb = 0;
+  for (int n = 0; n < N; ++n)
+    if (S.fused[n]) {
+      const size_t h = (size_t)S.r[n] * (S.r[n] + X.dims[n]);
+      const size_t nn = S.solve == TS_SOLVE_RSVD ? S.kc[n] : S.r[n];
+      if (h > gw) gw = h;
+      if (nn * X.dims[n] > mb) mb = nn * X.dims[n];
+    }
+  w.ZW = b.take<T>((size_t)m * (r + k));
+  w.GW = b.take<T>(gw);
+  w.Mbuf = b.take<T>(mb);
+  bool any_large = false;
+  for (int n = 0; n < N; ++n) any_large |= S.large[n];
+  if (any_large) {
+    w.Ginv = b.take<T>((size_t)r * r);
+    w.NS1 = b.take<T>(2 * (size_t)r * r);
+    w.NS2 = b.take<T>((size_t)r * r);
+    w.Cb = b.take<T>((size_t)r * k);
+  }
+  if (S.solve == TS_SOLVE_RSVD) w.Om = b.take<T>(S.om_sweep * S.sweeps);
   w.Q = b.take<T>((size_t)r * k);
   w.E = b.take<T>((size_t)r * k);
   w.Mm = b.take<T>((size_t)m * k);
@@ -224,12 +263,9 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
   w.K = b.take<T>((size_t)eign * eign);
   w.CnT = b.take<T>((size_t)r * R);
   w.Fm = b.take<T>((size_t)eign * R);
-  w.V = b.take<T>((size_t)s * R);
   if (S.solve == TS_SOLVE_EXACT) {
     w.H = b.take<T>((size_t)r * s);
     w.Xs = b.take<T>((size_t)r * s);
-  } else {
-    w.H = w.Xs = nullptr;
   }
   if (S.kind == TS_LEVERAGE) {
     w.Ylev = b.take<T>((size_t)m * s);
@@ -240,25 +276,19 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
       if (t > lv) lv = t;
     }
     w.levscr = b.take<double>(lv);
-  } else {
-    w.Ylev = nullptr;
-    w.samples = nullptr;
-    w.levscr = nullptr;
   }
-  size_t pm = (size_t)r * r;
-  const size_t cands[] = {(size_t)r * k, (size_t)m * k, (size_t)k * s, (size_t)s * R,
-                          (size_t)eign * eign, (size_t)s * S.k1max,
+  size_t pm = (size_t)r * (r + k);
+  const size_t cands[] = {(size_t)m * k, (size_t)k * s, (size_t)eign * eign, (size_t)s * S.k1max,
                           S.solve == TS_SOLVE_EXACT ? (size_t)r * s : 0};
   for (size_t c : cands)
     if (c > pm) pm = c;
-  w.partial_elems = 32 * pm;
-  w.partial = b.take<T>(w.partial_elems);
+  w.split.partial_elems = 32 * pm;
+  w.split.partial = b.take<T>(w.split.partial_elems);
+  w.split.counters = w.counters;
+  w.split.ncounters = kGemmCounters;
   if (want_residual && X.format == TS_DENSE) {
     w.fitQ = b.take<T>(fit_dense_scratch_elems<T>(X, S.ranks));
     w.fitacc = b.take<double>(2);
-  } else {
-    w.fitQ = nullptr;
-    w.fitacc = nullptr;
   }
 }
 
@@ -273,48 +303,60 @@ static OutView<T> ov(T* p, long rs, long cs) {
   return OutView<T>{p, rs, cs};
 }
 
-// Sketched subproblem: Z (column-major m x r), Y (m x s) -> CnT (r x R), A_out (s x R),
-// core scattered when core != null.  RSVD (Alg. 5) or exact (Theorem 4.1's solution).
+// Sketched subproblem on Z = ZW[:, :r] (column-major) and Y (m x s) -> CnT (r x R),
+// A_out (s x R), core scattered when core != null.  RSVD (Alg. 5) with the test
+// matrix Om (s x k), or the exact truncated solve (the solution of Theorem 4.1).
 template <typename T>
-static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc, uint64_t seed,
-                                  int sweep, int n, const T* Z, const T* Y, Work<T>& w, T* A_out,
-                                  T* core, const CoreMap& map, cudaStream_t st) {
-  const MatView<T> Zt = mv<T>(Z, m, 1);  // r x m view of Z^T
-  const MatView<T> Zm = mv<T>(Z, 1, m);  // m x r view of Z
-  T* P = w.partial;
-  const size_t PE = w.partial_elems;
-  // G = Z^T Z
-  TS_TRY(gemm<T>(r, r, m, 1.0, Zt, Zm, 0.0, ov<T>(w.G, r, 1), P, PE, st));
+static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc, bool fp64,
+                                  const T* Om, const T* Y, Work<T>& w, T* A_out, T* core,
+                                  const CoreMap& map, cudaStream_t st) {
+  T* ZW = w.ZW;
+  const MatView<T> Zt = mv<T>(ZW, m, 1);  // r x m view of Z^T
+  const MatView<T> Zm = mv<T>(ZW, 1, m);  // m x r view of Z
+  const GemmSplit<T>* sp = &w.split;
+  if (fused_ok(r, s, kc, R, solve, sizeof(T), fp64)) {
+    // [G | H] = Z^T [Z | Y] in one product, then the whole solve in one block
+    TS_TRY(gemm2<T>(r, r + s, m, 1.0, Zt, mv<T>(ZW, 1, m), r, mv<T>(Y, s, 1), 0.0,
+                    ov<T>(w.GW, r + s, 1), sp, st));
+    return launch_lrls_fused<T>(r, s, kc, R, solve, fp64, w.GW, r + s, w.GW + r, r + s, Om,
+                                w.Mbuf, w.CnT, A_out, core, map, w.flag, st);
+  }
   if (solve == TS_SOLVE_RSVD) {
     const int k = kc;
-    TS_TRY(launch_gaussian<T>(seed, make_tag(TS_PURPOSE_RSVD_GAUSS, sweep, n, 0), (int64_t)s * k,
-                              1.0, w.Om, st));
-    // YO = Y Omega (m x k);  W = Z^T YO (r x k)
-    TS_TRY(gemm<T>(m, k, s, 1.0, mv<T>(Y, s, 1), mv<T>(w.Om, k, 1), 0.0, ov<T>(w.YO, k, 1), P, PE,
-                   st));
-    TS_TRY(gemm<T>(r, k, m, 1.0, Zt, mv<T>(w.YO, k, 1), 0.0, ov<T>(w.W, k, 1), P, PE, st));
-    TS_TRY(launch_rsvd_stage1<T>(r, k, w.G, w.W, w.Q, w.E, w.flag, st));
+    // Y Omega into the k columns after Z, then [G | W] = Z^T [Z | Y Omega] in one product
+    TS_TRY(gemm<T>(m, k, s, 1.0, mv<T>(Y, s, 1), mv<T>(Om, k, 1), 0.0,
+                   ov<T>(ZW + (size_t)r * m, 1, m), sp, st));
+    TS_TRY(gemm<T>(r, r + k, m, 1.0, Zt, mv<T>(ZW, 1, m), 0.0, ov<T>(w.GW, r + k, 1), sp, st));
+    if (rsvd_stage1_smem_bytes(r, k, sizeof(T), fp64) <= kMaxSmem) {
+      TS_TRY(launch_rsvd_stage1<T>(r, k, w.GW, r + k, w.GW + r, r + k, w.Q, w.E, fp64, w.flag,
+                                   st));
+    } else {
+      // G^{-1} by Newton-Schulz; C = G^{-1} W; Q = qr(C); E = G^{-1} Q
+      TS_TRY(newton_schulz_inverse<T>(r, w.GW, r + k, w.Ginv, w.NS1, w.NS2, kNewtonSchulzIters,
+                                      sp, st));
+      TS_TRY(gemm<T>(r, k, r, 1.0, mv<T>(w.Ginv, r, 1), mv<T>(w.GW + r, r + k, 1), 0.0,
+                     ov<T>(w.Cb, k, 1), sp, st));
+      TS_TRY(launch_qr_only<T>(r, k, w.Cb, w.Q, fp64, st));
+      TS_TRY(gemm<T>(r, k, r, 1.0, mv<T>(w.Ginv, r, 1), mv<T>(w.Q, k, 1), 0.0, ov<T>(w.E, k, 1),
+                     sp, st));
+    }
     // M = Z E (m x k);  D = M^T Y (k x s);  K = D D^T (k x k)
-    TS_TRY(gemm<T>(m, k, r, 1.0, Zm, mv<T>(w.E, k, 1), 0.0, ov<T>(w.Mm, k, 1), P, PE, st));
-    TS_TRY(gemm<T>(k, s, m, 1.0, mv<T>(w.Mm, 1, k), mv<T>(Y, s, 1), 0.0, ov<T>(w.D, s, 1), P, PE,
+    TS_TRY(gemm<T>(m, k, r, 1.0, Zm, mv<T>(w.E, k, 1), 0.0, ov<T>(w.Mm, k, 1), sp, st));
+    TS_TRY(gemm<T>(k, s, m, 1.0, mv<T>(w.Mm, 1, k), mv<T>(Y, s, 1), 0.0, ov<T>(w.D, s, 1), sp, st));
+    TS_TRY(gemm<T>(k, k, s, 1.0, mv<T>(w.D, s, 1), mv<T>(w.D, 1, s), 0.0, ov<T>(w.K, k, 1), sp,
                    st));
-    TS_TRY(gemm<T>(k, k, s, 1.0, mv<T>(w.D, s, 1), mv<T>(w.D, 1, s), 0.0, ov<T>(w.K, k, 1), P, PE,
-                   st));
-    TS_TRY(launch_eig_small<T>(k, R, w.K, w.Q, r, w.CnT, w.Fm, nullptr, w.flag, st));
-    // V = D^T Fm (s x R)
-    TS_TRY(gemm<T>(s, R, k, 1.0, mv<T>(w.D, 1, s), mv<T>(w.Fm, R, 1), 0.0, ov<T>(w.V, R, 1), P,
-                   PE, st));
-  } else {
-    // H = Z^T Y (r x s);  X = G^{-1} H;  K = X X^T;  V = X^T Fm
-    TS_TRY(gemm<T>(r, s, m, 1.0, Zt, mv<T>(Y, s, 1), 0.0, ov<T>(w.H, s, 1), P, PE, st));
-    TS_TRY(launch_chol_solve<T>(r, s, w.G, w.H, w.Xs, w.flag, st));
-    TS_TRY(gemm<T>(r, r, s, 1.0, mv<T>(w.Xs, s, 1), mv<T>(w.Xs, 1, s), 0.0, ov<T>(w.K, r, 1), P,
-                   PE, st));
-    TS_TRY(launch_eig_small<T>(r, R, w.K, nullptr, r, w.CnT, w.Fm, nullptr, w.flag, st));
-    TS_TRY(gemm<T>(s, R, r, 1.0, mv<T>(w.Xs, 1, s), mv<T>(w.Fm, R, 1), 0.0, ov<T>(w.V, R, 1), P,
-                   PE, st));
+    TS_TRY(launch_eig_small<T>(k, R, w.K, w.Q, r, w.CnT, w.Fm, nullptr, fp64, w.flag, st));
+    // A = D^T Fm, signed; core written
+    return launch_finalize<T>(s, R, w.D, 1, s, k, w.Fm, A_out, w.CnT, r, core, map, st);
   }
-  return launch_finalize<T>(s, R, w.V, A_out, w.CnT, r, core, map, st);
+  // exact: G = Z^T Z;  H = Z^T Y;  X = G^{-1} H;  K = X X^T;  A = X^T Fm
+  TS_TRY(gemm<T>(r, r, m, 1.0, Zt, Zm, 0.0, ov<T>(w.GW, r, 1), sp, st));
+  TS_TRY(gemm<T>(r, s, m, 1.0, Zt, mv<T>(Y, s, 1), 0.0, ov<T>(w.H, s, 1), sp, st));
+  TS_TRY(launch_chol_solve<T>(r, s, w.GW, w.H, w.Xs, w.flag, st));
+  TS_TRY(gemm<T>(r, r, s, 1.0, mv<T>(w.Xs, s, 1), mv<T>(w.Xs, 1, s), 0.0, ov<T>(w.K, r, 1), sp,
+                 st));
+  TS_TRY(launch_eig_small<T>(r, R, w.K, nullptr, r, w.CnT, w.Fm, nullptr, fp64, w.flag, st));
+  return launch_finalize<T>(s, R, w.Xs, 1, s, r, w.Fm, A_out, w.CnT, r, core, map, st);
 }
 
 template <typename T>
@@ -337,7 +379,7 @@ static ts_status sketch_rhs_all(const ts_tensor& X, const Shape& S, Work<T>& w, 
     jobs[n].out = w.Y[n];
     for (int k = 0; k < S.N; ++k) jobs[n].tables[k] = w.tab[n][k];
   }
-  return launch_input_sketch<T>(X, jobs, S.N, st);
+  return launch_input_sketch<T>(X, jobs, S.N, w.flag, st);
 }
 
 // Init-RRF (Alg. 3) for every mode n >= 1: one pass over X for all CountSketch
@@ -358,7 +400,7 @@ static ts_status rrf_all(const ts_tensor& X, const Shape& S, uint64_t seed, Work
     for (int k = 0; k < S.N; ++k) jobs[nj].tables[k] = w.rtab[n][k];
     ++nj;
   }
-  TS_TRY(launch_input_sketch<T>(X, jobs, nj, st));
+  TS_TRY(launch_input_sketch<T>(X, jobs, nj, w.flag, st));
   CoreMap none{};
   for (int n = 1; n < S.N; ++n) {
     const int k1 = S.k1[n], k2 = S.k2[n], R = S.ranks[n];
@@ -366,14 +408,27 @@ static ts_status rrf_all(const ts_tensor& X, const Shape& S, uint64_t seed, Work
     TS_TRY(launch_gaussian<T>(seed, make_tag(TS_PURPOSE_RRF_GAUSS, 0, n, 0), (int64_t)k2 * k1,
                               1.0 / sqrt((double)k1), w.Gm, st));
     TS_TRY(gemm<T>(s, k1, k2, 1.0, mv<T>(w.Wt[n], 1, s), mv<T>(w.Gm, k1, 1), 0.0,
-                   ov<T>(w.Bm, k1, 1), w.partial, w.partial_elems, st));
+                   ov<T>(w.Bm, k1, 1), &w.split, st));
     TS_TRY(gemm<T>(k1, k1, s, 1.0, mv<T>(w.Bm, 1, k1), mv<T>(w.Bm, k1, 1), 0.0, ov<T>(w.K, k1, 1),
-                   w.partial, w.partial_elems, st));
-    TS_TRY(launch_eig_small<T>(k1, R, w.K, nullptr, k1, nullptr, w.Fm, nullptr, w.flag, st));
-    TS_TRY(gemm<T>(s, R, k1, 1.0, mv<T>(w.Bm, k1, 1), mv<T>(w.Fm, R, 1), 0.0, ov<T>(w.V, R, 1),
-                   w.partial, w.partial_elems, st));
-    TS_TRY(launch_finalize<T>(s, R, w.V, factors[n], nullptr, 0, nullptr, none, st));
+                   &w.split, st));
+    TS_TRY(launch_eig_small<T>(k1, R, w.K, nullptr, k1, nullptr, w.Fm, nullptr, S.fp64solve,
+                               w.flag, st));
+    TS_TRY(launch_finalize<T>(s, R, w.Bm, k1, 1, k1, w.Fm, factors[n], nullptr, 0, nullptr, none,
+                              st));
   }
+  return TS_OK;
+}
+
+// Gaussian test matrices of Alg. 5 for every (sweep, mode), drawn in one launch
+// per block: Omega(sweep, n) is the object (seed, RSVD_GAUSS, sweep, n, 0).
+template <typename T>
+static ts_status draw_omegas(const ts_tensor& X, const Shape& S, uint64_t seed, Work<T>& w,
+                             cudaStream_t st) {
+  for (int sweep = 0; sweep < S.sweeps; ++sweep)
+    for (int n = 0; n < S.N; ++n)
+      TS_TRY(launch_gaussian<T>(seed, make_tag(TS_PURPOSE_RSVD_GAUSS, sweep, n, 0),
+                                (int64_t)X.dims[n] * S.kc[n], 1.0,
+                                w.Om + S.om_sweep * sweep + S.om_off[n], st));
   return TS_OK;
 }
 
@@ -391,14 +446,18 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
   carve<T>(X, S, residual_out != nullptr, b, w);
   const int N = S.N, m = S.m;
   TS_TRY(phase(opt, 0, st));
-  TS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
+  TS_CUDA(cudaMemsetAsync(w.flag, 0, 256 + kGemmCounters * sizeof(unsigned), st));
   if (S.rrf) TS_TRY(rrf_all<T>(X, S, opt.seed, w, factors, st));
   TS_TRY(phase(opt, 1, st));
+  if (S.solve == TS_SOLVE_RSVD) TS_TRY(draw_omegas<T>(X, S, opt.seed, w, st));
   if (S.kind == TS_TENSORSKETCH) {
     TS_TRY(launch_twiddles<T>(m, w.tw, st));
     TS_TRY(build_ts_tables<T>(X, S, opt.seed, 0, w, st));
     TS_TRY(phase(opt, 2, st));
     TS_TRY(sketch_rhs_all<T>(X, S, w, st));
+    TS_TRY(phase(opt, 3, st));
+  } else {
+    TS_TRY(phase(opt, 2, st));
     TS_TRY(phase(opt, 3, st));
   }
   const T* chain[TS_MAX_ORDER];
@@ -422,19 +481,20 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
             cols[nf] = S.ranks[k];
             ++nf;
           }
-        TS_TRY(launch_ts_apply<T>(nf, chain, rows, cols, ctab, m, w.tw, w.spectra, w.Z, st));
+        TS_TRY(launch_ts_apply<T>(nf, chain, rows, cols, ctab, m, w.tw, w.spectra, w.ZW, st));
         Yn = w.Y[n];
       } else {
-        TS_TRY(launch_leverage<T>(X, n, S.ranks, (const T* const*)factors, m, opt.seed, sweep, w.Z,
-                                  w.Ylev, w.samples, w.levscr, st));
+        TS_TRY(launch_leverage<T>(X, n, S.ranks, (const T* const*)factors, m, opt.seed, sweep,
+                                  w.ZW, w.Ylev, w.samples, w.levscr, st));
         Yn = w.Ylev;
       }
       CoreMap map{};
       map.order = N;
       map.n = n;
       for (int k = 0; k < N; ++k) map.ranks[k] = S.ranks[k];
-      TS_TRY(solve_subproblem<T>(m, S.r[n], (int)X.dims[n], S.ranks[n], S.solve, S.kc[n], opt.seed,
-                                 sweep, n, w.Z, Yn, w, factors[n], core, map, st));
+      const T* Om = w.Om ? w.Om + S.om_sweep * sweep + S.om_off[n] : nullptr;
+      TS_TRY(solve_subproblem<T>(m, S.r[n], (int)X.dims[n], S.ranks[n], S.solve, S.kc[n],
+                                 S.fp64solve, Om, Yn, w, factors[n], core, map, st));
     }
     if (residual_out && opt.track_fit)
       TS_TRY(launch_fit_dense<T>(X, S.ranks, core, (const T* const*)factors, w.fitQ, w.fitacc,
@@ -445,6 +505,62 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
     TS_TRY(launch_fit_dense<T>(X, S.ranks, core, (const T* const*)factors, w.fitQ, w.fitacc,
                                residual_out, st));
   TS_TRY(phase(opt, 5, st));
+  return TS_OK;
+}
+
+// ---------------------------------------------------------------- graph replay
+
+// Small per-device cache of instantiated CUDA graphs keyed by the full argument set.
+// Capture runs on a library-owned stream (the legacy default stream cannot be
+// captured); the executable graph is then launched on the caller's stream.
+struct GraphEntry {
+  std::string key;
+  int device;
+  cudaGraphExec_t exec;
+};
+static std::mutex g_graph_mu;
+static std::vector<GraphEntry> g_graphs;  // most recent last
+static cudaStream_t g_capture_stream[64] = {};
+constexpr size_t kMaxGraphs = 8;
+
+template <typename F>
+static ts_status graph_replay(const std::string& key, F&& enqueue, cudaStream_t st) {
+  int dev = 0;
+  TS_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return enqueue(st);
+  std::lock_guard<std::mutex> lock(g_graph_mu);
+  for (size_t i = 0; i < g_graphs.size(); ++i)
+    if (g_graphs[i].device == dev && g_graphs[i].key == key) {
+      GraphEntry e = g_graphs[i];
+      g_graphs.erase(g_graphs.begin() + i);
+      g_graphs.push_back(e);
+      TS_CUDA(cudaGraphLaunch(e.exec, st));
+      return TS_OK;
+    }
+  if (!g_capture_stream[dev])
+    TS_CUDA(cudaStreamCreateWithFlags(&g_capture_stream[dev], cudaStreamNonBlocking));
+  cudaStream_t cs = g_capture_stream[dev];
+  TS_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  ts_status s = enqueue(cs);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ec = cudaStreamEndCapture(cs, &graph);
+  if (s != TS_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (ec != cudaSuccess)
+    return fail(TS_ERR_CUDA, "graph capture failed: %s", cudaGetErrorString(ec));
+  cudaGraphExec_t exec = nullptr;
+  ec = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ec != cudaSuccess)
+    return fail(TS_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(ec));
+  if (g_graphs.size() >= kMaxGraphs) {
+    cudaGraphExecDestroy(g_graphs.front().exec);
+    g_graphs.erase(g_graphs.begin());
+  }
+  g_graphs.push_back(GraphEntry{key, dev, exec});
+  TS_CUDA(cudaGraphLaunch(exec, st));
   return TS_OK;
 }
 
@@ -492,11 +608,36 @@ extern "C" ts_status tucker_als_sketched(const ts_tensor* X, const int32_t* rank
     return fail(TS_ERR_WORKSPACE, "tucker_als_sketched: need %zu bytes of 256-aligned workspace",
                 need);
   cudaStream_t st = (cudaStream_t)stream;
-  if (X->dtype == TS_F64)
-    return als_impl<double>(*X, S, *opt, workspace, static_cast<double*>(core_out),
-                            reinterpret_cast<double* const*>(factors_inout), residual_out, st);
-  return als_impl<float>(*X, S, *opt, workspace, static_cast<float*>(core_out),
-                         reinterpret_cast<float* const*>(factors_inout), residual_out, st);
+  ts_options eo = *opt;
+  if (opt->use_graph) eo.phase_events = nullptr;  // events inside a graph carry no timing
+  auto enqueue = [&](cudaStream_t s) -> ts_status {
+    if (X->dtype == TS_F64)
+      return als_impl<double>(*X, S, eo, workspace, static_cast<double*>(core_out),
+                              reinterpret_cast<double* const*>(factors_inout), residual_out, s);
+    return als_impl<float>(*X, S, eo, workspace, static_cast<float*>(core_out),
+                           reinterpret_cast<float* const*>(factors_inout), residual_out, s);
+  };
+  if (!opt->use_graph) return enqueue(st);
+  // Key: every argument the enqueued work depends on (values and addresses).
+  std::string key;
+  auto put = [&](const void* p, size_t n) { key.append(static_cast<const char*>(p), n); };
+  put(&X->order, sizeof(X->order));  // field by field: the struct has padding
+  put(X->dims, sizeof(int64_t) * X->order);
+  put(&X->format, sizeof(X->format));
+  put(&X->dtype, sizeof(X->dtype));
+  put(&X->values, sizeof(X->values));
+  put(&X->indices, sizeof(X->indices));
+  put(&X->nnz, sizeof(X->nnz));
+  put(ranks, sizeof(int32_t) * X->order);
+  put(&kind, sizeof(kind));
+  put(&m, sizeof(m));
+  put(&sweeps, sizeof(sweeps));
+  put(&eo, sizeof(eo));
+  put(&workspace, sizeof(workspace));
+  put(&core_out, sizeof(core_out));
+  put(factors_inout, sizeof(void*) * X->order);
+  put(&residual_out, sizeof(residual_out));
+  return graph_replay(key, enqueue, st);
 }
 
 extern "C" ts_status tensorsketch_input(const ts_tensor* X, int32_t mode,
@@ -518,8 +659,8 @@ extern "C" ts_status tensorsketch_input(const ts_tensor* X, int32_t mode,
     job.tables[k] = k == mode ? nullptr : tables[k];
   }
   cudaStream_t st = (cudaStream_t)stream;
-  return X->dtype == TS_F64 ? launch_input_sketch<double>(*X, &job, 1, st)
-                            : launch_input_sketch<float>(*X, &job, 1, st);
+  return X->dtype == TS_F64 ? launch_input_sketch<double>(*X, &job, 1, nullptr, st)
+                            : launch_input_sketch<float>(*X, &job, 1, nullptr, st);
 }
 
 // ---------------------------------------------------------------- Init-RRF, one mode
@@ -536,21 +677,32 @@ static ts_status rrf_check(const ts_tensor* X, int32_t mode, int32_t R, int32_t 
 }
 
 template <typename T>
-static size_t rrf_carve(const ts_tensor& X, int mode, int R, int k1, int k2, Bump& b, int** flag,
-                        int32_t** tabs, T** Wt, T** Gm, T** Bm, T** K, T** Fm, T** V, T** P,
-                        size_t* PE) {
-  *flag = b.take<int>(64);
-  for (int k = 0; k < X.order; ++k) tabs[k] = k == mode ? nullptr : b.take<int32_t>(X.dims[k]);
+struct RrfWork {
+  int* flag;
+  unsigned* counters;
+  int32_t* tabs[TS_MAX_ORDER];
+  T *Wt, *Gm, *Bm, *K, *Fm;
+  GemmSplit<T> split;
+};
+
+template <typename T>
+static size_t rrf_carve(const ts_tensor& X, int mode, int R, int k1, int k2, Bump& b,
+                        RrfWork<T>& w) {
+  memset(&w, 0, sizeof(w));
+  w.flag = b.take<int>(64);
+  w.counters = b.take<unsigned>(kGemmCounters);
+  for (int k = 0; k < X.order; ++k) w.tabs[k] = k == mode ? nullptr : b.take<int32_t>(X.dims[k]);
   const int64_t s = X.dims[mode];
-  *Wt = b.take<T>((size_t)k2 * s);
-  *Gm = b.take<T>((size_t)k2 * k1);
-  *Bm = b.take<T>((size_t)s * k1);
-  *K = b.take<T>((size_t)k1 * k1);
-  *Fm = b.take<T>((size_t)k1 * R);
-  *V = b.take<T>((size_t)s * R);
-  size_t pm = (size_t)s * k1 > (size_t)k1 * k1 ? (size_t)s * k1 : (size_t)k1 * k1;
-  *PE = 32 * pm;
-  *P = b.take<T>(*PE);
+  w.Wt = b.take<T>((size_t)k2 * s);
+  w.Gm = b.take<T>((size_t)k2 * k1);
+  w.Bm = b.take<T>((size_t)s * k1);
+  w.K = b.take<T>((size_t)k1 * k1);
+  w.Fm = b.take<T>((size_t)k1 * R);
+  const size_t pm = (size_t)s * k1 > (size_t)k1 * k1 ? (size_t)s * k1 : (size_t)k1 * k1;
+  w.split.partial_elems = 32 * pm;
+  w.split.partial = b.take<T>(w.split.partial_elems);
+  w.split.counters = w.counters;
+  w.split.ncounters = kGemmCounters;
   return b.off;
 }
 
@@ -558,48 +710,41 @@ extern "C" size_t range_finder_init_scratch_bytes(const ts_tensor* X, int32_t mo
                                                   int32_t k1, int32_t k2) {
   if (rrf_check(X, mode, R, k1, k2) != TS_OK) return 0;
   Bump b;
-  int* f;
-  int32_t* t[TS_MAX_ORDER];
-  size_t pe;
   if (X->dtype == TS_F64) {
-    double *a, *c, *d, *e, *g, *h, *p;
-    return rrf_carve<double>(*X, mode, R, k1, k2, b, &f, t, &a, &c, &d, &e, &g, &h, &p, &pe);
+    RrfWork<double> w;
+    return rrf_carve<double>(*X, mode, R, k1, k2, b, w);
   }
-  float *a, *c, *d, *e, *g, *h, *p;
-  return rrf_carve<float>(*X, mode, R, k1, k2, b, &f, t, &a, &c, &d, &e, &g, &h, &p, &pe);
+  RrfWork<float> w;
+  return rrf_carve<float>(*X, mode, R, k1, k2, b, w);
 }
 
 template <typename T>
 static ts_status rrf_one(const ts_tensor& X, int mode, int R, int k1, int k2, uint64_t seed,
                          T* A_out, void* scratch, cudaStream_t st) {
   Bump b{static_cast<char*>(scratch)};
-  int* flag;
-  int32_t* tabs[TS_MAX_ORDER];
-  T *Wt, *Gm, *Bm, *K, *Fm, *V, *P;
-  size_t PE;
-  rrf_carve<T>(X, mode, R, k1, k2, b, &flag, tabs, &Wt, &Gm, &Bm, &K, &Fm, &V, &P, &PE);
-  TS_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  RrfWork<T> w;
+  rrf_carve<T>(X, mode, R, k1, k2, b, w);
+  TS_CUDA(cudaMemsetAsync(w.flag, 0, 256 + kGemmCounters * sizeof(unsigned), st));
   SketchJob job{};
   job.mode = mode;
   job.nbins = k2;
-  job.out = Wt;
+  job.out = w.Wt;
   for (int k = 0; k < X.order; ++k) {
     if (k != mode)
-      TS_TRY(launch_hash_table(seed, TS_PURPOSE_RRF_HASH, 0, mode, k, X.dims[k], k2, tabs[k], st));
-    job.tables[k] = tabs[k];
+      TS_TRY(launch_hash_table(seed, TS_PURPOSE_RRF_HASH, 0, mode, k, X.dims[k], k2, w.tabs[k], st));
+    job.tables[k] = w.tabs[k];
   }
-  TS_TRY(launch_input_sketch<T>(X, &job, 1, st));
+  TS_TRY(launch_input_sketch<T>(X, &job, 1, w.flag, st));
   const int s = (int)X.dims[mode];
   TS_TRY(launch_gaussian<T>(seed, make_tag(TS_PURPOSE_RRF_GAUSS, 0, mode, 0), (int64_t)k2 * k1,
-                            1.0 / sqrt((double)k1), Gm, st));
-  TS_TRY(gemm<T>(s, k1, k2, 1.0, mv<T>(Wt, 1, s), mv<T>(Gm, k1, 1), 0.0, ov<T>(Bm, k1, 1), P, PE,
-                 st));
-  TS_TRY(gemm<T>(k1, k1, s, 1.0, mv<T>(Bm, 1, k1), mv<T>(Bm, k1, 1), 0.0, ov<T>(K, k1, 1), P, PE,
-                 st));
-  TS_TRY(launch_eig_small<T>(k1, R, K, nullptr, k1, nullptr, Fm, nullptr, flag, st));
-  TS_TRY(gemm<T>(s, R, k1, 1.0, mv<T>(Bm, k1, 1), mv<T>(Fm, R, 1), 0.0, ov<T>(V, R, 1), P, PE, st));
+                            1.0 / sqrt((double)k1), w.Gm, st));
+  TS_TRY(gemm<T>(s, k1, k2, 1.0, mv<T>(w.Wt, 1, s), mv<T>(w.Gm, k1, 1), 0.0, ov<T>(w.Bm, k1, 1),
+                 &w.split, st));
+  TS_TRY(gemm<T>(k1, k1, s, 1.0, mv<T>(w.Bm, 1, k1), mv<T>(w.Bm, k1, 1), 0.0, ov<T>(w.K, k1, 1),
+                 &w.split, st));
+  TS_TRY(launch_eig_small<T>(k1, R, w.K, nullptr, k1, nullptr, w.Fm, nullptr, false, w.flag, st));
   CoreMap none{};
-  return launch_finalize<T>(s, R, V, A_out, nullptr, 0, nullptr, none, st);
+  return launch_finalize<T>(s, R, w.Bm, k1, 1, k1, w.Fm, A_out, nullptr, 0, nullptr, none, st);
 }
 
 extern "C" ts_status range_finder_init(const ts_tensor* X, int32_t mode, int32_t R, int32_t k1,
@@ -620,32 +765,35 @@ extern "C" ts_status range_finder_init(const ts_tensor* X, int32_t mode, int32_t
 // ---------------------------------------------------------------- one subproblem
 
 static ts_status lrls_check(int32_t m, int32_t r, int32_t s, int32_t R, int32_t dtype,
-                            int32_t solve, int32_t oversample, int* kc) {
+                            int32_t solve, int32_t oversample, int32_t fp64, int* kc) {
   if (dtype != TS_F32 && dtype != TS_F64) return fail(TS_ERR_INVALID_ARG, "ts_lrls: bad dtype");
   if (solve != TS_SOLVE_RSVD && solve != TS_SOLVE_EXACT)
     return fail(TS_ERR_INVALID_ARG, "ts_lrls: bad solve kind");
   if (m < 1 || r < 1 || s < 1 || R < 1 || R > r || R > s || r > m)
     return fail(TS_ERR_SHAPE, "ts_lrls: need 1 <= R <= min(r, s) and r <= m");
   *kc = rsvd_width(R, oversample < 0 ? 5 : oversample, r, s);
+  const bool q64 = fp64 && dtype == TS_F32;
+  if (fused_ok(r, s, *kc, R, solve, dtype_size(dtype), q64)) return TS_OK;
   if (solve == TS_SOLVE_RSVD &&
-      (r > kMaxCholSmem || *kc > kMaxEig ||
-       rsvd_stage1_smem_bytes(r, *kc, dtype_size(dtype)) > kMaxSmem))
-    return fail(TS_ERR_SHAPE, "ts_lrls: RSVD limits r <= %d, k <= %d and on-chip footprint",
-                kMaxCholSmem, kMaxEig);
-  if (solve == TS_SOLVE_EXACT && r > kMaxEig)
+      (*kc > kMaxEig || rsvd_stage1_smem_bytes(r, *kc, dtype_size(dtype), q64) > kMaxSmem))
+    return fail(TS_ERR_SHAPE, "ts_lrls: RSVD limits k <= %d and the on-chip footprint", kMaxEig);
+  if (solve == TS_SOLVE_EXACT && (r > kMaxEig || chol_solve_smem_bytes(r, dtype_size(dtype)) > kMaxSmem))
     return fail(TS_ERR_SHAPE, "ts_lrls: exact limit r <= %d", kMaxEig);
   return TS_OK;
 }
 
 template <typename T>
-static size_t lrls_carve(int m, int r, int s, int R, int solve, int kc, Bump& b, Work<T>& w) {
+static size_t lrls_carve(int m, int r, int s, int R, int solve, int kc, bool fp64, Bump& b,
+                         Work<T>& w) {
   memset(&w, 0, sizeof(w));
   w.flag = b.take<int>(64);
+  w.counters = b.take<unsigned>(kGemmCounters);
   const int k = kc;
   const int eign = solve == TS_SOLVE_EXACT ? (r > k ? r : k) : k;
-  w.G = b.take<T>((size_t)r * r);
-  w.W = b.take<T>((size_t)r * k);
-  w.YO = b.take<T>((size_t)m * k);
+  const bool fused = fused_ok(r, s, kc, R, solve, sizeof(T), fp64);
+  w.ZW = b.take<T>((size_t)m * (r + k));
+  w.GW = b.take<T>((size_t)r * (r + (fused && s > k ? s : k)));
+  w.Mbuf = fused ? b.take<T>((size_t)(solve == TS_SOLVE_RSVD ? k : r) * s) : nullptr;
   w.Om = b.take<T>((size_t)s * k);
   w.Q = b.take<T>((size_t)r * k);
   w.E = b.take<T>((size_t)r * k);
@@ -653,57 +801,67 @@ static size_t lrls_carve(int m, int r, int s, int R, int solve, int kc, Bump& b,
   w.D = b.take<T>((size_t)k * s);
   w.K = b.take<T>((size_t)eign * eign);
   w.Fm = b.take<T>((size_t)eign * R);
-  w.V = b.take<T>((size_t)s * R);
   if (solve == TS_SOLVE_EXACT) {
     w.H = b.take<T>((size_t)r * s);
     w.Xs = b.take<T>((size_t)r * s);
   }
-  size_t pm = (size_t)r * r;
-  const size_t cands[] = {(size_t)r * k, (size_t)m * k, (size_t)k * s, (size_t)s * R,
-                          (size_t)eign * eign, solve == TS_SOLVE_EXACT ? (size_t)r * s : 0};
+  size_t pm = (size_t)r * (r + k);
+  const size_t cands[] = {(size_t)m * k, (size_t)k * s, (size_t)eign * eign,
+                          solve == TS_SOLVE_EXACT ? (size_t)r * s : 0};
   for (size_t c : cands)
     if (c > pm) pm = c;
-  w.partial_elems = 32 * pm;
-  w.partial = b.take<T>(w.partial_elems);
+  w.split.partial_elems = 32 * pm;
+  w.split.partial = b.take<T>(w.split.partial_elems);
+  w.split.counters = w.counters;
+  w.split.ncounters = kGemmCounters;
   return b.off;
 }
 
 extern "C" size_t ts_lrls_scratch_bytes(int32_t m, int32_t r, int32_t s, int32_t R, int32_t solve,
                                         int32_t oversample, int32_t dtype) {
   int kc;
-  if (lrls_check(m, r, s, R, dtype, solve, oversample, &kc) != TS_OK) return 0;
-  Bump b;
-  if (dtype == TS_F64) {
-    Work<double> w;
-    return lrls_carve<double>(m, r, s, R, solve, kc, b, w);
+  if (lrls_check(m, r, s, R, dtype, solve, oversample, 1, &kc) != TS_OK) return 0;
+  size_t best = 0;
+  for (int f64 = 0; f64 < 2; ++f64) {  // enough for either precision of the solve
+    Bump b;
+    if (dtype == TS_F64) {
+      Work<double> w;
+      lrls_carve<double>(m, r, s, R, solve, kc, false, b, w);
+    } else {
+      Work<float> w;
+      lrls_carve<float>(m, r, s, R, solve, kc, f64 != 0, b, w);
+    }
+    if (b.off > best) best = b.off;
   }
-  Work<float> w;
-  return lrls_carve<float>(m, r, s, R, solve, kc, b, w);
+  return best;
 }
 
 template <typename T>
-static ts_status lrls_one(int m, int r, int s, int R, int solve, int kc, const void* Z,
+static ts_status lrls_one(int m, int r, int s, int R, int solve, int kc, bool fp64, const void* Z,
                           const void* Y, uint64_t seed, int sweep, int n, void* CnT_out,
                           void* A_out, void* scratch, cudaStream_t st) {
   Bump b{static_cast<char*>(scratch)};
   Work<T> w;
-  lrls_carve<T>(m, r, s, R, solve, kc, b, w);
+  lrls_carve<T>(m, r, s, R, solve, kc, fp64, b, w);
   w.CnT = static_cast<T*>(CnT_out);
-  TS_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
+  TS_CUDA(cudaMemsetAsync(w.flag, 0, 256 + kGemmCounters * sizeof(unsigned), st));
+  TS_CUDA(cudaMemcpyAsync(w.ZW, Z, sizeof(T) * (size_t)m * r, cudaMemcpyDeviceToDevice, st));
+  if (solve == TS_SOLVE_RSVD)
+    TS_TRY(launch_gaussian<T>(seed, make_tag(TS_PURPOSE_RSVD_GAUSS, sweep, n, 0), (int64_t)s * kc,
+                              1.0, w.Om, st));
   CoreMap none{};
-  return solve_subproblem<T>(m, r, s, R, solve, kc, seed, sweep, n, static_cast<const T*>(Z),
-                             static_cast<const T*>(Y), w, static_cast<T*>(A_out), nullptr, none,
-                             st);
+  return solve_subproblem<T>(m, r, s, R, solve, kc, fp64, w.Om, static_cast<const T*>(Y), w,
+                             static_cast<T*>(A_out), nullptr, none, st);
 }
 
 extern "C" ts_status ts_lrls_solve(int32_t m, int32_t r, int32_t s, int32_t R, int32_t dtype,
                                    const void* Z_colmajor, const void* Y, int32_t solve,
                                    uint64_t seed, int32_t sweep, int32_t n, int32_t oversample,
-                                   void* CnT_out, void* A_out, void* scratch, size_t scratch_bytes,
-                                   ts_stream stream) {
+                                   int32_t solve_fp64, void* CnT_out, void* A_out, void* scratch,
+                                   size_t scratch_bytes, ts_stream stream) {
   clear_error();
   int kc;
-  TS_TRY(lrls_check(m, r, s, R, dtype, solve, oversample, &kc));
+  TS_TRY(lrls_check(m, r, s, R, dtype, solve, oversample, solve_fp64, &kc));
   if (!Z_colmajor || !Y || !CnT_out || !A_out)
     return fail(TS_ERR_INVALID_ARG, "ts_lrls_solve: NULL argument");
   if (sweep < 0 || sweep >= (1 << 24) || n < 0 || n > 255)
@@ -712,10 +870,11 @@ extern "C" ts_status ts_lrls_solve(int32_t m, int32_t r, int32_t s, int32_t R, i
   if (!scratch || scratch_bytes < need || ((uintptr_t)scratch & 255))
     return fail(TS_ERR_WORKSPACE, "ts_lrls_solve: need %zu bytes of 256-aligned scratch", need);
   cudaStream_t st = (cudaStream_t)stream;
-  return dtype == TS_F64 ? lrls_one<double>(m, r, s, R, solve, kc, Z_colmajor, Y, seed, sweep, n,
-                                            CnT_out, A_out, scratch, st)
-                         : lrls_one<float>(m, r, s, R, solve, kc, Z_colmajor, Y, seed, sweep, n,
-                                           CnT_out, A_out, scratch, st);
+  const bool fp64 = solve_fp64 != 0 && dtype == TS_F32;
+  return dtype == TS_F64 ? lrls_one<double>(m, r, s, R, solve, kc, false, Z_colmajor, Y, seed,
+                                            sweep, n, CnT_out, A_out, scratch, st)
+                         : lrls_one<float>(m, r, s, R, solve, kc, fp64, Z_colmajor, Y, seed,
+                                           sweep, n, CnT_out, A_out, scratch, st);
 }
 
 // ---------------------------------------------------------------- leverage sketch
@@ -820,7 +979,8 @@ static ts_status cp_check(const ts_tensor* X, int R_cp, const int32_t* tranks, i
     core *= tranks[k];
     if (tranks[k] < rmin) rmin = tranks[k];
   }
-  if (R_cp < 1 || R_cp > rmin || R_cp > kMaxEig || core > 65536)
+  if (R_cp < 1 || R_cp > rmin || R_cp > kMaxEig || core > 65536 ||
+      chol_solve_smem_bytes(R_cp, dtype_size(X->dtype)) > kMaxSmem)
     return fail(TS_ERR_SHAPE, "cp_via_tucker: need 1 <= R_cp <= min(tucker_ranks), R_cp <= %d and "
                               "prod(tucker_ranks) <= 65536", kMaxEig);
   return TS_OK;
@@ -875,7 +1035,7 @@ static ts_status cp_impl(const ts_tensor& X, const Shape& S, const ts_options& o
   TS_TRY(cp_als_core<T>(S.N, S.ranks, Rc, cp_sweeps, c.core, c.A, c.cps, flag, st));
   for (int k = 0; k < S.N; ++k)
     TS_TRY(gemm<T>((int)X.dims[k], Rc, S.ranks[k], 1.0, mv<T>(c.B[k], S.ranks[k], 1),
-                   mv<T>(c.A[k], Rc, 1), 0.0, ov<T>(out[k], Rc, 1), nullptr, 0, st));
+                   mv<T>(c.A[k], Rc, 1), 0.0, ov<T>(out[k], Rc, 1), nullptr, st));
   if (residual_out) {
     int rk[TS_MAX_ORDER];
     for (int k = 0; k < S.N; ++k) rk[k] = Rc;

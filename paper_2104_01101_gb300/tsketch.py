@@ -52,6 +52,7 @@ class _Options(C.Structure):
                 ("rsvd_oversample", C.c_int32), ("solve", C.c_int32),
                 ("resketch_each_sweep", C.c_int32), ("gram_bf16", C.c_int32),
                 ("init_given", C.c_int32), ("track_fit", C.c_int32),
+                ("solve_fp64", C.c_int32), ("use_graph", C.c_int32),
                 ("phase_events", C.POINTER(C.c_void_p))]
 
 
@@ -76,7 +77,8 @@ _PROTOS = {
     "range_finder_init_scratch_bytes": (SZ, [TP, I32, I32, I32, I32]),
     "range_finder_init": (I32, [TP, I32, I32, I32, I32, U64, P, P, SZ, P]),
     "ts_lrls_scratch_bytes": (SZ, [I32, I32, I32, I32, I32, I32, I32]),
-    "ts_lrls_solve": (I32, [I32, I32, I32, I32, I32, P, P, I32, U64, I32, I32, I32, P, P, P, SZ, P]),
+    "ts_lrls_solve": (I32, [I32, I32, I32, I32, I32, P, P, I32, U64, I32, I32, I32, I32, P, P, P,
+                            SZ, P]),
     "ts_leverage_sketch_scratch_bytes": (SZ, [TP, I32, I32]),
     "ts_leverage_sketch": (I32, [TP, I32, C.POINTER(I32), PP, I32, U64, I32, P, P, P, P, SZ, P]),
     "ts_fitness_scratch_bytes": (SZ, [TP, C.POINTER(I32)]),
@@ -260,7 +262,7 @@ def range_finder_init(X, mode: int, R: int, k1: int, k2: int, seed: int):
 
 
 def lrls_solve(Z, Y, R: int, solve: int = SOLVE_RSVD, seed: int = 0, sweep: int = 0, n: int = 0,
-               oversample: int = 5):
+               oversample: int = 5, solve_fp64: bool = False):
     """Sketched rank-constrained LS; Z is (m, r) (any strides), Y is (m, s)."""
     m, r = Z.shape
     s = Y.shape[1]
@@ -272,7 +274,8 @@ def lrls_solve(Z, Y, R: int, solve: int = SOLVE_RSVD, seed: int = 0, sweep: int 
     nbytes = lib().ts_lrls_scratch_bytes(m, r, s, R, solve, oversample, dt)
     scr = _scratch(nbytes, Y.device)
     _check(lib().ts_lrls_solve(m, r, s, R, dt, _ptr(Zc), _ptr(Yc), solve, seed, sweep, n, oversample,
-                               _ptr(CnT), _ptr(A), _ptr(scr), scr.numel(), _stream()))
+                               int(solve_fp64), _ptr(CnT), _ptr(A), _ptr(scr), scr.numel(),
+                               _stream()))
     return CnT, A
 
 
@@ -311,7 +314,8 @@ def fitness_residual(X, core, factors) -> float:
     return float(out.item())
 
 
-def _options(seed, solve, oversample, rrf_k1, rrf_k2, resketch, init_given, track_fit):
+def _options(seed, solve, oversample, rrf_k1, rrf_k2, resketch, init_given, track_fit,
+             solve_fp64=False, use_graph=False):
     o = _Options()
     o.seed = seed
     o.rrf_k1 = rrf_k1 or 0
@@ -322,6 +326,8 @@ def _options(seed, solve, oversample, rrf_k1, rrf_k2, resketch, init_given, trac
     o.gram_bf16 = 0
     o.init_given = int(bool(init_given))
     o.track_fit = int(bool(track_fit))
+    o.solve_fp64 = int(bool(solve_fp64))
+    o.use_graph = int(bool(use_graph))
     return o
 
 
@@ -330,12 +336,13 @@ class TuckerPlan:
 
     def __init__(self, X, ranks, m, sweeps, kind=TENSORSKETCH, seed=0, solve=SOLVE_RSVD,
                  oversample=5, rrf_k1=None, rrf_k2=None, resketch=False, track_fit=False,
-                 want_residual=True):
+                 want_residual=True, solve_fp64=False, use_graph=False):
         self.dims = _dims(X)
         self.N = len(self.dims)
         self.ranks = list(ranks)
         self.kind, self.m, self.sweeps = kind, m, sweeps
-        self.opt = _options(seed, solve, oversample, rrf_k1, rrf_k2, resketch, False, track_fit)
+        self.opt = _options(seed, solve, oversample, rrf_k1, rrf_k2, resketch, False, track_fit,
+                            solve_fp64, use_graph)
         self.track_fit = track_fit
         self.want_residual = want_residual
         dtype, dev = X.dtype, X.device
@@ -382,11 +389,11 @@ class TuckerPlan:
 
 def cp_via_tucker(X, R_cp: int, tucker_ranks, m: int, tucker_sweeps: int, cp_sweeps: int,
                   seed: int = 0, solve=SOLVE_RSVD, oversample: int = 5, rrf_k1=None, rrf_k2=None,
-                  want_residual=True):
+                  want_residual=True, solve_fp64=False):
     """Alg. 6: returns (CP factors [dims[k] x R_cp], residual float or None)."""
     dims = _dims(X)
     N = len(dims)
-    opt = _options(seed, solve, oversample, rrf_k1, rrf_k2, False, False, False)
+    opt = _options(seed, solve, oversample, rrf_k1, rrf_k2, False, False, False, solve_fp64)
     d = _desc(X)
     rk = (C.c_int32 * N)(*tucker_ranks)
     nbytes = C.c_size_t(0)
@@ -406,10 +413,10 @@ def cp_via_tucker(X, R_cp: int, tucker_ranks, m: int, tucker_sweeps: int, cp_swe
 def tucker_als_sketched(X, ranks, m: int, sweeps: int, kind=TENSORSKETCH, seed: int = 0,
                         solve=SOLVE_RSVD, oversample: int = 5, rrf_k1=None, rrf_k2=None,
                         resketch=False, init_factors=None, track_fit=False,
-                        want_residual=True):
+                        want_residual=True, solve_fp64=False):
     """Alg. 4.  Returns (core, factors, residuals tensor or None); raises TsError on breakdown."""
     plan = TuckerPlan(X, ranks, m, sweeps, kind, seed, solve, oversample, rrf_k1, rrf_k2, resketch,
-                      track_fit, want_residual)
+                      track_fit, want_residual, solve_fp64)
     plan.run(X, init_factors)
     if plan.numeric_flag() != 0:
         raise TsError(6, "numerical breakdown flagged by the device (Z^T Z not positive definite "

@@ -172,6 +172,21 @@ def test_rsvd_lrls_matches_oracle(ts, m, r, s, R, dtype):
     assert np.abs(Ag.cpu().numpy() - Aw).max() <= (1e-9 if dtype == torch.float64 else 1e-4)
 
 
+@pytest.mark.parametrize("m,r,s,R", [(2048, 256, 3000, 8), (3000, 625, 300, 25)])
+def test_rsvd_lrls_large_r_matches_oracle(ts, m, r, s, R):
+    # r too large for the on-chip Cholesky: G^{-1} by Newton-Schulz products
+    Z, Y = _solve_problem(6, m, r, s, R, 0.05)
+    Z = Z.astype(np.float32).astype(np.float64)
+    Y = Y.astype(np.float32).astype(np.float64)
+    k = solve.rsvd_oversampled_rank(R, 5, r, s)
+    Om = rng.gaussian(5, rng.make_tag(4, 0, 2, 0), s * k).reshape(s, k)
+    Cw, Aw = solve.rsvd_lrls(Z, Y, R, Om)
+    Cg, Ag = ts.lrls_solve(dev(Z, torch.float32), dev(Y, torch.float32), R, ts.SOLVE_RSVD, seed=5,
+                           sweep=0, n=2)
+    Bw, Bg = Cw @ Aw.T, Cg.cpu().numpy() @ Ag.cpu().numpy().T
+    assert np.linalg.norm(Bg - Bw) <= 1e-5 * np.linalg.norm(Bw)
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_exact_lrls_matches_oracle(ts, dtype):
     Z, Y = _solve_problem(4, 400, 25, 40, 5, 0.1)

@@ -4,9 +4,9 @@
 // the launcher first shrinks the output tile (64x64 -> 32x32) to reach one wave of
 // CTAs and only then splits the long dimension; split partials are summed in split
 // order by a second, fully parallel kernel, so results are deterministic.
-// The B operand may be two strided views side by side (columns [0, n1) from B1 and
-// [n1, N) from B2), so that Z^T [Z | Y] is one product even though Z is stored
-// column-major and Y row-major.
+// The B operand may be up to three strided views side by side (columns [0, n1) from
+// B1, [n1, n2) from B2 and [n2, N) from B3), so that Z^T [Z | Y Omega | Y] is one
+// product even though Z is stored column-major and the others row-major.
 #include "internal.cuh"
 
 namespace ts {
@@ -17,8 +17,9 @@ constexpr int BK = 16, NT = 256;
 
 template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, MatView<T> A,
-                                             MatView<T> B1, int n1, MatView<T> B2, T alpha,
-                                             T beta, OutView<T> C, T* __restrict__ partial) {
+                                             MatView<T> B1, int n1, MatView<T> B2, int n2,
+                                             MatView<T> B3, T alpha, T beta, OutView<T> C,
+                                             T* __restrict__ partial) {
   constexpr int TM = BM / 16, TN = BN / 16;  // outputs per thread: TM x TN
   __shared__ T As[BK][BM + 4];
   __shared__ T Bs[BK][BN + 4];
@@ -27,7 +28,7 @@ __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, Ma
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(K, kbeg + kchunk);
   const bool a_kfast = (A.cs == 1);
-  const MatView<T>& Bv = n0 < n1 ? B1 : B2;  // layout of the view this tile starts in
+  const MatView<T>& Bv = n0 < n1 ? B1 : (n0 < n2 ? B2 : B3);  // view this tile starts in
   const bool b_kfast = (Bv.rs == 1 && Bv.cs != 1);
   T acc[TM][TN];
 #pragma unroll
@@ -48,7 +49,8 @@ __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, Ma
       T v = 0;
       if (gj < N && gk < kend) {
         if (gj < n1) v = B1.p[(long)gk * B1.rs + (long)gj * B1.cs];
-        else v = B2.p[(long)gk * B2.rs + (long)(gj - n1) * B2.cs];
+        else if (gj < n2) v = B2.p[(long)gk * B2.rs + (long)(gj - n1) * B2.cs];
+        else v = B3.p[(long)gk * B3.rs + (long)(gj - n2) * B3.cs];
       }
       Bs[kk][j] = v;
     }
@@ -101,9 +103,9 @@ __global__ void k_gemm_reduce(int M, int N, int splits, const T* __restrict__ pa
 }
 
 template <typename T>
-ts_status gemm2(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, int n1,
-                MatView<T> B2, double beta, OutView<T> C, const GemmSplit<T>* split,
-                cudaStream_t st) {
+ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, int n1,
+                MatView<T> B2, int n2, MatView<T> B3, double beta, OutView<T> C,
+                const GemmSplit<T>* split, cudaStream_t st) {
   if (M <= 0 || N <= 0) return TS_OK;
   constexpr int kWave = 2 * 152;
   const int tiles64 = ceil_div(M, 64) * ceil_div(N, 64);
@@ -125,11 +127,11 @@ ts_status gemm2(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
   dim3 grid(ceil_div(N, bm), ceil_div(M, bm), splits);
   T* part = splits > 1 ? split->partial : nullptr;
   if (small)
-    k_gemm<T, 32, 32><<<grid, NT, 0, st>>>(M, N, K, kchunk, A, B1, n1, B2, (T)alpha, (T)beta, C,
-                                           part);
+    k_gemm<T, 32, 32><<<grid, NT, 0, st>>>(M, N, K, kchunk, A, B1, n1, B2, n2, B3, (T)alpha,
+                                           (T)beta, C, part);
   else
-    k_gemm<T, 64, 64><<<grid, NT, 0, st>>>(M, N, K, kchunk, A, B1, n1, B2, (T)alpha, (T)beta, C,
-                                           part);
+    k_gemm<T, 64, 64><<<grid, NT, 0, st>>>(M, N, K, kchunk, A, B1, n1, B2, n2, B3, (T)alpha,
+                                           (T)beta, C, part);
   TS_LAUNCH_CHECK();
   if (splits > 1) {
     const size_t MN = (size_t)M * N;
@@ -142,16 +144,26 @@ ts_status gemm2(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
 }
 
 template <typename T>
+ts_status gemm2(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, int n1,
+                MatView<T> B2, double beta, OutView<T> C, const GemmSplit<T>* split,
+                cudaStream_t st) {
+  return gemm3<T>(M, N, K, alpha, A, B1, n1, B2, N, B2, beta, C, split, st);
+}
+
+template <typename T>
 ts_status gemm(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B, double beta,
                OutView<T> C, const GemmSplit<T>* split, cudaStream_t st) {
-  return gemm2<T>(M, N, K, alpha, A, B, N, B, beta, C, split, st);
+  return gemm3<T>(M, N, K, alpha, A, B, N, B, N, B, beta, C, split, st);
 }
 
 #define TS_INST(T)                                                                              \
   template ts_status gemm<T>(int, int, int, double, MatView<T>, MatView<T>, double, OutView<T>, \
                              const GemmSplit<T>*, cudaStream_t);                                \
   template ts_status gemm2<T>(int, int, int, double, MatView<T>, MatView<T>, int, MatView<T>,   \
-                              double, OutView<T>, const GemmSplit<T>*, cudaStream_t);
+                              double, OutView<T>, const GemmSplit<T>*, cudaStream_t);           \
+  template ts_status gemm3<T>(int, int, int, double, MatView<T>, MatView<T>, int, MatView<T>,   \
+                              int, MatView<T>, double, OutView<T>, const GemmSplit<T>*,         \
+                              cudaStream_t);
 TS_INST(float)
 TS_INST(double)
 #undef TS_INST

@@ -84,6 +84,40 @@ ts_status launch_gaussian(uint64_t seed, uint64_t tag, int64_t count, double sca
   return TS_OK;
 }
 
+// Test matrices of Alg. 5 for a run of sweeps, every mode in one launch.  Mode n's block
+// starts at ob.off[n] (blocks contiguous, in mode order) and is s_n x (nsweeps k_n)
+// row-major: element (j, t k_n + c) is draw j k_n + c of the object
+// (seed, RSVD_GAUSS, sweep0 + t, n, 0), i.e. entry (j, c) of Omega(sweep0 + t, n).
+template <typename T>
+__global__ void k_omegas(uint64_t seed, OmegaBlocks ob, T* __restrict__ out) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < ob.total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int n = 0;
+    while (n + 1 < ob.N && e >= ob.off[n + 1]) ++n;
+    const int k = ob.k[n];
+    const int64_t width = (int64_t)ob.nsweeps * k;
+    const int64_t loc = e - ob.off[n];
+    const int64_t j = loc / width;
+    const int rem = (int)(loc - j * width);
+    const int t = rem / k, c = rem - t * k;
+    const uint64_t key = object_key(seed, make_tag(TS_PURPOSE_RSVD_GAUSS, ob.sweep0 + t, n, 0));
+    out[e] = (T)gauss01(key, (uint64_t)(j * k + c));
+  }
+}
+
+template <typename T>
+ts_status launch_omegas(uint64_t seed, const OmegaBlocks& ob, T* out, cudaStream_t st) {
+  if (ob.total <= 0) return TS_OK;
+  int blocks = (int)((ob.total + 127) / 128);
+  if (blocks > 8192) blocks = 8192;
+  k_omegas<T><<<blocks, 128, 0, st>>>(seed, ob, out);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+template ts_status launch_omegas<float>(uint64_t, const OmegaBlocks&, float*, cudaStream_t);
+template ts_status launch_omegas<double>(uint64_t, const OmegaBlocks&, double*, cudaStream_t);
+
 template ts_status launch_gaussian<float>(uint64_t, uint64_t, int64_t, double, float*,
                                           cudaStream_t);
 template ts_status launch_gaussian<double>(uint64_t, uint64_t, int64_t, double, double*,

@@ -12,6 +12,19 @@ ts_status launch_hash_table(uint64_t seed, int purpose, int sweep, int n, int k,
 template <typename T>
 ts_status launch_gaussian(uint64_t seed, uint64_t tag, int64_t count, double scale, T* out,
                           cudaStream_t st);
+// Gaussian test matrices of Alg. 5 for sweeps sweep0 .. sweep0 + nsweeps - 1 of every mode
+// in one launch.  Mode n's block (rows[n] x nsweeps k[n], row-major) starts at off[n];
+// blocks are contiguous in mode order and total = off[N-1] + rows[N-1] nsweeps k[N-1].
+// Columns [t k[n], (t+1) k[n]) hold Omega(sweep0 + t, n).
+struct OmegaBlocks {
+  int N, nsweeps, sweep0;
+  int64_t rows[TS_MAX_ORDER];
+  int k[TS_MAX_ORDER];
+  int64_t off[TS_MAX_ORDER];
+  int64_t total;
+};
+template <typename T>
+ts_status launch_omegas(uint64_t seed, const OmegaBlocks& ob, T* out, cudaStream_t st);
 
 // ---------------------------------------------------------------- fft_ts.cu
 constexpr int kMaxRadices = 32;
@@ -85,6 +98,12 @@ template <typename T>
 ts_status gemm2(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, int n1,
                 MatView<T> B2, double beta, OutView<T> C, const GemmSplit<T>* split,
                 cudaStream_t st);
+// Same, with B's columns [0, n1) from B1, [n1, n2) from B2 (column j - n1) and [n2, N)
+// from B3 (column j - n2).
+template <typename T>
+ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, int n1,
+                MatView<T> B2, int n2, MatView<T> B3, double beta, OutView<T> C,
+                const GemmSplit<T>* split, cudaStream_t st);
 constexpr int kGemmCounters = 4096;
 
 // ---------------------------------------------------------------- solve.cu
@@ -124,14 +143,16 @@ size_t chol_solve_smem_bytes(int r, size_t tsize);
 template <typename T>
 ts_status launch_eig_small(int n, int R, const T* K, const T* Q, int r, T* CnT, T* Fm, T* Uout,
                            bool polish64, int* flag, cudaStream_t st);
-// The whole subproblem after [G | H] = Z^T [Z | Y] in one block (RSVD or exact; see
-// solve.cu): writes A_out (s x R), CnT (r x R, may be null) and the core (may be null).
-// Mbuf: k x s (RSVD) or r x s (exact) scratch.
+// The whole subproblem in one block (lrls_fused.cu) after [G | W | H] =
+// Z^T [Z | Y Omega | Y] (RSVD) or [G | H] = Z^T [Z | Y] (exact, W unused): writes A_out
+// (s x R), CnT (r x R, may be null) and the core (may be null).  Mbuf: k x s scratch,
+// used when D does not fit on chip.  lrls_fused_supported() tells whether the shape fits.
 size_t lrls_fused_smem_bytes(int r, int s, int k, int R, int solve, size_t tsize, bool fp64,
-                             bool* stage_om);
+                             bool* m_smem);
+bool lrls_fused_supported(int r, int s, int k, int R, int solve, size_t tsize, bool fp64);
 template <typename T>
 ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, const T* G,
-                            long ldg, const T* H, long ldh, const T* Om, T* Mbuf, T* CnT,
+                            long ldg, const T* W, long ldw, const T* H, long ldh, T* Mbuf, T* CnT,
                             T* A_out, T* core, CoreMap map, int* flag, cudaStream_t st);
 // Factor columns V (s x R) with V(i, c) = sum_a M(i, a) Fm(a, c) (M element (i, a) at
 // M[i*rs + a*cs], a < kdim), or V(i, c) = M[i*rs + c*cs] when Fm is null.  Each

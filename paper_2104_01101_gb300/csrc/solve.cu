@@ -11,7 +11,7 @@
 // (FP32 data only) the QR of Alg. 5 runs in FP64 and the eigensolver ends with
 // FP64 Jacobi sweeps on V^T K V: GB300's FP64 rate is ~1/64 of FP32, so this is an
 // option, not the default.  FP64 data runs FP64 everywhere.
-#include "internal.cuh"
+#include "dense_la.cuh"
 
 namespace ts {
 
@@ -21,16 +21,6 @@ constexpr int NWARP = NT / 32;
 constexpr int NB = 16;  // Cholesky / triangular-solve panel width
 }  // namespace
 
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 // ---------------------------------------------------------------- Cholesky
 
@@ -371,126 +361,6 @@ __global__ void __launch_bounds__(NT) k_chol_solve(int r, int s, const T* __rest
 
 // ---------------------------------------------------------------- symmetric eigensolver
 
-struct JacobiShape {
-  int n;   // matrix order
-  int np;  // n rounded up to even (round-robin players)
-  int lg;  // log2 of the column stride (power of two >= n)
-};
-
-// Barrier policies: the whole block, or the first nthr threads (named barrier 1).
-struct BlockSync {
-  __device__ void operator()() const { __syncthreads(); }
-  __device__ int size() const { return blockDim.x; }
-};
-struct SubSync {
-  int nthr;  // multiple of 32
-  __device__ void operator()() const { asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory"); }
-  __device__ int size() const { return nthr; }
-};
-
-// Threads the Jacobi sweep of a matrix of order n keeps busy (pairs x padded columns).
-__host__ __device__ inline int jacobi_threads(int n) {
-  int lg = 0;
-  while ((1 << lg) < n) ++lg;
-  const int work = (((n + 1) & ~1) / 2) << lg;
-  int t = ((work + 31) / 32) * 32;
-  return t < 64 ? 64 : (t > 512 ? 512 : t);
-}
-
-// One cyclic sweep with round-robin pairing on A (n x n, row stride n); V accumulates.
-// Called by the threads of `sync` (threadIdx.x < sync.size()).
-template <typename U, typename Sync = BlockSync>
-__device__ void jacobi_sweep(U* A, U* V, const JacobiShape& js, int* rp, int* rq, U* rc, U* rs,
-                             Sync sync = Sync()) {
-  const int n = js.n, np = js.np, npairs = np / 2;
-  const int np2 = 1 << js.lg;
-  const int nthr = sync.size();
-  for (int t = 0; t < np - 1; ++t) {
-    if (threadIdx.x < npairs) {
-      const int i = threadIdx.x;
-      const int a = i == 0 ? t : (t + i) % (np - 1);
-      const int b = i == 0 ? np - 1 : (t - i + np - 1) % (np - 1);
-      int p = min(a, b);
-      const int q = max(a, b);
-      U c = 1, s = 0;
-      if (q < n) {
-        const U apq = A[p * n + q];
-        if (apq != (U)0) {
-          const U theta = (A[q * n + q] - A[p * n + p]) / (2 * apq);
-          const U tt = (theta >= (U)0 ? (U)1 : (U)-1) / (fabs(theta) + sqrt(theta * theta + (U)1));
-          c = (U)1 / sqrt(tt * tt + (U)1);
-          s = tt * c;
-        }
-      } else {
-        p = -1;
-      }
-      rp[i] = p;
-      rq[i] = q;
-      rc[i] = c;
-      rs[i] = s;
-    }
-    sync();
-    for (int e = threadIdx.x; e < npairs * np2; e += nthr) {  // rows p, q
-      const int i = e >> js.lg, l = e & (np2 - 1);
-      const int p = rp[i];
-      if (p < 0 || l >= n) continue;
-      const int q = rq[i];
-      const U c = rc[i], s = rs[i];
-      const U ap = A[p * n + l], aq = A[q * n + l];
-      A[p * n + l] = c * ap - s * aq;
-      A[q * n + l] = s * ap + c * aq;
-    }
-    sync();
-    for (int e = threadIdx.x; e < npairs * np2; e += nthr) {  // columns p, q and V
-      const int i = e >> js.lg, l = e & (np2 - 1);
-      const int p = rp[i];
-      if (p < 0 || l >= n) continue;
-      const int q = rq[i];
-      const U c = rc[i], s = rs[i];
-      const U ap = A[l * n + p], aq = A[l * n + q];
-      A[l * n + p] = c * ap - s * aq;
-      A[l * n + q] = s * ap + c * aq;
-      const U vp = V[l * n + p], vq = V[l * n + q];
-      V[l * n + p] = c * vp - s * vq;
-      V[l * n + q] = s * vp + c * vq;
-    }
-    sync();
-  }
-}
-
-// Off-diagonal and total squared Frobenius norms (valid in every participating thread;
-// red holds 2 * (threads / 32) + 2 values).
-template <typename U, typename Sync = BlockSync>
-__device__ void jacobi_norms(const U* A, int n, U* red, U& off, U& tot, Sync sync = Sync()) {
-  const int nthr = sync.size();
-  U o = 0, a = 0;
-  for (int e = threadIdx.x; e < n * n; e += nthr) {
-    const U v = A[e];
-    a += v * v;
-    if (e / n != e % n) o += v * v;
-  }
-  o = warp_sum(o);
-  a = warp_sum(a);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = nthr >> 5;
-  if (lane == 0) {
-    red[2 * warp] = o;
-    red[2 * warp + 1] = a;
-  }
-  sync();
-  if (threadIdx.x == 0) {
-    U so = 0, sa = 0;
-    for (int w = 0; w < nw; ++w) {
-      so += red[2 * w];
-      sa += red[2 * w + 1];
-    }
-    red[2 * nw] = so;
-    red[2 * nw + 1] = sa;
-  }
-  sync();
-  off = red[2 * nw];
-  tot = red[2 * nw + 1];
-  sync();
-}
 
 // K (n x n) = U Lambda U^T, eigenvalues descending, sigma = sqrt(lambda):
 // CnT = Q U_R Sigma_R (Q null: identity, r = n), Fm = U_R Sigma_R^{-1}, Uout = U_R.
@@ -684,410 +554,6 @@ __global__ void __launch_bounds__(256) k_finalize(int s, int R, const T* __restr
   }
 }
 
-// ---------------------------------------------------------------- fused subproblem solve
-
-// Shared-memory layout of k_lrls_fused (byte offsets; U = QR compute type).
-struct FusedLayout {
-  size_t hA, hV, hQ, htau, hred, Gi, colp, rowp, Cm, Qs, Es, Kk, Vk, Fm, CnTs, Oms, K64, V64, KV64,
-      total;
-};
-
-__host__ __device__ inline FusedLayout fused_layout(int r, int s, int k, int R, int solve,
-                                                    size_t tsz, size_t usz, bool stage_om,
-                                                    bool polish) {
-  FusedLayout L{};
-  const bool rsvd = solve == TS_SOLVE_RSVD;
-  const int n = rsvd ? k : r;
-  size_t off = 0;
-  auto take = [&](size_t bytes) {
-    off = (off + 15) & ~(size_t)15;
-    const size_t o = off;
-    off += bytes;
-    return o;
-  };
-  const size_t rk = rsvd ? (size_t)r * k : 0;
-  L.hA = take(usz * rk);
-  L.hV = take(usz * rk);
-  L.hQ = take(usz * rk);
-  L.htau = take(usz * (rsvd ? k : 0));
-  L.hred = take(usz * 2);
-  L.Gi = take(tsz * (size_t)r * (r + 1));
-  L.colp = take(tsz * r);
-  L.rowp = take(tsz * r);
-  L.Cm = take(tsz * rk);
-  L.Qs = take(tsz * rk);
-  L.Es = take(tsz * rk);
-  L.Kk = take(tsz * (size_t)n * n);
-  L.Vk = take(tsz * (size_t)n * n);
-  L.Fm = take(tsz * (size_t)n * R);
-  L.CnTs = take(tsz * (size_t)r * R);
-  L.Oms = take(stage_om ? tsz * (size_t)s * k : 0);
-  L.K64 = take(polish ? 8 * (size_t)n * n : 0);
-  L.V64 = take(polish ? 8 * (size_t)n * n : 0);
-  L.KV64 = take(polish ? 8 * (size_t)n * n : 0);
-  L.total = off;
-  return L;
-}
-
-template <typename T>
-struct FusedArgs {
-  int r, s, k, R, solve;
-  const T* G;
-  long ldg;  // r x r
-  const T* H;
-  long ldh;      // r x s
-  const T* Om;   // s x k (RSVD)
-  T* Mbuf;       // scratch: k x s (RSVD, D) or r x s (exact, X)
-  T* CnT;        // r x R out
-  T* A_out;      // s x R out
-  T* core;
-  CoreMap map;
-  int* flag;
-  bool stage_om;
-};
-
-// The whole sketched subproblem after [G | H] = Z^T [Z | Y], in one block:
-//   G^{-1} by Gauss-Jordan (G is SPD and well conditioned: Z = S P with P orthonormal);
-//   RSVD (Alg. 5): W = H Omega, C = G^{-1} W, Q = qr(C) (Householder, type U),
-//     E = G^{-1} Q, D = E^T H (= Q^T G^{-1} Z^T Y), K = D D^T;
-//   exact: X = G^{-1} H, K = X X^T;
-//   K = U Lambda U^T (Jacobi in T, optional FP64 polish), CnT = Q U_R Sigma_R (Q = I for
-//   exact), A = M^T U_R Sigma_R^{-1} with M = D or X, canonical signs, core scatter.
-template <typename T, typename U, bool POLISH64>
-__global__ void __launch_bounds__(1024) k_lrls_fused(FusedArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int rp[kMaxEig / 2 + 1], rq[kMaxEig / 2 + 1];
-  __shared__ T rcT[kMaxEig / 2 + 1], rsT[kMaxEig / 2 + 1];
-  __shared__ double rc64[kMaxEig / 2 + 1], rs64[kMaxEig / 2 + 1];
-  __shared__ T redT[2 * 16 + 2];
-  __shared__ double red64[2 * 16 + 2];
-  __shared__ int order[kMaxEig];
-  __shared__ T lamT[kMaxEig];
-  __shared__ T sgn[64];
-  const int r = a.r, s = a.s, R = a.R;
-  const bool rsvd = a.solve == TS_SOLVE_RSVD;
-  const int k = a.k;
-  const int n = rsvd ? k : r;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int nthr = blockDim.x, nwarp = nthr >> 5;
-  const int ld = r + 1;
-  const FusedLayout L = fused_layout(r, s, k, R, a.solve, sizeof(T), sizeof(U), a.stage_om,
-                                     POLISH64);
-  U* hA = reinterpret_cast<U*>(smem_raw + L.hA);
-  U* hV = reinterpret_cast<U*>(smem_raw + L.hV);
-  U* hQ = reinterpret_cast<U*>(smem_raw + L.hQ);
-  U* htau = reinterpret_cast<U*>(smem_raw + L.htau);
-  U* hred = reinterpret_cast<U*>(smem_raw + L.hred);
-  T* Gi = reinterpret_cast<T*>(smem_raw + L.Gi);
-  T* colp = reinterpret_cast<T*>(smem_raw + L.colp);
-  T* rowp = reinterpret_cast<T*>(smem_raw + L.rowp);
-  T* Cm = reinterpret_cast<T*>(smem_raw + L.Cm);
-  T* Qs = reinterpret_cast<T*>(smem_raw + L.Qs);
-  T* Es = reinterpret_cast<T*>(smem_raw + L.Es);
-  T* Kk = reinterpret_cast<T*>(smem_raw + L.Kk);
-  T* Vk = reinterpret_cast<T*>(smem_raw + L.Vk);
-  T* Fm = reinterpret_cast<T*>(smem_raw + L.Fm);
-  T* CnTs = reinterpret_cast<T*>(smem_raw + L.CnTs);
-  const T* Om = a.stage_om ? reinterpret_cast<T*>(smem_raw + L.Oms) : a.Om;
-
-  // 1. stage G (and Omega)
-  for (int i = warp; i < r; i += nwarp)
-    for (int j = lane; j < r; j += 32) Gi[i * ld + j] = a.G[i * a.ldg + j];
-  if (rsvd && a.stage_om)
-    for (int t = tid; t < s * k; t += nthr) const_cast<T*>(Om)[t] = a.Om[t];
-  __syncthreads();
-  // 2. G^{-1} in place (Gauss-Jordan, no pivoting)
-  for (int p = 0; p < r; ++p) {
-    for (int t = tid; t < r; t += nthr) {
-      colp[t] = Gi[t * ld + p];
-      rowp[t] = Gi[p * ld + t];
-    }
-    __syncthreads();
-    T piv = rowp[p];
-    if (!(piv > (T)0) || !isfinite((double)piv)) {
-      if (tid == 0 && a.flag) atomicExch(a.flag, 1);
-      piv = (T)1;
-    }
-    const T inv = (T)1 / piv;
-    for (int i = warp; i < r; i += nwarp) {
-      const T ci = colp[i] * inv;
-      for (int j = lane; j < r; j += 32) {
-        T v;
-        if (i == p) v = (j == p) ? inv : rowp[j] * inv;
-        else v = (j == p) ? -ci : Gi[i * ld + j] - ci * rowp[j];
-        Gi[i * ld + j] = v;
-      }
-    }
-    __syncthreads();
-  }
-  const T* M;  // n x s, the matrix whose Gram K is decomposed
-  if (rsvd) {
-    // 3. W = H Omega;  4. C = G^{-1} W
-    for (int e = tid; e < r * k; e += nthr) {
-      const int i = e / k, c = e - (e / k) * k;
-      const T* h = a.H + i * a.ldh;
-      T acc = 0;
-      for (int j = 0; j < s; ++j) acc += h[j] * Om[j * k + c];
-      Cm[e] = acc;
-    }
-    __syncthreads();
-    for (int e = tid; e < r * k; e += nthr) {
-      const int i = e / k, c = e - (e / k) * k;
-      T acc = 0;
-      for (int l = 0; l < r; ++l) acc += Gi[i * ld + l] * Cm[l * k + c];
-      hA[e] = (U)acc;
-    }
-    __syncthreads();
-    // 5. Q = qr(C)
-    householder_q<U>(hA, r, k, hV, htau, hQ, hred);
-    for (int t = tid; t < r * k; t += nthr) Qs[t] = (T)hQ[t];
-    __syncthreads();
-    // 6. E = G^{-1} Q;  7. D = E^T H
-    for (int e = tid; e < r * k; e += nthr) {
-      const int i = e / k, c = e - (e / k) * k;
-      T acc = 0;
-      for (int l = 0; l < r; ++l) acc += Gi[i * ld + l] * Qs[l * k + c];
-      Es[e] = acc;
-    }
-    __syncthreads();
-    for (int e = tid; e < k * s; e += nthr) {
-      const int c = e / s, j = e - (e / s) * s;
-      T acc = 0;
-      for (int i = 0; i < r; ++i) acc += Es[i * k + c] * a.H[i * a.ldh + j];
-      a.Mbuf[e] = acc;
-    }
-  } else {
-    // exact: X = G^{-1} H
-    for (int e = tid; e < r * s; e += nthr) {
-      const int i = e / s, j = e - (e / s) * s;
-      T acc = 0;
-      for (int l = 0; l < r; ++l) acc += Gi[i * ld + l] * a.H[l * a.ldh + j];
-      a.Mbuf[e] = acc;
-    }
-  }
-  __syncthreads();
-  M = a.Mbuf;
-  // 8. K = M M^T (upper triangle by warps, mirrored)
-  for (int pr = warp; pr < n * n; pr += nwarp) {
-    const int i = pr / n, j = pr - (pr / n) * n;
-    if (j < i) continue;
-    T acc = 0;
-    for (int t = lane; t < s; t += 32) acc += M[i * s + t] * M[j * s + t];
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      Kk[i * n + j] = acc;
-      Kk[j * n + i] = acc;
-    }
-  }
-  for (int e = tid; e < n * n; e += nthr) Vk[e] = (e / n == e % n) ? (T)1 : (T)0;
-  __syncthreads();
-  // 9. Jacobi on K by the first nj threads
-  JacobiShape js;
-  js.n = n;
-  js.np = (n + 1) & ~1;
-  js.lg = 0;
-  while ((1 << js.lg) < n) ++js.lg;
-  const int nj = jacobi_threads(n);
-  if (tid < nj) {
-    SubSync sync{nj};
-    const T tol = sizeof(T) == 4 ? (T)1e-11 : (T)1e-28;
-    T off, tot;
-    for (int sweep = 0; sweep < 24; ++sweep) {
-      jacobi_norms<T, SubSync>(Kk, n, redT, off, tot, sync);
-      if (off <= tol * tot || tot == (T)0) break;
-      jacobi_sweep<T, SubSync>(Kk, Vk, js, rp, rq, rcT, rsT, sync);
-    }
-    if constexpr (POLISH64) {
-      double* K64 = reinterpret_cast<double*>(smem_raw + L.K64);
-      double* V64 = reinterpret_cast<double*>(smem_raw + L.V64);
-      double* KV = reinterpret_cast<double*>(smem_raw + L.KV64);
-      // exact FP64 Gram of M, then V^T K V
-      for (int pr = warp; pr < n * n; pr += (nj >> 5)) {
-        const int i = pr / n, j = pr - (pr / n) * n;
-        if (j < i) continue;
-        double acc = 0;
-        for (int t = lane; t < s; t += 32) acc += (double)M[i * s + t] * (double)M[j * s + t];
-        acc = warp_sum(acc);
-        if (lane == 0) {
-          K64[i * n + j] = acc;
-          K64[j * n + i] = acc;
-        }
-      }
-      for (int e = tid; e < n * n; e += nj) V64[e] = (double)Vk[e];
-      sync();
-      for (int e = tid; e < n * n; e += nj) {
-        const int i = e / n, j = e % n;
-        double acc = 0;
-        for (int b = 0; b < n; ++b) acc += K64[i * n + b] * V64[b * n + j];
-        KV[e] = acc;
-      }
-      sync();
-      for (int e = tid; e < n * n; e += nj) {
-        const int i = e / n, j = e % n;
-        double acc = 0;
-        for (int b = 0; b < n; ++b) acc += V64[b * n + i] * KV[b * n + j];
-        K64[e] = acc;
-      }
-      sync();
-      for (int e = tid; e < n * n; e += nj) {
-        const int i = e / n, j = e % n;
-        if (i < j) {
-          const double v = 0.5 * (K64[i * n + j] + K64[j * n + i]);
-          K64[i * n + j] = v;
-          K64[j * n + i] = v;
-        }
-      }
-      sync();
-      double o64, t64;
-      for (int sweep = 0; sweep < 10; ++sweep) {
-        jacobi_norms<double, SubSync>(K64, n, red64, o64, t64, sync);
-        if (o64 <= 1e-28 * t64 || t64 == 0) break;
-        jacobi_sweep<double, SubSync>(K64, V64, js, rp, rq, rc64, rs64, sync);
-      }
-      for (int e = tid; e < n * n; e += nj) Vk[e] = (T)V64[e];
-      if (tid < n) Kk[tid * n + tid] = (T)K64[tid * n + tid];
-    }
-  }
-  __syncthreads();
-  // 10. eigenvalues descending; Fm = U_R / sigma; CnT = Q U_R sigma (Q = I for exact)
-  if (tid == 0) {
-    for (int i = 0; i < n; ++i) {
-      lamT[i] = Kk[i * n + i];
-      order[i] = i;
-    }
-    for (int i = 0; i < n; ++i) {
-      int best = i;
-      for (int j = i + 1; j < n; ++j)
-        if (lamT[order[j]] > lamT[order[best]]) best = j;
-      const int t = order[i];
-      order[i] = order[best];
-      order[best] = t;
-    }
-    for (int i = 0; i < n; ++i)
-      if (!isfinite((double)lamT[i]) && a.flag) atomicExch(a.flag, 1);
-  }
-  __syncthreads();
-  for (int e = tid; e < n * R; e += nthr) {
-    const int i = e / R, c = e - (e / R) * R;
-    const T l = lamT[order[c]];
-    const T sig = l > (T)0 ? sqrt(l) : (T)0;
-    Fm[e] = sig > (T)0 ? Vk[i * n + order[c]] / sig : (T)0;
-  }
-  for (int e = tid; e < r * R; e += nthr) {
-    const int i = e / R, c = e - (e / R) * R;
-    const T l = lamT[order[c]];
-    const T sig = l > (T)0 ? sqrt(l) : (T)0;
-    T acc;
-    if (rsvd) {
-      acc = 0;
-      for (int b = 0; b < k; ++b) acc += Qs[i * k + b] * Vk[b * n + order[c]];
-    } else {
-      acc = Vk[i * n + order[c]];
-    }
-    CnTs[e] = acc * sig;
-  }
-  __syncthreads();
-  // 11. A = M^T Fm (unsigned), 12. canonical signs, 13. signed outputs and core
-  for (int e = tid; e < s * R; e += nthr) {
-    const int i = e / R, c = e - (e / R) * R;
-    T acc = 0;
-    for (int b = 0; b < n; ++b) acc += M[b * s + i] * Fm[b * R + c];
-    a.A_out[e] = acc;
-  }
-  __syncthreads();
-  for (int c = warp; c < R; c += nwarp) {
-    T best = (T)-1;
-    int bidx = 0x7fffffff;
-    for (int i = lane; i < s; i += 32) {
-      const T v = fabs(a.A_out[(long)i * R + c]);
-      if (v > best || (v == best && i < bidx)) {
-        best = v;
-        bidx = i;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bidx, o);
-      if (ob > best || (ob == best && oi < bidx)) {
-        best = ob;
-        bidx = oi;
-      }
-    }
-    if (lane == 0) sgn[c] = a.A_out[(long)bidx * R + c] < (T)0 ? (T)-1 : (T)1;
-  }
-  __syncthreads();
-  for (int e = tid; e < s * R; e += nthr) {
-    const int c = e - (e / R) * R;
-    a.A_out[e] *= sgn[c];
-  }
-  for (int e = tid; e < r * R; e += nthr) {
-    const int rho = e / R, c = e - (e / R) * R;
-    const T v = sgn[c] * CnTs[e];
-    if (a.CnT) a.CnT[e] = v;
-    if (a.core) {
-      long idx = 0, stride = 1, x = rho;
-      for (int kk = a.map.order - 1; kk >= 0; --kk) {
-        int digit;
-        if (kk == a.map.n) {
-          digit = c;
-        } else {
-          digit = (int)(x % a.map.ranks[kk]);
-          x /= a.map.ranks[kk];
-        }
-        idx += digit * stride;
-        stride *= a.map.ranks[kk];
-      }
-      a.core[idx] = v;
-    }
-  }
-}
-
-size_t lrls_fused_smem_bytes(int r, int s, int k, int R, int solve, size_t tsize, bool fp64,
-                             bool* stage_om) {
-  const size_t usz = fp64 ? 8 : tsize;
-  FusedLayout L = fused_layout(r, s, k, R, solve, tsize, usz, false, fp64);
-  const size_t om = solve == TS_SOLVE_RSVD ? tsize * (size_t)s * k : 0;
-  const bool stage = om > 0 && L.total + om + 16 <= 160 * 1024;
-  if (stage_om) *stage_om = stage;
-  return fused_layout(r, s, k, R, solve, tsize, usz, stage, fp64).total + 16;
-}
-
-template <typename T>
-ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, const T* G,
-                            long ldg, const T* H, long ldh, const T* Om, T* Mbuf, T* CnT,
-                            T* A_out, T* core, CoreMap map, int* flag, cudaStream_t st) {
-  FusedArgs<T> a{};
-  a.r = r;
-  a.s = s;
-  a.k = k;
-  a.R = R;
-  a.solve = solve;
-  a.G = G;
-  a.ldg = ldg;
-  a.H = H;
-  a.ldh = ldh;
-  a.Om = Om;
-  a.Mbuf = Mbuf;
-  a.CnT = CnT;
-  a.A_out = A_out;
-  a.core = core;
-  a.map = map;
-  a.flag = flag;
-  const bool f64 = fp64 && sizeof(T) == 4;
-  const size_t smem = lrls_fused_smem_bytes(r, s, k, R, solve, sizeof(T), f64, &a.stage_om);
-  if (smem > kMaxSmem) return fail(TS_ERR_SHAPE, "fused solve: %zu bytes of shared memory", smem);
-  if (f64) {
-    TS_TRY(ensure_dynamic_smem((const void*)k_lrls_fused<T, double, true>, smem));
-    k_lrls_fused<T, double, true><<<1, 1024, smem, st>>>(a);
-  } else {
-    TS_TRY(ensure_dynamic_smem((const void*)k_lrls_fused<T, T, false>, smem));
-    k_lrls_fused<T, T, false><<<1, 1024, smem, st>>>(a);
-  }
-  TS_LAUNCH_CHECK();
-  return TS_OK;
-}
-
 // ---------------------------------------------------------------- launchers
 
 template <typename T>
@@ -1163,9 +629,6 @@ ts_status launch_finalize(int s, int R, const T* M, long rs, long cs, int kdim, 
                                          int*, cudaStream_t);                                    \
   template ts_status launch_finalize<T>(int, int, const T*, long, long, int, const T*, T*, T*,  \
                                         int, T*, CoreMap, cudaStream_t);                         \
-  template ts_status launch_lrls_fused<T>(int, int, int, int, int, bool, const T*, long,        \
-                                          const T*, long, const T*, T*, T*, T*, T*, CoreMap,     \
-                                          int*, cudaStream_t);                                   \
   template ts_status launch_qr_only<T>(int, int, const T*, T*, bool, cudaStream_t);             \
   template ts_status newton_schulz_inverse<T>(int, const T*, long, T*, T*, T*, int,             \
                                               const GemmSplit<T>*, cudaStream_t);

@@ -62,9 +62,7 @@ static void rrf_widths(const ts_tensor& X, int n, int R, int m, int k1_opt, int 
 // and the block's shared-memory layout fits.
 static bool fused_ok(int r, long s, int kc, int R, int solve, size_t tsize, bool fp64) {
   if ((long)r * s > (1l << 22)) return false;
-  const int n = solve == TS_SOLVE_RSVD ? kc : r;
-  if (n > kMaxEig) return false;
-  return lrls_fused_smem_bytes(r, (int)s, kc, R, solve, tsize, fp64, nullptr) <= kMaxSmem;
+  return lrls_fused_supported(r, (int)s, kc, R, solve, tsize, fp64);
 }
 
 static int rsvd_width(int R, int p, int r, int64_t s) {
@@ -89,8 +87,9 @@ struct Shape {
   bool fused[TS_MAX_ORDER];  // subproblem n takes the fused single-block solve
   bool large[TS_MAX_ORDER];  // subproblem n inverts Z^T Z by Newton-Schulz (large r)
   int k1[TS_MAX_ORDER], k2[TS_MAX_ORDER];
-  size_t om_off[TS_MAX_ORDER];  // offset of Omega(sweep, n) inside one sweep's block
-  size_t om_sweep;              // elements of all Omegas of one sweep
+  OmegaBlocks ob;                 // every Omega(sweep, n): mode blocks s_n x (sweeps k_n)
+  int64_t yom_off[TS_MAX_ORDER];  // Y_n Omega(., n): mode blocks m x (sweeps k_n)
+  int64_t yom_total;
   int64_t smax;
   int rmax, kmax, Rmax, k1max, k2max, chain_cols_max;
 };
@@ -119,7 +118,10 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
   S.fp64solve = opt->solve_fp64 != 0 && X->dtype == TS_F32;
   S.smax = 0;
   S.rmax = S.kmax = S.Rmax = S.k1max = S.k2max = S.chain_cols_max = 0;
-  S.om_sweep = 0;
+  memset(&S.ob, 0, sizeof(S.ob));
+  S.ob.N = S.N;
+  S.ob.nsweeps = sweeps;
+  S.yom_total = 0;
   const size_t tsz = dtype_size(X->dtype);
   for (int k = 0; k < S.N; ++k) {
     if (ranks[k] < 1 || ranks[k] >= X->dims[k])
@@ -169,8 +171,12 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
     if (r > S.rmax) S.rmax = (int)r;
     if (S.kc[n] > S.kmax) S.kmax = S.kc[n];
     if (cc > S.chain_cols_max) S.chain_cols_max = cc;
-    S.om_off[n] = S.om_sweep;
-    S.om_sweep += (size_t)X->dims[n] * S.kc[n];
+    S.ob.rows[n] = X->dims[n];
+    S.ob.k[n] = S.kc[n];
+    S.ob.off[n] = S.ob.total;
+    S.ob.total += X->dims[n] * (int64_t)sweeps * S.kc[n];
+    S.yom_off[n] = S.yom_total;
+    S.yom_total += (int64_t)m * sweeps * S.kc[n];
     S.k1[n] = S.k2[n] = 0;
     if (S.rrf && n >= 1) {
       rrf_widths(*X, n, ranks[n], m, opt->rrf_k1, opt->rrf_k2, &S.k1[n], &S.k2[n]);
@@ -200,7 +206,8 @@ struct Work {
   T* GW;   // [Z^T Z | Z^T Y Omega] (r x (r + k)) or [Z^T Z | Z^T Y] (r x (r + s), fused path)
   T* Mbuf; // fused path: D (k x s) or X (r x s)
   T *Ginv, *NS1, *NS2, *Cb;  // large-r path: G^{-1}, Newton-Schulz scratch, C = G^{-1} W
-  T* Om;   // Omega of every (sweep, mode), s_n x k_n each
+  T* Om;   // Omega of every (sweep, mode): mode blocks s_n x (sweeps k_n)
+  T* YOm;  // Y_n Omega(sweep, n) for every (sweep, mode): mode blocks m x (sweeps k_n)
   T *Q, *E, *Mm, *D, *K, *CnT, *Fm, *H, *Xs, *Gm, *Bm, *Ylev;
   int32_t* samples;
   double* levscr;
@@ -239,7 +246,7 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
   size_t gw = (size_t)r * (r + k), mb = 0;
   for (int n = 0; n < N; ++n)
     if (S.fused[n]) {
-      const size_t h = (size_t)S.r[n] * (S.r[n] + X.dims[n]);
+      const size_t h = (size_t)S.r[n] * (S.r[n] + S.kc[n] + X.dims[n]);
       const size_t nn = S.solve == TS_SOLVE_RSVD ? S.kc[n] : S.r[n];
       if (h > gw) gw = h;
       if (nn * X.dims[n] > mb) mb = nn * X.dims[n];
@@ -255,7 +262,10 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
     w.NS2 = b.take<T>((size_t)r * r);
     w.Cb = b.take<T>((size_t)r * k);
   }
-  if (S.solve == TS_SOLVE_RSVD) w.Om = b.take<T>(S.om_sweep * S.sweeps);
+  if (S.solve == TS_SOLVE_RSVD) {
+    w.Om = b.take<T>((size_t)S.ob.total);
+    if (S.kind == TS_TENSORSKETCH) w.YOm = b.take<T>((size_t)S.yom_total);
+  }
   w.Q = b.take<T>((size_t)r * k);
   w.E = b.take<T>((size_t)r * k);
   w.Mm = b.take<T>((size_t)m * k);
@@ -304,29 +314,48 @@ static OutView<T> ov(T* p, long rs, long cs) {
 }
 
 // Sketched subproblem on Z = ZW[:, :r] (column-major) and Y (m x s) -> CnT (r x R),
-// A_out (s x R), core scattered when core != null.  RSVD (Alg. 5) with the test
-// matrix Om (s x k), or the exact truncated solve (the solution of Theorem 4.1).
+// A_out (s x R), core scattered when core != null.  RSVD (Alg. 5): yom views Y Omega
+// (m x k) when the caller formed it, else it is formed here from the test matrix Om
+// (s x k, row stride ldo) into ZW[:, r:r+k].  Exact: the truncated solve of Theorem 4.1.
 template <typename T>
 static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc, bool fp64,
-                                  const T* Om, const T* Y, Work<T>& w, T* A_out, T* core,
-                                  const CoreMap& map, cudaStream_t st) {
+                                  const T* Om, long ldo, const MatView<T>* yom, const T* Y,
+                                  Work<T>& w, T* A_out, T* core, const CoreMap& map,
+                                  cudaStream_t st) {
   T* ZW = w.ZW;
   const MatView<T> Zt = mv<T>(ZW, m, 1);  // r x m view of Z^T
   const MatView<T> Zm = mv<T>(ZW, 1, m);  // m x r view of Z
   const GemmSplit<T>* sp = &w.split;
+  const int k = kc;
+  MatView<T> yv{};
+  if (solve == TS_SOLVE_RSVD) {
+    if (yom) {
+      yv = *yom;
+    } else {
+      TS_TRY(gemm<T>(m, k, s, 1.0, mv<T>(Y, s, 1), mv<T>(Om, ldo, 1), 0.0,
+                     ov<T>(ZW + (size_t)r * m, 1, m), sp, st));
+      yv = mv<T>(ZW + (size_t)r * m, 1, m);
+    }
+  }
   if (fused_ok(r, s, kc, R, solve, sizeof(T), fp64)) {
-    // [G | H] = Z^T [Z | Y] in one product, then the whole solve in one block
-    TS_TRY(gemm2<T>(r, r + s, m, 1.0, Zt, mv<T>(ZW, 1, m), r, mv<T>(Y, s, 1), 0.0,
-                    ov<T>(w.GW, r + s, 1), sp, st));
-    return launch_lrls_fused<T>(r, s, kc, R, solve, fp64, w.GW, r + s, w.GW + r, r + s, Om,
+    // [G | W | H] = Z^T [Z | Y Omega | Y] (exact: [G | H]) in one product, then the whole
+    // solve in one block
+    if (solve == TS_SOLVE_RSVD) {
+      const int N = r + k + s;
+      TS_TRY(gemm3<T>(r, N, m, 1.0, Zt, Zm, r, yv, r + k, mv<T>(Y, s, 1), 0.0,
+                      ov<T>(w.GW, N, 1), sp, st));
+      return launch_lrls_fused<T>(r, s, k, R, solve, fp64, w.GW, N, w.GW + r, N, w.GW + r + k,
+                                  N, w.Mbuf, w.CnT, A_out, core, map, w.flag, st);
+    }
+    const int N = r + s;
+    TS_TRY(gemm2<T>(r, N, m, 1.0, Zt, Zm, r, mv<T>(Y, s, 1), 0.0, ov<T>(w.GW, N, 1), sp, st));
+    return launch_lrls_fused<T>(r, s, k, R, solve, fp64, w.GW, N, nullptr, 0, w.GW + r, N,
                                 w.Mbuf, w.CnT, A_out, core, map, w.flag, st);
   }
   if (solve == TS_SOLVE_RSVD) {
-    const int k = kc;
-    // Y Omega into the k columns after Z, then [G | W] = Z^T [Z | Y Omega] in one product
-    TS_TRY(gemm<T>(m, k, s, 1.0, mv<T>(Y, s, 1), mv<T>(Om, k, 1), 0.0,
-                   ov<T>(ZW + (size_t)r * m, 1, m), sp, st));
-    TS_TRY(gemm<T>(r, r + k, m, 1.0, Zt, mv<T>(ZW, 1, m), 0.0, ov<T>(w.GW, r + k, 1), sp, st));
+    // [G | W] = Z^T [Z | Y Omega] in one product
+    TS_TRY(gemm3<T>(r, r + k, m, 1.0, Zt, Zm, r, yv, r + k, yv, 0.0, ov<T>(w.GW, r + k, 1), sp,
+                    st));
     if (rsvd_stage1_smem_bytes(r, k, sizeof(T), fp64) <= kMaxSmem) {
       TS_TRY(launch_rsvd_stage1<T>(r, k, w.GW, r + k, w.GW + r, r + k, w.Q, w.E, fp64, w.flag,
                                    st));
@@ -419,16 +448,18 @@ static ts_status rrf_all(const ts_tensor& X, const Shape& S, uint64_t seed, Work
   return TS_OK;
 }
 
-// Gaussian test matrices of Alg. 5 for every (sweep, mode), drawn in one launch
-// per block: Omega(sweep, n) is the object (seed, RSVD_GAUSS, sweep, n, 0).
+// Y_n Omega(sweep, n) for sweeps [t0, t0 + nt) of every mode, one product per mode.
 template <typename T>
-static ts_status draw_omegas(const ts_tensor& X, const Shape& S, uint64_t seed, Work<T>& w,
-                             cudaStream_t st) {
-  for (int sweep = 0; sweep < S.sweeps; ++sweep)
-    for (int n = 0; n < S.N; ++n)
-      TS_TRY(launch_gaussian<T>(seed, make_tag(TS_PURPOSE_RSVD_GAUSS, sweep, n, 0),
-                                (int64_t)X.dims[n] * S.kc[n], 1.0,
-                                w.Om + S.om_sweep * sweep + S.om_off[n], st));
+static ts_status rhs_times_omegas(const ts_tensor& X, const Shape& S, Work<T>& w, int t0, int nt,
+                                  cudaStream_t st) {
+  for (int n = 0; n < S.N; ++n) {
+    const int k = S.kc[n];
+    const long ld = (long)S.sweeps * k;
+    const int s = (int)X.dims[n];
+    TS_TRY(gemm<T>(S.m, nt * k, s, 1.0, mv<T>(w.Y[n], s, 1),
+                   mv<T>(w.Om + S.ob.off[n] + (size_t)t0 * k, ld, 1), 0.0,
+                   ov<T>(w.YOm + S.yom_off[n] + (size_t)t0 * k, ld, 1), &w.split, st));
+  }
   return TS_OK;
 }
 
@@ -449,12 +480,14 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
   TS_CUDA(cudaMemsetAsync(w.flag, 0, 256 + kGemmCounters * sizeof(unsigned), st));
   if (S.rrf) TS_TRY(rrf_all<T>(X, S, opt.seed, w, factors, st));
   TS_TRY(phase(opt, 1, st));
-  if (S.solve == TS_SOLVE_RSVD) TS_TRY(draw_omegas<T>(X, S, opt.seed, w, st));
+  if (S.solve == TS_SOLVE_RSVD) TS_TRY(launch_omegas<T>(opt.seed, S.ob, w.Om, st));
   if (S.kind == TS_TENSORSKETCH) {
     TS_TRY(launch_twiddles<T>(m, w.tw, st));
     TS_TRY(build_ts_tables<T>(X, S, opt.seed, 0, w, st));
     TS_TRY(phase(opt, 2, st));
     TS_TRY(sketch_rhs_all<T>(X, S, w, st));
+    if (S.solve == TS_SOLVE_RSVD)
+      TS_TRY(rhs_times_omegas<T>(X, S, w, 0, opt.resketch_each_sweep ? 1 : S.sweeps, st));
     TS_TRY(phase(opt, 3, st));
   } else {
     TS_TRY(phase(opt, 2, st));
@@ -468,6 +501,7 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
     if (S.kind == TS_TENSORSKETCH && opt.resketch_each_sweep && sweep > 0) {
       TS_TRY(build_ts_tables<T>(X, S, opt.seed, sweep, w, st));
       TS_TRY(sketch_rhs_all<T>(X, S, w, st));
+      if (S.solve == TS_SOLVE_RSVD) TS_TRY(rhs_times_omegas<T>(X, S, w, sweep, 1, st));
     }
     for (int n = 0; n < N; ++n) {
       const T* Yn;
@@ -492,9 +526,16 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
       map.order = N;
       map.n = n;
       for (int k = 0; k < N; ++k) map.ranks[k] = S.ranks[k];
-      const T* Om = w.Om ? w.Om + S.om_sweep * sweep + S.om_off[n] : nullptr;
+      const long ldo = (long)S.sweeps * S.kc[n];
+      const T* Om = w.Om ? w.Om + S.ob.off[n] + (size_t)sweep * S.kc[n] : nullptr;
+      MatView<T> yv{};
+      const MatView<T>* yom = nullptr;
+      if (w.YOm) {
+        yv = mv<T>(w.YOm + S.yom_off[n] + (size_t)sweep * S.kc[n], ldo, 1);
+        yom = &yv;
+      }
       TS_TRY(solve_subproblem<T>(m, S.r[n], (int)X.dims[n], S.ranks[n], S.solve, S.kc[n],
-                                 S.fp64solve, Om, Yn, w, factors[n], core, map, st));
+                                 S.fp64solve, Om, ldo, yom, Yn, w, factors[n], core, map, st));
     }
     if (residual_out && opt.track_fit)
       TS_TRY(launch_fit_dense<T>(X, S.ranks, core, (const T* const*)factors, w.fitQ, w.fitacc,
@@ -773,10 +814,15 @@ static ts_status lrls_check(int32_t m, int32_t r, int32_t s, int32_t R, int32_t 
     return fail(TS_ERR_SHAPE, "ts_lrls: need 1 <= R <= min(r, s) and r <= m");
   *kc = rsvd_width(R, oversample < 0 ? 5 : oversample, r, s);
   const bool q64 = fp64 && dtype == TS_F32;
-  if (fused_ok(r, s, *kc, R, solve, dtype_size(dtype), q64)) return TS_OK;
-  if (solve == TS_SOLVE_RSVD &&
-      (*kc > kMaxEig || rsvd_stage1_smem_bytes(r, *kc, dtype_size(dtype), q64) > kMaxSmem))
-    return fail(TS_ERR_SHAPE, "ts_lrls: RSVD limits k <= %d and the on-chip footprint", kMaxEig);
+  const size_t tsz = dtype_size(dtype);
+  if (fused_ok(r, s, *kc, R, solve, tsz, q64)) return TS_OK;
+  if (solve == TS_SOLVE_RSVD) {
+    if (*kc > kMaxEig) return fail(TS_ERR_SHAPE, "ts_lrls: RSVD width k=%d > %d", *kc, kMaxEig);
+    if (rsvd_stage1_smem_bytes(r, *kc, tsz, q64) > kMaxSmem &&
+        qr_only_smem_bytes(r, *kc, q64, tsz) > kMaxSmem)
+      return fail(TS_ERR_SHAPE, "ts_lrls: r=%d, k=%d too large for the RSVD solve", r, *kc);
+    return TS_OK;
+  }
   if (solve == TS_SOLVE_EXACT && (r > kMaxEig || chol_solve_smem_bytes(r, dtype_size(dtype)) > kMaxSmem))
     return fail(TS_ERR_SHAPE, "ts_lrls: exact limit r <= %d", kMaxEig);
   return TS_OK;
@@ -792,7 +838,13 @@ static size_t lrls_carve(int m, int r, int s, int R, int solve, int kc, bool fp6
   const int eign = solve == TS_SOLVE_EXACT ? (r > k ? r : k) : k;
   const bool fused = fused_ok(r, s, kc, R, solve, sizeof(T), fp64);
   w.ZW = b.take<T>((size_t)m * (r + k));
-  w.GW = b.take<T>((size_t)r * (r + (fused && s > k ? s : k)));
+  w.GW = b.take<T>((size_t)r * (r + k + (fused ? s : 0)));
+  if (!fused && solve == TS_SOLVE_RSVD && rsvd_stage1_smem_bytes(r, k, sizeof(T), fp64) > kMaxSmem) {
+    w.Ginv = b.take<T>((size_t)r * r);
+    w.NS1 = b.take<T>(2 * (size_t)r * r);
+    w.NS2 = b.take<T>((size_t)r * r);
+    w.Cb = b.take<T>((size_t)r * k);
+  }
   w.Mbuf = fused ? b.take<T>((size_t)(solve == TS_SOLVE_RSVD ? k : r) * s) : nullptr;
   w.Om = b.take<T>((size_t)s * k);
   w.Q = b.take<T>((size_t)r * k);
@@ -819,10 +871,10 @@ static size_t lrls_carve(int m, int r, int s, int R, int solve, int kc, bool fp6
 
 extern "C" size_t ts_lrls_scratch_bytes(int32_t m, int32_t r, int32_t s, int32_t R, int32_t solve,
                                         int32_t oversample, int32_t dtype) {
-  int kc;
-  if (lrls_check(m, r, s, R, dtype, solve, oversample, 1, &kc) != TS_OK) return 0;
   size_t best = 0;
-  for (int f64 = 0; f64 < 2; ++f64) {  // enough for either precision of the solve
+  for (int f64 = 0; f64 < 2; ++f64) {  // enough for either supported precision of the solve
+    int kc;
+    if (lrls_check(m, r, s, R, dtype, solve, oversample, f64, &kc) != TS_OK) continue;
     Bump b;
     if (dtype == TS_F64) {
       Work<double> w;
@@ -833,6 +885,7 @@ extern "C" size_t ts_lrls_scratch_bytes(int32_t m, int32_t r, int32_t s, int32_t
     }
     if (b.off > best) best = b.off;
   }
+  if (best) clear_error();
   return best;
 }
 
@@ -850,7 +903,8 @@ static ts_status lrls_one(int m, int r, int s, int R, int solve, int kc, bool fp
     TS_TRY(launch_gaussian<T>(seed, make_tag(TS_PURPOSE_RSVD_GAUSS, sweep, n, 0), (int64_t)s * kc,
                               1.0, w.Om, st));
   CoreMap none{};
-  return solve_subproblem<T>(m, r, s, R, solve, kc, fp64, w.Om, static_cast<const T*>(Y), w,
+  return solve_subproblem<T>(m, r, s, R, solve, kc, fp64, w.Om, kc, nullptr,
+                             static_cast<const T*>(Y), w,
                              static_cast<T*>(A_out), nullptr, none, st);
 }
 

@@ -69,3 +69,14 @@ def test_host_side_validation_without_gpu(libpath):
     assert L.tucker_als_workspace_bytes(ctypes.byref(d), rk, 0, 50, 1, ctypes.byref(opt),
                                         ctypes.byref(n)) == 0
     assert n.value > 0
+
+
+def test_lrls_scratch_query_covers_every_supported_path(libpath):
+    # Host-only sizing: the on-chip block solve, the Newton-Schulz large-r path (whose FP64
+    # QR variant does not fit one block) and an unsupported shape (k > 64).
+    from paper_2104_01101_gb300 import tsketch
+    L = tsketch.lib()
+    fused = L.ts_lrls_scratch_bytes(2000, 100, 400, 10, 0, 5, 0)
+    large = L.ts_lrls_scratch_bytes(3000, 625, 300, 25, 0, 5, 0)
+    assert fused > 0 and large > 4 * 625 * 625
+    assert L.ts_lrls_scratch_bytes(3000, 625, 300, 70, 0, 5, 0) == 0

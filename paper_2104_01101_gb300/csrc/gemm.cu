@@ -1,9 +1,11 @@
-// Small strided SIMT GEMM for the sketched-system products ([Z^T Z | Z^T Y],
+// Small strided SIMT GEMM for the sketched-system products ([Z^T Z | Z^T Y Omega | Z^T Y],
 // Y Omega, Z E, M^T Y, D D^T, the Init-RRF products ...).  These are tall-skinny
 // products of a few to a hundred MFLOP, latency-bound at the sizes of the method, so
-// the launcher first shrinks the output tile (64x64 -> 32x32) to reach one wave of
-// CTAs and only then splits the long dimension; split partials are summed in split
-// order by a second, fully parallel kernel, so results are deterministic.
+// the launcher picks the output tile (64x64 or 32x32) that comes closest to one wave of
+// CTAs and then splits the long dimension; split partials are summed in split order by
+// a second, fully parallel kernel, so results are deterministic.  Inside a CTA the next
+// K tile is fetched into registers while the current one is multiplied from shared
+// memory, so the global latency of a tile overlaps the arithmetic of the previous one.
 // The B operand may be up to three strided views side by side (columns [0, n1) from
 // B1, [n1, n2) from B2 and [n2, N) from B3), so that Z^T [Z | Y Omega | Y] is one
 // product even though Z is stored column-major and the others row-major.
@@ -12,17 +14,30 @@
 namespace ts {
 
 namespace {
-constexpr int BK = 16, NT = 256;
+constexpr int BK = 32, NT = 256;
 }
 
+// Element (gk, gj) of the three-view B operand (zero outside [0, K) x [0, N)).
+template <typename T>
+__device__ __forceinline__ T b_at(const MatView<T>& B1, int n1, const MatView<T>& B2, int n2,
+                                  const MatView<T>& B3, int N, int kend, int gk, int gj) {
+  if (gj >= N || gk >= kend) return (T)0;
+  if (gj < n1) return B1.p[(long)gk * B1.rs + (long)gj * B1.cs];
+  if (gj < n2) return B2.p[(long)gk * B2.rs + (long)(gj - n1) * B2.cs];
+  return B3.p[(long)gk * B3.rs + (long)(gj - n2) * B3.cs];
+}
+
+// C tile BM x BN over K range [kbeg, kend) of this split.  256 threads as 16 x 16, each
+// owning a TM x TN register tile; As and Bs hold the current K tile (k-major rows).
 template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, MatView<T> A,
                                              MatView<T> B1, int n1, MatView<T> B2, int n2,
                                              MatView<T> B3, T alpha, T beta, OutView<T> C,
                                              T* __restrict__ partial) {
-  constexpr int TM = BM / 16, TN = BN / 16;  // outputs per thread: TM x TN
-  __shared__ T As[BK][BM + 4];
-  __shared__ T Bs[BK][BN + 4];
+  constexpr int TM = BM / 16, TN = BN / 16;         // outputs per thread: TM x TN
+  constexpr int LA = BM * BK / NT, LB = BN * BK / NT;  // tile elements each thread fetches
+  __shared__ __align__(16) T As[BK][BM + 4];
+  __shared__ __align__(16) T Bs[BK][BN + 4];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   const int kbeg = blockIdx.z * kchunk;
@@ -30,32 +45,57 @@ __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, Ma
   const bool a_kfast = (A.cs == 1);
   const MatView<T>& Bv = n0 < n1 ? B1 : (n0 < n2 ? B2 : B3);  // view this tile starts in
   const bool b_kfast = (Bv.rs == 1 && Bv.cs != 1);
+  // fetch mapping (coalesced along the view's contiguous index)
+  auto a_idx = [&](int t, int& i, int& kk) {
+    if (a_kfast) { i = t / BK; kk = t % BK; } else { kk = t / BM; i = t % BM; }
+  };
+  auto b_idx = [&](int t, int& j, int& kk) {
+    if (b_kfast) { j = t / BK; kk = t % BK; } else { kk = t / BN; j = t % BN; }
+  };
+  T ra[LA], rb[LB];
+  auto fetch = [&](int k0) {
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      int i, kk;
+      a_idx(threadIdx.x + u * NT, i, kk);
+      const int gi = m0 + i, gk = k0 + kk;
+      ra[u] = (gi < M && gk < kend) ? A.p[(long)gi * A.rs + (long)gk * A.cs] : (T)0;
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      int j, kk;
+      b_idx(threadIdx.x + u * NT, j, kk);
+      rb[u] = b_at<T>(B1, n1, B2, n2, B3, N, kend, k0 + kk, n0 + j);
+    }
+  };
+  auto stage = [&]() {
+#pragma unroll
+    for (int u = 0; u < LA; ++u) {
+      int i, kk;
+      a_idx(threadIdx.x + u * NT, i, kk);
+      As[kk][i] = ra[u];
+    }
+#pragma unroll
+    for (int u = 0; u < LB; ++u) {
+      int j, kk;
+      b_idx(threadIdx.x + u * NT, j, kk);
+      Bs[kk][j] = rb[u];
+    }
+  };
   T acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
 #pragma unroll
     for (int j = 0; j < TN; ++j) acc[i][j] = 0;
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    for (int t = threadIdx.x; t < BM * BK; t += NT) {
-      int i, kk;
-      if (a_kfast) { i = t / BK; kk = t % BK; } else { kk = t / BM; i = t % BM; }
-      const int gi = m0 + i, gk = k0 + kk;
-      As[kk][i] = (gi < M && gk < kend) ? A.p[(long)gi * A.rs + (long)gk * A.cs] : (T)0;
-    }
-    for (int t = threadIdx.x; t < BN * BK; t += NT) {
-      int j, kk;
-      if (b_kfast) { j = t / BK; kk = t % BK; } else { kk = t / BN; j = t % BN; }
-      const int gj = n0 + j, gk = k0 + kk;
-      T v = 0;
-      if (gj < N && gk < kend) {
-        if (gj < n1) v = B1.p[(long)gk * B1.rs + (long)gj * B1.cs];
-        else if (gj < n2) v = B2.p[(long)gk * B2.rs + (long)(gj - n1) * B2.cs];
-        else v = B3.p[(long)gk * B3.rs + (long)(gj - n2) * B3.cs];
-      }
-      Bs[kk][j] = v;
-    }
+  if (kbeg < kend) {
+    fetch(kbeg);
+    stage();
     __syncthreads();
-#pragma unroll
+  }
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+    const bool more = k0 + BK < kend;
+    if (more) fetch(k0 + BK);  // in flight during the products below
+#pragma unroll 8
     for (int kk = 0; kk < BK; ++kk) {
       T a[TM], b[TN];
 #pragma unroll
@@ -68,6 +108,10 @@ __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, Ma
         for (int j = 0; j < TN; ++j) acc[i][j] += a[i] * b[j];
     }
     __syncthreads();
+    if (more) {
+      stage();
+      __syncthreads();
+    }
   }
   const size_t MN = (size_t)M * N;
 #pragma unroll
@@ -107,16 +151,17 @@ ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
                 MatView<T> B2, int n2, MatView<T> B3, double beta, OutView<T> C,
                 const GemmSplit<T>* split, cudaStream_t st) {
   if (M <= 0 || N <= 0) return TS_OK;
-  constexpr int kWave = 2 * 152;
+  constexpr int kWave = 152;
   const int tiles64 = ceil_div(M, 64) * ceil_div(N, 64);
   const int tiles32 = ceil_div(M, 32) * ceil_div(N, 32);
-  const bool small = tiles64 < kWave;
+  // 64x64 tiles when they alone, or split along K, can fill about a wave; else 32x32
+  const bool small = tiles64 * ceil_div(K > 0 ? K : 1, 4 * BK) < kWave;
   const int tiles = small ? tiles32 : tiles64;
   const int bm = small ? 32 : 64;
   int splits = 1;
-  if (split && split->partial && tiles < kWave / 2 && K > 8 * BK) {
-    splits = kWave / tiles;
-    if (splits > ceil_div(K, 8 * BK)) splits = ceil_div(K, 8 * BK);
+  if (split && split->partial && tiles < kWave && K > 4 * BK) {
+    splits = ceil_div(kWave, tiles);
+    if (splits > ceil_div(K, 4 * BK)) splits = ceil_div(K, 4 * BK);
     if (splits > 32) splits = 32;
     const size_t cap = split->partial_elems / ((size_t)M * N);
     if ((size_t)splits > cap) splits = (int)cap;

@@ -12,9 +12,9 @@
 //   2. RSVD: Q = qr(C) by Householder reflections with warp c owning column c (one
 //      barrier per reflector, then each warp forms its own column of Q); E = G^{-1} Q;
 //      D = E^T H (= Q^T G^{-1} Z^T Y, k x s); K = D D^T.   Exact: M = X, K = X X^T.
-//   3. K = U Lambda U^T by cyclic Jacobi with the whole block (round-robin pairs applied
-//      as one two-sided 2 x 2 block update per round; relative stopping rule with a
-//      rounding floor), optionally polished by FP64 sweeps on V^T K V, K formed in FP64.
+//   3. K = U Lambda U^T by cyclic Jacobi with the whole block (round-robin pairs; each
+//      round's rotations applied as one two-sided 2 x 2 block update; relative stopping
+//      rule with a rounding floor), optionally polished by FP64 sweeps on V^T K V.
 //   4. CnT = Q U_R Sigma_R (Q = I for exact), A = M^T U_R Sigma_R^{-1}, canonical column
 //      signs (largest-magnitude entry of each column of A positive, lowest index on ties)
 //      and C_(n)^T scattered into the core.
@@ -35,8 +35,8 @@ __host__ __device__ inline int quad_ld(int n) { return (n + 3) & ~3; }
 // Shared-memory layout (byte offsets).  T = data type, U = QR type.
 struct FusedLayout {
   int naug, lda, kq, ke, n;
-  size_t A, P0, P1, rowold, colbuf, QA, Qo, Qt, tau, E, M, Kk, Kk2, Vk, Am, Fm, CnTs, K64, K64b,
-      V64, KV64, sched, total;
+  size_t A, P0, P1, rowold, colbuf, QA, Qo, Qt, tau, E, M, Kk, Vk, Am, Fm, CnTs, K64, V64, KV64,
+      sched, total;
 };
 
 __host__ __device__ inline FusedLayout fused_layout(int r, int s, int k, int R, int solve,
@@ -69,13 +69,11 @@ __host__ __device__ inline FusedLayout fused_layout(int r, int s, int k, int R, 
   L.E = take(rsvd ? tsz * (size_t)r * L.ke : 0);
   L.M = take(rsvd && m_smem ? tsz * (size_t)k * s : 0);
   L.Kk = take(tsz * (size_t)L.n * L.n);
-  L.Kk2 = take(tsz * (size_t)L.n * L.n);
   L.Vk = take(tsz * (size_t)L.n * L.n);
   L.Am = take(m_smem ? tsz * (size_t)s * R : 0);
   L.Fm = take(tsz * (size_t)L.n * R);
   L.CnTs = take(tsz * (size_t)r * R);
   L.K64 = take(polish ? 8 * (size_t)L.n * L.n : 0);
-  L.K64b = take(polish ? 8 * (size_t)L.n * L.n : 0);
   L.V64 = take(polish ? 8 * (size_t)L.n * L.n : 0);
   L.KV64 = take(polish ? 8 * (size_t)L.n * L.n : 0);
   const int np = (L.n + 1) & ~1;
@@ -102,59 +100,31 @@ __device__ __forceinline__ void load4(const double* p, double (&v)[4]) {
 
 // ---------------------------------------------------------------- Gauss-Jordan
 
-// In-place inverse of the 16 x 16 SPD block B (row stride kPs, shared memory) by one
-// warp: Gauss-Jordan with 2 x 2 pivot blocks (8 steps; the inverse of a 2 x 2 block is
-// closed-form).  Lane l updates row (l & 15), columns 8 (l >> 4) .. 8 (l >> 4) + 7.  A
-// pivot block that is not positive definite (or not finite) sets *flag and is replaced
-// by the identity.
+// Inverse of a 16 x 16 SPD block held in registers by one warp: lane l owns row (l & 15),
+// columns 8 (l >> 4) .. 8 (l >> 4) + 7.  Gauss-Jordan without pivoting, pivot row and
+// column exchanged by shuffles; a non-positive or non-finite pivot sets *flag and is
+// replaced by 1.
 template <typename T>
-__device__ void warp_inverse_block(T* B, int* flag) {
-  const int lane = threadIdx.x & 31, i = lane & 15, j0 = 8 * (lane >> 4);
-#pragma unroll 1
-  for (int q = 0; q < kPb; q += 2) {
-    const T a = B[q * kPs + q], b = B[q * kPs + q + 1];
-    const T c = B[(q + 1) * kPs + q], d = B[(q + 1) * kPs + q + 1];
-    T det = a * d - b * c;
-    T e00, e01, e10, e11;
-    if (a > (T)0 && det > (T)0 && isfinite(det)) {
-      const T id = (T)1 / det;
-      e00 = d * id;
-      e01 = -b * id;
-      e10 = -c * id;
-      e11 = a * id;
-    } else {
+__device__ __forceinline__ void warp_inverse16(T (&a)[8], int* flag) {
+  const int lane = threadIdx.x & 31, i = lane & 15, h = lane >> 4;
+#pragma unroll
+  for (int q = 0; q < kPb; ++q) {
+    T piv = __shfl_sync(kFull, a[q & 7], q + 16 * (q >> 3));
+    if (!(piv > (T)0) || !isfinite(piv)) {
       if (lane == 0 && flag) atomicExch(flag, 1);
-      e00 = e11 = (T)1;
-      e01 = e10 = (T)0;
+      piv = (T)1;
     }
-    T y0[8], y1[8], x[8];
-    load4(B + q * kPs + j0, *reinterpret_cast<T(*)[4]>(y0));
-    load4(B + q * kPs + j0 + 4, *reinterpret_cast<T(*)[4]>(y0 + 4));
-    load4(B + (q + 1) * kPs + j0, *reinterpret_cast<T(*)[4]>(y1));
-    load4(B + (q + 1) * kPs + j0 + 4, *reinterpret_cast<T(*)[4]>(y1 + 4));
-    load4(B + i * kPs + j0, *reinterpret_cast<T(*)[4]>(x));
-    load4(B + i * kPs + j0 + 4, *reinterpret_cast<T(*)[4]>(x + 4));
-    const T x0 = B[i * kPs + q], x1 = B[i * kPs + q + 1];
-    __syncwarp();
-    const bool prow = (i == q) || (i == q + 1);
-    const T r0 = i == q ? e00 : e10, r1 = i == q ? e01 : e11;  // row of the pivot inverse
-    const T f0 = x0 * e00 + x1 * e10, f1 = x0 * e01 + x1 * e11;  // (A21 P^{-1}) of row i
+    const T inv = (T)1 / piv;
+    const T f = __shfl_sync(kFull, a[q & 7], i + 16 * (q >> 3)) * inv;
+    T aq[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) aq[t] = __shfl_sync(kFull, a[t], q + 16 * h);
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
-      const int j = j0 + t;
-      T v;
-      if (prow) {
-        if (j == q) v = r0;
-        else if (j == q + 1) v = r1;
-        else v = r0 * y0[t] + r1 * y1[t];
-      } else {
-        if (j == q) v = -f0;
-        else if (j == q + 1) v = -f1;
-        else v = x[t] - f0 * y0[t] - f1 * y1[t];
-      }
-      B[i * kPs + j] = v;
+      const bool colq = (h == (q >> 3)) && (t == (q & 7));
+      if (i == q) a[t] = colq ? inv : aq[t] * inv;
+      else a[t] = colq ? -f : a[t] - f * aq[t];
     }
-    __syncwarp();
   }
 }
 
@@ -226,13 +196,15 @@ __device__ void gauss_jordan(T* A, int r, int ncol, int lda, T* P0, T* P1, T* ro
   const int li = lane & 15, lh = lane >> 4;
   if (warp == 0) {
     const int nb = min(kPb, r);
+    T a8[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int j = lh * 8 + t;
-      P0[li * kPs + j] = (li < nb && j < nb) ? A[li * lda + j] : (li == j ? (T)1 : (T)0);
+      a8[t] = (li < nb && j < nb) ? A[li * lda + j] : (li == j ? (T)1 : (T)0);
     }
-    __syncwarp();
-    warp_inverse_block<T>(P0, flag);
+    warp_inverse16<T>(a8, flag);
+#pragma unroll
+    for (int t = 0; t < 8; ++t) P0[li * kPs + lh * 8 + t] = a8[t];
   }
   __syncthreads();
   const int nc64 = (ncol + 63) / 64, nitems = ((r + 7) / 8) * nc64;
@@ -265,7 +237,8 @@ __device__ void gauss_jordan(T* A, int r, int ncol, int lda, T* P0, T* P1, T* ro
 #pragma unroll
         for (int u = 0; u < kPb; u += 4)
           load4(colbuf + i * kPs + u, *reinterpret_cast<T(*)[4]>(ci + u));
-#pragma unroll 1
+        T a8[8];
+#pragma unroll
         for (int t = 0; t < 8; ++t) {
           const int jl = lh * 8 + t;
           T v = (li == jl) ? (T)1 : (T)0;
@@ -275,10 +248,11 @@ __device__ void gauss_jordan(T* A, int r, int ncol, int lda, T* P0, T* P1, T* ro
 #pragma unroll
             for (int u = 0; u < kPb; ++u) v += ci[u] * rowold[u * lda + j];
           }
-          Pn[li * kPs + jl] = v;
+          a8[t] = v;
         }
-        __syncwarp();
-        warp_inverse_block<T>(Pn, flag);
+        warp_inverse16<T>(a8, flag);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) Pn[li * kPs + lh * 8 + t] = a8[t];
       }
     } else if ((warp & 3) != 0) {
       // The update runs on the warps of the other three SM sub-partitions (warp w on
@@ -382,6 +356,8 @@ __device__ __forceinline__ float unit_rsqrt(float x) {
   return r * (1.5f - 0.5f * x * r * r);
 }
 __device__ __forceinline__ double unit_rsqrt(double x) { return 1.0 / sqrt(x); }
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
 
 // Rotation of pair pq (packed as in jacobi_schedule) for the current matrix A: J =
 // [[c, s], [-s, c]] on (p, q) makes (J^T A J)(p, q) zero; identity (rot = false) when
@@ -397,25 +373,29 @@ __device__ __forceinline__ void jacobi_rotation(const U* A, int n, int pq, U tol
   if (q < 0) return;
   const U apq = A[p * n + q], app = A[p * n + p], aqq = A[q * n + q];
   if (apq * apq > tol2 * fabs(app * aqq) && fabs(apq) > floor_abs) {
+    // t = sign(theta) / (|theta| + sqrt(theta^2 + 1)); its rounding only perturbs the angle,
+    // while c = (1 + t^2)^(-1/2) to working precision keeps the rotation orthogonal
     const U theta = fast_div(aqq - app, 2 * apq);
-    const U tt = fast_div(theta >= (U)0 ? (U)1 : (U)-1, fabs(theta) + sqrt(theta * theta + 1));
+    const U h = theta * theta + 1;
+    const U tt = fast_div(theta >= (U)0 ? (U)1 : (U)-1, fabs(theta) + h * fast_rsqrt(h));
     c = unit_rsqrt(tt * tt + 1);
     s = tt * c;
     rot = true;
   }
 }
 
-// Cyclic Jacobi by the whole block on the symmetric n x n matrix in A (row stride n,
-// n <= 64), double-buffered with A2; V (n x n) accumulates the rotations onto its start
-// basis.  In each round every thread derives the rotations it needs from the current
-// buffer and writes its 2 x 2 blocks of J^T A J into the other one (blocks of the
-// round's disjoint pairs), or its entries of V J: one barrier per round.  A pair rotates
-// when |a_pq| exceeds both tol sqrt(|a_pp a_qq|) (relative accuracy) and
+// Cyclic Jacobi by the whole block on the symmetric n x n matrix A (row stride n,
+// n <= 64); V (n x n) accumulates the rotations onto its start basis.  A round: one
+// thread per pair computes the rotation (J = [[c, s], [-s, c]] on (p, q)), then every
+// thread applies them to the items it owns for the whole run -- 2 x 2 blocks (pair i,
+// pair j) of J^T A J, or pairs (row l, pair j) of V J -- two barriers per round.  A pair
+// rotates when |a_pq| exceeds both tol sqrt(|a_pp a_qq|) (relative accuracy) and
 // floor_rel max_i |a_ii| (the rounding level of A itself); the loop ends after a sweep
-// without rotations or after max_sweeps.  Returns the buffer holding the result.
+// without rotations or after max_sweeps.  pp, qq, cs, sn hold n/2 + 1 entries.
 template <typename U>
-__device__ U* block_jacobi(U* A, U* A2, U* V, int n, U tol, U floor_rel, int max_sweeps,
-                           const int* sched, int* flags, U* red) {
+__device__ void block_jacobi(U* A, U* V, int n, U tol, U floor_rel, int max_sweeps,
+                             const int* sched, int* pp, int* qq, U* cs, U* sn, int* flags,
+                             U* red) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int np = (n + 1) & ~1, npairs = np >> 1, nrounds = np - 1;
   if (tid < 32) {
@@ -432,53 +412,50 @@ __device__ U* block_jacobi(U* A, U* A2, U* V, int n, U tol, U floor_rel, int max
   __syncthreads();
   const U floor_abs = floor_rel * red[0], tol2 = tol * tol;
   const int nblk = npairs * npairs, nitems = nblk + n * npairs;
-  U* Ao = A;
-  U* An = A2;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int t = 0; t < nrounds; ++t) {
-      const int* sc = sched + t * npairs;
-      for (int e = tid; e < nitems; e += nthr) {
-        if (e < nblk) {
-          const int i = e / npairs, j = e - i * npairs;
-          int p1, q1, p2, q2;
-          U c1, s1, c2, s2;
-          bool r1, r2;
-          jacobi_rotation<U>(Ao, n, sc[i], tol2, floor_abs, p1, q1, c1, s1, r1);
-          jacobi_rotation<U>(Ao, n, sc[j], tol2, floor_abs, p2, q2, c2, s2, r2);
-          if (r1 || r2) flags[sweep & 1] = 1;
-          const U b00 = Ao[p1 * n + p2];
-          const U b01 = q2 >= 0 ? Ao[p1 * n + q2] : (U)0;
-          const U b10 = q1 >= 0 ? Ao[q1 * n + p2] : (U)0;
-          const U b11 = (q1 >= 0 && q2 >= 0) ? Ao[q1 * n + q2] : (U)0;
-          const U t00 = c1 * b00 - s1 * b10, t01 = c1 * b01 - s1 * b11;
-          const U t10 = s1 * b00 + c1 * b10, t11 = s1 * b01 + c1 * b11;
-          An[p1 * n + p2] = c2 * t00 - s2 * t01;
-          if (q2 >= 0) An[p1 * n + q2] = s2 * t00 + c2 * t01;
-          if (q1 >= 0) An[q1 * n + p2] = c2 * t10 - s2 * t11;
-          if (q1 >= 0 && q2 >= 0) An[q1 * n + q2] = s2 * t10 + c2 * t11;
-        } else {
-          const int f = e - nblk;
-          const int l = f / npairs, i = f - l * npairs;
-          int p, q;
-          U c, s;
-          bool rot;
-          jacobi_rotation<U>(Ao, n, sc[i], tol2, floor_abs, p, q, c, s, rot);
-          if (rot) {
-            const U vp = V[l * n + p], vq = V[l * n + q];
-            V[l * n + p] = c * vp - s * vq;
-            V[l * n + q] = s * vp + c * vq;
-          }
-        }
+      if (tid < npairs) {
+        int p, q;
+        U c, s;
+        bool rot;
+        jacobi_rotation<U>(A, n, sched[t * npairs + tid], tol2, floor_abs, p, q, c, s, rot);
+        pp[tid] = p;
+        qq[tid] = q;
+        cs[tid] = c;
+        sn[tid] = s;
+        if (rot) flags[sweep & 1] = 1;
       }
-      U* tmp = Ao;
-      Ao = An;
-      An = tmp;
       __syncthreads();
       if (t == 0 && tid == 0) flags[(sweep + 1) & 1] = 0;
+      for (int e = tid; e < nitems; e += nthr) {
+        const bool blk = e < nblk;
+        const int f = blk ? e : e - nblk;
+        const int i = f / npairs, j = f - i * npairs;  // blocks: (pair i, pair j); V: (row i, pair j)
+        const int p2 = pp[j], q2 = qq[j];
+        const U c2 = cs[j], s2 = sn[j];
+        if (blk) {
+          const int p1 = pp[i], q1 = qq[i];
+          const U c1 = cs[i], s1 = sn[i];
+          const U b00 = A[p1 * n + p2];
+          const U b01 = q2 >= 0 ? A[p1 * n + q2] : (U)0;
+          const U b10 = q1 >= 0 ? A[q1 * n + p2] : (U)0;
+          const U b11 = (q1 >= 0 && q2 >= 0) ? A[q1 * n + q2] : (U)0;
+          const U t00 = c1 * b00 - s1 * b10, t01 = c1 * b01 - s1 * b11;
+          const U t10 = s1 * b00 + c1 * b10, t11 = s1 * b01 + c1 * b11;
+          A[p1 * n + p2] = c2 * t00 - s2 * t01;
+          if (q2 >= 0) A[p1 * n + q2] = s2 * t00 + c2 * t01;
+          if (q1 >= 0) A[q1 * n + p2] = c2 * t10 - s2 * t11;
+          if (q1 >= 0 && q2 >= 0) A[q1 * n + q2] = s2 * t10 + c2 * t11;
+        } else if (q2 >= 0 && s2 != (U)0) {
+          const U vp = V[i * n + p2], vq = V[i * n + q2];
+          V[i * n + p2] = c2 * vp - s2 * vq;
+          V[i * n + q2] = s2 * vp + c2 * vq;
+        }
+      }
+      __syncthreads();
     }
     if (!flags[sweep & 1]) break;
   }
-  return Ao;
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -504,8 +481,9 @@ struct FusedArgs {
 template <typename T, typename U, bool POLISH64>
 __global__ void __launch_bounds__(kThreads) k_lrls_fused(FusedArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int jflags[2];
-  __shared__ T jred[1];
+  __shared__ int jp[kMaxEig / 2 + 1], jq[kMaxEig / 2 + 1], jflags[2];
+  __shared__ T jc[kMaxEig / 2 + 1], js[kMaxEig / 2 + 1], jred[1];
+  __shared__ double jc64[POLISH64 ? kMaxEig / 2 + 1 : 1], js64[POLISH64 ? kMaxEig / 2 + 1 : 1];
   __shared__ double jred64[1];
   __shared__ int order[kMaxEig];
   __shared__ T sgn[kMaxEig];
@@ -647,8 +625,9 @@ __global__ void __launch_bounds__(kThreads) k_lrls_fused(FusedArgs<T> a) {
   int* sched = reinterpret_cast<int*>(smem_raw + L.sched);
   jacobi_schedule(n, sched);
   __syncthreads();
-  T* Kf = block_jacobi<T>(Kk, reinterpret_cast<T*>(smem_raw + L.Kk2), Vk, n, jacobi_tol<T>(),
-                          jacobi_floor<T>(), 20, sched, jflags, jred);
+  block_jacobi<T>(Kk, Vk, n, jacobi_tol<T>(), jacobi_floor<T>(), 20, sched, jp, jq, jc, js,
+                  jflags, jred);
+  T* Kf = Kk;
   if constexpr (POLISH64) {
     double* K64 = reinterpret_cast<double*>(smem_raw + L.K64);
     double* V64 = reinterpret_cast<double*>(smem_raw + L.V64);
@@ -690,10 +669,9 @@ __global__ void __launch_bounds__(kThreads) k_lrls_fused(FusedArgs<T> a) {
       }
     }
     __syncthreads();
-    const double* Kf64 =
-        block_jacobi<double>(K64, reinterpret_cast<double*>(smem_raw + L.K64b), V64, n,
-                             jacobi_tol<double>(), jacobi_floor<double>(), 10, sched, jflags,
-                             jred64);
+    block_jacobi<double>(K64, V64, n, jacobi_tol<double>(), jacobi_floor<double>(), 10, sched, jp,
+                         jq, jc64, js64, jflags, jred64);
+    const double* Kf64 = K64;
     for (int e = tid; e < n * n; e += nthr) Vk[e] = (T)V64[e];
     if (tid < n) Kf[tid * n + tid] = (T)Kf64[tid * n + tid];
     __syncthreads();

@@ -1,17 +1,21 @@
-// One-pass sketch of a dense order-3 FP32 tensor (Alg. 4, right-hand sides) at
-// HBM speed.  Every output Y_n[b, i_n] gathers ~s^2/m entries from all over the
-// tensor, so no CTA can own an output row; the kernel therefore reads the tensor
-// once in TB2 x TB3 tiles (TMA tensor loads into a multi-stage shared-memory ring)
-// and pushes each tile's contributions to the L2-resident sketches with TMA bulk
-// reductions of whole tile rows:
-//   mode 3  Y3[H31(i1) + H32(i2), i3-range] += S(i1,i2) * T[i1, i2, i3-range]   (tile rows)
-//   mode 2  Y2[H21(i1) + H23(i3), i2-range] += S(i1,i3) * T[i1, i2-range, i3]   (tile columns,
-//           transposed and signed in shared memory first)
-//   mode 1  Y1[H12(i2) + H13(i3), i1]       += S(i2,i3) * T[i1, i2, i3]         (shared-memory
-//           buckets of the current slice i1, flushed when i1 changes)
-// A CTA walks a contiguous range of tiles (slice-major), so a slice's mode-1 buckets
-// are flushed at most twice per CTA.  All waits are bounded: on a timeout the kernel
-// records TS_ERR_TIMEOUT in the caller's flag, drains its own bulk operations and exits.
+// One-pass sketch of a dense order-3 FP32 tensor (Alg. 4, right-hand sides; the
+// composite sketch of Init-RRF, Sec. 5) at HBM speed.  Every output Y_n[b, i_n]
+// gathers ~s^2/m entries from all over the tensor, so no CTA can own an output row;
+// the kernel reads the tensor once in TB2 x TB3 tiles and sends each entry's
+// contributions to the L2-resident sketches:
+//   mode 3  Y3[H31(i1) + H32(i2), i3]  += S(i1,i2) T[i1,i2,i3]   (vector reductions of
+//           4 consecutive i3 straight from registers)
+//   mode 2  Y2[H21(i1) + H23(i3), i2]  += S(i1,i3) T[i1,i2,i3]   (4 consecutive i2 after a
+//           transpose of the 16 x 16 micro-block in per-warp shared memory)
+//   mode 1  Y1[H12(i2) + H13(i3), i1]  += S(i2,i3) T[i1,i2,i3]   (shared-memory buckets of
+//           the current slice i1, double-buffered, flushed when i1 changes)
+// Warp roles: one producer warp streams tiles with TMA tensor loads into a ring of
+// shared-memory stages (full / empty mbarriers); the consumer warps split every tile
+// into 16 x 16 micro-blocks.  A CTA walks a contiguous, slice-major range of tiles, so
+// a slice's buckets are flushed at most twice per CTA.  Every wait is bounded by time:
+// on expiry the kernel records TS_ERR_TIMEOUT in the caller's flag, the warps fall
+// through the remaining tiles without computing (so the consumer barriers stay
+// matched), and the producer waits, again bounded, for its loads in flight.
 #include <cuda.h>
 
 #include "internal.cuh"
@@ -19,15 +23,18 @@
 namespace ts {
 
 namespace {
-constexpr int kStages = 3;
-constexpr int kThreads = 256;
-constexpr unsigned kSpinLimit = 1u << 24;
+constexpr int kConsumers = 16;  // consumer warps
+constexpr int kThreads = 32 * (kConsumers + 1);
+constexpr int kMaxStages = 6;
+constexpr int kTrs = 20;  // row stride of the transposed micro-block (16-byte rows)
+constexpr unsigned long long kWaitNs = 200ull * 1000 * 1000;  // 200 ms per wait
 }  // namespace
 
 struct Dense3Sketch {
   int s1, s2, s3;
   int TB2, TB3;            // tile rows (mode 2) and columns (mode 3)
   int tiles2, tiles3;      // tiles per slice along modes 2 and 3
+  int stages;
   long ntiles;
   float* Y1; int m1; const int32_t* t12; const int32_t* t13;   // Y1 may be null
   float* Y2; int m2; const int32_t* t21; const int32_t* t23;   // Y2 may be null
@@ -39,19 +46,35 @@ __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try(unsigned mbar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for the phase of the given parity to complete; false after kWaitNs.
 __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity) {
-  for (unsigned it = 0; it < kSpinLimit; ++it) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(mbar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
+  if (mbar_try(mbar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try(mbar, parity))
+    if (global_ns() - t0 > kWaitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_tile(const CUtensorMap* map, unsigned dst, unsigned mbar,
@@ -65,19 +88,11 @@ __device__ __forceinline__ void tma_load_tile(const CUtensorMap* map, unsigned d
       : "memory");
 }
 
-__device__ __forceinline__ void bulk_reduce_add(float* gdst, unsigned ssrc, unsigned bytes) {
-  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(
-                   gdst),
-               "r"(ssrc), "r"(bytes)
+// Y[0..3] += v[0..3] in L2 (16-byte aligned address).
+__device__ __forceinline__ void red_add4(float* p, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c),
+               "f"(d)
                : "memory");
-}
-
-// Row stride of the transposed tile: a multiple of 4 floats (16-byte aligned rows for
-// the bulk reductions) with stride/4 odd, so that a warp's 8 x 4 store pattern covers
-// all 32 banks.
-__host__ __device__ __forceinline__ int transposed_stride(int TB2) {
-  const int l = TB2 + 4;
-  return ((l / 4) & 1) ? l : l + 4;
 }
 
 __device__ __forceinline__ int add_mod(int a, int b, int m) {
@@ -85,173 +100,253 @@ __device__ __forceinline__ int add_mod(int a, int b, int m) {
   return s >= m ? s - m : s;
 }
 
+// Flip the sign of x when the sign bit of s is set.
+__device__ __forceinline__ float apply_sign(float x, int s) {
+  return __int_as_float(__float_as_int(x) ^ (s & (int)0x80000000));
+}
+
+// Byte offsets of the dynamic shared memory (16-byte aligned sections).
+struct SmemLayout {
+  size_t acc1, rowtab, coltab, scratch, total;
+};
+__host__ __device__ inline SmemLayout smem_layout(int stages, int tile_elems, int m1, int rows,
+                                                  int cols) {
+  auto up16 = [](size_t x) { return (x + 15) & ~(size_t)15; };
+  SmemLayout L;
+  L.acc1 = (size_t)stages * tile_elems * sizeof(float);
+  L.rowtab = up16(L.acc1 + 2 * (size_t)m1 * sizeof(float));
+  L.coltab = up16(L.rowtab + (size_t)rows * sizeof(int2));
+  L.scratch = up16(L.coltab + (size_t)cols * sizeof(int2));
+  L.total = L.scratch + (size_t)kConsumers * 16 * kTrs * sizeof(float);
+  return L;
+}
+
 __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_constant__ CUtensorMap tmap,
                                                                  Dense3Sketch d) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const int TB2 = d.TB2, TB3 = d.TB3;
+  __shared__ __align__(8) unsigned long long full_bar[kMaxStages], empty_bar[kMaxStages];
+  __shared__ int abort_flag;
+  const int TB2 = d.TB2, TB3 = d.TB3, S = d.stages;
   const int tile_elems = TB2 * TB3;
-  const int ldt = transposed_stride(TB2);
-  // layout: stages | 2 transposed tiles | mode-1 buckets | tables
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // layout: stages | mode-1 buckets (2 x m1) | row table | column table | scratch
+  const int m1b = d.Y1 ? d.m1 : 0;
+  const SmemLayout L = smem_layout(S, tile_elems, m1b, d.tiles2 * TB2, d.tiles3 * TB3);
   float* stage = reinterpret_cast<float*>(smem_raw);
-  float* tbuf = stage + kStages * tile_elems;
-  float* acc1 = tbuf + 2 * TB3 * ldt;
-  int* h12 = reinterpret_cast<int*>(acc1 + (d.Y1 ? d.m1 : 0));
-  int* h13 = h12 + d.s2;
-  int* h23 = h13 + d.s3;
-  int* h32 = h23 + d.s3;
-  __shared__ __align__(8) unsigned long long mbar[kStages];
-  __shared__ int timed_out;
+  float* acc1 = reinterpret_cast<float*>(smem_raw + L.acc1);
+  int2* rowtab = reinterpret_cast<int2*>(smem_raw + L.rowtab);  // {H12, H32} per i2 (reduced)
+  int2* coltab = reinterpret_cast<int2*>(smem_raw + L.coltab);  // {H13, H23} per i3 (reduced)
+  float* scratch = reinterpret_cast<float*>(smem_raw + L.scratch);
 
-  // contiguous tile range of this CTA
   const long per = (d.ntiles + gridDim.x - 1) / gridDim.x;
   const long t_begin = blockIdx.x * per;
   const long t_end = min(d.ntiles, t_begin + per);
   if (t_begin >= t_end) return;
+  const int ntl = (int)(t_end - t_begin);
   const int tiles_per_slice = d.tiles2 * d.tiles3;
 
-  // tables with buckets already reduced modulo their sketch size
+  // hash tables with buckets reduced modulo their sketch size; padding entries are zero
   auto reduced = [](int32_t e, int m) { return (int)(entry_bin(e) % m) | (e & (int)0x80000000); };
-  for (int i = threadIdx.x; i < d.s2; i += blockDim.x) {
-    if (d.Y1) h12[i] = reduced(d.t12[i], d.m1);
-    if (d.Y3) h32[i] = reduced(d.t32[i], d.m3);
+  for (int i = tid; i < d.tiles2 * TB2; i += blockDim.x) {
+    int2 v = make_int2(0, 0);
+    if (i < d.s2) {
+      if (d.Y1) v.x = reduced(d.t12[i], d.m1);
+      if (d.Y3) v.y = reduced(d.t32[i], d.m3);
+    }
+    rowtab[i] = v;
   }
-  for (int i = threadIdx.x; i < d.s3; i += blockDim.x) {
-    if (d.Y1) h13[i] = reduced(d.t13[i], d.m1);
-    if (d.Y2) h23[i] = reduced(d.t23[i], d.m2);
+  for (int i = tid; i < d.tiles3 * TB3; i += blockDim.x) {
+    int2 v = make_int2(0, 0);
+    if (i < d.s3) {
+      if (d.Y1) v.x = reduced(d.t13[i], d.m1);
+      if (d.Y2) v.y = reduced(d.t23[i], d.m2);
+    }
+    coltab[i] = v;
   }
-  if (d.Y1)
-    for (int i = threadIdx.x; i < d.m1; i += blockDim.x) acc1[i] = 0.f;
-  if (threadIdx.x == 0) {
-    timed_out = 0;
-    for (int s = 0; s < kStages; ++s)
-      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar[s])) : "memory");
+  for (int i = tid; i < 2 * m1b; i += blockDim.x) acc1[i] = 0.f;
+  if (tid == 0) {
+    abort_flag = 0;
+    for (int s = 0; s < S; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty_bar[s])),
+                   "r"(kConsumers)
+                   : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
 
-  const unsigned tile_bytes = (unsigned)tile_elems * 4u;
   auto coords = [&](long t, int& i1, int& r0, int& c0) {
     i1 = (int)(t / tiles_per_slice);
-    const int w = (int)(t % tiles_per_slice);
+    const int w = (int)(t - (long)i1 * tiles_per_slice);
     r0 = (w / d.tiles3) * TB2;
-    c0 = (w % d.tiles3) * TB3;
+    c0 = (w - (w / d.tiles3) * d.tiles3) * TB3;
   };
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < kStages - 1; ++s) {
-      const long t = t_begin + s;
-      if (t >= t_end) break;
+
+  if (warp == kConsumers) {
+    // ---------------- producer
+    if (lane == 0) {
+      const unsigned bytes = (unsigned)tile_elems * 4u;
+      int issued = 0;
+      for (int lt = 0; lt < ntl; ++lt) {
+        const int s = lt % S;
+        if (lt >= S && !mbar_wait(smem_u32(&empty_bar[s]), (unsigned)((lt / S - 1) & 1))) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (*(volatile int*)&abort_flag) break;
+        int i1, r0, c0;
+        coords(t_begin + lt, i1, r0, c0);
+        tma_load_tile(&tmap, smem_u32(stage + (size_t)s * tile_elems), smem_u32(&full_bar[s]), c0,
+                      r0, i1, bytes);
+        issued = lt + 1;
+      }
+      // the loads still in flight must land before the block's shared memory goes away
+      for (int lt = max(0, issued - S); lt < issued; ++lt)
+        mbar_wait(smem_u32(&full_bar[lt % S]), (unsigned)((lt / S) & 1));
+    }
+  } else {
+    // ---------------- consumers
+    const int nmb3 = TB3 >> 4, nmb = (TB2 >> 4) * nmb3;  // 16 x 16 micro-blocks per tile
+    float* tr = scratch + warp * 16 * kTrs;
+    const int rq = lane >> 2, cq = lane & 3;  // load: rows rq and rq + 8, columns 4 cq .. +3
+    const int tc = lane & 7, tq = lane >> 3;  // transposed read: column tc (+8), rows 4 tq .. +3
+    int buf = 0;
+    int cur_i1 = (int)(t_begin / tiles_per_slice);
+    bool aborted = false;
+    for (int lt = 0; lt < ntl; ++lt) {
+      const int s = lt % S;
       int i1, r0, c0;
-      coords(t, i1, r0, c0);
-      tma_load_tile(&tmap, smem_u32(stage + s * tile_elems), smem_u32(&mbar[s]), c0, r0, i1,
-                    tile_bytes);
-    }
-  }
-
-  int cur_i1 = -1;
-  unsigned phase_bits = 0;  // parity per stage
-  for (long t = t_begin; t < t_end; ++t) {
-    const int sidx = (int)((t - t_begin) % kStages);
-    float* tile = stage + sidx * tile_elems;
-    float* tb = tbuf + ((t - t_begin) & 1) * TB3 * ldt;
-    int i1, r0, c0;
-    coords(t, i1, r0, c0);
-    const bool ok = mbar_wait(smem_u32(&mbar[sidx]), (phase_bits >> sidx) & 1u);
-    phase_bits ^= 1u << sidx;
-    if (!ok) atomicExch(&timed_out, 1);
-    if (__syncthreads_or(!ok)) break;
-
-    if (d.Y1 && i1 != cur_i1) {  // new slice: flush the previous slice's buckets
-      if (cur_i1 >= 0) {
-        for (int b = threadIdx.x; b < d.m1; b += blockDim.x) {
-          const float v = acc1[b];
+      coords(t_begin + lt, i1, r0, c0);
+      if (d.Y1 && i1 != cur_i1) {  // new slice: flush the previous slice's buckets
+        asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory");
+        float* a = acc1 + buf * m1b;
+        for (int b = tid; b < d.m1; b += kConsumers * 32) {
+          const float v = a[b];
           if (v != 0.f) atomicAdd(d.Y1 + (long)b * d.s1 + cur_i1, v);
-          acc1[b] = 0.f;
+          a[b] = 0.f;
         }
-        __syncthreads();
+        buf ^= 1;
+      }
+      cur_i1 = i1;
+      if (!aborted) {
+        aborted = *(volatile int*)&abort_flag != 0;
+        if (!aborted && !mbar_wait(smem_u32(&full_bar[s]), (unsigned)((lt / S) & 1))) {
+          atomicExch(&abort_flag, 1);
+          aborted = true;
+        }
+      }
+      if (!aborted) {
+        const float* tile = stage + (size_t)s * tile_elems;
+        float* a1 = acc1 + buf * m1b;
+        int h21 = 0, h31 = 0;
+        if (d.Y2) h21 = (int)(entry_bin(d.t21[i1]) % d.m2) | (d.t21[i1] & (int)0x80000000);
+        if (d.Y3) h31 = (int)(entry_bin(d.t31[i1]) % d.m3) | (d.t31[i1] & (int)0x80000000);
+        int mb = (warp - (int)(((long)lt * nmb) % kConsumers) + kConsumers) % kConsumers;
+        for (; mb < nmb; mb += kConsumers) {
+          const int rr0 = (mb / nmb3) * 16, cc0 = (mb - (mb / nmb3) * nmb3) * 16;
+          const int i3 = c0 + cc0 + 4 * cq;
+          float v[2][4];
+          int2 rt[2];
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const float4 x = *reinterpret_cast<const float4*>(tile + (rr0 + rq + 8 * h) * TB3 + cc0 + 4 * cq);
+            v[h][0] = x.x;
+            v[h][1] = x.y;
+            v[h][2] = x.z;
+            v[h][3] = x.w;
+            rt[h] = rowtab[r0 + rr0 + rq + 8 * h];
+          }
+          const int4 ctA = *reinterpret_cast<const int4*>(coltab + i3);      // cols i3, i3+1
+          const int4 ctB = *reinterpret_cast<const int4*>(coltab + i3 + 2);  // cols i3+2, i3+3
+          const int c13[4] = {ctA.x, ctA.z, ctB.x, ctB.z};
+          const int c23[4] = {ctA.y, ctA.w, ctB.y, ctB.w};
+          const bool col_ok = i3 < d.s3;
+          if (d.Y1 && col_ok) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              if (r0 + rr0 + rq + 8 * h >= d.s2) continue;
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                if (v[h][c] == 0.f) continue;
+                const int b = add_mod(entry_bin(rt[h].x), entry_bin(c13[c]), d.m1);
+                atomicAdd(a1 + b, apply_sign(v[h][c], rt[h].x ^ c13[c]));
+              }
+            }
+          }
+          if (d.Y3 && col_ok) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              if (r0 + rr0 + rq + 8 * h >= d.s2) continue;
+              const int sg = h31 ^ rt[h].y;
+              const int b = add_mod(entry_bin(h31), entry_bin(rt[h].y), d.m3);
+              red_add4(d.Y3 + (long)b * d.s3 + i3, apply_sign(v[h][0], sg), apply_sign(v[h][1], sg),
+                       apply_sign(v[h][2], sg), apply_sign(v[h][3], sg));
+            }
+          }
+          if (d.Y2) {
+            // transpose: element (row rq + 8h, column 4 cq + c) to tr[col][row ^ swizzle]
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int c = 0; c < 4; ++c) {
+                const int col = 4 * cq + c, row = rq + 8 * h;
+                tr[col * kTrs + (row ^ ((col >> 3) << 3))] = v[h][c];
+              }
+            __syncwarp();
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+              const int col = tc + 8 * p;
+              const float4 x = *reinterpret_cast<const float4*>(tr + col * kTrs + ((4 * tq) ^ (8 * p)));
+              const int j3 = c0 + cc0 + col, j2 = r0 + rr0 + 4 * tq;
+              if (j3 < d.s3 && j2 < d.s2) {
+                const int e23 = coltab[j3].y;
+                const int sg = h21 ^ e23;
+                const int b = add_mod(entry_bin(h21), entry_bin(e23), d.m2);
+                red_add4(d.Y2 + (long)b * d.s2 + j2, apply_sign(x.x, sg), apply_sign(x.y, sg),
+                         apply_sign(x.z, sg), apply_sign(x.w, sg));
+              }
+            }
+            __syncwarp();
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
+    }
+    if (d.Y1) {
+      asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory");
+      const float* a = acc1 + buf * m1b;
+      for (int b = tid; b < d.m1; b += kConsumers * 32) {
+        const float v = a[b];
+        if (v != 0.f) atomicAdd(d.Y1 + (long)b * d.s1 + cur_i1, v);
       }
     }
-    cur_i1 = i1;
-    // per-element work: mode-1 buckets, transposed+signed copy (mode 2), in-place sign (mode 3)
-    int h21 = 0, h31 = 0;
-    bool n21 = false, n31 = false;
-    if (d.Y2) { const int e = d.t21[i1]; h21 = entry_bin(e) % d.m2; n21 = entry_neg(e); }
-    if (d.Y3) { const int e = d.t31[i1]; h31 = entry_bin(e) % d.m3; n31 = entry_neg(e); }
-    // Micro-blocks of 8 columns x 4 rows per warp instruction: the transposed store
-    // (row stride ldt = TB2 + 4) then hits 32 distinct banks.
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nqc = TB3 / 8, nmb = nqc * (TB2 / 4);
-    for (int mb = warp; mb < nmb; mb += (int)(blockDim.x >> 5)) {
-      const int cc = (mb % nqc) * 8 + (lane >> 2);
-      const int rr = (mb / nqc) * 4 + (lane & 3);
-      const int i2 = r0 + rr, i3 = c0 + cc;
-      const float v = tile[rr * TB3 + cc];
-      if (d.Y1) {
-        const int a = h12[i2], b = h13[i3];
-        const int bin = add_mod(entry_bin(a), entry_bin(b), d.m1);
-        if (v != 0.f) atomicAdd(&acc1[bin], (entry_neg(a) ^ entry_neg(b)) ? -v : v);
-      }
-      if (d.Y2) tb[cc * ldt + rr] = (n21 ^ entry_neg(h23[i3])) ? -v : v;
-      if (d.Y3 && (n31 ^ entry_neg(h32[i2]))) tile[rr * TB3 + cc] = -v;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {  // every lane issues and tracks its own share of the bulk reductions
-      if (d.Y3)
-        for (int rr = lane; rr < TB2; rr += 32) {
-          const int b = add_mod(h31, entry_bin(h32[r0 + rr]), d.m3);
-          bulk_reduce_add(d.Y3 + (long)b * d.s3 + c0, smem_u32(tile + rr * TB3), TB3 * 4u);
-        }
-      if (d.Y2)
-        for (int cc = lane; cc < TB3; cc += 32) {
-          const int b = add_mod(h21, entry_bin(h23[c0 + cc]), d.m2);
-          bulk_reduce_add(d.Y2 + (long)b * d.s2 + r0, smem_u32(tb + cc * ldt), TB2 * 4u);
-        }
-      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-      // the stage refilled next was read by the previous tile's reductions
-      asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory");
-    }
-    __syncwarp();
-    if (threadIdx.x == 0) {
-      const long tn = t + kStages - 1;
-      if (tn < t_end) {
-        const int sn = (int)((tn - t_begin) % kStages);
-        int ni1, nr0, nc0;
-        coords(tn, ni1, nr0, nc0);
-        tma_load_tile(&tmap, smem_u32(stage + sn * tile_elems), smem_u32(&mbar[sn]), nc0, nr0,
-                      ni1, tile_bytes);
-      }
-    }
-    __syncthreads();
   }
-  if ((threadIdx.x >> 5) == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-  if (timed_out) {
-    if (threadIdx.x == 0) {
-      if (d.flag) atomicExch(d.flag, (int)TS_ERR_TIMEOUT);
-      // let the tile loads still in flight land before the block's shared memory goes away
-      for (int s = 0; s < kStages; ++s) mbar_wait(smem_u32(&mbar[s]), (phase_bits >> s) & 1u);
-    }
-    __syncthreads();
-    return;
-  }
-  if (d.Y1 && cur_i1 >= 0) {
-    __syncthreads();
-    for (int b = threadIdx.x; b < d.m1; b += blockDim.x) {
-      const float v = acc1[b];
-      if (v != 0.f) atomicAdd(d.Y1 + (long)b * d.s1 + cur_i1, v);
-    }
-  }
+  __syncthreads();
+  if (tid == 0 && abort_flag && d.flag) atomicExch(d.flag, (int)TS_ERR_TIMEOUT);
 }
 
 // ---------------------------------------------------------------- host side
 
-// Largest divisor of s that is a multiple of `step` and at most `cap` (0 if none).
-static int tile_divisor(long s, int cap, int step) {
-  for (int t = cap - cap % step; t >= step; t -= step)
-    if (s % t == 0) return t;
-  return 0;
+// Tile extent along one mode: a multiple of 16 from the candidates, least padding first,
+// then the larger (extents = 16 mod 32 keep the micro-block loads free of bank conflicts).
+static int tile_extent(long s, const int* cand, int ncand) {
+  int best = 0;
+  long best_pad = 0;
+  for (int i = 0; i < ncand; ++i) {
+    const long pad = ceil_div(s, (long)cand[i]) * cand[i] - s;
+    if (best == 0 || pad < best_pad || (pad == best_pad && cand[i] > best)) {
+      best = cand[i];
+      best_pad = pad;
+    }
+  }
+  return best;
 }
-static int tile_rows(long s2) { return tile_divisor(s2, 80, 4); }
-static int tile_cols(long s3) { return tile_divisor(s3, 80, 8); }
+static const int kRowCand[] = {48, 64, 80, 96, 112};
+static const int kColCand[] = {48, 80, 112};
+static int tile_rows(long s2) { return s2 <= 16 ? 16 : tile_extent(s2, kRowCand, 5); }
+static int tile_cols(long s3) { return s3 <= 16 ? 16 : tile_extent(s3, kColCand, 3); }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                    const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
@@ -276,7 +371,8 @@ static ts_status encode_fn(EncodeTiledFn* out) {
 bool dense3_tma_eligible(const ts_tensor& X, const SketchJob* jobs, int njobs) {
   if (X.format != TS_DENSE || X.dtype != TS_F32 || X.order != 3) return false;
   if (((uintptr_t)X.values & 15) != 0) return false;
-  if (tile_rows(X.dims[1]) == 0 || tile_cols(X.dims[2]) == 0) return false;
+  if (X.dims[1] % 4 != 0 || X.dims[2] % 4 != 0) return false;  // 16-byte rows and reductions
+  if (X.dims[0] >= (1l << 31) || X.dims[1] * X.dims[2] >= (1l << 31)) return false;
   bool seen[3] = {false, false, false};
   for (int j = 0; j < njobs; ++j) {
     const int n = jobs[j].mode;
@@ -287,14 +383,27 @@ bool dense3_tma_eligible(const ts_tensor& X, const SketchJob* jobs, int njobs) {
   return true;
 }
 
-size_t dense3_tma_smem_bytes(const ts_tensor& X, const SketchJob* jobs, int njobs) {
-  const int TB2 = tile_rows(X.dims[1]), TB3 = tile_cols(X.dims[2]);
-  int m1 = 0;
+static int job_m1(const SketchJob* jobs, int njobs) {
   for (int j = 0; j < njobs; ++j)
-    if (jobs[j].mode == 0) m1 = jobs[j].nbins;
-  return sizeof(float) * ((size_t)kStages * TB2 * TB3 + 2 * (size_t)TB3 * transposed_stride(TB2) +
-                          m1) +
-         sizeof(int) * (2 * (size_t)X.dims[1] + 2 * (size_t)X.dims[2]);
+    if (jobs[j].mode == 0) return jobs[j].nbins;
+  return 0;
+}
+
+static SmemLayout layout_for(const ts_tensor& X, const SketchJob* jobs, int njobs, int stages) {
+  const int TB2 = tile_rows(X.dims[1]), TB3 = tile_cols(X.dims[2]);
+  return smem_layout(stages, TB2 * TB3, job_m1(jobs, njobs),
+                     (int)(ceil_div(X.dims[1], (long)TB2) * TB2),
+                     (int)(ceil_div(X.dims[2], (long)TB3) * TB3));
+}
+
+static int pick_stages(const ts_tensor& X, const SketchJob* jobs, int njobs) {
+  int s = kMaxStages;
+  while (s > 2 && layout_for(X, jobs, njobs, s).total + 1024 > kMaxSmem) --s;
+  return s;
+}
+
+size_t dense3_tma_smem_bytes(const ts_tensor& X, const SketchJob* jobs, int njobs) {
+  return layout_for(X, jobs, njobs, pick_stages(X, jobs, njobs)).total;
 }
 
 ts_status launch_dense3_tma(const ts_tensor& X, const SketchJob* jobs, int njobs, int* flag,
@@ -305,9 +414,10 @@ ts_status launch_dense3_tma(const ts_tensor& X, const SketchJob* jobs, int njobs
   d.s3 = (int)X.dims[2];
   d.TB2 = tile_rows(d.s2);
   d.TB3 = tile_cols(d.s3);
-  d.tiles2 = d.s2 / d.TB2;
-  d.tiles3 = d.s3 / d.TB3;
+  d.tiles2 = (int)ceil_div((long)d.s2, (long)d.TB2);
+  d.tiles3 = (int)ceil_div((long)d.s3, (long)d.TB3);
   d.ntiles = (long)d.s1 * d.tiles2 * d.tiles3;
+  d.stages = pick_stages(X, jobs, njobs);
   d.flag = flag;
   for (int j = 0; j < njobs; ++j) {
     const SketchJob& J = jobs[j];

@@ -75,7 +75,7 @@ def test_tensorsketch_apply_matches_explicit_kronecker(ts, dims, ranks, m, dtype
 # ---------------------------------------------------------------- a4 input sketch
 
 @pytest.mark.parametrize("dims,m", [((40, 40, 40), 400), ((13, 7, 11), 50), ((9, 8, 7, 6), 300),
-                                    ((64, 3), 17)])
+                                    ((64, 3), 17), ((50, 100, 172), 300)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_input_sketch_dense(ts, dims, m, dtype):
     T = np.random.default_rng(2).standard_normal(dims)

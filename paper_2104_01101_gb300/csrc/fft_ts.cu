@@ -45,8 +45,9 @@ ts_status launch_twiddles(int m, Cx<T>* tw, cudaStream_t st) {
   return TS_OK;
 }
 
-// In-register DFT of size P (forward).  Radices 2 and 4 are written out; the
-// others sum the P x P DFT directly with twiddles tw[(r q mod P) * m/P].
+// In-register DFT of size P (forward).  Radices 2, 3, 4 and 5 are written out (3 and 5
+// pair v_r with v_{P-r}, whose twiddles are complex conjugates); the others sum the
+// P x P DFT directly with twiddles tw[(r q mod P) * m/P].
 template <typename T, int P>
 __device__ __forceinline__ void dft_small(Cx<T> (&v)[P], const Cx<T>* __restrict__ tw, int mp) {
   if constexpr (P == 2) {
@@ -60,6 +61,30 @@ __device__ __forceinline__ void dft_small(Cx<T> (&v)[P], const Cx<T>* __restrict
     v[2] = csub(a, c);
     v[1] = Cx<T>{b.x + d.y, b.y - d.x};  // b - i d
     v[3] = Cx<T>{b.x - d.y, b.y + d.x};  // b + i d
+  } else if constexpr (P == 3) {
+    // y0 = v0 + t, y1,2 = (v0 - t/2) -/+ i (sqrt(3)/2)(v1 - v2), t = v1 + v2
+    const T h = (T)0.86602540378443865;
+    const Cx<T> t = cadd(v[1], v[2]), dd = csub(v[1], v[2]);
+    const Cx<T> a{v[0].x - (T)0.5 * t.x, v[0].y - (T)0.5 * t.y};
+    const Cx<T> bb{h * dd.x, h * dd.y};
+    v[0] = cadd(v[0], t);
+    v[1] = Cx<T>{a.x + bb.y, a.y - bb.x};
+    v[2] = Cx<T>{a.x - bb.y, a.y + bb.x};
+  } else if constexpr (P == 5) {
+    // pairs v1 +- v4, v2 +- v3 with c1,2 = cos(2 pi / 5, 4 pi / 5), s1,2 = sin(...)
+    const T c1 = (T)0.30901699437494742, c2 = (T)-0.80901699437494742;
+    const T s1 = (T)0.95105651629515357, s2 = (T)0.58778525229247313;
+    const Cx<T> t1 = cadd(v[1], v[4]), t3 = csub(v[1], v[4]);
+    const Cx<T> t2 = cadd(v[2], v[3]), t4 = csub(v[2], v[3]);
+    const Cx<T> a1{v[0].x + c1 * t1.x + c2 * t2.x, v[0].y + c1 * t1.y + c2 * t2.y};
+    const Cx<T> a2{v[0].x + c2 * t1.x + c1 * t2.x, v[0].y + c2 * t1.y + c1 * t2.y};
+    const Cx<T> b1{s1 * t3.x + s2 * t4.x, s1 * t3.y + s2 * t4.y};
+    const Cx<T> b2{s2 * t3.x - s1 * t4.x, s2 * t3.y - s1 * t4.y};
+    v[0] = Cx<T>{v[0].x + t1.x + t2.x, v[0].y + t1.y + t2.y};
+    v[1] = Cx<T>{a1.x + b1.y, a1.y - b1.x};  // a1 - i b1
+    v[4] = Cx<T>{a1.x - b1.y, a1.y + b1.x};  // a1 + i b1
+    v[2] = Cx<T>{a2.x + b2.y, a2.y - b2.x};  // a2 - i b2
+    v[3] = Cx<T>{a2.x - b2.y, a2.y + b2.x};  // a2 + i b2
   } else {
     Cx<T> o[P];
 #pragma unroll
@@ -156,7 +181,7 @@ struct ChainDesc {
 
 // Block b: flat factor columns 2b (real part) and 2b+1 (imaginary part).
 template <typename T>
-__global__ void __launch_bounds__(256) k_factor_spectra(ChainDesc d, FftPlan plan,
+__global__ void __launch_bounds__(512) k_factor_spectra(ChainDesc d, FftPlan plan,
                                                         const Cx<T>* __restrict__ tw,
                                                         Cx<T>* __restrict__ spectra) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -207,7 +232,7 @@ __global__ void __launch_bounds__(256) k_factor_spectra(ChainDesc d, FftPlan pla
 
 // Block b: Z columns 2b and 2b+1 (column multi-index, factor 0 slowest).
 template <typename T>
-__global__ void __launch_bounds__(256) k_hadamard_ifft(ChainDesc d, int ncols, FftPlan plan,
+__global__ void __launch_bounds__(512) k_hadamard_ifft(ChainDesc d, int ncols, FftPlan plan,
                                                        const Cx<T>* __restrict__ tw,
                                                        const Cx<T>* __restrict__ spectra,
                                                        T* __restrict__ Z) {
@@ -275,9 +300,9 @@ ts_status launch_ts_apply(int nf, const T* const* factors, const int64_t* rows, 
   const size_t smem = (2 + plan.stage_tw) * (size_t)m * sizeof(Cx<T>);
   TS_TRY(ensure_dynamic_smem((const void*)k_factor_spectra<T>, smem));
   TS_TRY(ensure_dynamic_smem((const void*)k_hadamard_ifft<T>, smem));
-  k_factor_spectra<T><<<ceil_div(total, 2), 256, smem, st>>>(d, plan, tw, spectra);
+  k_factor_spectra<T><<<ceil_div(total, 2), 512, smem, st>>>(d, plan, tw, spectra);
   TS_LAUNCH_CHECK();
-  k_hadamard_ifft<T><<<ceil_div(ncols, 2), 256, smem, st>>>(d, (int)ncols, plan, tw, spectra, Z);
+  k_hadamard_ifft<T><<<ceil_div(ncols, 2), 512, smem, st>>>(d, (int)ncols, plan, tw, spectra, Z);
   TS_LAUNCH_CHECK();
   return TS_OK;
 }

@@ -23,7 +23,7 @@
 namespace ts {
 
 namespace {
-constexpr int kConsumers = 16;  // consumer warps
+constexpr int kConsumers = 24;  // consumer warps
 constexpr int kThreads = 32 * (kConsumers + 1);
 constexpr int kMaxStages = 6;
 constexpr int kTrs = 20;  // row stride of the transposed micro-block (16-byte rows)
@@ -98,6 +98,11 @@ __device__ __forceinline__ void red_add4(float* p, float a, float b, float c, fl
 __device__ __forceinline__ int add_mod(int a, int b, int m) {
   const int s = a + b;
   return s >= m ? s - m : s;
+}
+
+// *p += v in shared memory, no return value.
+__device__ __forceinline__ void red_shared_add(float* p, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_u32(p)), "f"(v) : "memory");
 }
 
 // Flip the sign of x when the sign bit of s is set.
@@ -211,24 +216,40 @@ __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_con
     float* tr = scratch + warp * 16 * kTrs;
     const int rq = lane >> 2, cq = lane & 3;  // load: rows rq and rq + 8, columns 4 cq .. +3
     const int tc = lane & 7, tq = lane >> 3;  // transposed read: column tc (+8), rows 4 tq .. +3
+    // this lane's transposed-store offsets: element (row rq + 8h, column 4 cq + c) goes to
+    // tr[col][row ^ 8 (col >> 3)]; the XOR keeps the stores and the reads conflict-free
+    int st_off[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int col = 4 * cq + c, row = rq + 8 * h;
+        st_off[h][c] = col * kTrs + (row ^ ((col >> 3) << 3));
+      }
     int buf = 0;
-    int cur_i1 = (int)(t_begin / tiles_per_slice);
+    int cur_i1 = -1, h21 = 0, h31 = 0;
     bool aborted = false;
+    int i1 = (int)(t_begin / tiles_per_slice);
+    int w = (int)(t_begin - (long)i1 * tiles_per_slice);  // tile within the slice
+    int mb0 = warp;  // first micro-block of this warp in the current tile
     for (int lt = 0; lt < ntl; ++lt) {
       const int s = lt % S;
-      int i1, r0, c0;
-      coords(t_begin + lt, i1, r0, c0);
-      if (d.Y1 && i1 != cur_i1) {  // new slice: flush the previous slice's buckets
-        asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory");
-        float* a = acc1 + buf * m1b;
-        for (int b = tid; b < d.m1; b += kConsumers * 32) {
-          const float v = a[b];
-          if (v != 0.f) atomicAdd(d.Y1 + (long)b * d.s1 + cur_i1, v);
-          a[b] = 0.f;
+      const int r0 = (w / d.tiles3) * TB2, c0 = (w - (w / d.tiles3) * d.tiles3) * TB3;
+      if (i1 != cur_i1) {
+        if (d.Y1 && cur_i1 >= 0) {  // new slice: flush the previous slice's buckets
+          asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory");
+          float* a = acc1 + buf * m1b;
+          for (int b = tid; b < d.m1; b += kConsumers * 32) {
+            const float v = a[b];
+            if (v != 0.f) atomicAdd(d.Y1 + (long)b * d.s1 + cur_i1, v);
+            a[b] = 0.f;
+          }
+          buf ^= 1;
         }
-        buf ^= 1;
+        cur_i1 = i1;
+        if (d.Y2) h21 = reduced(d.t21[i1], d.m2);
+        if (d.Y3) h31 = reduced(d.t31[i1], d.m3);
       }
-      cur_i1 = i1;
       if (!aborted) {
         aborted = *(volatile int*)&abort_flag != 0;
         if (!aborted && !mbar_wait(smem_u32(&full_bar[s]), (unsigned)((lt / S) & 1))) {
@@ -239,73 +260,53 @@ __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_con
       if (!aborted) {
         const float* tile = stage + (size_t)s * tile_elems;
         float* a1 = acc1 + buf * m1b;
-        int h21 = 0, h31 = 0;
-        if (d.Y2) h21 = (int)(entry_bin(d.t21[i1]) % d.m2) | (d.t21[i1] & (int)0x80000000);
-        if (d.Y3) h31 = (int)(entry_bin(d.t31[i1]) % d.m3) | (d.t31[i1] & (int)0x80000000);
-        int mb = (warp - (int)(((long)lt * nmb) % kConsumers) + kConsumers) % kConsumers;
-        for (; mb < nmb; mb += kConsumers) {
+        const int b21 = entry_bin(h21), b31 = entry_bin(h31);
+        for (int mb = mb0; mb < nmb; mb += kConsumers) {
           const int rr0 = (mb / nmb3) * 16, cc0 = (mb - (mb / nmb3) * nmb3) * 16;
           const int i3 = c0 + cc0 + 4 * cq;
-          float v[2][4];
-          int2 rt[2];
+          const float* tp = tile + (rr0 + rq) * TB3 + cc0 + 4 * cq;
+          const float4 x0 = *reinterpret_cast<const float4*>(tp);
+          const float4 x1 = *reinterpret_cast<const float4*>(tp + 8 * TB3);
+          const float v[2][4] = {{x0.x, x0.y, x0.z, x0.w}, {x1.x, x1.y, x1.z, x1.w}};
+          const int2 rt0 = rowtab[r0 + rr0 + rq], rt1 = rowtab[r0 + rr0 + rq + 8];
+          const int2 rt[2] = {rt0, rt1};
+          if (d.Y1) {
+            // padding rows / columns carry zero values and zero hashes: no guards needed
+            const int4 ctA = *reinterpret_cast<const int4*>(coltab + i3);
+            const int4 ctB = *reinterpret_cast<const int4*>(coltab + i3 + 2);
+            const int c13[4] = {ctA.x, ctA.z, ctB.x, ctB.z};
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const float4 x = *reinterpret_cast<const float4*>(tile + (rr0 + rq + 8 * h) * TB3 + cc0 + 4 * cq);
-            v[h][0] = x.x;
-            v[h][1] = x.y;
-            v[h][2] = x.z;
-            v[h][3] = x.w;
-            rt[h] = rowtab[r0 + rr0 + rq + 8 * h];
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                red_shared_add(a1 + add_mod(entry_bin(rt[h].x), entry_bin(c13[c]), d.m1),
+                               apply_sign(v[h][c], rt[h].x ^ c13[c]));
           }
-          const int4 ctA = *reinterpret_cast<const int4*>(coltab + i3);      // cols i3, i3+1
-          const int4 ctB = *reinterpret_cast<const int4*>(coltab + i3 + 2);  // cols i3+2, i3+3
-          const int c13[4] = {ctA.x, ctA.z, ctB.x, ctB.z};
-          const int c23[4] = {ctA.y, ctA.w, ctB.y, ctB.w};
-          const bool col_ok = i3 < d.s3;
-          if (d.Y1 && col_ok) {
+          if (d.Y3 && i3 < d.s3) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-              if (r0 + rr0 + rq + 8 * h >= d.s2) continue;
-#pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                if (v[h][c] == 0.f) continue;
-                const int b = add_mod(entry_bin(rt[h].x), entry_bin(c13[c]), d.m1);
-                atomicAdd(a1 + b, apply_sign(v[h][c], rt[h].x ^ c13[c]));
-              }
-            }
-          }
-          if (d.Y3 && col_ok) {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              if (r0 + rr0 + rq + 8 * h >= d.s2) continue;
               const int sg = h31 ^ rt[h].y;
-              const int b = add_mod(entry_bin(h31), entry_bin(rt[h].y), d.m3);
-              red_add4(d.Y3 + (long)b * d.s3 + i3, apply_sign(v[h][0], sg), apply_sign(v[h][1], sg),
+              float* dst = d.Y3 + (long)add_mod(b31, entry_bin(rt[h].y), d.m3) * d.s3 + i3;
+              red_add4(dst, apply_sign(v[h][0], sg), apply_sign(v[h][1], sg),
                        apply_sign(v[h][2], sg), apply_sign(v[h][3], sg));
             }
           }
           if (d.Y2) {
-            // transpose: element (row rq + 8h, column 4 cq + c) to tr[col][row ^ swizzle]
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
-              for (int c = 0; c < 4; ++c) {
-                const int col = 4 * cq + c, row = rq + 8 * h;
-                tr[col * kTrs + (row ^ ((col >> 3) << 3))] = v[h][c];
-              }
+              for (int c = 0; c < 4; ++c) tr[st_off[h][c]] = v[h][c];
             __syncwarp();
+            const int j2 = r0 + rr0 + 4 * tq;
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
               const int col = tc + 8 * p;
               const float4 x = *reinterpret_cast<const float4*>(tr + col * kTrs + ((4 * tq) ^ (8 * p)));
-              const int j3 = c0 + cc0 + col, j2 = r0 + rr0 + 4 * tq;
-              if (j3 < d.s3 && j2 < d.s2) {
-                const int e23 = coltab[j3].y;
-                const int sg = h21 ^ e23;
-                const int b = add_mod(entry_bin(h21), entry_bin(e23), d.m2);
-                red_add4(d.Y2 + (long)b * d.s2 + j2, apply_sign(x.x, sg), apply_sign(x.y, sg),
-                         apply_sign(x.z, sg), apply_sign(x.w, sg));
-              }
+              const int e23 = coltab[c0 + cc0 + col].y;
+              const int sg = h21 ^ e23;
+              if (j2 < d.s2)
+                red_add4(d.Y2 + (long)add_mod(b21, entry_bin(e23), d.m2) * d.s2 + j2, apply_sign(x.x, sg),
+                         apply_sign(x.y, sg), apply_sign(x.z, sg), apply_sign(x.w, sg));
             }
             __syncwarp();
           }
@@ -313,6 +314,12 @@ __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_con
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty_bar[s]));
+      // advance: next tile of the walk, and this warp's first micro-block in it
+      mb0 = (mb0 - nmb % kConsumers + kConsumers) % kConsumers;
+      if (++w == tiles_per_slice) {
+        w = 0;
+        ++i1;
+      }
     }
     if (d.Y1) {
       asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory");

@@ -412,6 +412,11 @@ __device__ void block_jacobi(U* A, U* V, int n, U tol, U floor_rel, int max_swee
   __syncthreads();
   const U floor_abs = floor_rel * red[0], tol2 = tol * tol;
   const int nblk = npairs * npairs, nitems = nblk + n * npairs;
+  // this thread's item for the whole run (one per thread when nitems <= blockDim.x)
+  const bool one = nitems <= nthr;
+  const bool blk0 = tid < nblk;
+  const int f0 = blk0 ? tid : tid - nblk;
+  const int i0 = f0 / npairs, j0 = f0 - (f0 / npairs) * npairs;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int t = 0; t < nrounds; ++t) {
       if (tid < npairs) {
@@ -428,9 +433,10 @@ __device__ void block_jacobi(U* A, U* V, int n, U tol, U floor_rel, int max_swee
       __syncthreads();
       if (t == 0 && tid == 0) flags[(sweep + 1) & 1] = 0;
       for (int e = tid; e < nitems; e += nthr) {
-        const bool blk = e < nblk;
+        const bool blk = one ? blk0 : e < nblk;
         const int f = blk ? e : e - nblk;
-        const int i = f / npairs, j = f - i * npairs;  // blocks: (pair i, pair j); V: (row i, pair j)
+        // blocks: (pair i, pair j); V: (row i, pair j)
+        const int i = one ? i0 : f / npairs, j = one ? j0 : f - (f / npairs) * npairs;
         const int p2 = pp[j], q2 = qq[j];
         const U c2 = cs[j], s2 = sn[j];
         if (blk) {

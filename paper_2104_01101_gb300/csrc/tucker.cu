@@ -486,9 +486,9 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
     TS_TRY(build_ts_tables<T>(X, S, opt.seed, 0, w, st));
     TS_TRY(phase(opt, 2, st));
     TS_TRY(sketch_rhs_all<T>(X, S, w, st));
+    TS_TRY(phase(opt, 3, st));
     if (S.solve == TS_SOLVE_RSVD)
       TS_TRY(rhs_times_omegas<T>(X, S, w, 0, opt.resketch_each_sweep ? 1 : S.sweeps, st));
-    TS_TRY(phase(opt, 3, st));
   } else {
     TS_TRY(phase(opt, 2, st));
     TS_TRY(phase(opt, 3, st));

@@ -151,11 +151,12 @@ ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
                 MatView<T> B2, int n2, MatView<T> B3, double beta, OutView<T> C,
                 const GemmSplit<T>* split, cudaStream_t st) {
   if (M <= 0 || N <= 0) return TS_OK;
-  constexpr int kWave = 152;
+  constexpr int kWave = 2 * 152;  // two resident CTAs per SM: 4 warps per sub-partition
   const int tiles64 = ceil_div(M, 64) * ceil_div(N, 64);
   const int tiles32 = ceil_div(M, 32) * ceil_div(N, 32);
-  // 64x64 tiles when they alone, or split along K, can fill about a wave; else 32x32
-  const bool small = tiles64 * ceil_div(K > 0 ? K : 1, 4 * BK) < kWave;
+  // 64x64 tiles (twice the FMAs per shared-memory load) when they alone, or split along
+  // K, can give every SM a CTA; else 32x32
+  const bool small = tiles64 * ceil_div(K > 0 ? K : 1, 4 * BK) < kWave / 2;
   const int tiles = small ? tiles32 : tiles64;
   const int bm = small ? 32 : 64;
   int splits = 1;

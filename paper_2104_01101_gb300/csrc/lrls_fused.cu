@@ -13,8 +13,9 @@
 //      barrier per reflector, then each warp forms its own column of Q); E = G^{-1} Q;
 //      D = E^T H (= Q^T G^{-1} Z^T Y, k x s); K = D D^T.   Exact: M = X, K = X X^T.
 //   3. K = U Lambda U^T by cyclic Jacobi with the whole block (round-robin pairs; each
-//      round's rotations applied as one two-sided 2 x 2 block update; relative stopping
-//      rule with a rounding floor), optionally polished by FP64 sweeps on V^T K V.
+//      round's rotations applied as one two-sided 2 x 2 block update while the next
+//      round's rotations are formed; relative stopping rule with a rounding floor),
+//      optionally polished by FP64 sweeps on V^T K V.
 //   4. CnT = Q U_R Sigma_R (Q = I for exact), A = M^T U_R Sigma_R^{-1}, canonical column
 //      signs (largest-magnitude entry of each column of A positive, lowest index on ties)
 //      and C_(n)^T scattered into the core.
@@ -36,7 +37,7 @@ __host__ __device__ inline int quad_ld(int n) { return (n + 3) & ~3; }
 struct FusedLayout {
   int naug, lda, kq, ke, n;
   size_t A, P0, P1, rowold, colbuf, QA, Qo, Qt, tau, E, M, Kk, Vk, Am, Fm, CnTs, K64, V64, KV64,
-      sched, total;
+      sched, memb, Kk2, K64b, total;
 };
 
 __host__ __device__ inline FusedLayout fused_layout(int r, int s, int k, int R, int solve,
@@ -78,6 +79,9 @@ __host__ __device__ inline FusedLayout fused_layout(int r, int s, int k, int R, 
   L.KV64 = take(polish ? 8 * (size_t)L.n * L.n : 0);
   const int np = (L.n + 1) & ~1;
   L.sched = take(sizeof(int) * (size_t)(np - 1) * (np / 2));
+  L.memb = take(sizeof(int) * (size_t)(np - 1) * np);
+  L.Kk2 = take(tsz * (size_t)L.n * L.n);
+  L.K64b = take(polish ? 8 * (size_t)L.n * L.n : 0);
   L.total = off;
   return L;
 }
@@ -337,7 +341,9 @@ __host__ __device__ constexpr U jacobi_floor() {
 // Round-robin schedule of cyclic Jacobi for order n (n <= 64): np - 1 rounds of np / 2
 // disjoint pairs (np = n rounded up to even), pair (p, q) packed as p | q << 8 with
 // q = 255 for the padding index.
-__device__ void jacobi_schedule(int n, int* sched) {
+// memb[t * np + a] = 2 i + (a is the second index of its pair) for the pair i of round t
+// that holds index a.
+__device__ void jacobi_schedule(int n, int* sched, int* memb) {
   const int np = (n + 1) & ~1, npairs = np >> 1, nrounds = np - 1;
   for (int e = threadIdx.x; e < nrounds * npairs; e += blockDim.x) {
     const int t = e / npairs, i = e - t * npairs;
@@ -345,6 +351,8 @@ __device__ void jacobi_schedule(int n, int* sched) {
     const int b = i == 0 ? nrounds : (t - i + nrounds) % nrounds;
     const int p = min(a, b), q = max(a, b);
     sched[e] = p | ((q < n ? q : 255) << 8);
+    memb[t * np + p] = 2 * i;
+    memb[t * np + q] = 2 * i + 1;
   }
 }
 
@@ -384,18 +392,48 @@ __device__ __forceinline__ void jacobi_rotation(const U* A, int n, int pq, U tol
   }
 }
 
-// Cyclic Jacobi by the whole block on the symmetric n x n matrix A (row stride n,
-// n <= 64); V (n x n) accumulates the rotations onto its start basis.  A round: one
-// thread per pair computes the rotation (J = [[c, s], [-s, c]] on (p, q)), then every
-// thread applies them to the items it owns for the whole run -- 2 x 2 blocks (pair i,
-// pair j) of J^T A J, or pairs (row l, pair j) of V J -- two barriers per round.  A pair
-// rotates when |a_pq| exceeds both tol sqrt(|a_pp a_qq|) (relative accuracy) and
-// floor_rel max_i |a_ii| (the rounding level of A itself); the loop ends after a sweep
-// without rotations or after max_sweeps.  pp, qq, cs, sn hold n/2 + 1 entries.
+// The 2 x 2 block of J^T A J on rows {p1, q1} x columns {p2, q2} for the rotations
+// J = [[c, s], [-s, c]] of the two pairs (q < 0: padding index, entries zero).  The
+// products are written as explicit fused multiply-adds so that every caller obtains the
+// same rounded values.
 template <typename U>
-__device__ void block_jacobi(U* A, U* V, int n, U tol, U floor_rel, int max_sweeps,
-                             const int* sched, int* pp, int* qq, U* cs, U* sn, int* flags,
-                             U* red) {
+__device__ __forceinline__ void rotate_block(const U* A, int n, int p1, int q1, U c1, U s1,
+                                             int p2, int q2, U c2, U s2, U& n00, U& n01,
+                                             U& n10, U& n11) {
+  const U b00 = A[p1 * n + p2];
+  const U b01 = q2 >= 0 ? A[p1 * n + q2] : (U)0;
+  const U b10 = q1 >= 0 ? A[q1 * n + p2] : (U)0;
+  const U b11 = (q1 >= 0 && q2 >= 0) ? A[q1 * n + q2] : (U)0;
+  const U t00 = fma(c1, b00, -(s1 * b10)), t01 = fma(c1, b01, -(s1 * b11));
+  const U t10 = fma(s1, b00, c1 * b10), t11 = fma(s1, b01, c1 * b11);
+  n00 = fma(c2, t00, -(s2 * t01));
+  n01 = fma(s2, t00, c2 * t01);
+  n10 = fma(c2, t10, -(s2 * t11));
+  n11 = fma(s2, t10, c2 * t11);
+}
+
+// Rotation parameters of one round (np / 2 <= 32 pairs), double-buffered.
+template <typename U>
+struct JacobiRound {
+  int p[2][kMaxEig / 2 + 1], q[2][kMaxEig / 2 + 1];
+  U c[2][kMaxEig / 2 + 1], s[2][kMaxEig / 2 + 1];
+};
+
+// Cyclic Jacobi by the whole block on the symmetric n x n matrix in A (row stride n,
+// n <= 64), double-buffered with A2; V (n x n) accumulates the rotations onto its start
+// basis.  Each round applies its rotations (J = [[c, s], [-s, c]] on each pair of the
+// round-robin schedule) as one update of the 2 x 2 blocks of J^T A J into the other
+// buffer, plus V J.  The rotations of the NEXT round are computed at the same time by
+// threads without items: the three entries they need are formed from the current buffer
+// and this round's rotations with the same arithmetic as the block update, so one
+// barrier per round suffices.  A pair rotates when |a_pq| exceeds both tol sqrt(|a_pp
+// a_qq|) (relative accuracy) and floor_rel max_i |a_ii| (the rounding level of A); the
+// loop ends after a sweep without rotations or after max_sweeps (<= 31).  sched and memb
+// come from jacobi_schedule.  Returns the buffer holding the result.
+template <typename U>
+__device__ U* block_jacobi(U* A, U* A2, U* V, int n, U tol, U floor_rel, int max_sweeps,
+                           const int* sched, const int* memb, JacobiRound<U>& rd, int* flags,
+                           U* red) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int np = (n + 1) & ~1, npairs = np >> 1, nrounds = np - 1;
   if (tid < 32) {
@@ -403,65 +441,101 @@ __device__ void block_jacobi(U* A, U* V, int n, U tol, U floor_rel, int max_swee
     for (int i = tid; i < n; i += 32) d = fmax(d, fabs(A[i * n + i]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(kFull, d, o));
-    if (tid == 0) {
-      red[0] = d;
-      flags[0] = 0;
-      flags[1] = 0;
-    }
+    if (tid == 0) red[0] = d;
   }
+  for (int i = tid; i < 32; i += nthr) flags[i] = 0;
   __syncthreads();
   const U floor_abs = floor_rel * red[0], tol2 = tol * tol;
   const int nblk = npairs * npairs, nitems = nblk + n * npairs;
-  // this thread's item for the whole run (one per thread when nitems <= blockDim.x)
-  const bool one = nitems <= nthr;
-  const bool blk0 = tid < nblk;
-  const int f0 = blk0 ? tid : tid - nblk;
-  const int i0 = f0 / npairs, j0 = f0 - (f0 / npairs) * npairs;
+  // rotation threads: the last npairs threads (they own no item when the block is large)
+  const int rbase = nthr - npairs;
+  const bool rthread = tid >= rbase;
+  const int ri = tid - rbase;
+  if (tid < npairs) {  // rotations of round 0 from the start matrix
+    int p, q;
+    U c, s;
+    bool rot;
+    jacobi_rotation<U>(A, n, sched[tid], tol2, floor_abs, p, q, c, s, rot);
+    rd.p[0][tid] = p;
+    rd.q[0][tid] = q;
+    rd.c[0][tid] = c;
+    rd.s[0][tid] = s;
+    if (rot) flags[0] = 1;
+  }
+  __syncthreads();
+  U* Ao = A;
+  U* An = A2;
+  int cur = 0;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int t = 0; t < nrounds; ++t) {
-      if (tid < npairs) {
-        int p, q;
-        U c, s;
-        bool rot;
-        jacobi_rotation<U>(A, n, sched[t * npairs + tid], tol2, floor_abs, p, q, c, s, rot);
-        pp[tid] = p;
-        qq[tid] = q;
-        cs[tid] = c;
-        sn[tid] = s;
-        if (rot) flags[sweep & 1] = 1;
-      }
-      __syncthreads();
-      if (t == 0 && tid == 0) flags[(sweep + 1) & 1] = 0;
-      for (int e = tid; e < nitems; e += nthr) {
-        const bool blk = one ? blk0 : e < nblk;
-        const int f = blk ? e : e - nblk;
-        // blocks: (pair i, pair j); V: (row i, pair j)
-        const int i = one ? i0 : f / npairs, j = one ? j0 : f - (f / npairs) * npairs;
-        const int p2 = pp[j], q2 = qq[j];
-        const U c2 = cs[j], s2 = sn[j];
-        if (blk) {
-          const int p1 = pp[i], q1 = qq[i];
-          const U c1 = cs[i], s1 = sn[i];
-          const U b00 = A[p1 * n + p2];
-          const U b01 = q2 >= 0 ? A[p1 * n + q2] : (U)0;
-          const U b10 = q1 >= 0 ? A[q1 * n + p2] : (U)0;
-          const U b11 = (q1 >= 0 && q2 >= 0) ? A[q1 * n + q2] : (U)0;
-          const U t00 = c1 * b00 - s1 * b10, t01 = c1 * b01 - s1 * b11;
-          const U t10 = s1 * b00 + c1 * b10, t11 = s1 * b01 + c1 * b11;
-          A[p1 * n + p2] = c2 * t00 - s2 * t01;
-          if (q2 >= 0) A[p1 * n + q2] = s2 * t00 + c2 * t01;
-          if (q1 >= 0) A[q1 * n + p2] = c2 * t10 - s2 * t11;
-          if (q1 >= 0 && q2 >= 0) A[q1 * n + q2] = s2 * t10 + c2 * t11;
-        } else if (q2 >= 0 && s2 != (U)0) {
-          const U vp = V[i * n + p2], vq = V[i * n + q2];
-          V[i * n + p2] = c2 * vp - s2 * vq;
-          V[i * n + q2] = s2 * vp + c2 * vq;
+      const int* rp = rd.p[cur];
+      const int* rq = rd.q[cur];
+      const U* rc = rd.c[cur];
+      const U* rs = rd.s[cur];
+      for (int e = tid; tid < rbase && e < nitems; e += rbase) {
+        if (e < nblk) {
+          const int i = e / npairs, j = e - (e / npairs) * npairs;
+          const int p1 = rp[i], q1 = rq[i], p2 = rp[j], q2 = rq[j];
+          U n00, n01, n10, n11;
+          rotate_block<U>(Ao, n, p1, q1, rc[i], rs[i], p2, q2, rc[j], rs[j], n00, n01, n10, n11);
+          An[p1 * n + p2] = n00;
+          if (q2 >= 0) An[p1 * n + q2] = n01;
+          if (q1 >= 0) An[q1 * n + p2] = n10;
+          if (q1 >= 0 && q2 >= 0) An[q1 * n + q2] = n11;
+        } else {
+          const int f = e - nblk;
+          const int l = f / npairs, j = f - (f / npairs) * npairs;
+          const int p2 = rp[j], q2 = rq[j];
+          const U c2 = rc[j], s2 = rs[j];
+          if (q2 >= 0 && s2 != (U)0) {
+            const U vp = V[l * n + p2], vq = V[l * n + q2];
+            V[l * n + p2] = c2 * vp - s2 * vq;
+            V[l * n + q2] = s2 * vp + c2 * vq;
+          }
         }
       }
+      if (rthread) {  // rotation of pair ri for the next round, from J^T Ao J
+        const int tn = t + 1 < nrounds ? t + 1 : 0;
+        const int sn = t + 1 < nrounds ? sweep : sweep + 1;
+        const int pq = sched[tn * npairs + ri];
+        const int p = pq & 255, q = (pq >> 8) == 255 ? -1 : (pq >> 8);
+        U c = 1, s = 0;
+        if (q >= 0) {
+          const int ma = memb[t * np + p], mb = memb[t * np + q];
+          const int ia = ma >> 1, ib = mb >> 1, ra = ma & 1, rb = mb & 1;
+          U x00, x01, x10, x11, y00, y01, y10, y11, z00, z01, z10, z11;
+          rotate_block<U>(Ao, n, rp[ia], rq[ia], rc[ia], rs[ia], rp[ia], rq[ia], rc[ia], rs[ia],
+                          x00, x01, x10, x11);
+          rotate_block<U>(Ao, n, rp[ib], rq[ib], rc[ib], rs[ib], rp[ib], rq[ib], rc[ib], rs[ib],
+                          y00, y01, y10, y11);
+          rotate_block<U>(Ao, n, rp[ia], rq[ia], rc[ia], rs[ia], rp[ib], rq[ib], rc[ib], rs[ib],
+                          z00, z01, z10, z11);
+          const U app = ra ? x11 : x00, aqq = rb ? y11 : y00;
+          const U apq = ra ? (rb ? z11 : z10) : (rb ? z01 : z00);
+          if (apq * apq > tol2 * fabs(app * aqq) && fabs(apq) > floor_abs) {
+            const U theta = fast_div(aqq - app, 2 * apq);
+            const U h = theta * theta + 1;
+            const U tt =
+                fast_div(theta >= (U)0 ? (U)1 : (U)-1, fabs(theta) + h * fast_rsqrt(h));
+            c = unit_rsqrt(tt * tt + 1);
+            s = tt * c;
+            if (sn < 32) flags[sn] = 1;
+          }
+        }
+        rd.p[cur ^ 1][ri] = p;
+        rd.q[cur ^ 1][ri] = q;
+        rd.c[cur ^ 1][ri] = c;
+        rd.s[cur ^ 1][ri] = s;
+      }
+      U* tmp = Ao;
+      Ao = An;
+      An = tmp;
+      cur ^= 1;
       __syncthreads();
     }
-    if (!flags[sweep & 1]) break;
+    if (!flags[sweep]) break;
   }
+  return Ao;
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -487,9 +561,10 @@ struct FusedArgs {
 template <typename T, typename U, bool POLISH64>
 __global__ void __launch_bounds__(kThreads) k_lrls_fused(FusedArgs<T> a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int jp[kMaxEig / 2 + 1], jq[kMaxEig / 2 + 1], jflags[2];
-  __shared__ T jc[kMaxEig / 2 + 1], js[kMaxEig / 2 + 1], jred[1];
-  __shared__ double jc64[POLISH64 ? kMaxEig / 2 + 1 : 1], js64[POLISH64 ? kMaxEig / 2 + 1 : 1];
+  __shared__ JacobiRound<T> jround;
+  __shared__ JacobiRound<double> jround64;
+  __shared__ int jflags[32];
+  __shared__ T jred[1];
   __shared__ double jred64[1];
   __shared__ int order[kMaxEig];
   __shared__ T sgn[kMaxEig];
@@ -629,11 +704,11 @@ __global__ void __launch_bounds__(kThreads) k_lrls_fused(FusedArgs<T> a) {
   __syncthreads();
   // 6. eigen-decomposition of K (optionally polished in FP64 on V^T K V, K formed in FP64)
   int* sched = reinterpret_cast<int*>(smem_raw + L.sched);
-  jacobi_schedule(n, sched);
+  int* memb = reinterpret_cast<int*>(smem_raw + L.memb);
+  jacobi_schedule(n, sched, memb);
   __syncthreads();
-  block_jacobi<T>(Kk, Vk, n, jacobi_tol<T>(), jacobi_floor<T>(), 20, sched, jp, jq, jc, js,
-                  jflags, jred);
-  T* Kf = Kk;
+  T* Kf = block_jacobi<T>(Kk, reinterpret_cast<T*>(smem_raw + L.Kk2), Vk, n, jacobi_tol<T>(),
+                          jacobi_floor<T>(), 20, sched, memb, jround, jflags, jred);
   if constexpr (POLISH64) {
     double* K64 = reinterpret_cast<double*>(smem_raw + L.K64);
     double* V64 = reinterpret_cast<double*>(smem_raw + L.V64);
@@ -675,9 +750,9 @@ __global__ void __launch_bounds__(kThreads) k_lrls_fused(FusedArgs<T> a) {
       }
     }
     __syncthreads();
-    block_jacobi<double>(K64, V64, n, jacobi_tol<double>(), jacobi_floor<double>(), 10, sched, jp,
-                         jq, jc64, js64, jflags, jred64);
-    const double* Kf64 = K64;
+    const double* Kf64 = block_jacobi<double>(
+        K64, reinterpret_cast<double*>(smem_raw + L.K64b), V64, n, jacobi_tol<double>(),
+        jacobi_floor<double>(), 10, sched, memb, jround64, jflags, jred64);
     for (int e = tid; e < n * n; e += nthr) Vk[e] = (T)V64[e];
     if (tid < n) Kf[tid * n + tid] = (T)Kf64[tid * n + tid];
     __syncthreads();

@@ -13,6 +13,7 @@ path does not shard at this size): value sums over ranks, time is the max.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -140,6 +141,21 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(values, world, device):
+    """Per-rank timings -> their maximum over the ranks (the job's wall time)."""
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t]
+
+
+def job_sweeps_per_s(world, ms):
+    """Whole-job throughput: every rank decomposes its own tensor (replicas) in ms."""
+    return world * SWEEPS * 1e3 / ms
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -231,19 +247,17 @@ def run_ours(args, rank, world):
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
 
     ms = sum(step_ms) / len(step_ms)
-    t_max = torch.tensor([ms, sum(e2e_ms) / len(e2e_ms)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms, e2e = float(t_max[0]), float(t_max[1])
+    ms, e2e = max_over_ranks([ms, sum(e2e_ms) / len(e2e_ms)], world, dev)
     if rank != 0:
         return
     hbm, src = peaks()
+    traffic = sketch_traffic()
     # Dominant HBM kernel: the one-pass sketch of the tensor (all 3 right-hand sides).
     alg_bytes = 4 * np.prod(DIMS) + 4 * M * sum(DIMS)
     sk = statistics.mean(sketch_ms)
     achieved = alg_bytes / (sk * 1e-3) / 1e9
     line = {
-        "metric": METRIC, "value": world * SWEEPS * 1e3 / ms, "unit": "sweeps/s",
+        "metric": METRIC, "value": job_sweeps_per_s(world, ms), "unit": "sweeps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
@@ -259,11 +273,13 @@ def run_ours(args, rank, world):
         "phases_ms": {"init_rrf": statistics.mean(rrf_ms), "input_sketch": sk,
                       "sweeps": statistics.mean(sweeps_ms)},
         "input_sketch_gbs": achieved,
-        "roofline": {"kernel": "input sketch pass (3 right-hand sides, one read of T)",
+        "roofline": {"kernel": "k_sketch_dense3_tma, right-hand-side pass (3 modes, one read "
+                               "of T); the step's largest kernel, the single-block solve, is "
+                               "latency-bound and has no HBM or tensor roofline",
                      "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm, "peak_source": src, "traffic": None,
+                     "frac": achieved / hbm, "peak_source": src, "traffic": traffic,
                      "algorithmic_bytes": int(alg_bytes)},
-        "e2e": {"value": world * SWEEPS * 1e3 / e2e, "unit": "sweeps/s",
+        "e2e": {"value": job_sweeps_per_s(world, e2e), "unit": "sweeps/s",
                 "h2d_bytes_per_step": int(T.nbytes), "d2h_bytes_per_step": int(out_bytes)},
         "gpu_launches": int(launches),
         "clocks": clk_summary,
@@ -276,6 +292,22 @@ def run_ours(args, rank, world):
                                 "sample": "one complete FP64 numpy decomposition of the full "
                                           "workload (10 sweeps + prep + residual)"}
     print(json.dumps(line), flush=True)
+
+
+# DRAM bytes (read + write) of one right-hand-side launch of k_sketch_dense3_tma on this
+# workload, from the ncu capture in profiles/input_sketch_dense400_fp32.md.  The figure
+# belongs to the kernel source it was taken on: another source reports null.
+SKETCH_TRAFFIC_BYTES = 271.7e6
+SKETCH_SOURCE_SHA1 = "5c2f4c508c50"
+
+
+def sketch_traffic():
+    path = os.path.join(ROOT, "paper_2104_01101_gb300", "csrc", "input_sketch_tma.cu")
+    try:
+        digest = hashlib.sha1(open(path, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return SKETCH_TRAFFIC_BYTES if digest.startswith(SKETCH_SOURCE_SHA1) else None
 
 
 def main():

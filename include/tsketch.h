@@ -95,7 +95,10 @@ typedef struct {
   int32_t rsvd_oversample;    /* p in the k = R + p columns of Alg. 5's test matrix; <0 = 5 */
   int32_t solve;              /* ts_solve_kind; TS_SOLVE_RSVD is the routine Alg. 4 calls */
   int32_t resketch_each_sweep;/* 1: redraw TensorSketch tables and re-sketch T every sweep */
-  int32_t gram_bf16;          /* reserved: must be 0 in this build */
+  int32_t gram_bf16;          /* 1 (FP32 data): the product [Z^T Z | Z^T Y Omega | Z^T Y]
+                                 of every subproblem solved in one block runs in BF16 on
+                                 the tensor cores with FP32 accumulation (the precision
+                                 form); the sketches and the solve stay FP32 */
   int32_t init_given;         /* 1: factors_inout already hold the initial A^(2..N) (no RRF) */
   int32_t track_fit;          /* 1: write the relative residual after every sweep */
   int32_t solve_fp64;         /* FP32 data: 1 runs the QR of Alg. 5 and the last Jacobi
@@ -196,6 +199,20 @@ ts_status tensorsketch_apply_static_scratch(int32_t nf, const void* const* facto
  * Errors: TS_ERR_SHAPE if order < 2 or > TS_MAX_ORDER or mode out of range. */
 ts_status tensorsketch_input(const ts_tensor* X, int32_t mode, const int32_t* const* tables,
                              int32_t m, void* Y_out, ts_stream stream);
+
+/* ------------------------------------------------------------------------- */
+/* The Gram products of Alg. 5 in the BF16 precision form (the tensor-core path of the
+ * sketched solve): C = bf16(A) bf16(B)^T accumulated in FP32.  A (M x K) and B (N x K)
+ * are FP32 row-major device arrays, C (M x N) FP32 row-major; in the decomposition
+ * A = Z^T and B = [Z | Y Omega | Y]^T.  The operands are rounded to BF16 (nearest, ties
+ * to even) in scratch; each product of two BF16 values is exact in FP32, so C differs
+ * from the exact product of the rounded operands only by the FP32 accumulation.  K is
+ * split across CTAs and the partial sums are added in split order (deterministic).
+ * Errors: TS_ERR_SHAPE unless M, N, K >= 1; TS_ERR_WORKSPACE for short or misaligned
+ * scratch. */
+size_t ts_gram_bf16_scratch_bytes(int32_t M, int32_t N, int32_t K);
+ts_status ts_gram_bf16(int32_t M, int32_t N, int32_t K, const void* A, const void* B,
+                       void* C_out, void* scratch, size_t scratch_bytes, ts_stream stream);
 
 /* ------------------------------------------------------------------------- */
 /* Init-RRF for one mode (Alg. 3 with the composite sketch of Sec. 5).

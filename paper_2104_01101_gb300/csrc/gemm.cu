@@ -190,6 +190,17 @@ ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
 }
 
 template <typename T>
+ts_status launch_split_reduce(int M, int N, int splits, const T* partial, T* C, long ldc,
+                              cudaStream_t st) {
+  const size_t MN = (size_t)M * N;
+  int blocks = (int)((MN + 255) / 256);
+  if (blocks > 2048) blocks = 2048;
+  k_gemm_reduce<T><<<blocks, 256, 0, st>>>(M, N, splits, partial, (T)1, (T)0, OutView<T>{C, ldc, 1});
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+template <typename T>
 ts_status gemm2(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, int n1,
                 MatView<T> B2, double beta, OutView<T> C, const GemmSplit<T>* split,
                 cudaStream_t st) {
@@ -207,6 +218,7 @@ ts_status gemm(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B, do
                              const GemmSplit<T>*, cudaStream_t);                                \
   template ts_status gemm2<T>(int, int, int, double, MatView<T>, MatView<T>, int, MatView<T>,   \
                               double, OutView<T>, const GemmSplit<T>*, cudaStream_t);           \
+  template ts_status launch_split_reduce<T>(int, int, int, const T*, T*, long, cudaStream_t);    \
   template ts_status gemm3<T>(int, int, int, double, MatView<T>, MatView<T>, int, MatView<T>,   \
                               int, MatView<T>, double, OutView<T>, const GemmSplit<T>*,         \
                               cudaStream_t);

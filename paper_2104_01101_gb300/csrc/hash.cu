@@ -118,6 +118,21 @@ ts_status launch_omegas(uint64_t seed, const OmegaBlocks& ob, T* out, cudaStream
 template ts_status launch_omegas<float>(uint64_t, const OmegaBlocks&, float*, cudaStream_t);
 template ts_status launch_omegas<double>(uint64_t, const OmegaBlocks&, double*, cudaStream_t);
 
+ts_status encode_fn(EncodeTiledFn* out) {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    TS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !p)
+      return fail(TS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  *out = fn;
+  return TS_OK;
+}
+
 template ts_status launch_gaussian<float>(uint64_t, uint64_t, int64_t, double, float*,
                                           cudaStream_t);
 template ts_status launch_gaussian<double>(uint64_t, uint64_t, int64_t, double, double*,

@@ -355,26 +355,6 @@ static const int kColCand[] = {48, 80, 112};
 static int tile_rows(long s2) { return s2 <= 16 ? 16 : tile_extent(s2, kRowCand, 5); }
 static int tile_cols(long s3) { return s3 <= 16 ? 16 : tile_extent(s3, kColCand, 3); }
 
-using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
-                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
-                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-static ts_status encode_fn(EncodeTiledFn* out) {
-  static EncodeTiledFn fn = nullptr;
-  if (!fn) {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    TS_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q));
-    if (q != cudaDriverEntryPointSuccess || !p)
-      return fail(TS_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    fn = reinterpret_cast<EncodeTiledFn>(p);
-  }
-  *out = fn;
-  return TS_OK;
-}
-
 bool dense3_tma_eligible(const ts_tensor& X, const SketchJob* jobs, int njobs) {
   if (X.format != TS_DENSE || X.dtype != TS_F32 || X.order != 3) return false;
   if (((uintptr_t)X.values & 15) != 0) return false;

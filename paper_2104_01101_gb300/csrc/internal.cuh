@@ -1,9 +1,18 @@
 // Internal launch interfaces shared by the translation units of libtsketch.
 #pragma once
 
+#include <cuda.h>
+
 #include "common.cuh"
 
 namespace ts {
+
+// cuTensorMapEncodeTiled, obtained from the driver once (TMA tensor maps).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+ts_status encode_fn(EncodeTiledFn* out);
 
 // ---------------------------------------------------------------- hash.cu
 ts_status launch_hash_table(uint64_t seed, int purpose, int sweep, int n, int k, int64_t size,
@@ -105,6 +114,24 @@ ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
                 MatView<T> B2, int n2, MatView<T> B3, double beta, OutView<T> C,
                 const GemmSplit<T>* split, cudaStream_t st);
 constexpr int kGemmCounters = 4096;
+// C (M x N, row stride ldc) = sum over splits of partial (split-major M x N).
+template <typename T>
+ts_status launch_split_reduce(int M, int N, int splits, const T* partial, T* C, long ldc,
+                              cudaStream_t st);
+
+// ---------------------------------------------------------------- gram_tc.cu
+// BF16 precision form of the Gram products (tcgen05): operands are BF16 row-major with
+// a row stride of gram_tc_ld(K) elements (16-byte rows).  pack_bf16 writes rows x K of
+// src (element (i, k) at src[i rs + k cs]); gram_tc_map encodes a TMA map over such a
+// buffer; gram_tc forms C (M x N, row stride ldc) = A B^T, summing split-K partials
+// (gram_tc_partial_elems floats) in split order.
+int gram_tc_ld(int K);
+ts_status pack_bf16(const float* src, long rs, long cs, int rows, int K, void* dst,
+                    cudaStream_t st);
+ts_status gram_tc_map(const void* base, int rows, int K, CUtensorMap* map);
+size_t gram_tc_partial_elems(int M, int N, int K);
+ts_status gram_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, int M, int N, int K,
+                  float* C, long ldc, float* partial, int* flag, cudaStream_t st);
 
 // ---------------------------------------------------------------- solve.cu
 // Layout of the core for scattering C_(n)^T into it.

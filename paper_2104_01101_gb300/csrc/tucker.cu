@@ -81,6 +81,7 @@ struct Shape {
   int oversample;
   bool rrf;
   bool fp64solve;  // FP64 QR / polish on FP32 data
+  bool bf16gram;   // [G | W | H] on the tensor cores in BF16 (FP32 data, fused subproblems)
   int ranks[TS_MAX_ORDER];
   int r[TS_MAX_ORDER];   // prod_{k != n} ranks[k]
   int kc[TS_MAX_ORDER];  // RSVD width of subproblem n
@@ -102,7 +103,6 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
     return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: bad sketch kind %d", kind);
   if (opt->solve != TS_SOLVE_RSVD && opt->solve != TS_SOLVE_EXACT)
     return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: bad solve kind %d", opt->solve);
-  if (opt->gram_bf16) return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: gram_bf16 not built");
   if (sweeps < 1) return fail(TS_ERR_SHAPE, "tucker_als_sketched: sweeps %d < 1", sweeps);
   if (kind == TS_LEVERAGE && X->format != TS_DENSE)
     return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: leverage sampling needs a dense tensor");
@@ -116,6 +116,7 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
   S.oversample = opt->rsvd_oversample < 0 ? 5 : opt->rsvd_oversample;
   S.rrf = !opt->init_given;
   S.fp64solve = opt->solve_fp64 != 0 && X->dtype == TS_F32;
+  S.bf16gram = opt->gram_bf16 != 0 && X->dtype == TS_F32;
   S.smax = 0;
   S.rmax = S.kmax = S.Rmax = S.k1max = S.k2max = S.chain_cols_max = 0;
   memset(&S.ob, 0, sizeof(S.ob));
@@ -213,7 +214,14 @@ struct Work {
   double* levscr;
   T* fitQ;
   double* fitacc;
+  void* Bt[TS_MAX_ORDER];  // BF16 precision form: [Z | Y Omega | Y]^T per mode (rows x ld)
+  float* gpart;            // its split-K partial sums
 };
+
+// Rows of the BF16 operand [Z | Y Omega | Y]^T of subproblem n (exact solve: [Z | Y]^T).
+static int bf16_cols(const Shape& S, int n, int s) {
+  return S.r[n] + (S.solve == TS_SOLVE_RSVD ? S.kc[n] : 0) + s;
+}
 
 template <typename T>
 static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& b, Work<T>& w) {
@@ -300,6 +308,17 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
     w.fitQ = b.take<T>(fit_dense_scratch_elems<T>(X, S.ranks));
     w.fitacc = b.take<double>(2);
   }
+  if (S.bf16gram) {
+    size_t part = 0;
+    for (int n = 0; n < N; ++n) {
+      if (!S.fused[n]) continue;
+      const int cols = bf16_cols(S, n, (int)X.dims[n]);
+      w.Bt[n] = b.take<uint16_t>((size_t)cols * gram_tc_ld(m));
+      const size_t p = gram_tc_partial_elems(S.r[n], cols, m);
+      if (p > part) part = p;
+    }
+    w.gpart = b.take<float>(part);
+  }
 }
 
 // ---------------------------------------------------------------- building blocks
@@ -313,6 +332,13 @@ static OutView<T> ov(T* p, long rs, long cs) {
   return OutView<T>{p, rs, cs};
 }
 
+// The BF16 operand of one subproblem: rows [0, r) Z^T, then (Y Omega)^T, then Y^T;
+// y_packed: Y^T is already in place (written once per pass over T).
+struct Bf16Op {
+  void* Bt;
+  bool y_packed;
+};
+
 // Sketched subproblem on Z = ZW[:, :r] (column-major) and Y (m x s) -> CnT (r x R),
 // A_out (s x R), core scattered when core != null.  RSVD (Alg. 5): yom views Y Omega
 // (m x k) when the caller formed it, else it is formed here from the test matrix Om
@@ -321,7 +347,7 @@ template <typename T>
 static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc, bool fp64,
                                   const T* Om, long ldo, const MatView<T>* yom, const T* Y,
                                   Work<T>& w, T* A_out, T* core, const CoreMap& map,
-                                  cudaStream_t st) {
+                                  cudaStream_t st, const Bf16Op* bf = nullptr) {
   T* ZW = w.ZW;
   const MatView<T> Zt = mv<T>(ZW, m, 1);  // r x m view of Z^T
   const MatView<T> Zm = mv<T>(ZW, 1, m);  // m x r view of Z
@@ -340,6 +366,24 @@ static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc,
   if (fused_ok(r, s, kc, R, solve, sizeof(T), fp64)) {
     // [G | W | H] = Z^T [Z | Y Omega | Y] (exact: [G | H]) in one product, then the whole
     // solve in one block
+    if constexpr (sizeof(T) == 4) {
+      if (bf) {  // BF16 precision form of the product, on the tensor cores
+        const int kk = solve == TS_SOLVE_RSVD ? k : 0;
+        const int N = r + kk + s;
+        char* bt = static_cast<char*>(bf->Bt);
+        const size_t row = 2 * (size_t)gram_tc_ld(m);
+        TS_TRY(pack_bf16(ZW, m, 1, r, m, bt, st));  // Z^T: Z is column-major
+        if (kk) TS_TRY(pack_bf16(yv.p, yv.cs, yv.rs, kk, m, bt + r * row, st));
+        if (!bf->y_packed) TS_TRY(pack_bf16(Y, 1, s, s, m, bt + (size_t)(r + kk) * row, st));
+        CUtensorMap ma, mb;
+        TS_TRY(gram_tc_map(bt, r, m, &ma));
+        TS_TRY(gram_tc_map(bt, N, m, &mb));
+        TS_TRY(gram_tc(ma, mb, r, N, m, w.GW, N, w.gpart, w.flag, st));
+        return launch_lrls_fused<T>(r, s, k, R, solve, fp64, w.GW, N, kk ? w.GW + r : nullptr,
+                                    N, w.GW + r + kk, N, w.Mbuf, w.CnT, A_out, core, map,
+                                    w.flag, st);
+      }
+    }
     if (solve == TS_SOLVE_RSVD) {
       const int N = r + k + s;
       TS_TRY(gemm3<T>(r, N, m, 1.0, Zt, Zm, r, yv, r + k, mv<T>(Y, s, 1), 0.0,
@@ -448,6 +492,23 @@ static ts_status rrf_all(const ts_tensor& X, const Shape& S, uint64_t seed, Work
   return TS_OK;
 }
 
+// BF16 precision form: Y_n^T into the last s_n rows of each mode's operand, once per
+// pass over T (the sketches are fixed between passes).
+template <typename T>
+static ts_status pack_rhs_bf16(const ts_tensor& X, const Shape& S, Work<T>& w, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (!S.bf16gram || S.kind != TS_TENSORSKETCH) return TS_OK;
+    for (int n = 0; n < S.N; ++n) {
+      if (!S.fused[n]) continue;
+      const int s = (int)X.dims[n];
+      const int first = bf16_cols(S, n, s) - s;
+      char* dst = static_cast<char*>(w.Bt[n]) + (size_t)first * 2 * gram_tc_ld(S.m);
+      TS_TRY(pack_bf16(w.Y[n], 1, s, s, S.m, dst, st));
+    }
+  }
+  return TS_OK;
+}
+
 // Y_n Omega(sweep, n) for sweeps [t0, t0 + nt) of every mode, one product per mode.
 template <typename T>
 static ts_status rhs_times_omegas(const ts_tensor& X, const Shape& S, Work<T>& w, int t0, int nt,
@@ -487,6 +548,7 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
     TS_TRY(phase(opt, 2, st));
     TS_TRY(sketch_rhs_all<T>(X, S, w, st));
     TS_TRY(phase(opt, 3, st));
+    TS_TRY(pack_rhs_bf16<T>(X, S, w, st));
     if (S.solve == TS_SOLVE_RSVD)
       TS_TRY(rhs_times_omegas<T>(X, S, w, 0, opt.resketch_each_sweep ? 1 : S.sweeps, st));
   } else {
@@ -501,6 +563,7 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
     if (S.kind == TS_TENSORSKETCH && opt.resketch_each_sweep && sweep > 0) {
       TS_TRY(build_ts_tables<T>(X, S, opt.seed, sweep, w, st));
       TS_TRY(sketch_rhs_all<T>(X, S, w, st));
+      TS_TRY(pack_rhs_bf16<T>(X, S, w, st));
       if (S.solve == TS_SOLVE_RSVD) TS_TRY(rhs_times_omegas<T>(X, S, w, sweep, 1, st));
     }
     for (int n = 0; n < N; ++n) {
@@ -534,8 +597,11 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
         yv = mv<T>(w.YOm + S.yom_off[n] + (size_t)sweep * S.kc[n], ldo, 1);
         yom = &yv;
       }
+      Bf16Op bop{w.Bt[n], S.kind == TS_TENSORSKETCH};
+      const Bf16Op* bf = (S.bf16gram && S.fused[n]) ? &bop : nullptr;
       TS_TRY(solve_subproblem<T>(m, S.r[n], (int)X.dims[n], S.ranks[n], S.solve, S.kc[n],
-                                 S.fp64solve, Om, ldo, yom, Yn, w, factors[n], core, map, st));
+                                 S.fp64solve, Om, ldo, yom, Yn, w, factors[n], core, map, st,
+                                 bf));
     }
     if (residual_out && opt.track_fit)
       TS_TRY(launch_fit_dense<T>(X, S.ranks, core, (const T* const*)factors, w.fitQ, w.fitacc,

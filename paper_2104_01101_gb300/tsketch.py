@@ -76,6 +76,8 @@ _PROTOS = {
     "tensorsketch_input": (I32, [TP, I32, PP, I32, P, P]),
     "range_finder_init_scratch_bytes": (SZ, [TP, I32, I32, I32, I32]),
     "range_finder_init": (I32, [TP, I32, I32, I32, I32, U64, P, P, SZ, P]),
+    "ts_gram_bf16_scratch_bytes": (SZ, [I32, I32, I32]),
+    "ts_gram_bf16": (I32, [I32, I32, I32, P, P, P, P, SZ, P]),
     "ts_lrls_scratch_bytes": (SZ, [I32, I32, I32, I32, I32, I32, I32]),
     "ts_lrls_solve": (I32, [I32, I32, I32, I32, I32, P, P, I32, U64, I32, I32, I32, I32, P, P, P,
                             SZ, P]),
@@ -261,6 +263,20 @@ def range_finder_init(X, mode: int, R: int, k1: int, k2: int, seed: int):
     return A
 
 
+def gram_bf16(A, B):
+    """C = bf16(A) bf16(B)^T with FP32 accumulation on the tensor cores; A (M, K) and
+    B (N, K) FP32 on the device."""
+    M, K = A.shape
+    N = B.shape[0]
+    Ac = A.contiguous()
+    Bc = B.contiguous()
+    Cout = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    scr = _scratch(lib().ts_gram_bf16_scratch_bytes(M, N, K), A.device)
+    _check(lib().ts_gram_bf16(M, N, K, _ptr(Ac), _ptr(Bc), _ptr(Cout), _ptr(scr), scr.numel(),
+                              _stream()))
+    return Cout
+
+
 def lrls_solve(Z, Y, R: int, solve: int = SOLVE_RSVD, seed: int = 0, sweep: int = 0, n: int = 0,
                oversample: int = 5, solve_fp64: bool = False):
     """Sketched rank-constrained LS; Z is (m, r) (any strides), Y is (m, s)."""
@@ -315,7 +331,7 @@ def fitness_residual(X, core, factors) -> float:
 
 
 def _options(seed, solve, oversample, rrf_k1, rrf_k2, resketch, init_given, track_fit,
-             solve_fp64=False, use_graph=False):
+             solve_fp64=False, use_graph=False, gram_bf16=False):
     o = _Options()
     o.seed = seed
     o.rrf_k1 = rrf_k1 or 0
@@ -323,7 +339,7 @@ def _options(seed, solve, oversample, rrf_k1, rrf_k2, resketch, init_given, trac
     o.rsvd_oversample = oversample
     o.solve = solve
     o.resketch_each_sweep = int(bool(resketch))
-    o.gram_bf16 = 0
+    o.gram_bf16 = int(bool(gram_bf16))
     o.init_given = int(bool(init_given))
     o.track_fit = int(bool(track_fit))
     o.solve_fp64 = int(bool(solve_fp64))
@@ -336,13 +352,13 @@ class TuckerPlan:
 
     def __init__(self, X, ranks, m, sweeps, kind=TENSORSKETCH, seed=0, solve=SOLVE_RSVD,
                  oversample=5, rrf_k1=None, rrf_k2=None, resketch=False, track_fit=False,
-                 want_residual=True, solve_fp64=False, use_graph=False):
+                 want_residual=True, solve_fp64=False, use_graph=False, gram_bf16=False):
         self.dims = _dims(X)
         self.N = len(self.dims)
         self.ranks = list(ranks)
         self.kind, self.m, self.sweeps = kind, m, sweeps
         self.opt = _options(seed, solve, oversample, rrf_k1, rrf_k2, resketch, False, track_fit,
-                            solve_fp64, use_graph)
+                            solve_fp64, use_graph, gram_bf16)
         self.track_fit = track_fit
         self.want_residual = want_residual
         dtype, dev = X.dtype, X.device
@@ -413,10 +429,10 @@ def cp_via_tucker(X, R_cp: int, tucker_ranks, m: int, tucker_sweeps: int, cp_swe
 def tucker_als_sketched(X, ranks, m: int, sweeps: int, kind=TENSORSKETCH, seed: int = 0,
                         solve=SOLVE_RSVD, oversample: int = 5, rrf_k1=None, rrf_k2=None,
                         resketch=False, init_factors=None, track_fit=False,
-                        want_residual=True, solve_fp64=False):
+                        want_residual=True, solve_fp64=False, gram_bf16=False):
     """Alg. 4.  Returns (core, factors, residuals tensor or None); raises TsError on breakdown."""
     plan = TuckerPlan(X, ranks, m, sweeps, kind, seed, solve, oversample, rrf_k1, rrf_k2, resketch,
-                      track_fit, want_residual, solve_fp64)
+                      track_fit, want_residual, solve_fp64, gram_bf16=gram_bf16)
     plan.run(X, init_factors)
     if plan.numeric_flag() != 0:
         raise TsError(6, "numerical breakdown flagged by the device (Z^T Z not positive definite "

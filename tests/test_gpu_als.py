@@ -119,6 +119,29 @@ def test_medium_dense_fp32_with_fp64_solve_matches_oracle(ts):
         assert np.abs(proj(fac[n].double().cpu().numpy()) - proj(f_o[n])).max() < 1e-4
 
 
+@pytest.mark.parametrize("solve", ["rsvd", "exact"])
+def test_medium_dense_bf16_gram_form_matches_oracle(ts, solve):
+    # precision form: every subproblem's [Z^T Z | Z^T Y Omega | Z^T Y] in BF16 on the tensor
+    # cores with FP32 accumulation.  BF16 stages are held to 1e-2 (relative) against the
+    # FP64 oracle, and the residual to 1e-3 absolute, the equal-residual criterion.
+    dims, ranks, m, sweeps, seed = (120, 120, 120), (10, 10, 10), 2000, 3, 5
+    kind = ts.SOLVE_RSVD if solve == "rsvd" else ts.SOLVE_EXACT
+    if solve == "exact":
+        ranks, m = (5, 5, 5), 400
+    T, _, _ = synth.dense_tucker(dims, ranks, 1e-2, seed=3, core_decay=0.9, dtype=np.float32)
+    core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, sweeps,
+                                            seed=seed, rrf_k1=15, track_fit=True, solve=kind,
+                                            gram_bf16=True)
+    _, f_o, r_o = tucker.sketch_tucker_als(T.astype(np.float64), ranks, m, sweeps, seed=seed,
+                                           rrf_k1=15, track_fit=True,
+                                           solve="rsvd" if solve == "rsvd" else "exact")
+    res, r_o = res.cpu().numpy(), np.asarray(r_o)
+    assert np.all(np.abs(res - r_o) <= 1e-2 * r_o)
+    assert np.all(np.abs(res - r_o) <= 1e-3)
+    for n in range(3):
+        assert np.abs(proj(fac[n].double().cpu().numpy()) - proj(f_o[n])).max() < 1e-2
+
+
 def test_graph_replay_matches_direct_enqueue(ts):
     # use_graph captures the decomposition once and replays it; replays must read the
     # current contents of the caller's buffers (here the tensor is rescaled in place).

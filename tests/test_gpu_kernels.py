@@ -245,3 +245,28 @@ def test_fitness_matches_direct_reconstruction(ts, dims, ranks, dtype):
     got = ts.fitness_residual(dev(T), coreg, Ag)
     tol = 1e-12 if dtype == torch.float64 else 1e-5
     assert abs(got - want) <= tol * want
+
+
+# ---------------------------------------------------------------- a7/a10 BF16 Gram products
+
+def _bf16_round(x):
+    """Round FP32 values to BF16 (nearest, ties to even), returned as FP32."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+@pytest.mark.parametrize("M,N,K", [(100, 515, 2000), (37, 70, 100), (128, 256, 64),
+                                   (200, 300, 1000), (1, 1, 1), (130, 129, 65)])
+def test_gram_bf16_matches_rounded_product(ts, M, N, K):
+    g = np.random.default_rng(M * 7 + N + K)
+    A = g.standard_normal((M, K)).astype(np.float32)
+    B = g.standard_normal((N, K)).astype(np.float32)
+    C = ts.gram_bf16(dev(A, torch.float32), dev(B, torch.float32)).cpu().numpy()
+    want = _bf16_round(A).astype(np.float64) @ _bf16_round(B).astype(np.float64).T
+    # products of BF16 values are exact in FP32: only the FP32 accumulation differs
+    scale = np.sqrt(K) * np.abs(_bf16_round(A)).max() * np.abs(_bf16_round(B)).max()
+    assert np.max(np.abs(C - want)) <= 4e-6 * scale
+    # and the rounding of the operands is what separates it from the FP64 product
+    exact = A.astype(np.float64) @ B.astype(np.float64).T
+    assert np.max(np.abs(C - exact)) <= 2e-2 * scale

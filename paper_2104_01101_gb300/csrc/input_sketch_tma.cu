@@ -8,7 +8,8 @@
 //   mode 2  Y2[H21(i1) + H23(i3), i2]  += S(i1,i3) T[i1,i2,i3]   (4 consecutive i2 after a
 //           transpose of the 16 x 16 micro-block in per-warp shared memory)
 //   mode 1  Y1[H12(i2) + H13(i3), i1]  += S(i2,i3) T[i1,i2,i3]   (shared-memory buckets of
-//           the current slice i1, double-buffered, flushed when i1 changes)
+//           the current slice i1 in 32-bit fixed point, double-buffered, flushed when i1
+//           changes; see below)
 // Warp roles: one producer warp streams tiles with TMA tensor loads into a ring of
 // shared-memory stages (full / empty mbarriers); the consumer warps split every tile
 // into 16 x 16 micro-blocks.  A CTA walks a contiguous, slice-major range of tiles, so
@@ -16,6 +17,18 @@
 // on expiry the kernel records TS_ERR_TIMEOUT in the caller's flag, the warps fall
 // through the remaining tiles without computing (so the consumer barriers stay
 // matched), and the producer waits, again bounded, for its loads in flight.
+//
+// Mode-1 buckets in fixed point.  Shared-memory float adds are a compare-and-swap loop on
+// this GPU (measured: 4 lane-ops per clock per SM at random addresses, against 14.5 for
+// 32-bit integer adds), so each slice's buckets accumulate integers: a value v becomes
+// round(v * 2^q / B), where B is the largest |v| of the first tile of the slice that this
+// CTA reads, and q (<= 22) leaves room for the largest number of entries any bucket can
+// receive, bounded by min(s2 * mult(H13), s3 * mult(H12)) with mult the largest number of
+// indices sharing one bucket in a table (q < 18, e.g. degenerate tables that send whole
+// slices to one bucket: no fixed point, every value goes to L2 in FP32).  Integer sums are exact and independent of the
+// order of the adds; the flush multiplies by B / 2^q.  Values with |v| > B (rare: larger
+// than everything in the slice's first tile) are added to the sketch in L2 directly, in
+// FP32.  The quantisation error of one entry is at most B 2^-(q+1).
 #include <cuda.h>
 
 #include "internal.cuh"
@@ -105,6 +118,23 @@ __device__ __forceinline__ void red_shared_add(float* p, float v) {
   asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(smem_u32(p)), "f"(v) : "memory");
 }
 
+// *p += v in shared memory (32-bit integer add, no return value).
+__device__ __forceinline__ void red_shared_add_s32(int* p, int v) {
+  asm volatile("red.shared.add.s32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+
+// round(x) for |x| <= 2^22: adding 1.5 * 2^23 leaves the rounded integer in the low
+// mantissa bits (round-to-nearest-even of the float addition).
+__device__ __forceinline__ int round_small(float x, float scale) {
+  return __float_as_int(fmaf(x, scale, 12582912.0f)) - 0x4B400000;
+}
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
 // Flip the sign of x when the sign bit of s is set.
 __device__ __forceinline__ float apply_sign(float x, int s) {
   return __int_as_float(__float_as_int(x) ^ (s & (int)0x80000000));
@@ -131,6 +161,8 @@ __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_con
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full_bar[kMaxStages], empty_bar[kMaxStages];
   __shared__ int abort_flag;
+  __shared__ int q1_mult[2];    // largest bucket multiplicity of H12 and H13 (mode 1)
+  __shared__ int q1_max[2];     // per bucket buffer: largest |v| bits of the slice's first tile
   const int TB2 = d.TB2, TB3 = d.TB3, S = d.stages;
   const int tile_elems = TB2 * TB3;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -138,7 +170,7 @@ __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_con
   const int m1b = d.Y1 ? d.m1 : 0;
   const SmemLayout L = smem_layout(S, tile_elems, m1b, d.tiles2 * TB2, d.tiles3 * TB3);
   float* stage = reinterpret_cast<float*>(smem_raw);
-  float* acc1 = reinterpret_cast<float*>(smem_raw + L.acc1);
+  int* acc1 = reinterpret_cast<int*>(smem_raw + L.acc1);  // mode-1 buckets, fixed point
   int2* rowtab = reinterpret_cast<int2*>(smem_raw + L.rowtab);  // {H12, H32} per i2 (reduced)
   int2* coltab = reinterpret_cast<int2*>(smem_raw + L.coltab);  // {H13, H23} per i3 (reduced)
   float* scratch = reinterpret_cast<float*>(smem_raw + L.scratch);
@@ -168,9 +200,11 @@ __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_con
     }
     coltab[i] = v;
   }
-  for (int i = tid; i < 2 * m1b; i += blockDim.x) acc1[i] = 0.f;
+  for (int i = tid; i < 2 * m1b; i += blockDim.x) acc1[i] = 0;
   if (tid == 0) {
     abort_flag = 0;
+    q1_mult[0] = q1_mult[1] = 0;
+    q1_max[0] = q1_max[1] = 0;
     for (int s = 0; s < S; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full_bar[s])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&empty_bar[s])),
@@ -226,30 +260,52 @@ __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_con
         const int col = 4 * cq + c, row = rq + 8 * h;
         st_off[h][c] = col * kTrs + (row ^ ((col >> 3) << 3));
       }
+    // mode-1 fixed point (see the header): the precision q from the tables' bucket
+    // multiplicities; the scale per slice from the first tile of the slice
+    int qbits = 0;
+    if (d.Y1) {
+      int* hist12 = acc1;
+      int* hist13 = acc1 + m1b;
+      int mx12 = 0, mx13 = 0;
+      for (int i = tid; i < d.s2; i += kConsumers * 32)
+        mx12 = max(mx12, atomicAdd(hist12 + entry_bin(rowtab[i].x), 1) + 1);
+      for (int i = tid; i < d.s3; i += kConsumers * 32)
+        mx13 = max(mx13, atomicAdd(hist13 + entry_bin(coltab[i].x), 1) + 1);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        mx12 = max(mx12, __shfl_xor_sync(0xffffffffu, mx12, o));
+        mx13 = max(mx13, __shfl_xor_sync(0xffffffffu, mx13, o));
+      }
+      if (lane == 0) {
+        atomicMax(&q1_mult[0], mx12);
+        atomicMax(&q1_mult[1], mx13);
+      }
+      asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory");
+      for (int i = tid; i < 2 * m1b; i += kConsumers * 32) acc1[i] = 0;
+      const long bound = min((long)d.s2 * q1_mult[1], (long)d.s3 * q1_mult[0]);
+      qbits = 22;
+      while (qbits > 0 && ((long)1 << qbits) * bound > 2147483647l) --qbits;
+      if (qbits < 18) qbits = 0;  // too coarse: every value goes to L2 in FP32 instead
+    }
     int buf = 0;
+    float q_lim = 0.f, q_scale = 0.f, q_back = 0.f;  // this slice's fixed-point scale
     int cur_i1 = -1, h21 = 0, h31 = 0;
     bool aborted = false;
     int i1 = (int)(t_begin / tiles_per_slice);
     int w = (int)(t_begin - (long)i1 * tiles_per_slice);  // tile within the slice
     int mb0 = warp;  // first micro-block of this warp in the current tile
+    // every consumer warp runs this at the start of a slice (same control flow in all)
+    auto flush1 = [&](int slice, int b_, float back) {
+      int* a = acc1 + b_ * m1b;
+      for (int b = tid; b < d.m1; b += kConsumers * 32) {
+        const int q = a[b];
+        if (q != 0) atomicAdd(d.Y1 + (long)b * d.s1 + slice, (float)q * back);
+        a[b] = 0;
+      }
+    };
     for (int lt = 0; lt < ntl; ++lt) {
       const int s = lt % S;
       const int r0 = (w / d.tiles3) * TB2, c0 = (w - (w / d.tiles3) * d.tiles3) * TB3;
-      if (i1 != cur_i1) {
-        if (d.Y1 && cur_i1 >= 0) {  // new slice: flush the previous slice's buckets
-          asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory");
-          float* a = acc1 + buf * m1b;
-          for (int b = tid; b < d.m1; b += kConsumers * 32) {
-            const float v = a[b];
-            if (v != 0.f) atomicAdd(d.Y1 + (long)b * d.s1 + cur_i1, v);
-            a[b] = 0.f;
-          }
-          buf ^= 1;
-        }
-        cur_i1 = i1;
-        if (d.Y2) h21 = reduced(d.t21[i1], d.m2);
-        if (d.Y3) h31 = reduced(d.t31[i1], d.m3);
-      }
       if (!aborted) {
         aborted = *(volatile int*)&abort_flag != 0;
         if (!aborted && !mbar_wait(smem_u32(&full_bar[s]), (unsigned)((lt / S) & 1))) {
@@ -257,9 +313,47 @@ __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_con
           aborted = true;
         }
       }
+      const float* tile = stage + (size_t)s * tile_elems;
+      if (i1 != cur_i1) {
+        if (d.Y1) {
+          // all warps are done with the previous slice's buckets; reset the new slice's max
+          if (tid == 0) q1_max[buf ^ 1] = 0;
+          asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory");
+          if (cur_i1 >= 0) {
+            flush1(cur_i1, buf, q_back);
+            buf ^= 1;
+          }
+          // largest |v| of this tile (the slice's first tile in this CTA's walk)
+          float mx = 0.f;
+          if (!aborted)
+            for (int mb = mb0; mb < nmb; mb += kConsumers) {
+              const int rr0 = (mb / nmb3) * 16, cc0 = (mb - (mb / nmb3) * nmb3) * 16;
+              const float* tp = tile + (rr0 + rq) * TB3 + cc0 + 4 * cq;
+              const float4 x0 = *reinterpret_cast<const float4*>(tp);
+              const float4 x1 = *reinterpret_cast<const float4*>(tp + 8 * TB3);
+              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x0.x), fabsf(x0.y)), fmaxf(fabsf(x0.z), fabsf(x0.w))));
+              mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x1.x), fabsf(x1.y)), fmaxf(fabsf(x1.z), fabsf(x1.w))));
+            }
+          mx = warp_max(mx);
+          if (lane == 0) atomicMax(&q1_max[buf], __float_as_int(mx));
+          asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory");
+          const float B = __int_as_float(q1_max[buf]);
+          if (qbits > 0 && B > 0.f && B < 1e30f) {
+            q_lim = B;
+            q_scale = (float)(1 << qbits) / B;
+            q_back = B / (float)(1 << qbits);
+          } else {
+            q_lim = -1.f;  // no fixed point for this slice: every value goes to L2
+            q_scale = 0.f;
+            q_back = 0.f;
+          }
+        }
+        cur_i1 = i1;
+        if (d.Y2) h21 = reduced(d.t21[i1], d.m2);
+        if (d.Y3) h31 = reduced(d.t31[i1], d.m3);
+      }
       if (!aborted) {
-        const float* tile = stage + (size_t)s * tile_elems;
-        float* a1 = acc1 + buf * m1b;
+        int* a1 = acc1 + buf * m1b;
         const int b21 = entry_bin(h21), b31 = entry_bin(h31);
         for (int mb = mb0; mb < nmb; mb += kConsumers) {
           const int rr0 = (mb / nmb3) * 16, cc0 = (mb - (mb / nmb3) * nmb3) * 16;
@@ -278,9 +372,14 @@ __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_con
 #pragma unroll
             for (int h = 0; h < 2; ++h)
 #pragma unroll
-              for (int c = 0; c < 4; ++c)
-                red_shared_add(a1 + add_mod(entry_bin(rt[h].x), entry_bin(c13[c]), d.m1),
-                               apply_sign(v[h][c], rt[h].x ^ c13[c]));
+              for (int c = 0; c < 4; ++c) {
+                const int b = add_mod(entry_bin(rt[h].x), entry_bin(c13[c]), d.m1);
+                const float sv = apply_sign(v[h][c], rt[h].x ^ c13[c]);
+                if (fabsf(sv) <= q_lim)
+                  red_shared_add_s32(a1 + b, round_small(sv, q_scale));
+                else
+                  atomicAdd(d.Y1 + (long)b * d.s1 + i1, sv);
+              }
           }
           if (d.Y3 && i3 < d.s3) {
 #pragma unroll
@@ -323,11 +422,7 @@ __global__ void __launch_bounds__(kThreads) k_sketch_dense3_tma(const __grid_con
     }
     if (d.Y1) {
       asm volatile("bar.sync 1, %0;" ::"n"(kConsumers * 32) : "memory");
-      const float* a = acc1 + buf * m1b;
-      for (int b = tid; b < d.m1; b += kConsumers * 32) {
-        const float v = a[b];
-        if (v != 0.f) atomicAdd(d.Y1 + (long)b * d.s1 + cur_i1, v);
-      }
+      flush1(cur_i1, buf, q_back);
     }
   }
   __syncthreads();

@@ -91,6 +91,36 @@ def test_input_sketch_dense(ts, dims, m, dtype):
         assert np.linalg.norm(Y - want) <= tol * np.linalg.norm(want)
 
 
+@pytest.mark.parametrize("case", ["late_spikes", "scaled_slices", "one_bucket_tables"])
+def test_input_sketch_dense_fixed_point_edges(ts, case):
+    # The FP32 order-3 kernel keeps each slice's mode-1 buckets in 32-bit fixed point
+    # scaled by the largest value of the slice's first tile; larger values take an FP32
+    # path, and tables that send too many entries to one bucket disable fixed point.
+    dims, m = (50, 100, 172), 300
+    g = np.random.default_rng(11)
+    T = g.standard_normal(dims).astype(np.float32)
+    if case == "late_spikes":
+        T[::7, -1, -4:] = 3e4          # in the last tile of those slices
+    if case == "scaled_slices":
+        T *= (10.0 ** g.integers(-6, 4, size=dims[0]))[:, None, None].astype(np.float32)
+    tabs = packed_tables(13, dims, 0, m)
+    if case == "one_bucket_tables":
+        for k in (1, 2):
+            b, sg = tabs[k][:2]
+            b = np.zeros_like(b)
+            tabs[k] = (b, sg, dev(rng.pack_table(b, sg)))
+    Y = ts.tensorsketch_input(dev(T), 0, [None, tabs[1][2], tabs[2][2]], m).cpu().numpy()
+    want = sketch.input_sketch_dense(T.astype(np.float64), 0, [tabs[1][:2], tabs[2][:2]], m)
+    # FP32 summation error is relative to the sum of |terms| of each bucket: with one
+    # bucket per slice (17200 cancelling terms) that, not the sum, is the scale
+    ref = want
+    if case == "one_bucket_tables":
+        ref = sketch.input_sketch_dense(np.abs(T).astype(np.float64), 0,
+                                        [(tabs[k][0], np.ones_like(tabs[k][1])) for k in (1, 2)], m)
+    for i in range(dims[0]):
+        assert np.linalg.norm(Y[:, i] - want[:, i]) <= 1e-5 * np.linalg.norm(ref[:, i])
+
+
 def test_input_sketch_dense_full_size_sampled_columns(ts):
     # The 400^3 FP32 workload: compare a few whole columns Y_n[:, i] with the oracle
     # applied to the slab T(i along mode n), plus the squared-norm invariant.

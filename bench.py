@@ -301,7 +301,7 @@ def run_ours(args, rank, world):
 # workload, from the ncu capture in profiles/input_sketch_dense400_fp32.md.  The figure
 # belongs to the kernel source it was taken on: another source reports null.
 SKETCH_TRAFFIC_BYTES = 271.7e6
-SKETCH_SOURCE_SHA1 = "5c2f4c508c50"
+SKETCH_SOURCE_SHA1 = "4cf4b8dc9a81"
 
 
 def sketch_traffic():

@@ -333,6 +333,52 @@ ts_status cp_via_tucker(const ts_tensor* X, int32_t R_cp, const int32_t* tucker_
                         void* workspace, size_t workspace_bytes, void* const* cp_factors_out,
                         double* residual_out, ts_stream stream);
 
+/* ------------------------------------------------------------------------- */
+/* Batched Sketch-Tucker-ALS: Alg. 4 on many independent dense tensors at once.
+ *
+ * Tensor i of `count` (X[i], HOST array of descriptors; one order N and dtype for the
+ * batch) has ranks ranks[i*N .. i*N+N) (HOST), sketch size m[i] (HOST), and is
+ * decomposed exactly as tucker_als_sketched decomposes it with the same options and
+ * seed opt->seed + i (TensorSketch, Init-RRF unless opt->init_given, opt->solve); the
+ * results equal that call's up to the summation order of the sketched products.
+ * Every subproblem must fit the single-block solve (TS_ERR_UNSUPPORTED otherwise);
+ * resketch_each_sweep, gram_bf16 and use_graph are not offered (TS_ERR_UNSUPPORTED).
+ *
+ * ts_batch_prepare: cores (HOST array of count device pointers, prod ranks, C order) and
+ * factors (HOST array of count*N device pointers, tensor i's factor k at i*N + k,
+ * dims[k] x ranks[k] row-major, holding the initial factors when opt->init_given) are
+ * kept by the batch and updated in place by the sweeps.  Runs the setup of every
+ * tensor (tables, the one-pass sketches, Init-RRF, the Gaussians of every sweep and
+ * their products with the sketches), writes the per-subproblem launch descriptors into
+ * the workspace, and times the product kernel with its two tile shapes on this batch
+ * to keep the faster one per mode (the autotuner); synchronises `stream`.  *batch_out:
+ * an opaque HOST handle, released with ts_batch_destroy (not before the work it
+ * enqueued has finished).
+ * ts_batch_sweeps: enqueues sweeps [first, first + nsweeps) of every tensor (in order;
+ * sweep t uses the Gaussians of sweep t): per mode, four kernel launches over the whole
+ * batch (factor CountSketch + FFT, Hadamard product + inverse FFT, the products
+ * [Z^T Z | Z^T Y Omega | Z^T Y], the single-block solves); nothing else, so the call can
+ * be captured in a CUDA graph.
+ * ts_batch_residuals: residuals (DEVICE, count doubles) = the relative residual of each
+ * tensor's current decomposition.
+ * ts_batch_flags: flags_out (HOST, count int32) = each tensor's numerical-breakdown flag
+ * (0: none); synchronous.
+ * ts_batch_tiles: tiles_out (HOST, N int32) = the product tile kept per mode; ms_out
+ * (HOST, 2N floats, nullable) = the measured times of tiles 32 and 64 per mode. */
+typedef void* ts_batch;
+ts_status ts_batch_workspace_bytes(int32_t count, const ts_tensor* X, const int32_t* ranks,
+                                   const int32_t* m, int32_t sweeps, const ts_options* opt,
+                                   size_t* bytes_out);
+ts_status ts_batch_prepare(int32_t count, const ts_tensor* X, const int32_t* ranks,
+                           const int32_t* m, int32_t sweeps, const ts_options* opt,
+                           void* workspace, size_t workspace_bytes, void* const* cores,
+                           void* const* factors, ts_batch* batch_out, ts_stream stream);
+ts_status ts_batch_sweeps(ts_batch batch, int32_t first, int32_t nsweeps, ts_stream stream);
+ts_status ts_batch_residuals(ts_batch batch, double* residuals, ts_stream stream);
+ts_status ts_batch_flags(ts_batch batch, int32_t* flags_out);
+ts_status ts_batch_tiles(ts_batch batch, int32_t* tiles_out, float* ms_out);
+void ts_batch_destroy(ts_batch batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -169,21 +169,11 @@ __device__ Cx<T>* fft_run(Cx<T>* a, Cx<T>* b, const FftPlan& plan,
   return a;
 }
 
-struct ChainDesc {
-  int nf;
-  int total_cols;
-  const void* factors[TS_MAX_ORDER];
-  int64_t rows[TS_MAX_ORDER];
-  int cols[TS_MAX_ORDER];
-  int colbase[TS_MAX_ORDER];
-  const int32_t* tables[TS_MAX_ORDER];
-};
-
-// Block b: flat factor columns 2b (real part) and 2b+1 (imaginary part).
+// Block bx: flat factor columns 2 bx (real part) and 2 bx + 1 (imaginary part).
 template <typename T>
-__global__ void __launch_bounds__(512) k_factor_spectra(ChainDesc d, FftPlan plan,
-                                                        const Cx<T>* __restrict__ tw,
-                                                        Cx<T>* __restrict__ spectra) {
+__device__ __forceinline__ void factor_spectra_body(const ChainDesc& d, const FftPlan& plan,
+                                                    const Cx<T>* __restrict__ tw,
+                                                    Cx<T>* __restrict__ spectra, int bx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = plan.m;
   Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw);
@@ -194,7 +184,7 @@ __global__ void __launch_bounds__(512) k_factor_spectra(ChainDesc d, FftPlan pla
     for (int i = threadIdx.x; i < m; i += blockDim.x) tws[i] = tw[i];
     twp = tws;
   }
-  const int c0 = 2 * blockIdx.x;
+  const int c0 = 2 * bx;
   const int c1 = c0 + 1;
   for (int i = threadIdx.x; i < m; i += blockDim.x) a[i] = Cx<T>{0, 0};
   __syncthreads();
@@ -230,12 +220,20 @@ __global__ void __launch_bounds__(512) k_factor_spectra(ChainDesc d, FftPlan pla
   }
 }
 
-// Block b: Z columns 2b and 2b+1 (column multi-index, factor 0 slowest).
 template <typename T>
-__global__ void __launch_bounds__(512) k_hadamard_ifft(ChainDesc d, int ncols, FftPlan plan,
-                                                       const Cx<T>* __restrict__ tw,
-                                                       const Cx<T>* __restrict__ spectra,
-                                                       T* __restrict__ Z) {
+__global__ void __launch_bounds__(512) k_factor_spectra(ChainDesc d, FftPlan plan,
+                                                        const Cx<T>* __restrict__ tw,
+                                                        Cx<T>* __restrict__ spectra) {
+  factor_spectra_body<T>(d, plan, tw, spectra, blockIdx.x);
+}
+
+// Block bx: Z columns 2 bx and 2 bx + 1 (column multi-index, factor 0 slowest).
+template <typename T>
+__device__ __forceinline__ void hadamard_ifft_body(const ChainDesc& d, int ncols,
+                                                   const FftPlan& plan,
+                                                   const Cx<T>* __restrict__ tw,
+                                                   const Cx<T>* __restrict__ spectra,
+                                                   T* __restrict__ Z, int bx) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = plan.m;
   Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw);
@@ -246,7 +244,7 @@ __global__ void __launch_bounds__(512) k_hadamard_ifft(ChainDesc d, int ncols, F
     for (int i = threadIdx.x; i < m; i += blockDim.x) tws[i] = tw[i];
     twp = tws;
   }
-  const int c0 = 2 * blockIdx.x;
+  const int c0 = 2 * bx;
   const bool has1 = c0 + 1 < ncols;
   int sp0[TS_MAX_ORDER], sp1[TS_MAX_ORDER];
   {
@@ -278,6 +276,75 @@ __global__ void __launch_bounds__(512) k_hadamard_ifft(ChainDesc d, int ncols, F
 }
 
 template <typename T>
+__global__ void __launch_bounds__(512) k_hadamard_ifft(ChainDesc d, int ncols, FftPlan plan,
+                                                       const Cx<T>* __restrict__ tw,
+                                                       const Cx<T>* __restrict__ spectra,
+                                                       T* __restrict__ Z) {
+  hadamard_ifft_body<T>(d, ncols, plan, tw, spectra, Z, blockIdx.x);
+}
+
+// Many independent chains (one per blockIdx.y), each as in launch_ts_apply.
+template <typename T>
+__global__ void __launch_bounds__(512) k_factor_spectra_batched(const TsChainJob<T>* __restrict__ jobs) {
+  const TsChainJob<T>& j = jobs[blockIdx.y];
+  if ((int)blockIdx.x * 2 >= j.d.total_cols) return;
+  factor_spectra_body<T>(j.d, j.plan, j.tw, j.spectra, blockIdx.x);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) k_hadamard_ifft_batched(const TsChainJob<T>* __restrict__ jobs) {
+  const TsChainJob<T>& j = jobs[blockIdx.y];
+  if ((int)blockIdx.x * 2 >= j.ncols) return;
+  hadamard_ifft_body<T>(j.d, j.ncols, j.plan, j.tw, j.spectra, j.Z, blockIdx.x);
+}
+
+template <typename T>
+TsChainJob<T> make_chain_job(int nf, const T* const* factors, const int64_t* rows,
+                             const int* cols, const int32_t* const* tables, int m,
+                             const Cx<T>* tw, Cx<T>* spectra, T* Z) {
+  TsChainJob<T> j{};
+  ChainDesc& d = j.d;
+  d.nf = nf;
+  int total = 0;
+  long ncols = 1;
+  for (int f = 0; f < nf; ++f) {
+    d.factors[f] = factors[f];
+    d.rows[f] = rows[f];
+    d.cols[f] = cols[f];
+    d.colbase[f] = total;
+    d.tables[f] = tables[f];
+    total += cols[f];
+    ncols *= cols[f];
+  }
+  d.total_cols = total;
+  j.ncols = (int)ncols;
+  j.plan = make_fft_plan(m);
+  j.plan.stage_tw = 3 * (size_t)m * sizeof(Cx<T>) <= kMaxSmem ? 1 : 0;
+  j.tw = tw;
+  j.spectra = spectra;
+  j.Z = Z;
+  return j;
+}
+
+template <typename T>
+size_t chain_job_smem(const TsChainJob<T>& j) {
+  return (2 + j.plan.stage_tw) * (size_t)j.plan.m * sizeof(Cx<T>);
+}
+
+template <typename T>
+ts_status launch_ts_apply_batched(const TsChainJob<T>* jobs, int count, int max_spectra_blocks,
+                                  int max_z_blocks, size_t smem, cudaStream_t st) {
+  if (count < 1) return TS_OK;
+  TS_TRY(ensure_dynamic_smem((const void*)k_factor_spectra_batched<T>, smem));
+  TS_TRY(ensure_dynamic_smem((const void*)k_hadamard_ifft_batched<T>, smem));
+  k_factor_spectra_batched<T><<<dim3(max_spectra_blocks, count), 512, smem, st>>>(jobs);
+  TS_LAUNCH_CHECK();
+  k_hadamard_ifft_batched<T><<<dim3(max_z_blocks, count), 512, smem, st>>>(jobs);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+template <typename T>
 ts_status launch_ts_apply(int nf, const T* const* factors, const int64_t* rows, const int* cols,
                           const int32_t* const* tables, int m, const Cx<T>* tw, Cx<T>* spectra,
                           T* Z, cudaStream_t st) {
@@ -306,6 +373,17 @@ ts_status launch_ts_apply(int nf, const T* const* factors, const int64_t* rows, 
   TS_LAUNCH_CHECK();
   return TS_OK;
 }
+
+#define TS_INST_CHAIN(T)                                                                   \
+  template TsChainJob<T> make_chain_job<T>(int, const T* const*, const int64_t*, const int*,   \
+                                           const int32_t* const*, int, const Cx<T>*, Cx<T>*,  \
+                                           T*);                                               \
+  template size_t chain_job_smem<T>(const TsChainJob<T>&);                                     \
+  template ts_status launch_ts_apply_batched<T>(const TsChainJob<T>*, int, int, int, size_t,   \
+                                                cudaStream_t);
+TS_INST_CHAIN(float)
+TS_INST_CHAIN(double)
+#undef TS_INST_CHAIN
 
 template ts_status launch_twiddles<float>(int, Cx<float>*, cudaStream_t);
 template ts_status launch_twiddles<double>(int, Cx<double>*, cudaStream_t);

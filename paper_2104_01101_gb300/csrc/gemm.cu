@@ -30,17 +30,18 @@ __device__ __forceinline__ T b_at(const MatView<T>& B1, int n1, const MatView<T>
 // C tile BM x BN over K range [kbeg, kend) of this split.  256 threads as 16 x 16, each
 // owning a TM x TN register tile; As and Bs hold the current K tile (k-major rows).
 template <typename T, int BM, int BN>
-__global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, MatView<T> A,
-                                             MatView<T> B1, int n1, MatView<T> B2, int n2,
-                                             MatView<T> B3, T alpha, T beta, OutView<T> C,
-                                             T* __restrict__ partial) {
+__device__ __forceinline__ void gemm_tile(int M, int N, int K, int kchunk, const MatView<T>& A,
+                                          const MatView<T>& B1, int n1, const MatView<T>& B2,
+                                          int n2, const MatView<T>& B3, T alpha, T beta,
+                                          const OutView<T>& C, T* __restrict__ partial, int bx,
+                                          int by, int bz) {
   constexpr int TM = BM / 16, TN = BN / 16;         // outputs per thread: TM x TN
   constexpr int LA = BM * BK / NT, LB = BN * BK / NT;  // tile elements each thread fetches
   __shared__ __align__(16) T As[BK][BM + 4];
   __shared__ __align__(16) T Bs[BK][BN + 4];
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int kbeg = blockIdx.z * kchunk;
+  const int m0 = by * BM, n0 = bx * BN;
+  const int kbeg = bz * kchunk;
   const int kend = min(K, kbeg + kchunk);
   const bool a_kfast = (A.cs == 1);
   const MatView<T>& Bv = n0 < n1 ? B1 : (n0 < n2 ? B2 : B3);  // view this tile starts in
@@ -123,13 +124,43 @@ __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, Ma
       const int gj = n0 + tx * TN + j;
       if (gj >= N) continue;
       if (partial) {
-        partial[blockIdx.z * MN + (size_t)gi * N + gj] = acc[i][j];
+        partial[bz * MN + (size_t)gi * N + gj] = acc[i][j];
       } else {
         T* c = C.p + (long)gi * C.rs + (long)gj * C.cs;
         *c = beta == (T)0 ? alpha * acc[i][j] : alpha * acc[i][j] + beta * *c;
       }
     }
   }
+}
+
+template <typename T, int BM, int BN>
+__global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, MatView<T> A,
+                                             MatView<T> B1, int n1, MatView<T> B2, int n2,
+                                             MatView<T> B3, T alpha, T beta, OutView<T> C,
+                                             T* __restrict__ partial) {
+  gemm_tile<T, BM, BN>(M, N, K, kchunk, A, B1, n1, B2, n2, B3, alpha, beta, C, partial,
+                       blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
+// Independent products, one per blockIdx.z, each C = A [B1 | B2 | B3] (no split).
+template <typename T, int BM, int BN>
+__global__ void __launch_bounds__(NT) k_gemm_batched(const GemmJob<T>* __restrict__ jobs) {
+  const GemmJob<T>& j = jobs[blockIdx.z];
+  if ((int)blockIdx.x * BN >= j.N || (int)blockIdx.y * BM >= j.M) return;
+  gemm_tile<T, BM, BN>(j.M, j.N, j.K, ((j.K + BK - 1) / BK) * BK, j.A, j.B1, j.n1, j.B2, j.n2,
+                       j.B3, (T)1, (T)0, j.C, nullptr, blockIdx.x, blockIdx.y, 0);
+}
+
+template <typename T>
+ts_status launch_gemm_batched(const GemmJob<T>* jobs, int count, int maxM, int maxN, int tile,
+                              cudaStream_t st) {
+  if (count < 1 || maxM < 1 || maxN < 1) return TS_OK;
+  if (tile == 32)
+    k_gemm_batched<T, 32, 32><<<dim3(ceil_div(maxN, 32), ceil_div(maxM, 32), count), NT, 0, st>>>(jobs);
+  else
+    k_gemm_batched<T, 64, 64><<<dim3(ceil_div(maxN, 64), ceil_div(maxM, 64), count), NT, 0, st>>>(jobs);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
 }
 
 template <typename T>
@@ -219,6 +250,7 @@ ts_status gemm(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B, do
   template ts_status gemm2<T>(int, int, int, double, MatView<T>, MatView<T>, int, MatView<T>,   \
                               double, OutView<T>, const GemmSplit<T>*, cudaStream_t);           \
   template ts_status launch_split_reduce<T>(int, int, int, const T*, T*, long, cudaStream_t);    \
+  template ts_status launch_gemm_batched<T>(const GemmJob<T>*, int, int, int, int, cudaStream_t); \
   template ts_status gemm3<T>(int, int, int, double, MatView<T>, MatView<T>, int, MatView<T>,   \
                               int, MatView<T>, double, OutView<T>, const GemmSplit<T>*,         \
                               cudaStream_t);

@@ -48,6 +48,38 @@ template <typename T>
 int fft_max_len();
 template <typename T>
 ts_status launch_twiddles(int m, Cx<T>* tw, cudaStream_t st);
+// The factor chain of one TensorSketch: factors, their rows and columns, their tables.
+struct ChainDesc {
+  int nf;
+  int total_cols;
+  const void* factors[TS_MAX_ORDER];
+  int64_t rows[TS_MAX_ORDER];
+  int cols[TS_MAX_ORDER];
+  int colbase[TS_MAX_ORDER];
+  const int32_t* tables[TS_MAX_ORDER];
+};
+// One TensorSketch of a batch: chain, FFT plan, twiddles, spectra scratch, output Z.
+template <typename T>
+struct TsChainJob {
+  ChainDesc d;
+  FftPlan plan;
+  int ncols;  // prod cols: the columns of Z
+  const Cx<T>* tw;
+  Cx<T>* spectra;
+  T* Z;
+};
+template <typename T>
+TsChainJob<T> make_chain_job(int nf, const T* const* factors, const int64_t* rows,
+                             const int* cols, const int32_t* const* tables, int m,
+                             const Cx<T>* tw, Cx<T>* spectra, T* Z);
+template <typename T>
+size_t chain_job_smem(const TsChainJob<T>& j);
+// jobs: device array of count chain jobs; the grids are max_spectra_blocks (ceil of the
+// largest total_cols / 2) and max_z_blocks (ceil of the largest ncols / 2) by count;
+// smem: the largest chain_job_smem.
+template <typename T>
+ts_status launch_ts_apply_batched(const TsChainJob<T>* jobs, int count, int max_spectra_blocks,
+                                  int max_z_blocks, size_t smem, cudaStream_t st);
 // Z (column-major m x prod cols) = TensorSketch of factors[0] (x) ... (x) factors[nf-1].
 // spectra: scratch of (sum cols) * m complex values; tw: twiddles from launch_twiddles.
 template <typename T>
@@ -114,6 +146,18 @@ ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
                 MatView<T> B2, int n2, MatView<T> B3, double beta, OutView<T> C,
                 const GemmSplit<T>* split, cudaStream_t st);
 constexpr int kGemmCounters = 4096;
+// One product of a batch: C (M x N) = A (M x K) [B1 | B2 | B3] (columns [0, n1) of B from
+// B1, [n1, n2) from B2, [n2, N) from B3).
+template <typename T>
+struct GemmJob {
+  int M, N, K, n1, n2;
+  MatView<T> A, B1, B2, B3;
+  OutView<T> C;
+};
+// jobs: device array of count products; grid from the largest M and N; tile 32 or 64.
+template <typename T>
+ts_status launch_gemm_batched(const GemmJob<T>* jobs, int count, int maxM, int maxN, int tile,
+                              cudaStream_t st);
 // C (M x N, row stride ldc) = sum over splits of partial (split-major M x N).
 template <typename T>
 ts_status launch_split_reduce(int M, int N, int splits, const T* partial, T* C, long ldc,
@@ -177,6 +221,34 @@ ts_status launch_eig_small(int n, int R, const T* K, const T* Q, int r, T* CnT, 
 size_t lrls_fused_smem_bytes(int r, int s, int k, int R, int solve, size_t tsize, bool fp64,
                              bool* m_smem);
 bool lrls_fused_supported(int r, int s, int k, int R, int solve, size_t tsize, bool fp64);
+// Arguments of the single-block solve of one subproblem (see launch_lrls_fused).
+template <typename T>
+struct FusedArgs {
+  int r, s, k, R, solve;
+  const T* G;
+  long ldg;  // r x r
+  const T* W;
+  long ldw;  // r x k (RSVD)
+  const T* H;
+  long ldh;   // r x s
+  T* Mbuf;    // k x s when D is not kept on chip
+  T* CnT;     // r x R out (may be null)
+  T* A_out;   // s x R out
+  T* core;    // may be null
+  CoreMap map;
+  int* flag;
+  bool m_smem;
+};
+// The arguments and dynamic shared memory of one subproblem; TS_ERR_SHAPE when it does
+// not fit one block.
+template <typename T>
+ts_status make_fused_args(int r, int s, int k, int R, int solve, bool fp64, const T* G, long ldg,
+                          const T* W, long ldw, const T* H, long ldh, T* Mbuf, T* CnT, T* A_out,
+                          T* core, CoreMap map, int* flag, FusedArgs<T>* out, size_t* smem);
+// count subproblems (device array of arguments), one block each; smem: the largest.
+template <typename T>
+ts_status launch_lrls_fused_batched(const FusedArgs<T>* args, int count, bool fp64, size_t smem,
+                                    cudaStream_t st);
 template <typename T>
 ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, const T* G,
                             long ldg, const T* W, long ldw, const T* H, long ldh, T* Mbuf, T* CnT,

@@ -540,26 +540,8 @@ __device__ U* block_jacobi(U* A, U* A2, U* V, int n, U tol, U floor_rel, int max
 
 // ---------------------------------------------------------------- the kernel
 
-template <typename T>
-struct FusedArgs {
-  int r, s, k, R, solve;
-  const T* G;
-  long ldg;  // r x r
-  const T* W;
-  long ldw;  // r x k (RSVD)
-  const T* H;
-  long ldh;   // r x s
-  T* Mbuf;    // k x s when D is not kept on chip
-  T* CnT;     // r x R out (may be null)
-  T* A_out;   // s x R out
-  T* core;    // may be null
-  CoreMap map;
-  int* flag;
-  bool m_smem;
-};
-
 template <typename T, typename U, bool POLISH64>
-__global__ void __launch_bounds__(kThreads) k_lrls_fused(FusedArgs<T> a) {
+__device__ __forceinline__ void lrls_fused_body(const FusedArgs<T>& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ JacobiRound<T> jround;
   __shared__ JacobiRound<double> jround64;
@@ -857,6 +839,18 @@ __global__ void __launch_bounds__(kThreads) k_lrls_fused(FusedArgs<T> a) {
   }
 }
 
+template <typename T, typename U, bool POLISH64>
+__global__ void __launch_bounds__(kThreads) k_lrls_fused(FusedArgs<T> a) {
+  lrls_fused_body<T, U, POLISH64>(a);
+}
+
+// Independent subproblems, one per block.
+template <typename T, typename U, bool POLISH64>
+__global__ void __launch_bounds__(kThreads) k_lrls_fused_batched(const FusedArgs<T>* __restrict__ args) {
+  const FusedArgs<T> a = args[blockIdx.x];
+  lrls_fused_body<T, U, POLISH64>(a);
+}
+
 // ---------------------------------------------------------------- host side
 
 // Static shared memory of the kernel plus slack, kept out of the dynamic budget.
@@ -887,9 +881,9 @@ bool lrls_fused_supported(int r, int s, int k, int R, int solve, size_t tsize, b
 }
 
 template <typename T>
-ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, const T* G,
-                            long ldg, const T* W, long ldw, const T* H, long ldh, T* Mbuf, T* CnT,
-                            T* A_out, T* core, CoreMap map, int* flag, cudaStream_t st) {
+ts_status make_fused_args(int r, int s, int k, int R, int solve, bool fp64, const T* G, long ldg,
+                          const T* W, long ldw, const T* H, long ldh, T* Mbuf, T* CnT, T* A_out,
+                          T* core, CoreMap map, int* flag, FusedArgs<T>* out, size_t* smem) {
   if (!lrls_fused_supported(r, s, k, R, solve, sizeof(T), fp64))
     return fail(TS_ERR_SHAPE, "fused solve: r=%d s=%d k=%d R=%d does not fit one block", r, s, k,
                 R);
@@ -911,9 +905,20 @@ ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, co
   a.core = core;
   a.map = map;
   a.flag = flag;
+  *smem = lrls_fused_smem_bytes(r, s, k, R, solve, sizeof(T), fp64, &a.m_smem) - kStaticReserve;
+  *out = a;
+  return TS_OK;
+}
+
+template <typename T>
+ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, const T* G,
+                            long ldg, const T* W, long ldw, const T* H, long ldh, T* Mbuf, T* CnT,
+                            T* A_out, T* core, CoreMap map, int* flag, cudaStream_t st) {
+  FusedArgs<T> a;
+  size_t smem = 0;
+  TS_TRY(make_fused_args<T>(r, s, k, R, solve, fp64, G, ldg, W, ldw, H, ldh, Mbuf, CnT, A_out,
+                            core, map, flag, &a, &smem));
   const bool polish = fp64 && sizeof(T) == 4;
-  const size_t smem =
-      lrls_fused_smem_bytes(r, s, k, R, solve, sizeof(T), fp64, &a.m_smem) - kStaticReserve;
   if constexpr (sizeof(T) == 4) {
     if (polish) {
       TS_TRY(ensure_dynamic_smem((const void*)k_lrls_fused<T, double, true>, smem));
@@ -927,6 +932,34 @@ ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, co
   TS_LAUNCH_CHECK();
   return TS_OK;
 }
+
+template <typename T>
+ts_status launch_lrls_fused_batched(const FusedArgs<T>* args, int count, bool fp64, size_t smem,
+                                    cudaStream_t st) {
+  if (count < 1) return TS_OK;
+  if constexpr (sizeof(T) == 4) {
+    if (fp64) {
+      TS_TRY(ensure_dynamic_smem((const void*)k_lrls_fused_batched<T, double, true>, smem));
+      k_lrls_fused_batched<T, double, true><<<count, kThreads, smem, st>>>(args);
+      TS_LAUNCH_CHECK();
+      return TS_OK;
+    }
+  }
+  TS_TRY(ensure_dynamic_smem((const void*)k_lrls_fused_batched<T, T, false>, smem));
+  k_lrls_fused_batched<T, T, false><<<count, kThreads, smem, st>>>(args);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+#define TS_INST_FUSED(T)                                                                       \
+  template ts_status make_fused_args<T>(int, int, int, int, int, bool, const T*, long, const T*, \
+                                        long, const T*, long, T*, T*, T*, T*, CoreMap, int*,    \
+                                        FusedArgs<T>*, size_t*);                                \
+  template ts_status launch_lrls_fused_batched<T>(const FusedArgs<T>*, int, bool, size_t,       \
+                                                  cudaStream_t);
+TS_INST_FUSED(float)
+TS_INST_FUSED(double)
+#undef TS_INST_FUSED
 
 template ts_status launch_lrls_fused<float>(int, int, int, int, int, bool, const float*, long,
                                             const float*, long, const float*, long, float*,

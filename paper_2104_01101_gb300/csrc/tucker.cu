@@ -6,6 +6,8 @@
 #include <math.h>
 #include <string.h>
 
+#include <algorithm>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -671,6 +673,252 @@ static ts_status graph_replay(const std::string& key, F&& enqueue, cudaStream_t 
   return TS_OK;
 }
 
+// ---------------------------------------------------------------- batched form
+
+// Many independent dense tensors advanced together: every tensor keeps its own
+// workspace region (the single-tensor layout), its setup (tables, one-pass sketches,
+// Init-RRF, Gaussians, Y_n Omega) runs once in ts_batch_prepare, and each subproblem
+// step of a sweep is one launch over the whole batch: the TensorSketch chains, the
+// products [Z^T Z | Z^T Y Omega | Z^T Y], the single-block solves.  The per-tensor
+// arguments of every launch live in device descriptor arrays written once by prepare,
+// so the sweeps enqueue nothing but kernel launches (capturable in a CUDA graph).
+struct BatchPlan {
+  int count = 0, N = 0, sweeps = 0, dtype = TS_F32, solve = TS_SOLVE_RSVD;
+  bool fp64 = false;
+  int device = 0;
+  std::vector<Shape> S;
+  std::vector<ts_tensor> X;
+  std::vector<void*> cores, factors;  // factors: count x N
+  std::vector<int*> flags;
+  std::vector<void*> fitQ, fitacc;
+  void* chain = nullptr;  // TsChainJob<T> [N][count]
+  void* gemm = nullptr;   // GemmJob<T> [sweeps][N][count]
+  void* fused = nullptr;  // FusedArgs<T> [N][count]
+  int spec_blocks[TS_MAX_ORDER] = {}, z_blocks[TS_MAX_ORDER] = {};
+  int maxM[TS_MAX_ORDER] = {}, maxN[TS_MAX_ORDER] = {}, tile[TS_MAX_ORDER] = {};
+  size_t chain_smem[TS_MAX_ORDER] = {}, fused_smem[TS_MAX_ORDER] = {};
+  float tile_ms[TS_MAX_ORDER][2] = {};  // autotuner: product time per tile shape (32, 64)
+};
+
+static ts_status batch_check(int count, const ts_tensor* X, const int32_t* ranks,
+                             const int32_t* m, int sweeps, const ts_options* opt) {
+  if (count < 1 || !X || !ranks || !m || !opt)
+    return fail(TS_ERR_INVALID_ARG, "ts_batch: need count >= 1 and non-NULL X, ranks, m, opt");
+  if (opt->resketch_each_sweep || opt->gram_bf16 || opt->use_graph)
+    return fail(TS_ERR_UNSUPPORTED,
+                "ts_batch: resketch_each_sweep, gram_bf16 and use_graph are not offered");
+  for (int i = 0; i < count; ++i) {
+    if (X[i].format != TS_DENSE || X[i].order != X[0].order || X[i].dtype != X[0].dtype)
+      return fail(TS_ERR_UNSUPPORTED, "ts_batch: tensor %d: dense tensors of one order and dtype",
+                  i);
+  }
+  if (sweeps < 1) return fail(TS_ERR_SHAPE, "ts_batch: sweeps %d < 1", sweeps);
+  return TS_OK;
+}
+
+static ts_status batch_shapes(int count, const ts_tensor* X, const int32_t* ranks,
+                              const int32_t* m, int sweeps, const ts_options* opt,
+                              std::vector<Shape>& S) {
+  S.resize(count);
+  const int N = X[0].order;
+  for (int i = 0; i < count; ++i) {
+    TS_TRY(plan_shape(&X[i], ranks + (size_t)i * N, TS_TENSORSKETCH, m[i], sweeps, opt, true,
+                      S[i]));
+    for (int n = 0; n < N; ++n)
+      if (!S[i].fused[n])
+        return fail(TS_ERR_UNSUPPORTED,
+                    "ts_batch: tensor %d mode %d (r=%d, s=%lld) does not fit the single-block solve",
+                    i, n, S[i].r[n], (long long)X[i].dims[n]);
+  }
+  return TS_OK;
+}
+
+template <typename T>
+static size_t batch_desc_bytes(int count, int N, int sweeps) {
+  Bump b;
+  b.take<TsChainJob<T>>((size_t)N * count);
+  b.take<GemmJob<T>>((size_t)sweeps * N * count);
+  b.take<FusedArgs<T>>((size_t)N * count);
+  return align_up(b.off, 256);
+}
+
+template <typename T>
+static size_t batch_bytes(int count, const ts_tensor* X, const std::vector<Shape>& S) {
+  const int N = X[0].order;
+  size_t total = batch_desc_bytes<T>(count, N, S[0].sweeps);
+  for (int i = 0; i < count; ++i) {
+    Bump b;
+    Work<T> w;
+    carve<T>(X[i], S[i], true, b, w);
+    total += align_up(b.off, 256);
+  }
+  return total;
+}
+
+// Setup of every tensor, then the descriptors of every (sweep, mode, tensor) and the
+// autotuned product tiles.  Synchronises the stream.
+template <typename T>
+static ts_status batch_prepare_impl(BatchPlan& P, const ts_options& opt, char* ws,
+                                    cudaStream_t st) {
+  const int count = P.count, N = P.N, sweeps = P.sweeps;
+  std::vector<Work<T>> W(count);
+  size_t off = batch_desc_bytes<T>(count, N, sweeps);
+  {
+    Bump b{ws};
+    P.chain = b.take<TsChainJob<T>>((size_t)N * count);
+    P.gemm = b.take<GemmJob<T>>((size_t)sweeps * N * count);
+    P.fused = b.take<FusedArgs<T>>((size_t)N * count);
+  }
+  for (int i = 0; i < count; ++i) {
+    Bump b{ws + off};
+    carve<T>(P.X[i], P.S[i], true, b, W[i]);
+    off += align_up(b.off, 256);
+  }
+  // per-tensor setup, exactly as the single-tensor driver (seed of tensor i: seed + i)
+  for (int i = 0; i < count; ++i) {
+    const ts_tensor& X = P.X[i];
+    const Shape& S = P.S[i];
+    Work<T>& w = W[i];
+    T* const* fac = reinterpret_cast<T* const*>(&P.factors[(size_t)i * N]);
+    const uint64_t seed = opt.seed + (uint64_t)i;
+    TS_CUDA(cudaMemsetAsync(w.flag, 0, 256 + kGemmCounters * sizeof(unsigned), st));
+    if (S.rrf) TS_TRY(rrf_all<T>(X, S, seed, w, fac, st));
+    if (S.solve == TS_SOLVE_RSVD) TS_TRY(launch_omegas<T>(seed, S.ob, w.Om, st));
+    TS_TRY(launch_twiddles<T>(S.m, w.tw, st));
+    TS_TRY(build_ts_tables<T>(X, S, seed, 0, w, st));
+    TS_TRY(sketch_rhs_all<T>(X, S, w, st));
+    if (S.solve == TS_SOLVE_RSVD) TS_TRY(rhs_times_omegas<T>(X, S, w, 0, S.sweeps, st));
+    P.flags[i] = w.flag;
+    P.fitQ[i] = w.fitQ;
+    P.fitacc[i] = w.fitacc;
+  }
+  // descriptors
+  std::vector<TsChainJob<T>> chain((size_t)N * count);
+  std::vector<GemmJob<T>> gemm((size_t)sweeps * N * count);
+  std::vector<FusedArgs<T>> fused((size_t)N * count);
+  for (int n = 0; n < N; ++n) {
+    P.spec_blocks[n] = P.z_blocks[n] = P.maxM[n] = P.maxN[n] = 0;
+    P.chain_smem[n] = P.fused_smem[n] = 0;
+    for (int i = 0; i < count; ++i) {
+      const ts_tensor& X = P.X[i];
+      const Shape& S = P.S[i];
+      Work<T>& w = W[i];
+      T* const* fac = reinterpret_cast<T* const*>(&P.factors[(size_t)i * N]);
+      const T* cf[TS_MAX_ORDER];
+      const int32_t* ct[TS_MAX_ORDER];
+      int64_t rows[TS_MAX_ORDER];
+      int cols[TS_MAX_ORDER];
+      int nf = 0;
+      for (int k = 0; k < N; ++k)
+        if (k != n) {
+          cf[nf] = fac[k];
+          ct[nf] = w.tab[n][k];
+          rows[nf] = X.dims[k];
+          cols[nf] = S.ranks[k];
+          ++nf;
+        }
+      TsChainJob<T>& cj = chain[(size_t)n * count + i];
+      cj = make_chain_job<T>(nf, cf, rows, cols, ct, S.m, w.tw, w.spectra, w.ZW);
+      P.spec_blocks[n] = std::max(P.spec_blocks[n], ceil_div(cj.d.total_cols, 2));
+      P.z_blocks[n] = std::max(P.z_blocks[n], ceil_div(cj.ncols, 2));
+      P.chain_smem[n] = std::max(P.chain_smem[n], chain_job_smem<T>(cj));
+      const int r = S.r[n], k = S.kc[n], s = (int)X.dims[n], m = S.m;
+      const bool rsvd = S.solve == TS_SOLVE_RSVD;
+      const int kk = rsvd ? k : 0;
+      const int Ncol = r + kk + s;
+      const MatView<T> Zt = mv<T>(w.ZW, m, 1), Zm = mv<T>(w.ZW, 1, m);
+      const MatView<T> Yv = mv<T>(w.Y[n], s, 1);
+      for (int t = 0; t < sweeps; ++t) {
+        GemmJob<T>& g = gemm[((size_t)t * N + n) * count + i];
+        g.M = r;
+        g.N = Ncol;
+        g.K = m;
+        g.A = Zt;
+        g.B1 = Zm;
+        g.n1 = r;
+        if (rsvd) {
+          g.B2 = mv<T>(w.YOm + S.yom_off[n] + (size_t)t * k, (long)S.sweeps * k, 1);
+          g.n2 = r + k;
+          g.B3 = Yv;
+        } else {
+          g.B2 = Yv;
+          g.n2 = Ncol;
+          g.B3 = Yv;
+        }
+        g.C = ov<T>(w.GW, Ncol, 1);
+      }
+      P.maxM[n] = std::max(P.maxM[n], r);
+      P.maxN[n] = std::max(P.maxN[n], Ncol);
+      CoreMap map{};
+      map.order = N;
+      map.n = n;
+      for (int q = 0; q < N; ++q) map.ranks[q] = S.ranks[q];
+      size_t sm = 0;
+      TS_TRY(make_fused_args<T>(r, s, k, S.ranks[n], S.solve, S.fp64solve, w.GW, Ncol,
+                                rsvd ? w.GW + r : nullptr, Ncol, w.GW + r + kk, Ncol, w.Mbuf,
+                                w.CnT, fac[n], static_cast<T*>(P.cores[i]), map, w.flag,
+                                &fused[(size_t)n * count + i], &sm));
+      P.fused_smem[n] = std::max(P.fused_smem[n], sm);
+    }
+  }
+  TS_CUDA(cudaMemcpyAsync(P.chain, chain.data(), chain.size() * sizeof(chain[0]),
+                          cudaMemcpyHostToDevice, st));
+  TS_CUDA(cudaMemcpyAsync(P.gemm, gemm.data(), gemm.size() * sizeof(gemm[0]),
+                          cudaMemcpyHostToDevice, st));
+  TS_CUDA(cudaMemcpyAsync(P.fused, fused.data(), fused.size() * sizeof(fused[0]),
+                          cudaMemcpyHostToDevice, st));
+  // autotuner: time the batched product of every mode with both tile shapes, keep the
+  // faster (the operands' values do not matter for the timing; the sweeps overwrite
+  // the products)
+  cudaEvent_t e0, e1;
+  TS_CUDA(cudaEventCreate(&e0));
+  TS_CUDA(cudaEventCreate(&e1));
+  ts_status rc = TS_OK;
+  for (int n = 0; n < N && rc == TS_OK; ++n) {
+    const GemmJob<T>* jobs = static_cast<const GemmJob<T>*>(P.gemm) + (size_t)n * count;
+    for (int v = 0; v < 2 && rc == TS_OK; ++v) {
+      const int tile = v ? 64 : 32;
+      rc = launch_gemm_batched<T>(jobs, count, P.maxM[n], P.maxN[n], tile, st);  // warm-up
+      if (rc != TS_OK) break;
+      cudaEventRecord(e0, st);
+      for (int rep = 0; rep < 5 && rc == TS_OK; ++rep)
+        rc = launch_gemm_batched<T>(jobs, count, P.maxM[n], P.maxN[n], tile, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        rc = fail(TS_ERR_CUDA, "ts_batch_prepare: autotuner timing failed");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      P.tile_ms[n][v] = ms / 5;
+    }
+    P.tile[n] = P.tile_ms[n][1] < P.tile_ms[n][0] ? 64 : 32;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  TS_TRY(rc);
+  TS_CUDA(cudaStreamSynchronize(st));
+  return TS_OK;
+}
+
+template <typename T>
+static ts_status batch_sweeps_impl(const BatchPlan& P, int first, int nsweeps, cudaStream_t st) {
+  const int count = P.count, N = P.N;
+  const TsChainJob<T>* chain = static_cast<const TsChainJob<T>*>(P.chain);
+  const GemmJob<T>* gemm = static_cast<const GemmJob<T>*>(P.gemm);
+  const FusedArgs<T>* fused = static_cast<const FusedArgs<T>*>(P.fused);
+  for (int t = first; t < first + nsweeps; ++t)
+    for (int n = 0; n < N; ++n) {
+      TS_TRY(launch_ts_apply_batched<T>(chain + (size_t)n * count, count, P.spec_blocks[n],
+                                        P.z_blocks[n], P.chain_smem[n], st));
+      TS_TRY(launch_gemm_batched<T>(gemm + ((size_t)t * N + n) * count, count, P.maxM[n],
+                                    P.maxN[n], P.tile[n], st));
+      TS_TRY(launch_lrls_fused_batched<T>(fused + (size_t)n * count, count, P.fp64,
+                                          P.fused_smem[n], st));
+    }
+  return TS_OK;
+}
+
 }  // namespace ts
 
 using namespace ts;
@@ -1209,3 +1457,125 @@ extern "C" ts_status cp_via_tucker(const ts_tensor* X, int32_t R_cp, const int32
   return cp_impl<float>(*X, S, *opt, R_cp, cp_sweeps, workspace,
                         reinterpret_cast<float* const*>(cp_factors_out), residual_out, st);
 }
+
+// ---------------------------------------------------------------- batched form
+
+extern "C" ts_status ts_batch_workspace_bytes(int32_t count, const ts_tensor* X,
+                                              const int32_t* ranks, const int32_t* m,
+                                              int32_t sweeps, const ts_options* opt,
+                                              size_t* bytes_out) {
+  clear_error();
+  if (!bytes_out) return fail(TS_ERR_INVALID_ARG, "ts_batch_workspace_bytes: NULL bytes_out");
+  TS_TRY(batch_check(count, X, ranks, m, sweeps, opt));
+  std::vector<Shape> S;
+  TS_TRY(batch_shapes(count, X, ranks, m, sweeps, opt, S));
+  *bytes_out = X[0].dtype == TS_F64 ? batch_bytes<double>(count, X, S)
+                                    : batch_bytes<float>(count, X, S);
+  return TS_OK;
+}
+
+extern "C" ts_status ts_batch_prepare(int32_t count, const ts_tensor* X, const int32_t* ranks,
+                                      const int32_t* m, int32_t sweeps, const ts_options* opt,
+                                      void* workspace, size_t workspace_bytes,
+                                      void* const* cores, void* const* factors,
+                                      ts_batch* batch_out, ts_stream stream) {
+  clear_error();
+  if (!batch_out) return fail(TS_ERR_INVALID_ARG, "ts_batch_prepare: NULL batch_out");
+  *batch_out = nullptr;
+  TS_TRY(batch_check(count, X, ranks, m, sweeps, opt));
+  if (!cores || !factors) return fail(TS_ERR_INVALID_ARG, "ts_batch_prepare: NULL cores/factors");
+  const int N = X[0].order;
+  for (int i = 0; i < count; ++i) {
+    if (!cores[i]) return fail(TS_ERR_INVALID_ARG, "ts_batch_prepare: core %d NULL", i);
+    for (int k = 0; k < N; ++k)
+      if (!factors[(size_t)i * N + k])
+        return fail(TS_ERR_INVALID_ARG, "ts_batch_prepare: factor %d of tensor %d NULL", k, i);
+  }
+  std::unique_ptr<BatchPlan> P(new BatchPlan);
+  TS_TRY(batch_shapes(count, X, ranks, m, sweeps, opt, P->S));
+  const size_t need = X[0].dtype == TS_F64 ? batch_bytes<double>(count, X, P->S)
+                                           : batch_bytes<float>(count, X, P->S);
+  if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255))
+    return fail(TS_ERR_WORKSPACE, "ts_batch_prepare: need %zu bytes of 256-aligned workspace",
+                need);
+  P->count = count;
+  P->N = N;
+  P->sweeps = sweeps;
+  P->dtype = X[0].dtype;
+  P->solve = opt->solve;
+  P->fp64 = P->S[0].fp64solve;
+  TS_CUDA(cudaGetDevice(&P->device));
+  P->X.assign(X, X + count);
+  P->cores.assign(cores, cores + count);
+  P->factors.assign(factors, factors + (size_t)count * N);
+  P->flags.assign(count, nullptr);
+  P->fitQ.assign(count, nullptr);
+  P->fitacc.assign(count, nullptr);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* ws = static_cast<char*>(workspace);
+  TS_TRY(P->dtype == TS_F64 ? batch_prepare_impl<double>(*P, *opt, ws, st)
+                            : batch_prepare_impl<float>(*P, *opt, ws, st));
+  *batch_out = P.release();
+  return TS_OK;
+}
+
+extern "C" ts_status ts_batch_sweeps(ts_batch batch, int32_t first, int32_t nsweeps,
+                                     ts_stream stream) {
+  clear_error();
+  const BatchPlan* P = static_cast<const BatchPlan*>(batch);
+  if (!P) return fail(TS_ERR_INVALID_ARG, "ts_batch_sweeps: NULL batch");
+  if (first < 0 || nsweeps < 0 || first + nsweeps > P->sweeps)
+    return fail(TS_ERR_SHAPE, "ts_batch_sweeps: sweeps [%d, %d) outside [0, %d)", first,
+                first + nsweeps, P->sweeps);
+  cudaStream_t st = (cudaStream_t)stream;
+  return P->dtype == TS_F64 ? batch_sweeps_impl<double>(*P, first, nsweeps, st)
+                            : batch_sweeps_impl<float>(*P, first, nsweeps, st);
+}
+
+extern "C" ts_status ts_batch_residuals(ts_batch batch, double* residuals, ts_stream stream) {
+  clear_error();
+  const BatchPlan* P = static_cast<const BatchPlan*>(batch);
+  if (!P || !residuals) return fail(TS_ERR_INVALID_ARG, "ts_batch_residuals: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int i = 0; i < P->count; ++i) {
+    const int N = P->N;
+    if (P->dtype == TS_F64)
+      TS_TRY(launch_fit_dense<double>(P->X[i], P->S[i].ranks,
+                                      static_cast<const double*>(P->cores[i]),
+                                      reinterpret_cast<const double* const*>(&P->factors[(size_t)i * N]),
+                                      static_cast<double*>(P->fitQ[i]),
+                                      static_cast<double*>(P->fitacc[i]), residuals + i, st));
+    else
+      TS_TRY(launch_fit_dense<float>(P->X[i], P->S[i].ranks,
+                                     static_cast<const float*>(P->cores[i]),
+                                     reinterpret_cast<const float* const*>(&P->factors[(size_t)i * N]),
+                                     static_cast<float*>(P->fitQ[i]),
+                                     static_cast<double*>(P->fitacc[i]), residuals + i, st));
+  }
+  return TS_OK;
+}
+
+extern "C" ts_status ts_batch_flags(ts_batch batch, int32_t* flags_out) {
+  clear_error();
+  const BatchPlan* P = static_cast<const BatchPlan*>(batch);
+  if (!P || !flags_out) return fail(TS_ERR_INVALID_ARG, "ts_batch_flags: NULL argument");
+  for (int i = 0; i < P->count; ++i)
+    TS_CUDA(cudaMemcpy(flags_out + i, P->flags[i], sizeof(int32_t), cudaMemcpyDeviceToHost));
+  return TS_OK;
+}
+
+extern "C" ts_status ts_batch_tiles(ts_batch batch, int32_t* tiles_out, float* ms_out) {
+  clear_error();
+  const BatchPlan* P = static_cast<const BatchPlan*>(batch);
+  if (!P || !tiles_out) return fail(TS_ERR_INVALID_ARG, "ts_batch_tiles: NULL argument");
+  for (int n = 0; n < P->N; ++n) {
+    tiles_out[n] = P->tile[n];
+    if (ms_out) {
+      ms_out[2 * n] = P->tile_ms[n][0];
+      ms_out[2 * n + 1] = P->tile_ms[n][1];
+    }
+  }
+  return TS_OK;
+}
+
+extern "C" void ts_batch_destroy(ts_batch batch) { delete static_cast<BatchPlan*>(batch); }

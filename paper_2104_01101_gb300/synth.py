@@ -11,6 +11,10 @@ dense_tucker     Tucker product of a Gaussian core with column-orthonormal facto
                  (QR of Gaussian matrices) plus Gaussian noise of a given relative
                  norm (the paper's Tensor 1 with alpha = 1, plus noise); optional
                  geometric decay of the core entries (weight**(i+j+k)).
+dense_tucker_batch_torch
+                 many dense_tucker tensors of uneven shapes and ranks, built on the
+                 device with torch (the batched workload: mode sizes and one rank per
+                 tensor drawn uniformly).
 coo_zipf_tucker  COO tensor whose coordinates are i.i.d. Zipf(a) per mode truncated
                  to the mode size, values N(0,1) noise plus a planted Tucker
                  component sampled at the same coordinates, both of equal norm.
@@ -53,6 +57,31 @@ def dense_tucker(dims, ranks, noise: float, seed: int, core_decay: float | None 
         E = rng.standard_normal(T.shape)
         T = T + E * (noise * np.linalg.norm(T) / np.linalg.norm(E))
     return np.ascontiguousarray(T.astype(dtype)), core, factors
+
+
+def dense_tucker_batch_torch(count: int, size_range, rank_range, noise: float, seed: int,
+                             device, dtype=None):
+    """``count`` tensors as dense_tucker (Gaussian core, orthonormal factors, Gaussian
+    noise of relative norm ``noise``), built on ``device``: mode sizes uniform in
+    ``size_range`` (inclusive), one rank R uniform in ``rank_range`` per tensor.
+    Returns (tensors, ranks): a list of contiguous torch tensors and [(R, R, R)]."""
+    import torch
+    dtype = dtype or torch.float32
+    rng = np.random.default_rng(seed)
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    tensors, ranks = [], []
+    for _ in range(count):
+        dims = [int(x) for x in rng.integers(size_range[0], size_range[1] + 1, size=3)]
+        R = int(rng.integers(rank_range[0], rank_range[1] + 1))
+        core = torch.from_numpy(rng.standard_normal((R, R, R))).to(device, torch.float64)
+        A = [torch.from_numpy(orthonormal(rng, s, R)).to(device, torch.float64) for s in dims]
+        T = torch.einsum("abc,ia,jb,kc->ijk", core, A[0], A[1], A[2])
+        E = torch.randn(dims, generator=g, device=device, dtype=torch.float64)
+        T = T + E * (noise * torch.linalg.norm(T) / torch.linalg.norm(E))
+        tensors.append(T.to(dtype).contiguous())
+        ranks.append((R, R, R))
+    return tensors, ranks
 
 
 def zipf_table(s: int, a: float) -> np.ndarray:

@@ -89,6 +89,15 @@ _PROTOS = {
     "tucker_als_sketched": (I32, [TP, C.POINTER(I32), I32, I32, I32, OP, P, SZ, P, PP, P, P]),
     "cp_via_tucker_workspace_bytes": (I32, [TP, I32, C.POINTER(I32), I32, I32, OP, C.POINTER(SZ)]),
     "cp_via_tucker": (I32, [TP, I32, C.POINTER(I32), I32, I32, I32, OP, P, SZ, PP, P, P]),
+    "ts_batch_workspace_bytes": (I32, [I32, TP, C.POINTER(I32), C.POINTER(I32), I32, OP,
+                                       C.POINTER(SZ)]),
+    "ts_batch_prepare": (I32, [I32, TP, C.POINTER(I32), C.POINTER(I32), I32, OP, P, SZ, PP, PP,
+                               C.POINTER(P), P]),
+    "ts_batch_sweeps": (I32, [P, I32, I32, P]),
+    "ts_batch_residuals": (I32, [P, P, P]),
+    "ts_batch_flags": (I32, [P, C.POINTER(I32)]),
+    "ts_batch_tiles": (I32, [P, C.POINTER(I32), C.POINTER(C.c_float)]),
+    "ts_batch_destroy": (None, [P]),
 }
 
 
@@ -401,6 +410,78 @@ class TuckerPlan:
 
     def numeric_flag(self) -> int:
         return int(self.workspace[:4].view(torch.int32).item())
+
+
+class TuckerBatch:
+    """Batched Sketch-Tucker-ALS of many dense tensors (ts_batch_* in the C ABI).
+
+    ``tensors``: list of contiguous CUDA tensors of one order and dtype; ``ranks``: one
+    rank tuple per tensor; ``ms``: one sketch size per tensor.  Tensor i uses seed
+    ``seed + i``.  Construction runs the one-time setup (and the tile autotuner) and
+    synchronises; ``sweeps(first, n)`` enqueues sweeps [first, first + n) of every
+    tensor on the current stream (capturable in a CUDA graph)."""
+
+    def __init__(self, tensors, ranks, ms, sweeps, seed=0, solve=SOLVE_RSVD, oversample=5,
+                 rrf_k1=None, rrf_k2=None, solve_fp64=False):
+        self.count = len(tensors)
+        self.N = tensors[0].dim()
+        self.sweeps_total = sweeps
+        self.tensors = tensors  # kept alive: the batch reads them
+        self.opt = _options(seed, solve, oversample, rrf_k1, rrf_k2, False, False, False,
+                            solve_fp64)
+        self._X = (_Tensor * self.count)(*[_desc(t) for t in tensors])
+        flat = [int(r) for rk in ranks for r in rk]
+        self._rk = (C.c_int32 * len(flat))(*flat)
+        self._m = (C.c_int32 * self.count)(*[int(m) for m in ms])
+        nbytes = C.c_size_t(0)
+        _check(lib().ts_batch_workspace_bytes(self.count, self._X, self._rk, self._m, sweeps,
+                                              C.byref(self.opt), C.byref(nbytes)))
+        dev, dtype = tensors[0].device, tensors[0].dtype
+        self.workspace = _scratch(nbytes.value, dev)
+        self.cores = [torch.zeros(tuple(rk), dtype=dtype, device=dev) for rk in ranks]
+        self.factors = [[torch.zeros((s, R), dtype=dtype, device=dev)
+                         for s, R in zip(t.shape, rk)] for t, rk in zip(tensors, ranks)]
+        self._cores = _ptr_array(self.cores)
+        self._facs = _ptr_array([f for fs in self.factors for f in fs])
+        self.residuals = torch.zeros(self.count, dtype=torch.float64, device=dev)
+        h = C.c_void_p(None)
+        _check(lib().ts_batch_prepare(self.count, self._X, self._rk, self._m, sweeps,
+                                      C.byref(self.opt), _ptr(self.workspace),
+                                      self.workspace.numel(), self._cores, self._facs,
+                                      C.byref(h), _stream()))
+        self._h = h
+
+    def sweeps(self, first=0, n=None):
+        n = self.sweeps_total - first if n is None else n
+        _check(lib().ts_batch_sweeps(self._h, first, n, _stream()))
+        return self
+
+    def residual(self):
+        _check(lib().ts_batch_residuals(self._h, _ptr(self.residuals), _stream()))
+        return self.residuals
+
+    def flags(self):
+        out = (C.c_int32 * self.count)()
+        _check(lib().ts_batch_flags(self._h, out))
+        return list(out)
+
+    def tiles(self):
+        t = (C.c_int32 * self.N)()
+        ms = (C.c_float * (2 * self.N))()
+        _check(lib().ts_batch_tiles(self._h, t, ms))
+        return list(t), [(ms[2 * n], ms[2 * n + 1]) for n in range(self.N)]
+
+    def close(self):
+        if self._h:
+            torch.cuda.synchronize()
+            lib().ts_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def cp_via_tucker(X, R_cp: int, tucker_ranks, m: int, tucker_sweeps: int, cp_sweeps: int,

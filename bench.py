@@ -33,6 +33,12 @@ WORKLOAD = ("dense 400x400x400 FP32 Tucker rank (10,10,10), core N(0,1)*0.9^(i+j
             "orthonormal factors, noise 1e-2; TensorSketch m=2000; RRF init k1=15; "
             "RSVD-LRLS (p=5); 10 sweeps")
 METRIC = "sketched Tucker-ALS sweeps/sec"
+# The batched form (many independent tensors per launch): mode sizes uniform in
+# [32, 160], one rank R uniform in [4, 12] per tensor, m = 8 R^2, noise 1e-2.
+BATCH_COUNT, BATCH_SIZES, BATCH_RANKS, BATCH_SWEEPS, BATCH_SEED = 256, (32, 160), (4, 12), 5, 11
+BATCH_WORKLOAD = ("256 dense 3-way FP32 tensors, mode sizes uniform in [32,160], one Tucker "
+                  "rank R uniform in [4,12] per tensor, noise 1e-2; TensorSketch m=8R^2; RRF "
+                  "init; RSVD-LRLS (p=5); 5 sweeps")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -154,6 +160,67 @@ def max_over_ranks(values, world, device):
 def job_sweeps_per_s(world, ms):
     """Whole-job throughput: every rank decomposes its own tensor (replicas) in ms."""
     return world * SWEEPS * 1e3 / ms
+
+
+def time_batched(args, dev, flush):
+    """The batched form against the plain single-tensor FP32 driver on the same tensors:
+    tensor-sweeps per second of the sweeps (setup excluded on both sides), and the final
+    residuals of both (same seeds)."""
+    import torch
+    from paper_2104_01101_gb300 import synth, tsketch as ts
+
+    tensors, ranks = synth.dense_tucker_batch_torch(BATCH_COUNT, BATCH_SIZES, BATCH_RANKS, 1e-2,
+                                                    seed=4, device=dev)
+    ms = [8 * r[0] ** 2 for r in ranks]
+    b = ts.TuckerBatch(tensors, ranks, ms, BATCH_SWEEPS, seed=BATCH_SEED)
+    b.sweeps()
+    res_b = b.residual().cpu().numpy().copy()
+    flags = sum(1 for f in b.flags() if f)
+    g = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        with torch.cuda.graph(g, stream=side):
+            b.sweeps()
+    torch.cuda.current_stream().wait_stream(side)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        step.append(e0.elapsed_time(e1))
+    tiles, tile_ms = b.tiles()
+    b.close()
+    # plain FP32, one tensor at a time: the sweep phase of each decomposition
+    seq_ms, res_s = 0.0, []
+    for i, T in enumerate(tensors):
+        plan = ts.TuckerPlan(T, ranks[i], ms[i], BATCH_SWEEPS, seed=BATCH_SEED + i)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        plan.set_phase_events(ev)
+        plan.run(T)
+        plan.run(T)
+        torch.cuda.synchronize()
+        seq_ms += ev[3].elapsed_time(ev[4])
+        res_s.append(float(plan.residuals[0]))
+    res_s = np.array(res_s)
+    work = BATCH_COUNT * BATCH_SWEEPS
+    batch_ms = statistics.mean(step)
+    return {"workload": BATCH_WORKLOAD,
+            "tensor_sweeps_per_s": work * 1e3 / batch_ms, "ms_per_step": batch_ms,
+            "plain_fp32_one_tensor_at_a_time": {"tensor_sweeps_per_s": work * 1e3 / seq_ms,
+                                                "sweeps_ms": seq_ms},
+            "speedup": seq_ms / batch_ms,
+            "max_abs_residual_diff": float(np.abs(res_b - res_s).max()),
+            "mean_residual": float(res_s.mean()), "flagged_tensors": flags,
+            "product_tiles": tiles, "product_tile_ms_32_64": tile_ms,
+            "launches_per_step": 4 * 3 * BATCH_SWEEPS,
+            "graph": "all sweeps of the batch captured once, replayed"}
 
 
 def run_ours(args, rank, world):
@@ -287,6 +354,8 @@ def run_ours(args, rank, world):
         "gpu_launches": int(launches),
         "clocks": clk_summary,
     }
+    if not args.no_batched:
+        line["batched"] = time_batched(args, dev, flush)
     if not args.no_cpu_baseline:
         T64 = T.astype(np.float64)
         dt, _ = cpu_oracle_step(T64)
@@ -320,6 +389,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-form measurement (256 small tensors)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

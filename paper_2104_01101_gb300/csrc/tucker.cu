@@ -861,6 +861,38 @@ static ts_status batch_prepare_impl(BatchPlan& P, const ts_options& opt, char* w
       P.fused_smem[n] = std::max(P.fused_smem[n], sm);
     }
   }
+  // longest work first within every launch (blocks start in index order, so the batch's
+  // makespan is not set by a long solve that starts last)
+  for (int n = 0; n < N; ++n) {
+    std::vector<int> ord(count);
+    std::vector<double> cost(count), ccost(count);
+    for (int i = 0; i < count; ++i) {
+      const Shape& S = P.S[i];
+      const double r = S.r[n], k = S.kc[n], sn = (double)P.X[i].dims[n];
+      cost[i] = r * (r + k) + 4.0 * k * sn;       // the single-block solve
+      ccost[i] = (double)S.m * (r + 2.0 * S.Rmax);  // the FFT chain
+      ord[i] = i;
+    }
+    auto sorted = [&](const std::vector<double>& c) {
+      std::vector<int> o = ord;
+      std::stable_sort(o.begin(), o.end(), [&](int a, int b) { return c[a] > c[b]; });
+      return o;
+    };
+    const std::vector<int> of = sorted(cost), oc = sorted(ccost);
+    std::vector<FusedArgs<T>> f2(count);
+    std::vector<TsChainJob<T>> c2(count);
+    for (int j = 0; j < count; ++j) {
+      f2[j] = fused[(size_t)n * count + of[j]];
+      c2[j] = chain[(size_t)n * count + oc[j]];
+    }
+    std::copy(f2.begin(), f2.end(), fused.begin() + (size_t)n * count);
+    std::copy(c2.begin(), c2.end(), chain.begin() + (size_t)n * count);
+    for (int t = 0; t < sweeps; ++t) {
+      std::vector<GemmJob<T>> g2(count);
+      for (int j = 0; j < count; ++j) g2[j] = gemm[((size_t)t * N + n) * count + of[j]];
+      std::copy(g2.begin(), g2.end(), gemm.begin() + ((size_t)t * N + n) * count);
+    }
+  }
   TS_CUDA(cudaMemcpyAsync(P.chain, chain.data(), chain.size() * sizeof(chain[0]),
                           cudaMemcpyHostToDevice, st));
   TS_CUDA(cudaMemcpyAsync(P.gemm, gemm.data(), gemm.size() * sizeof(gemm[0]),

@@ -232,3 +232,27 @@ def test_cp_via_tucker_fp32_collinear_workload(ts):
     # so the final fitness is compared as a quality bound, as the Tucker + CP experiments
     # compare methods: within 25% of the FP64 oracle's residual.
     assert res <= 1.25 * want + 1e-4
+
+
+def test_sparse_order4_scaled_workload_matches_oracle(ts):
+    # The sparse 4-way workload scaled down (SURVEY C3 recipe at dims 2000, 1e6 nonzeros):
+    # Zipf(1.1) coordinates with duplicates, planted rank-(8,8,8,8) Tucker component of the
+    # noise's norm, m = 4096, RRF k1 = 64, k2 = 128, re-sketched every sweep.  r = 512 per
+    # subproblem: the RSVD solve inverts Z^T Z by Newton-Schulz products.
+    dims, ranks, m = (2000, 2000, 2000, 2000), (8, 8, 8, 8), 4096
+    idx, vals, _, _ = synth.coo_zipf_tucker(dims, 1_000_000, ranks, seed=9, val_dtype=np.float64)
+    X = ts.Coo(torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(), dims)
+    core, fac, _ = ts.tucker_als_sketched(X, ranks, m, 2, seed=6, rrf_k1=64, rrf_k2=128,
+                                          resketch=True, want_residual=False)
+    c_o, f_o, _ = tucker.sketch_tucker_als(tucker.Coo(idx.astype(np.int64), vals, dims), ranks, m,
+                                           2, seed=6, rrf_k1=64, rrf_k2=128, resketch=True)
+    for n in range(4):
+        assert np.abs(proj(fac[n].cpu().numpy()) - proj(f_o[n])).max() < 1e-8
+    # the core in the gauge of the factors: C x_n A_n^T A_n' is gauge-invariant per mode
+    Cg = core.cpu().numpy()
+    for n in range(4):
+        U = np.moveaxis(Cg, n, 0).reshape(ranks[n], -1)
+        V = np.moveaxis(c_o, n, 0).reshape(ranks[n], -1)
+        sg = np.linalg.svd(U, compute_uv=False)
+        so = np.linalg.svd(V, compute_uv=False)
+        assert np.allclose(sg, so, rtol=1e-8, atol=1e-10 * so[0])

@@ -139,6 +139,32 @@ def test_input_sketch_dense_full_size_sampled_columns(ts):
             assert np.linalg.norm(Y[:, i] - want) <= 1e-5 * np.linalg.norm(want)
 
 
+def test_input_sketch_coo_full_size_sampled_columns(ts):
+    # The full sparse 4-way workload: dims 2e5 per mode, 1e8 Zipf(1.1) coordinates with
+    # duplicates, m = 4096.  Whole columns Y_n[:, i] are recomputed by the oracle from the
+    # nonzeros with i_n = i (the Zipf head index 0 alone has ~1e7 of them).
+    dims, nnz, m = (200_000,) * 4, 100_000_000, 4096
+    idx, vals = synth.coo_zipf_tucker_torch(dims, nnz, (8, 8, 8, 8), seed=3, device="cuda")
+    X = ts.Coo(idx, vals, dims)
+    for n in (0, 3):
+        tabs = packed_tables(21, dims, n, m)
+        Y = ts.tensorsketch_input(X, n, [tabs[k][2] if k in tabs else None for k in range(4)], m)
+        host_tabs = [tabs[k][:2] for k in sorted(tabs)]
+        for i in (0, 1, 777, 150_000):
+            sel = idx[n] == i
+            sub_idx = idx[:, sel].cpu().numpy().astype(np.int64)
+            sub_vals = vals[sel].cpu().numpy()
+            sub_idx[n] = 0                       # one column: mode n of extent 1
+            d1 = list(dims)
+            d1[n] = 1
+            want = sketch.input_sketch_coo(sub_idx, sub_vals, d1, n, host_tabs, m)[:, 0]
+            scale = sketch.input_sketch_coo(sub_idx, np.abs(sub_vals), d1, n,
+                                            [(b, np.ones_like(sg)) for b, sg in host_tabs], m)[:, 0]
+            got = Y[:, i].double().cpu().numpy()
+            assert np.linalg.norm(got - want) <= 1e-5 * max(np.linalg.norm(scale), 1e-30)
+        del Y
+
+
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_input_sketch_coo_with_duplicates_and_empty(ts, dtype):
     dims, m = (2000, 1500, 1000, 700), 512

@@ -18,10 +18,12 @@ solve    the sketched rank-constrained least-squares solves: the exact form of
 tucker   unfolding/TTM helpers, fitness (Sec. 7), HOSVD + HOOI (Alg. 1),
          Init-RRF (Alg. 3), Sketch-Tucker-ALS (Alg. 4), CP-ALS (Alg. 2) and
          CP-Sketch-Tucker (Alg. 6).
+grad     the sketched fit of one subproblem and its gradient with respect to the
+         core and every factor, by explicit matrices and the chain rule.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against
 something other than itself (brute force, closed forms, invariants, HOOI
 equivalence); none is "parity unpinned".
 """
 
-from . import rng, sketch, solve, tucker  # noqa: F401
+from . import grad, rng, sketch, solve, tucker  # noqa: F401

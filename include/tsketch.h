@@ -334,6 +334,31 @@ ts_status cp_via_tucker(const ts_tensor* X, int32_t R_cp, const int32_t* tucker_
                         double* residual_out, ts_stream stream);
 
 /* ------------------------------------------------------------------------- */
+/* Gradient of the sketched fit of subproblem `mode` (the objective that each step of
+ * Alg. 4 minimises: eq. (tucker_ls) with the TensorSketch of Sec. 3.1 applied):
+ *   L = 1/2 || Z C_(mode)^T A^(mode)T - Y ||_F^2,
+ * Z = TensorSketch of the factors k != mode (tables[k], m buckets; columns in C order
+ * of the remaining modes), C_(mode) the mode-`mode` unfolding of the core (C order),
+ * Y (m x dims[mode], row-major) the sketched right-hand side, e.g. tensorsketch_input
+ * with the same tables.  The factors k != mode enter through Z: their gradient is the
+ * adjoint of the FFT chain (a circular cross-correlation per factor column) followed
+ * by the transpose of each CountSketch (a hash/sign gather).
+ * Inputs (all in `dtype`): core (prod ranks, C order), factors (HOST array of `order`
+ * device pointers, dims[k] x ranks[k] row-major), tables (HOST array of `order` device
+ * pointers, tables[mode] ignored), Y.  Outputs: loss (DEVICE, one double), grad_core
+ * (prod ranks), grad_factors (HOST array of `order` device pointers, dims[k] x ranks[k]).
+ * Errors: TS_ERR_SHAPE for an order outside [2, TS_MAX_ORDER], a mode out of range,
+ * m outside [2, FFT limit] or non-positive sizes; TS_ERR_WORKSPACE for short or
+ * misaligned scratch (ts_fit_grad_scratch_bytes; 0 for invalid shapes). */
+size_t ts_fit_grad_scratch_bytes(int32_t order, const int64_t* dims, const int32_t* ranks,
+                                 int32_t mode, int32_t m, int32_t dtype);
+ts_status ts_fit_grad(int32_t order, const int64_t* dims, const int32_t* ranks, int32_t mode,
+                      int32_t m, int32_t dtype, const void* core, const void* const* factors,
+                      const int32_t* const* tables, const void* Y, double* loss,
+                      void* grad_core, void* const* grad_factors, void* scratch,
+                      size_t scratch_bytes, ts_stream stream);
+
+/* ------------------------------------------------------------------------- */
 /* Batched Sketch-Tucker-ALS: Alg. 4 on many independent dense tensors at once.
  *
  * Tensor i of `count` (X[i], HOST array of descriptors; one order N and dtype for the

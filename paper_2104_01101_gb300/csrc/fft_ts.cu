@@ -298,6 +298,182 @@ __global__ void __launch_bounds__(512) k_hadamard_ifft_batched(const TsChainJob<
   hadamard_ifft_body<T>(j.d, j.ncols, j.plan, j.tw, j.spectra, j.Z, blockIdx.x);
 }
 
+// ---------------------------------------------------------------- adjoint of the chain
+
+// Adjoint of Z = TensorSketch(chain) for a gradient dZ (column-major m x prod cols):
+// column c of Z is the inverse FFT of prod_f U_f^(c_f) (U_f = CountSketch of factor f,
+// ^ the DFT), so for real signals
+//   dU_f[:, r] = IFFT( sum_{c : c_f = r} DFT(dZ[:, c]) * conj(prod_{j != f} U^_j[:, c_j]) )
+// (a circular cross-correlation), and dA_f[i, r] = S_f(i) dU_f[H_f(i), r] (the transpose
+// of the CountSketch: a hash/sign gather).
+
+// Block bx: DFT of dZ columns 2 bx and 2 bx + 1 (one complex FFT of the pair).
+template <typename T>
+__global__ void __launch_bounds__(512) k_dz_spectra(int ncols, FftPlan plan,
+                                                    const Cx<T>* __restrict__ tw,
+                                                    const T* __restrict__ dZ,
+                                                    Cx<T>* __restrict__ dspec) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = plan.m;
+  Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw);
+  Cx<T>* b = a + m;
+  const Cx<T>* twp = tw;
+  if (plan.stage_tw) {
+    Cx<T>* tws = b + m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) tws[i] = tw[i];
+    twp = tws;
+  }
+  const int c0 = 2 * blockIdx.x, c1 = c0 + 1;
+  const bool has1 = c1 < ncols;
+  for (int k = threadIdx.x; k < m; k += blockDim.x)
+    a[k] = Cx<T>{dZ[(size_t)c0 * m + k], has1 ? dZ[(size_t)c1 * m + k] : (T)0};
+  __syncthreads();
+  const Cx<T>* F = fft_run<T>(a, b, plan, twp);
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    const Cx<T> z = F[k];
+    const Cx<T> zc = cconj(F[k == 0 ? 0 : m - k]);
+    dspec[(size_t)c0 * m + k] = Cx<T>{(z.x + zc.x) * (T)0.5, (z.y + zc.y) * (T)0.5};
+    if (has1) {
+      const Cx<T> df = csub(z, zc);
+      dspec[(size_t)c1 * m + k] = Cx<T>{df.y * (T)0.5, -df.x * (T)0.5};
+    }
+  }
+}
+
+// Block bx: dU of flat factor columns 2 bx and 2 bx + 1 (real pair in one inverse FFT).
+template <typename T>
+__global__ void __launch_bounds__(512) k_adjoint_factor(ChainDesc d, FftPlan plan,
+                                                        const Cx<T>* __restrict__ tw,
+                                                        const Cx<T>* __restrict__ spectra,
+                                                        const Cx<T>* __restrict__ dspec,
+                                                        T* __restrict__ dU) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = plan.m;
+  Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw);
+  Cx<T>* b = a + m;
+  const Cx<T>* twp = tw;
+  if (plan.stage_tw) {
+    Cx<T>* tws = b + m;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) tws[i] = tw[i];
+    twp = tws;
+  }
+  int fc[2], rc[2];
+  bool has[2];
+  for (int h = 0; h < 2; ++h) {
+    const int c = 2 * blockIdx.x + h;
+    has[h] = c < d.total_cols;
+    int f = 0;
+    while (has[h] && f + 1 < d.nf && c >= d.colbase[f + 1]) ++f;
+    fc[h] = f;
+    rc[h] = has[h] ? c - d.colbase[f] : 0;
+  }
+  // columns of Z: multi-index (c_0 .. c_{nf-1}), factor 0 slowest
+  int ncols = 1;
+  for (int f = 0; f < d.nf; ++f) ncols *= d.cols[f];
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    Cx<T> acc[2] = {Cx<T>{0, 0}, Cx<T>{0, 0}};
+    for (int h = 0; h < 2; ++h) {
+      if (!has[h]) continue;
+      const int f = fc[h], r = rc[h];
+      const int nother = ncols / d.cols[f];
+      for (int o = 0; o < nother; ++o) {
+        // multi-index with c_f = r and the others enumerated by o (C order)
+        int rem = o, col = 0, stride = 1;
+        Cx<T> p{1, 0};
+        int cidx[TS_MAX_ORDER];
+        for (int j = d.nf - 1; j >= 0; --j) {
+          if (j == f) {
+            cidx[j] = r;
+          } else {
+            cidx[j] = rem % d.cols[j];
+            rem /= d.cols[j];
+          }
+        }
+        for (int j = d.nf - 1; j >= 0; --j) {
+          col += cidx[j] * stride;
+          stride *= d.cols[j];
+          if (j != f) p = cmul(p, spectra[(size_t)(d.colbase[j] + cidx[j]) * m + k]);
+        }
+        const Cx<T> g = dspec[(size_t)col * m + k];
+        const Cx<T> t = cmul(g, cconj(p));
+        acc[h].x += t.x;
+        acc[h].y += t.y;
+      }
+    }
+    // inverse FFT of s = acc0 + i acc1 as conj(FFT(conj(s))) / m
+    a[k] = Cx<T>{acc[0].x - acc[1].y, -(acc[0].y + acc[1].x)};
+  }
+  __syncthreads();
+  const Cx<T>* F = fft_run<T>(a, b, plan, twp);
+  const T inv_m = (T)1 / (T)m;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) {
+    if (has[0]) dU[(size_t)(2 * blockIdx.x) * m + k] = F[k].x * inv_m;
+    if (has[1]) dU[(size_t)(2 * blockIdx.x + 1) * m + k] = -F[k].y * inv_m;
+  }
+}
+
+// dA_f[i, r] = S_f(i) dU[(colbase_f + r) m + H_f(i)] for every factor of the chain.
+template <typename T>
+struct GradOut {
+  T* p[TS_MAX_ORDER];
+};
+
+template <typename T>
+__global__ void k_adjoint_gather(ChainDesc d, int m, const T* __restrict__ dU, GradOut<T> grads) {
+  const int f = blockIdx.y;
+  if (f >= d.nf) return;
+  const int R = d.cols[f];
+  const int64_t total = d.rows[f] * R;
+  T* g = grads.p[f];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / R;
+    const int r = (int)(e - i * R);
+    const int32_t t = d.tables[f][i];
+    const int bin = entry_bin(t);
+    T v = bin < m ? dU[(size_t)(d.colbase[f] + r) * m + bin] : (T)0;
+    g[e] = entry_neg(t) ? -v : v;
+  }
+}
+
+template <typename T>
+ts_status launch_ts_adjoint(int nf, const int64_t* rows, const int* cols,
+                            const int32_t* const* tables, int m, const Cx<T>* tw,
+                            const Cx<T>* spectra, const T* dZ, Cx<T>* dspec, T* dU,
+                            T* const* grads, cudaStream_t st) {
+  ChainDesc d{};
+  GradOut<T> go{};
+  for (int f = 0; f < nf; ++f) go.p[f] = grads[f];
+  d.nf = nf;
+  int total = 0;
+  long ncols = 1;
+  int64_t maxrows = 0;
+  for (int f = 0; f < nf; ++f) {
+    d.rows[f] = rows[f];
+    d.cols[f] = cols[f];
+    d.colbase[f] = total;
+    d.tables[f] = tables[f];
+    total += cols[f];
+    ncols *= cols[f];
+    if (rows[f] * cols[f] > maxrows) maxrows = rows[f] * cols[f];
+  }
+  d.total_cols = total;
+  FftPlan plan = make_fft_plan(m);
+  plan.stage_tw = 3 * (size_t)m * sizeof(Cx<T>) <= kMaxSmem ? 1 : 0;
+  const size_t smem = (2 + plan.stage_tw) * (size_t)m * sizeof(Cx<T>);
+  TS_TRY(ensure_dynamic_smem((const void*)k_dz_spectra<T>, smem));
+  TS_TRY(ensure_dynamic_smem((const void*)k_adjoint_factor<T>, smem));
+  k_dz_spectra<T><<<ceil_div(ncols, 2), 512, smem, st>>>((int)ncols, plan, tw, dZ, dspec);
+  TS_LAUNCH_CHECK();
+  k_adjoint_factor<T><<<ceil_div(total, 2), 512, smem, st>>>(d, plan, tw, spectra, dspec, dU);
+  TS_LAUNCH_CHECK();
+  int blocks = ceil_div(maxrows, 256);
+  if (blocks > 1024) blocks = 1024;
+  k_adjoint_gather<T><<<dim3(blocks, nf), 256, 0, st>>>(d, m, dU, go);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
 template <typename T>
 TsChainJob<T> make_chain_job(int nf, const T* const* factors, const int64_t* rows,
                              const int* cols, const int32_t* const* tables, int m,
@@ -383,6 +559,14 @@ ts_status launch_ts_apply(int nf, const T* const* factors, const int64_t* rows, 
                                                 cudaStream_t);
 TS_INST_CHAIN(float)
 TS_INST_CHAIN(double)
+template ts_status launch_ts_adjoint<float>(int, const int64_t*, const int*,
+                                            const int32_t* const*, int, const Cx<float>*,
+                                            const Cx<float>*, const float*, Cx<float>*, float*,
+                                            float* const*, cudaStream_t);
+template ts_status launch_ts_adjoint<double>(int, const int64_t*, const int*,
+                                             const int32_t* const*, int, const Cx<double>*,
+                                             const Cx<double>*, const double*, Cx<double>*,
+                                             double*, double* const*, cudaStream_t);
 #undef TS_INST_CHAIN
 
 template ts_status launch_twiddles<float>(int, Cx<float>*, cudaStream_t);

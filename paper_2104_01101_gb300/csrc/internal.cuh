@@ -80,6 +80,15 @@ size_t chain_job_smem(const TsChainJob<T>& j);
 template <typename T>
 ts_status launch_ts_apply_batched(const TsChainJob<T>* jobs, int count, int max_spectra_blocks,
                                   int max_z_blocks, size_t smem, cudaStream_t st);
+// Adjoint of launch_ts_apply: given dZ = dL/dZ (column-major m x prod cols) and the
+// factor spectra the forward call left in `spectra`, writes dL/d(factor f) into
+// grads[f] (HOST array of nf device pointers, rows[f] x cols[f] row-major).
+// dspec: m x prod cols complex scratch; dU: m x (sum cols) real scratch.
+template <typename T>
+ts_status launch_ts_adjoint(int nf, const int64_t* rows, const int* cols,
+                            const int32_t* const* tables, int m, const Cx<T>* tw,
+                            const Cx<T>* spectra, const T* dZ, Cx<T>* dspec, T* dU,
+                            T* const* grads, cudaStream_t st);
 // Z (column-major m x prod cols) = TensorSketch of factors[0] (x) ... (x) factors[nf-1].
 // spectra: scratch of (sum cols) * m complex values; tw: twiddles from launch_twiddles.
 template <typename T>

@@ -89,6 +89,9 @@ _PROTOS = {
     "tucker_als_sketched": (I32, [TP, C.POINTER(I32), I32, I32, I32, OP, P, SZ, P, PP, P, P]),
     "cp_via_tucker_workspace_bytes": (I32, [TP, I32, C.POINTER(I32), I32, I32, OP, C.POINTER(SZ)]),
     "cp_via_tucker": (I32, [TP, I32, C.POINTER(I32), I32, I32, I32, OP, P, SZ, PP, P, P]),
+    "ts_fit_grad_scratch_bytes": (SZ, [I32, C.POINTER(I64), C.POINTER(I32), I32, I32, I32]),
+    "ts_fit_grad": (I32, [I32, C.POINTER(I64), C.POINTER(I32), I32, I32, I32, P, PP, PP, P, P, P,
+                          PP, P, SZ, P]),
     "ts_batch_workspace_bytes": (I32, [I32, TP, C.POINTER(I32), C.POINTER(I32), I32, OP,
                                        C.POINTER(SZ)]),
     "ts_batch_prepare": (I32, [I32, TP, C.POINTER(I32), C.POINTER(I32), I32, OP, P, SZ, PP, PP,
@@ -410,6 +413,54 @@ class TuckerPlan:
 
     def numeric_flag(self) -> int:
         return int(self.workspace[:4].view(torch.int32).item())
+
+
+def fit_grad(core, factors, Y, tables, mode: int, m: int):
+    """Sketched fit of subproblem ``mode`` and its gradient (ts_fit_grad):
+    returns (loss float64 0-dim tensor, grad_core, [grad of every factor]).
+    ``tables``: one packed int32 device table per mode (the entry of ``mode`` is ignored,
+    may be None)."""
+    N = len(factors)
+    dims = (C.c_int64 * N)(*[f.shape[0] for f in factors])
+    rk = (C.c_int32 * N)(*[f.shape[1] for f in factors])
+    dtype = _dt(core)
+    nbytes = lib().ts_fit_grad_scratch_bytes(N, dims, rk, mode, m, dtype)
+    if nbytes == 0:
+        raise TsError(2, "ts_fit_grad: invalid shape")
+    scr = _scratch(nbytes, core.device)
+    core = core.contiguous()
+    factors = [f.contiguous() for f in factors]
+    Y = Y.contiguous()
+    loss = torch.zeros((), dtype=torch.float64, device=core.device)
+    gcore = torch.empty_like(core)
+    gfac = [torch.empty_like(f) for f in factors]
+    tabs = [t if t is not None else factors[0] for t in tables]  # mode's entry ignored
+    _check(lib().ts_fit_grad(N, dims, rk, mode, m, dtype, _ptr(core), _ptr_array(factors),
+                             _ptr_array(tabs), _ptr(Y), _ptr(loss), _ptr(gcore),
+                             _ptr_array(gfac), _ptr(scr), scr.numel(), _stream()))
+    return loss, gcore, gfac
+
+
+class SketchedFit(torch.autograd.Function):
+    """L = 1/2 ||Z C_(n)^T A^(n)T - Y||^2 as a differentiable function of the core and the
+    factors; forward computes the loss and every gradient in one library call, backward
+    scales them by the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, Y, tables, mode, m, core, *factors):
+        loss, gcore, gfac = fit_grad(core, list(factors), Y, tables, mode, m)
+        ctx.save_for_backward(gcore, *gfac)
+        return loss.to(core.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        gcore, *gfac = ctx.saved_tensors
+        return (None, None, None, None, g * gcore, *[g * x for x in gfac])
+
+
+def sketched_fit(core, factors, Y, tables, mode: int, m: int):
+    """Differentiable sketched fit (see SketchedFit)."""
+    return SketchedFit.apply(Y, tables, mode, m, core, *factors)
 
 
 class TuckerBatch:

@@ -62,7 +62,7 @@ __host__ __device__ inline FusedLayout fused_layout(int r, int s, int k, int R, 
   L.P0 = take(tsz * kPb * kPs);
   L.P1 = take(tsz * kPb * kPs);
   L.rowold = take(tsz * kPb * (size_t)L.lda);
-  L.colbuf = take(tsz * r8 * kPs);
+  L.colbuf = take(tsz * (r8 + 8) * kPs);  // + 8 rows: the last 10-row update item's overhang
   L.QA = take(rsvd ? usz * (size_t)r * L.kq : 0);
   L.Qo = take(rsvd ? usz * (size_t)r * L.kq : 0);
   L.Qt = take(rsvd ? tsz * (size_t)r * L.ke : 0);
@@ -132,30 +132,32 @@ __device__ __forceinline__ void warp_inverse16(T (&a)[8], int* flag) {
   }
 }
 
-// One 8-row x 2-column tile per lane (columns jb and jb + 32) of the panel update.
-// Rows of the panel: A <- P A_panel (A11 <- P); rows outside: A <- A + colbuf rowold
-// (A21 <- colbuf = -A21 P).  The next panel's pivot block is left to warp 0.
-template <typename T>
+// One RPI-row x 2-column tile per lane (columns jb and jb + 32) of the panel update,
+// with L = colbuf holding -A21 P on rows outside the panel and P on the panel rows:
+// rows of the panel: A <- P A_panel (A11 <- P); rows outside: A <- A + L rowold
+// (A21 <- L).  The next panel's pivot block is left to warp 0.  Rows are classified one
+// by one (an item may straddle the panel's 16-row boundary).
+template <typename T, int RPI>
 __device__ __forceinline__ void gj_update_tile(T* A, int r, int ncol, int lda, int i0, int jb,
-                                               int p0, int nb, int q0, int nbn, const T* P,
-                                               const T* rowold, const T* colbuf) {
-  const bool in_panel = i0 >= p0 && i0 < p0 + kPb;
-  const bool in_next = nbn > 0 && i0 >= q0 && i0 < q0 + kPb;
+                                               int p0, int nb, int q0, int nbn,
+                                               const T* rowold, const T* L) {
   const int jc[2] = {jb, jb + 32};
-  bool valid[2], pcol[2], skip[2];
+  bool valid[2], pcol[2], ncolq[2];
 #pragma unroll
   for (int x = 0; x < 2; ++x) {
     valid[x] = jc[x] < ncol;
     pcol[x] = jc[x] >= p0 && jc[x] < p0 + nb;
-    skip[x] = in_next && jc[x] >= q0 && jc[x] < q0 + nbn;
+    ncolq[x] = nbn > 0 && jc[x] >= q0 && jc[x] < q0 + nbn;
   }
-  const T* Lrow = in_panel ? P + (i0 - p0) * kPs : colbuf + i0 * kPs;
-  T acc[2][8];
+  T acc[2][RPI];
 #pragma unroll
-  for (int rr = 0; rr < 8; ++rr)
+  for (int rr = 0; rr < RPI; ++rr) {
+    const int i = i0 + rr;
+    const bool keep = (i < p0 || i >= p0 + kPb) && i < r;
 #pragma unroll
-    for (int x = 0; x < 2; ++x)
-      acc[x][rr] = (!in_panel && valid[x] && i0 + rr < r) ? A[(i0 + rr) * lda + jc[x]] : (T)0;
+    for (int x = 0; x < 2; ++x) acc[x][rr] = (keep && valid[x]) ? A[i * lda + jc[x]] : (T)0;
+  }
+  const T* Lrow = L + i0 * kPs;
 #pragma unroll 1
   for (int u = 0; u < kPb; u += 4) {
     T b[2][4];
@@ -164,7 +166,7 @@ __device__ __forceinline__ void gj_update_tile(T* A, int r, int ncol, int lda, i
 #pragma unroll
       for (int x = 0; x < 2; ++x) b[x][q] = valid[x] ? rowold[(u + q) * lda + jc[x]] : (T)0;
 #pragma unroll
-    for (int rr = 0; rr < 8; ++rr) {
+    for (int rr = 0; rr < RPI; ++rr) {
       T l4[4];
       load4(Lrow + rr * kPs + u, l4);
 #pragma unroll
@@ -175,15 +177,14 @@ __device__ __forceinline__ void gj_update_tile(T* A, int r, int ncol, int lda, i
     }
   }
 #pragma unroll
-  for (int rr = 0; rr < 8; ++rr) {
+  for (int rr = 0; rr < RPI; ++rr) {
     const int i = i0 + rr;
     if (i >= r) break;
+    const bool in_next = nbn > 0 && i >= q0 && i < q0 + kPb;
 #pragma unroll
     for (int x = 0; x < 2; ++x) {
-      if (!valid[x] || skip[x]) continue;
-      T v = acc[x][rr];
-      if (pcol[x]) v = in_panel ? P[(i - p0) * kPs + (jc[x] - p0)] : colbuf[i * kPs + (jc[x] - p0)];
-      A[i * lda + jc[x]] = v;
+      if (!valid[x] || (in_next && ncolq[x])) continue;
+      A[i * lda + jc[x]] = pcol[x] ? Lrow[rr * kPs + (jc[x] - p0)] : acc[x][rr];
     }
   }
 }
@@ -211,7 +212,12 @@ __device__ void gauss_jordan(T* A, int r, int ncol, int lda, T* P0, T* P1, T* ro
     for (int t = 0; t < 8; ++t) P0[li * kPs + lh * 8 + t] = a8[t];
   }
   __syncthreads();
-  const int nc64 = (ncol + 63) / 64, nitems = ((r + 7) / 8) * nc64;
+  // rows per update item: the fewest that give every update warp at most one item
+  const int nw3 = nwarp - nwarp / 4;
+  const int nc64 = (ncol + 63) / 64;
+  const int r8 = (r + 7) & ~7;  // colbuf rows (the buffer's extent)
+  const int rpi = ((r + 7) / 8) * nc64 <= nw3 ? 8 : ((r + 9) / 10) * nc64 <= nw3 ? 10 : 8;
+  const int nitems = ((r + rpi - 1) / rpi) * nc64;
   int pb = 0;
   for (int p0 = 0; p0 < r; p0 += kPb, pb ^= 1) {
     const int nb = min(kPb, r - p0);
@@ -222,13 +228,22 @@ __device__ void gauss_jordan(T* A, int r, int ncol, int lda, T* P0, T* P1, T* ro
       const int t = e / ncol, j = e - t * ncol;
       rowold[t * lda + j] = t < nb ? A[(p0 + t) * lda + j] : (T)0;
     }
-    for (int e = tid; e < r * kPb; e += nthr) {
+    for (int e = tid; e < r8 * kPb; e += nthr) {
       const int i = e >> 4, u = e & 15;
-      if (i >= p0 && i < p0 + nb) continue;
-      T acc = 0;
-      if (u < nb)
-        for (int t = 0; t < nb; ++t) acc += A[i * lda + p0 + t] * P[t * kPs + u];
-      colbuf[i * kPs + u] = -acc;
+      if (i >= p0 && i < p0 + kPb) {  // the panel rows: P itself
+        colbuf[i * kPs + u] = P[(i - p0) * kPs + u];
+        continue;
+      }
+      T acc0 = 0, acc1 = 0;  // two chains; t >= nb reads stay inside the row (masked)
+      if (u < nb && i < r) {
+        const T* Ai = A + i * lda + p0;
+#pragma unroll
+        for (int t = 0; t < kPb; t += 2) {
+          if (t < nb) acc0 += Ai[t] * P[t * kPs + u];
+          if (t + 1 < nb) acc1 += Ai[t + 1] * P[(t + 1) * kPs + u];
+        }
+      }
+      colbuf[i * kPs + u] = -(acc0 + acc1);
     }
     __syncthreads();
     // (b) rank-nb update; warp 0 forms and inverts the next pivot block
@@ -261,10 +276,14 @@ __device__ void gauss_jordan(T* A, int r, int ncol, int lda, T* P0, T* P1, T* ro
     } else if ((warp & 3) != 0) {
       // The update runs on the warps of the other three SM sub-partitions (warp w on
       // sub-partition w % 4), so that warp 0's dependent chain is not starved of issue slots.
-      const int nw3 = nwarp - nwarp / 4, w3 = (warp >> 2) * 3 + (warp & 3) - 1;
-      for (int it = w3; it < nitems; it += nw3)
-        gj_update_tile<T>(A, r, ncol, lda, (it / nc64) * 8, (it % nc64) * 64 + lane, p0, nb, q0,
-                          nbn, P, rowold, colbuf);
+      const int w3 = (warp >> 2) * 3 + (warp & 3) - 1;
+      for (int it = w3; it < nitems; it += nw3) {
+        const int i0 = (it / nc64) * rpi, jb = (it % nc64) * 64 + lane;
+        if (rpi == 8)
+          gj_update_tile<T, 8>(A, r, ncol, lda, i0, jb, p0, nb, q0, nbn, rowold, colbuf);
+        else
+          gj_update_tile<T, 10>(A, r, ncol, lda, i0, jb, p0, nb, q0, nbn, rowold, colbuf);
+      }
     }
     __syncthreads();
   }
@@ -433,7 +452,7 @@ struct JacobiRound {
 template <typename U>
 __device__ U* block_jacobi(U* A, U* A2, U* V, int n, U tol, U floor_rel, int max_sweeps,
                            const int* sched, const int* memb, JacobiRound<U>& rd, int* flags,
-                           U* red) {
+                           int* smax, U* red) {
   const int tid = threadIdx.x, nthr = blockDim.x;
   const int np = (n + 1) & ~1, npairs = np >> 1, nrounds = np - 1;
   if (tid < 32) {
@@ -443,9 +462,15 @@ __device__ U* block_jacobi(U* A, U* A2, U* V, int n, U tol, U floor_rel, int max
     for (int o = 16; o > 0; o >>= 1) d = fmax(d, __shfl_xor_sync(kFull, d, o));
     if (tid == 0) red[0] = d;
   }
-  for (int i = tid; i < 32; i += nthr) flags[i] = 0;
+  for (int i = tid; i < 32; i += nthr) {
+    flags[i] = 0;
+    smax[i] = 0;
+  }
   __syncthreads();
   const U floor_abs = floor_rel * red[0], tol2 = tol * tol;
+  // A sweep whose largest rotation has |s| <= sqrt(tol) ends the loop: Jacobi converges
+  // quadratically, so the next sweep's angles would be ~tol, below the rotation test.
+  const float stop_s = (float)sqrt(tol);
   const int nblk = npairs * npairs, nitems = nblk + n * npairs;
   // rotation threads: the last npairs threads (they own no item when the block is large)
   const int rbase = nthr - npairs;
@@ -460,7 +485,10 @@ __device__ U* block_jacobi(U* A, U* A2, U* V, int n, U tol, U floor_rel, int max
     rd.q[0][tid] = q;
     rd.c[0][tid] = c;
     rd.s[0][tid] = s;
-    if (rot) flags[0] = 1;
+    if (rot) {
+      flags[0] = 1;
+      atomicMax(&smax[0], __float_as_int((float)fabs(s)));
+    }
   }
   __syncthreads();
   U* Ao = A;
@@ -519,7 +547,10 @@ __device__ U* block_jacobi(U* A, U* A2, U* V, int n, U tol, U floor_rel, int max
                 fast_div(theta >= (U)0 ? (U)1 : (U)-1, fabs(theta) + h * fast_rsqrt(h));
             c = unit_rsqrt(tt * tt + 1);
             s = tt * c;
-            if (sn < 32) flags[sn] = 1;
+            if (sn < 32) {
+              flags[sn] = 1;
+              atomicMax(&smax[sn], __float_as_int((float)fabs(s)));
+            }
           }
         }
         rd.p[cur ^ 1][ri] = p;
@@ -533,7 +564,7 @@ __device__ U* block_jacobi(U* A, U* A2, U* V, int n, U tol, U floor_rel, int max
       cur ^= 1;
       __syncthreads();
     }
-    if (!flags[sweep]) break;
+    if (!flags[sweep] || __int_as_float(smax[sweep]) <= stop_s) break;
   }
   return Ao;
 }
@@ -545,7 +576,7 @@ __device__ __forceinline__ void lrls_fused_body(const FusedArgs<T>& a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ JacobiRound<T> jround;
   __shared__ JacobiRound<double> jround64;
-  __shared__ int jflags[32];
+  __shared__ int jflags[32], jsmax[32];
   __shared__ T jred[1];
   __shared__ double jred64[1];
   __shared__ int order[kMaxEig];
@@ -690,7 +721,7 @@ __device__ __forceinline__ void lrls_fused_body(const FusedArgs<T>& a) {
   jacobi_schedule(n, sched, memb);
   __syncthreads();
   T* Kf = block_jacobi<T>(Kk, reinterpret_cast<T*>(smem_raw + L.Kk2), Vk, n, jacobi_tol<T>(),
-                          jacobi_floor<T>(), 20, sched, memb, jround, jflags, jred);
+                          jacobi_floor<T>(), 20, sched, memb, jround, jflags, jsmax, jred);
   if constexpr (POLISH64) {
     double* K64 = reinterpret_cast<double*>(smem_raw + L.K64);
     double* V64 = reinterpret_cast<double*>(smem_raw + L.V64);
@@ -734,7 +765,7 @@ __device__ __forceinline__ void lrls_fused_body(const FusedArgs<T>& a) {
     __syncthreads();
     const double* Kf64 = block_jacobi<double>(
         K64, reinterpret_cast<double*>(smem_raw + L.K64b), V64, n, jacobi_tol<double>(),
-        jacobi_floor<double>(), 10, sched, memb, jround64, jflags, jred64);
+        jacobi_floor<double>(), 10, sched, memb, jround64, jflags, jsmax, jred64);
     for (int e = tid; e < n * n; e += nthr) Vk[e] = (T)V64[e];
     if (tid < n) Kf[tid * n + tid] = (T)Kf64[tid * n + tid];
     __syncthreads();

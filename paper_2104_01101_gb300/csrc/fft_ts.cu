@@ -4,6 +4,8 @@
 // packed table), transformed by a shared-memory mixed-radix Stockham FFT, and the
 // spectra of every column multi-index are multiplied and inverse transformed.
 // Two real columns share one complex transform (x + i y), both forward and inverse.
+#include <cuda_bf16.h>
+
 #include "internal.cuh"
 
 namespace ts {
@@ -233,7 +235,9 @@ __device__ __forceinline__ void hadamard_ifft_body(const ChainDesc& d, int ncols
                                                    const FftPlan& plan,
                                                    const Cx<T>* __restrict__ tw,
                                                    const Cx<T>* __restrict__ spectra,
-                                                   T* __restrict__ Z, int bx) {
+                                                   T* __restrict__ Z, int bx,
+                                                   __nv_bfloat16* __restrict__ Zb = nullptr,
+                                                   int ldb = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = plan.m;
   Cx<T>* a = reinterpret_cast<Cx<T>*>(smem_raw);
@@ -270,8 +274,15 @@ __device__ __forceinline__ void hadamard_ifft_body(const ChainDesc& d, int ncols
   const Cx<T>* F = fft_run<T>(a, b, plan, twp);
   const T inv_m = (T)1 / (T)m;
   for (int k = threadIdx.x; k < m; k += blockDim.x) {
-    Z[(size_t)c0 * m + k] = F[k].x * inv_m;
-    if (has1) Z[(size_t)(c0 + 1) * m + k] = -F[k].y * inv_m;
+    const T z0 = F[k].x * inv_m, z1 = -F[k].y * inv_m;
+    Z[(size_t)c0 * m + k] = z0;
+    if (has1) Z[(size_t)(c0 + 1) * m + k] = z1;
+    if constexpr (sizeof(T) == 4) {
+      if (Zb) {  // row c of Z^T in BF16 (the precision form's product operand)
+        Zb[(size_t)c0 * ldb + k] = __float2bfloat16_rn((float)z0);
+        if (has1) Zb[(size_t)(c0 + 1) * ldb + k] = __float2bfloat16_rn((float)z1);
+      }
+    }
   }
 }
 
@@ -279,8 +290,9 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_hadamard_ifft(ChainDesc d, int ncols, FftPlan plan,
                                                        const Cx<T>* __restrict__ tw,
                                                        const Cx<T>* __restrict__ spectra,
-                                                       T* __restrict__ Z) {
-  hadamard_ifft_body<T>(d, ncols, plan, tw, spectra, Z, blockIdx.x);
+                                                       T* __restrict__ Z,
+                                                       __nv_bfloat16* __restrict__ Zb, int ldb) {
+  hadamard_ifft_body<T>(d, ncols, plan, tw, spectra, Z, blockIdx.x, Zb, ldb);
 }
 
 // Many independent chains (one per blockIdx.y), each as in launch_ts_apply.
@@ -523,7 +535,7 @@ ts_status launch_ts_apply_batched(const TsChainJob<T>* jobs, int count, int max_
 template <typename T>
 ts_status launch_ts_apply(int nf, const T* const* factors, const int64_t* rows, const int* cols,
                           const int32_t* const* tables, int m, const Cx<T>* tw, Cx<T>* spectra,
-                          T* Z, cudaStream_t st) {
+                          T* Z, cudaStream_t st, void* Zb_bf16, int ldb) {
   ChainDesc d{};
   d.nf = nf;
   int total = 0;
@@ -545,7 +557,8 @@ ts_status launch_ts_apply(int nf, const T* const* factors, const int64_t* rows, 
   TS_TRY(ensure_dynamic_smem((const void*)k_hadamard_ifft<T>, smem));
   k_factor_spectra<T><<<ceil_div(total, 2), 512, smem, st>>>(d, plan, tw, spectra);
   TS_LAUNCH_CHECK();
-  k_hadamard_ifft<T><<<ceil_div(ncols, 2), 512, smem, st>>>(d, (int)ncols, plan, tw, spectra, Z);
+  k_hadamard_ifft<T><<<ceil_div(ncols, 2), 512, smem, st>>>(
+      d, (int)ncols, plan, tw, spectra, Z, static_cast<__nv_bfloat16*>(Zb_bf16), ldb);
   TS_LAUNCH_CHECK();
   return TS_OK;
 }
@@ -573,10 +586,10 @@ template ts_status launch_twiddles<float>(int, Cx<float>*, cudaStream_t);
 template ts_status launch_twiddles<double>(int, Cx<double>*, cudaStream_t);
 template ts_status launch_ts_apply<float>(int, const float* const*, const int64_t*, const int*,
                                           const int32_t* const*, int, const Cx<float>*,
-                                          Cx<float>*, float*, cudaStream_t);
+                                          Cx<float>*, float*, cudaStream_t, void*, int);
 template ts_status launch_ts_apply<double>(int, const double* const*, const int64_t*, const int*,
                                            const int32_t* const*, int, const Cx<double>*,
-                                           Cx<double>*, double*, cudaStream_t);
+                                           Cx<double>*, double*, cudaStream_t, void*, int);
 
 }  // namespace ts
 

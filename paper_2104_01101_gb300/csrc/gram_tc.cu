@@ -293,8 +293,9 @@ ts_status gram_tc_map(const void* base, int rows, int K, CUtensorMap* map) {
 int gram_tc_splits(int M, int N, int K) {
   const int tiles = ceil_div(M, kBM) * ceil_div(N, kBN);
   const int nkb = ceil_div(K > 0 ? K : 1, kBK);
+  // at least four K blocks per split: the 4-stage ring fills, and fewer partials to add
   int splits = ceil_div(152, tiles);
-  if (splits > ceil_div(nkb, 2)) splits = ceil_div(nkb, 2);
+  if (splits > ceil_div(nkb, 4)) splits = ceil_div(nkb, 4);
   if (splits > 32) splits = 32;
   return splits < 1 ? 1 : splits;
 }

@@ -91,10 +91,11 @@ ts_status launch_ts_adjoint(int nf, const int64_t* rows, const int* cols,
                             T* const* grads, cudaStream_t st);
 // Z (column-major m x prod cols) = TensorSketch of factors[0] (x) ... (x) factors[nf-1].
 // spectra: scratch of (sum cols) * m complex values; tw: twiddles from launch_twiddles.
+// Zb_bf16 (FP32 only, nullable): Z^T also written in BF16, row c of Z^T at c * ldb.
 template <typename T>
 ts_status launch_ts_apply(int nf, const T* const* factors, const int64_t* rows, const int* cols,
                           const int32_t* const* tables, int m, const Cx<T>* tw, Cx<T>* spectra,
-                          T* Z, cudaStream_t st);
+                          T* Z, cudaStream_t st, void* Zb_bf16 = nullptr, int ldb = 0);
 
 // ---------------------------------------------------------------- input_sketch.cu
 // One output of a pass over the data tensor: Y (nbins x dims[mode], row-major) =

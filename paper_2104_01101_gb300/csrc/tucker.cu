@@ -216,7 +216,8 @@ struct Work {
   double* levscr;
   T* fitQ;
   double* fitacc;
-  void* Bt[TS_MAX_ORDER];  // BF16 precision form: [Z | Y Omega | Y]^T per mode (rows x ld)
+  void* Bt[TS_MAX_ORDER];  // BF16 precision form: [Z | Y Omega | Y]^T per mode and sweep
+  size_t bt_stride[TS_MAX_ORDER];  // bytes between consecutive sweeps' operands
   float* gpart;            // its split-K partial sums
 };
 
@@ -315,7 +316,8 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
     for (int n = 0; n < N; ++n) {
       if (!S.fused[n]) continue;
       const int cols = bf16_cols(S, n, (int)X.dims[n]);
-      w.Bt[n] = b.take<uint16_t>((size_t)cols * gram_tc_ld(m));
+      w.bt_stride[n] = (size_t)cols * gram_tc_ld(m) * 2;
+      w.Bt[n] = b.take<uint16_t>((size_t)cols * gram_tc_ld(m) * S.sweeps);
       const size_t p = gram_tc_partial_elems(S.r[n], cols, m);
       if (p > part) part = p;
     }
@@ -335,10 +337,11 @@ static OutView<T> ov(T* p, long rs, long cs) {
 }
 
 // The BF16 operand of one subproblem: rows [0, r) Z^T, then (Y Omega)^T, then Y^T;
-// y_packed: Y^T is already in place (written once per pass over T).
+// prefilled: Z^T (written by the inverse FFT), (Y Omega)^T and Y^T (written once per pass
+// over T) are already in place.
 struct Bf16Op {
   void* Bt;
-  bool y_packed;
+  bool prefilled;
 };
 
 // Sketched subproblem on Z = ZW[:, :r] (column-major) and Y (m x s) -> CnT (r x R),
@@ -374,9 +377,11 @@ static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc,
         const int N = r + kk + s;
         char* bt = static_cast<char*>(bf->Bt);
         const size_t row = 2 * (size_t)gram_tc_ld(m);
-        TS_TRY(pack_bf16(ZW, m, 1, r, m, bt, st));  // Z^T: Z is column-major
-        if (kk) TS_TRY(pack_bf16(yv.p, yv.cs, yv.rs, kk, m, bt + r * row, st));
-        if (!bf->y_packed) TS_TRY(pack_bf16(Y, 1, s, s, m, bt + (size_t)(r + kk) * row, st));
+        if (!bf->prefilled) {
+          TS_TRY(pack_bf16(ZW, m, 1, r, m, bt, st));  // Z^T: Z is column-major
+          if (kk) TS_TRY(pack_bf16(yv.p, yv.cs, yv.rs, kk, m, bt + r * row, st));
+          TS_TRY(pack_bf16(Y, 1, s, s, m, bt + (size_t)(r + kk) * row, st));
+        }
         CUtensorMap ma, mb;
         TS_TRY(gram_tc_map(bt, r, m, &ma));
         TS_TRY(gram_tc_map(bt, N, m, &mb));
@@ -497,15 +502,22 @@ static ts_status rrf_all(const ts_tensor& X, const Shape& S, uint64_t seed, Work
 // BF16 precision form: Y_n^T into the last s_n rows of each mode's operand, once per
 // pass over T (the sketches are fixed between passes).
 template <typename T>
-static ts_status pack_rhs_bf16(const ts_tensor& X, const Shape& S, Work<T>& w, cudaStream_t st) {
+static ts_status pack_rhs_bf16(const ts_tensor& X, const Shape& S, Work<T>& w, int t0, int nt,
+                               cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
     if (!S.bf16gram || S.kind != TS_TENSORSKETCH) return TS_OK;
+    const size_t row = 2 * (size_t)gram_tc_ld(S.m);
     for (int n = 0; n < S.N; ++n) {
       if (!S.fused[n]) continue;
-      const int s = (int)X.dims[n];
-      const int first = bf16_cols(S, n, s) - s;
-      char* dst = static_cast<char*>(w.Bt[n]) + (size_t)first * 2 * gram_tc_ld(S.m);
-      TS_TRY(pack_bf16(w.Y[n], 1, s, s, S.m, dst, st));
+      const int s = (int)X.dims[n], r = S.r[n];
+      const int kk = S.solve == TS_SOLVE_RSVD ? S.kc[n] : 0;
+      for (int t = t0; t < t0 + nt; ++t) {
+        char* bt = static_cast<char*>(w.Bt[n]) + (size_t)t * w.bt_stride[n];
+        if (kk)
+          TS_TRY(pack_bf16(w.YOm + S.yom_off[n] + (size_t)t * kk, 1, (long)S.sweeps * kk, kk,
+                           S.m, bt + (size_t)r * row, st));
+        TS_TRY(pack_bf16(w.Y[n], 1, s, s, S.m, bt + (size_t)(r + kk) * row, st));
+      }
     }
   }
   return TS_OK;
@@ -550,9 +562,9 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
     TS_TRY(phase(opt, 2, st));
     TS_TRY(sketch_rhs_all<T>(X, S, w, st));
     TS_TRY(phase(opt, 3, st));
-    TS_TRY(pack_rhs_bf16<T>(X, S, w, st));
-    if (S.solve == TS_SOLVE_RSVD)
-      TS_TRY(rhs_times_omegas<T>(X, S, w, 0, opt.resketch_each_sweep ? 1 : S.sweeps, st));
+    const int npass = opt.resketch_each_sweep ? 1 : S.sweeps;
+    if (S.solve == TS_SOLVE_RSVD) TS_TRY(rhs_times_omegas<T>(X, S, w, 0, npass, st));
+    TS_TRY(pack_rhs_bf16<T>(X, S, w, 0, npass, st));
   } else {
     TS_TRY(phase(opt, 2, st));
     TS_TRY(phase(opt, 3, st));
@@ -565,8 +577,8 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
     if (S.kind == TS_TENSORSKETCH && opt.resketch_each_sweep && sweep > 0) {
       TS_TRY(build_ts_tables<T>(X, S, opt.seed, sweep, w, st));
       TS_TRY(sketch_rhs_all<T>(X, S, w, st));
-      TS_TRY(pack_rhs_bf16<T>(X, S, w, st));
       if (S.solve == TS_SOLVE_RSVD) TS_TRY(rhs_times_omegas<T>(X, S, w, sweep, 1, st));
+      TS_TRY(pack_rhs_bf16<T>(X, S, w, sweep, 1, st));
     }
     for (int n = 0; n < N; ++n) {
       const T* Yn;
@@ -580,7 +592,11 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
             cols[nf] = S.ranks[k];
             ++nf;
           }
-        TS_TRY(launch_ts_apply<T>(nf, chain, rows, cols, ctab, m, w.tw, w.spectra, w.ZW, st));
+        void* zb = (S.bf16gram && S.fused[n])
+                       ? static_cast<char*>(w.Bt[n]) + (size_t)sweep * w.bt_stride[n]
+                       : nullptr;
+        TS_TRY(launch_ts_apply<T>(nf, chain, rows, cols, ctab, m, w.tw, w.spectra, w.ZW, st, zb,
+                                  gram_tc_ld(m)));
         Yn = w.Y[n];
       } else {
         TS_TRY(launch_leverage<T>(X, n, S.ranks, (const T* const*)factors, m, opt.seed, sweep,
@@ -599,7 +615,9 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
         yv = mv<T>(w.YOm + S.yom_off[n] + (size_t)sweep * S.kc[n], ldo, 1);
         yom = &yv;
       }
-      Bf16Op bop{w.Bt[n], S.kind == TS_TENSORSKETCH};
+      Bf16Op bop{S.bf16gram ? static_cast<char*>(w.Bt[n]) + (size_t)sweep * w.bt_stride[n]
+                            : nullptr,
+                 S.kind == TS_TENSORSKETCH};
       const Bf16Op* bf = (S.bf16gram && S.fused[n]) ? &bop : nullptr;
       TS_TRY(solve_subproblem<T>(m, S.r[n], (int)X.dims[n], S.ranks[n], S.solve, S.kc[n],
                                  S.fp64solve, Om, ldo, yom, Yn, w, factors[n], core, map, st,

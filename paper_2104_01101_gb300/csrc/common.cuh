@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <utility>
 #include <stdint.h>
 #include <stddef.h>
 
@@ -48,6 +49,35 @@ void note_launch();
 ts_status ensure_dynamic_smem(const void* fn, size_t bytes);
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Programmatic dependent launch.  A kernel launched by launch_pdl may be scheduled while
+// the kernel before it in the stream is still running: pdl_trigger() at its start lets
+// the next kernel launch once every block of this one has started, and pdl_wait()
+// blocks until the previous kernel has completed and its writes are visible, so a
+// kernel calls it before reading anything the previous one wrote.  Both are no-ops
+// when the launch carried no programmatic dependency.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+ts_status launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                     cudaStream_t st, Args&&... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TS_CUDA(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
 
 // Bump allocator over caller-provided scratch.  With base == nullptr it only
 // measures, which is how every *_bytes query is answered.

@@ -226,6 +226,8 @@ template <typename T>
 __global__ void __launch_bounds__(512) k_factor_spectra(ChainDesc d, FftPlan plan,
                                                         const Cx<T>* __restrict__ tw,
                                                         Cx<T>* __restrict__ spectra) {
+  pdl_trigger();
+  pdl_wait();
   factor_spectra_body<T>(d, plan, tw, spectra, blockIdx.x);
 }
 
@@ -292,6 +294,8 @@ __global__ void __launch_bounds__(512) k_hadamard_ifft(ChainDesc d, int ncols, F
                                                        const Cx<T>* __restrict__ spectra,
                                                        T* __restrict__ Z,
                                                        __nv_bfloat16* __restrict__ Zb, int ldb) {
+  pdl_trigger();
+  pdl_wait();
   hadamard_ifft_body<T>(d, ncols, plan, tw, spectra, Z, blockIdx.x, Zb, ldb);
 }
 
@@ -555,11 +559,11 @@ ts_status launch_ts_apply(int nf, const T* const* factors, const int64_t* rows, 
   const size_t smem = (2 + plan.stage_tw) * (size_t)m * sizeof(Cx<T>);
   TS_TRY(ensure_dynamic_smem((const void*)k_factor_spectra<T>, smem));
   TS_TRY(ensure_dynamic_smem((const void*)k_hadamard_ifft<T>, smem));
-  k_factor_spectra<T><<<ceil_div(total, 2), 512, smem, st>>>(d, plan, tw, spectra);
-  TS_LAUNCH_CHECK();
-  k_hadamard_ifft<T><<<ceil_div(ncols, 2), 512, smem, st>>>(
-      d, (int)ncols, plan, tw, spectra, Z, static_cast<__nv_bfloat16*>(Zb_bf16), ldb);
-  TS_LAUNCH_CHECK();
+  TS_TRY(launch_pdl(k_factor_spectra<T>, dim3(ceil_div(total, 2)), dim3(512), smem, st, d, plan,
+                    tw, spectra));
+  TS_TRY(launch_pdl(k_hadamard_ifft<T>, dim3(ceil_div(ncols, 2)), dim3(512), smem, st, d,
+                    (int)ncols, plan, tw, static_cast<const Cx<T>*>(spectra), Z,
+                    static_cast<__nv_bfloat16*>(Zb_bf16), ldb));
   return TS_OK;
 }
 

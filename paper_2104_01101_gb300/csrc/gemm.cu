@@ -138,6 +138,8 @@ __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, Ma
                                              MatView<T> B1, int n1, MatView<T> B2, int n2,
                                              MatView<T> B3, T alpha, T beta, OutView<T> C,
                                              T* __restrict__ partial) {
+  pdl_trigger();
+  pdl_wait();
   gemm_tile<T, BM, BN>(M, N, K, kchunk, A, B1, n1, B2, n2, B3, alpha, beta, C, partial,
                        blockIdx.x, blockIdx.y, blockIdx.z);
 }
@@ -166,6 +168,8 @@ ts_status launch_gemm_batched(const GemmJob<T>* jobs, int count, int maxM, int m
 template <typename T>
 __global__ void k_gemm_reduce(int M, int N, int splits, const T* __restrict__ partial, T alpha,
                               T beta, OutView<T> C) {
+  pdl_trigger();
+  pdl_wait();
   const size_t MN = (size_t)M * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < MN;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -204,18 +208,17 @@ ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
   dim3 grid(ceil_div(N, bm), ceil_div(M, bm), splits);
   T* part = splits > 1 ? split->partial : nullptr;
   if (small)
-    k_gemm<T, 32, 32><<<grid, NT, 0, st>>>(M, N, K, kchunk, A, B1, n1, B2, n2, B3, (T)alpha,
-                                           (T)beta, C, part);
+    TS_TRY(launch_pdl(k_gemm<T, 32, 32>, grid, dim3(NT), 0, st, M, N, K, kchunk, A, B1, n1, B2,
+                      n2, B3, (T)alpha, (T)beta, C, part));
   else
-    k_gemm<T, 64, 64><<<grid, NT, 0, st>>>(M, N, K, kchunk, A, B1, n1, B2, n2, B3, (T)alpha,
-                                           (T)beta, C, part);
-  TS_LAUNCH_CHECK();
+    TS_TRY(launch_pdl(k_gemm<T, 64, 64>, grid, dim3(NT), 0, st, M, N, K, kchunk, A, B1, n1, B2,
+                      n2, B3, (T)alpha, (T)beta, C, part));
   if (splits > 1) {
     const size_t MN = (size_t)M * N;
     int blocks = (int)((MN + 255) / 256);
     if (blocks > 2048) blocks = 2048;
-    k_gemm_reduce<T><<<blocks, 256, 0, st>>>(M, N, splits, part, (T)alpha, (T)beta, C);
-    TS_LAUNCH_CHECK();
+    TS_TRY(launch_pdl(k_gemm_reduce<T>, dim3(blocks), dim3(256), 0, st, M, N, splits,
+                      static_cast<const T*>(part), (T)alpha, (T)beta, C));
   }
   return TS_OK;
 }
@@ -226,9 +229,8 @@ ts_status launch_split_reduce(int M, int N, int splits, const T* partial, T* C, 
   const size_t MN = (size_t)M * N;
   int blocks = (int)((MN + 255) / 256);
   if (blocks > 2048) blocks = 2048;
-  k_gemm_reduce<T><<<blocks, 256, 0, st>>>(M, N, splits, partial, (T)1, (T)0, OutView<T>{C, ldc, 1});
-  TS_LAUNCH_CHECK();
-  return TS_OK;
+  return launch_pdl(k_gemm_reduce<T>, dim3(blocks), dim3(256), 0, st, M, N, splits, partial, (T)1,
+                    (T)0, OutView<T>{C, ldc, 1});
 }
 
 template <typename T>

@@ -91,6 +91,8 @@ __host__ __device__ constexpr unsigned mma_idesc() {
 __global__ void __launch_bounds__(kThreads) k_gram_tc(const __grid_constant__ CUtensorMap mapA,
                                                       const __grid_constant__ CUtensorMap mapB,
                                                       GramArgs g) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ unsigned char smem_raw[];
   __shared__ __align__(8) unsigned long long full_bar[kStages], empty_bar[kStages], done_bar;
   __shared__ unsigned tmem_slot;
@@ -330,8 +332,7 @@ ts_status gram_tc(const CUtensorMap& mapA, const CUtensorMap& mapB, int M, int N
   const size_t smem = (size_t)kStages * 2 * kTileBytes + 1024;
   TS_TRY(ensure_dynamic_smem((const void*)k_gram_tc, smem));
   dim3 grid(ceil_div(N, kBN), ceil_div(M, kBM), splits);
-  k_gram_tc<<<grid, kThreads, smem, st>>>(mapA, mapB, g);
-  TS_LAUNCH_CHECK();
+  TS_TRY(launch_pdl(k_gram_tc, grid, dim3(kThreads), smem, st, mapA, mapB, g));
   if (splits > 1) TS_TRY(launch_split_reduce<float>(M, N, splits, partial, C, ldc, st));
   return TS_OK;
 }

@@ -872,6 +872,8 @@ __device__ __forceinline__ void lrls_fused_body(const FusedArgs<T>& a) {
 
 template <typename T, typename U, bool POLISH64>
 __global__ void __launch_bounds__(kThreads) k_lrls_fused(FusedArgs<T> a) {
+  pdl_trigger();
+  pdl_wait();
   lrls_fused_body<T, U, POLISH64>(a);
 }
 
@@ -953,15 +955,11 @@ ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, co
   if constexpr (sizeof(T) == 4) {
     if (polish) {
       TS_TRY(ensure_dynamic_smem((const void*)k_lrls_fused<T, double, true>, smem));
-      k_lrls_fused<T, double, true><<<1, kThreads, smem, st>>>(a);
-      TS_LAUNCH_CHECK();
-      return TS_OK;
+      return launch_pdl(k_lrls_fused<T, double, true>, dim3(1), dim3(kThreads), smem, st, a);
     }
   }
   TS_TRY(ensure_dynamic_smem((const void*)k_lrls_fused<T, T, false>, smem));
-  k_lrls_fused<T, T, false><<<1, kThreads, smem, st>>>(a);
-  TS_LAUNCH_CHECK();
-  return TS_OK;
+  return launch_pdl(k_lrls_fused<T, T, false>, dim3(1), dim3(kThreads), smem, st, a);
 }
 
 template <typename T>

@@ -148,6 +148,35 @@ def leverage_sample_mode(ell: np.ndarray, u: np.ndarray):
     return idx, ell[idx] / total
 
 
+def leverage_select_det(scores_per_mode, m: int) -> np.ndarray:
+    """Deterministic leverage selection (the "Lev-fix" variant of Sec. 3.2): the m
+    multi-indices with the largest Kronecker score prod_k l_k(i_k), ties broken by the
+    lower C-order linear index; returned in ascending linear index."""
+    sc = np.ones(1)
+    for ell in scores_per_mode:
+        sc = (sc[:, None] * ell[None, :]).reshape(-1)
+    m = min(m, sc.shape[0])
+    order = np.lexsort((np.arange(sc.shape[0]), -sc))  # score descending, index ascending
+    return np.sort(order[:m])
+
+
+def leverage_sketch_dense_det(T: np.ndarray, n: int, factors, m: int):
+    """Sketched LHS and RHS of subproblem n by deterministic leverage sampling: the rows
+    of P^(n) and the fibres of T at the multi-indices of leverage_select_det, without
+    rescaling.  Returns Z (m x prod R_k), Y (m x s_n) and the multi-indices."""
+    N = T.ndim
+    others = [k for k in range(N) if k != n]
+    lin = leverage_select_det([leverage_scores(factors[k]) for k in others], m)
+    samples = np.stack(np.unravel_index(lin, [T.shape[k] for k in others]), axis=1)
+    Z = np.ones((lin.shape[0], 1))
+    for j, k in enumerate(others):
+        rows = factors[k][samples[:, j], :]
+        Z = (Z[:, :, None] * rows[:, None, :]).reshape(lin.shape[0], -1)
+    Tn = np.moveaxis(T, n, -1)
+    Y = Tn[tuple(samples[:, j] for j in range(len(others)))]
+    return Z, Y, samples
+
+
 def leverage_sketch_dense(T: np.ndarray, n: int, factors, m: int, seed: int, sweep: int):
     """Sketched LHS and RHS of subproblem n by leverage-score sampling.
 

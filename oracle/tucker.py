@@ -17,7 +17,7 @@ import numpy as np
 
 from . import rng
 from .sketch import (input_sketch_coo, input_sketch_dense, leverage_sketch_dense,
-                     ts_apply_fft, ts_tables_for_mode)
+                     leverage_sketch_dense_det, ts_apply_fft, ts_tables_for_mode)
 from .solve import canonical_signs, lrls_exact, rsvd_lrls, rsvd_oversampled_rank
 from .tensor import fold, kron_chain, reconstruct, ttm, unfold
 
@@ -184,8 +184,9 @@ def sketch_tucker_als(X, ranks, m: int, sweeps: int, seed: int, kind: str = "ts"
     """Alg. 4.  Returns (core, factors, per-sweep residuals or []).
 
     kind       "ts" (TensorSketch, RHS sketch built once and reused across sweeps
-               unless ``resketch``) or "lev" (leverage-score sampling, dense only,
-               redrawn for every subproblem).
+               unless ``resketch``), "lev" (leverage-score sampling, dense only,
+               redrawn for every subproblem) or "lev_det" (the m rows of largest
+               leverage score, dense only, reselected for every subproblem).
     solve      "rsvd" (Alg. 5, the routine Alg. 4 calls) or "exact" (the solution
                Theorem 4.1 is stated for).
     init_factors  replaces the RRF initialisation of modes 2..N when given.
@@ -221,6 +222,8 @@ def sketch_tucker_als(X, ranks, m: int, sweeps: int, seed: int, kind: str = "ts"
                 Z = ts_apply_fft([factors[k] for k in others], tables, m)
             elif kind == "lev":
                 Z, Y, _, _ = leverage_sketch_dense(X, n, factors, m, seed, sweep)
+            elif kind == "lev_det":
+                Z, Y, _ = leverage_sketch_dense_det(X, n, factors, m)
             else:
                 raise ValueError(kind)
             if solve == "exact":

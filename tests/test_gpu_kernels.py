@@ -210,8 +210,13 @@ def _solve_problem(seed, m, r, s, R, noise):
     return Z, Z @ X0 + noise * g.standard_normal((m, s))
 
 
+# The single-block Gauss-Jordan cuts its rank-16 update into 8-row items, or 10-row
+# items when 8 would give some update warp a second item: r = 100, 105, 110, 120 take
+# 10-row items (straddling the 16-row panels; r = 105 overhangs the last one), r = 125
+# falls back to 8-row items in several rounds, r = 13 and 25 fit 8-row items.
 @pytest.mark.parametrize("m,r,s,R", [(400, 25, 40, 5), (2000, 100, 400, 10), (97, 13, 31, 3),
-                                     (3000, 125, 300, 12)])
+                                     (3000, 125, 300, 12), (1500, 120, 200, 3),
+                                     (1500, 105, 300, 6), (1500, 110, 300, 6)])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_rsvd_lrls_matches_oracle(ts, m, r, s, R, dtype):
     Z, Y = _solve_problem(3, m, r, s, R, 0.05)

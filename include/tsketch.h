@@ -56,7 +56,7 @@ typedef enum {
 
 typedef enum { TS_F32 = 0, TS_F64 = 1 } ts_dtype;
 typedef enum { TS_DENSE = 0, TS_COO = 1 } ts_format;
-typedef enum { TS_TENSORSKETCH = 0, TS_LEVERAGE = 1 } ts_sketch_kind;
+typedef enum { TS_TENSORSKETCH = 0, TS_LEVERAGE = 1, TS_LEVERAGE_DET = 2 } ts_sketch_kind;
 typedef enum { TS_SOLVE_RSVD = 0, TS_SOLVE_EXACT = 1 } ts_solve_kind;
 
 /* Purposes of the library's random objects (the top byte of their tag). */
@@ -273,6 +273,17 @@ ts_status ts_leverage_sketch(const ts_tensor* X, int32_t mode, const int32_t* ra
                              void* Z_out, void* Y_out, int32_t* samples_out, void* scratch,
                              size_t scratch_bytes, ts_stream stream);
 
+/* Deterministic leverage sketch ("Lev-fix", Sec. 3.2; kind TS_LEVERAGE_DET of
+ * tucker_als_sketched): the min(m, C) multi-indices (i_k)_{k != mode} of largest score
+ * prod_k l^(k)_{i_k} (C = prod_{k != mode} dims[k]; scores as above, products in FP64
+ * rounded in ascending k), ties to the lower C-order linear index, in ascending linear
+ * index; rows are not rescaled (weight 1), rows j >= C are zero.  Arguments and scratch
+ * as ts_leverage_sketch (no seed: nothing is drawn). */
+ts_status ts_leverage_sketch_det(const ts_tensor* X, int32_t mode, const int32_t* ranks,
+                                 const void* const* factors, int32_t m, void* Z_out, void* Y_out,
+                                 int32_t* samples_out, void* scratch, size_t scratch_bytes,
+                                 ts_stream stream);
+
 /* ------------------------------------------------------------------------- */
 /* Relative residual ||T - C x_1 A^(1) ... x_N A^(N)||_F / ||T||_F (Sec. 7 fitness
  * is 1 minus this).  Dense: direct reconstruction streamed against T with FP64
@@ -292,9 +303,10 @@ ts_status ts_fitness(const ts_tensor* X, const int32_t* ranks, const void* core,
  * Initialisation: Init-RRF for modes 1..N-1 (0-based) unless opt->init_given.
  * Each sweep updates modes 0..N-1 in order; subproblem n forms Z = S P^(n) and
  * Y = S T_(n)^T with TensorSketch (Y formed once and reused, or redrawn every
- * sweep with resketch_each_sweep) or leverage-score sampling (redrawn every
- * subproblem, dense tensors only), then solves it (opt->solve) and writes A^(n)
- * and the core.
+ * sweep with resketch_each_sweep), leverage-score sampling (redrawn every
+ * subproblem, dense tensors only) or deterministic leverage selection
+ * (TS_LEVERAGE_DET: the m rows of largest score, reselected every subproblem, dense
+ * only), then solves it (opt->solve) and writes A^(n) and the core.
  * Outputs: core_out (prod ranks, C order), factors_inout (HOST array of order
  * device pointers, dims[k] x ranks[k]), residual_out (DEVICE, nullable):
  * `sweeps` doubles if opt->track_fit else one double, the final relative residual.

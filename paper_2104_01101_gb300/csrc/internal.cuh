@@ -278,7 +278,8 @@ size_t leverage_scratch_doubles(const ts_tensor& X, int mode, int m);
 template <typename T>
 ts_status launch_leverage(const ts_tensor& X, int mode, const int* ranks, const T* const* factors,
                           int m, uint64_t seed, int sweep, T* Z, T* Y, int32_t* samples,
-                          double* scratch, cudaStream_t st);
+                          double* scratch, cudaStream_t st,
+                          bool det = false);
 
 // ---------------------------------------------------------------- cp.cu
 // HOSVD initialisation and CP-ALS sweeps on a core of the given ranks; A[k] is

@@ -65,19 +65,150 @@ __global__ void k_lev_sample(LevDesc d, int m, uint64_t seed, int sweep, double*
   }
 }
 
+// ---------------------------------------------------------------- deterministic selection
+
+// Block-wide exclusive prefix sum of one value per thread (blockDim.x <= 1024); returns
+// this thread's prefix and writes the total to *total.
+__device__ __forceinline__ long block_exclusive_scan(long v, long* warp_sums, long* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long t = lane < nw ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const long y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < nw) warp_sums[lane] = t;  // inclusive warp totals
+  }
+  __syncthreads();
+  const long base = warp ? warp_sums[warp - 1] : 0;
+  *total = warp_sums[nw - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+// The "Lev-fix" variant of Sec. 3.2: the m multi-indices (i_k)_{k != n} of largest
+// score prod_k l_k(i_k) (modes ascending, FP64 products rounded left to right), ties to
+// the lower C-order linear index, written to samples in ascending linear index.  One
+// block.  The m-th largest score is found by a radix select on the bit patterns of the
+// (non-negative) scores, 8 bits at a time from the top; each thread then owns a
+// contiguous chunk of candidates and two prefix sums place the selected ones in order.
+// Rows j >= min(m, C) get the multi-index 0 and are zeroed by the gather.
+__global__ void __launch_bounds__(1024) k_lev_select_det(LevDesc d, int m, long C,
+                                                          const double* __restrict__ ell,
+                                                          double* __restrict__ score,
+                                                          int32_t* __restrict__ samples) {
+  __shared__ unsigned hist[256];
+  __shared__ long warp_sums[32];
+  __shared__ unsigned long long s_prefix;
+  __shared__ long s_above;
+  const int tid = threadIdx.x, nthr = blockDim.x;
+  const int nm1 = d.order - 1;
+  int km[TS_MAX_ORDER], sz[TS_MAX_ORDER];
+  for (int k = 0, j = 0; k < d.order; ++k)
+    if (k != d.mode) {
+      km[j] = k;
+      sz[j] = (int)d.dims[k];
+      ++j;
+    }
+  // scores of every candidate (C order over the modes k != n, last fastest)
+  for (long c = tid; c < C; c += nthr) {
+    long rem = c;
+    int idx[TS_MAX_ORDER];
+    for (int j = nm1 - 1; j >= 0; --j) {
+      idx[j] = (int)(rem % sz[j]);
+      rem /= sz[j];
+    }
+    double p = 1.0;
+    for (int j = 0; j < nm1; ++j) p = __dmul_rn(p, ell[d.off[km[j]] + idx[j]]);
+    score[c] = p;
+  }
+  const long want = m < C ? m : C;
+  if (tid == 0) {
+    s_prefix = 0;
+    s_above = 0;
+  }
+  __syncthreads();
+  // radix select: after the loop s_prefix holds the bits of the want-th largest score
+  for (int shift = 56; shift >= 0; shift -= 8) {
+    for (int i = tid; i < 256; i += nthr) hist[i] = 0;
+    __syncthreads();
+    const unsigned long long pre = s_prefix;
+    const unsigned long long mask = shift == 56 ? 0ull : (~0ull << (shift + 8));
+    for (long c = tid; c < C; c += nthr) {
+      const unsigned long long b = (unsigned long long)__double_as_longlong(score[c]);
+      if ((b & mask) == pre) atomicAdd(&hist[(b >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      long above = s_above;
+      int digit = 255;
+      for (; digit > 0; --digit) {
+        if (above + (long)hist[digit] >= want) break;
+        above += hist[digit];
+      }
+      s_above = above;  // candidates strictly above the chosen digit so far
+      s_prefix = pre | ((unsigned long long)digit << shift);
+    }
+    __syncthreads();
+  }
+  const unsigned long long kth = s_prefix;
+  const long need_ties = want - s_above;  // the lowest-index candidates equal to kth
+  // chunk per thread, in index order
+  const long per = (C + nthr - 1) / nthr;
+  const long c0 = (long)tid * per, c1 = c0 + per < C ? c0 + per : C;
+  long ties = 0;
+  for (long c = c0; c < c1; ++c)
+    ties += (unsigned long long)__double_as_longlong(score[c]) == kth;
+  long tot;
+  long tie_base = block_exclusive_scan(ties, warp_sums, &tot);
+  long sel = 0, tr = tie_base;
+  for (long c = c0; c < c1; ++c) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(score[c]);
+    if (b > kth) ++sel;
+    else if (b == kth) sel += (tr++ < need_ties);
+  }
+  long out = block_exclusive_scan(sel, warp_sums, &tot);
+  tr = tie_base;
+  for (long c = c0; c < c1; ++c) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(score[c]);
+    bool take = b > kth;
+    if (b == kth) take = tr++ < need_ties;
+    if (!take) continue;
+    long rem = c;
+    for (int j = nm1 - 1; j >= 0; --j) {
+      samples[out * nm1 + j] = (int32_t)(rem % sz[j]);
+      rem /= sz[j];
+    }
+    ++out;
+  }
+  for (long j = want + tid; j < m; j += nthr)
+    for (int q = 0; q < nm1; ++q) samples[j * nm1 + q] = 0;
+}
+
 // Row j: weight, Z row (Kronecker product of sampled factor rows), Y row (fibre).
+// unit: weights 1 for rows j < nrows and 0 beyond (deterministic selection).
 template <typename T>
 __global__ void k_lev_gather(LevDesc d, int m, int ncols, const T* __restrict__ X,
                              const int32_t* __restrict__ samples, const double* __restrict__ prob,
-                             T* __restrict__ Z, T* __restrict__ Y) {
+                             T* __restrict__ Z, T* __restrict__ Y, int unit, long nrows) {
   const int j = blockIdx.x;
   const int nm1 = d.order - 1;
   __shared__ double w;
   __shared__ long base;
   if (threadIdx.x == 0) {
     double p = 1.0;
-    for (int jj = 0; jj < nm1; ++jj) p = p * prob[(long)jj * m + j];
-    w = 1.0 / sqrt((double)m * p);
+    if (!unit)
+      for (int jj = 0; jj < nm1; ++jj) p = p * prob[(long)jj * m + j];
+    w = unit ? (j < nrows ? 1.0 : 0.0) : 1.0 / sqrt((double)m * p);
     long b = 0, stride = 1;
     for (int k = d.order - 1, jj = nm1 - 1; k >= 0; --k) {
       if (k != d.mode) {
@@ -109,16 +240,19 @@ __global__ void k_lev_gather(LevDesc d, int m, int ncols, const T* __restrict__ 
 }
 
 size_t leverage_scratch_doubles(const ts_tensor& X, int mode, int m) {
-  size_t s = 0;
+  size_t s = 0, C = 1;
   for (int k = 0; k < X.order; ++k)
-    if (k != mode) s += (size_t)X.dims[k];
-  return 2 * s + (size_t)(X.order - 1) * m;
+    if (k != mode) {
+      s += (size_t)X.dims[k];
+      C *= (size_t)X.dims[k];
+    }
+  return 2 * s + (size_t)(X.order - 1) * m + C;  // + C: the scores of every multi-index
 }
 
 template <typename T>
 ts_status launch_leverage(const ts_tensor& X, int mode, const int* ranks, const T* const* factors,
                           int m, uint64_t seed, int sweep, T* Z, T* Y, int32_t* samples,
-                          double* scratch, cudaStream_t st) {
+                          double* scratch, cudaStream_t st, bool det) {
   LevDesc d{};
   d.order = X.order;
   d.mode = mode;
@@ -137,19 +271,29 @@ ts_status launch_leverage(const ts_tensor& X, int mode, const int* ranks, const 
   double* ell = scratch;
   double* cdf = scratch + off;
   double* prob = scratch + 2 * off;
-  k_lev_sample<T><<<X.order - 1, 256, 0, st>>>(d, m, seed, sweep, ell, cdf, samples, prob);
+  long C = 1;
+  for (int k = 0; k < X.order; ++k)
+    if (k != mode) C *= (long)X.dims[k];
+  // deterministic: the scores only (no draws), then the selection
+  k_lev_sample<T><<<X.order - 1, 256, 0, st>>>(d, det ? 0 : m, seed, sweep, ell, cdf, samples,
+                                                prob);
   TS_LAUNCH_CHECK();
+  if (det) {
+    k_lev_select_det<<<1, 1024, 0, st>>>(d, m, C, ell, prob + (size_t)(X.order - 1) * m,
+                                          samples);
+    TS_LAUNCH_CHECK();
+  }
   k_lev_gather<T><<<m, 128, 0, st>>>(d, m, ncols, static_cast<const T*>(X.values), samples, prob,
-                                     Z, Y);
+                                     Z, Y, det ? 1 : 0, det ? (m < C ? (long)m : C) : (long)m);
   TS_LAUNCH_CHECK();
   return TS_OK;
 }
 
 template ts_status launch_leverage<float>(const ts_tensor&, int, const int*, const float* const*,
                                           int, uint64_t, int, float*, float*, int32_t*, double*,
-                                          cudaStream_t);
+                                          cudaStream_t, bool);
 template ts_status launch_leverage<double>(const ts_tensor&, int, const int*,
                                            const double* const*, int, uint64_t, int, double*,
-                                           double*, int32_t*, double*, cudaStream_t);
+                                           double*, int32_t*, double*, cudaStream_t, bool);
 
 }  // namespace ts

@@ -101,12 +101,12 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
                             const ts_options* opt, bool want_residual, Shape& S) {
   TS_TRY(check_tensor(X, "tucker_als_sketched"));
   if (!ranks || !opt) return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: NULL ranks/options");
-  if (kind != TS_TENSORSKETCH && kind != TS_LEVERAGE)
+  if (kind != TS_TENSORSKETCH && kind != TS_LEVERAGE && kind != TS_LEVERAGE_DET)
     return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: bad sketch kind %d", kind);
   if (opt->solve != TS_SOLVE_RSVD && opt->solve != TS_SOLVE_EXACT)
     return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: bad solve kind %d", opt->solve);
   if (sweeps < 1) return fail(TS_ERR_SHAPE, "tucker_als_sketched: sweeps %d < 1", sweeps);
-  if (kind == TS_LEVERAGE && X->format != TS_DENSE)
+  if (kind != TS_TENSORSKETCH && X->format != TS_DENSE)
     return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: leverage sampling needs a dense tensor");
   if (want_residual && X->format != TS_DENSE)
     return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: COO residuals are not built");
@@ -288,7 +288,7 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
     w.H = b.take<T>((size_t)r * s);
     w.Xs = b.take<T>((size_t)r * s);
   }
-  if (S.kind == TS_LEVERAGE) {
+  if (S.kind != TS_TENSORSKETCH) {
     w.Ylev = b.take<T>((size_t)m * s);
     w.samples = b.take<int32_t>((size_t)m * (N - 1));
     size_t lv = 0;
@@ -600,7 +600,8 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
         Yn = w.Y[n];
       } else {
         TS_TRY(launch_leverage<T>(X, n, S.ranks, (const T* const*)factors, m, opt.seed, sweep,
-                                  w.ZW, w.Ylev, w.samples, w.levscr, st));
+                                  w.ZW, w.Ylev, w.samples, w.levscr, st,
+                                  S.kind == TS_LEVERAGE_DET));
         Yn = w.Ylev;
       }
       CoreMap map{};
@@ -1339,6 +1340,39 @@ extern "C" ts_status ts_leverage_sketch(const ts_tensor* X, int32_t mode, const 
   return launch_leverage<float>(*X, mode, ranks, reinterpret_cast<const float* const*>(factors), m,
                                 seed, sweep, static_cast<float*>(Z_out),
                                 static_cast<float*>(Y_out), smp, lv, st);
+}
+
+extern "C" ts_status ts_leverage_sketch_det(const ts_tensor* X, int32_t mode, const int32_t* ranks,
+                                            const void* const* factors, int32_t m, void* Z_out,
+                                            void* Y_out, int32_t* samples_out, void* scratch,
+                                            size_t scratch_bytes, ts_stream stream) {
+  clear_error();
+  TS_TRY(check_tensor(X, "ts_leverage_sketch_det"));
+  if (X->format != TS_DENSE)
+    return fail(TS_ERR_SHAPE, "ts_leverage_sketch_det: dense tensors only");
+  if (mode < 0 || mode >= X->order || m < 1)
+    return fail(TS_ERR_SHAPE, "ts_leverage_sketch_det: bad mode or m");
+  if (!ranks || !factors || !Z_out || !Y_out)
+    return fail(TS_ERR_INVALID_ARG, "ts_leverage_sketch_det: NULL argument");
+  for (int k = 0; k < X->order; ++k)
+    if (k != mode && (!factors[k] || ranks[k] < 1))
+      return fail(TS_ERR_INVALID_ARG, "ts_leverage_sketch_det: bad factor %d", k);
+  const size_t need = ts_leverage_sketch_scratch_bytes(X, mode, m);
+  if (!scratch || scratch_bytes < need || ((uintptr_t)scratch & 255))
+    return fail(TS_ERR_WORKSPACE,
+                "ts_leverage_sketch_det: need %zu bytes of 256-aligned scratch", need);
+  Bump b{static_cast<char*>(scratch)};
+  int32_t* smp = b.take<int32_t>((size_t)m * (X->order - 1));
+  double* lv = b.take<double>(leverage_scratch_doubles(*X, mode, m));
+  if (samples_out) smp = samples_out;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (X->dtype == TS_F64)
+    return launch_leverage<double>(*X, mode, ranks, reinterpret_cast<const double* const*>(factors),
+                                   m, 0, 0, static_cast<double*>(Z_out),
+                                   static_cast<double*>(Y_out), smp, lv, st, true);
+  return launch_leverage<float>(*X, mode, ranks, reinterpret_cast<const float* const*>(factors), m,
+                                0, 0, static_cast<float*>(Z_out), static_cast<float*>(Y_out), smp,
+                                lv, st, true);
 }
 
 // ---------------------------------------------------------------- fitness

@@ -27,7 +27,7 @@ MAX_ORDER = 8
 
 TS_F32, TS_F64 = 0, 1
 TS_DENSE, TS_COO = 0, 1
-TENSORSKETCH, LEVERAGE = 0, 1
+TENSORSKETCH, LEVERAGE, LEVERAGE_DET = 0, 1, 2
 SOLVE_RSVD, SOLVE_EXACT = 0, 1
 PURPOSE_TS_HASH, PURPOSE_RRF_HASH, PURPOSE_RRF_GAUSS, PURPOSE_RSVD_GAUSS, PURPOSE_LEV_UNIFORM = 1, 2, 3, 4, 5
 
@@ -83,6 +83,7 @@ _PROTOS = {
                             SZ, P]),
     "ts_leverage_sketch_scratch_bytes": (SZ, [TP, I32, I32]),
     "ts_leverage_sketch": (I32, [TP, I32, C.POINTER(I32), PP, I32, U64, I32, P, P, P, P, SZ, P]),
+    "ts_leverage_sketch_det": (I32, [TP, I32, C.POINTER(I32), PP, I32, P, P, P, P, SZ, P]),
     "ts_fitness_scratch_bytes": (SZ, [TP, C.POINTER(I32)]),
     "ts_fitness": (I32, [TP, C.POINTER(I32), P, PP, P, P, SZ, P]),
     "tucker_als_workspace_bytes": (I32, [TP, C.POINTER(I32), I32, I32, I32, OP, C.POINTER(SZ)]),
@@ -326,6 +327,28 @@ def leverage_sketch(X, mode: int, factors, m: int, seed: int, sweep: int = 0):
     _check(lib().ts_leverage_sketch(C.byref(d), mode, rk, _ptr_array(facs), m, seed, sweep,
                                     _ptr(Zt), _ptr(Y), _ptr(samples), _ptr(scr), scr.numel(),
                                     _stream()))
+    return Zt.t(), Y, samples
+
+
+def leverage_sketch_det(X, mode: int, factors, m: int):
+    """Deterministic leverage sketch (ts_leverage_sketch_det): (Z, Y, samples)."""
+    dims = _dims(X)
+    N = len(dims)
+    ranks = [f.shape[1] if f is not None else 1 for f in factors]
+    r = 1
+    for k in range(N):
+        if k != mode:
+            r *= ranks[k]
+    d = _desc(X)
+    Zt = torch.empty((r, m), dtype=X.dtype, device=X.device)
+    Y = torch.empty((m, dims[mode]), dtype=X.dtype, device=X.device)
+    samples = torch.empty((m, N - 1), dtype=torch.int32, device=X.device)
+    nbytes = lib().ts_leverage_sketch_scratch_bytes(C.byref(d), mode, m)
+    scr = _scratch(nbytes, X.device)
+    rk = (C.c_int32 * N)(*ranks)
+    facs = [factors[k] if k != mode else None for k in range(N)]
+    _check(lib().ts_leverage_sketch_det(C.byref(d), mode, rk, _ptr_array(facs), m, _ptr(Zt),
+                                        _ptr(Y), _ptr(samples), _ptr(scr), scr.numel(), _stream()))
     return Zt.t(), Y, samples
 
 

@@ -23,12 +23,13 @@ def proj(A):
 
 
 @pytest.mark.parametrize("kind,solve", [("ts", "rsvd"), ("ts", "exact"), ("lev", "rsvd"),
-                                        ("lev", "exact")])
+                                        ("lev", "exact"), ("lev_det", "rsvd"),
+                                        ("lev_det", "exact")])
 def test_small_dense_fp64_matches_oracle(ts, kind, solve):
     # 40^3 FP64, Tucker rank 5 plus 1e-3 noise, m = 400, 5 sweeps, RRF init
     dims, ranks, m, sweeps, seed = (40, 40, 40), (5, 5, 5), 400, 5, 1
     T, _, _ = synth.dense_tucker(dims, ranks, 1e-3, seed=0)
-    k = ts.TENSORSKETCH if kind == "ts" else ts.LEVERAGE
+    k = {"ts": ts.TENSORSKETCH, "lev": ts.LEVERAGE, "lev_det": ts.LEVERAGE_DET}[kind]
     s = ts.SOLVE_RSVD if solve == "rsvd" else ts.SOLVE_EXACT
     core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, sweeps, kind=k,
                                             seed=seed, solve=s, track_fit=True)
@@ -256,3 +257,20 @@ def test_sparse_order4_scaled_workload_matches_oracle(ts):
         sg = np.linalg.svd(U, compute_uv=False)
         so = np.linalg.svd(V, compute_uv=False)
         assert np.allclose(sg, so, rtol=1e-8, atol=1e-10 * so[0])
+
+
+def test_deterministic_leverage_all_rows_is_hooi_on_gpu(ts):
+    # m = prod of the other mode sizes keeps every row: with the exact solve the sketched
+    # ALS is HOOI from the same initial factors
+    dims, ranks = (7, 6, 5), (3, 2, 2)
+    T, _, _ = synth.dense_tucker(dims, ranks, 0.3, seed=3)
+    init = tucker.hosvd(T, ranks)
+    m = 42
+    Tg = torch.from_numpy(T).cuda()
+    plan = ts.TuckerPlan(Tg, ranks, m, 3, kind=ts.LEVERAGE_DET, solve=ts.SOLVE_EXACT)
+    plan.run(Tg, init_factors=[None] + [torch.from_numpy(a).cuda() for a in init[1:]])
+    torch.cuda.synchronize()
+    _, f_h = tucker.hooi(T, ranks, 3, init=init)
+    for n in range(3):
+        f = plan.factors[n].cpu().numpy()
+        assert np.abs(f @ f.T - f_h[n] @ f_h[n].T).max() < 1e-10

@@ -273,6 +273,35 @@ def test_rsvd_exact_rank_input_equals_exact_solve(ts):
 
 # ---------------------------------------------------------------- a5 leverage sampling
 
+@pytest.mark.parametrize("dims,mode,m,ties", [((40, 40, 40), 0, 400, False),
+                                              ((40, 40, 40), 2, 2000, False),
+                                              ((12, 10, 9, 8), 1, 150, False),
+                                              ((16, 12, 10), 0, 50, True)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_leverage_det_sketch_matches_oracle(ts, dims, mode, m, ties, dtype):
+    # deterministic selection: the same multi-indices as the oracle (bit-exact), rows
+    # beyond prod dims zero (m = 2000 > 1600), ties (equal row norms) to the lower index
+    g = np.random.default_rng(4)
+    T = g.standard_normal(dims)
+    R = 3
+    fac = [np.linalg.qr(g.standard_normal((s, R)))[0] for s in dims]
+    if ties:
+        for k in range(len(dims)):
+            fac[k] = np.zeros((dims[k], R))
+            fac[k][np.arange(dims[k]), np.arange(dims[k]) % R] = 1.0  # equal row norms
+    if dtype == torch.float32:
+        T = T.astype(np.float32).astype(np.float64)
+        fac = [f.astype(np.float32).astype(np.float64) for f in fac]
+    Zw, Yw, sw = sketch.leverage_sketch_dense_det(T, mode, fac, m)
+    Zg, Yg, sg = ts.leverage_sketch_det(dev(T, dtype), mode, [dev(f, dtype) for f in fac], m)
+    nsel = sw.shape[0]
+    assert np.array_equal(sg.cpu().numpy()[:nsel], sw.astype(np.int32))
+    tol = 1e-14 if dtype == torch.float64 else 1e-6
+    Zg, Yg = Zg.double().cpu().numpy(), Yg.double().cpu().numpy()
+    assert np.abs(Zg[:nsel] - Zw).max() <= tol * max(1.0, np.abs(Zw).max())
+    assert np.abs(Yg[:nsel] - Yw).max() <= tol * max(1.0, np.abs(Yw).max())
+    assert not np.any(Zg[nsel:]) and not np.any(Yg[nsel:])
+
 @pytest.mark.parametrize("dims,ranks,m", [((40, 40, 40), (5, 5, 5), 400), ((30, 20, 25, 10), (3, 2, 4, 2), 300)])
 def test_leverage_sketch_samples_bit_exact(ts, dims, ranks, m):
     T, _, A = synth.dense_tucker(dims, ranks, 0.01, seed=8)

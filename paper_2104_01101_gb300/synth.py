@@ -20,6 +20,9 @@ coo_zipf_tucker  COO tensor whose coordinates are i.i.d. Zipf(a) per mode trunca
                  component sampled at the same coordinates, both of equal norm.
 cp_collinear     sum of R rank-1 terms whose factor columns have unit norm and a
                  fixed pairwise cosine, plus Gaussian noise.
+spiked_tucker    the paper's tensor with large coherence (Sec. 7, Tensor 4): a
+                 dense_tucker tensor plus n entries at distinct random positions,
+                 each N(||T||_F / sqrt(n), 1), so that E ||N|| / ||T|| is about 1.
 """
 
 from __future__ import annotations
@@ -164,3 +167,20 @@ def cp_collinear(dims, R: int, cosine: float, noise: float, seed: int, dtype=np.
         E = rng.standard_normal(T.shape)
         T = T + E * (noise * np.linalg.norm(T) / np.linalg.norm(E))
     return np.ascontiguousarray(T.astype(dtype)), factors
+
+
+def spiked_tucker(dims, ranks, noise: float, seed: int, n_spikes: int = 10,
+                  dtype=np.float64):
+    """Returns (T + N, positions (n_spikes, N) int64, spike values).
+
+    T is :func:`dense_tucker` (dims, ranks, noise, seed); N adds at ``n_spikes``
+    distinct random linear positions values drawn from N(||T||_F / sqrt(n_spikes), 1).
+    """
+    T, _, _ = dense_tucker(dims, ranks, noise, seed)
+    rng = np.random.default_rng(seed + 0x5EED)
+    flat = T.reshape(-1).copy()
+    lin = np.sort(rng.choice(flat.size, n_spikes, replace=False))
+    vals = rng.normal(np.linalg.norm(flat) / np.sqrt(n_spikes), 1.0, n_spikes)
+    flat[lin] += vals
+    pos = np.stack(np.unravel_index(lin, tuple(dims)), axis=1).astype(np.int64)
+    return np.ascontiguousarray(flat.reshape(tuple(dims)).astype(dtype)), pos, vals

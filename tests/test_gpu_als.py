@@ -43,6 +43,22 @@ def test_small_dense_fp64_matches_oracle(ts, kind, solve):
     assert np.linalg.norm(Tg - To) <= 1e-9 * np.linalg.norm(To)
 
 
+@pytest.mark.parametrize("kind", ["ts", "lev", "lev_det"])
+def test_tensor_with_large_coherence_fp64_matches_oracle(ts, kind):
+    # Sec. 7's Tensor 4 at 40^3: rank-5 Tucker plus 10 large entries; the leverage
+    # scores of the RRF-initialised factors concentrate on the spikes' rows.
+    dims, ranks, m, sweeps, seed = (40, 40, 40), (5, 5, 5), 400, 5, 3
+    T, _, _ = synth.spiked_tucker(dims, ranks, 1e-3, seed=2)
+    k = {"ts": ts.TENSORSKETCH, "lev": ts.LEVERAGE, "lev_det": ts.LEVERAGE_DET}[kind]
+    core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, sweeps, kind=k,
+                                            seed=seed, track_fit=True)
+    c_o, f_o, r_o = tucker.sketch_tucker_als(T, ranks, m, sweeps, seed=seed, kind=kind,
+                                             track_fit=True)
+    assert np.allclose(res.cpu().numpy(), r_o, rtol=1e-9, atol=0)
+    for n in range(3):
+        assert np.abs(proj(fac[n].cpu().numpy()) - proj(f_o[n])).max() < 1e-9
+
+
 @pytest.mark.parametrize("kind", ["ts", "lev"])
 def test_exact_recovery_noiseless(ts, kind):
     T, _, _ = synth.dense_tucker((40, 40, 40), (5, 5, 5), 0.0, seed=2)

@@ -12,7 +12,8 @@ Modules
 rng      counter-based random numbers (splitmix64) and the polynomial hash family
          that realises the paper's 3-/4-wise independent hash maps (Sec. 3.1).
 sketch   CountSketch / TensorSketch definitions, the FFT identity for SP,
-         the one-pass sketch of the data tensor, leverage-score sampling (Sec. 3).
+         the one-pass sketch of the data tensor, leverage-score sampling on dense and
+         COO tensors, random and deterministic (Sec. 3).
 solve    the sketched rank-constrained least-squares solves: the exact form of
          Theorem 4.1's definition and RSVD-LRLS (Alg. 5).
 tucker   unfolding/TTM helpers, fitness (Sec. 7), HOSVD + HOOI (Alg. 1),

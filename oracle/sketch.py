@@ -168,27 +168,22 @@ def leverage_sketch_dense_det(T: np.ndarray, n: int, factors, m: int):
     others = [k for k in range(N) if k != n]
     lin = leverage_select_det([leverage_scores(factors[k]) for k in others], m)
     samples = np.stack(np.unravel_index(lin, [T.shape[k] for k in others]), axis=1)
-    Z = np.ones((lin.shape[0], 1))
-    for j, k in enumerate(others):
-        rows = factors[k][samples[:, j], :]
-        Z = (Z[:, :, None] * rows[:, None, :]).reshape(lin.shape[0], -1)
+    Z = kron_rows(factors, others, samples)
     Tn = np.moveaxis(T, n, -1)
     Y = Tn[tuple(samples[:, j] for j in range(len(others)))]
     return Z, Y, samples
 
 
-def leverage_sketch_dense(T: np.ndarray, n: int, factors, m: int, seed: int, sweep: int):
-    """Sketched LHS and RHS of subproblem n by leverage-score sampling.
+def leverage_draws(dims, n: int, factors, m: int, seed: int, sweep: int):
+    """The m leverage-score draws of subproblem n (Sec. 3.2).
 
     Lemma (Kronecker leverage scores, Sec. 3.2): the score of row (i_k)_{k != n} of
     P^(n) is prod_k l_{i_k}(A^(k)), so each i_k is drawn independently with
-    p^(k) = l(A^(k)) / R_k, m times with replacement.  Row j of the sketch is
-    rescaled by 1 / sqrt(m p_j) with p_j = prod_k p^(k)_{i_k} (importance-sampling
-    definition).  Returns Z (m x prod R_k), Y (m x s_n), the sampled multi-indices
-    (m x (N-1)) and the weights.
+    p^(k) = l(A^(k)) / R_k, m times with replacement.  Returns the multi-indices
+    (m x (N-1)) and the weights 1 / sqrt(m p_j), p_j = prod_k p^(k)_{i_k}
+    (importance-sampling definition).
     """
-    N = T.ndim
-    others = [k for k in range(N) if k != n]
+    others = [k for k in range(len(dims)) if k != n]
     samples = np.zeros((m, len(others)), dtype=np.int64)
     prob = np.ones(m)
     for j, k in enumerate(others):
@@ -197,12 +192,72 @@ def leverage_sketch_dense(T: np.ndarray, n: int, factors, m: int, seed: int, swe
         i_k, p_k = leverage_sample_mode(leverage_scores(factors[k]), u)
         samples[:, j] = i_k
         prob = prob * p_k
-    w = 1.0 / np.sqrt(m * prob)
-    Z = np.ones((m, 1))
+    return samples, 1.0 / np.sqrt(m * prob)
+
+
+def kron_rows(factors, others, samples: np.ndarray) -> np.ndarray:
+    """Rows ``samples`` of P^(n) = kron of the factors of modes ``others``: entry (j, c)
+    is the product of A^(k)(i_k, c_k) over the modes, first mode slowest in c."""
+    Z = np.ones((samples.shape[0], 1))
     for j, k in enumerate(others):
         rows = factors[k][samples[:, j], :]
-        Z = (Z[:, :, None] * rows[:, None, :]).reshape(m, -1)
-    Z = Z * w[:, None]
+        Z = (Z[:, :, None] * rows[:, None, :]).reshape(samples.shape[0], -1)
+    return Z
+
+
+def leverage_sketch_dense(T: np.ndarray, n: int, factors, m: int, seed: int, sweep: int):
+    """Sketched LHS and RHS of subproblem n by leverage-score sampling (leverage_draws).
+    Row j of both is rescaled by its weight.  Returns Z (m x prod R_k), Y (m x s_n),
+    the sampled multi-indices (m x (N-1)) and the weights.
+    """
+    N = T.ndim
+    others = [k for k in range(N) if k != n]
+    samples, w = leverage_draws(T.shape, n, factors, m, seed, sweep)
+    Z = kron_rows(factors, others, samples) * w[:, None]
     Tn = np.moveaxis(T, n, -1)                     # fibres along mode n
     Y = Tn[tuple(samples[:, j] for j in range(len(others)))] * w[:, None]
     return Z, Y, samples, w
+
+
+def fibre_rows_coo(idx: np.ndarray, vals: np.ndarray, dims, n: int, samples: np.ndarray,
+                   w: np.ndarray) -> np.ndarray:
+    """Sampled rows of the unfolding of a COO tensor: Y = S T_(n)^T for a sampling
+    sketch S whose row j picks column (sample j) of T_(n) with weight w_j (Sec. 3.2,
+    importance-sampling definition).  Row j is w_j times the mode-n fibre of T at the
+    sampled multi-index: the values of the nonzeros whose other coordinates equal it,
+    added at their mode-n coordinate (repeated coordinates add).  The cost is the
+    paper's O(m s) gather once the nonzeros are grouped by fibre (here by a sort)."""
+    N = len(dims)
+    others = [k for k in range(N) if k != n]
+    odims = [int(dims[k]) for k in others]
+    col = np.ravel_multi_index(tuple(idx[k].astype(np.int64) for k in others), odims)
+    key = np.ravel_multi_index(tuple(samples[:, j].astype(np.int64) for j in range(len(others))),
+                               odims)
+    order = np.argsort(col, kind="stable")
+    sc = col[order]
+    Y = np.zeros((samples.shape[0], int(dims[n])))
+    for j in range(samples.shape[0]):
+        lo = np.searchsorted(sc, key[j], side="left")
+        hi = np.searchsorted(sc, key[j], side="right")
+        e = order[lo:hi]
+        np.add.at(Y[j], idx[n, e].astype(np.int64), vals[e].astype(np.float64))
+        Y[j] *= w[j]
+    return Y
+
+
+def leverage_sketch_coo(idx, vals, dims, n: int, factors, m: int, seed: int, sweep: int):
+    """leverage_sketch_dense for a COO tensor: the same draws and Z; Y gathered from
+    the nonzeros of the sampled fibres (fibre_rows_coo)."""
+    others = [k for k in range(len(dims)) if k != n]
+    samples, w = leverage_draws(dims, n, factors, m, seed, sweep)
+    Z = kron_rows(factors, others, samples) * w[:, None]
+    return Z, fibre_rows_coo(idx, vals, dims, n, samples, w), samples, w
+
+
+def leverage_sketch_coo_det(idx, vals, dims, n: int, factors, m: int):
+    """leverage_sketch_dense_det for a COO tensor (unit weights)."""
+    others = [k for k in range(len(dims)) if k != n]
+    lin = leverage_select_det([leverage_scores(factors[k]) for k in others], m)
+    samples = np.stack(np.unravel_index(lin, [int(dims[k]) for k in others]), axis=1)
+    Z = kron_rows(factors, others, samples)
+    return Z, fibre_rows_coo(idx, vals, dims, n, samples, np.ones(lin.shape[0])), samples

@@ -16,8 +16,9 @@ from dataclasses import dataclass
 import numpy as np
 
 from . import rng
-from .sketch import (input_sketch_coo, input_sketch_dense, leverage_sketch_dense,
-                     leverage_sketch_dense_det, ts_apply_fft, ts_tables_for_mode)
+from .sketch import (input_sketch_coo, input_sketch_dense, leverage_sketch_coo,
+                     leverage_sketch_coo_det, leverage_sketch_dense, leverage_sketch_dense_det,
+                     ts_apply_fft, ts_tables_for_mode)
 from .solve import canonical_signs, lrls_exact, rsvd_lrls, rsvd_oversampled_rank
 from .tensor import fold, kron_chain, reconstruct, ttm, unfold
 
@@ -184,9 +185,10 @@ def sketch_tucker_als(X, ranks, m: int, sweeps: int, seed: int, kind: str = "ts"
     """Alg. 4.  Returns (core, factors, per-sweep residuals or []).
 
     kind       "ts" (TensorSketch, RHS sketch built once and reused across sweeps
-               unless ``resketch``), "lev" (leverage-score sampling, dense only,
-               redrawn for every subproblem) or "lev_det" (the m rows of largest
-               leverage score, dense only, reselected for every subproblem).
+               unless ``resketch``), "lev" (leverage-score sampling, redrawn for every
+               subproblem) or "lev_det" (the m rows of largest leverage score,
+               reselected for every subproblem); the leverage kinds gather the sampled
+               fibres of a COO tensor from its nonzeros.
     solve      "rsvd" (Alg. 5, the routine Alg. 4 calls) or "exact" (the solution
                Theorem 4.1 is stated for).
     init_factors  replaces the RRF initialisation of modes 2..N when given.
@@ -221,9 +223,16 @@ def sketch_tucker_als(X, ranks, m: int, sweeps: int, seed: int, kind: str = "ts"
                 Y = y_cache[key]
                 Z = ts_apply_fft([factors[k] for k in others], tables, m)
             elif kind == "lev":
-                Z, Y, _, _ = leverage_sketch_dense(X, n, factors, m, seed, sweep)
+                if isinstance(X, Coo):
+                    Z, Y, _, _ = leverage_sketch_coo(X.idx, X.vals, dims, n, factors, m, seed,
+                                                     sweep)
+                else:
+                    Z, Y, _, _ = leverage_sketch_dense(X, n, factors, m, seed, sweep)
             elif kind == "lev_det":
-                Z, Y, _ = leverage_sketch_dense_det(X, n, factors, m)
+                if isinstance(X, Coo):
+                    Z, Y, _ = leverage_sketch_coo_det(X.idx, X.vals, dims, n, factors, m)
+                else:
+                    Z, Y, _ = leverage_sketch_dense_det(X, n, factors, m)
             else:
                 raise ValueError(kind)
             if solve == "exact":

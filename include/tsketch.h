@@ -254,7 +254,7 @@ ts_status ts_lrls_solve(int32_t m, int32_t r, int32_t s, int32_t R, int32_t dtyp
                         ts_stream stream);
 
 /* ------------------------------------------------------------------------- */
-/* Leverage-score sketch of subproblem `mode` of a dense tensor (Sec. 3.2).
+/* Leverage-score sketch of subproblem `mode` of a dense or COO tensor (Sec. 3.2).
  *
  * For k != mode: l^(k)_i = sum_r A^(k)(i,r)^2 (ascending r, FP64), cdf by a
  * running FP64 sum in index order; sample j draws i_k = min{i : cdf_i > u cdf_last}
@@ -265,7 +265,18 @@ ts_status ts_lrls_solve(int32_t m, int32_t r, int32_t s, int32_t R, int32_t dtyp
  * dims[k] x ranks[k] in X's dtype.  samples_out (nullable): m x (order-1) int32,
  * the drawn i_k in ascending k.  Sampling uses the running-sum order above, so
  * for identical factor bits the samples are bit-identical to the oracle's.
- * Errors: TS_ERR_SHAPE for COO input, order > TS_MAX_ORDER or m < 1;
+ * COO input (Sec. 6 counts O(m s) for gathering the sampled fibres): the call first
+ * builds, in the scratch, a hash index of the mode-`mode` fibres (keyed by the C-order
+ * linear index of (i_k)_{k != mode}; capacity the power of two >= 2 nnz, about
+ * 16 bytes per slot plus 4 + sizeof(value) per nonzero), then row j of Y is w_j times
+ * the sum of the nonzeros of the sampled fibre at their mode coordinate (zero for an
+ * empty fibre; repeated coordinates add, in an unspecified order).  Coordinates must
+ * lie in [0, dims[k]); an out-of-range mode coordinate is dropped.
+ * The int32 at offset 0 of the scratch is zeroed by the call and set non-zero if the
+ * index could not place a nonzero (excluded by its capacity); read it after
+ * synchronising.
+ * Errors: TS_ERR_SHAPE for order > TS_MAX_ORDER or m < 1; TS_ERR_UNSUPPORTED for COO
+ * input with >= 2^30 nonzeros or prod_{k != mode} dims[k] >= 9e18;
  * TS_ERR_WORKSPACE if scratch_bytes < ts_leverage_sketch_scratch_bytes(). */
 size_t ts_leverage_sketch_scratch_bytes(const ts_tensor* X, int32_t mode, int32_t m);
 ts_status ts_leverage_sketch(const ts_tensor* X, int32_t mode, const int32_t* ranks,
@@ -277,8 +288,9 @@ ts_status ts_leverage_sketch(const ts_tensor* X, int32_t mode, const int32_t* ra
  * tucker_als_sketched): the min(m, C) multi-indices (i_k)_{k != mode} of largest score
  * prod_k l^(k)_{i_k} (C = prod_{k != mode} dims[k]; scores as above, products in FP64
  * rounded in ascending k), ties to the lower C-order linear index, in ascending linear
- * index; rows are not rescaled (weight 1), rows j >= C are zero.  Arguments and scratch
- * as ts_leverage_sketch (no seed: nothing is drawn). */
+ * index; rows are not rescaled (weight 1), rows j >= C are zero.  Arguments, COO
+ * handling and scratch as ts_leverage_sketch (no seed: nothing is drawn).
+ * TS_ERR_UNSUPPORTED if C > 2^31 (every candidate is scored). */
 ts_status ts_leverage_sketch_det(const ts_tensor* X, int32_t mode, const int32_t* ranks,
                                  const void* const* factors, int32_t m, void* Z_out, void* Y_out,
                                  int32_t* samples_out, void* scratch, size_t scratch_bytes,
@@ -304,16 +316,19 @@ ts_status ts_fitness(const ts_tensor* X, const int32_t* ranks, const void* core,
  * Each sweep updates modes 0..N-1 in order; subproblem n forms Z = S P^(n) and
  * Y = S T_(n)^T with TensorSketch (Y formed once and reused, or redrawn every
  * sweep with resketch_each_sweep), leverage-score sampling (redrawn every
- * subproblem, dense tensors only) or deterministic leverage selection
- * (TS_LEVERAGE_DET: the m rows of largest score, reselected every subproblem, dense
- * only), then solves it (opt->solve) and writes A^(n) and the core.
+ * subproblem) or deterministic leverage selection (TS_LEVERAGE_DET: the m rows of
+ * largest score, reselected every subproblem), then solves it (opt->solve) and
+ * writes A^(n) and the core.  Leverage sampling of a COO tensor builds the N fibre
+ * indices of ts_leverage_sketch once, in the workspace, and gathers the sampled
+ * fibres from them (< 2^30 nonzeros).
  * Outputs: core_out (prod ranks, C order), factors_inout (HOST array of order
  * device pointers, dims[k] x ranks[k]), residual_out (DEVICE, nullable):
  * `sweeps` doubles if opt->track_fit else one double, the final relative residual.
  * All outputs in X's dtype except residuals.
  * Numerical breakdown (a non-positive pivot of Z^T Z, a non-finite eigenvalue)
  * does not stop the enqueued work; it sets the int32 at offset 0 of the
- * workspace to a non-zero value, which the caller reads after synchronising.
+ * workspace to a non-zero value (2: a COO fibre index could not place a nonzero,
+ * excluded by its capacity), which the caller reads after synchronising.
  * Residuals of COO tensors are not implemented in this build (residual_out must
  * be NULL for TS_COO input, else TS_ERR_UNSUPPORTED).
  * Errors: TS_ERR_SHAPE if order < 2, any ranks[k] < 1 or ranks[k] >= dims[k]

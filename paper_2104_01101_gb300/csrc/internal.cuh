@@ -271,15 +271,45 @@ template <typename T>
 ts_status launch_finalize(int s, int R, const T* M, long rs, long cs, int kdim, const T* Fm,
                           T* A_out, T* CnT, int r, T* core, CoreMap map, cudaStream_t st);
 
+// ---------------------------------------------------------------- fibre_index.cu
+// Hash index of the mode-`mode` fibres of a COO tensor (device arrays; passed to
+// kernels by value).  Slot h of the table (capacity mask + 1) holds key keys[h] (the
+// C-order linear index of the other coordinates, ~0 when empty) and owns the entries
+// beg[h] .. beg[h+1]-1 of pos (mode-`mode` coordinate) and val (value, X's dtype).
+struct FibreIndex {
+  int order, mode;
+  int64_t stride[TS_MAX_ORDER];  // key = sum_{k != mode} i_k stride[k]
+  uint64_t mask;
+  unsigned long long* keys;
+  int32_t* beg;   // capacity + 1
+  int32_t* cur;   // capacity (counts, then fill cursors)
+  int32_t* pos;   // nnz
+  void* val;      // nnz
+  int32_t* part;  // scan partials
+};
+int64_t fibre_index_capacity(int64_t nnz);
+bool fibre_keys_fit(const ts_tensor& X, int mode);
+// Carves one mode's index from b (sizes from X.nnz and X.dtype).
+FibreIndex fibre_index_carve(const ts_tensor& X, int mode, Bump& b);
+// Builds it from the COO tensor X; sets *flag = 2 if a key finds no slot (excluded by
+// the capacity >= 2 nnz).
+ts_status launch_fibre_index_build(const ts_tensor& X, const FibreIndex& F, int* flag,
+                                   cudaStream_t st);
+
 // ---------------------------------------------------------------- leverage.cu
-// Leverage-score sketch of subproblem `mode` (dense X).  Z column-major m x prod R_k,
+// Leverage-score sketch of subproblem `mode`.  Z column-major m x prod R_k,
 // Y m x dims[mode]; samples m x (order-1); scratch: leverage_scratch_doubles() doubles.
+// A COO tensor needs `fib`, the built fibre index of `mode`.
+// The deterministic selection scores every one of the C = prod_{k != mode} dims[k]
+// candidate rows; it runs when C <= kLevDetMaxCandidates.
+constexpr int64_t kLevDetMaxCandidates = int64_t(1) << 31;
+int64_t leverage_det_candidates(const ts_tensor& X, int mode);  // C, or -1 above the limit
 size_t leverage_scratch_doubles(const ts_tensor& X, int mode, int m);
 template <typename T>
 ts_status launch_leverage(const ts_tensor& X, int mode, const int* ranks, const T* const* factors,
                           int m, uint64_t seed, int sweep, T* Z, T* Y, int32_t* samples,
                           double* scratch, cudaStream_t st,
-                          bool det = false);
+                          bool det = false, const FibreIndex* fib = nullptr);
 
 // ---------------------------------------------------------------- cp.cu
 // HOSVD initialisation and CP-ALS sweeps on a core of the given ranks; A[k] is

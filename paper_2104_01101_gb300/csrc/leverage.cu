@@ -199,7 +199,8 @@ __global__ void __launch_bounds__(1024) k_lev_select_det(LevDesc d, int m, long 
 template <typename T>
 __global__ void k_lev_gather(LevDesc d, int m, int ncols, const T* __restrict__ X,
                              const int32_t* __restrict__ samples, const double* __restrict__ prob,
-                             T* __restrict__ Z, T* __restrict__ Y, int unit, long nrows) {
+                             T* __restrict__ Z, T* __restrict__ Y, int unit, long nrows,
+                             FibreIndex F, int coo) {
   const int j = blockIdx.x;
   const int nm1 = d.order - 1;
   __shared__ double w;
@@ -233,26 +234,64 @@ __global__ void k_lev_gather(LevDesc d, int m, int ncols, const T* __restrict__ 
     }
     Z[(long)c * m + j] = (T)(v * w);
   }
+  if (coo) {
+    // the sampled fibre's nonzeros from the index; Y was zeroed, repeated coordinates add
+    __shared__ int32_t fb[2];
+    if (threadIdx.x == 0) {
+      unsigned long long key = 0;
+      for (int k = 0, jj = 0; k < d.order; ++k)
+        if (k != d.mode) key += (unsigned long long)samples[(long)j * nm1 + jj++] * F.stride[k];
+      uint64_t h = mix64(key) & F.mask;
+      fb[0] = fb[1] = 0;
+      for (uint64_t p = 0; p <= F.mask; ++p) {
+        const unsigned long long cur = F.keys[h];
+        if (cur == key) {
+          fb[0] = F.beg[h];
+          fb[1] = F.beg[h + 1];
+          break;
+        }
+        if (cur == ~0ull) break;  // empty fibre
+        h = (h + 1) & F.mask;
+      }
+    }
+    __syncthreads();
+    if (w != 0.0) {
+      const T* val = static_cast<const T*>(F.val);
+      T* yr = Y + (long)j * d.dims[d.mode];
+      const unsigned sn = (unsigned)d.dims[d.mode];
+      for (int p = fb[0] + threadIdx.x; p < fb[1]; p += blockDim.x) {
+        const unsigned i = (unsigned)F.pos[p];
+        if (i < sn) atomicAdd(yr + i, (T)((double)val[p] * w));  // coordinates out of range drop
+      }
+    }
+    return;
+  }
   long sn = 1;
   for (int k = d.mode + 1; k < d.order; ++k) sn *= d.dims[k];
   for (int t = threadIdx.x; t < d.dims[d.mode]; t += blockDim.x)
     Y[(long)j * d.dims[d.mode] + t] = (T)((double)X[base + (long)t * sn] * w);
 }
 
-size_t leverage_scratch_doubles(const ts_tensor& X, int mode, int m) {
-  size_t s = 0, C = 1;
+int64_t leverage_det_candidates(const ts_tensor& X, int mode) {
+  double c = 1;
   for (int k = 0; k < X.order; ++k)
-    if (k != mode) {
-      s += (size_t)X.dims[k];
-      C *= (size_t)X.dims[k];
-    }
-  return 2 * s + (size_t)(X.order - 1) * m + C;  // + C: the scores of every multi-index
+    if (k != mode) c *= (double)X.dims[k];
+  return c > (double)kLevDetMaxCandidates ? -1 : (int64_t)c;
+}
+
+size_t leverage_scratch_doubles(const ts_tensor& X, int mode, int m) {
+  size_t s = 0;
+  for (int k = 0; k < X.order; ++k)
+    if (k != mode) s += (size_t)X.dims[k];
+  // + C: the deterministic selection's score of every multi-index (when it can run)
+  const int64_t C = leverage_det_candidates(X, mode);
+  return 2 * s + (size_t)(X.order - 1) * m + (C > 0 ? (size_t)C : 0);
 }
 
 template <typename T>
 ts_status launch_leverage(const ts_tensor& X, int mode, const int* ranks, const T* const* factors,
                           int m, uint64_t seed, int sweep, T* Z, T* Y, int32_t* samples,
-                          double* scratch, cudaStream_t st, bool det) {
+                          double* scratch, cudaStream_t st, bool det, const FibreIndex* fib) {
   LevDesc d{};
   d.order = X.order;
   d.mode = mode;
@@ -272,8 +311,13 @@ ts_status launch_leverage(const ts_tensor& X, int mode, const int* ranks, const 
   double* cdf = scratch + off;
   double* prob = scratch + 2 * off;
   long C = 1;
-  for (int k = 0; k < X.order; ++k)
-    if (k != mode) C *= (long)X.dims[k];
+  if (det) {
+    C = (long)leverage_det_candidates(X, mode);
+    if (C < 0)
+      return fail(TS_ERR_UNSUPPORTED,
+                  "deterministic leverage: more than %lld candidate rows for mode %d",
+                  (long long)kLevDetMaxCandidates, mode);
+  }
   // deterministic: the scores only (no draws), then the selection
   k_lev_sample<T><<<X.order - 1, 256, 0, st>>>(d, det ? 0 : m, seed, sweep, ell, cdf, samples,
                                                 prob);
@@ -283,17 +327,26 @@ ts_status launch_leverage(const ts_tensor& X, int mode, const int* ranks, const 
                                           samples);
     TS_LAUNCH_CHECK();
   }
-  k_lev_gather<T><<<m, 128, 0, st>>>(d, m, ncols, static_cast<const T*>(X.values), samples, prob,
-                                     Z, Y, det ? 1 : 0, det ? (m < C ? (long)m : C) : (long)m);
+  const bool coo = X.format == TS_COO;
+  if (coo && !fib) return fail(TS_ERR_INVALID_ARG, "leverage sketch of a COO tensor: no index");
+  FibreIndex F{};
+  if (coo) {
+    F = *fib;
+    TS_CUDA(cudaMemsetAsync(Y, 0, (size_t)m * X.dims[mode] * sizeof(T), st));
+  }
+  k_lev_gather<T><<<m, 128, 0, st>>>(d, m, ncols, coo ? nullptr : static_cast<const T*>(X.values),
+                                     samples, prob, Z, Y, det ? 1 : 0,
+                                     det ? (m < C ? (long)m : C) : (long)m, F, coo ? 1 : 0);
   TS_LAUNCH_CHECK();
   return TS_OK;
 }
 
 template ts_status launch_leverage<float>(const ts_tensor&, int, const int*, const float* const*,
                                           int, uint64_t, int, float*, float*, int32_t*, double*,
-                                          cudaStream_t, bool);
+                                          cudaStream_t, bool, const FibreIndex*);
 template ts_status launch_leverage<double>(const ts_tensor&, int, const int*,
                                            const double* const*, int, uint64_t, int, double*,
-                                           double*, int32_t*, double*, cudaStream_t, bool);
+                                           double*, int32_t*, double*, cudaStream_t, bool,
+                                           const FibreIndex*);
 
 }  // namespace ts

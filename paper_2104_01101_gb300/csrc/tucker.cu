@@ -84,6 +84,7 @@ struct Shape {
   bool rrf;
   bool fp64solve;  // FP64 QR / polish on FP32 data
   bool bf16gram;   // [G | W | H] on the tensor cores in BF16 (FP32 data, fused subproblems)
+  bool coo_lev;    // leverage sampling of a COO tensor: per-mode fibre indices
   int ranks[TS_MAX_ORDER];
   int r[TS_MAX_ORDER];   // prod_{k != n} ranks[k]
   int kc[TS_MAX_ORDER];  // RSVD width of subproblem n
@@ -106,8 +107,24 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
   if (opt->solve != TS_SOLVE_RSVD && opt->solve != TS_SOLVE_EXACT)
     return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: bad solve kind %d", opt->solve);
   if (sweeps < 1) return fail(TS_ERR_SHAPE, "tucker_als_sketched: sweeps %d < 1", sweeps);
-  if (kind != TS_TENSORSKETCH && X->format != TS_DENSE)
-    return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: leverage sampling needs a dense tensor");
+  if (kind != TS_TENSORSKETCH && X->format == TS_COO) {
+    if (X->nnz >= (int64_t(1) << 30))
+      return fail(TS_ERR_UNSUPPORTED,
+                  "tucker_als_sketched: leverage sampling of COO tensors takes < 2^30 nonzeros");
+    for (int n = 0; n < X->order; ++n) {
+      if (!fibre_keys_fit(*X, n))
+        return fail(TS_ERR_UNSUPPORTED,
+                    "tucker_als_sketched: fibre keys of mode %d exceed 64 bits", n);
+      if (kind == TS_LEVERAGE_DET && leverage_det_candidates(*X, n) < 0)
+        return fail(TS_ERR_UNSUPPORTED,
+                    "tucker_als_sketched: deterministic leverage over more than 2^31 rows");
+    }
+  }
+  if (kind == TS_LEVERAGE_DET && X->format == TS_DENSE)
+    for (int n = 0; n < X->order; ++n)
+      if (leverage_det_candidates(*X, n) < 0)
+        return fail(TS_ERR_UNSUPPORTED,
+                    "tucker_als_sketched: deterministic leverage over more than 2^31 rows");
   if (want_residual && X->format != TS_DENSE)
     return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: COO residuals are not built");
   S.N = X->order;
@@ -119,6 +136,7 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
   S.rrf = !opt->init_given;
   S.fp64solve = opt->solve_fp64 != 0 && X->dtype == TS_F32;
   S.bf16gram = opt->gram_bf16 != 0 && X->dtype == TS_F32;
+  S.coo_lev = kind != TS_TENSORSKETCH && X->format == TS_COO;
   S.smax = 0;
   S.rmax = S.kmax = S.Rmax = S.k1max = S.k2max = S.chain_cols_max = 0;
   memset(&S.ob, 0, sizeof(S.ob));
@@ -214,6 +232,7 @@ struct Work {
   T *Q, *E, *Mm, *D, *K, *CnT, *Fm, *H, *Xs, *Gm, *Bm, *Ylev;
   int32_t* samples;
   double* levscr;
+  FibreIndex fib[TS_MAX_ORDER];  // COO leverage sampling: mode-n fibre indices
   T* fitQ;
   double* fitacc;
   void* Bt[TS_MAX_ORDER];  // BF16 precision form: [Z | Y Omega | Y]^T per mode and sweep
@@ -297,6 +316,8 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
       if (t > lv) lv = t;
     }
     w.levscr = b.take<double>(lv);
+    if (S.coo_lev)
+      for (int n = 0; n < N; ++n) w.fib[n] = fibre_index_carve(X, n, b);
   }
   size_t pm = (size_t)r * (r + k);
   const size_t cands[] = {(size_t)m * k, (size_t)k * s, (size_t)eign * eign, (size_t)s * S.k1max,
@@ -567,6 +588,8 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
     TS_TRY(pack_rhs_bf16<T>(X, S, w, 0, npass, st));
   } else {
     TS_TRY(phase(opt, 2, st));
+    if (S.coo_lev)
+      for (int n = 0; n < N; ++n) TS_TRY(launch_fibre_index_build(X, w.fib[n], w.flag, st));
     TS_TRY(phase(opt, 3, st));
   }
   const T* chain[TS_MAX_ORDER];
@@ -601,7 +624,7 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
       } else {
         TS_TRY(launch_leverage<T>(X, n, S.ranks, (const T* const*)factors, m, opt.seed, sweep,
                                   w.ZW, w.Ylev, w.samples, w.levscr, st,
-                                  S.kind == TS_LEVERAGE_DET));
+                                  S.kind == TS_LEVERAGE_DET, S.coo_lev ? &w.fib[n] : nullptr));
         Yn = w.Ylev;
       }
       CoreMap map{};
@@ -1298,13 +1321,74 @@ extern "C" ts_status ts_lrls_solve(int32_t m, int32_t r, int32_t s, int32_t R, i
 
 // ---------------------------------------------------------------- leverage sketch
 
+// Scratch of the standalone leverage sketches: [flag ints | samples | scores, cdf,
+// probabilities (+ the deterministic selection's scores) | COO: the mode's fibre index].
+static size_t lev_carve(const ts_tensor& X, int mode, int m, Bump& b, int** flag, int32_t** smp,
+                        double** lv, FibreIndex* F) {
+  *flag = b.take<int>(64);
+  *smp = b.take<int32_t>((size_t)m * (X.order - 1));
+  *lv = b.take<double>(leverage_scratch_doubles(X, mode, m));
+  if (X.format == TS_COO) *F = fibre_index_carve(X, mode, b);
+  return b.off;
+}
+
+static ts_status lev_check(const ts_tensor* X, int32_t mode, const int32_t* ranks,
+                           const void* const* factors, int32_t m, const void* Z_out,
+                           const void* Y_out, const char* who) {
+  TS_TRY(check_tensor(X, who));
+  if (mode < 0 || mode >= X->order || m < 1) return fail(TS_ERR_SHAPE, "%s: bad mode or m", who);
+  if (!ranks || !factors || !Z_out || !Y_out) return fail(TS_ERR_INVALID_ARG, "%s: NULL argument", who);
+  for (int k = 0; k < X->order; ++k)
+    if (k != mode && (!factors[k] || ranks[k] < 1))
+      return fail(TS_ERR_INVALID_ARG, "%s: bad factor %d", who, k);
+  if (X->format == TS_COO) {
+    if (X->nnz >= (int64_t(1) << 30))
+      return fail(TS_ERR_UNSUPPORTED, "%s: COO tensors take < 2^30 nonzeros", who);
+    if (!fibre_keys_fit(*X, mode))
+      return fail(TS_ERR_UNSUPPORTED, "%s: fibre keys of mode %d exceed 64 bits", who, mode);
+  }
+  return TS_OK;
+}
+
 extern "C" size_t ts_leverage_sketch_scratch_bytes(const ts_tensor* X, int32_t mode, int32_t m) {
   if (check_tensor(X, "ts_leverage_sketch") != TS_OK || mode < 0 || mode >= X->order || m < 1)
     return 0;
   Bump b;
-  b.take<int32_t>((size_t)m * (X->order - 1));
-  b.take<double>(leverage_scratch_doubles(*X, mode, m));
-  return b.off;
+  int* f;
+  int32_t* smp;
+  double* lv;
+  FibreIndex F;
+  return lev_carve(*X, mode, m, b, &f, &smp, &lv, &F);
+}
+
+static ts_status lev_run(const ts_tensor* X, int32_t mode, const int32_t* ranks,
+                         const void* const* factors, int32_t m, uint64_t seed, int32_t sweep,
+                         void* Z_out, void* Y_out, int32_t* samples_out, void* scratch,
+                         size_t scratch_bytes, ts_stream stream, bool det, const char* who) {
+  const size_t need = ts_leverage_sketch_scratch_bytes(X, mode, m);
+  if (!scratch || scratch_bytes < need || ((uintptr_t)scratch & 255))
+    return fail(TS_ERR_WORKSPACE, "%s: need %zu bytes of 256-aligned scratch", who, need);
+  Bump b{static_cast<char*>(scratch)};
+  int* flag;
+  int32_t* smp;
+  double* lv;
+  FibreIndex F{};
+  lev_carve(*X, mode, m, b, &flag, &smp, &lv, &F);
+  if (samples_out) smp = samples_out;
+  cudaStream_t st = (cudaStream_t)stream;
+  TS_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  const FibreIndex* fib = nullptr;
+  if (X->format == TS_COO) {
+    TS_TRY(launch_fibre_index_build(*X, F, flag, st));
+    fib = &F;
+  }
+  if (X->dtype == TS_F64)
+    return launch_leverage<double>(*X, mode, ranks, reinterpret_cast<const double* const*>(factors),
+                                   m, seed, sweep, static_cast<double*>(Z_out),
+                                   static_cast<double*>(Y_out), smp, lv, st, det, fib);
+  return launch_leverage<float>(*X, mode, ranks, reinterpret_cast<const float* const*>(factors), m,
+                                seed, sweep, static_cast<float*>(Z_out),
+                                static_cast<float*>(Y_out), smp, lv, st, det, fib);
 }
 
 extern "C" ts_status ts_leverage_sketch(const ts_tensor* X, int32_t mode, const int32_t* ranks,
@@ -1313,33 +1397,11 @@ extern "C" ts_status ts_leverage_sketch(const ts_tensor* X, int32_t mode, const 
                                         int32_t* samples_out, void* scratch, size_t scratch_bytes,
                                         ts_stream stream) {
   clear_error();
-  TS_TRY(check_tensor(X, "ts_leverage_sketch"));
-  if (X->format != TS_DENSE) return fail(TS_ERR_SHAPE, "ts_leverage_sketch: dense tensors only");
-  if (mode < 0 || mode >= X->order || m < 1)
-    return fail(TS_ERR_SHAPE, "ts_leverage_sketch: bad mode or m");
-  if (!ranks || !factors || !Z_out || !Y_out)
-    return fail(TS_ERR_INVALID_ARG, "ts_leverage_sketch: NULL argument");
+  TS_TRY(lev_check(X, mode, ranks, factors, m, Z_out, Y_out, "ts_leverage_sketch"));
   if (sweep < 0 || sweep >= (1 << 24))
     return fail(TS_ERR_INVALID_ARG, "ts_leverage_sketch: sweep out of range");
-  for (int k = 0; k < X->order; ++k)
-    if (k != mode && (!factors[k] || ranks[k] < 1))
-      return fail(TS_ERR_INVALID_ARG, "ts_leverage_sketch: bad factor %d", k);
-  const size_t need = ts_leverage_sketch_scratch_bytes(X, mode, m);
-  if (!scratch || scratch_bytes < need || ((uintptr_t)scratch & 255))
-    return fail(TS_ERR_WORKSPACE, "ts_leverage_sketch: need %zu bytes of 256-aligned scratch",
-                need);
-  Bump b{static_cast<char*>(scratch)};
-  int32_t* smp = b.take<int32_t>((size_t)m * (X->order - 1));
-  double* lv = b.take<double>(leverage_scratch_doubles(*X, mode, m));
-  if (samples_out) smp = samples_out;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (X->dtype == TS_F64)
-    return launch_leverage<double>(*X, mode, ranks, reinterpret_cast<const double* const*>(factors),
-                                   m, seed, sweep, static_cast<double*>(Z_out),
-                                   static_cast<double*>(Y_out), smp, lv, st);
-  return launch_leverage<float>(*X, mode, ranks, reinterpret_cast<const float* const*>(factors), m,
-                                seed, sweep, static_cast<float*>(Z_out),
-                                static_cast<float*>(Y_out), smp, lv, st);
+  return lev_run(X, mode, ranks, factors, m, seed, sweep, Z_out, Y_out, samples_out, scratch,
+                 scratch_bytes, stream, false, "ts_leverage_sketch");
 }
 
 extern "C" ts_status ts_leverage_sketch_det(const ts_tensor* X, int32_t mode, const int32_t* ranks,
@@ -1347,32 +1409,9 @@ extern "C" ts_status ts_leverage_sketch_det(const ts_tensor* X, int32_t mode, co
                                             void* Y_out, int32_t* samples_out, void* scratch,
                                             size_t scratch_bytes, ts_stream stream) {
   clear_error();
-  TS_TRY(check_tensor(X, "ts_leverage_sketch_det"));
-  if (X->format != TS_DENSE)
-    return fail(TS_ERR_SHAPE, "ts_leverage_sketch_det: dense tensors only");
-  if (mode < 0 || mode >= X->order || m < 1)
-    return fail(TS_ERR_SHAPE, "ts_leverage_sketch_det: bad mode or m");
-  if (!ranks || !factors || !Z_out || !Y_out)
-    return fail(TS_ERR_INVALID_ARG, "ts_leverage_sketch_det: NULL argument");
-  for (int k = 0; k < X->order; ++k)
-    if (k != mode && (!factors[k] || ranks[k] < 1))
-      return fail(TS_ERR_INVALID_ARG, "ts_leverage_sketch_det: bad factor %d", k);
-  const size_t need = ts_leverage_sketch_scratch_bytes(X, mode, m);
-  if (!scratch || scratch_bytes < need || ((uintptr_t)scratch & 255))
-    return fail(TS_ERR_WORKSPACE,
-                "ts_leverage_sketch_det: need %zu bytes of 256-aligned scratch", need);
-  Bump b{static_cast<char*>(scratch)};
-  int32_t* smp = b.take<int32_t>((size_t)m * (X->order - 1));
-  double* lv = b.take<double>(leverage_scratch_doubles(*X, mode, m));
-  if (samples_out) smp = samples_out;
-  cudaStream_t st = (cudaStream_t)stream;
-  if (X->dtype == TS_F64)
-    return launch_leverage<double>(*X, mode, ranks, reinterpret_cast<const double* const*>(factors),
-                                   m, 0, 0, static_cast<double*>(Z_out),
-                                   static_cast<double*>(Y_out), smp, lv, st, true);
-  return launch_leverage<float>(*X, mode, ranks, reinterpret_cast<const float* const*>(factors), m,
-                                0, 0, static_cast<float*>(Z_out), static_cast<float*>(Y_out), smp,
-                                lv, st, true);
+  TS_TRY(lev_check(X, mode, ranks, factors, m, Z_out, Y_out, "ts_leverage_sketch_det"));
+  return lev_run(X, mode, ranks, factors, m, 0, 0, Z_out, Y_out, samples_out, scratch,
+                 scratch_bytes, stream, true, "ts_leverage_sketch_det");
 }
 
 // ---------------------------------------------------------------- fitness

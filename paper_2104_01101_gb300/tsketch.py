@@ -308,6 +308,13 @@ def lrls_solve(Z, Y, R: int, solve: int = SOLVE_RSVD, seed: int = 0, sweep: int 
     return CnT, A
 
 
+def _check_scratch_flag(scr):
+    """The int32 at offset 0 of a leverage sketch's scratch: non-zero if the fibre index
+    of a COO tensor could not place a nonzero (synchronises)."""
+    if int(scr[:4].view(torch.int32).item()) != 0:
+        raise TsError(6, "fibre index overflow flagged by the device")
+
+
 def leverage_sketch(X, mode: int, factors, m: int, seed: int, sweep: int = 0):
     dims = _dims(X)
     N = len(dims)
@@ -327,6 +334,7 @@ def leverage_sketch(X, mode: int, factors, m: int, seed: int, sweep: int = 0):
     _check(lib().ts_leverage_sketch(C.byref(d), mode, rk, _ptr_array(facs), m, seed, sweep,
                                     _ptr(Zt), _ptr(Y), _ptr(samples), _ptr(scr), scr.numel(),
                                     _stream()))
+    _check_scratch_flag(scr)
     return Zt.t(), Y, samples
 
 
@@ -349,6 +357,7 @@ def leverage_sketch_det(X, mode: int, factors, m: int):
     facs = [factors[k] if k != mode else None for k in range(N)]
     _check(lib().ts_leverage_sketch_det(C.byref(d), mode, rk, _ptr_array(facs), m, _ptr(Zt),
                                         _ptr(Y), _ptr(samples), _ptr(scr), scr.numel(), _stream()))
+    _check_scratch_flag(scr)
     return Zt.t(), Y, samples
 
 

@@ -213,6 +213,27 @@ def test_coo_tensor_matches_oracle(ts):
         assert np.abs(proj(fac[n].cpu().numpy()) - proj(f_o[n])).max() < 1e-9
 
 
+@pytest.mark.parametrize("kind", ["lev", "lev_det"])
+@pytest.mark.parametrize("dtype", [torch.float64])
+def test_coo_leverage_als_matches_oracle(ts, kind, dtype):
+    # Leverage sampling of a COO tensor (fibre index on the device) against the
+    # oracle's COO run (FP64: the draws and the selection follow the factor bits, so
+    # FP32 runs may pick other rows; the FP32 sketch is checked on its own).
+    dims, ranks, m, sweeps, seed = (30, 25, 20), (3, 3, 2), 60, 3, 4
+    npd = np.float64 if dtype == torch.float64 else np.float32
+    idx, vals, _, _ = synth.coo_zipf_tucker(dims, 4000, ranks, seed=3, val_dtype=npd)
+    X = ts.Coo(torch.from_numpy(idx).cuda().contiguous(), torch.from_numpy(vals).cuda(), dims)
+    k = ts.LEVERAGE if kind == "lev" else ts.LEVERAGE_DET
+    core, fac, _ = ts.tucker_als_sketched(X, ranks, m, sweeps, kind=k, seed=seed,
+                                          want_residual=False)
+    Xo = tucker.Coo(idx, vals.astype(np.float64), dims)
+    c_o, f_o, _ = tucker.sketch_tucker_als(Xo, ranks, m, sweeps, seed=seed, kind=kind)
+    Tg = tucker.reconstruct(core.double().cpu().numpy(), [f.double().cpu().numpy() for f in fac])
+    To = tucker.reconstruct(c_o, f_o)
+    tol = 1e-9 if dtype == torch.float64 else 2e-3
+    assert np.linalg.norm(Tg - To) <= tol * np.linalg.norm(To)
+
+
 def test_shape_errors(ts):
     T = torch.zeros((10, 10, 10), dtype=torch.float64, device="cuda")
     with pytest.raises(ts.TsError) as e:

@@ -315,6 +315,57 @@ def test_leverage_sketch_samples_bit_exact(ts, dims, ranks, m):
         assert np.allclose(Yg.cpu().numpy(), Yw, rtol=1e-13, atol=0)
 
 
+def _coo_dup(dims, nnz, seed, zipf=False):
+    g = np.random.default_rng(seed)
+    if zipf:
+        idx = np.stack([np.minimum(np.searchsorted(synth.zipf_table(s, 1.1), g.random(nnz),
+                                                   side="right"), s - 1) for s in dims])
+    else:
+        idx = np.stack([g.integers(0, s, nnz) for s in dims])
+    idx = idx.astype(np.int32)
+    idx[:, nnz // 2:nnz // 2 + 7] = idx[:, :7]     # repeated coordinates
+    return idx, g.standard_normal(nnz)
+
+
+@pytest.mark.parametrize("dims,nnz,m,zipf", [((40, 30, 20), 3000, 400, False),
+                                             ((12, 10, 9, 8), 2000, 150, False),
+                                             ((3000, 2000, 1500), 200000, 1000, True)])
+@pytest.mark.parametrize("det", [False, True])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_leverage_coo_sketch_matches_oracle(ts, dims, nnz, m, zipf, det, dtype):
+    # COO leverage sketch through the fibre index: the same multi-indices as the oracle
+    # (bit-exact), Y rows gathered from the nonzeros of the sampled fibres (empty
+    # fibres give zero rows; repeated coordinates add)
+    if det and zipf:
+        pytest.skip("deterministic selection scores all 3e6 candidates: covered by the dense test")
+    idx, vals = _coo_dup(dims, nnz, seed=6, zipf=zipf)
+    if dtype == torch.float32:
+        vals = vals.astype(np.float32).astype(np.float64)
+    g = np.random.default_rng(7)
+    R = 3
+    fac = [np.linalg.qr(g.standard_normal((s, R)))[0] for s in dims]
+    if dtype == torch.float32:
+        fac = [f.astype(np.float32).astype(np.float64) for f in fac]
+    X = ts.Coo(torch.from_numpy(idx).cuda().contiguous(), dev(vals, dtype), tuple(dims))
+    Ag = [dev(f, dtype) for f in fac]
+    tol = 1e-13 if dtype == torch.float64 else 1e-5
+    for n in range(len(dims)):
+        if det:
+            Zw, Yw, sw = sketch.leverage_sketch_coo_det(idx, vals, dims, n, fac, m)
+            Zg, Yg, sg = ts.leverage_sketch_det(X, n, Ag, m)
+        else:
+            Zw, Yw, sw, _ = sketch.leverage_sketch_coo(idx, vals, dims, n, fac, m, 5, 2)
+            Zg, Yg, sg = ts.leverage_sketch(X, n, Ag, m, seed=5, sweep=2)
+        nsel = sw.shape[0]
+        assert np.array_equal(sg.cpu().numpy()[:nsel], sw.astype(np.int32))
+        Zg, Yg = Zg.double().cpu().numpy(), Yg.double().cpu().numpy()
+        assert np.abs(Zg[:nsel] - Zw).max() <= tol * max(1.0, np.abs(Zw).max())
+        assert np.abs(Yg[:nsel] - Yw).max() <= tol * max(1.0, np.abs(Yw).max())
+        assert np.count_nonzero(Yw) > 0
+        if zipf:
+            assert (np.abs(Yw).sum(axis=1) == 0).any()  # sampled fibres holding no nonzero
+
+
 # ---------------------------------------------------------------- a9 fitness
 
 @pytest.mark.parametrize("dims,ranks,dtype", [((40, 40, 40), (5, 5, 5), torch.float64),

@@ -299,10 +299,19 @@ ts_status ts_leverage_sketch_det(const ts_tensor* X, int32_t mode, const int32_t
 /* ------------------------------------------------------------------------- */
 /* Relative residual ||T - C x_1 A^(1) ... x_N A^(N)||_F / ||T||_F (Sec. 7 fitness
  * is 1 minus this).  Dense: direct reconstruction streamed against T with FP64
- * accumulation.  COO: ||T||^2 - 2<T, T~> + ||T~||^2 with duplicates summed
- * (requires scratch for a sorted copy of the coordinates).
+ * accumulation.  COO: ||T||^2 - 2<T, T~> + ||T~||^2 (clamped at 0) without forming
+ * T~: ||T||^2 over distinct coordinates (repeated coordinates added first, through a
+ * fibre index of the largest mode and a hash table of (fibre, coordinate) keys, both
+ * in the scratch, about 40 bytes per nonzero), <T, T~> summed over the stored entries
+ * with T~(i) formed in the data type, ||T~||^2 = <C, C x_1 G_1 ... x_N G_N> with
+ * G_n = A^(n)T A^(n) (no orthonormality assumed); FP64 across entries.  The int32 at
+ * offset 0 of the scratch is set non-zero if a hash table could not place an entry
+ * (excluded by its capacity).
  * factors: HOST array of order device pointers (dims[k] x ranks[k]).
- * residual_out: DEVICE pointer to one double. */
+ * residual_out: DEVICE pointer to one double.
+ * Errors: TS_ERR_UNSUPPORTED for COO input with order < 2, >= 2^30 nonzeros, the
+ * product of the other dims of the largest mode >= 9e18, a core larger than 200 KB or
+ * ranks[order-1] > 64. */
 size_t ts_fitness_scratch_bytes(const ts_tensor* X, const int32_t* ranks);
 ts_status ts_fitness(const ts_tensor* X, const int32_t* ranks, const void* core,
                      const void* const* factors, double* residual_out, void* scratch,
@@ -329,8 +338,8 @@ ts_status ts_fitness(const ts_tensor* X, const int32_t* ranks, const void* core,
  * does not stop the enqueued work; it sets the int32 at offset 0 of the
  * workspace to a non-zero value (2: a COO fibre index could not place a nonzero,
  * excluded by its capacity), which the caller reads after synchronising.
- * Residuals of COO tensors are not implemented in this build (residual_out must
- * be NULL for TS_COO input, else TS_ERR_UNSUPPORTED).
+ * Residuals of COO tensors follow ts_fitness (||T||^2 formed once per call, with its
+ * fibre index and hash table in the workspace; TS_ERR_UNSUPPORTED under its limits).
  * Errors: TS_ERR_SHAPE if order < 2, any ranks[k] < 1 or ranks[k] >= dims[k]
  * (the theory assumes s > R), m < prod_{k != n} ranks[k] for some n (the sketched
  * system must be able to have full column rank), or a per-call limit above is

@@ -1,0 +1,328 @@
+// Relative residual ||T - T~||_F / ||T||_F of a Tucker model against a COO tensor
+// (Sec. 7 fitness f = 1 - residual), without forming T~:
+//   ||T - T~||^2 = ||T||^2 - 2 <T, T~> + ||T~||^2
+//   ||T||^2  over distinct coordinates, repeated ones added first (once per tensor):
+//            the nonzeros are grouped by the fibres of mode nf (fibre index), and
+//            (fibre slot, i_nf) keys a second hash table that sums the repeats
+//   <T, T~>  = sum over stored entries of v_e T~(i_e) (linear in the entries, so
+//            repeats need no merging); T~(i) = sum_r C(r) prod_n A^(n)(i_n, r_n) with
+//            the core in shared memory and the last mode's factor row in registers
+//   ||T~||^2 = <C, C x_1 G_1 ... x_N G_N>, G_n = A^(n)T A^(n) (exact without
+//            orthonormal factors)
+// Every sum across threads is FP64; the per-entry value T~(i) is formed in the data type.
+#include "internal.cuh"
+
+namespace ts {
+
+namespace {
+
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[warp] = v;
+  __syncthreads();
+  double t = 0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+  return t;  // valid in thread 0
+}
+
+// Slot of the fibre index that owns entry p: the last h with beg[h] <= p.
+__device__ __forceinline__ int64_t owner_slot(const int32_t* __restrict__ beg, int64_t cap,
+                                              int p) {
+  int64_t lo = 0, hi = cap;  // beg[lo] <= p < beg[hi]
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (beg[mid] <= p) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// Adds every entry's value into the slot of key (fibre slot, i_nf) of the value table.
+template <typename T>
+__global__ void k_merge_repeats(FibreIndex F, int64_t nnz, int64_t sn,
+                                unsigned long long* __restrict__ vkeys, double* __restrict__ vsum,
+                                uint64_t vmask, int* flag) {
+  const T* val = static_cast<const T*>(F.val);
+  const int64_t cap = (int64_t)F.mask + 1;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t h = owner_slot(F.beg, cap, (int)p);
+    const unsigned long long key = (unsigned long long)h * (unsigned long long)sn +
+                                   (unsigned long long)(unsigned)F.pos[p];
+    uint64_t g = mix64(key) & vmask;
+    bool placed = false;
+    for (uint64_t q = 0; q <= vmask; ++q) {
+      unsigned long long cur = __ldcg(vkeys + g);
+      if (cur == kEmptyKey) cur = atomicCAS(vkeys + g, kEmptyKey, key);
+      if (cur == kEmptyKey || cur == key) {
+        atomicAdd(vsum + g, (double)val[p]);
+        placed = true;
+        break;
+      }
+      g = (g + 1) & vmask;
+    }
+    if (!placed && flag) atomicExch(flag, 2);
+  }
+}
+
+__global__ void k_sum_squares(const double* __restrict__ v, int64_t n, double* out) {
+  __shared__ double sh[32];
+  double s = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s += v[i] * v[i];
+  s = block_sum_d(s, sh);
+  if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
+struct CooModel {
+  int order;
+  int64_t dims[TS_MAX_ORDER];
+  int ranks[TS_MAX_ORDER];
+  const void* factors[TS_MAX_ORDER];
+  int npre;  // prod_{k < order-1} ranks[k]
+};
+
+// <T, T~>: one thread per stored entry.  RL >= ranks[last] (the last factor row in
+// registers, zero-padded; the core rows in shared memory are padded to match).
+template <typename T, int RL>
+__global__ void __launch_bounds__(256) k_coo_inner(const int32_t* __restrict__ idx,
+                                                   const T* __restrict__ vals, int64_t nnz,
+                                                   CooModel d, const T* __restrict__ core,
+                                                   double* out) {
+  extern __shared__ unsigned char smraw[];
+  T* sc = reinterpret_cast<T*>(smraw);
+  __shared__ double sh[32];
+  const int N = d.order, L = N - 1, RLr = d.ranks[L];
+  const int ctot = d.npre * RLr;
+  for (int i = threadIdx.x; i < ctot + RL; i += blockDim.x) sc[i] = i < ctot ? core[i] : (T)0;
+  __syncthreads();
+  const T* AL = static_cast<const T*>(d.factors[L]);
+  double acc = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    T al[RL];
+    const int64_t il = idx[(int64_t)L * nnz + e];
+#pragma unroll
+    for (int r = 0; r < RL; ++r) al[r] = r < RLr ? AL[il * RLr + r] : (T)0;
+    int64_t ik[TS_MAX_ORDER];
+    int rk[TS_MAX_ORDER];
+    T pp[TS_MAX_ORDER];  // pp[k] = prod_{j <= k} A^(j)(i_j, r_j)
+    for (int k = 0; k < L; ++k) {
+      ik[k] = idx[(int64_t)k * nnz + e];
+      rk[k] = 0;
+      const T a = static_cast<const T*>(d.factors[k])[ik[k] * d.ranks[k]];
+      pp[k] = k ? pp[k - 1] * a : a;
+    }
+    T s = 0;
+    for (int c = 0; c < d.npre; ++c) {
+      const T* crow = sc + (long)c * RLr;
+      T inner = 0;
+#pragma unroll
+      for (int r = 0; r < RL; ++r) inner += crow[r] * al[r];
+      s += pp[L - 1] * inner;
+      int k = L - 1;  // odometer over (r_0, ..., r_{L-1}), last fastest
+      while (k >= 0 && ++rk[k] == d.ranks[k]) rk[k--] = 0;
+      if (k < 0) break;
+      for (int j = k; j < L; ++j) {
+        const T a = static_cast<const T*>(d.factors[j])[ik[j] * d.ranks[j] + rk[j]];
+        pp[j] = j ? pp[j - 1] * a : a;
+      }
+    }
+    acc += (double)s * (double)vals[e];
+  }
+  acc = block_sum_d(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
+// G_n = A^(n)T A^(n): block (a, b, n) sums A(:, a) A(:, b) over the rows in FP64.
+template <typename T>
+__global__ void k_gram_cols(CooModel d, T* G, int gstride) {
+  __shared__ double sh[32];
+  const int n = blockIdx.z;
+  const int R = d.ranks[n];
+  const int a = blockIdx.x, b = blockIdx.y;
+  if (a >= R || b >= R) return;
+  const T* A = static_cast<const T*>(d.factors[n]);
+  double s = 0;
+  for (int64_t i = threadIdx.x; i < d.dims[n]; i += blockDim.x)
+    s += (double)A[i * R + a] * (double)A[i * R + b];
+  s = block_sum_d(s, sh);
+  if (threadIdx.x == 0) G[(long)n * gstride + a * R + b] = (T)s;
+}
+
+// out = in x_k G (G square R x R): in, out are (pre x R x post), C order.
+template <typename T>
+__global__ void k_ttm_square(long pre, int R, long post, const T* __restrict__ in,
+                             const T* __restrict__ G, T* __restrict__ out) {
+  const long total = pre * R * post;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < total;
+       e += (long)gridDim.x * blockDim.x) {
+    const long y = e % post;
+    const long xi = e / post;
+    const int i = (int)(xi % R);
+    const long x = xi / R;
+    const T* src = in + x * R * post + y;
+    double acc = 0;
+    for (int r = 0; r < R; ++r) acc += (double)G[i * R + r] * (double)src[r * post];
+    out[e] = (T)acc;
+  }
+}
+
+// acc[2] = <C, M> = ||T~||^2; the residual from *t2 = ||T||^2 and acc[1] = <T, T~>.
+template <typename T>
+__global__ void k_fit_coo_final(const T* __restrict__ C, const T* __restrict__ M, long n,
+                                const double* __restrict__ t2, double* acc, double* residual) {
+  __shared__ double sh[32];
+  double s = 0;
+  for (long i = threadIdx.x; i < n; i += blockDim.x) s += (double)C[i] * (double)M[i];
+  s = block_sum_d(s, sh);
+  if (threadIdx.x == 0) {
+    const double tt = *t2;
+    const double r2 = tt - 2.0 * acc[1] + s;
+    acc[2] = s;
+    *residual = sqrt((r2 > 0 ? r2 : 0.0) / tt);
+  }
+}
+
+int fit_coo_mode(const ts_tensor& X) {
+  int nf = 0;
+  for (int k = 1; k < X.order; ++k)
+    if (X.dims[k] > X.dims[nf]) nf = k;
+  return nf;
+}
+
+}  // namespace
+
+bool fit_coo_supported(const ts_tensor& X) {
+  if (X.order < 2 || X.nnz >= (int64_t(1) << 30)) return false;
+  return fibre_keys_fit(X, fit_coo_mode(X));
+}
+
+bool fit_coo_model_ok(const ts_tensor& X, const int* ranks) {
+  long ctot = 1;
+  for (int k = 0; k < X.order; ++k) ctot *= ranks[k];
+  return ranks[X.order - 1] <= 64 && (ctot + 64) * (long)dtype_size(X.dtype) <= 200 * 1024;
+}
+
+FitCooWork fit_coo_carve(const ts_tensor& X, const int* ranks, Bump& b) {
+  FitCooWork w{};
+  w.F = fibre_index_carve(X, fit_coo_mode(X), b);
+  const int64_t cap = fibre_index_capacity(X.nnz);
+  w.vmask = (uint64_t)cap - 1;
+  w.vkeys = b.take<unsigned long long>((size_t)cap);
+  w.vsum = b.take<double>((size_t)cap);
+  long ctot = 1;
+  int gmax = 0;
+  for (int k = 0; k < X.order; ++k) {
+    ctot *= ranks[k];
+    if (ranks[k] * ranks[k] > gmax) gmax = ranks[k] * ranks[k];
+  }
+  const size_t ts = dtype_size(X.dtype);
+  w.gstride = gmax;
+  w.G = b.take<char>((size_t)X.order * gmax * ts);
+  w.M1 = b.take<char>((size_t)ctot * ts);
+  w.M2 = b.take<char>((size_t)ctot * ts);
+  w.acc = b.take<double>(4);
+  return w;
+}
+
+ts_status launch_fit_coo_norm(const ts_tensor& X, const FitCooWork& w, int* flag,
+                              cudaStream_t st) {
+  TS_TRY(launch_fibre_index_build(X, w.F, flag, st));
+  const int64_t cap = (int64_t)w.vmask + 1;
+  TS_CUDA(cudaMemsetAsync(w.vkeys, 0xFF, (size_t)cap * sizeof(unsigned long long), st));
+  TS_CUDA(cudaMemsetAsync(w.vsum, 0, (size_t)cap * sizeof(double), st));
+  TS_CUDA(cudaMemsetAsync(w.acc, 0, 4 * sizeof(double), st));
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(X.nnz, 256), 1), 152 * 16);
+  const int64_t sn = X.dims[w.F.mode];
+  if (X.nnz > 0) {
+    if (X.dtype == TS_F64)
+      k_merge_repeats<double><<<grid, 256, 0, st>>>(w.F, X.nnz, sn, w.vkeys, w.vsum, w.vmask, flag);
+    else
+      k_merge_repeats<float><<<grid, 256, 0, st>>>(w.F, X.nnz, sn, w.vkeys, w.vsum, w.vmask, flag);
+    TS_LAUNCH_CHECK();
+  }
+  k_sum_squares<<<(int)std::min<int64_t>(ceil_div(cap, 256), 152 * 8), 256, 0, st>>>(w.vsum, cap,
+                                                                                     w.acc + 3);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+template <typename T, int RL>
+static ts_status inner_launch(const ts_tensor& X, const CooModel& d, const T* core, double* out,
+                              cudaStream_t st) {
+  const size_t smem = ((size_t)d.npre * d.ranks[X.order - 1] + RL) * sizeof(T);
+  if (smem > 200 * 1024)
+    return fail(TS_ERR_UNSUPPORTED, "COO fitness: core of %zu bytes exceeds shared memory", smem);
+  if (smem > 48 * 1024)
+    TS_CUDA(cudaFuncSetAttribute(k_coo_inner<T, RL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(X.nnz, 256), 1), 152 * 8);
+  k_coo_inner<T, RL><<<grid, 256, smem, st>>>(X.indices, static_cast<const T*>(X.values), X.nnz,
+                                              d, core, out);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+template <typename T>
+ts_status launch_fit_coo(const ts_tensor& X, const int* ranks, const T* core,
+                         const T* const* factors, const FitCooWork& w, double* residual,
+                         cudaStream_t st) {
+  const int N = X.order;
+  CooModel d{};
+  d.order = N;
+  d.npre = 1;
+  for (int k = 0; k < N; ++k) {
+    d.dims[k] = X.dims[k];
+    d.ranks[k] = ranks[k];
+    d.factors[k] = factors[k];
+    if (k < N - 1) d.npre *= ranks[k];
+  }
+  TS_CUDA(cudaMemsetAsync(w.acc + 1, 0, sizeof(double), st));
+  const int RLr = ranks[N - 1];
+  if (RLr <= 8) TS_TRY((inner_launch<T, 8>(X, d, core, w.acc + 1, st)));
+  else if (RLr <= 16) TS_TRY((inner_launch<T, 16>(X, d, core, w.acc + 1, st)));
+  else if (RLr <= 32) TS_TRY((inner_launch<T, 32>(X, d, core, w.acc + 1, st)));
+  else if (RLr <= 64) TS_TRY((inner_launch<T, 64>(X, d, core, w.acc + 1, st)));
+  else return fail(TS_ERR_UNSUPPORTED, "COO fitness: last rank %d > 64", RLr);
+  // ||T~||^2 = <C, C x_1 G_1 ... x_N G_N>
+  int Rm = 0;
+  for (int k = 0; k < N; ++k)
+    if (ranks[k] > Rm) Rm = ranks[k];
+  T* G = static_cast<T*>(w.G);
+  k_gram_cols<T><<<dim3(Rm, Rm, N), 256, 0, st>>>(d, G, w.gstride);
+  TS_LAUNCH_CHECK();
+  long ctot = 1;
+  for (int k = 0; k < N; ++k) ctot *= ranks[k];
+  const T* in = core;
+  T* bufs[2] = {static_cast<T*>(w.M1), static_cast<T*>(w.M2)};
+  long pre = 1;
+  for (int k = 0; k < N; ++k) {
+    const long post = ctot / (pre * ranks[k]);
+    T* out = bufs[k & 1];
+    k_ttm_square<T><<<std::max(1, std::min(ceil_div(ctot, 256), 152 * 4)), 256, 0, st>>>(
+        pre, ranks[k], post, in, G + (long)k * w.gstride, out);
+    TS_LAUNCH_CHECK();
+    in = out;
+    pre *= ranks[k];
+  }
+  k_fit_coo_final<T><<<1, 256, 0, st>>>(core, in, ctot, w.acc + 3, w.acc, residual);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+template ts_status launch_fit_coo<float>(const ts_tensor&, const int*, const float*,
+                                         const float* const*, const FitCooWork&, double*,
+                                         cudaStream_t);
+template ts_status launch_fit_coo<double>(const ts_tensor&, const int*, const double*,
+                                          const double* const*, const FitCooWork&, double*,
+                                          cudaStream_t);
+
+}  // namespace ts

@@ -296,6 +296,34 @@ FibreIndex fibre_index_carve(const ts_tensor& X, int mode, Bump& b);
 ts_status launch_fibre_index_build(const ts_tensor& X, const FibreIndex& F, int* flag,
                                    cudaStream_t st);
 
+// ---------------------------------------------------------------- fit_coo.cu
+// Residual of a Tucker model against a COO tensor.  Scratch: the fibre index of the
+// largest mode, a hash table merging repeated coordinates, the Gram matrices
+// G_n = A^(n)T A^(n) (stride gstride elements), two core-sized buffers and
+// acc[4] (acc[1] = <T, T~>, acc[2] = ||T~||^2, acc[3] = ||T||^2).
+struct FitCooWork {
+  FibreIndex F;
+  unsigned long long* vkeys;
+  double* vsum;
+  uint64_t vmask;
+  void* G;
+  int gstride;
+  void* M1;
+  void* M2;
+  double* acc;
+};
+bool fit_coo_supported(const ts_tensor& X);  // order >= 2, < 2^30 nonzeros, keys fit
+bool fit_coo_model_ok(const ts_tensor& X, const int* ranks);  // core <= 200 KB, last rank <= 64
+FitCooWork fit_coo_carve(const ts_tensor& X, const int* ranks, Bump& b);
+// ||T||^2 with repeated coordinates merged, into acc[3] (once per tensor).
+ts_status launch_fit_coo_norm(const ts_tensor& X, const FitCooWork& w, int* flag,
+                              cudaStream_t st);
+// The relative residual into *residual (after launch_fit_coo_norm on the same work).
+template <typename T>
+ts_status launch_fit_coo(const ts_tensor& X, const int* ranks, const T* core,
+                         const T* const* factors, const FitCooWork& w, double* residual,
+                         cudaStream_t st);
+
 // ---------------------------------------------------------------- leverage.cu
 // Leverage-score sketch of subproblem `mode`.  Z column-major m x prod R_k,
 // Y m x dims[mode]; samples m x (order-1); scratch: leverage_scratch_doubles() doubles.

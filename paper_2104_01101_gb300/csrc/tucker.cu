@@ -125,8 +125,11 @@ static ts_status plan_shape(const ts_tensor* X, const int32_t* ranks, int kind, 
       if (leverage_det_candidates(*X, n) < 0)
         return fail(TS_ERR_UNSUPPORTED,
                     "tucker_als_sketched: deterministic leverage over more than 2^31 rows");
-  if (want_residual && X->format != TS_DENSE)
-    return fail(TS_ERR_UNSUPPORTED, "tucker_als_sketched: COO residuals are not built");
+  if (want_residual && X->format == TS_COO &&
+      (!fit_coo_supported(*X) || !fit_coo_model_ok(*X, ranks)))
+    return fail(TS_ERR_UNSUPPORTED,
+                "tucker_als_sketched: COO residual needs < 2^30 nonzeros, fibre keys of the "
+                "largest mode within 64 bits, a core <= 200 KB and a last rank <= 64");
   S.N = X->order;
   S.m = m;
   S.sweeps = sweeps;
@@ -235,6 +238,7 @@ struct Work {
   FibreIndex fib[TS_MAX_ORDER];  // COO leverage sampling: mode-n fibre indices
   T* fitQ;
   double* fitacc;
+  FitCooWork fitc;  // COO residual
   void* Bt[TS_MAX_ORDER];  // BF16 precision form: [Z | Y Omega | Y]^T per mode and sweep
   size_t bt_stride[TS_MAX_ORDER];  // bytes between consecutive sweeps' operands
   float* gpart;            // its split-K partial sums
@@ -332,6 +336,7 @@ static void carve(const ts_tensor& X, const Shape& S, bool want_residual, Bump& 
     w.fitQ = b.take<T>(fit_dense_scratch_elems<T>(X, S.ranks));
     w.fitacc = b.take<double>(2);
   }
+  if (want_residual && X.format == TS_COO) w.fitc = fit_coo_carve(X, S.ranks, b);
   if (S.bf16gram) {
     size_t part = 0;
     for (int n = 0; n < N; ++n) {
@@ -574,6 +579,13 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
   const int N = S.N, m = S.m;
   TS_TRY(phase(opt, 0, st));
   TS_CUDA(cudaMemsetAsync(w.flag, 0, 256 + kGemmCounters * sizeof(unsigned), st));
+  if (residual_out && X.format == TS_COO) TS_TRY(launch_fit_coo_norm(X, w.fitc, w.flag, st));
+  auto fit = [&](double* out) -> ts_status {
+    if (X.format == TS_COO)
+      return launch_fit_coo<T>(X, S.ranks, core, (const T* const*)factors, w.fitc, out, st);
+    return launch_fit_dense<T>(X, S.ranks, core, (const T* const*)factors, w.fitQ, w.fitacc, out,
+                               st);
+  };
   if (S.rrf) TS_TRY(rrf_all<T>(X, S, opt.seed, w, factors, st));
   TS_TRY(phase(opt, 1, st));
   if (S.solve == TS_SOLVE_RSVD) TS_TRY(launch_omegas<T>(opt.seed, S.ob, w.Om, st));
@@ -647,14 +659,10 @@ static ts_status als_impl(const ts_tensor& X, const Shape& S, const ts_options& 
                                  S.fp64solve, Om, ldo, yom, Yn, w, factors[n], core, map, st,
                                  bf));
     }
-    if (residual_out && opt.track_fit)
-      TS_TRY(launch_fit_dense<T>(X, S.ranks, core, (const T* const*)factors, w.fitQ, w.fitacc,
-                                 residual_out + sweep, st));
+    if (residual_out && opt.track_fit) TS_TRY(fit(residual_out + sweep));
   }
   TS_TRY(phase(opt, 4, st));
-  if (residual_out && !opt.track_fit)
-    TS_TRY(launch_fit_dense<T>(X, S.ranks, core, (const T* const*)factors, w.fitQ, w.fitacc,
-                               residual_out, st));
+  if (residual_out && !opt.track_fit) TS_TRY(fit(residual_out));
   TS_TRY(phase(opt, 5, st));
   return TS_OK;
 }
@@ -1417,8 +1425,13 @@ extern "C" ts_status ts_leverage_sketch_det(const ts_tensor* X, int32_t mode, co
 // ---------------------------------------------------------------- fitness
 
 extern "C" size_t ts_fitness_scratch_bytes(const ts_tensor* X, const int32_t* ranks) {
-  if (check_tensor(X, "ts_fitness") != TS_OK || !ranks || X->format != TS_DENSE) return 0;
+  if (check_tensor(X, "ts_fitness") != TS_OK || !ranks) return 0;
   Bump b;
+  if (X->format == TS_COO) {
+    b.take<int>(64);
+    fit_coo_carve(*X, ranks, b);
+    return b.off;
+  }
   if (X->dtype == TS_F64)
     b.take<double>(fit_dense_scratch_elems<double>(*X, ranks));
   else
@@ -1432,10 +1445,12 @@ extern "C" ts_status ts_fitness(const ts_tensor* X, const int32_t* ranks, const 
                                 size_t scratch_bytes, ts_stream stream) {
   clear_error();
   TS_TRY(check_tensor(X, "ts_fitness"));
-  if (X->format != TS_DENSE)
-    return fail(TS_ERR_UNSUPPORTED, "ts_fitness: COO residuals are not built");
   if (!ranks || !core || !factors || !residual_out)
     return fail(TS_ERR_INVALID_ARG, "ts_fitness: NULL argument");
+  if (X->format == TS_COO && (!fit_coo_supported(*X) || !fit_coo_model_ok(*X, ranks)))
+    return fail(TS_ERR_UNSUPPORTED,
+                "ts_fitness: COO residual needs < 2^30 nonzeros, fibre keys of the largest mode "
+                "within 64 bits, a core <= 200 KB and a last rank <= 64");
   for (int k = 0; k < X->order; ++k)
     if (!factors[k] || ranks[k] < 1) return fail(TS_ERR_INVALID_ARG, "ts_fitness: bad factor %d", k);
   const size_t need = ts_fitness_scratch_bytes(X, ranks);
@@ -1443,6 +1458,19 @@ extern "C" ts_status ts_fitness(const ts_tensor* X, const int32_t* ranks, const 
     return fail(TS_ERR_WORKSPACE, "ts_fitness: need %zu bytes of 256-aligned scratch", need);
   Bump b{static_cast<char*>(scratch)};
   cudaStream_t st = (cudaStream_t)stream;
+  if (X->format == TS_COO) {
+    int* flag = b.take<int>(64);
+    const FitCooWork w = fit_coo_carve(*X, ranks, b);
+    TS_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    TS_TRY(launch_fit_coo_norm(*X, w, flag, st));
+    if (X->dtype == TS_F64)
+      return launch_fit_coo<double>(*X, ranks, static_cast<const double*>(core),
+                                    reinterpret_cast<const double* const*>(factors), w,
+                                    residual_out, st);
+    return launch_fit_coo<float>(*X, ranks, static_cast<const float*>(core),
+                                 reinterpret_cast<const float* const*>(factors), w, residual_out,
+                                 st);
+  }
   if (X->dtype == TS_F64) {
     double* q = b.take<double>(fit_dense_scratch_elems<double>(*X, ranks));
     double* acc = b.take<double>(2);
@@ -1463,7 +1491,13 @@ namespace ts {
 
 static ts_status cp_check(const ts_tensor* X, int R_cp, const int32_t* tranks, int m, int sweeps,
                           const ts_options* opt, bool want_residual, Shape& S) {
-  TS_TRY(plan_shape(X, tranks, TS_TENSORSKETCH, m, sweeps, opt, want_residual, S));
+  TS_TRY(plan_shape(X, tranks, TS_TENSORSKETCH, m, sweeps, opt, false, S));
+  if (want_residual && X->format == TS_COO) {
+    int rk[TS_MAX_ORDER];
+    for (int k = 0; k < X->order; ++k) rk[k] = R_cp;
+    if (!fit_coo_supported(*X) || !fit_coo_model_ok(*X, rk))
+      return fail(TS_ERR_UNSUPPORTED, "cp_via_tucker: COO residual outside its limits");
+  }
   long core = 1;
   int rmin = 1 << 30;
   for (int k = 0; k < X->order; ++k) {
@@ -1488,6 +1522,7 @@ struct CpWork {
   T* D;
   T* fq;
   double* acc;
+  FitCooWork fitc;  // COO residual
 };
 
 template <typename T>
@@ -1508,6 +1543,7 @@ static size_t cp_carve(const ts_tensor& X, const Shape& S, int Rc, Bump& b, CpWo
   c.D = b.take<T>((size_t)dcore);
   c.fq = X.format == TS_DENSE ? b.take<T>(fit_dense_scratch_elems<T>(X, rk)) : nullptr;
   c.acc = b.take<double>(2);
+  if (X.format == TS_COO) c.fitc = fit_coo_carve(X, rk, b);
   return b.off;
 }
 
@@ -1531,7 +1567,13 @@ static ts_status cp_impl(const ts_tensor& X, const Shape& S, const ts_options& o
     int rk[TS_MAX_ORDER];
     for (int k = 0; k < S.N; ++k) rk[k] = Rc;
     TS_TRY(launch_superdiag<T>(S.N, Rc, c.D, st));
-    TS_TRY(launch_fit_dense<T>(X, rk, c.D, (const T* const*)out, c.fq, c.acc, residual_out, st));
+    if (X.format == TS_COO) {
+      TS_TRY(launch_fit_coo_norm(X, c.fitc, flag, st));
+      TS_TRY(launch_fit_coo<T>(X, rk, c.D, (const T* const*)out, c.fitc, residual_out, st));
+    } else {
+      TS_TRY(launch_fit_dense<T>(X, rk, c.D, (const T* const*)out, c.fq, c.acc, residual_out,
+                                 st));
+    }
   }
   return TS_OK;
 }

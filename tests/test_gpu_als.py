@@ -206,11 +206,13 @@ def test_coo_tensor_matches_oracle(ts):
     dims, ranks, m = (300, 250, 200), (4, 4, 4), 400
     idx, vals, _, _ = synth.coo_zipf_tucker(dims, 60000, ranks, seed=5, val_dtype=np.float64)
     X = ts.Coo(torch.from_numpy(idx).cuda(), torch.from_numpy(vals).cuda(), dims)
-    core, fac, _ = ts.tucker_als_sketched(X, ranks, m, 2, seed=8, want_residual=False)
-    c_o, f_o, _ = tucker.sketch_tucker_als(tucker.Coo(idx.astype(np.int64), vals, dims), ranks, m,
-                                           2, seed=8)
+    core, fac, res = ts.tucker_als_sketched(X, ranks, m, 2, seed=8, track_fit=True)
+    Xo = tucker.Coo(idx.astype(np.int64), vals, dims)
+    c_o, f_o, r_o = tucker.sketch_tucker_als(Xo, ranks, m, 2, seed=8, track_fit=True)
     for n in range(3):
         assert np.abs(proj(fac[n].cpu().numpy()) - proj(f_o[n])).max() < 1e-9
+    # COO residuals on the device (repeated coordinates merged) after every sweep
+    assert np.allclose(res.cpu().numpy(), r_o, rtol=1e-9, atol=0)
 
 
 @pytest.mark.parametrize("kind", ["lev", "lev_det"])
@@ -254,6 +256,25 @@ def test_cp_via_tucker_fp64_matches_oracle(ts):
         assert np.abs(outs[k].cpu().numpy() - B[k]).max() <= 1e-6 * np.abs(B[k]).max()
     want = np.linalg.norm(T - tucker.cp_reconstruct(B)) / np.linalg.norm(T)
     assert abs(res - want) <= 1e-7 * max(want, 1e-12)
+
+
+def test_cp_via_tucker_coo_residual(ts):
+    # Alg. 6 on a COO copy of a small CP tensor (every entry once plus cancelling
+    # repeats): the residual on the device equals the oracle's COO identity on the
+    # returned factors and the dense residual of the same factors.
+    T, _ = synth.cp_collinear((20, 18, 16), 3, 0.5, 1e-3, seed=5)
+    dims = T.shape
+    idx = np.stack(np.unravel_index(np.arange(T.size), dims)).astype(np.int32)
+    vals = T.reshape(-1).copy()
+    idx = np.concatenate([idx, idx[:, :40]], axis=1)
+    vals = np.concatenate([vals, np.zeros(40)])
+    vals[:40] -= 0.5
+    vals[-40:] += 0.5
+    X = ts.Coo(torch.from_numpy(idx).cuda().contiguous(), torch.from_numpy(vals).cuda(), dims)
+    outs, res = ts.cp_via_tucker(X, 3, (5, 5, 5), 200, 3, 10, seed=3)
+    B = [o.cpu().numpy() for o in outs]
+    want = np.linalg.norm(T - tucker.cp_reconstruct(B)) / np.linalg.norm(T)
+    assert abs(res - want) <= 1e-7 * max(want, 1e-9) + 1e-9
 
 
 def test_cp_via_tucker_fp32_collinear_workload(ts):

@@ -388,6 +388,45 @@ def test_fitness_matches_direct_reconstruction(ts, dims, ranks, dtype):
     assert abs(got - want) <= tol * want
 
 
+@pytest.mark.parametrize("dims,ranks,nnz,dtype", [((40, 30, 20), (5, 4, 3), 5000, torch.float64),
+                                                   ((40, 30, 20), (5, 4, 3), 5000, torch.float32),
+                                                   ((30, 20, 25, 10), (3, 2, 4, 2), 8000,
+                                                    torch.float64),
+                                                   ((3000, 2000, 1500), (8, 8, 8), 300000,
+                                                    torch.float32)])
+def test_fitness_coo_matches_oracle(ts, dims, ranks, nnz, dtype):
+    # ||T||^2 - 2 <T, T~> + ||T~||^2 with repeated coordinates merged for ||T||^2, against
+    # the oracle's identity (itself pinned to direct reconstruction); factors not
+    # orthonormal, so ||T~|| is not ||C||
+    idx, vals = _coo_dup(dims, nnz, seed=8, zipf=dims[0] > 1000)
+    g = np.random.default_rng(9)
+    core = g.standard_normal(ranks)
+    A = [g.standard_normal((s, R)) / np.sqrt(s) for s, R in zip(dims, ranks)]
+    if dtype == torch.float32:
+        vals = vals.astype(np.float32).astype(np.float64)
+        core = core.astype(np.float32).astype(np.float64)
+        A = [a.astype(np.float32).astype(np.float64) for a in A]
+    want = tucker.residual(tucker.Coo(idx.astype(np.int64), vals, dims), core, A)
+    X = ts.Coo(torch.from_numpy(idx).cuda().contiguous(), dev(vals, dtype), tuple(dims))
+    got = ts.fitness_residual(X, dev(core, dtype), [dev(a, dtype) for a in A])
+    tol = 1e-11 if dtype == torch.float64 else 1e-5
+    assert abs(got - want) <= tol * max(want, 1e-3)
+
+
+def test_fitness_coo_exact_model_is_zero(ts):
+    # a COO tensor holding every entry of a Tucker tensor once (plus explicit repeats
+    # that cancel) has residual ~0 against its own model
+    dims, ranks = (12, 9, 7), (3, 2, 2)
+    T, core, A = synth.dense_tucker(dims, ranks, 0.0, seed=10)
+    idx = np.stack(np.unravel_index(np.arange(T.size), dims)).astype(np.int32)
+    vals = T.reshape(-1)
+    idx = np.concatenate([idx, idx[:, :50], idx[:, :50]], axis=1)
+    vals = np.concatenate([vals, np.full(50, 0.25), np.full(50, -0.25)])
+    X = ts.Coo(torch.from_numpy(idx).cuda().contiguous(), dev(vals), dims)
+    got = ts.fitness_residual(X, dev(core), [dev(a) for a in A])
+    assert got < 1e-6   # sqrt of a cancellation at FP64 rounding
+
+
 # ---------------------------------------------------------------- a7/a10 BF16 Gram products
 
 def _bf16_round(x):

@@ -340,6 +340,9 @@ ts_status ts_fitness(const ts_tensor* X, const int32_t* ranks, const void* core,
  * excluded by its capacity), which the caller reads after synchronising.
  * Residuals of COO tensors follow ts_fitness (||T||^2 formed once per call, with its
  * fibre index and hash table in the workspace; TS_ERR_UNSUPPORTED under its limits).
+ * tucker_als_workspace_bytes counts the residual's scratch whenever a residual can be
+ * formed (for COO input about 40 bytes per nonzero), so one size serves calls with and
+ * without residual_out.
  * Errors: TS_ERR_SHAPE if order < 2, any ranks[k] < 1 or ranks[k] >= dims[k]
  * (the theory assumes s > R), m < prod_{k != n} ranks[k] for some n (the sketched
  * system must be able to have full column rank), or a per-call limit above is

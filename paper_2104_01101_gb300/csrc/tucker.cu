@@ -1013,15 +1013,17 @@ extern "C" ts_status tucker_als_workspace_bytes(const ts_tensor* X, const int32_
   clear_error();
   if (!bytes_out) return fail(TS_ERR_INVALID_ARG, "tucker_als_workspace_bytes: NULL bytes_out");
   Shape S;
-  // Residual scratch is always counted so one size serves both uses.
+  // Residual scratch is always counted (where a residual can be formed) so that one size
+  // serves calls with and without residual_out; without it the carve only shrinks.
   TS_TRY(plan_shape(X, ranks, kind, m, sweeps, opt, X && X->format == TS_DENSE, S));
+  const bool fit = X->format == TS_DENSE || (fit_coo_supported(*X) && fit_coo_model_ok(*X, ranks));
   Bump b;
   if (X->dtype == TS_F64) {
     Work<double> w;
-    carve<double>(*X, S, X->format == TS_DENSE, b, w);
+    carve<double>(*X, S, fit, b, w);
   } else {
     Work<float> w;
-    carve<float>(*X, S, X->format == TS_DENSE, b, w);
+    carve<float>(*X, S, fit, b, w);
   }
   *bytes_out = b.off;
   return TS_OK;
@@ -1041,6 +1043,18 @@ extern "C" ts_status tucker_als_sketched(const ts_tensor* X, const int32_t* rank
     if (!factors_inout[k]) return fail(TS_ERR_INVALID_ARG, "tucker_als_sketched: factor %d NULL", k);
   size_t need = 0;
   TS_TRY(tucker_als_workspace_bytes(X, ranks, kind, m, sweeps, opt, &need));
+  {
+    // the carve of this very call (with or without the residual) must fit as well
+    Bump b;
+    if (X->dtype == TS_F64) {
+      Work<double> w;
+      carve<double>(*X, S, residual_out != nullptr, b, w);
+    } else {
+      Work<float> w;
+      carve<float>(*X, S, residual_out != nullptr, b, w);
+    }
+    if (b.off > need) need = b.off;
+  }
   if (!workspace || workspace_bytes < need || ((uintptr_t)workspace & 255))
     return fail(TS_ERR_WORKSPACE, "tucker_als_sketched: need %zu bytes of 256-aligned workspace",
                 need);

@@ -80,3 +80,41 @@ def test_lrls_scratch_query_covers_every_supported_path(libpath):
     large = L.ts_lrls_scratch_bytes(3000, 625, 300, 25, 0, 5, 0)
     assert fused > 0 and large > 4 * 625 * 625
     assert L.ts_lrls_scratch_bytes(3000, 625, 300, 70, 0, 5, 0) == 0
+
+
+def _coo_desc(ts, dims, nnz):
+    d = ts._Tensor()
+    d.order = len(dims)
+    for k, s in enumerate(dims):
+        d.dims[k] = s
+    d.format = ts.TS_COO
+    d.dtype = ts.TS_F32
+    d.values, d.indices, d.nnz = 0x1000, 0x2000, nnz   # never dereferenced by the queries
+    return d
+
+
+def test_coo_workspace_counts_the_residual_scratch(libpath):
+    # A COO decomposition asked for its residual carves a fibre index and a hash table
+    # (~40 bytes per nonzero and more); the one workspace size must cover that carve.
+    from paper_2104_01101_gb300 import tsketch as ts
+    L = ts.lib()
+    rk = (ctypes.c_int32 * 3)(4, 4, 4)
+    opt = ts._options(0, ts.SOLVE_RSVD, 5, None, None, False, False, False)
+
+    def need(nnz, kind=ts.TENSORSKETCH):
+        n = ctypes.c_size_t(0)
+        d = _coo_desc(ts, (300, 250, 200), nnz)
+        assert L.tucker_als_workspace_bytes(ctypes.byref(d), rk, kind, 400, 2, ctypes.byref(opt),
+                                            ctypes.byref(n)) == 0
+        return n.value
+
+    assert need(1_000_000) - need(100_000) >= 40 * 900_000
+    # leverage sampling adds a fibre index per mode
+    assert need(1_000_000, ts.LEVERAGE) - need(100_000, ts.LEVERAGE) >= 3 * 20 * 900_000
+    # a workspace one byte short is refused before any work is enqueued
+    d = _coo_desc(ts, (300, 250, 200), 1000)
+    fac = (ctypes.c_void_p * 3)(0x10, 0x20, 0x30)
+    st = L.tucker_als_sketched(ctypes.byref(d), rk, ts.TENSORSKETCH, 400, 2, ctypes.byref(opt),
+                               ctypes.c_void_p(0x100000), need(1000) - 1, ctypes.c_void_p(0x40),
+                               fac, ctypes.c_void_p(0x50), None)
+    assert st == 3 and b"workspace" in L.ts_last_error()   # TS_ERR_WORKSPACE

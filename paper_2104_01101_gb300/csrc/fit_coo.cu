@@ -141,6 +141,82 @@ __global__ void __launch_bounds__(256) k_coo_inner(const int32_t* __restrict__ i
   if (threadIdx.x == 0) atomicAdd(out, acc);
 }
 
+// Unrolled form for order N <= 4 with every rank <= RR: the core zero-padded to RR^N in
+// shared memory; the rows of the last two modes in registers and their RR^2 terms fully
+// unrolled (the last mode innermost); the leading modes looped, their factor entries
+// read through L1.
+template <typename T, int N, int RR>
+__global__ void __launch_bounds__(256) k_coo_inner_fixed(const int32_t* __restrict__ idx,
+                                                         const T* __restrict__ vals, int64_t nnz,
+                                                         CooModel d, const T* __restrict__ core,
+                                                         double* out) {
+  static_assert(N >= 2 && N <= 4, "orders 2..4");
+  constexpr int P = N == 2 ? RR * RR : N == 3 ? RR * RR * RR : RR * RR * RR * RR;
+  extern __shared__ unsigned char smraw[];
+  T* sc = reinterpret_cast<T*>(smraw);
+  __shared__ double sh[32];
+  for (int i = threadIdx.x; i < P; i += blockDim.x) {
+    int rem = i;
+    long src = 0, stride = 1;
+    bool in = true;
+    for (int k = N - 1; k >= 0; --k) {
+      const int rk = rem % RR;
+      rem /= RR;
+      in &= rk < d.ranks[k];
+      src += rk * stride;
+      stride *= d.ranks[k];
+    }
+    sc[i] = in ? core[src] : (T)0;
+  }
+  __syncthreads();
+  double acc = 0;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    T a[2][RR];  // rows of modes N-2 and N-1
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int k = N - 2 + q;
+      const T* A = static_cast<const T*>(d.factors[k]);
+      const int64_t i = idx[(int64_t)k * nnz + e];
+      const int R = d.ranks[k];
+#pragma unroll
+      for (int r = 0; r < RR; ++r) a[q][r] = r < R ? __ldg(A + i * R + r) : (T)0;
+    }
+    // leading modes 0 .. N-3: npre = RR^(N-2) prefixes, each weighting one RR x RR block
+    const T* A0 = static_cast<const T*>(d.factors[0]);
+    const T* A1 = static_cast<const T*>(d.factors[1]);
+    const int R0 = d.ranks[0], R1 = d.ranks[1];
+    const int64_t i0 = idx[e];
+    const int64_t i1 = N == 4 ? idx[nnz + e] : 0;
+    constexpr int NPRE = N == 2 ? 1 : N == 3 ? RR : RR * RR;
+    T s = 0;
+    for (int c = 0; c < NPRE; ++c) {
+      T w = 1;
+      if constexpr (N == 3) {
+        if (c >= R0) continue;
+        w = __ldg(A0 + i0 * R0 + c);
+      } else if constexpr (N == 4) {
+        const int r0 = c / RR, r1 = c % RR;
+        if (r0 >= R0 || r1 >= R1) continue;
+        w = __ldg(A0 + i0 * R0 + r0) * __ldg(A1 + i1 * R1 + r1);
+      }
+      const T* blk = sc + c * RR * RR;
+      T s2 = 0;
+#pragma unroll
+      for (int r2 = 0; r2 < RR; ++r2) {
+        T inner = 0;
+#pragma unroll
+        for (int r3 = 0; r3 < RR; ++r3) inner += blk[r2 * RR + r3] * a[1][r3];
+        s2 += a[0][r2] * inner;
+      }
+      s += w * s2;
+    }
+    acc += (double)s * (double)vals[e];
+  }
+  acc = block_sum_d(acc, sh);
+  if (threadIdx.x == 0) atomicAdd(out, acc);
+}
+
 // G_n = A^(n)T A^(n): block (a, b, n) sums A(:, a) A(:, b) over the rows in FP64.
 template <typename T>
 __global__ void k_gram_cols(CooModel d, T* G, int gstride) {
@@ -287,7 +363,23 @@ ts_status launch_fit_coo(const ts_tensor& X, const int* ranks, const T* core,
   }
   TS_CUDA(cudaMemsetAsync(w.acc + 1, 0, sizeof(double), st));
   const int RLr = ranks[N - 1];
-  if (RLr <= 8) TS_TRY((inner_launch<T, 8>(X, d, core, w.acc + 1, st)));
+  int rmax = 0;
+  for (int k = 0; k < N; ++k) rmax = std::max(rmax, ranks[k]);
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(X.nnz, 256), 1), 152 * 8);
+  const T* vals = static_cast<const T*>(X.values);
+  auto fixed = [&](auto kern, int P) -> ts_status {
+    const size_t smem = (size_t)P * sizeof(T);
+    if (smem > 48 * 1024)
+      TS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, 256, smem, st>>>(X.indices, vals, X.nnz, d, core, w.acc + 1);
+    TS_LAUNCH_CHECK();
+    return TS_OK;
+  };
+  if (N == 4 && rmax <= 8) TS_TRY(fixed(k_coo_inner_fixed<T, 4, 8>, 4096));
+  else if (N == 3 && rmax <= 8) TS_TRY(fixed(k_coo_inner_fixed<T, 3, 8>, 512));
+  else if (N == 3 && rmax <= 16) TS_TRY(fixed(k_coo_inner_fixed<T, 3, 16>, 4096));
+  else if (N == 2 && rmax <= 16) TS_TRY(fixed(k_coo_inner_fixed<T, 2, 16>, 256));
+  else if (RLr <= 8) TS_TRY((inner_launch<T, 8>(X, d, core, w.acc + 1, st)));
   else if (RLr <= 16) TS_TRY((inner_launch<T, 16>(X, d, core, w.acc + 1, st)));
   else if (RLr <= 32) TS_TRY((inner_launch<T, 32>(X, d, core, w.acc + 1, st)));
   else if (RLr <= 64) TS_TRY((inner_launch<T, 64>(X, d, core, w.acc + 1, st)));

@@ -266,10 +266,13 @@ ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, co
 // Factor columns V (s x R) with V(i, c) = sum_a M(i, a) Fm(a, c) (M element (i, a) at
 // M[i*rs + a*cs], a < kdim), or V(i, c) = M[i*rs + c*cs] when Fm is null.  Each
 // column is signed so that its largest-|.| entry is positive; A_out = V; CnT (r x R)
-// is flipped with it and, when core != null, scattered into the core.
+// is flipped with it and, when core != null, scattered into the core.  Tall columns
+// (s >= 6145) run over many blocks when `scratch` (stream-ordered, free) holds the
+// chunk maxima: nb * R * (sizeof(T) + 4) + 256 bytes, nb = ceil(s / max(2048, ceil(s / 256))).
 template <typename T>
 ts_status launch_finalize(int s, int R, const T* M, long rs, long cs, int kdim, const T* Fm,
-                          T* A_out, T* CnT, int r, T* core, CoreMap map, cudaStream_t st);
+                          T* A_out, T* CnT, int r, T* core, CoreMap map, cudaStream_t st,
+                          void* scratch = nullptr, size_t scratch_bytes = 0);
 
 // ---------------------------------------------------------------- fibre_index.cu
 // Hash index of the mode-`mode` fibres of a COO tensor (device arrays; passed to

@@ -491,6 +491,54 @@ __device__ __forceinline__ T vcol(const T* M, long rs, long cs, int kdim, const 
   return v;
 }
 
+// Column c of C_(n)^T flipped by sgn and, when core != null, scattered into the core.
+template <typename T>
+__device__ __forceinline__ void flip_core_column(int c, int R, T sgn, T* __restrict__ CnT, int r,
+                                                 T* __restrict__ core, const CoreMap& map) {
+  for (int rho = threadIdx.x; rho < r; rho += blockDim.x) {
+    const T v = sgn * CnT[(long)rho * R + c];
+    CnT[(long)rho * R + c] = v;
+    if (core) {
+      long idx = 0, stride = 1, x = rho;
+      for (int k = map.order - 1; k >= 0; --k) {
+        int digit;
+        if (k == map.n) {
+          digit = c;
+        } else {
+          digit = (int)(x % map.ranks[k]);
+          x /= map.ranks[k];
+        }
+        idx += digit * stride;
+        stride *= map.ranks[k];
+      }
+      core[idx] = v;
+    }
+  }
+}
+
+// (value, index) of the larger magnitude, the lower index on ties
+template <typename T>
+__device__ __forceinline__ void keep_larger(T& bv, int& bi, T v, int i) {
+  if (v > bv || (v == bv && i < bi)) {
+    bv = v;
+    bi = i;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void block_argmax(T& best, int& bidx, T* bv, int* bi) {
+  bv[threadIdx.x] = best;
+  bi[threadIdx.x] = bidx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) keep_larger(bv[threadIdx.x], bi[threadIdx.x], bv[threadIdx.x + w],
+                                     bi[threadIdx.x + w]);
+    __syncthreads();
+  }
+  best = bv[0];
+  bidx = bi[0];
+}
+
 // Block c: canonical sign of column c of V (entry of largest magnitude positive,
 // lowest index on ties); A_out(:, c) = sign * V(:, c), CnT(:, c) *= sign and, when
 // core != null, C_(n)^T is scattered into the core.
@@ -501,57 +549,62 @@ __global__ void __launch_bounds__(256) k_finalize(int s, int R, const T* __restr
                                                   int r, T* __restrict__ core, CoreMap map) {
   __shared__ T bv[256];
   __shared__ int bi[256];
-  __shared__ T sgn_s;
   const int c = blockIdx.x;
   T best = (T)-1;
   int bidx = 0x7fffffff;
-  for (int i = threadIdx.x; i < s; i += blockDim.x) {
-    const T a = fabs(vcol<T>(M, rs, cs, kdim, Fm, R, i, c));
-    if (a > best || (a == best && i < bidx)) {
-      best = a;
-      bidx = i;
-    }
-  }
-  bv[threadIdx.x] = best;
-  bi[threadIdx.x] = bidx;
-  __syncthreads();
-  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      const T ob = bv[threadIdx.x + w];
-      const int oi = bi[threadIdx.x + w];
-      if (ob > bv[threadIdx.x] || (ob == bv[threadIdx.x] && oi < bi[threadIdx.x])) {
-        bv[threadIdx.x] = ob;
-        bi[threadIdx.x] = oi;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) sgn_s = vcol<T>(M, rs, cs, kdim, Fm, R, bi[0], c) < (T)0 ? (T)-1 : (T)1;
-  __syncthreads();
-  const T sgn = sgn_s;
+  for (int i = threadIdx.x; i < s; i += blockDim.x)
+    keep_larger(best, bidx, (T)fabs(vcol<T>(M, rs, cs, kdim, Fm, R, i, c)), i);
+  block_argmax(best, bidx, bv, bi);
+  const T sgn = vcol<T>(M, rs, cs, kdim, Fm, R, bidx, c) < (T)0 ? (T)-1 : (T)1;
   for (int i = threadIdx.x; i < s; i += blockDim.x)
     A_out[(long)i * R + c] = sgn * vcol<T>(M, rs, cs, kdim, Fm, R, i, c);
-  if (CnT) {
-    for (int rho = threadIdx.x; rho < r; rho += blockDim.x) {
-      const T v = sgn * CnT[(long)rho * R + c];
-      CnT[(long)rho * R + c] = v;
-      if (core) {
-        long idx = 0, stride = 1, x = rho;
-        for (int k = map.order - 1; k >= 0; --k) {
-          int digit;
-          if (k == map.n) {
-            digit = c;
-          } else {
-            digit = (int)(x % map.ranks[k]);
-            x /= map.ranks[k];
-          }
-          idx += digit * stride;
-          stride *= map.ranks[k];
-        }
-        core[idx] = v;
-      }
-    }
+  if (CnT) flip_core_column(c, R, sgn, CnT, r, core, map);
+}
+
+// Tall columns, first pass: block (b, c) finds the largest |V(i, c)| over its chunk of rows.
+template <typename T>
+__global__ void __launch_bounds__(256) k_finalize_scan(int s, int R, const T* __restrict__ M,
+                                                       long rs, long cs, int kdim,
+                                                       const T* __restrict__ Fm, int chunk,
+                                                       T* __restrict__ pv, int* __restrict__ pi) {
+  __shared__ T bv[256];
+  __shared__ int bi[256];
+  const int c = blockIdx.y, b = blockIdx.x;
+  const int i1 = min(s, (b + 1) * chunk);
+  T best = (T)-1;
+  int bidx = 0x7fffffff;
+  for (int i = b * chunk + threadIdx.x; i < i1; i += blockDim.x)
+    keep_larger(best, bidx, (T)fabs(vcol<T>(M, rs, cs, kdim, Fm, R, i, c)), i);
+  block_argmax(best, bidx, bv, bi);
+  if (threadIdx.x == 0) {
+    pv[(long)c * gridDim.x + b] = best;
+    pi[(long)c * gridDim.x + b] = bidx;
   }
+}
+
+// Second pass: every block reduces the column's chunk maxima (the same winner as the
+// one-block pass), writes its chunk of A_out; block (0, c) flips C_(n)^T.
+template <typename T>
+__global__ void __launch_bounds__(256) k_finalize_write(int s, int R, const T* __restrict__ M,
+                                                        long rs, long cs, int kdim,
+                                                        const T* __restrict__ Fm, int chunk,
+                                                        const T* __restrict__ pv,
+                                                        const int* __restrict__ pi,
+                                                        T* __restrict__ A_out, T* __restrict__ CnT,
+                                                        int r, T* __restrict__ core, CoreMap map) {
+  __shared__ T bv[256];
+  __shared__ int bi[256];
+  const int c = blockIdx.y, b = blockIdx.x, nb = gridDim.x;
+  T best = (T)-1;
+  int bidx = 0x7fffffff;
+  for (int j = threadIdx.x; j < nb; j += blockDim.x)
+    keep_larger(best, bidx, pv[(long)c * nb + j], pi[(long)c * nb + j]);
+  block_argmax(best, bidx, bv, bi);
+  const T sgn = vcol<T>(M, rs, cs, kdim, Fm, R, bidx, c) < (T)0 ? (T)-1 : (T)1;
+  const int i1 = min(s, (b + 1) * chunk);
+  for (int i = b * chunk + threadIdx.x; i < i1; i += blockDim.x)
+    A_out[(long)i * R + c] = sgn * vcol<T>(M, rs, cs, kdim, Fm, R, i, c);
+  if (CnT && b == 0) flip_core_column(c, R, sgn, CnT, r, core, map);
 }
 
 // ---------------------------------------------------------------- launchers
@@ -615,7 +668,23 @@ ts_status launch_eig_small(int n, int R, const T* K, const T* Q, int r, T* CnT, 
 
 template <typename T>
 ts_status launch_finalize(int s, int R, const T* M, long rs, long cs, int kdim, const T* Fm,
-                          T* A_out, T* CnT, int r, T* core, CoreMap map, cudaStream_t st) {
+                          T* A_out, T* CnT, int r, T* core, CoreMap map, cudaStream_t st,
+                          void* scratch, size_t scratch_bytes) {
+  // tall columns over many SMs when the caller lends scratch for the chunk maxima
+  const int chunk = std::max(2048, ceil_div(s, 256));
+  const int nb = ceil_div(s, chunk);
+  if (nb >= 4 && scratch &&
+      scratch_bytes >= (size_t)nb * R * (sizeof(T) + sizeof(int)) + 256) {
+    T* pv = static_cast<T*>(scratch);
+    int* pi = reinterpret_cast<int*>(static_cast<char*>(scratch) +
+                                     align_up((size_t)nb * R * sizeof(T), 256));
+    k_finalize_scan<T><<<dim3(nb, R), 256, 0, st>>>(s, R, M, rs, cs, kdim, Fm, chunk, pv, pi);
+    TS_LAUNCH_CHECK();
+    k_finalize_write<T><<<dim3(nb, R), 256, 0, st>>>(s, R, M, rs, cs, kdim, Fm, chunk, pv, pi,
+                                                     A_out, CnT, r, core, map);
+    TS_LAUNCH_CHECK();
+    return TS_OK;
+  }
   k_finalize<T><<<R, 256, 0, st>>>(s, R, M, rs, cs, kdim, Fm, A_out, CnT, r, core, map);
   TS_LAUNCH_CHECK();
   return TS_OK;
@@ -628,7 +697,7 @@ ts_status launch_finalize(int s, int R, const T* M, long rs, long cs, int kdim, 
   template ts_status launch_eig_small<T>(int, int, const T*, const T*, int, T*, T*, T*, bool,   \
                                          int*, cudaStream_t);                                    \
   template ts_status launch_finalize<T>(int, int, const T*, long, long, int, const T*, T*, T*,  \
-                                        int, T*, CoreMap, cudaStream_t);                         \
+                                        int, T*, CoreMap, cudaStream_t, void*, size_t);          \
   template ts_status launch_qr_only<T>(int, int, const T*, T*, bool, cudaStream_t);             \
   template ts_status newton_schulz_inverse<T>(int, const T*, long, T*, T*, T*, int,             \
                                               const GemmSplit<T>*, cudaStream_t);

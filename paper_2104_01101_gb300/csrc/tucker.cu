@@ -453,7 +453,8 @@ static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc,
                    st));
     TS_TRY(launch_eig_small<T>(k, R, w.K, w.Q, r, w.CnT, w.Fm, nullptr, fp64, w.flag, st));
     // A = D^T Fm, signed; core written
-    return launch_finalize<T>(s, R, w.D, 1, s, k, w.Fm, A_out, w.CnT, r, core, map, st);
+    return launch_finalize<T>(s, R, w.D, 1, s, k, w.Fm, A_out, w.CnT, r, core, map, st,
+                              w.split.partial, w.split.partial_elems * sizeof(T));
   }
   // exact: G = Z^T Z;  H = Z^T Y;  X = G^{-1} H;  K = X X^T;  A = X^T Fm
   TS_TRY(gemm<T>(r, r, m, 1.0, Zt, Zm, 0.0, ov<T>(w.GW, r, 1), sp, st));
@@ -462,7 +463,8 @@ static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc,
   TS_TRY(gemm<T>(r, r, s, 1.0, mv<T>(w.Xs, s, 1), mv<T>(w.Xs, 1, s), 0.0, ov<T>(w.K, r, 1), sp,
                  st));
   TS_TRY(launch_eig_small<T>(r, R, w.K, nullptr, r, w.CnT, w.Fm, nullptr, fp64, w.flag, st));
-  return launch_finalize<T>(s, R, w.Xs, 1, s, r, w.Fm, A_out, w.CnT, r, core, map, st);
+  return launch_finalize<T>(s, R, w.Xs, 1, s, r, w.Fm, A_out, w.CnT, r, core, map, st,
+                            w.split.partial, w.split.partial_elems * sizeof(T));
 }
 
 template <typename T>
@@ -520,7 +522,7 @@ static ts_status rrf_all(const ts_tensor& X, const Shape& S, uint64_t seed, Work
     TS_TRY(launch_eig_small<T>(k1, R, w.K, nullptr, k1, nullptr, w.Fm, nullptr, S.fp64solve,
                                w.flag, st));
     TS_TRY(launch_finalize<T>(s, R, w.Bm, k1, 1, k1, w.Fm, factors[n], nullptr, 0, nullptr, none,
-                              st));
+                              st, w.split.partial, w.split.partial_elems * sizeof(T)));
   }
   return TS_OK;
 }
@@ -1195,7 +1197,8 @@ static ts_status rrf_one(const ts_tensor& X, int mode, int R, int k1, int k2, ui
                  &w.split, st));
   TS_TRY(launch_eig_small<T>(k1, R, w.K, nullptr, k1, nullptr, w.Fm, nullptr, false, w.flag, st));
   CoreMap none{};
-  return launch_finalize<T>(s, R, w.Bm, k1, 1, k1, w.Fm, A_out, nullptr, 0, nullptr, none, st);
+  return launch_finalize<T>(s, R, w.Bm, k1, 1, k1, w.Fm, A_out, nullptr, 0, nullptr, none, st,
+                            w.split.partial, w.split.partial_elems * sizeof(T));
 }
 
 extern "C" ts_status range_finder_init(const ts_tensor* X, int32_t mode, int32_t R, int32_t k1,

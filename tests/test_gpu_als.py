@@ -59,6 +59,23 @@ def test_tensor_with_large_coherence_fp64_matches_oracle(ts, kind):
         assert np.abs(proj(fac[n].cpu().numpy()) - proj(f_o[n])).max() < 1e-9
 
 
+@pytest.mark.parametrize("solve", ["rsvd", "exact"])
+def test_tall_mode_matches_oracle(ts, solve):
+    # s = 8000 in mode 1: its Init-RRF factor and its subproblem take the multi-block
+    # finalize (column signs over 2048-row chunks, then the write), not the fused solve
+    dims, ranks, m, sweeps, seed = (30, 8000, 20), (3, 3, 2), 200, 2, 5
+    T, _, _ = synth.dense_tucker(dims, ranks, 1e-2, seed=6)
+    s_kind = ts.SOLVE_RSVD if solve == "rsvd" else ts.SOLVE_EXACT
+    core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, sweeps,
+                                            seed=seed, solve=s_kind, track_fit=True)
+    c_o, f_o, r_o = tucker.sketch_tucker_als(T, ranks, m, sweeps, seed=seed, solve=solve,
+                                             track_fit=True)
+    assert np.allclose(res.cpu().numpy(), r_o, rtol=1e-9, atol=0)
+    for n in range(3):
+        # factors themselves (signs included), not only their projectors
+        assert np.abs(fac[n].cpu().numpy() - f_o[n]).max() < 1e-9
+
+
 @pytest.mark.parametrize("kind", ["ts", "lev"])
 def test_exact_recovery_noiseless(ts, kind):
     T, _, _ = synth.dense_tucker((40, 40, 40), (5, 5, 5), 0.0, seed=2)

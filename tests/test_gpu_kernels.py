@@ -393,11 +393,16 @@ def test_fitness_matches_direct_reconstruction(ts, dims, ranks, dtype):
                                                    ((30, 20, 25, 10), (3, 2, 4, 2), 8000,
                                                     torch.float64),
                                                    ((3000, 2000, 1500), (8, 8, 8), 300000,
-                                                    torch.float32)])
+                                                    torch.float32),
+                                                   ((20, 25, 30), (3, 4, 20), 3000, torch.float64),
+                                                   ((9, 8, 7, 6, 5), (2, 3, 2, 3, 2), 2000,
+                                                    torch.float64),
+                                                   ((50, 40), (12, 9), 1500, torch.float32)])
 def test_fitness_coo_matches_oracle(ts, dims, ranks, nnz, dtype):
     # ||T||^2 - 2 <T, T~> + ||T~||^2 with repeated coordinates merged for ||T||^2, against
     # the oracle's identity (itself pinned to direct reconstruction); factors not
-    # orthonormal, so ||T~|| is not ||C||
+    # orthonormal, so ||T~|| is not ||C||.  Shapes cover the unrolled order-2/3/4 forms
+    # and the general one (a rank above 16, order 5).
     idx, vals = _coo_dup(dims, nnz, seed=8, zipf=dims[0] > 1000)
     g = np.random.default_rng(9)
     core = g.standard_normal(ranks)

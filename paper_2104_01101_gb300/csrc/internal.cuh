@@ -156,6 +156,18 @@ ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
                 MatView<T> B2, int n2, MatView<T> B3, double beta, OutView<T> C,
                 const GemmSplit<T>* split, cudaStream_t st);
 constexpr int kGemmCounters = 4096;
+// tall_products.cu: products with a huge dimension s (used from kTallMinS on).
+constexpr long kTallMinS = 16384;
+// D (k x s, row stride ldd) = M^T Y, M (m x k, row stride ldm, k <= 32), Y (m x s, ldy).
+template <typename T>
+ts_status tall_tn(int m, int k, long s, const T* M, long ldm, const T* Y, long ldy, T* D,
+                  long ldd, cudaStream_t st);
+// P (m x n; element (i, c) at P[i prs + c pcs]) = Y (m x s, ldy) Om (s x n, ldo), summed
+// over chunks of s through `part` (wide_nn_partial_elems values).
+size_t wide_nn_partial_elems(int m, int n, long s);
+template <typename T>
+ts_status wide_nn(int m, int n, long s, const T* Y, long ldy, const T* Om, long ldo, T* P,
+                  long prs, long pcs, T* part, size_t part_elems, cudaStream_t st);
 // One product of a batch: C (M x N) = A (M x K) [B1 | B2 | B3] (columns [0, n1) of B from
 // B1, [n1, n2) from B2, [n2, N) from B3).
 template <typename T>

@@ -389,8 +389,12 @@ static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc,
     if (yom) {
       yv = *yom;
     } else {
-      TS_TRY(gemm<T>(m, k, s, 1.0, mv<T>(Y, s, 1), mv<T>(Om, ldo, 1), 0.0,
-                     ov<T>(ZW + (size_t)r * m, 1, m), sp, st));
+      if (s >= kTallMinS)
+        TS_TRY(wide_nn<T>(m, k, s, Y, s, Om, ldo, ZW + (size_t)r * m, 1, m, sp->partial,
+                          sp->partial_elems, st));
+      else
+        TS_TRY(gemm<T>(m, k, s, 1.0, mv<T>(Y, s, 1), mv<T>(Om, ldo, 1), 0.0,
+                       ov<T>(ZW + (size_t)r * m, 1, m), sp, st));
       yv = mv<T>(ZW + (size_t)r * m, 1, m);
     }
   }
@@ -448,7 +452,11 @@ static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc,
     }
     // M = Z E (m x k);  D = M^T Y (k x s);  K = D D^T (k x k)
     TS_TRY(gemm<T>(m, k, r, 1.0, Zm, mv<T>(w.E, k, 1), 0.0, ov<T>(w.Mm, k, 1), sp, st));
-    TS_TRY(gemm<T>(k, s, m, 1.0, mv<T>(w.Mm, 1, k), mv<T>(Y, s, 1), 0.0, ov<T>(w.D, s, 1), sp, st));
+    if (s >= kTallMinS)
+      TS_TRY(tall_tn<T>(m, k, s, w.Mm, k, Y, s, w.D, s, st));
+    else
+      TS_TRY(gemm<T>(k, s, m, 1.0, mv<T>(w.Mm, 1, k), mv<T>(Y, s, 1), 0.0, ov<T>(w.D, s, 1), sp,
+                     st));
     TS_TRY(gemm<T>(k, k, s, 1.0, mv<T>(w.D, s, 1), mv<T>(w.D, 1, s), 0.0, ov<T>(w.K, k, 1), sp,
                    st));
     TS_TRY(launch_eig_small<T>(k, R, w.K, w.Q, r, w.CnT, w.Fm, nullptr, fp64, w.flag, st));
@@ -559,9 +567,14 @@ static ts_status rhs_times_omegas(const ts_tensor& X, const Shape& S, Work<T>& w
     const int k = S.kc[n];
     const long ld = (long)S.sweeps * k;
     const int s = (int)X.dims[n];
-    TS_TRY(gemm<T>(S.m, nt * k, s, 1.0, mv<T>(w.Y[n], s, 1),
-                   mv<T>(w.Om + S.ob.off[n] + (size_t)t0 * k, ld, 1), 0.0,
-                   ov<T>(w.YOm + S.yom_off[n] + (size_t)t0 * k, ld, 1), &w.split, st));
+    if (s >= kTallMinS)
+      TS_TRY(wide_nn<T>(S.m, nt * k, s, w.Y[n], s, w.Om + S.ob.off[n] + (size_t)t0 * k, ld,
+                        w.YOm + S.yom_off[n] + (size_t)t0 * k, ld, 1, w.split.partial,
+                        w.split.partial_elems, st));
+    else
+      TS_TRY(gemm<T>(S.m, nt * k, s, 1.0, mv<T>(w.Y[n], s, 1),
+                     mv<T>(w.Om + S.ob.off[n] + (size_t)t0 * k, ld, 1), 0.0,
+                     ov<T>(w.YOm + S.yom_off[n] + (size_t)t0 * k, ld, 1), &w.split, st));
   }
   return TS_OK;
 }

@@ -233,6 +233,29 @@ def test_rsvd_lrls_matches_oracle(ts, m, r, s, R, dtype):
     assert np.abs(Ag.cpu().numpy() - Aw).max() <= (1e-9 if dtype == torch.float64 else 1e-4)
 
 
+@pytest.mark.parametrize("m,r,s,R,k", [(600, 225, 20000, 3, None), (700, 64, 70000, 8, None),
+                                       (512, 300, 17000, 20, 28)])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_rsvd_lrls_wide_s_matches_oracle(ts, m, r, s, R, k, dtype):
+    # s >= 16384 (a mode size of the sparse workloads): Y Omega and D = (Z E)^T Y take the
+    # one-pass products over Y (split over s; k sums per column), the factor signs the
+    # multi-block finalize; r s > 2^22 keeps the multi-kernel solve.  k = 28 takes the
+    # 32-wide register form of the D product.
+    Z, Y = _solve_problem(4, m, r, s, R, 0.05)
+    if dtype == torch.float32:
+        Z = Z.astype(np.float32).astype(np.float64)
+        Y = Y.astype(np.float32).astype(np.float64)
+    p = 5 if k is None else k - R
+    kk = solve.rsvd_oversampled_rank(R, p, r, s)
+    Om = rng.gaussian(91, rng.make_tag(4, 1, 0, 0), s * kk).reshape(s, kk)
+    Cw, Aw = solve.rsvd_lrls(Z, Y, R, Om)
+    Cg, Ag = ts.lrls_solve(dev(Z, dtype), dev(Y, dtype), R, ts.SOLVE_RSVD, seed=91, sweep=1, n=0,
+                           oversample=p)
+    Bw, Bg = Cw @ Aw.T, Cg.cpu().numpy() @ Ag.cpu().numpy().T
+    tol = 1e-11 if dtype == torch.float64 else 2e-5
+    assert np.linalg.norm(Bg - Bw) <= tol * np.linalg.norm(Bw)
+
+
 @pytest.mark.parametrize("m,r,s,R", [(2048, 256, 3000, 8), (3000, 625, 300, 25)])
 def test_rsvd_lrls_large_r_matches_oracle(ts, m, r, s, R):
     # r too large for the on-chip Cholesky: G^{-1} by Newton-Schulz products

@@ -39,6 +39,13 @@ BATCH_COUNT, BATCH_SIZES, BATCH_RANKS, BATCH_SWEEPS, BATCH_SEED = 256, (32, 160)
 BATCH_WORKLOAD = ("256 dense 3-way FP32 tensors, mode sizes uniform in [32,160], one Tucker "
                   "rank R uniform in [4,12] per tensor, noise 1e-2; TensorSketch m=8R^2; RRF "
                   "init; RSVD-LRLS (p=5); 5 sweeps")
+# The sparse 4-way workload at full size: 200000^4, 1e8 nonzeros with Zipf(1.1) coordinates
+# and values N(0,1) plus a planted rank-(8,8,8,8) Tucker component of equal norm.
+SPARSE_DIMS, SPARSE_NNZ, SPARSE_RANKS, SPARSE_M, SPARSE_SWEEPS = (200000,) * 4, 100_000_000, \
+    (8, 8, 8, 8), 4096, 5
+SPARSE_WORKLOAD = ("sparse 4-way COO 200000^4, 1e8 nonzeros, Zipf(1.1) int32 coordinates, FP32 "
+                   "values N(0,1) plus a planted rank-(8,8,8,8) Tucker component; TensorSketch "
+                   "m=4096; RRF init k1=64, k2=128; RSVD-LRLS (p=5); 5 sweeps; COO residual")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -223,6 +230,45 @@ def time_batched(args, dev, flush):
             "graph": "all sweeps of the batch captured once, replayed"}
 
 
+def time_sparse(args, dev):
+    """The sparse 4-way workload at full size, one decomposition per step (the COO input
+    sketch, Init-RRF, 5 sweeps and the COO residual): sweeps/s, phases and the input
+    sketch's bytes per second.  Inputs (2 GB of nonzeros, 13 GB of sketches) exceed L2."""
+    import torch
+    from paper_2104_01101_gb300 import synth, tsketch as ts
+
+    idx, vals = synth.coo_zipf_tucker_torch(SPARSE_DIMS, SPARSE_NNZ, SPARSE_RANKS, seed=11,
+                                            device=dev)
+    X = ts.Coo(idx, vals, SPARSE_DIMS)
+    plan = ts.TuckerPlan(X, SPARSE_RANKS, SPARSE_M, SPARSE_SWEEPS, seed=3, rrf_k1=64,
+                         rrf_k2=128)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    plan.set_phase_events(ev)
+    steps = []
+    for i in range(1 + max(1, min(args.steps, 3))):
+        plan.run(X)
+        torch.cuda.synchronize()
+        if i:
+            steps.append([ev[j].elapsed_time(ev[j + 1]) for j in range(5)])
+    if plan.numeric_flag() != 0:
+        raise RuntimeError("sparse workload: breakdown flagged by the device")
+    ph = [statistics.mean(x[j] for x in steps) for j in range(5)]
+    total = sum(ph)
+    # one read of the coordinates and values; every sketch Y_n (m x s_n) written once
+    alg = SPARSE_NNZ * (4 * len(SPARSE_DIMS) + 4) + 4 * SPARSE_M * sum(SPARSE_DIMS)
+    out = {"workload": SPARSE_WORKLOAD, "sweeps_per_s": SPARSE_SWEEPS * 1e3 / total,
+           "ms_per_decomposition": total,
+           "phases_ms": {"init_and_norm": ph[0], "tables": ph[1], "input_sketch": ph[2],
+                         "sweeps": ph[3], "residual": ph[4]},
+           "input_sketch_gbs": alg / (ph[2] * 1e-3) / 1e9,
+           "input_sketch_algorithmic_bytes": int(alg),
+           "residual": float(plan.residuals[0]), "steps": len(steps),
+           "workspace_gb": plan.workspace.numel() / 1e9}
+    del plan, X, idx, vals
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args, rank, world):
     import torch
     import torch.distributed as dist
@@ -356,6 +402,8 @@ def run_ours(args, rank, world):
     }
     if not args.no_batched:
         line["batched"] = time_batched(args, dev, flush)
+    if not args.no_sparse:
+        line["sparse"] = time_sparse(args, dev)
     if not args.no_cpu_baseline:
         T64 = T.astype(np.float64)
         dt, _ = cpu_oracle_step(T64)
@@ -391,6 +439,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched-form measurement (256 small tensors)")
+    ap.add_argument("--no-sparse", action="store_true",
+                    help="skip the full-size sparse 4-way measurement (1e8 nonzeros)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -182,25 +182,9 @@ __global__ void __launch_bounds__(256) k_coo_inner_fixed(const int32_t* __restri
 #pragma unroll
       for (int r = 0; r < RR; ++r) a[q][r] = r < R ? __ldg(A + i * R + r) : (T)0;
     }
-    // leading modes 0 .. N-3: npre = RR^(N-2) prefixes, each weighting one RR x RR block
-    const T* A0 = static_cast<const T*>(d.factors[0]);
-    const T* A1 = static_cast<const T*>(d.factors[1]);
-    const int R0 = d.ranks[0], R1 = d.ranks[1];
-    const int64_t i0 = idx[e];
-    const int64_t i1 = N == 4 ? idx[nnz + e] : 0;
-    constexpr int NPRE = N == 2 ? 1 : N == 3 ? RR : RR * RR;
-    T s = 0;
-    for (int c = 0; c < NPRE; ++c) {
-      T w = 1;
-      if constexpr (N == 3) {
-        if (c >= R0) continue;
-        w = __ldg(A0 + i0 * R0 + c);
-      } else if constexpr (N == 4) {
-        const int r0 = c / RR, r1 = c % RR;
-        if (r0 >= R0 || r1 >= R1) continue;
-        w = __ldg(A0 + i0 * R0 + r0) * __ldg(A1 + i1 * R1 + r1);
-      }
-      const T* blk = sc + c * RR * RR;
+    // one RR x RR block of the core per prefix (r_0, ..., r_{N-3}) of the leading modes,
+    // weighted by the product of their factor entries
+    auto block_sum = [&](const T* blk) -> T {
       T s2 = 0;
 #pragma unroll
       for (int r2 = 0; r2 < RR; ++r2) {
@@ -209,7 +193,33 @@ __global__ void __launch_bounds__(256) k_coo_inner_fixed(const int32_t* __restri
         for (int r3 = 0; r3 < RR; ++r3) inner += blk[r2 * RR + r3] * a[1][r3];
         s2 += a[0][r2] * inner;
       }
-      s += w * s2;
+      return s2;
+    };
+    T s = 0;
+    if constexpr (N == 2) {
+      s = block_sum(sc);
+    } else {
+      const T* A0 = static_cast<const T*>(d.factors[0]);
+      const int R0 = d.ranks[0];
+      const int64_t i0 = idx[e];
+      if constexpr (N == 3) {
+        for (int r0 = 0; r0 < R0; ++r0)
+          s += __ldg(A0 + i0 * R0 + r0) * block_sum(sc + r0 * RR * RR);
+      } else {
+        // mode 1's row in registers too: the RR blocks of one r0 unrolled
+        T a1[RR];
+        const T* A1 = static_cast<const T*>(d.factors[1]);
+        const int R1 = d.ranks[1];
+        const int64_t i1 = idx[nnz + e];
+#pragma unroll
+        for (int r = 0; r < RR; ++r) a1[r] = r < R1 ? __ldg(A1 + i1 * R1 + r) : (T)0;
+        for (int r0 = 0; r0 < R0; ++r0) {
+          T s1 = 0;
+#pragma unroll
+          for (int r1 = 0; r1 < RR; ++r1) s1 += a1[r1] * block_sum(sc + (r0 * RR + r1) * RR * RR);
+          s += __ldg(A0 + i0 * R0 + r0) * s1;
+        }
+      }
     }
     acc += (double)s * (double)vals[e];
   }

@@ -164,6 +164,11 @@ ts_status tall_tn(int m, int k, long s, const T* M, long ldm, const T* Y, long l
                   long ldd, cudaStream_t st);
 // P (m x n; element (i, c) at P[i prs + c pcs]) = Y (m x s, ldy) Om (s x n, ldo), summed
 // over chunks of s through `part` (wide_nn_partial_elems values).
+// K (k x k, row stride ldk) = D D^T, D (k x s, row stride ldd), k <= 32; through `part`
+// (min(304, ceil(s / 1024)) k^2 values).
+template <typename T>
+ts_status gram_wide(int k, long s, const T* D, long ldd, T* K, long ldk, T* part,
+                    size_t part_elems, cudaStream_t st);
 size_t wide_nn_partial_elems(int m, int n, long s);
 template <typename T>
 ts_status wide_nn(int m, int n, long s, const T* Y, long ldy, const T* Om, long ldo, T* P,

@@ -2,9 +2,11 @@
 // of Alg. 5, where the general tiled product wastes most of its tile on the narrow
 // side:
 //   D = M^T Y   (k x s):  M (m x k, k <= 32) tall, Y (m x s) wide.  One pass over Y,
-//               the operand that dominates the bytes; each thread owns 4 columns and
-//               keeps k sums per column in registers, M's rows broadcast from shared
-//               memory.  Each output is one thread's sum in row order.
+//               the operand that dominates the bytes; each thread owns one column and
+//               keeps its k sums in registers, M's rows broadcast from shared memory.
+//               Each output is one thread's sum in row order.
+//   K = D D^T   (k x k):  D (k x s) wide; a block per chunk of columns, partial
+//               products summed in chunk order.
 //   P = Y Om    (m x n):  Y (m x s) wide, Om (s x n, n <= 80) tall.  A 128 x 80 output
 //               tile per block over a chunk of s (split over s across blocks), the
 //               chunks' partial products summed in chunk order by a second kernel.
@@ -14,18 +16,20 @@ namespace ts {
 
 namespace {
 
+// One column of D per thread, 16 rows of Y in flight per thread (enough bytes in flight
+// to stream Y near HBM speed with ~1300 threads per SM).
 template <typename T, int KM>
-__global__ void __launch_bounds__(128) k_tall_tn(int m, int k, long s, const T* __restrict__ M,
+__global__ void __launch_bounds__(256) k_tall_tn(int m, int k, long s, const T* __restrict__ M,
                                                  long ldm, const T* __restrict__ Y, long ldy,
                                                  T* __restrict__ D, long ldd) {
   constexpr int RB = 64;  // rows of M staged per round
+  constexpr int U = 16;   // rows of Y loaded ahead
   __shared__ __align__(16) T sm[RB][KM];
-  const long j0 = (long)blockIdx.x * 512 + threadIdx.x;
-  T acc[4][KM];
+  const long j = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool in = j < s;
+  T acc[KM];
 #pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int a = 0; a < KM; ++a) acc[q][a] = 0;
+  for (int a = 0; a < KM; ++a) acc[a] = 0;
   for (int i0 = 0; i0 < m; i0 += RB) {
     const int ni = min(RB, m - i0);
     __syncthreads();
@@ -34,31 +38,23 @@ __global__ void __launch_bounds__(128) k_tall_tn(int m, int k, long s, const T* 
       sm[r][a] = (r < ni && a < k) ? M[(long)(i0 + r) * ldm + a] : (T)0;
     }
     __syncthreads();
-#pragma unroll 4
-    for (int r = 0; r < ni; ++r) {
-      const T* yr = Y + (long)(i0 + r) * ldy;
-      T y[4];
+    for (int r0 = 0; r0 < ni; r0 += U) {
+      T y[U];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const long j = j0 + q * 128;
-        y[q] = j < s ? __ldcs(yr + j) : (T)0;  // streamed once: evict first
-      }
+      for (int u = 0; u < U; ++u)
+        y[u] = (in && r0 + u < ni) ? __ldcs(Y + (long)(i0 + r0 + u) * ldy + j) : (T)0;
 #pragma unroll
-      for (int a = 0; a < KM; ++a) {
-        const T mv = sm[r][a];
+      for (int u = 0; u < U; ++u) {
+        const int r = min(r0 + u, RB - 1);  // y[u] is 0 beyond ni
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q][a] += mv * y[q];
+        for (int a = 0; a < KM; ++a) acc[a] += sm[r][a] * y[u];
       }
     }
   }
+  if (in)
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const long j = j0 + q * 128;
-    if (j < s)
-#pragma unroll
-      for (int a = 0; a < KM; ++a)
-        if (a < k) D[(long)a * ldd + j] = acc[q][a];
-  }
+    for (int a = 0; a < KM; ++a)
+      if (a < k) D[(long)a * ldd + j] = acc[a];
 }
 
 template <typename T>
@@ -66,12 +62,15 @@ struct WideTile {
   static constexpr int BM = 128, BN = 80, BK = sizeof(T) == 4 ? 32 : 16;
 };
 
-// Block (rt, c): rows [128 rt, 128 rt + 128) of P over s-chunk c, into part[c].
+// Block (rt, c): rows [128 rt, 128 rt + 128) of P over s-chunk c, into part[c].  The
+// next tile's global loads are issued into registers before the current tile's products
+// (one tile in flight while computing).
 template <typename T>
 __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* __restrict__ Y,
                                                  long ldy, const T* __restrict__ Om, long ldo,
                                                  long chunk, T* __restrict__ part) {
   constexpr int BM = WideTile<T>::BM, BN = WideTile<T>::BN, BK = WideTile<T>::BK;
+  constexpr int NY = BM * BK / 256, NO = BK * BN / 256;
   __shared__ T ys[BK][BM + 1];  // Y tile, transposed (k-major): conflict-free both ways
   __shared__ T os[BK][BN];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads
@@ -83,19 +82,41 @@ __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* 
   for (int u = 0; u < 8; ++u)
 #pragma unroll
     for (int v = 0; v < 5; ++v) acc[u][v] = 0;
-  for (long kk = k0; kk < k1; kk += BK) {
-    // Y tile: BM rows x BK columns, lanes along the row (coalesced)
-    for (int t = threadIdx.x; t < BM * BK; t += blockDim.x) {
+  T yv[NY], ov[NO];
+  auto fetch = [&](long kk) {
+#pragma unroll
+    for (int q = 0; q < NY; ++q) {  // lanes along a row of Y (coalesced)
+      const int t = threadIdx.x + 256 * q;
       const int c = t % BK, r = t / BK;
       const long j = kk + c;
-      ys[c][r] = (r0 + r < m && j < k1) ? __ldcs(Y + (long)(r0 + r) * ldy + j) : (T)0;
+      yv[q] = (r0 + r < m && j < k1) ? __ldcs(Y + (long)(r0 + r) * ldy + j) : (T)0;
     }
-    for (int t = threadIdx.x; t < BK * BN; t += blockDim.x) {
+#pragma unroll
+    for (int q = 0; q < NO; ++q) {
+      const int t = threadIdx.x + 256 * q;
       const int c = t % BN, kr = t / BN;
       const long j = kk + kr;
-      os[kr][c] = (c < n && j < k1) ? Om[j * ldo + c] : (T)0;
+      ov[q] = (c < n && j < k1) ? Om[j * ldo + c] : (T)0;
     }
+  };
+  auto stage = [&]() {
+#pragma unroll
+    for (int q = 0; q < NY; ++q) {
+      const int t = threadIdx.x + 256 * q;
+      ys[t % BK][t / BK] = yv[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NO; ++q) {
+      const int t = threadIdx.x + 256 * q;
+      os[t / BN][t % BN] = ov[q];
+    }
+  };
+  if (k0 < k1) fetch(k0);
+  for (long kk = k0; kk < k1; kk += BK) {
+    __syncthreads();  // the previous tile's products are done
+    stage();
     __syncthreads();
+    if (kk + BK < k1) fetch(kk + BK);
 #pragma unroll 8
     for (int kr = 0; kr < BK; ++kr) {
       T y[8], o[5];
@@ -108,7 +129,6 @@ __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* 
 #pragma unroll
         for (int v = 0; v < 5; ++v) acc[u][v] += y[u] * o[v];
     }
-    __syncthreads();
   }
   T* out = part + (size_t)blockIdx.y * m * n;
 #pragma unroll
@@ -120,6 +140,37 @@ __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* 
         const int c = tx + 16 * v;
         if (c < n) out[(long)r * n + c] = acc[u][v];
       }
+  }
+}
+
+// Block b: the k x k products of D's rows over its chunk of columns, into part[b].
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram_wide(int k, long s, const T* __restrict__ D,
+                                                   long ldd, long chunk, T* __restrict__ part) {
+  __shared__ T ds[32][257];  // padded rows: conflict-free column reads across rows
+  const long c1 = min(s, (long)(blockIdx.x + 1) * chunk);
+  T acc[4] = {0, 0, 0, 0};
+  for (long c0 = (long)blockIdx.x * chunk; c0 < c1; c0 += 256) {
+    const int nc = (int)min(256L, c1 - c0);
+    __syncthreads();
+    for (int a = 0; a < k; ++a)
+      ds[a][threadIdx.x] = threadIdx.x < nc ? D[(long)a * ldd + c0 + threadIdx.x] : (T)0;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = threadIdx.x + 256 * q;
+      if (p < k * k) {
+        const int a = p / k, b = p % k;
+        T v = 0;
+        for (int t = 0; t < nc; ++t) v += ds[a][t] * ds[b][t];
+        acc[q] += v;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int p = threadIdx.x + 256 * q;
+    if (p < k * k) part[(long)blockIdx.x * k * k + p] = acc[q];
   }
 }
 
@@ -143,11 +194,26 @@ template <typename T>
 ts_status tall_tn(int m, int k, long s, const T* M, long ldm, const T* Y, long ldy, T* D,
                   long ldd, cudaStream_t st) {
   if (k < 1 || k > 32) return fail(TS_ERR_INVALID_ARG, "tall_tn: k=%d outside [1, 32]", k);
-  const unsigned grid = (unsigned)((s + 511) / 512);
+  const unsigned grid = (unsigned)((s + 255) / 256);
   if (k <= 16)
-    k_tall_tn<T, 16><<<grid, 128, 0, st>>>(m, k, s, M, ldm, Y, ldy, D, ldd);
+    k_tall_tn<T, 16><<<grid, 256, 0, st>>>(m, k, s, M, ldm, Y, ldy, D, ldd);
   else
-    k_tall_tn<T, 32><<<grid, 128, 0, st>>>(m, k, s, M, ldm, Y, ldy, D, ldd);
+    k_tall_tn<T, 32><<<grid, 256, 0, st>>>(m, k, s, M, ldm, Y, ldy, D, ldd);
+  TS_LAUNCH_CHECK();
+  return TS_OK;
+}
+
+template <typename T>
+ts_status gram_wide(int k, long s, const T* D, long ldd, T* K, long ldk, T* part,
+                    size_t part_elems, cudaStream_t st) {
+  if (k < 1 || k > 32) return fail(TS_ERR_INVALID_ARG, "gram_wide: k=%d outside [1, 32]", k);
+  const int nb = (int)std::min<long>(2 * 152, (s + 1023) / 1024);
+  const long chunk = (s + nb - 1) / nb;
+  if ((size_t)nb * k * k > part_elems)
+    return fail(TS_ERR_WORKSPACE, "gram_wide: partial buffer too small");
+  k_gram_wide<T><<<nb, 256, 0, st>>>(k, s, D, ldd, chunk, part);
+  TS_LAUNCH_CHECK();
+  k_chunk_sum<T><<<1, 256, 0, st>>>(k, k, nb, part, K, ldk, 1);
   TS_LAUNCH_CHECK();
   return TS_OK;
 }
@@ -181,6 +247,10 @@ template ts_status tall_tn<float>(int, int, long, const float*, long, const floa
                                   long, cudaStream_t);
 template ts_status tall_tn<double>(int, int, long, const double*, long, const double*, long,
                                    double*, long, cudaStream_t);
+template ts_status gram_wide<float>(int, long, const float*, long, float*, long, float*, size_t,
+                                    cudaStream_t);
+template ts_status gram_wide<double>(int, long, const double*, long, double*, long, double*,
+                                     size_t, cudaStream_t);
 template ts_status wide_nn<float>(int, int, long, const float*, long, const float*, long, float*,
                                   long, long, float*, size_t, cudaStream_t);
 template ts_status wide_nn<double>(int, int, long, const double*, long, const double*, long,

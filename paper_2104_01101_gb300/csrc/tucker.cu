@@ -457,8 +457,11 @@ static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc,
     else
       TS_TRY(gemm<T>(k, s, m, 1.0, mv<T>(w.Mm, 1, k), mv<T>(Y, s, 1), 0.0, ov<T>(w.D, s, 1), sp,
                      st));
-    TS_TRY(gemm<T>(k, k, s, 1.0, mv<T>(w.D, s, 1), mv<T>(w.D, 1, s), 0.0, ov<T>(w.K, k, 1), sp,
-                   st));
+    if (s >= kTallMinS)
+      TS_TRY(gram_wide<T>(k, s, w.D, s, w.K, k, sp->partial, sp->partial_elems, st));
+    else
+      TS_TRY(gemm<T>(k, k, s, 1.0, mv<T>(w.D, s, 1), mv<T>(w.D, 1, s), 0.0, ov<T>(w.K, k, 1), sp,
+                     st));
     TS_TRY(launch_eig_small<T>(k, R, w.K, w.Q, r, w.CnT, w.Fm, nullptr, fp64, w.flag, st));
     // A = D^T Fm, signed; core written
     return launch_finalize<T>(s, R, w.D, 1, s, k, w.Fm, A_out, w.CnT, r, core, map, st,

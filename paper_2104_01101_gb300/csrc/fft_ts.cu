@@ -200,13 +200,24 @@ __device__ __forceinline__ void factor_spectra_body(const ChainDesc& d, const Ff
     const int R = d.cols[f];
     const int32_t* tab = d.tables[f];
     T* dst = half == 0 ? &a[0].x : &a[0].y;
-    for (int64_t i = threadIdx.x; i < d.rows[f]; i += blockDim.x) {
-      const int32_t e = tab[i];
-      const int bin = entry_bin(e);
-      if (bin >= m) continue;  // caller-supplied table outside [0, m): entry ignored
-      T v = A[i * R + r];
-      if (entry_neg(e)) v = -v;
-      atomicAdd(dst + 2 * (size_t)bin, v);
+    // 8 rows per thread in flight (tall factors are latency-bound otherwise)
+    const int64_t rows = d.rows[f];
+    for (int64_t i0 = threadIdx.x; i0 < rows; i0 += 8 * (int64_t)blockDim.x) {
+      int32_t e[8];
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t i = i0 + (int64_t)u * blockDim.x;
+        e[u] = i < rows ? tab[i] : 0;
+        v[u] = i < rows ? A[i * R + r] : (T)0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (i0 + (int64_t)u * blockDim.x >= rows) break;
+        const int bin = entry_bin(e[u]);
+        if (bin >= m) continue;  // caller-supplied table outside [0, m): entry ignored
+        atomicAdd(dst + 2 * (size_t)bin, entry_neg(e[u]) ? -v[u] : v[u]);
+      }
     }
   }
   __syncthreads();

@@ -259,10 +259,12 @@ template <typename T>
 __global__ void k_ns_init(int r, const T* __restrict__ G, long ldg, T* __restrict__ X,
                           T* __restrict__ twoI) {
   __shared__ double red[32];
-  double mx = 0;
-  for (int i = threadIdx.x; i < r; i += blockDim.x) {
+  double mx = 0;  // a warp per row, lanes along it (coalesced)
+  const int lane = threadIdx.x & 31;
+  for (int i = threadIdx.x >> 5; i < r; i += blockDim.x >> 5) {
     double srow = 0;
-    for (int j = 0; j < r; ++j) srow += fabs((double)G[(long)i * ldg + j]);
+    for (int j = lane; j < r; j += 32) srow += fabs((double)G[(long)i * ldg + j]);
+    for (int o = 16; o > 0; o >>= 1) srow += __shfl_xor_sync(0xffffffffu, srow, o);
     mx = srow > mx ? srow : mx;
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -387,8 +389,11 @@ __global__ void __launch_bounds__(NT) k_eig_small(int n, int R, JacobiShape js,
     V[e] = (i == j) ? (T)1 : (T)0;
   }
   __syncthreads();
-  // stop on squared norms: the FP32 rounding floor of off/tot is ~n^2 eps^2 ~ 1e-12
-  const T tol = sizeof(T) == 4 ? (T)1e-11 : (T)1e-28;
+  // stop on squared norms: off/tot cannot fall much below its rounding floor n^2 eps^2
+  // (~1e-12 in FP32 at n = 8, ~6e-11 at n = 64), so the tolerance follows it for large n
+  const T eps = sizeof(T) == 4 ? (T)1.1920929e-7 : (T)2.220446049250313e-16;
+  const T floor4 = (T)4 * (T)n * (T)n * eps * eps;
+  const T tol = sizeof(T) == 4 ? max((T)1e-11, floor4) : max((T)1e-28, floor4);
   T off, tot;
   for (int sweep = 0; sweep < 24; ++sweep) {
     jacobi_norms<T>(A, n, redT, off, tot);

@@ -302,7 +302,7 @@ ts_status ts_leverage_sketch_det(const ts_tensor* X, int32_t mode, const int32_t
  * accumulation.  COO: ||T||^2 - 2<T, T~> + ||T~||^2 (clamped at 0) without forming
  * T~: ||T||^2 over distinct coordinates (repeated coordinates added first, through a
  * fibre index of the largest mode and a hash table of (fibre, coordinate) keys, both
- * in the scratch, about 40 bytes per nonzero), <T, T~> summed over the stored entries
+ * in the scratch, about 56 bytes per nonzero), <T, T~> summed over the stored entries
  * with T~(i) formed in the data type, ||T~||^2 = <C, C x_1 G_1 ... x_N G_N> with
  * G_n = A^(n)T A^(n) (no orthonormality assumed); FP64 across entries.  The int32 at
  * offset 0 of the scratch is set non-zero if a hash table could not place an entry
@@ -341,7 +341,7 @@ ts_status ts_fitness(const ts_tensor* X, const int32_t* ranks, const void* core,
  * Residuals of COO tensors follow ts_fitness (||T||^2 formed once per call, with its
  * fibre index and hash table in the workspace; TS_ERR_UNSUPPORTED under its limits).
  * tucker_als_workspace_bytes counts the residual's scratch whenever a residual can be
- * formed (for COO input about 40 bytes per nonzero), so one size serves calls with and
+ * formed (for COO input about 56 bytes per nonzero), so one size serves calls with and
  * without residual_out.
  * Errors: TS_ERR_SHAPE if order < 2, any ranks[k] < 1 or ranks[k] >= dims[k]
  * (the theory assumes s > R), m < prod_{k != n} ranks[k] for some n (the sketched

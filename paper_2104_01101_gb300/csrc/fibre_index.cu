@@ -32,7 +32,7 @@ __device__ __forceinline__ unsigned long long fibre_key(const int32_t* __restric
 }
 
 __global__ void k_fib_insert(const int32_t* __restrict__ idx, int64_t nnz, FibreIndex F,
-                             int* flag) {
+                             int32_t* __restrict__ eslot, int* flag) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
        e += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long key = fibre_key(idx, nnz, e, F);
@@ -44,7 +44,8 @@ __global__ void k_fib_insert(const int32_t* __restrict__ idx, int64_t nnz, Fibre
       unsigned long long cur = __ldcg(F.keys + h);
       if (cur == kEmptyKey) cur = atomicCAS(F.keys + h, kEmptyKey, key);
       if (cur == kEmptyKey || cur == key) {
-        atomicAdd(F.cur + h, 1);
+        if (eslot) eslot[e] = (int32_t)h;  // keys only: the slot of every nonzero
+        else atomicAdd(F.cur + h, 1);
         placed = true;
         break;
       }
@@ -204,7 +205,7 @@ ts_status launch_fibre_index_build(const ts_tensor& X, const FibreIndex& F, int*
   const int64_t nnz = X.nnz;
   const int grid = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(nnz, 256), 1), 152 * 16);
   if (nnz > 0) {
-    k_fib_insert<<<grid, 256, 0, st>>>(X.indices, nnz, F, flag);
+    k_fib_insert<<<grid, 256, 0, st>>>(X.indices, nnz, F, nullptr, flag);
     TS_LAUNCH_CHECK();
   }
   const int64_t nb = cap / kScanChunk + (cap % kScanChunk ? 1 : 0);
@@ -222,6 +223,19 @@ ts_status launch_fibre_index_build(const ts_tensor& X, const FibreIndex& F, int*
     else
       k_fib_fill<float><<<grid, 256, 0, st>>>(X.indices, static_cast<const float*>(X.values), nnz,
                                               F, flag);
+    TS_LAUNCH_CHECK();
+  }
+  return TS_OK;
+}
+
+ts_status launch_fibre_keys(const ts_tensor& X, const FibreIndex& F, int32_t* eslot, int* flag,
+                            cudaStream_t st) {
+  const int64_t cap = (int64_t)F.mask + 1;
+  TS_CUDA(cudaMemsetAsync(F.keys, 0xFF, (size_t)cap * sizeof(unsigned long long), st));
+  const int64_t nnz = X.nnz;
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(nnz, 256), 1), 152 * 16);
+  if (nnz > 0) {
+    k_fib_insert<<<grid, 256, 0, st>>>(X.indices, nnz, F, eslot, flag);
     TS_LAUNCH_CHECK();
   }
   return TS_OK;

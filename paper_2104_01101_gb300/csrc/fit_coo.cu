@@ -2,8 +2,8 @@
 // (Sec. 7 fitness f = 1 - residual), without forming T~:
 //   ||T - T~||^2 = ||T||^2 - 2 <T, T~> + ||T~||^2
 //   ||T||^2  over distinct coordinates, repeated ones added first (once per tensor):
-//            the nonzeros are grouped by the fibres of mode nf (fibre index), and
-//            (fibre slot, i_nf) keys a second hash table that sums the repeats
+//            every nonzero finds the hash slot of its mode-nf fibre (the fibre index's
+//            keys), and (fibre slot, i_nf) keys a second hash table that sums the repeats
 //   <T, T~>  = sum over stored entries of v_e T~(i_e) (linear in the entries, so
 //            repeats need no merging); T~(i) = sum_r C(r) prod_n A^(n)(i_n, r_n) with
 //            the core in shared memory and the last mode's factor row in registers
@@ -31,37 +31,24 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
-// Slot of the fibre index that owns entry p: the last h with beg[h] <= p.
-__device__ __forceinline__ int64_t owner_slot(const int32_t* __restrict__ beg, int64_t cap,
-                                              int p) {
-  int64_t lo = 0, hi = cap;  // beg[lo] <= p < beg[hi]
-  while (hi - lo > 1) {
-    const int64_t mid = (lo + hi) >> 1;
-    if (beg[mid] <= p) lo = mid;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// Adds every entry's value into the slot of key (fibre slot, i_nf) of the value table.
+// Adds every nonzero's value into the slot of key (fibre slot, i_nf) of the value table.
 template <typename T>
-__global__ void k_merge_repeats(FibreIndex F, int64_t nnz, int64_t sn,
+__global__ void k_merge_repeats(const int32_t* __restrict__ idx, const T* __restrict__ vals,
+                                int64_t nnz, int nf, int64_t sn,
+                                const int32_t* __restrict__ eslot,
                                 unsigned long long* __restrict__ vkeys, double* __restrict__ vsum,
                                 uint64_t vmask, int* flag) {
-  const T* val = static_cast<const T*>(F.val);
-  const int64_t cap = (int64_t)F.mask + 1;
-  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < nnz;
-       p += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t h = owner_slot(F.beg, cap, (int)p);
-    const unsigned long long key = (unsigned long long)h * (unsigned long long)sn +
-                                   (unsigned long long)(unsigned)F.pos[p];
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long key = (unsigned long long)(unsigned)eslot[e] * (unsigned long long)sn +
+                                   (unsigned long long)(unsigned)idx[(int64_t)nf * nnz + e];
     uint64_t g = mix64(key) & vmask;
     bool placed = false;
     for (uint64_t q = 0; q <= vmask; ++q) {
       unsigned long long cur = __ldcg(vkeys + g);
       if (cur == kEmptyKey) cur = atomicCAS(vkeys + g, kEmptyKey, key);
       if (cur == kEmptyKey || cur == key) {
-        atomicAdd(vsum + g, (double)val[p]);
+        atomicAdd(vsum + g, (double)vals[e]);
         placed = true;
         break;
       }
@@ -299,8 +286,18 @@ bool fit_coo_model_ok(const ts_tensor& X, const int* ranks) {
 
 FitCooWork fit_coo_carve(const ts_tensor& X, const int* ranks, Bump& b) {
   FitCooWork w{};
-  w.F = fibre_index_carve(X, fit_coo_mode(X), b);
+  const int nf = fit_coo_mode(X);
   const int64_t cap = fibre_index_capacity(X.nnz);
+  w.F.order = X.order;
+  w.F.mode = nf;
+  int64_t st = 1;
+  for (int k = X.order - 1; k >= 0; --k) {
+    w.F.stride[k] = k == nf ? 0 : st;
+    if (k != nf) st *= X.dims[k];
+  }
+  w.F.mask = (uint64_t)cap - 1;
+  w.F.keys = b.take<unsigned long long>((size_t)cap);
+  w.eslot = b.take<int32_t>((size_t)(X.nnz > 0 ? X.nnz : 1));
   w.vmask = (uint64_t)cap - 1;
   w.vkeys = b.take<unsigned long long>((size_t)cap);
   w.vsum = b.take<double>((size_t)cap);
@@ -321,7 +318,7 @@ FitCooWork fit_coo_carve(const ts_tensor& X, const int* ranks, Bump& b) {
 
 ts_status launch_fit_coo_norm(const ts_tensor& X, const FitCooWork& w, int* flag,
                               cudaStream_t st) {
-  TS_TRY(launch_fibre_index_build(X, w.F, flag, st));
+  TS_TRY(launch_fibre_keys(X, w.F, w.eslot, flag, st));
   const int64_t cap = (int64_t)w.vmask + 1;
   TS_CUDA(cudaMemsetAsync(w.vkeys, 0xFF, (size_t)cap * sizeof(unsigned long long), st));
   TS_CUDA(cudaMemsetAsync(w.vsum, 0, (size_t)cap * sizeof(double), st));
@@ -330,9 +327,14 @@ ts_status launch_fit_coo_norm(const ts_tensor& X, const FitCooWork& w, int* flag
   const int64_t sn = X.dims[w.F.mode];
   if (X.nnz > 0) {
     if (X.dtype == TS_F64)
-      k_merge_repeats<double><<<grid, 256, 0, st>>>(w.F, X.nnz, sn, w.vkeys, w.vsum, w.vmask, flag);
+      k_merge_repeats<double><<<grid, 256, 0, st>>>(X.indices,
+                                                    static_cast<const double*>(X.values), X.nnz,
+                                                    w.F.mode, sn, w.eslot, w.vkeys, w.vsum,
+                                                    w.vmask, flag);
     else
-      k_merge_repeats<float><<<grid, 256, 0, st>>>(w.F, X.nnz, sn, w.vkeys, w.vsum, w.vmask, flag);
+      k_merge_repeats<float><<<grid, 256, 0, st>>>(X.indices, static_cast<const float*>(X.values),
+                                                   X.nnz, w.F.mode, sn, w.eslot, w.vkeys, w.vsum,
+                                                   w.vmask, flag);
     TS_LAUNCH_CHECK();
   }
   k_sum_squares<<<(int)std::min<int64_t>(ceil_div(cap, 256), 152 * 8), 256, 0, st>>>(w.vsum, cap,

@@ -315,6 +315,9 @@ FibreIndex fibre_index_carve(const ts_tensor& X, int mode, Bump& b);
 // the capacity >= 2 nnz).
 ts_status launch_fibre_index_build(const ts_tensor& X, const FibreIndex& F, int* flag,
                                    cudaStream_t st);
+// The keys only (no counts, ranges or entries): eslot[e] = the slot of nonzero e's fibre.
+ts_status launch_fibre_keys(const ts_tensor& X, const FibreIndex& F, int32_t* eslot, int* flag,
+                            cudaStream_t st);
 
 // ---------------------------------------------------------------- fit_coo.cu
 // Residual of a Tucker model against a COO tensor.  Scratch: the fibre index of the
@@ -322,7 +325,8 @@ ts_status launch_fibre_index_build(const ts_tensor& X, const FibreIndex& F, int*
 // G_n = A^(n)T A^(n) (stride gstride elements), two core-sized buffers and
 // acc[4] (acc[1] = <T, T~>, acc[2] = ||T~||^2, acc[3] = ||T||^2).
 struct FitCooWork {
-  FibreIndex F;
+  FibreIndex F;       // keys of the largest mode's fibres (no ranges or entries)
+  int32_t* eslot;     // nnz: fibre slot of every nonzero
   unsigned long long* vkeys;
   double* vsum;
   uint64_t vmask;

@@ -394,10 +394,14 @@ __global__ void __launch_bounds__(NT) k_eig_small(int n, int R, JacobiShape js,
   const T eps = sizeof(T) == 4 ? (T)1.1920929e-7 : (T)2.220446049250313e-16;
   const T floor4 = (T)4 * (T)n * (T)n * eps * eps;
   const T tol = sizeof(T) == 4 ? max((T)1e-11, floor4) : max((T)1e-28, floor4);
-  T off, tot;
+  T off, tot, prev = (T)-1;
   for (int sweep = 0; sweep < 24; ++sweep) {
     jacobi_norms<T>(A, n, redT, off, tot);
     if (off <= tol * tot || tot == (T)0) break;
+    // a sweep that no longer cuts a small off-norm by 4x has met the rounding floor
+    // (converging sweeps cut it quadratically)
+    if (prev >= (T)0 && off <= (T)1e-6 * tot && off > (T)0.25 * prev) break;
+    prev = off;
     jacobi_sweep<T>(A, V, js, rp, rq, rcT, rsT);
   }
   if constexpr (POLISH64) {

@@ -89,10 +89,12 @@ __device__ void jacobi_sweep(U* A, U* V, const JacobiShape& js, int* rp, int* rq
       A[q * n + l] = s * ap + c * aq;
     }
     sync();
-    for (int e = threadIdx.x; e < npairs * np2; e += nthr) {  // columns p, q and V
-      const int i = e >> js.lg, l = e & (np2 - 1);
+    // columns p, q and V: consecutive threads take consecutive pairs of one row l (the
+    // other order, a column per warp, hits one bank 32 times when n is a multiple of 32)
+    for (int e = threadIdx.x; e < npairs * n; e += nthr) {
+      const int i = e % npairs, l = e / npairs;
       const int p = rp[i];
-      if (p < 0 || l >= n) continue;
+      if (p < 0) continue;
       const int q = rq[i];
       const U c = rc[i], s = rs[i];
       const U ap = A[l * n + p], aq = A[l * n + q];

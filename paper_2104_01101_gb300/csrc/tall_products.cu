@@ -2,8 +2,8 @@
 // of Alg. 5, where the general tiled product wastes most of its tile on the narrow
 // side:
 //   D = M^T Y   (k x s):  M (m x k, k <= 32) tall, Y (m x s) wide.  One pass over Y,
-//               the operand that dominates the bytes; each thread owns one column and
-//               keeps its k sums in registers, M's rows broadcast from shared memory.
+//               the operand that dominates the bytes; each thread owns two columns and
+//               keeps their k sums in registers, M's rows broadcast from shared memory.
 //               Each output is one thread's sum in row order.
 //   K = D D^T   (k x k):  D (k x s) wide; a block per chunk of columns, partial
 //               products summed in chunk order.
@@ -16,8 +16,8 @@ namespace ts {
 
 namespace {
 
-// One column of D per thread, 16 rows of Y in flight per thread (enough bytes in flight
-// to stream Y near HBM speed with ~1300 threads per SM).
+// Two columns of D per thread, 32 values of Y in flight per thread (enough bytes in
+// flight to stream Y near HBM speed in a single wave of blocks).
 template <typename T, int KM>
 __global__ void __launch_bounds__(256) k_tall_tn(int m, int k, long s, const T* __restrict__ M,
                                                  long ldm, const T* __restrict__ Y, long ldy,
@@ -25,11 +25,12 @@ __global__ void __launch_bounds__(256) k_tall_tn(int m, int k, long s, const T* 
   constexpr int RB = 64;  // rows of M staged per round
   constexpr int U = 16;   // rows of Y loaded ahead
   __shared__ __align__(16) T sm[RB][KM];
-  const long j = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool in = j < s;
-  T acc[KM];
+  const long j = (long)blockIdx.x * 2 * blockDim.x + threadIdx.x;  // and j + blockDim.x
+  const long j2 = j + blockDim.x;
+  const bool in = j < s, in2 = j2 < s;
+  T acc[KM], acc2[KM];
 #pragma unroll
-  for (int a = 0; a < KM; ++a) acc[a] = 0;
+  for (int a = 0; a < KM; ++a) acc[a] = acc2[a] = 0;
   for (int i0 = 0; i0 < m; i0 += RB) {
     const int ni = min(RB, m - i0);
     __syncthreads();
@@ -39,22 +40,30 @@ __global__ void __launch_bounds__(256) k_tall_tn(int m, int k, long s, const T* 
     }
     __syncthreads();
     for (int r0 = 0; r0 < ni; r0 += U) {
-      T y[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        y[u] = (in && r0 + u < ni) ? __ldcs(Y + (long)(i0 + r0 + u) * ldy + j) : (T)0;
+      T y[U], y2[U];
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const int r = min(r0 + u, RB - 1);  // y[u] is 0 beyond ni
+        const T* row = Y + (long)(i0 + r0 + u) * ldy;
+        y[u] = (in && r0 + u < ni) ? __ldcs(row + j) : (T)0;
+        y2[u] = (in2 && r0 + u < ni) ? __ldcs(row + j2) : (T)0;
+      }
 #pragma unroll
-        for (int a = 0; a < KM; ++a) acc[a] += sm[r][a] * y[u];
+      for (int u = 0; u < U; ++u) {
+        const int r = r0 + u;  // < RB; y[u] = y2[u] = 0 beyond ni
+#pragma unroll
+        for (int a = 0; a < KM; ++a) {
+          acc[a] += sm[r][a] * y[u];
+          acc2[a] += sm[r][a] * y2[u];
+        }
       }
     }
   }
-  if (in)
 #pragma unroll
-    for (int a = 0; a < KM; ++a)
-      if (a < k) D[(long)a * ldd + j] = acc[a];
+  for (int a = 0; a < KM; ++a)
+    if (a < k) {
+      if (in) D[(long)a * ldd + j] = acc[a];
+      if (in2) D[(long)a * ldd + j2] = acc2[a];
+    }
 }
 
 template <typename T>
@@ -71,7 +80,7 @@ __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* 
                                                  long chunk, T* __restrict__ part) {
   constexpr int BM = WideTile<T>::BM, BN = WideTile<T>::BN, BK = WideTile<T>::BK;
   constexpr int NY = BM * BK / 256, NO = BK * BN / 256;
-  __shared__ T ys[BK][BM + 1];  // Y tile, transposed (k-major): conflict-free both ways
+  __shared__ __align__(16) T ys[BK][BM + 4];  // Y tile, transposed (k-major), 16-byte rows
   __shared__ T os[BK][BN];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;  // 16 x 16 threads
   const int r0 = blockIdx.x * BM;
@@ -121,7 +130,7 @@ __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* 
     for (int kr = 0; kr < BK; ++kr) {
       T y[8], o[5];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) y[u] = ys[kr][ty + 16 * u];
+      for (int u = 0; u < 8; ++u) y[u] = ys[kr][8 * ty + u];  // two 16-byte loads
 #pragma unroll
       for (int v = 0; v < 5; ++v) o[v] = os[kr][tx + 16 * v];
 #pragma unroll
@@ -133,7 +142,7 @@ __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* 
   T* out = part + (size_t)blockIdx.y * m * n;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
-    const int r = r0 + ty + 16 * u;
+    const int r = r0 + 8 * ty + u;
     if (r < m)
 #pragma unroll
       for (int v = 0; v < 5; ++v) {
@@ -194,7 +203,7 @@ template <typename T>
 ts_status tall_tn(int m, int k, long s, const T* M, long ldm, const T* Y, long ldy, T* D,
                   long ldd, cudaStream_t st) {
   if (k < 1 || k > 32) return fail(TS_ERR_INVALID_ARG, "tall_tn: k=%d outside [1, 32]", k);
-  const unsigned grid = (unsigned)((s + 255) / 256);
+  const unsigned grid = (unsigned)((s + 511) / 512);
   if (k <= 16)
     k_tall_tn<T, 16><<<grid, 256, 0, st>>>(m, k, s, M, ldm, Y, ldy, D, ldd);
   else

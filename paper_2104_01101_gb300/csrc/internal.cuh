@@ -158,18 +158,18 @@ ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
 constexpr int kGemmCounters = 4096;
 // tall_products.cu: products with a huge dimension s (used from kTallMinS on).
 constexpr long kTallMinS = 16384;
-// D (k x s, row stride ldd) = M^T Y, M (m x k, row stride ldm, k <= 32), Y (m x s, ldy).
+// D (k x s, row stride ldd) = M^T Y, M (m x k, row stride ldm, k <= 32), Y (m x s, ldy);
+// the rows may be split over blocks, their partials (in `part`) summed in order.
 template <typename T>
 ts_status tall_tn(int m, int k, long s, const T* M, long ldm, const T* Y, long ldy, T* D,
-                  long ldd, cudaStream_t st);
-// P (m x n; element (i, c) at P[i prs + c pcs]) = Y (m x s, ldy) Om (s x n, ldo), summed
-// over chunks of s through `part` (wide_nn_partial_elems values).
+                  long ldd, T* part, size_t part_elems, cudaStream_t st);
 // K (k x k, row stride ldk) = D D^T, D (k x s, row stride ldd), k <= 32; through `part`
 // (min(304, ceil(s / 1024)) k^2 values).
 template <typename T>
 ts_status gram_wide(int k, long s, const T* D, long ldd, T* K, long ldk, T* part,
                     size_t part_elems, cudaStream_t st);
-size_t wide_nn_partial_elems(int m, int n, long s);
+// P (m x n; element (i, c) at P[i prs + c pcs]) = Y (m x s, ldy) Om (s x n, ldo), summed
+// over chunks of s through `part` (chunks x m x min(n, 80) values).
 template <typename T>
 ts_status wide_nn(int m, int n, long s, const T* Y, long ldy, const T* Om, long ldo, T* P,
                   long prs, long pcs, T* part, size_t part_elems, cudaStream_t st);

@@ -21,7 +21,14 @@ namespace {
 template <typename T, int KM>
 __global__ void __launch_bounds__(256) k_tall_tn(int m, int k, long s, const T* __restrict__ M,
                                                  long ldm, const T* __restrict__ Y, long ldy,
-                                                 T* __restrict__ D, long ldd) {
+                                                 T* __restrict__ D, long ldd, int rows_per) {
+  // rows [rows_per * blockIdx.y, +rows_per) of M and Y; with gridDim.y > 1 the block
+  // writes its partial product to D + blockIdx.y * k * ldd (summed in order afterwards)
+  const int ib = blockIdx.y * rows_per;
+  M += (long)ib * ldm;
+  Y += (long)ib * ldy;
+  m = min(rows_per, m - ib);
+  D += (long)blockIdx.y * k * ldd;
   constexpr int RB = 64;  // rows of M staged per round
   constexpr int U = 16;   // rows of Y loaded ahead
   __shared__ __align__(16) T sm[RB][KM];
@@ -201,14 +208,37 @@ __global__ void k_chunk_sum(int m, int n, int nsplit, const T* __restrict__ part
 
 template <typename T>
 ts_status tall_tn(int m, int k, long s, const T* M, long ldm, const T* Y, long ldy, T* D,
-                  long ldd, cudaStream_t st) {
+                  long ldd, T* part, size_t part_elems, cudaStream_t st) {
   if (k < 1 || k > 32) return fail(TS_ERR_INVALID_ARG, "tall_tn: k=%d outside [1, 32]", k);
-  const unsigned grid = (unsigned)((s + 511) / 512);
+  const int tiles = (int)((s + 511) / 512);
+  // rows split so that the blocks fill ~8 waves (a partial last wave then costs little)
+  static int slots[2] = {0, 0};
+  int& sl = slots[sizeof(T) == 8];
+  if (sl == 0) {
+    int dev = 0, nsm = 0, b = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tall_tn<T, 16>, 256, 0);
+    sl = std::max(1, nsm * std::max(1, b));
+  }
+  int ns = (8 * sl + tiles / 2) / tiles;
+  ns = std::max(1, std::min(ns, std::min(32, m / 256)));
+  while (ns > 1 && (size_t)ns * k * s > part_elems) --ns;
+  const int rows_per = ceil_div(m, ns);
+  ns = ceil_div(m, rows_per);
+  T* out = ns > 1 ? part : D;
+  const long ldo = ns > 1 ? s : ldd;
+  const dim3 grid((unsigned)tiles, (unsigned)ns);
   if (k <= 16)
-    k_tall_tn<T, 16><<<grid, 256, 0, st>>>(m, k, s, M, ldm, Y, ldy, D, ldd);
+    k_tall_tn<T, 16><<<grid, 256, 0, st>>>(m, k, s, M, ldm, Y, ldy, out, ldo, rows_per);
   else
-    k_tall_tn<T, 32><<<grid, 256, 0, st>>>(m, k, s, M, ldm, Y, ldy, D, ldd);
+    k_tall_tn<T, 32><<<grid, 256, 0, st>>>(m, k, s, M, ldm, Y, ldy, out, ldo, rows_per);
   TS_LAUNCH_CHECK();
+  if (ns > 1) {
+    const int blocks = std::max(1, std::min(ceil_div((long)k * s, 256), 2048));
+    k_chunk_sum<T><<<blocks, 256, 0, st>>>(k, (int)s, ns, part, D, ldd, 1);
+    TS_LAUNCH_CHECK();
+  }
   return TS_OK;
 }
 
@@ -227,17 +257,28 @@ ts_status gram_wide(int k, long s, const T* D, long ldd, T* K, long ldk, T* part
   return TS_OK;
 }
 
-size_t wide_nn_partial_elems(int m, int n, long s) {
+// Chunks of s per row tile: as many as fill one wave of resident blocks (a partial
+// second wave would cost a whole block time), at least 4096 columns each.
+template <typename T>
+static int wide_nn_splits(int m, long s) {
+  static int per_sm[2] = {0, 0};
+  int& b = per_sm[sizeof(T) == 8];
+  if (b == 0) {
+    int dev = 0, nsm = 0, blocks = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_wide_nn<T>, 256, 0);
+    b = std::max(1, nsm * std::max(1, blocks));
+  }
   const int rt = ceil_div(m, 128);
-  const int nsplit = std::max(1, std::min(ceil_div(2 * 152, rt), ceil_div(s, 4096)));
-  return (size_t)nsplit * m * std::min(n, 80);
+  return std::max(1, std::min(b / rt, ceil_div(s, 4096)));
 }
 
 template <typename T>
 ts_status wide_nn(int m, int n, long s, const T* Y, long ldy, const T* Om, long ldo, T* P,
                   long prs, long pcs, T* part, size_t part_elems, cudaStream_t st) {
+  const int nsplit = wide_nn_splits<T>(m, s);
   const int rt = ceil_div(m, 128);
-  const int nsplit = std::max(1, std::min(ceil_div(2 * 152, rt), ceil_div(s, 4096)));
   const long chunk = ((s + nsplit - 1) / nsplit + 31) / 32 * 32;
   for (int c0 = 0; c0 < n; c0 += 80) {
     const int nc = std::min(80, n - c0);
@@ -253,9 +294,9 @@ ts_status wide_nn(int m, int n, long s, const T* Y, long ldy, const T* Om, long 
 }
 
 template ts_status tall_tn<float>(int, int, long, const float*, long, const float*, long, float*,
-                                  long, cudaStream_t);
+                                  long, float*, size_t, cudaStream_t);
 template ts_status tall_tn<double>(int, int, long, const double*, long, const double*, long,
-                                   double*, long, cudaStream_t);
+                                   double*, long, double*, size_t, cudaStream_t);
 template ts_status gram_wide<float>(int, long, const float*, long, float*, long, float*, size_t,
                                     cudaStream_t);
 template ts_status gram_wide<double>(int, long, const double*, long, double*, long, double*,

@@ -453,7 +453,7 @@ static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc,
     // M = Z E (m x k);  D = M^T Y (k x s);  K = D D^T (k x k)
     TS_TRY(gemm<T>(m, k, r, 1.0, Zm, mv<T>(w.E, k, 1), 0.0, ov<T>(w.Mm, k, 1), sp, st));
     if (s >= kTallMinS)
-      TS_TRY(tall_tn<T>(m, k, s, w.Mm, k, Y, s, w.D, s, st));
+      TS_TRY(tall_tn<T>(m, k, s, w.Mm, k, Y, s, w.D, s, sp->partial, sp->partial_elems, st));
     else
       TS_TRY(gemm<T>(k, s, m, 1.0, mv<T>(w.Mm, 1, k), mv<T>(Y, s, 1), 0.0, ov<T>(w.D, s, 1), sp,
                      st));

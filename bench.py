@@ -441,11 +441,18 @@ def main():
                     help="skip the batched-form measurement (256 small tensors)")
     ap.add_argument("--no-sparse", action="store_true",
                     help="skip the full-size sparse 4-way measurement (1e8 nonzeros)")
+    ap.add_argument("--sparse-only", action="store_true",
+                    help="run only the sparse 4-way measurement and print its JSON object "
+                         "(for profiling that workload alone)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.sparse_only:
+        import torch
+        print(json.dumps(time_sparse(args, torch.device("cuda:0"))), flush=True)
         return
     if world > 1:
         import torch

@@ -253,34 +253,30 @@ __global__ void __launch_bounds__(NT) k_qr_only(int r, int k, const T* __restric
 }
 
 // Newton-Schulz for G^{-1}: X0 = I / beta with beta the Gershgorin bound of lambda_max
-// (max absolute row sum), so that ||I - G X0|| < 1 for SPD G.  Writes X0 into X and
-// 2I into twoI (the additive term of each iteration X <- X (2I - G X)).
+// (max absolute row sum), so that ||I - G X0|| < 1 for SPD G.  First kernel: a warp per
+// row, the row sums' maximum into *beta_bits (FP64 bits of a non-negative value: integer
+// order is value order); second: X0 into X and 2I into twoI (the additive term of each
+// iteration X <- X (2I - G X)).
 template <typename T>
-__global__ void k_ns_init(int r, const T* __restrict__ G, long ldg, T* __restrict__ X,
-                          T* __restrict__ twoI) {
-  __shared__ double red[32];
-  double mx = 0;  // a warp per row, lanes along it (coalesced)
+__global__ void k_ns_rowmax(int r, const T* __restrict__ G, long ldg,
+                            unsigned long long* beta_bits) {
   const int lane = threadIdx.x & 31;
-  for (int i = threadIdx.x >> 5; i < r; i += blockDim.x >> 5) {
-    double srow = 0;
-    for (int j = lane; j < r; j += 32) srow += fabs((double)G[(long)i * ldg + j]);
-    for (int o = 16; o > 0; o >>= 1) srow += __shfl_xor_sync(0xffffffffu, srow, o);
-    mx = srow > mx ? srow : mx;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const double v = __shfl_xor_sync(0xffffffffu, mx, o);
-    mx = v > mx ? v : mx;
-  }
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double m = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = red[w] > m ? red[w] : m;
-    red[0] = m > 0 ? m : 1.0;
-  }
-  __syncthreads();
-  const T inv = (T)(1.0 / red[0]);
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (i >= r) return;
+  double srow = 0;
+  for (int j = lane; j < r; j += 32) srow += fabs((double)G[(long)i * ldg + j]);
+  for (int o = 16; o > 0; o >>= 1) srow += __shfl_xor_sync(0xffffffffu, srow, o);
+  if (lane == 0) atomicMax(beta_bits, (unsigned long long)__double_as_longlong(srow));
+}
+
+template <typename T>
+__global__ void k_ns_init(int r, const unsigned long long* __restrict__ beta_bits,
+                          T* __restrict__ X, T* __restrict__ twoI) {
+  const double beta = __longlong_as_double((long long)*beta_bits);
+  const T inv = (T)(1.0 / (beta > 0 ? beta : 1.0));
+  const long rr = (long)r * r;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < rr;
+       e += (long)gridDim.x * blockDim.x) {
     const bool diag = (e / r) == (e % r);
     X[e] = diag ? inv : (T)0;
     twoI[e] = diag ? (T)2 : (T)0;
@@ -316,9 +312,15 @@ size_t qr_only_smem_bytes(int r, int k, bool qr64, size_t tsize) {
 template <typename T>
 ts_status newton_schulz_inverse(int r, const T* G, long ldg, T* X, T* S1, T* S2, int iters,
                                 const GemmSplit<T>* split, cudaStream_t st) {
-  k_ns_init<T><<<1, 1024, 0, st>>>(r, G, ldg, X, S2);
-  TS_LAUNCH_CHECK();
   const long rr = (long)r * r;
+  // beta's bits live in S1 until the first iteration overwrites it
+  unsigned long long* beta_bits = reinterpret_cast<unsigned long long*>(S1);
+  TS_CUDA(cudaMemsetAsync(beta_bits, 0, sizeof(unsigned long long), st));
+  k_ns_rowmax<T><<<ceil_div(r, 8), 256, 0, st>>>(r, G, ldg, beta_bits);
+  TS_LAUNCH_CHECK();
+  k_ns_init<T><<<ceil_div(rr, 256) > 1024 ? 1024 : ceil_div(rr, 256), 256, 0, st>>>(r, beta_bits,
+                                                                                     X, S2);
+  TS_LAUNCH_CHECK();
   for (int it = 0; it < iters; ++it) {
     // S1 = 2I - G X
     k_copy<T><<<ceil_div(rr, 256) > 1024 ? 1024 : ceil_div(rr, 256), 256, 0, st>>>(rr, S2, S1);

@@ -33,7 +33,7 @@ def countsketch_matrix(bins: np.ndarray, signs: np.ndarray, m: int) -> np.ndarra
     n = bins.shape[0]
     Omega = np.zeros((m, n))
     Omega[bins, np.arange(n)] = 1.0
-    return Omega @ np.diag(signs)
+    return Omega * np.asarray(signs, dtype=np.float64)[None, :]  # Omega D, D diagonal
 
 
 def ts_hash(tables, m: int):

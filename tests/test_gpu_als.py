@@ -76,6 +76,20 @@ def test_tall_mode_matches_oracle(ts, solve):
         assert np.abs(fac[n].cpu().numpy() - f_o[n]).max() < 1e-9
 
 
+def test_wide_mode_many_sweeps_matches_oracle(ts):
+    # s = 20000 in mode 0 with 6 sweeps of k = 14 (oversampling 10): Y_0 Omega for all
+    # sweeps (84 columns) takes the split product over s in two column groups of <= 80
+    dims, ranks, m, sweeps, seed = (20000, 20, 20), (4, 4, 4), 256, 6, 2
+    T, _, _ = synth.dense_tucker(dims, ranks, 1e-2, seed=12)
+    core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, sweeps,
+                                            seed=seed, oversample=10)
+    c_o, f_o, _ = tucker.sketch_tucker_als(T, ranks, m, sweeps, seed=seed, oversample=10)
+    r_o = tucker.residual(T, c_o, f_o)
+    assert abs(float(res[0]) - r_o) <= 1e-9 * r_o
+    for n in range(3):
+        assert np.abs(proj(fac[n].cpu().numpy()) - proj(f_o[n])).max() < 1e-9
+
+
 @pytest.mark.parametrize("kind", ["ts", "lev"])
 def test_exact_recovery_noiseless(ts, kind):
     T, _, _ = synth.dense_tucker((40, 40, 40), (5, 5, 5), 0.0, seed=2)

@@ -206,21 +206,29 @@ __global__ void k_chunk_sum(int m, int n, int nsplit, const T* __restrict__ part
 
 }  // namespace
 
+// Resident blocks of a kernel on the current device (cached per device; racing first
+// calls compute the same value).
+static int resident_blocks(const void* kernel, int threads, int* cache) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 16) dev = 0;
+  if (cache[dev] == 0) {
+    int nsm = 0, b = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, 0);
+    cache[dev] = std::max(1, nsm * std::max(1, b));
+  }
+  return cache[dev];
+}
+
 template <typename T>
 ts_status tall_tn(int m, int k, long s, const T* M, long ldm, const T* Y, long ldy, T* D,
                   long ldd, T* part, size_t part_elems, cudaStream_t st) {
   if (k < 1 || k > 32) return fail(TS_ERR_INVALID_ARG, "tall_tn: k=%d outside [1, 32]", k);
   const int tiles = (int)((s + 511) / 512);
   // rows split so that the blocks fill ~8 waves (a partial last wave then costs little)
-  static int slots[2] = {0, 0};
-  int& sl = slots[sizeof(T) == 8];
-  if (sl == 0) {
-    int dev = 0, nsm = 0, b = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_tall_tn<T, 16>, 256, 0);
-    sl = std::max(1, nsm * std::max(1, b));
-  }
+  static int cache[16] = {};
+  const int sl = resident_blocks((const void*)k_tall_tn<T, 16>, 256, cache);
   int ns = (8 * sl + tiles / 2) / tiles;
   ns = std::max(1, std::min(ns, std::min(32, m / 256)));
   while (ns > 1 && (size_t)ns * k * s > part_elems) --ns;
@@ -261,15 +269,8 @@ ts_status gram_wide(int k, long s, const T* D, long ldd, T* K, long ldk, T* part
 // second wave would cost a whole block time), at least 4096 columns each.
 template <typename T>
 static int wide_nn_splits(int m, long s) {
-  static int per_sm[2] = {0, 0};
-  int& b = per_sm[sizeof(T) == 8];
-  if (b == 0) {
-    int dev = 0, nsm = 0, blocks = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_wide_nn<T>, 256, 0);
-    b = std::max(1, nsm * std::max(1, blocks));
-  }
+  static int cache[16] = {};
+  const int b = resident_blocks((const void*)k_wide_nn<T>, 256, cache);
   const int rt = ceil_div(m, 128);
   return std::max(1, std::min(b / rt, ceil_div(s, 4096)));
 }

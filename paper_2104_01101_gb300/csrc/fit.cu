@@ -50,27 +50,38 @@ __global__ void __launch_bounds__(256) k_fit_stream_tiled(const T* __restrict__ 
 #pragma unroll
       for (int r = 0; r < RMAX; ++r) a[c][r] = r < Rl ? Alast[(long)(4 * q + c) * Rl + r] : (T)0;
     T pd = 0, pt = 0;
-    for (int64_t row = blockIdx.x; row < nrows; row += gridDim.x) {
-      T qr[RMAX];
+    // 4 rows of T in flight per thread (the read of T is the bound)
+    const int64_t G = gridDim.x;
+    for (int64_t row0 = blockIdx.x; row0 < nrows; row0 += 4 * G) {
+      T xs[4][4];
 #pragma unroll
-      for (int r = 0; r < RMAX; ++r) qr[r] = r < Rl ? __ldg(&Q[row * Rl + r]) : (T)0;
-      const T* xr = X + row * sl + 4 * q;
-      T x[4];
-      if constexpr (sizeof(T) == 4) {
-        const float4 v = *reinterpret_cast<const float4*>(xr);
-        x[0] = v.x; x[1] = v.y; x[2] = v.z; x[3] = v.w;
-      } else {
+      for (int u = 0; u < 4; ++u) {
+        const int64_t row = row0 + u * G;
+        const T* xr = X + (row < nrows ? row : 0) * sl + 4 * q;
+        if constexpr (sizeof(T) == 4) {
+          const float4 v = __ldcs(reinterpret_cast<const float4*>(xr));
+          xs[u][0] = v.x; xs[u][1] = v.y; xs[u][2] = v.z; xs[u][3] = v.w;
+        } else {
 #pragma unroll
-        for (int c = 0; c < 4; ++c) x[c] = xr[c];
+          for (int c = 0; c < 4; ++c) xs[u][c] = xr[c];
+        }
       }
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        T t = 0;
+      for (int u = 0; u < 4; ++u) {
+        const int64_t row = row0 + u * G;
+        if (row >= nrows) break;
+        T qr[RMAX];
 #pragma unroll
-        for (int r = 0; r < RMAX; ++r) t += qr[r] * a[c][r];
-        const T df = x[c] - t;
-        pd += df * df;
-        pt += x[c] * x[c];
+        for (int r = 0; r < RMAX; ++r) qr[r] = r < Rl ? __ldg(&Q[row * Rl + r]) : (T)0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          T t = 0;
+#pragma unroll
+          for (int r = 0; r < RMAX; ++r) t += qr[r] * a[c][r];
+          const T df = xs[u][c] - t;
+          pd += df * df;
+          pt += xs[u][c] * xs[u][c];
+        }
       }
     }
     d2 += (double)pd;

@@ -325,7 +325,7 @@ def test_cp_via_tucker_fp32_collinear_workload(ts):
 
 
 def test_sparse_order4_scaled_workload_matches_oracle(ts):
-    # The sparse 4-way workload scaled down (SURVEY C3 recipe at dims 2000, 1e6 nonzeros):
+    # The sparse 4-way workload scaled down (its recipe at dims 2000, 1e6 nonzeros):
     # Zipf(1.1) coordinates with duplicates, planted rank-(8,8,8,8) Tucker component of the
     # noise's norm, m = 4096, RRF k1 = 64, k2 = 128, re-sketched every sweep.  r = 512 per
     # subproblem: the RSVD solve inverts Z^T Z by Newton-Schulz products.

@@ -7,9 +7,9 @@
 //               Each output is one thread's sum in row order.
 //   K = D D^T   (k x k):  D (k x s) wide; a block per chunk of columns, partial
 //               products summed in chunk order.
-//   P = Y Om    (m x n):  Y (m x s) wide, Om (s x n, n <= 80) tall.  A 128 x 80 output
-//               tile per block over a chunk of s (split over s across blocks), the
-//               chunks' partial products summed in chunk order by a second kernel.
+//   P = Y Om    (m x n):  Y (m x s) wide, Om (s x n) tall.  A 128 x 80 output tile (128 x
+//               16 when n <= 16) per block over a chunk of s (split over s across
+//               blocks), the chunks' partial products summed in chunk order afterwards.
 #include "internal.cuh"
 
 namespace ts {
@@ -73,19 +73,21 @@ __global__ void __launch_bounds__(256) k_tall_tn(int m, int k, long s, const T* 
     }
 }
 
-template <typename T>
+template <typename T, int BN_>
 struct WideTile {
-  static constexpr int BM = 128, BN = 80, BK = sizeof(T) == 4 ? 32 : 16;
+  static constexpr int BM = 128, BN = BN_, BK = sizeof(T) == 4 ? 32 : 16;
+  static constexpr int TN = BN_ / 16;  // columns per thread (strided by 16)
 };
 
 // Block (rt, c): rows [128 rt, 128 rt + 128) of P over s-chunk c, into part[c].  The
 // next tile's global loads are issued into registers before the current tile's products
 // (one tile in flight while computing).
-template <typename T>
+template <typename T, int BNW>
 __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* __restrict__ Y,
                                                  long ldy, const T* __restrict__ Om, long ldo,
                                                  long chunk, T* __restrict__ part) {
-  constexpr int BM = WideTile<T>::BM, BN = WideTile<T>::BN, BK = WideTile<T>::BK;
+  constexpr int BM = WideTile<T, BNW>::BM, BN = WideTile<T, BNW>::BN, BK = WideTile<T, BNW>::BK;
+  constexpr int TN = WideTile<T, BNW>::TN;
   constexpr int NY = BM * BK / 256, NO = BK * BN / 256;
   __shared__ __align__(16) T ys[BK][BM + 4];  // Y tile, transposed (k-major), 16-byte rows
   __shared__ T os[BK][BN];
@@ -93,11 +95,11 @@ __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* 
   const int r0 = blockIdx.x * BM;
   const long k0 = (long)blockIdx.y * chunk;
   const long k1 = min(s, k0 + chunk);
-  T acc[8][5];
+  T acc[8][TN];
 #pragma unroll
   for (int u = 0; u < 8; ++u)
 #pragma unroll
-    for (int v = 0; v < 5; ++v) acc[u][v] = 0;
+    for (int v = 0; v < TN; ++v) acc[u][v] = 0;
   T yv[NY], ov[NO];
   auto fetch = [&](long kk) {
 #pragma unroll
@@ -135,15 +137,15 @@ __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* 
     if (kk + BK < k1) fetch(kk + BK);
 #pragma unroll 8
     for (int kr = 0; kr < BK; ++kr) {
-      T y[8], o[5];
+      T y[8], o[TN];
 #pragma unroll
       for (int u = 0; u < 8; ++u) y[u] = ys[kr][8 * ty + u];  // two 16-byte loads
 #pragma unroll
-      for (int v = 0; v < 5; ++v) o[v] = os[kr][tx + 16 * v];
+      for (int v = 0; v < TN; ++v) o[v] = os[kr][tx + 16 * v];
 #pragma unroll
       for (int u = 0; u < 8; ++u)
 #pragma unroll
-        for (int v = 0; v < 5; ++v) acc[u][v] += y[u] * o[v];
+        for (int v = 0; v < TN; ++v) acc[u][v] += y[u] * o[v];
     }
   }
   T* out = part + (size_t)blockIdx.y * m * n;
@@ -152,7 +154,7 @@ __global__ void __launch_bounds__(256) k_wide_nn(int m, int n, long s, const T* 
     const int r = r0 + 8 * ty + u;
     if (r < m)
 #pragma unroll
-      for (int v = 0; v < 5; ++v) {
+      for (int v = 0; v < TN; ++v) {
         const int c = tx + 16 * v;
         if (c < n) out[(long)r * n + c] = acc[u][v];
       }
@@ -267,10 +269,10 @@ ts_status gram_wide(int k, long s, const T* D, long ldd, T* K, long ldk, T* part
 
 // Chunks of s per row tile: as many as fill one wave of resident blocks (a partial
 // second wave would cost a whole block time), at least 4096 columns each.
-template <typename T>
+template <typename T, int BNW>
 static int wide_nn_splits(int m, long s) {
   static int cache[16] = {};
-  const int b = resident_blocks((const void*)k_wide_nn<T>, 256, cache);
+  const int b = resident_blocks((const void*)k_wide_nn<T, BNW>, 256, cache);
   const int rt = ceil_div(m, 128);
   return std::max(1, std::min(b / rt, ceil_div(s, 4096)));
 }
@@ -278,14 +280,20 @@ static int wide_nn_splits(int m, long s) {
 template <typename T>
 ts_status wide_nn(int m, int n, long s, const T* Y, long ldy, const T* Om, long ldo, T* P,
                   long prs, long pcs, T* part, size_t part_elems, cudaStream_t st) {
-  const int nsplit = wide_nn_splits<T>(m, s);
+  const bool narrow = n <= 16;  // a 16-column tile: the 80-column one would idle 5/6 of it
+  const int nsplit = narrow ? wide_nn_splits<T, 16>(m, s) : wide_nn_splits<T, 80>(m, s);
   const int rt = ceil_div(m, 128);
   const long chunk = ((s + nsplit - 1) / nsplit + 31) / 32 * 32;
   for (int c0 = 0; c0 < n; c0 += 80) {
     const int nc = std::min(80, n - c0);
     if ((size_t)nsplit * m * nc > part_elems)
       return fail(TS_ERR_WORKSPACE, "wide_nn: partial buffer too small");
-    k_wide_nn<T><<<dim3(rt, nsplit), 256, 0, st>>>(m, nc, s, Y, ldy, Om + c0, ldo, chunk, part);
+    if (narrow)
+      k_wide_nn<T, 16><<<dim3(rt, nsplit), 256, 0, st>>>(m, nc, s, Y, ldy, Om + c0, ldo, chunk,
+                                                         part);
+    else
+      k_wide_nn<T, 80><<<dim3(rt, nsplit), 256, 0, st>>>(m, nc, s, Y, ldy, Om + c0, ldo, chunk,
+                                                         part);
     TS_LAUNCH_CHECK();
     const int blocks = std::max(1, std::min(ceil_div((long)m * nc, 256), 2048));
     k_chunk_sum<T><<<blocks, 256, 0, st>>>(m, nc, nsplit, part, P + c0 * pcs, prs, pcs);

@@ -334,9 +334,10 @@ ts_status launch_leverage(const ts_tensor& X, int mode, const int* ranks, const 
     F = *fib;
     TS_CUDA(cudaMemsetAsync(Y, 0, (size_t)m * X.dims[mode] * sizeof(T), st));
   }
-  k_lev_gather<T><<<m, 128, 0, st>>>(d, m, ncols, coo ? nullptr : static_cast<const T*>(X.values),
-                                     samples, prob, Z, Y, det ? 1 : 0,
-                                     det ? (m < C ? (long)m : C) : (long)m, F, coo ? 1 : 0);
+  // COO: 512 threads per sampled fibre (the heavy fibres of skewed data hold 10^4+ nonzeros)
+  k_lev_gather<T><<<m, coo ? 512 : 128, 0, st>>>(
+      d, m, ncols, coo ? nullptr : static_cast<const T*>(X.values), samples, prob, Z, Y,
+      det ? 1 : 0, det ? (m < C ? (long)m : C) : (long)m, F, coo ? 1 : 0);
   TS_LAUNCH_CHECK();
   return TS_OK;
 }

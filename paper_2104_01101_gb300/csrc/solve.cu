@@ -374,6 +374,8 @@ __global__ void __launch_bounds__(NT) k_eig_small(int n, int R, JacobiShape js,
                                                   const T* __restrict__ Q, int r,
                                                   T* __restrict__ CnT, T* __restrict__ Fm,
                                                   T* __restrict__ Uout, int* flag) {
+  pdl_trigger();
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int rp[kMaxEig / 2 + 1], rq[kMaxEig / 2 + 1];
   __shared__ T rcT[kMaxEig / 2 + 1], rsT[kMaxEig / 2 + 1];
@@ -558,6 +560,8 @@ __global__ void __launch_bounds__(256) k_finalize(int s, int R, const T* __restr
                                                   long cs, int kdim, const T* __restrict__ Fm,
                                                   T* __restrict__ A_out, T* __restrict__ CnT,
                                                   int r, T* __restrict__ core, CoreMap map) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ T bv[256];
   __shared__ int bi[256];
   const int c = blockIdx.x;
@@ -578,6 +582,8 @@ __global__ void __launch_bounds__(256) k_finalize_scan(int s, int R, const T* __
                                                        long rs, long cs, int kdim,
                                                        const T* __restrict__ Fm, int chunk,
                                                        T* __restrict__ pv, int* __restrict__ pi) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ T bv[256];
   __shared__ int bi[256];
   const int c = blockIdx.y, b = blockIdx.x;
@@ -603,6 +609,8 @@ __global__ void __launch_bounds__(256) k_finalize_write(int s, int R, const T* _
                                                         const int* __restrict__ pi,
                                                         T* __restrict__ A_out, T* __restrict__ CnT,
                                                         int r, T* __restrict__ core, CoreMap map) {
+  pdl_trigger();
+  pdl_wait();
   __shared__ T bv[256];
   __shared__ int bi[256];
   const int c = blockIdx.y, b = blockIdx.x, nb = gridDim.x;
@@ -667,11 +675,13 @@ ts_status launch_eig_small(int n, int R, const T* K, const T* Q, int r, T* CnT, 
   if (polish64 && sizeof(T) == 4) {
     const size_t smem = nn * 2 * sizeof(T) + 8 + nn * 3 * sizeof(double);
     TS_TRY(ensure_dynamic_smem((const void*)k_eig_small<T, true>, smem));
-    k_eig_small<T, true><<<1, threads, smem, st>>>(n, R, js, K, Q, r, CnT, Fm, Uout, flag);
+    TS_TRY(launch_pdl(k_eig_small<T, true>, dim3(1), dim3(threads), smem, st, n, R, js, K, Q, r,
+                      CnT, Fm, Uout, flag));
   } else {
     const size_t smem = nn * 2 * sizeof(T);
     TS_TRY(ensure_dynamic_smem((const void*)k_eig_small<T, false>, smem));
-    k_eig_small<T, false><<<1, threads, smem, st>>>(n, R, js, K, Q, r, CnT, Fm, Uout, flag);
+    TS_TRY(launch_pdl(k_eig_small<T, false>, dim3(1), dim3(threads), smem, st, n, R, js, K, Q, r,
+                      CnT, Fm, Uout, flag));
   }
   TS_LAUNCH_CHECK();
   return TS_OK;
@@ -689,16 +699,13 @@ ts_status launch_finalize(int s, int R, const T* M, long rs, long cs, int kdim, 
     T* pv = static_cast<T*>(scratch);
     int* pi = reinterpret_cast<int*>(static_cast<char*>(scratch) +
                                      align_up((size_t)nb * R * sizeof(T), 256));
-    k_finalize_scan<T><<<dim3(nb, R), 256, 0, st>>>(s, R, M, rs, cs, kdim, Fm, chunk, pv, pi);
-    TS_LAUNCH_CHECK();
-    k_finalize_write<T><<<dim3(nb, R), 256, 0, st>>>(s, R, M, rs, cs, kdim, Fm, chunk, pv, pi,
-                                                     A_out, CnT, r, core, map);
-    TS_LAUNCH_CHECK();
-    return TS_OK;
+    TS_TRY(launch_pdl(k_finalize_scan<T>, dim3(nb, R), dim3(256), 0, st, s, R, M, rs, cs, kdim,
+                      Fm, chunk, pv, pi));
+    return launch_pdl(k_finalize_write<T>, dim3(nb, R), dim3(256), 0, st, s, R, M, rs, cs, kdim,
+                      Fm, chunk, (const T*)pv, (const int*)pi, A_out, CnT, r, core, map);
   }
-  k_finalize<T><<<R, 256, 0, st>>>(s, R, M, rs, cs, kdim, Fm, A_out, CnT, r, core, map);
-  TS_LAUNCH_CHECK();
-  return TS_OK;
+  return launch_pdl(k_finalize<T>, dim3(R), dim3(256), 0, st, s, R, M, rs, cs, kdim, Fm, A_out,
+                    CnT, r, core, map);
 }
 
 #define TS_INST(T)                                                                               \

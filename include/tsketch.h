@@ -75,7 +75,9 @@ enum {
  * format TS_COO:   `indices` holds N arrays of nnz int32 coordinates, mode after
  *                  mode (structure of arrays: indices[k*nnz + e]); `values` holds
  *                  nnz values.  Repeated coordinates add (every operation here is
- *                  linear in the entries).
+ *                  linear in the entries).  Coordinates must lie in [0, dims[k]): the
+ *                  kernels skip entries outside rather than read out of bounds, and
+ *                  results for such input are unspecified.
  * dtype: element type of `values` (TS_F32 or TS_F64). */
 typedef struct {
   int32_t order;

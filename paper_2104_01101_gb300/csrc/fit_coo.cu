@@ -76,6 +76,17 @@ struct CooModel {
   int npre;  // prod_{k < order-1} ranks[k]
 };
 
+// Entries with a coordinate outside [0, dims[k]) are skipped (as in the input sketch).
+__device__ __forceinline__ bool entry_in_range(const int32_t* __restrict__ idx, int64_t nnz,
+                                               int64_t e, const CooModel& d) {
+  bool ok = true;
+  for (int k = 0; k < d.order; ++k) {
+    const int32_t i = idx[(int64_t)k * nnz + e];
+    ok &= (i >= 0) & (i < d.dims[k]);
+  }
+  return ok;
+}
+
 // <T, T~>: one thread per stored entry.  RL >= ranks[last] (the last factor row in
 // registers, zero-padded; the core rows in shared memory are padded to match).
 template <typename T, int RL>
@@ -94,6 +105,7 @@ __global__ void __launch_bounds__(256) k_coo_inner(const int32_t* __restrict__ i
   double acc = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
        e += (int64_t)gridDim.x * blockDim.x) {
+    if (!entry_in_range(idx, nnz, e, d)) continue;
     T al[RL];
     const int64_t il = idx[(int64_t)L * nnz + e];
 #pragma unroll
@@ -159,6 +171,7 @@ __global__ void __launch_bounds__(256) k_coo_inner_fixed(const int32_t* __restri
   double acc = 0;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
        e += (int64_t)gridDim.x * blockDim.x) {
+    if (!entry_in_range(idx, nnz, e, d)) continue;
     T a[2][RR];  // rows of modes N-2 and N-1
 #pragma unroll
     for (int q = 0; q < 2; ++q) {

@@ -137,9 +137,10 @@ template <typename T, int BM, int BN>
 __global__ void __launch_bounds__(NT) k_gemm(int M, int N, int K, int kchunk, MatView<T> A,
                                              MatView<T> B1, int n1, MatView<T> B2, int n2,
                                              MatView<T> B3, T alpha, T beta, OutView<T> C,
-                                             T* __restrict__ partial) {
+                                             T* __restrict__ partial, const int* skip) {
   pdl_trigger();
   pdl_wait();
+  if (skip && *skip) return;
   gemm_tile<T, BM, BN>(M, N, K, kchunk, A, B1, n1, B2, n2, B3, alpha, beta, C, partial,
                        blockIdx.x, blockIdx.y, blockIdx.z);
 }
@@ -167,9 +168,10 @@ ts_status launch_gemm_batched(const GemmJob<T>* jobs, int count, int maxM, int m
 
 template <typename T>
 __global__ void k_gemm_reduce(int M, int N, int splits, const T* __restrict__ partial, T alpha,
-                              T beta, OutView<T> C) {
+                              T beta, OutView<T> C, const int* skip) {
   pdl_trigger();
   pdl_wait();
+  if (skip && *skip) return;
   const size_t MN = (size_t)M * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < MN;
        e += (size_t)gridDim.x * blockDim.x) {
@@ -207,18 +209,19 @@ ts_status gemm3(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B1, 
   splits = ceil_div(K > 0 ? K : 1, kchunk);
   dim3 grid(ceil_div(N, bm), ceil_div(M, bm), splits);
   T* part = splits > 1 ? split->partial : nullptr;
+  const int* skip = split ? split->skip : nullptr;
   if (small)
     TS_TRY(launch_pdl(k_gemm<T, 32, 32>, grid, dim3(NT), 0, st, M, N, K, kchunk, A, B1, n1, B2,
-                      n2, B3, (T)alpha, (T)beta, C, part));
+                      n2, B3, (T)alpha, (T)beta, C, part, skip));
   else
     TS_TRY(launch_pdl(k_gemm<T, 64, 64>, grid, dim3(NT), 0, st, M, N, K, kchunk, A, B1, n1, B2,
-                      n2, B3, (T)alpha, (T)beta, C, part));
+                      n2, B3, (T)alpha, (T)beta, C, part, skip));
   if (splits > 1) {
     const size_t MN = (size_t)M * N;
     int blocks = (int)((MN + 255) / 256);
     if (blocks > 2048) blocks = 2048;
     TS_TRY(launch_pdl(k_gemm_reduce<T>, dim3(blocks), dim3(256), 0, st, M, N, splits,
-                      static_cast<const T*>(part), (T)alpha, (T)beta, C));
+                      static_cast<const T*>(part), (T)alpha, (T)beta, C, skip));
   }
   return TS_OK;
 }
@@ -230,7 +233,7 @@ ts_status launch_split_reduce(int M, int N, int splits, const T* partial, T* C, 
   int blocks = (int)((MN + 255) / 256);
   if (blocks > 2048) blocks = 2048;
   return launch_pdl(k_gemm_reduce<T>, dim3(blocks), dim3(256), 0, st, M, N, splits, partial, (T)1,
-                    (T)0, OutView<T>{C, ldc, 1});
+                    (T)0, OutView<T>{C, ldc, 1}, (const int*)nullptr);
 }
 
 template <typename T>

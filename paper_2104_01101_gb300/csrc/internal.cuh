@@ -140,6 +140,8 @@ struct GemmSplit {
   size_t partial_elems;
   unsigned* counters;    // unused (kept for layout stability of the workspaces)
   int ncounters;
+  const int* skip;       // nullable device flag: non-zero when the product's kernels start
+                         // (after the previous kernel completed) makes them return at once
 };
 template <typename T>
 ts_status gemm(int M, int N, int K, double alpha, MatView<T> A, MatView<T> B, double beta,
@@ -222,13 +224,14 @@ ts_status launch_rsvd_stage1(int r, int k, const T* G, int ldg, const T* W, int 
                              bool qr64, int* flag, cudaStream_t st);
 size_t rsvd_stage1_smem_bytes(int r, int k, size_t tsize, bool qr64);
 // Large-r pieces of stage 1: Q = orth(C) in one block, and G^{-1} by Newton-Schulz
-// (S1: 2 r^2 values, S2: r^2 values of scratch).
+// (S1: 2 r^2 values, S2: r^2 values of scratch; conv: 3 device ints, or null, through
+// which the steps after convergence return at once).
 template <typename T>
 ts_status launch_qr_only(int r, int k, const T* C, T* Q, bool qr64, cudaStream_t st);
 size_t qr_only_smem_bytes(int r, int k, bool qr64, size_t tsize);
 template <typename T>
 ts_status newton_schulz_inverse(int r, const T* G, long ldg, T* X, T* S1, T* S2, int iters,
-                                const GemmSplit<T>* split, cudaStream_t st);
+                                int* conv, const GemmSplit<T>* split, cudaStream_t st);
 constexpr int kNewtonSchulzIters = 14;
 // X = G^{-1} H for G (r x r) SPD and H (r x s).
 template <typename T>

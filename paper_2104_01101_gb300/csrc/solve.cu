@@ -284,9 +284,45 @@ __global__ void k_ns_init(int r, const unsigned long long* __restrict__ beta_bit
 }
 
 template <typename T>
-__global__ void k_copy(long n, const T* __restrict__ src, T* __restrict__ dst) {
+__global__ void k_copy(long n, const T* __restrict__ src, T* __restrict__ dst,
+                       const int* skip = nullptr) {
+  if (skip && *skip) return;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
     dst[e] = src[e];
+}
+
+// Newton-Schulz convergence: conv[0] = 1 once max |S1 - I| <= tol, S1 = 2I - G X (so the
+// current X already inverts G to that accuracy; later steps would change it by ~tol^2).
+// Blocks count their failures into conv[1]; the last block to finish (ticket conv[2])
+// decides and resets both counters.
+template <typename T>
+__global__ void k_ns_check(int r, const T* __restrict__ S1, int* conv, T tol) {
+  __shared__ int bad;
+  __shared__ bool last;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  if (conv[0]) return;  // uniform: every thread reads the same flag
+  const long rr = (long)r * r;
+  int mine = 0;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < rr;
+       e += (long)gridDim.x * blockDim.x) {
+    const T d = S1[e] - ((e / r) == (e % r) ? (T)1 : (T)0);
+    mine |= !(fabs(d) <= tol);  // NaN counts as not converged
+  }
+  if (mine) atomicOr(&bad, 1);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (bad) atomicAdd(conv + 1, 1);
+    __threadfence();
+    last = atomicAdd(conv + 2, 1) == (int)gridDim.x - 1;
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(conv + 1, 0) == 0) conv[0] = 1;
+    conv[1] = 0;
+    conv[2] = 0;
+  }
 }
 
 template <typename T>
@@ -311,7 +347,7 @@ size_t qr_only_smem_bytes(int r, int k, bool qr64, size_t tsize) {
 // G^{-1} (r x r, into X) by `iters` Newton-Schulz steps; S1 holds 2 r^2 and S2 r^2 values.
 template <typename T>
 ts_status newton_schulz_inverse(int r, const T* G, long ldg, T* X, T* S1, T* S2, int iters,
-                                const GemmSplit<T>* split, cudaStream_t st) {
+                                int* conv, const GemmSplit<T>* split, cudaStream_t st) {
   const long rr = (long)r * r;
   // beta's bits live in S1 until the first iteration overwrites it
   unsigned long long* beta_bits = reinterpret_cast<unsigned long long*>(S1);
@@ -321,16 +357,29 @@ ts_status newton_schulz_inverse(int r, const T* G, long ldg, T* X, T* S1, T* S2,
   k_ns_init<T><<<ceil_div(rr, 256) > 1024 ? 1024 : ceil_div(rr, 256), 256, 0, st>>>(r, beta_bits,
                                                                                      X, S2);
   TS_LAUNCH_CHECK();
+  // once the iteration has converged (conv set by k_ns_check) the remaining launches of
+  // the fixed schedule return at once: the schedule stays graph-capturable
+  GemmSplit<T> sp = split ? *split : GemmSplit<T>{};
+  sp.skip = conv;
+  if (conv) TS_CUDA(cudaMemsetAsync(conv, 0, 3 * sizeof(int), st));
+  const T tol = sizeof(T) == 4 ? (T)2e-6 : (T)1e-13;
+  const int cb = ceil_div(rr, 256) > 1024 ? 1024 : ceil_div(rr, 256);
+  const int chk = ceil_div(rr, 2048) > 256 ? 256 : ceil_div(rr, 2048);
+  constexpr int kFirstCheck = 6;  // from a Gershgorin start the error halves at best early on
   for (int it = 0; it < iters; ++it) {
     // S1 = 2I - G X
-    k_copy<T><<<ceil_div(rr, 256) > 1024 ? 1024 : ceil_div(rr, 256), 256, 0, st>>>(rr, S2, S1);
+    k_copy<T><<<cb, 256, 0, st>>>(rr, S2, S1, conv);
     TS_LAUNCH_CHECK();
     TS_TRY(gemm<T>(r, r, r, -1.0, MatView<T>{G, ldg, 1}, MatView<T>{X, r, 1}, 1.0,
-                   OutView<T>{S1, r, 1}, split, st));
+                   OutView<T>{S1, r, 1}, &sp, st));
+    if (conv && it >= kFirstCheck) {
+      k_ns_check<T><<<chk, 256, 0, st>>>(r, S1, conv, tol);
+      TS_LAUNCH_CHECK();
+    }
     // X <- X S1 (written through the first r*r of the split buffer)
     TS_TRY(gemm<T>(r, r, r, 1.0, MatView<T>{X, r, 1}, MatView<T>{S1, r, 1}, 0.0,
-                   OutView<T>{S1 + rr, r, 1}, split, st));
-    k_copy<T><<<ceil_div(rr, 256) > 1024 ? 1024 : ceil_div(rr, 256), 256, 0, st>>>(rr, S1 + rr, X);
+                   OutView<T>{S1 + rr, r, 1}, &sp, st));
+    k_copy<T><<<cb, 256, 0, st>>>(rr, S1 + rr, X, conv);
     TS_LAUNCH_CHECK();
   }
   return TS_OK;
@@ -717,7 +766,7 @@ ts_status launch_finalize(int s, int R, const T* M, long rs, long cs, int kdim, 
   template ts_status launch_finalize<T>(int, int, const T*, long, long, int, const T*, T*, T*,  \
                                         int, T*, CoreMap, cudaStream_t, void*, size_t);          \
   template ts_status launch_qr_only<T>(int, int, const T*, T*, bool, cudaStream_t);             \
-  template ts_status newton_schulz_inverse<T>(int, const T*, long, T*, T*, T*, int,             \
+  template ts_status newton_schulz_inverse<T>(int, const T*, long, T*, T*, T*, int, int*,       \
                                               const GemmSplit<T>*, cudaStream_t);
 TS_INST(float)
 TS_INST(double)

@@ -443,6 +443,7 @@ static ts_status solve_subproblem(int m, int r, int s, int R, int solve, int kc,
     } else {
       // G^{-1} by Newton-Schulz; C = G^{-1} W; Q = qr(C); E = G^{-1} Q
       TS_TRY(newton_schulz_inverse<T>(r, w.GW, r + k, w.Ginv, w.NS1, w.NS2, kNewtonSchulzIters,
+                                      w.flag + 8,
                                       sp, st));
       TS_TRY(gemm<T>(r, k, r, 1.0, mv<T>(w.Ginv, r, 1), mv<T>(w.GW + r, r + k, 1), 0.0,
                      ov<T>(w.Cb, k, 1), sp, st));

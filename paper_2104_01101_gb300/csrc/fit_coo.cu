@@ -273,7 +273,7 @@ __global__ void k_fit_coo_final(const T* __restrict__ C, const T* __restrict__ M
     const double tt = *t2;
     const double r2 = tt - 2.0 * acc[1] + s;
     acc[2] = s;
-    *residual = sqrt((r2 > 0 ? r2 : 0.0) / tt);
+    *residual = tt > 0 ? sqrt((r2 > 0 ? r2 : 0.0) / tt) : 0.0;  // as the dense form: 0 for T = 0
   }
 }
 

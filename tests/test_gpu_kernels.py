@@ -441,6 +441,25 @@ def test_fitness_coo_matches_oracle(ts, dims, ranks, nnz, dtype):
     assert abs(got - want) <= tol * max(want, 1e-3)
 
 
+def test_coo_empty_tensor(ts):
+    # nnz = 0: the leverage sketch has zero right-hand sides (Z is still the sampled rows
+    # of the Kronecker product) and the residual of the empty tensor is reported as 0,
+    # as in the dense form
+    dims = (12, 10, 9)
+    g = np.random.default_rng(3)
+    fac = [np.linalg.qr(g.standard_normal((s, 3)))[0] for s in dims]
+    X = ts.Coo(torch.zeros((3, 0), dtype=torch.int32, device="cuda"),
+               torch.zeros(0, dtype=torch.float64, device="cuda"), dims)
+    Zg, Yg, sg = ts.leverage_sketch(X, 1, [dev(f) for f in fac], 50, seed=2, sweep=0)
+    Zw, Yw, sw, _ = sketch.leverage_sketch_coo(np.zeros((3, 0), np.int32), np.zeros(0), dims, 1,
+                                               fac, 50, 2, 0)
+    assert np.array_equal(sg.cpu().numpy(), sw.astype(np.int32))
+    assert np.allclose(Zg.cpu().numpy(), Zw, rtol=1e-13, atol=0)
+    assert not Yg.cpu().numpy().any() and not Yw.any()
+    core = g.standard_normal((3, 3, 3))
+    assert ts.fitness_residual(X, dev(core), [dev(f) for f in fac]) == 0.0
+
+
 def test_fitness_coo_exact_model_is_zero(ts):
     # a COO tensor holding every entry of a Tucker tensor once (plus explicit repeats
     # that cancel) has residual ~0 against its own model

@@ -310,7 +310,7 @@ ts_status ts_leverage_sketch_det(const ts_tensor* X, int32_t mode, const int32_t
  * offset 0 of the scratch is set non-zero if a hash table could not place an entry
  * (excluded by its capacity).
  * factors: HOST array of order device pointers (dims[k] x ranks[k]).
- * residual_out: DEVICE pointer to one double.
+ * residual_out: DEVICE pointer to one double (0 when ||T|| = 0).
  * Errors: TS_ERR_UNSUPPORTED for COO input with order < 2, >= 2^30 nonzeros, the
  * product of the other dims of the largest mode >= 9e18, a core larger than 200 KB or
  * ranks[order-1] > 64. */

@@ -348,6 +348,26 @@ def test_sparse_order4_scaled_workload_matches_oracle(ts):
         assert np.allclose(sg, so, rtol=1e-8, atol=1e-10 * so[0])
 
 
+def test_sparse_full_size_decomposition_properties(ts):
+    # The sparse 4-way workload at the size the benchmark times (200000^4, 1e8 nonzeros,
+    # m = 4096, rank 8, 5 sweeps): too large for the oracle, so checked by properties that
+    # hold at any size: no breakdown, orthonormal factors, a residual that repeats to the
+    # rounding of the FP32 atomics, and one well below 1 (the planted component is found).
+    dims, ranks, nnz, m = (200000,) * 4, (8,) * 4, 100_000_000, 4096
+    idx, vals = synth.coo_zipf_tucker_torch(dims, nnz, ranks, seed=11, device="cuda")
+    X = ts.Coo(idx, vals, dims)
+    plan = ts.TuckerPlan(X, ranks, m, 5, seed=3, rrf_k1=64, rrf_k2=128)
+    plan.run(X)
+    r1 = float(plan.residuals[0])
+    assert plan.numeric_flag() == 0
+    for A in plan.factors:
+        G = (A.double().t() @ A.double()).cpu().numpy()
+        assert np.abs(G - np.eye(G.shape[0])).max() < 1e-4
+    plan.run(X)
+    r2 = float(plan.residuals[0])
+    assert 0.0 < r1 < 0.5 and abs(r1 - r2) <= 1e-4 * r1
+
+
 def test_deterministic_leverage_all_rows_is_hooi_on_gpu(ts):
     # m = prod of the other mode sizes keeps every row: with the exact solve the sketched
     # ALS is HOOI from the same initial factors

@@ -45,7 +45,8 @@ SPARSE_DIMS, SPARSE_NNZ, SPARSE_RANKS, SPARSE_M, SPARSE_SWEEPS = (200000,) * 4, 
     (8, 8, 8, 8), 4096, 5
 SPARSE_WORKLOAD = ("sparse 4-way COO 200000^4, 1e8 nonzeros, Zipf(1.1) int32 coordinates, FP32 "
                    "values N(0,1) plus a planted rank-(8,8,8,8) Tucker component; TensorSketch "
-                   "m=4096; RRF init k1=64, k2=128; RSVD-LRLS (p=5); 5 sweeps; COO residual")
+                   "m=4096 redrawn every sweep (one pass per mode over the nonzeros per sweep); "
+                   "RRF init k1=64, k2=128; RSVD-LRLS (p=5); 5 sweeps; COO residual")
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
 
@@ -241,7 +242,7 @@ def time_sparse(args, dev):
                                             device=dev)
     X = ts.Coo(idx, vals, SPARSE_DIMS)
     plan = ts.TuckerPlan(X, SPARSE_RANKS, SPARSE_M, SPARSE_SWEEPS, seed=3, rrf_k1=64,
-                         rrf_k2=128)
+                         rrf_k2=128, resketch=True)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
     plan.set_phase_events(ev)
     steps = []
@@ -415,8 +416,8 @@ def run_ours(args, rank, world):
 
 
 # DRAM bytes (read + write) of one right-hand-side launch of k_sketch_dense3_tma on this
-# workload, from the ncu capture in profiles/input_sketch_dense400_fp32.md.  The figure
-# belongs to the kernel source it was taken on: another source reports null.
+# workload, from an ncu capture of dram__bytes_read.sum + dram__bytes_write.sum.  The
+# figure belongs to the kernel source it was taken on: another source reports null.
 SKETCH_TRAFFIC_BYTES = 271.7e6
 SKETCH_SOURCE_SHA1 = "4cf4b8dc9a81"
 

@@ -180,7 +180,10 @@ ts_status tensorsketch_apply(int32_t nf, const void* const* factors, const int64
  *   exits.
  * - Set-up: the first call on each device looks up the array's device address
  *   with that device current (cudaGetSymbolAddress) and caches it; make that first
- *   call before any stream capture.
+ *   call before any stream capture.  The cache assumes the device's primary context
+ *   lives until the process exits: after cudaDeviceReset the library's module is
+ *   loaded again and the cached address may be stale, so do not call this entry
+ *   point after resetting a device that it has already been called on.
  * - Concurrency: all calls share the one array and it keeps the last call's
  *   contents; calls that overlap on the GPU (any streams, any host threads) race,
  *   so order them (one stream, or events).  Nothing in it needs clearing: each

@@ -31,15 +31,29 @@ __device__ __forceinline__ double block_sum_d(double v, double* sh) {
   return t;  // valid in thread 0
 }
 
+struct CooExtent {
+  int order;
+  int64_t dims[TS_MAX_ORDER];
+};
+
 // Adds every nonzero's value into the slot of key (fibre slot, i_nf) of the value table.
+// Entries with a coordinate outside [0, dims[k]) are skipped, as in <T, T~> and the input
+// sketch (their fibre key could alias another fibre's).
 template <typename T>
 __global__ void k_merge_repeats(const int32_t* __restrict__ idx, const T* __restrict__ vals,
-                                int64_t nnz, int nf, int64_t sn,
+                                int64_t nnz, int nf, CooExtent ext,
                                 const int32_t* __restrict__ eslot,
                                 unsigned long long* __restrict__ vkeys, double* __restrict__ vsum,
                                 uint64_t vmask, int* flag) {
+  const int64_t sn = ext.dims[nf];
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz;
        e += (int64_t)gridDim.x * blockDim.x) {
+    bool ok = true;
+    for (int k = 0; k < ext.order; ++k) {
+      const int32_t i = idx[(int64_t)k * nnz + e];
+      ok &= (i >= 0) & (i < ext.dims[k]);
+    }
+    if (!ok) continue;
     const unsigned long long key = (unsigned long long)(unsigned)eslot[e] * (unsigned long long)sn +
                                    (unsigned long long)(unsigned)idx[(int64_t)nf * nnz + e];
     uint64_t g = mix64(key) & vmask;
@@ -337,16 +351,18 @@ ts_status launch_fit_coo_norm(const ts_tensor& X, const FitCooWork& w, int* flag
   TS_CUDA(cudaMemsetAsync(w.vsum, 0, (size_t)cap * sizeof(double), st));
   TS_CUDA(cudaMemsetAsync(w.acc, 0, 4 * sizeof(double), st));
   const int grid = (int)std::min<int64_t>(std::max<int64_t>(ceil_div(X.nnz, 256), 1), 152 * 16);
-  const int64_t sn = X.dims[w.F.mode];
+  CooExtent ext{};
+  ext.order = X.order;
+  for (int k = 0; k < X.order; ++k) ext.dims[k] = X.dims[k];
   if (X.nnz > 0) {
     if (X.dtype == TS_F64)
       k_merge_repeats<double><<<grid, 256, 0, st>>>(X.indices,
                                                     static_cast<const double*>(X.values), X.nnz,
-                                                    w.F.mode, sn, w.eslot, w.vkeys, w.vsum,
+                                                    w.F.mode, ext, w.eslot, w.vkeys, w.vsum,
                                                     w.vmask, flag);
     else
       k_merge_repeats<float><<<grid, 256, 0, st>>>(X.indices, static_cast<const float*>(X.values),
-                                                   X.nnz, w.F.mode, sn, w.eslot, w.vkeys, w.vsum,
+                                                   X.nnz, w.F.mode, ext, w.eslot, w.vkeys, w.vsum,
                                                    w.vmask, flag);
     TS_LAUNCH_CHECK();
   }

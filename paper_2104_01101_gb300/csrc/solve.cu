@@ -291,17 +291,34 @@ __global__ void k_copy(long n, const T* __restrict__ src, T* __restrict__ dst,
     dst[e] = src[e];
 }
 
-// Newton-Schulz convergence: conv[0] = 1 once max |S1 - I| <= tol, S1 = 2I - G X (so the
-// current X already inverts G to that accuracy; later steps would change it by ~tol^2).
-// Blocks count their failures into conv[1]; the last block to finish (ticket conv[2])
-// decides and resets both counters.
+// First launch of a Newton-Schulz step: S1 <- 2I, unless the iteration has stopped.
+// conv[3] = "the previous step's check passed": that step's own update X <- X S1 has run,
+// so from here on every launch returns (conv[0] = 1, read by the products and copies).
+// All blocks read the same conv[3] (written by an earlier launch), so they agree.
+template <typename T>
+__global__ void k_ns_start(long n, const T* __restrict__ twoI, T* __restrict__ S1, int* conv) {
+  if (conv[0]) return;
+  if (conv[3]) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) conv[0] = 1;
+    return;
+  }
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x)
+    S1[e] = twoI[e];
+}
+
+// Newton-Schulz convergence: conv[3] = 1 once max |S1 - I| <= tol, S1 = 2I - G X, i.e.
+// the residual E = I - G X of the current X is below tol entrywise.  The step's own update
+// X <- X S1 = X (I + E) still runs and leaves a residual E^2 (quadratic convergence: at
+// the rounding floor); the next step's k_ns_start turns conv[3] into the stop flag
+// conv[0].  Blocks count their failures into conv[1]; the last block to finish (ticket
+// conv[2]) decides and resets both counters.
 template <typename T>
 __global__ void k_ns_check(int r, const T* __restrict__ S1, int* conv, T tol) {
   __shared__ int bad;
   __shared__ bool last;
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  if (conv[0]) return;  // uniform: every thread reads the same flag
+  if (conv[0] || conv[3]) return;  // uniform: every thread reads the same flags
   const long rr = (long)r * r;
   int mine = 0;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < rr;
@@ -319,7 +336,7 @@ __global__ void k_ns_check(int r, const T* __restrict__ S1, int* conv, T tol) {
   __syncthreads();
   if (last && threadIdx.x == 0) {
     __threadfence();
-    if (atomicAdd(conv + 1, 0) == 0) conv[0] = 1;
+    if (atomicAdd(conv + 1, 0) == 0) conv[3] = 1;
     conv[1] = 0;
     conv[2] = 0;
   }
@@ -357,18 +374,22 @@ ts_status newton_schulz_inverse(int r, const T* G, long ldg, T* X, T* S1, T* S2,
   k_ns_init<T><<<ceil_div(rr, 256) > 1024 ? 1024 : ceil_div(rr, 256), 256, 0, st>>>(r, beta_bits,
                                                                                      X, S2);
   TS_LAUNCH_CHECK();
-  // once the iteration has converged (conv set by k_ns_check) the remaining launches of
-  // the fixed schedule return at once: the schedule stays graph-capturable
+  // once the iteration has converged (k_ns_check, then the update of that step) the
+  // remaining launches of the fixed schedule return at once: the schedule stays
+  // graph-capturable.  conv holds 4 ints (stop flag, two counters, check passed).
   GemmSplit<T> sp = split ? *split : GemmSplit<T>{};
   sp.skip = conv;
-  if (conv) TS_CUDA(cudaMemsetAsync(conv, 0, 3 * sizeof(int), st));
+  if (conv) TS_CUDA(cudaMemsetAsync(conv, 0, 4 * sizeof(int), st));
   const T tol = sizeof(T) == 4 ? (T)2e-6 : (T)1e-13;
   const int cb = ceil_div(rr, 256) > 1024 ? 1024 : ceil_div(rr, 256);
   const int chk = ceil_div(rr, 2048) > 256 ? 256 : ceil_div(rr, 2048);
   constexpr int kFirstCheck = 6;  // from a Gershgorin start the error halves at best early on
   for (int it = 0; it < iters; ++it) {
     // S1 = 2I - G X
-    k_copy<T><<<cb, 256, 0, st>>>(rr, S2, S1, conv);
+    if (conv)
+      k_ns_start<T><<<cb, 256, 0, st>>>(rr, S2, S1, conv);
+    else
+      k_copy<T><<<cb, 256, 0, st>>>(rr, S2, S1, nullptr);
     TS_LAUNCH_CHECK();
     TS_TRY(gemm<T>(r, r, r, -1.0, MatView<T>{G, ldg, 1}, MatView<T>{X, r, 1}, 1.0,
                    OutView<T>{S1, r, 1}, &sp, st));

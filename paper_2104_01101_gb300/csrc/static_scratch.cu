@@ -5,7 +5,11 @@
 // The array is a file-scope __device__ object, so every GPU that loads this
 // library holds kStaticScratchBytes of it until the process exits.  In host code
 // its name is only a host-side stand-in; the device address is fetched once per
-// device with cudaGetSymbolAddress (with that device current) and cached.
+// device with cudaGetSymbolAddress (with that device current) and cached.  The cache
+// is keyed by device ordinal and never invalidated: it assumes the primary context is
+// not reset (cudaDeviceReset reloads the module, and the cached address may then be
+// stale).  Looking the address up on every call would survive a reset but could not
+// run inside a stream capture, which the cached form can.
 #include <mutex>
 
 #include "internal.cuh"

@@ -1,0 +1,877 @@
+// RSVD-LRLS (Alg. 5) of one sketched subproblem in ONE thread block, organised around
+// the short dependency chains of a single SM.  Inputs are the blocks of the augmented
+// product [G | W | H] = Z^T [Z | Y Omega | Y] (G = Z^T Z, r x r SPD; W, r x k; H, r x s).
+//
+//   1. Symmetric elimination (G = L D L^T, L unit lower) of the augmented block [G | W],
+//      one pivot per step, held in registers by NWE warps: warp w owns the RS consecutive
+//      rows RS w .. RS w + RS - 1, lane l the 4 consecutive columns 4 l .. 4 l + 3 of
+//      [G | W].  As column j of G is eliminated it is replaced in place by column j of
+//      N = L^{-1} (the in-place inverse), so after r steps the registers hold N (strictly
+//      lower), D (diagonal) and N W.  Step j reads the "cross" of pivot j (row j of N and
+//      W, column j of G, the pivot's reciprocal) from a double-buffered shared row that
+//      the owners of pivot j+1 fill during step j: one barrier per pivot.  The pivot loop
+//      runs over (row block, row slot) with the slot a compile-time index, so the slot
+//      of every row, the column slot of the pivot and which rows are still active are
+//      all known at compile time.  Meanwhile the other warps copy H into shared memory.
+//   2. B = G^{-1} = N^T D^{-1} N is never formed: C = B W = N^T (D^{-1} (N W)) and
+//      E = B Q = N^T (D^{-1} (N Q)) are triangular products with k <= 16 columns.
+//   3. Q = qr(C): Householder, warp c owning column c (one barrier per reflector), then
+//      warp c forms column c of Q.
+//   4. D = E^T H (k x s; E^T H = Q^T B Z^T Y of Alg. 5), K = D D^T.
+//   5. K = U Lambda U^T by cyclic Jacobi in ONE warp (round-robin pairs; rotations of a
+//      round applied as 2 x 2 block updates into a second buffer; no block barrier).
+//   6. C_(n)^T = Q U_R Sigma_R, A^(n) = D^T U_R Sigma_R^{-1}, canonical column signs, core.
+#include "dense_la.cuh"
+
+namespace ts {
+
+namespace {
+constexpr int kCT = 512;  // threads of the block
+constexpr int kCW = kCT / 32;
+constexpr int kCK = 16;    // widest RSVD sketch (k) and Jacobi order
+constexpr int kCKs = 17;   // row stride of the k x k Jacobi buffers
+constexpr int kCX = 132;   // one cross: 128 columns + the pivot's reciprocal at kCX - 1
+constexpr int kCMax = 128; // r + k limit of the elimination tile
+constexpr unsigned kAll = 0xffffffffu;
+}  // namespace
+
+// Rows per warp of the elimination (all 16 warps): FP32 8 (r <= 128), FP64 4 (r <= 64,
+// the register budget of 512 threads).  RS % 4 == 0 and 4 | RS keep the parity of a
+// pivot and its column slot compile-time constants of the 4-pivot loop body.
+template <typename T>
+struct ElimShape {
+  static constexpr int NWE = kCW;
+  static constexpr int RS = sizeof(T) == 4 ? 8 : 4;
+};
+
+__device__ __forceinline__ void elim_sync(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// Shared-memory layout (byte offsets).  T = data type, U = QR type.
+struct CholLayout {
+  int ldn;
+  size_t H, D, Am, N, dinv, Y, Q, E, buf, late, C, tau, K0, K1, V, F, CnT, total;
+  bool h_smem, d_smem, a_smem;
+};
+
+__host__ __device__ inline CholLayout chol_layout(int r, int s, int k, int R, size_t tsz,
+                                                  size_t usz, bool h_smem, bool d_smem,
+                                                  bool a_smem) {
+  CholLayout L{};
+  L.ldn = (r + 3) & ~3;
+  L.h_smem = h_smem;
+  L.d_smem = d_smem;
+  L.a_smem = a_smem;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    off = (off + 15) & ~(size_t)15;
+    const size_t o = off;
+    off += bytes;
+    return o;
+  };
+  // H (r x s) when it is copied in; D (k x s) then overwrites its first k rows and A
+  // (s x R) follows them (row stride s for H and D)
+  if (h_smem) {
+    L.H = take(tsz * (size_t)r * s);
+    L.D = L.H;
+    L.Am = L.H + tsz * (size_t)k * s;
+  } else {
+    L.D = take(d_smem ? tsz * (size_t)k * s : 0);
+    L.Am = take(a_smem ? tsz * (size_t)s * R : 0);
+  }
+  L.N = take(tsz * (size_t)r * L.ldn);
+  L.dinv = take(tsz * (size_t)((r + 3) & ~3));
+  L.Y = take(tsz * (size_t)r * kCK);
+  L.Q = take(tsz * (size_t)r * kCK);
+  L.E = take(tsz * (size_t)r * kCK);
+  L.buf = take(tsz * 2 * kCX);
+  // the QR workspace, then (after Q is formed) the Jacobi buffers and C_(n)^T
+  const size_t qr = ((usz * (size_t)r * 17 + 15) & ~(size_t)15) + usz * kCK;
+  const size_t kb = ((tsz * kCK * kCKs + 15) & ~(size_t)15);
+  const size_t lt = 3 * kb + ((tsz * kCK * kCK + 15) & ~(size_t)15) + tsz * (size_t)r * R;
+  L.late = take(qr > lt ? qr : lt);
+  L.C = L.late;
+  L.tau = L.late + ((usz * (size_t)r * 17 + 15) & ~(size_t)15);
+  L.K0 = L.late;
+  L.K1 = L.K0 + kb;
+  L.V = L.K1 + kb;
+  L.F = L.V + kb;
+  L.CnT = L.F + ((tsz * kCK * kCK + 15) & ~(size_t)15);
+  L.total = off;
+  return L;
+}
+
+template <typename T>
+struct V4;
+template <>
+struct V4<float> {
+  __device__ static void ld(const float* p, float (&v)[4]) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x;
+    v[1] = t.y;
+    v[2] = t.z;
+    v[3] = t.w;
+  }
+  __device__ static void st(float* p, const float (&v)[4]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct V4<double> {
+  __device__ static void ld(const double* p, double (&v)[4]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0];
+    const double2 b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+    v[3] = b.y;
+  }
+  __device__ static void st(double* p, const double (&v)[4]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+  }
+};
+
+// ---------------------------------------------------------------- 1. elimination
+
+// Reciprocal of a pivot: the hardware approximation refined by one Newton step (FP32),
+// or the division (FP64).
+__device__ __forceinline__ float elim_rcp(float v) {
+  const float y = __fdividef(1.0f, v);
+  return y * fmaf(-v, y, 2.0f);
+}
+__device__ __forceinline__ double elim_rcp(double v) { return 1.0 / v; }
+
+// Row j + 1's part of the next cross: its N part (c < jn), its W part and the reciprocal
+// of its pivot (the pivot itself goes out with its column).
+template <typename T>
+__device__ __forceinline__ void elim_row_publish(const T (&xr)[4], int jn, int r, int k, T* nxt,
+                                                 int* flag) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int c = 4 * lane + u;
+    const T v = xr[u];
+    if (c < jn || (c >= r && c - r < k)) nxt[c] = v;
+    if (c == jn) {
+      const bool bad = !(v > (T)0) || !isfinite(v);
+      if (bad && flag) atomicExch(flag, 1);
+      nxt[kCX - 1] = elim_rcp(bad ? (T)1 : v);
+    }
+  }
+}
+
+// Row `slot` of the tile by a select tree (no dynamic register index).
+template <typename T, int RS>
+__device__ __forceinline__ void elim_pick_row(const T (&x)[RS][4], int slot, T (&v)[4]) {
+  static_assert(RS == 4 || RS == 8, "select tree for 4 or 8 rows");
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const bool b0 = slot & 1, b1 = slot & 2;
+    const T a01 = b0 ? x[1][u] : x[0][u], a23 = b0 ? x[3][u] : x[2][u];
+    T lo = b1 ? a23 : a01;
+    if constexpr (RS == 8) {
+      const T a45 = b0 ? x[5][u] : x[4][u], a67 = b0 ? x[7][u] : x[6][u];
+      const T hi = b1 ? a67 : a45;
+      lo = (slot & 4) ? hi : lo;
+    }
+    v[u] = lo;
+  }
+}
+
+// Pivot j = 4 jb + U0 (U0 static: the pivot's column slot and the buffer parity).  Warps
+// whose rows are all above or at the pivot only wait at the barrier; the warp holding
+// the pivot row updates the rows below it under predicates (no branches, so its loads
+// are not serialised); the others update all their rows and publish column j + 1 with
+// vector stores.
+template <typename T, int NWE, int RS, int U0>
+__device__ __forceinline__ void elim_step(T (&x)[RS][4], int j, int r, int k, T* buf, int* flag) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  constexpr int UJ = U0, UJN = (U0 + 1) & 3;
+  const int rb0 = RS * w;
+  if (rb0 + RS - 1 > j) {
+    const T* cur = buf + (U0 & 1) * kCX;  // j = 4 jb + U0 has the parity of U0
+    T* nxt = buf + ((U0 & 1) ^ 1) * kCX;
+    const T inv = cur[kCX - 1];
+    T colv[4];
+    V4<T>::ld(cur + 4 * lane, colv);
+    T mv[RS];
+#pragma unroll
+    for (int q = 0; q < RS / 4; ++q) {
+      T t4[4];
+      V4<T>::ld(cur + rb0 + 4 * q, t4);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) mv[4 * q + e] = t4[e] * inv;
+    }
+    const int jn = j + 1;
+    const bool fix = lane == (j >> 2);
+    const bool pub = lane == (jn >> 2) && jn < r;
+    if (rb0 > j) {  // every row of this warp is below the pivot
+#pragma unroll
+      for (int t = 0; t < RS; ++t) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[t][u] = fma(-mv[t], colv[u], x[t][u]);
+        if (fix) x[t][UJ] = -mv[t];  // column j of G becomes column j of N
+      }
+      if (pub) {  // column j + 1 on this warp's rows
+        if (rb0 + RS <= r) {
+#pragma unroll
+          for (int q = 0; q < RS / 4; ++q) {
+            T o[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) o[e] = x[4 * q + e][UJN];
+            V4<T>::st(nxt + rb0 + 4 * q, o);
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < RS; ++t)
+            if (rb0 + t < r) nxt[rb0 + t] = x[t][UJN];
+        }
+      }
+    } else {  // the pivot row's warp: rows below the pivot
+#pragma unroll
+      for (int t = 0; t < RS; ++t) {
+        const bool act = rb0 + t > j;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const T nv = fma(-mv[t], colv[u], x[t][u]);
+          x[t][u] = act ? nv : x[t][u];
+        }
+        if (act && fix) x[t][UJ] = -mv[t];
+        if (act && pub && rb0 + t < r) nxt[rb0 + t] = x[t][UJN];
+      }
+    }
+    if (jn < r && w == jn / RS) {  // row j + 1 (updated above by this warp)
+      T v[4];
+      elim_pick_row<T, RS>(x, jn % RS, v);
+      elim_row_publish<T>(v, jn, r, k, nxt, flag);
+    }
+  }
+  elim_sync(NWE * 32);
+}
+
+// Symmetric elimination of [G | W] (r + k <= 128) by warps 0 .. NWE - 1; on exit N (unit
+// lower, r x ldn, zeros above), dinv = D^{-1} and Y = N W (r x 16, zero columns >= k)
+// are in shared memory (the caller synchronises the block).  A non-positive or
+// non-finite pivot sets *flag and is replaced by 1.  Tile slots above the diagonal and
+// beyond W take harmless garbage: they are never published and the dump masks them.
+template <typename T, int NWE, int RS>
+__device__ void chol_eliminate(const T* __restrict__ G, long ldg, const T* __restrict__ W,
+                               long ldw, int r, int k, T* buf, T* Nm, int ldn, T* dinv, T* Y,
+                               int* flag) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  T x[RS][4];
+#pragma unroll
+  for (int t = 0; t < RS; ++t) {
+    const int i = RS * w + t;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = 4 * lane + u;
+      T v = (T)0;
+      if (i < r) {
+        if (c < r) {
+          if (c <= i) v = G[(long)i * ldg + c];
+        } else if (c - r < k) {
+          v = W[(long)i * ldw + (c - r)];
+        }
+      }
+      x[t][u] = v;
+    }
+  }
+  for (int e = tid; e < 2 * kCX; e += NWE * 32) buf[e] = (T)0;
+  elim_sync(NWE * 32);
+  // cross of pivot 0: column 0 (every row; the pivot included) from lane 0, row 0's W
+  // part and the pivot's reciprocal from warp 0
+  if (lane == 0) {
+#pragma unroll
+    for (int t = 0; t < RS; ++t)
+      if (RS * w + t < r) buf[RS * w + t] = x[t][0];
+  }
+  if (w == 0) elim_row_publish<T>(x[0], 0, r, k, buf, flag);
+  elim_sync(NWE * 32);
+  for (int j = 0; j < r; j += 4) {
+    elim_step<T, NWE, RS, 0>(x, j, r, k, buf, flag);
+    if (j + 1 < r) elim_step<T, NWE, RS, 1>(x, j + 1, r, k, buf, flag);
+    if (j + 2 < r) elim_step<T, NWE, RS, 2>(x, j + 2, r, k, buf, flag);
+    if (j + 3 < r) elim_step<T, NWE, RS, 3>(x, j + 3, r, k, buf, flag);
+  }
+  // N (unit diagonal, zeros above), D^{-1}, N W
+#pragma unroll
+  for (int t = 0; t < RS; ++t) {
+    const int i = RS * w + t;
+    if (i >= r) continue;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = 4 * lane + u;
+      if (c < r) {
+        if (c == i) {
+          T d = x[t][u];
+          if (!(d > (T)0) || !isfinite(d)) d = (T)1;  // flagged during elimination
+          dinv[i] = (T)1 / d;
+          Nm[i * ldn + c] = (T)1;
+        } else {
+          Nm[i * ldn + c] = c < i ? x[t][u] : (T)0;
+        }
+      } else if (c - r < kCK) {
+        Y[i * kCK + (c - r)] = (c - r < k) ? x[t][u] : (T)0;
+      }
+    }
+  }
+  // Y columns c with r + c >= 128 are outside the tile
+  for (int e = tid; e < r * kCK; e += NWE * 32) {
+    const int i = e >> 4, c = e & 15;
+    if (r + c >= kCMax) Y[i * kCK + c] = (T)0;
+  }
+  // padding columns r .. ldn - 1 of N
+  for (int e = tid; e < r * 4; e += NWE * 32) {
+    const int i = e >> 2, c = r + (e & 3);
+    if (c < ldn) Nm[i * ldn + c] = (T)0;
+  }
+}
+
+// ---------------------------------------------------------------- 2. triangular products
+
+// out(i, :) = post(i) * sum_a N~(i, a) * pre(a) * in(a, :) with N~ = N^T (UPPER: a >= i,
+// coefficient N(a, i)) or N (lower: a <= i, coefficient N(i, a)); N has a unit diagonal
+// and zeros above it, so the sums may run over whole 4-row blocks.  in/out are r x 16;
+// pre/post may be null (1).  A thread owns a 4 x 4 block of out and a quarter of the
+// sum (4-row blocks x 4 column blocks x 4 quarters = 512 threads for r <= 128).
+template <typename T, bool UPPER>
+__device__ void tri_product(const T* Nm, int ldn, int r, const T* pre, const T* in, const T* post,
+                            T* out) {
+  const int tid = threadIdx.x, q = tid & 3, cb = (tid >> 2) & 3, ib = tid >> 4;
+  const int i0 = 4 * ib;
+  T acc[4][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[e][b] = (T)0;
+  if (i0 < r) {
+    const int a0 = UPPER ? i0 + q : q;
+    const int a1 = UPPER ? r : min(r, i0 + 4);
+#pragma unroll 2
+    for (int a = a0; a < a1; a += 4) {
+      T cf[4], v[4];
+      if (UPPER) {
+        V4<T>::ld(Nm + a * ldn + i0, cf);  // N(a, i0 .. i0 + 3)
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) cf[e] = (i0 + e < r) ? Nm[(i0 + e) * ldn + a] : (T)0;
+      }
+      V4<T>::ld(in + a * kCK + 4 * cb, v);
+      if (pre) {
+        const T p = pre[a];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) v[b] *= p;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[e][b] = fma(cf[e], v[b], acc[e][b]);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      acc[e][b] += __shfl_xor_sync(kAll, acc[e][b], 1);
+      acc[e][b] += __shfl_xor_sync(kAll, acc[e][b], 2);
+    }
+  if (i0 < r && q == 0) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int i = i0 + e;
+      if (i < r) {
+        const T sc = post ? post[i] : (T)1;
+        T o[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) o[b] = acc[e][b] * sc;
+        V4<T>::st(out + i * kCK + 4 * cb, o);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- 3. Householder QR
+
+// Thin QR of A (r x k, row stride lda, type U) by Householder reflections, warp c owning
+// column c.  Warp j+1 applies reflector j to its column and then forms reflector j+1
+// without a barrier in between, so one block barrier per reflector.  On exit Qout
+// (r x 16, type T, zero columns >= k) holds the orthonormal factor.  A zero column gives
+// tau = 0 (an identity reflector).
+template <typename U, typename T>
+__device__ void chol_householder(U* A, int lda, int r, int k, U* tau, T* Qout) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = 0; j < k; ++j) {
+    if (warp == j) {
+      U sq = 0;
+      for (int i = j + lane; i < r; i += 32) {
+        const U v = A[i * lda + j];
+        sq += v * v;
+      }
+      sq = warp_sum(sq);
+      const U ajj = A[j * lda + j];
+      U tj = 0, v0 = ajj;
+      if (sq > (U)0) {
+        const U alpha = ajj >= (U)0 ? -sqrt(sq) : sqrt(sq);
+        v0 = ajj - alpha;
+        const U vn2 = sq - ajj * ajj + v0 * v0;
+        tj = vn2 > (U)0 ? (U)2 / vn2 : (U)0;
+      }
+      __syncwarp();
+      if (lane == 0) {
+        A[j * lda + j] = v0;
+        tau[j] = tj;
+      }
+    }
+    __syncthreads();
+    if (warp > j && warp < k) {
+      const U tj = tau[j];
+      U wsum = 0;
+      for (int i = j + lane; i < r; i += 32) wsum += A[i * lda + j] * A[i * lda + warp];
+      wsum = warp_sum(wsum) * tj;
+      for (int i = j + lane; i < r; i += 32) A[i * lda + warp] -= wsum * A[i * lda + j];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (warp < kCK) {  // Q(:, c) = H_0 ... H_c e_c; columns >= k are zero
+    const int c = warp;
+    U q[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int i = lane + 32 * t;
+      q[t] = (c < k && i == c) ? (U)1 : (U)0;
+    }
+    if (c < k) {
+      for (int j = c; j >= 0; --j) {
+        const U tj = tau[j];
+        U wsum = 0;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = lane + 32 * t;
+          if (i >= j && i < r) wsum += A[i * lda + j] * q[t];
+        }
+        wsum = warp_sum(wsum) * tj;
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int i = lane + 32 * t;
+          if (i >= j && i < r) q[t] -= wsum * A[i * lda + j];
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int i = lane + 32 * t;
+      if (i < r) Qout[i * kCK + c] = (T)q[t];
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- 5. one-warp Jacobi
+
+template <typename T>
+__host__ __device__ constexpr T cj_tol() {
+  return sizeof(T) == 4 ? (T)4.8e-7 : (T)8.9e-16;  // 8 unit roundoffs
+}
+template <typename T>
+__host__ __device__ constexpr T cj_floor() {
+  return sizeof(T) == 4 ? (T)1.2e-7 : (T)2.2e-16;  // 2 unit roundoffs
+}
+
+// 1 / sqrt(x) to working precision (one Newton step on the hardware approximation)
+__device__ __forceinline__ float cj_rsqrt(float x) {
+  const float y = rsqrtf(x);
+  return y * fmaf(-0.5f * x * y, y, 1.5f);
+}
+__device__ __forceinline__ double cj_rsqrt(double x) { return 1.0 / sqrt(x); }
+
+// Pair a (0..7) of round t (0..14) of the round-robin schedule on 16 indices.
+__device__ __forceinline__ void cj_pair(int t, int a, int& p, int& q) {
+  int x = t + a, y = t - a + 15;
+  x = x >= 15 ? x - 15 : x;
+  y = y >= 15 ? y - 15 : y;
+  if (a == 0) {
+    x = t;
+    y = 15;
+  }
+  p = min(x, y);
+  q = max(x, y);
+}
+
+// Rotation J = [[c, s], [-s, c]] on (p, q) with (J^T A J)(p, q) = 0, from the half-angle
+// form: with x = a_qq - a_pp, y = 2 a_pq, cos^2(phi) = (1 + |x| / sqrt(x^2 + y^2)) / 2
+// and sin(phi) = sign(x) y / (2 sqrt(x^2 + y^2) cos(phi)) (tan(phi) = t, the root of
+// t^2 + 2 theta t - 1 = 0 of smaller magnitude, theta = x / y).  Both reciprocal square
+// roots are refined to working precision, so c^2 + s^2 = 1 to rounding.
+template <typename T>
+__device__ __forceinline__ void cj_rotation(T app, T aqq, T apq, T tol2, T floor_abs, T& c,
+                                            T& s, bool& rot) {
+  rot = apq * apq > tol2 * fabs(app * aqq) && fabs(apq) > floor_abs;
+  const T x = aqq - app, y = 2 * apq;
+  const T h = fma(x, x, y * y);
+  const T ih = cj_rsqrt(rot ? h : (T)1);
+  const T c2 = fma((T)0.5 * fabs(x), ih, (T)0.5);
+  const T rc = cj_rsqrt(c2);
+  c = rot ? c2 * rc : (T)1;
+  s = rot ? (x >= (T)0 ? y : -y) * ((T)0.5 * ih * rc) : (T)0;
+}
+
+// Symmetric eigen-decomposition of K (16 x 16, row stride kCKs, zero-padded beyond the
+// order) by cyclic Jacobi in the calling warp: K <- V^T K V, V (start: identity) holds
+// the eigenvectors.  A pair rotates when |a_pq| exceeds both tol sqrt(|a_pp a_qq|) and
+// floor max_i |a_ii|; a sweep whose largest |sin| is at most sqrt(tol) ends the loop
+// (quadratic convergence: the next sweep's angles would be ~tol).  Lane L works on pair
+// a = L & 7: every lane forms a's rotation itself, updates the 2 x 2 blocks (a, bj) for
+// the two column pairs bj = 2 (L >> 3) + {0, 1} (their rotations by shuffles from lanes
+// bj) and rows 4 (L >> 3) .. + 3 of V on a's columns.  Returns the buffer holding the
+// diagonalised matrix.
+template <typename T>
+__device__ T* cj_jacobi_warp(T* K, T* K2, T* V, int max_sweeps) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int e = lane; e < kCK * kCK; e += 32) {
+    const int i = e >> 4, j = e & 15;
+    V[i * kCKs + j] = i == j ? (T)1 : (T)0;
+  }
+  T dmax = 0;
+  if (lane < 16) dmax = fabs(K[lane * kCKs + lane]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(kAll, dmax, o));
+  const T tol = cj_tol<T>(), tol2 = tol * tol, floor_abs = cj_floor<T>() * dmax;
+  const float stop_s = sqrtf((float)tol);
+  __syncwarp();
+  T* A = K;
+  T* B = K2;
+  const int a = lane & 7, g = lane >> 3;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    bool any = false;
+    float smax = 0.f;
+    for (int t = 0; t < 15; ++t) {
+      int p, q;
+      cj_pair(t, a, p, q);
+      int pb[2], qb[2];
+      cj_pair(t, 2 * g, pb[0], qb[0]);
+      cj_pair(t, 2 * g + 1, pb[1], qb[1]);
+      // the blocks (a, bj) of the current matrix (independent of the rotations)
+      T blk[2][4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        blk[h][0] = A[p * kCKs + pb[h]];
+        blk[h][1] = A[p * kCKs + qb[h]];
+        blk[h][2] = A[q * kCKs + pb[h]];
+        blk[h][3] = A[q * kCKs + qb[h]];
+      }
+      T vp[4], vq[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        vp[e] = V[(4 * g + e) * kCKs + p];
+        vq[e] = V[(4 * g + e) * kCKs + q];
+      }
+      T c, s;
+      bool rot;
+      cj_rotation<T>(A[p * kCKs + p], A[q * kCKs + q], A[p * kCKs + q], tol2, floor_abs, c, s,
+                     rot);
+      if (rot && lane < 8) {
+        any = true;
+        smax = fmaxf(smax, (float)fabs(s));
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const T cj = __shfl_sync(kAll, c, 2 * g + h), sj = __shfl_sync(kAll, s, 2 * g + h);
+        // (J_a^T B J_bj)
+        const T t00 = c * blk[h][0] - s * blk[h][2], t01 = c * blk[h][1] - s * blk[h][3];
+        const T t10 = s * blk[h][0] + c * blk[h][2], t11 = s * blk[h][1] + c * blk[h][3];
+        B[p * kCKs + pb[h]] = cj * t00 - sj * t01;
+        B[p * kCKs + qb[h]] = sj * t00 + cj * t01;
+        B[q * kCKs + pb[h]] = cj * t10 - sj * t11;
+        B[q * kCKs + qb[h]] = sj * t10 + cj * t11;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        V[(4 * g + e) * kCKs + p] = c * vp[e] - s * vq[e];
+        V[(4 * g + e) * kCKs + q] = s * vp[e] + c * vq[e];
+      }
+      __syncwarp();
+      T* tmp = A;
+      A = B;
+      B = tmp;
+    }
+    any = __any_sync(kAll, any);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) smax = fmaxf(smax, __shfl_xor_sync(kAll, smax, o));
+    if (!any || smax <= stop_s) break;
+  }
+  return A;
+}
+
+// ---------------------------------------------------------------- the kernel
+
+template <typename T, typename U>
+__device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_smem) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int order[kCK];
+  __shared__ T sgn[kCK];
+  __shared__ T* Kfin;
+  constexpr int NWE = ElimShape<T>::NWE, RS = ElimShape<T>::RS;
+  const int r = a.r, s = a.s, k = a.k, R = a.R;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const CholLayout L =
+      chol_layout(r, s, k, R, sizeof(T), sizeof(U), h_smem, a.m_smem, a.m_smem);
+  T* Hs = reinterpret_cast<T*>(smem_raw + L.H);
+  T* Nm = reinterpret_cast<T*>(smem_raw + L.N);
+  T* dinv = reinterpret_cast<T*>(smem_raw + L.dinv);
+  T* Y = reinterpret_cast<T*>(smem_raw + L.Y);
+  U* Cq = reinterpret_cast<U*>(smem_raw + L.C);
+  U* tau = reinterpret_cast<U*>(smem_raw + L.tau);
+  T* Q = reinterpret_cast<T*>(smem_raw + L.Q);
+  T* E = reinterpret_cast<T*>(smem_raw + L.E);
+  T* buf = reinterpret_cast<T*>(smem_raw + L.buf);
+  T* D = (h_smem || L.d_smem) ? reinterpret_cast<T*>(smem_raw + L.D) : a.Mbuf;
+  T* K0 = reinterpret_cast<T*>(smem_raw + L.K0);
+  T* K1 = reinterpret_cast<T*>(smem_raw + L.K1);
+  T* V = reinterpret_cast<T*>(smem_raw + L.V);
+  T* F = reinterpret_cast<T*>(smem_raw + L.F);
+  T* CnTs = reinterpret_cast<T*>(smem_raw + L.CnT);
+  T* Am = (h_smem || L.a_smem) ? reinterpret_cast<T*>(smem_raw + L.Am) : a.A_out;
+  const T* Hsrc = h_smem ? Hs : a.H;
+  const long ldh = h_smem ? s : a.ldh;
+
+  // 1. G = L D L^T with N = L^{-1} and N W, while H streams into shared memory by
+  //    asynchronous copies issued first (waited for before step 5)
+  if (h_smem) {
+    for (int i = 0; i < r; ++i) {
+      const T* src = a.H + (long)i * a.ldh;
+      T* dst = Hs + (long)i * s;
+      for (int j = tid; j < s; j += kCT) {
+        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + j);
+        if constexpr (sizeof(T) == 4)
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + j)
+                       : "memory");
+        else
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src + j)
+                       : "memory");
+      }
+    }
+  }
+  chol_eliminate<T, NWE, RS>(a.G, a.ldg, a.W, a.ldw, r, k, buf, Nm, L.ldn, dinv, Y, a.flag);
+  __syncthreads();
+  // 2. C = N^T D^{-1} (N W)  (staged in Q, then widened into the QR buffer)
+  tri_product<T, true>(Nm, L.ldn, r, dinv, Y, nullptr, Q);
+  __syncthreads();
+  for (int e = tid; e < r * kCK; e += kCT) {
+    const int i = e >> 4, c = e & 15;
+    if (c < k) Cq[i * 17 + c] = (U)Q[e];
+  }
+  __syncthreads();
+  // 3. Q = qr(C)
+  chol_householder<U, T>(Cq, 17, r, k, tau, Q);
+  // 4. E = N^T D^{-1} N Q
+  tri_product<T, false>(Nm, L.ldn, r, nullptr, Q, dinv, Y);
+  __syncthreads();
+  tri_product<T, true>(Nm, L.ldn, r, nullptr, Y, nullptr, E);
+  __syncthreads();
+  // 5. D = E^T H (k x s): a thread per column of H, k sums in registers (D may overwrite
+  //    H's first k rows in place: a thread writes only the column it has read)
+  if (h_smem) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+  }
+  for (int j = tid; j < s; j += kCT) {
+    T acc[kCK];
+#pragma unroll
+    for (int c = 0; c < kCK; ++c) acc[c] = (T)0;
+#pragma unroll 4
+    for (int i = 0; i < r; ++i) {
+      const T hv = Hsrc[(long)i * ldh + j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        T ev[4];
+        V4<T>::ld(E + i * kCK + 4 * q, ev);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[4 * q + e] = fma(ev[e], hv, acc[4 * q + e]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kCK; ++c)
+      if (c < k) D[(long)c * s + j] = acc[c];
+  }
+  __syncthreads();
+  // K = D D^T (upper triangle by warps, mirrored; padded to 16 with zeros)
+  for (int pr = warp; pr < kCK * kCK; pr += kCW) {
+    const int i = pr >> 4, j = pr & 15;
+    if (j < i) continue;
+    T acc = 0;
+    if (i < k && j < k)
+      for (int t = lane; t < s; t += 32) acc = fma(D[(long)i * s + t], D[(long)j * s + t], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      K0[i * kCKs + j] = acc;
+      K0[j * kCKs + i] = acc;
+    }
+  }
+  __syncthreads();
+  // 6. eigen-decomposition of K in warp 0
+  if (warp == 0) {
+    T* Kf = cj_jacobi_warp<T>(K0, K1, V, 20);
+    if (lane == 0) Kfin = Kf;
+  }
+  __syncthreads();
+  const T* Kf = Kfin;
+  if (tid < kCK) order[tid] = tid;  // stays a valid index if a NaN breaks the ranking
+  __syncthreads();
+  // eigenvalues descending (rank by counting; ties keep index order); padded indices
+  // (>= k) rank after the real ones
+  if (tid < kCK) {
+    const bool real = tid < k;
+    const T l = Kf[tid * kCKs + tid];
+    int rank = 0;
+    for (int j = 0; j < kCK; ++j) {
+      const T o = Kf[j * kCKs + j];
+      const bool before = (j < k) ? (!real || o > l || (o == l && j < tid)) : (!real && j < tid);
+      rank += before;
+    }
+    order[rank] = tid;
+    if (real && !isfinite(l) && a.flag) atomicExch(a.flag, 1);
+  }
+  __syncthreads();
+  // F = U_R / sigma (16 x 16 with zero rows >= k and columns >= R), CnT = Q U_R sigma
+  for (int e = tid; e < kCK * kCK; e += kCT) {
+    const int i = e >> 4, c = e & 15;
+    T f = (T)0;
+    if (c < R && i < k) {
+      const T l = Kf[order[c] * kCKs + order[c]];
+      const T sig = l > (T)0 ? sqrt(l) : (T)0;
+      if (sig > (T)0) f = V[i * kCKs + order[c]] / sig;
+    }
+    F[i * kCK + c] = f;
+  }
+  for (int e = tid; e < r * kCK; e += kCT) {
+    const int i = e >> 4, c = e & 15;
+    if (c >= R) continue;
+    const T l = Kf[order[c] * kCKs + order[c]];
+    const T sig = l > (T)0 ? sqrt(l) : (T)0;
+    T acc = 0;
+    for (int b = 0; b < k; ++b) acc = fma(Q[i * kCK + b], V[b * kCKs + order[c]], acc);
+    CnTs[i * R + c] = acc * sig;
+  }
+  __syncthreads();
+  // 7. A = D^T F (unsigned)
+  for (int j = tid; j < s; j += kCT) {
+    T acc[kCK];
+#pragma unroll
+    for (int c = 0; c < kCK; ++c) acc[c] = (T)0;
+    for (int b = 0; b < k; ++b) {
+      const T dv = D[(long)b * s + j];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        T fv[4];
+        V4<T>::ld(F + b * kCK + 4 * q, fv);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc[4 * q + e] = fma(dv, fv[e], acc[4 * q + e]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kCK; ++c)
+      if (c < R) Am[(long)j * R + c] = acc[c];
+  }
+  __syncthreads();
+  // 8. canonical signs (largest-|.| entry of each column of A positive, lowest index on
+  //    ties), then the signed outputs and the core
+  for (int c = warp; c < R; c += kCW) {
+    T best = (T)-1;
+    int bidx = 0x7fffffff;
+    for (int i = lane; i < s; i += 32) {
+      const T v = fabs(Am[(long)i * R + c]);
+      if (v > best || (v == best && i < bidx)) {
+        best = v;
+        bidx = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(kAll, best, o);
+      const int oi = __shfl_xor_sync(kAll, bidx, o);
+      if (ob > best || (ob == best && oi < bidx)) {
+        best = ob;
+        bidx = oi;
+      }
+    }
+    if (lane == 0) sgn[c] = (bidx < s && Am[(long)bidx * R + c] < (T)0) ? (T)-1 : (T)1;
+  }
+  __syncthreads();
+  for (int e = tid; e < s * R; e += kCT) {
+    const int c = e % R;
+    a.A_out[e] = sgn[c] * Am[e];
+  }
+  for (int e = tid; e < r * R; e += kCT) {
+    const int rho = e / R, c = e - rho * R;
+    const T v = sgn[c] * CnTs[e];
+    if (a.CnT) a.CnT[e] = v;
+    if (a.core) {
+      long idx = 0, stride = 1, x = rho;
+      for (int kk = a.map.order - 1; kk >= 0; --kk) {
+        int digit;
+        if (kk == a.map.n) {
+          digit = c;
+        } else {
+          digit = (int)(x % a.map.ranks[kk]);
+          x /= a.map.ranks[kk];
+        }
+        idx += digit * stride;
+        stride *= a.map.ranks[kk];
+      }
+      a.core[idx] = v;
+    }
+  }
+}
+
+template <typename T, typename U>
+__global__ void __launch_bounds__(kCT) k_lrls_chol(FusedArgs<T> a, bool h_smem) {
+  pdl_trigger();
+  pdl_wait();
+  lrls_chol_body<T, U>(a, h_smem);
+}
+
+// ---------------------------------------------------------------- host side
+
+constexpr size_t kCholReserve = 1024;  // static shared memory of the kernel (~0.2 KB), with slack
+
+// Layout of a subproblem: H copied in when it fits (FP32), else D and A in shared
+// memory when they fit, else in global memory.
+static CholLayout chol_pick(int r, int s, int k, int R, size_t tsz, size_t usz) {
+  const size_t cap = kMaxSmem - kCholReserve;
+  if (tsz == 4 && R <= r - k) {
+    CholLayout L = chol_layout(r, s, k, R, tsz, usz, true, false, false);
+    if (L.total <= cap) return L;
+  }
+  CholLayout L = chol_layout(r, s, k, R, tsz, usz, false, true, true);
+  if (L.total <= cap) return L;
+  return chol_layout(r, s, k, R, tsz, usz, false, false, false);
+}
+
+bool lrls_chol_supported(int r, int s, int k, int R, int solve, size_t tsize, bool fp64) {
+  if (solve != TS_SOLVE_RSVD || fp64) return false;
+  if (r < 1 || s < 1 || R < 1 || k < R || k > kCK || r + k > kCMax) return false;
+  if (tsize == 8 ? r > ElimShape<double>::NWE * ElimShape<double>::RS
+                 : r > ElimShape<float>::NWE * ElimShape<float>::RS)
+    return false;
+  return chol_pick(r, s, k, R, tsize, tsize).total <= kMaxSmem - kCholReserve;
+}
+
+template <typename T>
+ts_status launch_lrls_chol(const FusedArgs<T>& in, cudaStream_t st) {
+  FusedArgs<T> a = in;
+  const CholLayout L = chol_pick(a.r, a.s, a.k, a.R, sizeof(T), sizeof(T));
+  a.m_smem = L.d_smem;
+  const bool h = L.h_smem;
+  TS_TRY(ensure_dynamic_smem((const void*)k_lrls_chol<T, T>, L.total));
+  return launch_pdl(k_lrls_chol<T, T>, dim3(1), dim3(kCT), L.total, st, a, h);
+}
+
+template ts_status launch_lrls_chol<float>(const FusedArgs<float>&, cudaStream_t);
+template ts_status launch_lrls_chol<double>(const FusedArgs<double>&, cudaStream_t);
+
+}  // namespace ts

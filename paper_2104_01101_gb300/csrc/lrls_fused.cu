@@ -947,6 +947,27 @@ template <typename T>
 ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, const T* G,
                             long ldg, const T* W, long ldw, const T* H, long ldh, T* Mbuf, T* CnT,
                             T* A_out, T* core, CoreMap map, int* flag, cudaStream_t st) {
+  if (lrls_chol_supported(r, s, k, R, solve, sizeof(T), fp64)) {
+    FusedArgs<T> c{};
+    c.r = r;
+    c.s = s;
+    c.k = k;
+    c.R = R;
+    c.solve = solve;
+    c.G = G;
+    c.ldg = ldg;
+    c.W = W;
+    c.ldw = ldw;
+    c.H = H;
+    c.ldh = ldh;
+    c.Mbuf = Mbuf;
+    c.CnT = CnT;
+    c.A_out = A_out;
+    c.core = core;
+    c.map = map;
+    c.flag = flag;
+    return launch_lrls_chol<T>(c, st);
+  }
   FusedArgs<T> a;
   size_t smem = 0;
   TS_TRY(make_fused_args<T>(r, s, k, R, solve, fp64, G, ldg, W, ldw, H, ldh, Mbuf, CnT, A_out,

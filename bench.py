@@ -445,6 +445,9 @@ def main():
     ap.add_argument("--sparse-only", action="store_true",
                     help="run only the sparse 4-way measurement and print its JSON object "
                          "(for profiling that workload alone)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched-form measurement (256 small tensors) and print "
+                         "its JSON object (for profiling that workload alone)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -454,6 +457,12 @@ def main():
     if args.sparse_only:
         import torch
         print(json.dumps(time_sparse(args, torch.device("cuda:0"))), flush=True)
+        return
+    if args.batched_only:
+        import torch
+        dev = torch.device("cuda:0")
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+        print(json.dumps(time_batched(args, dev, flush)), flush=True)
         return
     if world > 1:
         import torch

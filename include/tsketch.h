@@ -378,6 +378,27 @@ ts_status cp_via_tucker(const ts_tensor* X, int32_t R_cp, const int32_t* tucker_
                         double* residual_out, ts_stream stream);
 
 /* ------------------------------------------------------------------------- */
+/* CP-ALS on a dense Tucker core: the inner step of Alg. 6 (CP decomposition of the
+ * core produced by the sketched Tucker-ALS), exposed on its own so that it can be run
+ * on any core.  The factors start from the HOSVD of the core (Sec. 7.2: the leading
+ * R_cp left singular vectors of each unfolding, each column signed so that its
+ * largest-magnitude entry is positive), then `sweeps` sweeps of Alg. 2 update every
+ * factor by the normal equations: A^(n) = C_(n) KR_n (*_{k != n} A^(k)T A^(k))^{-1},
+ * KR_n the Khatri-Rao product of the other factors (first factor slowest), the R_cp x
+ * R_cp system solved in FP64 by Cholesky.  core: prod(ranks) values in C order (dtype
+ * TS_F32 or TS_F64, DEVICE); factors_out: HOST array of `order` DEVICE pointers,
+ * ranks[k] x R_cp row-major, overwritten.  R_cp <= min(ranks) (the HOSVD start).
+ * Scratch: ts_cp_als_scratch_bytes (256-byte aligned); its first int32 is a device flag
+ * set to non-zero when a Gram system is not positive definite (read it after the call).
+ * Errors: TS_ERR_SHAPE for an order outside [2, TS_MAX_ORDER], non-positive ranks,
+ * R_cp < 1 or R_cp > min(ranks), sweeps < 0; TS_ERR_WORKSPACE for short or misaligned
+ * scratch. */
+size_t ts_cp_als_scratch_bytes(int32_t order, const int32_t* ranks, int32_t R_cp, int32_t dtype);
+ts_status ts_cp_als(int32_t order, const int32_t* ranks, int32_t R_cp, int32_t sweeps,
+                    int32_t dtype, const void* core, void* const* factors_out, void* scratch,
+                    size_t scratch_bytes, ts_stream stream);
+
+/* ------------------------------------------------------------------------- */
 /* Gradient of the sketched fit of subproblem `mode` (the objective that each step of
  * Alg. 4 minimises: eq. (tucker_ls) with the TensorSketch of Sec. 3.1 applied):
  *   L = 1/2 || Z C_(mode)^T A^(mode)T - Y ||_F^2,
@@ -391,6 +412,8 @@ ts_status cp_via_tucker(const ts_tensor* X, int32_t R_cp, const int32_t* tucker_
  * device pointers, dims[k] x ranks[k] row-major), tables (HOST array of `order` device
  * pointers, tables[mode] ignored), Y.  Outputs: loss (DEVICE, one double), grad_core
  * (prod ranks), grad_factors (HOST array of `order` device pointers, dims[k] x ranks[k]).
+ * grad_core and grad_factors may both be NULL: then only the loss is computed (the
+ * backward products and the adjoint of the FFT chain are skipped).
  * Errors: TS_ERR_SHAPE for an order outside [2, TS_MAX_ORDER], a mode out of range,
  * m outside [2, FFT limit] or non-positive sizes; TS_ERR_WORKSPACE for short or
  * misaligned scratch (ts_fit_grad_scratch_bytes; 0 for invalid shapes). */

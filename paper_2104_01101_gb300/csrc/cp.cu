@@ -261,3 +261,48 @@ TS_INST(double)
 #undef TS_INST
 
 }  // namespace ts
+
+using namespace ts;
+
+static bool cp_als_shape_ok(int32_t order, const int32_t* ranks, int32_t R_cp, int32_t dtype) {
+  if (order < 2 || order > TS_MAX_ORDER || !ranks || R_cp < 1) return false;
+  if (dtype != TS_F32 && dtype != TS_F64) return false;
+  for (int k = 0; k < order; ++k)
+    if (ranks[k] < 1 || R_cp > ranks[k]) return false;
+  return true;
+}
+
+extern "C" size_t ts_cp_als_scratch_bytes(int32_t order, const int32_t* ranks, int32_t R_cp,
+                                          int32_t dtype) {
+  if (!cp_als_shape_ok(order, ranks, R_cp, dtype)) return 0;
+  const size_t e = dtype == TS_F64 ? cp_core_scratch_elems<double>(order, ranks, R_cp) * 8
+                                   : cp_core_scratch_elems<float>(order, ranks, R_cp) * 4;
+  return 256 + e;
+}
+
+extern "C" ts_status ts_cp_als(int32_t order, const int32_t* ranks, int32_t R_cp, int32_t sweeps,
+                               int32_t dtype, const void* core, void* const* factors_out,
+                               void* scratch, size_t scratch_bytes, ts_stream stream) {
+  clear_error();
+  if (!cp_als_shape_ok(order, ranks, R_cp, dtype) || sweeps < 0)
+    return fail(TS_ERR_SHAPE, "ts_cp_als: order %d, R_cp %d, sweeps %d (R_cp <= every rank)",
+                order, R_cp, sweeps);
+  if (!core || !factors_out || !scratch)
+    return fail(TS_ERR_INVALID_ARG, "ts_cp_als: NULL argument");
+  for (int k = 0; k < order; ++k)
+    if (!factors_out[k]) return fail(TS_ERR_INVALID_ARG, "ts_cp_als: NULL factor %d", k);
+  const size_t need = ts_cp_als_scratch_bytes(order, ranks, R_cp, dtype);
+  if (scratch_bytes < need || (reinterpret_cast<uintptr_t>(scratch) & 255))
+    return fail(TS_ERR_WORKSPACE, "ts_cp_als: need %zu bytes of 256-aligned scratch", need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int* flag = static_cast<int*>(scratch);
+  TS_CUDA(cudaMemsetAsync(flag, 0, 256, st));
+  char* rest = static_cast<char*>(scratch) + 256;
+  if (dtype == TS_F64)
+    return cp_als_core<double>(order, ranks, R_cp, sweeps, static_cast<const double*>(core),
+                               reinterpret_cast<double* const*>(factors_out),
+                               reinterpret_cast<double*>(rest), flag, st);
+  return cp_als_core<float>(order, ranks, R_cp, sweeps, static_cast<const float*>(core),
+                            reinterpret_cast<float* const*>(factors_out),
+                            reinterpret_cast<float*>(rest), flag, st);
+}

@@ -141,7 +141,7 @@ ts_status fit_grad_impl(const GradShape& g, const T* core, const T* const* A,
       ctab[nf] = tables[k];
       rows[nf] = g.dims[k];
       cols[nf] = g.ranks[k];
-      gchain[nf] = grad_A[k];
+      gchain[nf] = grad_A ? grad_A[k] : nullptr;
       ++nf;
     }
   // Z = S P (and the factor spectra, kept for the adjoint)
@@ -165,6 +165,7 @@ ts_status fit_grad_impl(const GradShape& g, const T* core, const T* const* A,
   k_half_sumsq<T><<<(int)std::min<long>(1024, ((long)m * s + 255) / 256), 256, 0, st>>>(
       (long)m * s, w.R, loss);
   TS_LAUNCH_CHECK();
+  if (!grad_core) return TS_OK;  // the loss alone
   // W = Z^T R (r x s);  dA^(n) = W^T C_(n)^T;  dC_(n)^T = W A^(n)
   TS_TRY(gemm<T>((int)r, (int)s, m, 1.0, view<T>(w.Z, m, 1), view<T>(w.R, s, 1), 0.0,
                  oview<T>(w.W, s, 1), nullptr, st));
@@ -247,10 +248,13 @@ extern "C" ts_status ts_fit_grad(int32_t order, const int64_t* dims, const int32
   clear_error();
   GradShape g;
   TS_TRY(grad_shape(order, dims, ranks, mode, m, dtype, g));
-  if (!core || !factors || !tables || !Y || !loss || !grad_core || !grad_factors)
+  if (!core || !factors || !tables || !Y || !loss)
     return fail(TS_ERR_INVALID_ARG, "ts_fit_grad: NULL argument");
+  if (!grad_core != !grad_factors)
+    return fail(TS_ERR_INVALID_ARG, "ts_fit_grad: grad_core and grad_factors must both be "
+                                    "given or both be NULL");
   for (int k = 0; k < order; ++k) {
-    if (!factors[k] || !grad_factors[k])
+    if (!factors[k] || (grad_factors && !grad_factors[k]))
       return fail(TS_ERR_INVALID_ARG, "ts_fit_grad: factor %d or its gradient NULL", k);
     if (k != mode && !tables[k]) return fail(TS_ERR_INVALID_ARG, "ts_fit_grad: table %d NULL", k);
   }

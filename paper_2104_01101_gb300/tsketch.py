@@ -90,6 +90,8 @@ _PROTOS = {
     "tucker_als_sketched": (I32, [TP, C.POINTER(I32), I32, I32, I32, OP, P, SZ, P, PP, P, P]),
     "cp_via_tucker_workspace_bytes": (I32, [TP, I32, C.POINTER(I32), I32, I32, OP, C.POINTER(SZ)]),
     "cp_via_tucker": (I32, [TP, I32, C.POINTER(I32), I32, I32, I32, OP, P, SZ, PP, P, P]),
+    "ts_cp_als_scratch_bytes": (SZ, [I32, C.POINTER(I32), I32, I32]),
+    "ts_cp_als": (I32, [I32, C.POINTER(I32), I32, I32, I32, P, PP, P, SZ, P]),
     "ts_fit_grad_scratch_bytes": (SZ, [I32, C.POINTER(I64), C.POINTER(I32), I32, I32, I32]),
     "ts_fit_grad": (I32, [I32, C.POINTER(I64), C.POINTER(I32), I32, I32, I32, P, PP, PP, P, P, P,
                           PP, P, SZ, P]),
@@ -447,9 +449,10 @@ class TuckerPlan:
         return int(self.workspace[:4].view(torch.int32).item())
 
 
-def fit_grad(core, factors, Y, tables, mode: int, m: int):
+def fit_grad(core, factors, Y, tables, mode: int, m: int, want_grad: bool = True):
     """Sketched fit of subproblem ``mode`` and its gradient (ts_fit_grad):
-    returns (loss float64 0-dim tensor, grad_core, [grad of every factor]).
+    returns (loss float64 0-dim tensor, grad_core, [grad of every factor]); with
+    ``want_grad=False`` only the loss is computed (the gradients are None).
     ``tables``: one packed int32 device table per mode (the entry of ``mode`` is ignored,
     may be None)."""
     N = len(factors)
@@ -464,12 +467,14 @@ def fit_grad(core, factors, Y, tables, mode: int, m: int):
     factors = [f.contiguous() for f in factors]
     Y = Y.contiguous()
     loss = torch.zeros((), dtype=torch.float64, device=core.device)
-    gcore = torch.empty_like(core)
-    gfac = [torch.empty_like(f) for f in factors]
+    gcore = torch.empty_like(core) if want_grad else None
+    gfac = [torch.empty_like(f) for f in factors] if want_grad else None
     tabs = [t if t is not None else factors[0] for t in tables]  # mode's entry ignored
     _check(lib().ts_fit_grad(N, dims, rk, mode, m, dtype, _ptr(core), _ptr_array(factors),
-                             _ptr_array(tabs), _ptr(Y), _ptr(loss), _ptr(gcore),
-                             _ptr_array(gfac), _ptr(scr), scr.numel(), _stream()))
+                             _ptr_array(tabs), _ptr(Y), _ptr(loss),
+                             _ptr(gcore) if want_grad else None,
+                             _ptr_array(gfac) if want_grad else None, _ptr(scr), scr.numel(),
+                             _stream()))
     return loss, gcore, gfac
 
 
@@ -480,8 +485,10 @@ class SketchedFit(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, Y, tables, mode, m, core, *factors):
-        loss, gcore, gfac = fit_grad(core, list(factors), Y, tables, mode, m)
-        ctx.save_for_backward(gcore, *gfac)
+        want = any(ctx.needs_input_grad[4:])  # the gradients only when autograd needs them
+        loss, gcore, gfac = fit_grad(core, list(factors), Y, tables, mode, m, want_grad=want)
+        if want:
+            ctx.save_for_backward(gcore, *gfac)
         return loss.to(core.dtype)
 
     @staticmethod
@@ -588,6 +595,25 @@ def cp_via_tucker(X, R_cp: int, tucker_ranks, m: int, tucker_sweeps: int, cp_swe
     if int(ws[:4].view(torch.int32).item()) != 0:
         raise TsError(6, "numerical breakdown flagged by the device")
     return outs, (float(res.item()) if want_residual else None)
+
+
+def cp_als(core, R_cp: int, sweeps: int):
+    """CP-ALS on a dense core (ts_cp_als: HOSVD start, Alg. 2 sweeps): returns the factors
+    [ranks[k] x R_cp]; raises TsError if a Gram system was flagged (synchronises)."""
+    core = core.contiguous()
+    order = core.dim()
+    rk = (C.c_int32 * order)(*core.shape)
+    dt = _dt(core)
+    nbytes = lib().ts_cp_als_scratch_bytes(order, rk, R_cp, dt)
+    if nbytes == 0:
+        raise TsError(2, "ts_cp_als: invalid shape")
+    scr = _scratch(nbytes, core.device)
+    outs = [torch.empty((int(r), R_cp), dtype=core.dtype, device=core.device) for r in core.shape]
+    _check(lib().ts_cp_als(order, rk, R_cp, sweeps, dt, _ptr(core), _ptr_array(outs), _ptr(scr),
+                           scr.numel(), _stream()))
+    if int(scr[:4].view(torch.int32).item()) != 0:
+        raise TsError(6, "CP-ALS: Gram system not positive definite")
+    return outs
 
 
 def tucker_als_sketched(X, ranks, m: int, sweeps: int, kind=TENSORSKETCH, seed: int = 0,

@@ -75,6 +75,32 @@ def test_batch_fp32_equals_single_tensor_driver(ts):
     b.close()
 
 
+def test_batch_fp32_matches_oracle(ts):
+    # 8 FP32 tensors of the batched workload's kind (uneven shapes and ranks, m = 8 R^2,
+    # noise 1e-2) against the FP64 oracle run on each tensor's FP32 values with the same
+    # seed: residuals and factor projectors at the FP32 tolerances of the single-tensor
+    # tests.
+    tensors, ranks, ms = batch_case(8, 6, np.float32, hi=96, rhi=9)
+    sweeps, seed = 4, 21
+    b = ts.TuckerBatch([torch.from_numpy(T).cuda() for T in tensors], ranks, ms, sweeps,
+                       seed=seed)
+    b.sweeps()
+    res = b.residual().cpu().numpy()
+    assert b.flags() == [0] * len(tensors)
+    worst_r, worst_p = 0.0, 0.0
+    for i, T in enumerate(tensors):
+        T64 = T.astype(np.float64)
+        c_o, f_o, _ = tucker.sketch_tucker_als(T64, ranks[i], ms[i], sweeps, seed=seed + i)
+        r_o = tucker.residual(T64, c_o, f_o)
+        worst_r = max(worst_r, abs(res[i] - r_o) / r_o)
+        for n in range(3):
+            worst_p = max(worst_p, np.abs(proj(b.factors[i][n].double().cpu().numpy()) -
+                                          proj(f_o[n])).max())
+    print({"residual": worst_r, "projector": worst_p})
+    assert worst_r <= 1e-5 and worst_p <= 1e-4
+    b.close()
+
+
 def test_batch_sweeps_replay_as_a_cuda_graph(ts):
     tensors, ranks, ms = batch_case(6, 3, np.float32)
     Tg = [torch.from_numpy(T).cuda() for T in tensors]

@@ -8,6 +8,8 @@ import torch
 from oracle import grad, rng, sketch
 from paper_2104_01101_gb300 import synth
 
+from bounds import U32, fit_grad_abs, fit_grad_depth
+
 pytestmark = pytest.mark.gpu
 
 
@@ -45,12 +47,24 @@ def test_fit_grad_matches_oracle(ts, dims, ranks, n, m, dtype):
     L_o, gc_o, gA_o = grad.sketched_fit_grad(core, fac, Y, host_tabs, n, m)
     cast = lambda a: torch.from_numpy(a).to(dtype).cuda()
     L, gc, gA = ts.fit_grad(cast(core), [cast(f) for f in fac], cast(Y), dev_tabs, n, m)
-    tol = 1e-10 if dtype == torch.float64 else 2e-4
-    assert abs(float(L) - L_o) <= tol * L_o
-    assert np.linalg.norm(gc.double().cpu().numpy() - gc_o) <= tol * np.linalg.norm(gc_o)
+    if dtype == torch.float64:
+        tol = 1e-10
+        assert abs(float(L) - L_o) <= tol * L_o
+        assert np.linalg.norm(gc.double().cpu().numpy() - gc_o) <= tol * np.linalg.norm(gc_o)
+        for k in range(len(dims)):
+            d = np.linalg.norm(gA[k].double().cpu().numpy() - gA_o[k])
+            assert d <= tol * np.linalg.norm(gA_o[k])
+        return
+    # FP32: the gradient sums terms of both signs (Z^T R, and R = Z M - Y itself), so its
+    # error is relative to the same chain run on absolute values, not to the gradient:
+    # first order, ||error|| <= depth u ||gradient of |.| chain|| with depth the roundings
+    # along the longest chain (m terms in Z^T R dominate at m = 3000)
+    assert abs(float(L) - L_o) <= 1e-5 * L_o
+    gc_b, gA_b = fit_grad_abs(core, fac, Y, host_tabs, n, m)
+    c = fit_grad_depth(dims, ranks, n, m) * U32
+    assert np.linalg.norm(gc.double().cpu().numpy() - gc_o) <= c * np.linalg.norm(gc_b)
     for k in range(len(dims)):
-        d = np.linalg.norm(gA[k].double().cpu().numpy() - gA_o[k])
-        assert d <= tol * np.linalg.norm(gA_o[k])
+        assert np.linalg.norm(gA[k].double().cpu().numpy() - gA_o[k]) <= c * np.linalg.norm(gA_b[k])
 
 
 def test_fit_grad_central_differences_on_a_30_cube_slice(ts):
@@ -109,3 +123,27 @@ def test_autograd_function_backward(ts):
     assert np.abs(core.grad.cpu().numpy() - 3.0 * gc_o).max() <= 1e-9 * np.abs(gc_o).max()
     for k in range(3):
         assert np.abs(fac[k].grad.cpu().numpy() - 3.0 * gA_o[k]).max() <= 1e-9 * np.abs(gA_o[k]).max()
+
+
+def test_loss_only_call_skips_the_gradient(ts):
+    # Without requires_grad the autograd function asks the library for the loss alone
+    # (null gradient outputs: no backward products, no adjoint FFT chain); the loss is the
+    # same as the one computed with the gradients.
+    dims, ranks, n, m = (10, 9, 8), (3, 2, 3), 1, 50
+    g = np.random.default_rng(2)
+    host_tabs, dev_tabs = tables_for(dims, n, m)
+    Y = torch.from_numpy(g.standard_normal((m, dims[n]))).cuda()
+    core = torch.from_numpy(g.standard_normal(ranks)).cuda()
+    fac = [torch.from_numpy(g.standard_normal((s, R))).cuda() for s, R in zip(dims, ranks)]
+    l0 = ts.kernel_launches()
+    L = ts.sketched_fit(core, fac, Y, dev_tabs, n, m)
+    loss_only = ts.kernel_launches() - l0
+    l0 = ts.kernel_launches()
+    L2, gc, _ = ts.fit_grad(core, fac, Y, dev_tabs, n, m)
+    with_grad = ts.kernel_launches() - l0
+    assert loss_only < with_grad
+    assert abs(float(L) - float(L2)) <= 1e-12 * abs(float(L2))
+    L_o = grad.sketched_fit(core.cpu().numpy(), [f.cpu().numpy() for f in fac], Y.cpu().numpy(),
+                            host_tabs, n, m)
+    assert abs(float(L) - L_o) <= 1e-10 * L_o
+

@@ -8,6 +8,9 @@ import oracle
 from oracle import rng, sketch, solve, tucker
 from paper_2104_01101_gb300 import synth
 
+from bounds import (U32, U64, input_sketch_coo_terms, input_sketch_terms, summation_bound,
+                    ts_fft_column_bound, unit_tables)
+
 pytestmark = pytest.mark.gpu
 
 
@@ -70,6 +73,9 @@ def test_tensorsketch_apply_matches_explicit_kronecker(ts, dims, ranks, m, dtype
                               [dev(rng.pack_table(*t)) for t in tabs], m).cpu().numpy()
     tol = 1e-12 if dtype == torch.float64 else 1e-5
     assert np.linalg.norm(Z - want) <= tol * np.linalg.norm(want)
+    # element-wise: every entry within the FFT-convolution bound of its column
+    u = U64 if dtype == torch.float64 else U32
+    assert np.all(np.abs(Z - want) <= ts_fft_column_bound(factors, tabs, m, u))
 
 
 # ---------------------------------------------------------------- a4 input sketch
@@ -84,11 +90,19 @@ def test_input_sketch_dense(ts, dims, m, dtype):
         tabs = packed_tables(7, dims, n, m)
         Y = ts.tensorsketch_input(Tg, n, [tabs[k][2] if k in tabs else None
                                           for k in range(len(dims))], m).cpu().numpy()
-        want = sketch.input_sketch_dense(T.astype(np.float64) if dtype == torch.float64
-                                         else T.astype(np.float32).astype(np.float64),
-                                         n, [tabs[k][:2] for k in sorted(tabs)], m)
+        Tx = T.astype(np.float64) if dtype == torch.float64 else \
+            T.astype(np.float32).astype(np.float64)
+        host = [tabs[k][:2] for k in sorted(tabs)]
+        want = sketch.input_sketch_dense(Tx, n, host, m)
         tol = 1e-12 if dtype == torch.float64 else 1e-5
         assert np.linalg.norm(Y - want) <= tol * np.linalg.norm(want)
+        # element-wise: any-order summation of each bin's terms, plus (FP32, first mode of
+        # an order-3 tensor) the fixed-point quantisation of at most max|T slice| 2^-19 a term
+        absY, cnt = input_sketch_terms(Tx, n, host, m)
+        bound = summation_bound(absY, cnt, U64 if dtype == torch.float64 else U32)
+        if dtype == torch.float32 and n == 0 and len(dims) == 3:
+            bound = bound + cnt * np.abs(Tx).reshape(dims[0], -1).max(axis=1)[None, :] * 2.0 ** -19
+        assert np.all(np.abs(Y - want) <= bound + 1e-300)
 
 
 @pytest.mark.parametrize("case", ["late_spikes", "scaled_slices", "one_bucket_tables"])
@@ -119,6 +133,9 @@ def test_input_sketch_dense_fixed_point_edges(ts, case):
                                         [(tabs[k][0], np.ones_like(tabs[k][1])) for k in (1, 2)], m)
     for i in range(dims[0]):
         assert np.linalg.norm(Y[:, i] - want[:, i]) <= 1e-5 * np.linalg.norm(ref[:, i])
+    absY, cnt = input_sketch_terms(T.astype(np.float64), 0, [tabs[1][:2], tabs[2][:2]], m)
+    quant = cnt * np.abs(T).reshape(dims[0], -1).max(axis=1)[None, :].astype(np.float64) * 2.0 ** -19
+    assert np.all(np.abs(Y - want) <= summation_bound(absY, cnt, U32) + quant)
 
 
 def test_input_sketch_dense_full_size_sampled_columns(ts):
@@ -132,11 +149,18 @@ def test_input_sketch_dense_full_size_sampled_columns(ts):
         tabs = packed_tables(9, dims, n, m)
         Y = ts.tensorsketch_input(Tg, n, [tabs[k][2] if k in tabs else None for k in range(3)], m)
         Y = Y.cpu().numpy().astype(np.float64)
-        S = sketch.tensorsketch_sparse([tabs[k][:2] for k in sorted(tabs)], m)
+        host = [tabs[k][:2] for k in sorted(tabs)]
+        S = sketch.tensorsketch_sparse(host, m)
+        Su = sketch.tensorsketch_sparse(unit_tables(host), m)
         for i in (0, 17, 399):
             slab = np.take(T, i, axis=n).astype(np.float64).reshape(-1)
             want = S @ slab
             assert np.linalg.norm(Y[:, i] - want) <= 1e-5 * np.linalg.norm(want)
+            cnt = Su @ np.ones_like(slab)
+            bound = cnt * U32 * (Su @ np.abs(slab))
+            if n == 0:  # fixed-point buckets of the first mode
+                bound = bound + cnt * np.abs(slab).max() * 2.0 ** -19
+            assert np.all(np.abs(Y[:, i] - want) <= bound)
 
 
 def test_input_sketch_coo_full_size_sampled_columns(ts):
@@ -162,6 +186,9 @@ def test_input_sketch_coo_full_size_sampled_columns(ts):
                                             [(b, np.ones_like(sg)) for b, sg in host_tabs], m)[:, 0]
             got = Y[:, i].double().cpu().numpy()
             assert np.linalg.norm(got - want) <= 1e-5 * max(np.linalg.norm(scale), 1e-30)
+            cnt = sketch.input_sketch_coo(sub_idx, np.ones(sub_vals.shape[0]), d1, n,
+                                          [(b, np.ones_like(sg)) for b, sg in host_tabs], m)[:, 0]
+            assert np.all(np.abs(got - want) <= cnt * U32 * scale)
         del Y
 
 
@@ -179,6 +206,10 @@ def test_input_sketch_coo_with_duplicates_and_empty(ts, dtype):
                                        dims, n, [tabs[k][:2] for k in sorted(tabs)], m)
         tol = 1e-12 if dtype == torch.float64 else 1e-5
         assert np.linalg.norm(Y.cpu().numpy() - want) <= tol * np.linalg.norm(want)
+        vx = vals if dtype == torch.float64 else vals.astype(np.float32).astype(np.float64)
+        absY, cnt = input_sketch_coo_terms(idx, vx, dims, n, [tabs[k][:2] for k in sorted(tabs)], m)
+        u = U64 if dtype == torch.float64 else U32
+        assert np.all(np.abs(Y.cpu().numpy() - want) <= summation_bound(absY, cnt, u) + 1e-300)
     empty = ts.Coo(torch.zeros((4, 0), dtype=torch.int32, device="cuda"),
                    torch.zeros(0, dtype=dtype, device="cuda"), dims)
     tabs = packed_tables(3, dims, 0, m)
@@ -256,19 +287,25 @@ def test_rsvd_lrls_wide_s_matches_oracle(ts, m, r, s, R, k, dtype):
     assert np.linalg.norm(Bg - Bw) <= tol * np.linalg.norm(Bw)
 
 
-@pytest.mark.parametrize("m,r,s,R", [(2048, 256, 3000, 8), (3000, 625, 300, 25)])
-def test_rsvd_lrls_large_r_matches_oracle(ts, m, r, s, R):
-    # r too large for the on-chip Cholesky: G^{-1} by Newton-Schulz products
+@pytest.mark.parametrize("dtype,m,r,s,R", [(torch.float32, 2048, 256, 3000, 8),
+                                           (torch.float32, 3000, 625, 300, 25),
+                                           (torch.float64, 2048, 256, 3000, 8),
+                                           (torch.float64, 3000, 512, 2000, 8)])
+def test_rsvd_lrls_large_r_matches_oracle(ts, dtype, m, r, s, R):
+    # r too large for the on-chip factorization: G^{-1} by Newton-Schulz products, whose
+    # early stop must leave the inverse at the rounding floor (FP64: 1e-11 as the other
+    # FP64 solves; r = 512 is the largest FP64 core whose QR fits one block)
     Z, Y = _solve_problem(6, m, r, s, R, 0.05)
-    Z = Z.astype(np.float32).astype(np.float64)
-    Y = Y.astype(np.float32).astype(np.float64)
+    if dtype == torch.float32:
+        Z = Z.astype(np.float32).astype(np.float64)
+        Y = Y.astype(np.float32).astype(np.float64)
     k = solve.rsvd_oversampled_rank(R, 5, r, s)
     Om = rng.gaussian(5, rng.make_tag(4, 0, 2, 0), s * k).reshape(s, k)
     Cw, Aw = solve.rsvd_lrls(Z, Y, R, Om)
-    Cg, Ag = ts.lrls_solve(dev(Z, torch.float32), dev(Y, torch.float32), R, ts.SOLVE_RSVD, seed=5,
-                           sweep=0, n=2)
+    Cg, Ag = ts.lrls_solve(dev(Z, dtype), dev(Y, dtype), R, ts.SOLVE_RSVD, seed=5, sweep=0, n=2)
     Bw, Bg = Cw @ Aw.T, Cg.cpu().numpy() @ Ag.cpu().numpy().T
-    assert np.linalg.norm(Bg - Bw) <= 1e-5 * np.linalg.norm(Bw)
+    tol = 1e-5 if dtype == torch.float32 else 1e-11
+    assert np.linalg.norm(Bg - Bw) <= tol * np.linalg.norm(Bw)
 
 
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])

@@ -33,6 +33,10 @@ WORKLOAD = ("dense 400x400x400 FP32 Tucker rank (10,10,10), core N(0,1)*0.9^(i+j
             "orthonormal factors, noise 1e-2; TensorSketch m=2000; RRF init k1=15; "
             "RSVD-LRLS (p=5); 10 sweeps")
 METRIC = "sketched Tucker-ALS sweeps/sec"
+# The precision form of the method: BF16 Gram products with FP32 accumulation, FP32
+# sketches, FP64 for the QR of the small system's range basis and the SVD of the rank
+# truncation.
+PRECISION_FORM = "BF16 Gram products on tcgen05 + FP64 QR/SVD"
 # The batched form (many independent tensors per launch): mode sizes uniform in
 # [32, 160], one rank R uniform in [4, 12] per tensor, m = 8 R^2, noise 1e-2.
 BATCH_COUNT, BATCH_SIZES, BATCH_RANKS, BATCH_SWEEPS, BATCH_SEED = 256, (32, 160), (4, 12), 5, 11
@@ -333,11 +337,15 @@ def run_ours(args, rank, world):
 
     forms = {"plain FP32": time_form(False),
              "BF16 Gram products on tcgen05 + FP32 solve": time_form(False, True),
-             "FP32 + FP64 QR/SVD": time_form(True)}
-    # chosen form: the fastest whose final residual is within 1e-3 (absolute) of plain FP32
+             "FP32 + FP64 QR/SVD": time_form(True),
+             PRECISION_FORM: time_form(True, True)}
+    # chosen form: among the forms that keep FP64 for the QR of the small system and the
+    # SVD of the rank truncation, the fastest whose final residual is within 1e-3
+    # (absolute) of plain FP32's
     base_res = forms["plain FP32"]["residual"]
-    ok = {k: v for k, v in forms.items() if abs(v["residual"] - base_res) <= 1e-3}
-    chosen = min(ok, key=lambda k: statistics.mean(ok[k]["step"]))
+    ok = {k: v for k, v in forms.items()
+          if k.endswith("FP64 QR/SVD") and abs(v["residual"] - base_res) <= 1e-3}
+    chosen = min(ok, key=lambda k: statistics.mean(ok[k]["step"])) if ok else "plain FP32"
     R = forms[chosen]
     plan = R["plan"]
     step_ms, rrf_ms, sketch_ms, sweeps_ms = R["step"], R["rrf"], R["sketch"], R["sweeps"]
@@ -376,9 +384,12 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": job_sweeps_per_s(world, ms), "unit": "sweeps/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16+f32" if chosen.startswith("BF16") else "f32",
+        "dtype": ("bf16+f32" if chosen.startswith("BF16") else "f32")
+                 + ("+f64" if chosen.endswith("FP64 QR/SVD") else ""),
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": chosen,
+                   "chosen_among": "forms with FP64 QR/SVD whose residual is within 1e-3 of "
+                                   "plain FP32's (fastest)",
                    "flush": "256 MB L2 flush between steps; tensor 256 MB > L2",
                    "parallelism": f"replicas x{world}", "graph": "captured once, replayed"},
         "residual": residual,
@@ -407,7 +418,10 @@ def run_ours(args, rank, world):
         line["sparse"] = time_sparse(args, dev)
     if not args.no_cpu_baseline:
         T64 = T.astype(np.float64)
-        dt, _ = cpu_oracle_step(T64)
+        dt, res_oracle = cpu_oracle_step(T64)
+        line["oracle_residual"] = res_oracle
+        for k, v in line["forms"].items():
+            v["residual_minus_oracle"] = v["residual"] - res_oracle
         line["cpu_baseline"] = {"value": SWEEPS / dt, "unit": "sweeps/s", "cores": cores(),
                                 "kind": "oracle",
                                 "sample": "one complete FP64 numpy decomposition of the full "

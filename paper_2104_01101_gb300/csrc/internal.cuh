@@ -284,10 +284,11 @@ ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, co
                             long ldg, const T* W, long ldw, const T* H, long ldh, T* Mbuf, T* CnT,
                             T* A_out, T* core, CoreMap map, int* flag, cudaStream_t st);
 // lrls_chol.cu: the RSVD subproblem by symmetric elimination of [G | W] in registers
-// (r <= 128, k <= 16); the same arguments as the fused solve (m_smem is recomputed).
+// (r + k <= 128, k <= 16); the same arguments as the fused solve (m_smem is recomputed);
+// fp64 (FP32 data): the precision form, the QR of C and K's eigen-decomposition in FP64.
 bool lrls_chol_supported(int r, int s, int k, int R, int solve, size_t tsize, bool fp64);
 template <typename T>
-ts_status launch_lrls_chol(const FusedArgs<T>& a, cudaStream_t st);
+ts_status launch_lrls_chol(const FusedArgs<T>& a, bool fp64, cudaStream_t st);
 // Factor columns V (s x R) with V(i, c) = sum_a M(i, a) Fm(a, c) (M element (i, a) at
 // M[i*rs + a*cs], a < kdim), or V(i, c) = M[i*rs + c*cs] when Fm is null.  Each
 // column is signed so that its largest-|.| entry is positive; A_out = V; CnT (r x R)

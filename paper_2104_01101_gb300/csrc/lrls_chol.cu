@@ -80,16 +80,21 @@ __host__ __device__ inline CholLayout chol_layout(int r, int s, int k, int R, si
     L.D = take(d_smem ? tsz * (size_t)k * s : 0);
     L.Am = take(a_smem ? tsz * (size_t)s * R : 0);
   }
-  L.N = take(tsz * (size_t)r * L.ldn);
+  // N is dead after step 4: the FP64 eigen refinement's workspace (3 16 x 17 + 16
+  // doubles) reuses it; Y is dead during the QR: the FP64 Gram (16 x 17 + 16 doubles)
+  const size_t n_bytes = tsz * (size_t)r * L.ldn, y_bytes = tsz * (size_t)r * kCK;
+  L.N = take(n_bytes > 6656 ? n_bytes : 6656);
   L.dinv = take(tsz * (size_t)((r + 3) & ~3));
-  L.Y = take(tsz * (size_t)r * kCK);
+  L.Y = take(y_bytes > 2304 ? y_bytes : 2304);
   L.Q = take(tsz * (size_t)r * kCK);
   L.E = take(tsz * (size_t)r * kCK);
   L.buf = take(tsz * 2 * kCX);
   // the QR workspace, then (after Q is formed) the Jacobi buffers and C_(n)^T
   const size_t qr = ((usz * (size_t)r * 17 + 15) & ~(size_t)15) + usz * kCK;
   const size_t kb = ((tsz * kCK * kCKs + 15) & ~(size_t)15);
-  const size_t lt = 3 * kb + ((tsz * kCK * kCK + 15) & ~(size_t)15) + tsz * (size_t)r * R;
+  // C_(n)^T's buffer also holds a copy of K (16 x 17) in the precision form
+  const size_t cnt = tsz * (size_t)(r * R > kCK * kCKs ? r * R : kCK * kCKs);
+  const size_t lt = 3 * kb + ((tsz * kCK * kCK + 15) & ~(size_t)15) + cnt;
   L.late = take(qr > lt ? qr : lt);
   L.C = L.late;
   L.tau = L.late + ((usz * (size_t)r * 17 + 15) & ~(size_t)15);
@@ -607,9 +612,190 @@ __device__ T* cj_jacobi_warp(T* K, T* K2, T* V, int max_sweeps) {
   return A;
 }
 
+// ---------------------------------------------------------------- FP64 precision form
+
+// FP64 reciprocal: FP32 seed, two Newton steps (each doubles the correct digits).
+__device__ __forceinline__ double p64_rcp(double x) {
+  double y = (double)__frcp_rn((float)x);
+  y = y * fma(-x, y, 2.0);
+  return y * fma(-x, y, 2.0);
+}
+// FP64 1/sqrt(x): FP32 seed, two Newton steps.
+__device__ __forceinline__ double p64_rsqrt(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  return y * fma(-0.5 * x * y, y, 1.5);
+}
+
+// One FP64 Cholesky-QR pass: C^T C + sigma I = N^{-1} D N^{-T} (LDL^T with L^{-1} = N
+// formed in place), Qout = C N^T D^{-1/2}.  With `shifted`, sigma = 11 (r k + k (k + 1))
+// u ||C||_F^2 keeps the Gram positive definite however small C's last singular values
+// (shifted Cholesky-QR, Fukaya et al. 2020); it moves only directions below its own
+// level.  Without it (sigma = 0), a pivot at or below 2^-40 ||C||_F^2 / k drops its
+// direction (a zero column of Qout: C has nothing there above the data type's rounding);
+// a NaN pivot propagates.  The Gram takes four threads per entry, the LDL^T one warp
+// (lane i owns row i), Qout a thread per row (so Qout may be C itself).  C: r x 16 in
+// the data type (its products are exact in FP64); S: 16 x 17 FP64 workspace; dsq: 16
+// FP64; columns >= k of Qout are zero.
+template <typename T>
+__device__ void p64_cholqr_pass(const T* C, int r, int k, bool shifted, double* S, double* dsq,
+                                T* Qout) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int npair = k * (k + 1) / 2;
+  for (int e = tid; e < 4 * ((npair + 127) / 128) * 128; e += kCT) {
+    const int pr = e >> 2, part = e & 3;
+    double acc = 0;
+    int a = 0, b = 0;
+    if (pr < npair) {  // pair index -> (a, b), a <= b
+      int rem = pr;
+      while (rem >= k - a) {
+        rem -= k - a;
+        ++a;
+      }
+      b = a + rem;
+      for (int i = part; i < r; i += 4)
+        acc = fma((double)C[i * kCK + a], (double)C[i * kCK + b], acc);
+    }
+    acc += __shfl_xor_sync(kAll, acc, 1);
+    acc += __shfl_xor_sync(kAll, acc, 2);
+    if (pr < npair && part == 0) {
+      S[a * 17 + b] = acc;
+      S[b * 17 + a] = acc;
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double tr = lane < k ? S[lane * 17 + lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(kAll, tr, o);
+    const double shift =
+        shifted ? 11.0 * ((double)r * k + (double)k * (k + 1)) * 0x1.0p-53 * tr : 0.0;
+    const double thr = 0x1.0p-40 * tr / k;
+    double row[kCK];
+#pragma unroll
+    for (int c = 0; c < kCK; ++c) row[c] = (lane < k && c < k) ? S[lane * 17 + c] : 0.0;
+#pragma unroll
+    for (int c = 0; c < kCK; ++c)
+      if (c == lane) row[c] += shift;
+    double dinv_own = 1.0;
+    for (int j = 0; j < k; ++j) {
+      // pivot row j by shuffles: N(j, c < j), then the updated Gram row
+      double pj[kCK];
+#pragma unroll
+      for (int c = 0; c < kCK; ++c) pj[c] = __shfl_sync(kAll, row[c], j);
+      const double dj = pj[j];
+      const double di = !(dj <= thr) ? p64_rcp(dj) : 0.0;
+      if (lane == j) dinv_own = di;
+      if (lane > j && lane < k) {
+        double m = 0;
+#pragma unroll
+        for (int c = 0; c < kCK; ++c)
+          if (c == j) m = row[c] * di;
+#pragma unroll
+        for (int c = 0; c < kCK; ++c) {
+          if (c == j) row[c] = -m;
+          else row[c] = fma(-m, pj[c], row[c]);  // c < j: N's row; c > j: the Schur update
+        }
+      }
+    }
+    if (lane < k) {
+      dsq[lane] = sqrt(dinv_own);
+#pragma unroll
+      for (int c = 0; c < kCK; ++c) S[lane * 17 + c] = c < lane ? row[c] : (c == lane ? 1.0 : 0.0);
+    }
+  }
+  __syncthreads();
+  // Qout(i, c) = dsq_c sum_{a <= c} C(i, a) N(c, a)
+  for (int i = tid; i < r; i += kCT) {
+    double ci[kCK];
+#pragma unroll
+    for (int a = 0; a < kCK; ++a) ci[a] = a < k ? (double)C[i * kCK + a] : 0.0;
+#pragma unroll
+    for (int c = 0; c < kCK; ++c) {
+      double acc = 0;
+#pragma unroll
+      for (int a = 0; a <= c; ++a) acc = fma(ci[a], S[c * 17 + a], acc);
+      Qout[i * kCK + c] = c < k ? (T)(acc * dsq[c]) : (T)0;
+    }
+  }
+  __syncthreads();
+}
+
+// Q = qr(C) in FP64: a shifted Cholesky-QR pass, then an unshifted pass on its (rounded)
+// result (shifted CholeskyQR2: the first pass leaves Q1 with condition number below
+// about u^{-1/2}, the second makes it orthonormal to the data type's rounding; a shift in
+// the second pass would move Q1's weakest directions by sigma / sigma_min(Q1)^2).  Q may
+// not be C.
+template <typename T>
+__device__ void p64_cholqr(const T* C, int r, int k, double* S, double* dsq, T* Q) {
+  p64_cholqr_pass<T>(C, r, k, true, S, dsq, Q);
+  p64_cholqr_pass<T>(Q, r, k, false, S, dsq, Q);
+}
+
+// One FP64 refinement of the eigen-decomposition K ~ X diag(lambda) X^T from the FP32
+// Jacobi (iterative refinement for symmetric eigenproblems, Ogita & Aishima 2018):
+// R = I - X^T X, S = X^T K X, lambda_i = S_ii / (1 - R_ii), and for i != j
+// E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i) when the eigenvalues are apart
+// (|lambda_j - lambda_i| > delta), else R_ij / 2 (a cluster: only its subspace is
+// determined); E_ii = R_ii / 2; X <- X + X E.  K (16 x 17) and X (16 x 17) are T; the
+// results overwrite X and the diagonal of Kd (T).  W0..W2: 16 x 17 FP64 workspace.
+template <typename T>
+__device__ void p64_eig_refine(const T* K, T* X, T* Kd, double* W0, double* W1, double* W2,
+                               double* lam) {
+  const int tid = threadIdx.x;
+  const int i = tid >> 4, j = tid & 15;  // 256 threads: one entry each
+  const bool act = tid < 256;
+  // W0 = K X, W1 = X^T X
+  if (act) {
+    double kx = 0, xx = 0;
+#pragma unroll
+    for (int a = 0; a < kCK; ++a) {
+      kx = fma((double)K[i * kCKs + a], (double)X[a * kCKs + j], kx);
+      xx = fma((double)X[a * kCKs + i], (double)X[a * kCKs + j], xx);
+    }
+    W0[i * 17 + j] = kx;
+    W1[i * 17 + j] = (i == j ? 1.0 : 0.0) - xx;  // R
+  }
+  __syncthreads();
+  if (act) {  // W2 = X^T (K X)
+    double sx = 0;
+#pragma unroll
+    for (int a = 0; a < kCK; ++a) sx = fma((double)X[a * kCKs + i], W0[a * 17 + j], sx);
+    W2[i * 17 + j] = sx;
+  }
+  __syncthreads();
+  if (tid < kCK) lam[tid] = W2[tid * 17 + tid] / (1.0 - W1[tid * 17 + tid]);
+  __syncthreads();
+  double lmax = 0;
+  for (int a = 0; a < kCK; ++a) lmax = fmax(lmax, fabs(lam[a]));
+  const double delta = 1e-5 * lmax;
+  if (act) {  // W0 = E
+    double e;
+    if (i == j) {
+      e = 0.5 * W1[i * 17 + i];
+    } else {
+      const double gap = lam[j] - lam[i];
+      e = fabs(gap) > delta ? (W2[i * 17 + j] + lam[j] * W1[i * 17 + j]) / gap
+                            : 0.5 * W1[i * 17 + j];
+    }
+    W0[i * 17 + j] = e;
+  }
+  __syncthreads();
+  double xn = 0;
+  if (act) {  // X + X E
+    xn = (double)X[i * kCKs + j];
+#pragma unroll
+    for (int a = 0; a < kCK; ++a) xn = fma((double)X[i * kCKs + a], W0[a * 17 + j], xn);
+  }
+  __syncthreads();
+  if (act) X[i * kCKs + j] = (T)xn;
+  if (tid < kCK) Kd[tid * kCKs + tid] = (T)lam[tid];
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- the kernel
 
-template <typename T, typename U>
+template <typename T, typename U, bool P64>
 __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_smem) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int order[kCK];
@@ -658,16 +844,26 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
   }
   chol_eliminate<T, NWE, RS>(a.G, a.ldg, a.W, a.ldw, r, k, buf, Nm, L.ldn, dinv, Y, a.flag);
   __syncthreads();
-  // 2. C = N^T D^{-1} (N W)  (staged in Q, then widened into the QR buffer)
-  tri_product<T, true>(Nm, L.ldn, r, dinv, Y, nullptr, Q);
-  __syncthreads();
-  for (int e = tid; e < r * kCK; e += kCT) {
-    const int i = e >> 4, c = e & 15;
-    if (c < k) Cq[i * 17 + c] = (U)Q[e];
+  // 2. C = N^T D^{-1} (N W)
+  if constexpr (P64) {  // staged in E (free until step 4)
+    tri_product<T, true>(Nm, L.ldn, r, dinv, Y, nullptr, E);
+    __syncthreads();
+  } else {  // staged in Q, then widened into the Householder buffer
+    tri_product<T, true>(Nm, L.ldn, r, dinv, Y, nullptr, Q);
+    __syncthreads();
+    for (int e = tid; e < r * kCK; e += kCT) {
+      const int i = e >> 4, c = e & 15;
+      if (c < k) Cq[i * 17 + c] = (U)Q[e];
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  // 3. Q = qr(C)
-  chol_householder<U, T>(Cq, 17, r, k, tau, Q);
+  // 3. Q = qr(C): Householder in the data type, or Cholesky-QR in FP64 (precision form;
+  //    its Gram lives in Y, dead until step 4)
+  if constexpr (P64)
+    p64_cholqr<T>(E, r, k, reinterpret_cast<double*>(Y), reinterpret_cast<double*>(Y) + 16 * 17,
+                  Q);
+  else
+    chol_householder<U, T>(Cq, 17, r, k, tau, Q);
   // 4. E = N^T D^{-1} N Q
   tri_product<T, false>(Nm, L.ldn, r, nullptr, Q, dinv, Y);
   __syncthreads();
@@ -714,12 +910,20 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
   }
   __syncthreads();
   // 6. eigen-decomposition of K in warp 0
+  if constexpr (P64) {  // keep K for the FP64 refinement (the Jacobi overwrites it)
+    for (int e = tid; e < kCK * kCKs; e += kCT) CnTs[e] = K0[e];
+    __syncthreads();
+  }
   if (warp == 0) {
     T* Kf = cj_jacobi_warp<T>(K0, K1, V, 20);
     if (lane == 0) Kfin = Kf;
   }
   __syncthreads();
-  const T* Kf = Kfin;
+  T* Kf = Kfin;
+  if constexpr (P64) {  // FP64 refinement; its workspace reuses N (dead after step 4)
+    double* w64 = reinterpret_cast<double*>(Nm);
+    p64_eig_refine<T>(CnTs, V, Kf, w64, w64 + 16 * 17, w64 + 2 * 16 * 17, w64 + 3 * 16 * 17);
+  }
   if (tid < kCK) order[tid] = tid;  // stays a valid index if a NaN breaks the ranking
   __syncthreads();
   // eigenvalues descending (rank by counting; ties keep index order); padded indices
@@ -828,11 +1032,11 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
   }
 }
 
-template <typename T, typename U>
+template <typename T, typename U, bool P64>
 __global__ void __launch_bounds__(kCT) k_lrls_chol(FusedArgs<T> a, bool h_smem) {
   pdl_trigger();
   pdl_wait();
-  lrls_chol_body<T, U>(a, h_smem);
+  lrls_chol_body<T, U, P64>(a, h_smem);
 }
 
 // ---------------------------------------------------------------- host side
@@ -853,7 +1057,7 @@ static CholLayout chol_pick(int r, int s, int k, int R, size_t tsz, size_t usz) 
 }
 
 bool lrls_chol_supported(int r, int s, int k, int R, int solve, size_t tsize, bool fp64) {
-  if (solve != TS_SOLVE_RSVD || fp64) return false;
+  if (solve != TS_SOLVE_RSVD || (fp64 && tsize == 8)) return false;
   if (r < 1 || s < 1 || R < 1 || k < R || k > kCK || r + k > kCMax) return false;
   if (tsize == 8 ? r > ElimShape<double>::NWE * ElimShape<double>::RS
                  : r > ElimShape<float>::NWE * ElimShape<float>::RS)
@@ -862,16 +1066,22 @@ bool lrls_chol_supported(int r, int s, int k, int R, int solve, size_t tsize, bo
 }
 
 template <typename T>
-ts_status launch_lrls_chol(const FusedArgs<T>& in, cudaStream_t st) {
+ts_status launch_lrls_chol(const FusedArgs<T>& in, bool fp64, cudaStream_t st) {
   FusedArgs<T> a = in;
   const CholLayout L = chol_pick(a.r, a.s, a.k, a.R, sizeof(T), sizeof(T));
   a.m_smem = L.d_smem;
   const bool h = L.h_smem;
-  TS_TRY(ensure_dynamic_smem((const void*)k_lrls_chol<T, T>, L.total));
-  return launch_pdl(k_lrls_chol<T, T>, dim3(1), dim3(kCT), L.total, st, a, h);
+  if constexpr (sizeof(T) == 4) {
+    if (fp64) {  // the precision form: FP64 QR of C and FP64 refinement of K's eigenpairs
+      TS_TRY(ensure_dynamic_smem((const void*)k_lrls_chol<T, T, true>, L.total));
+      return launch_pdl(k_lrls_chol<T, T, true>, dim3(1), dim3(kCT), L.total, st, a, h);
+    }
+  }
+  TS_TRY(ensure_dynamic_smem((const void*)k_lrls_chol<T, T, false>, L.total));
+  return launch_pdl(k_lrls_chol<T, T, false>, dim3(1), dim3(kCT), L.total, st, a, h);
 }
 
-template ts_status launch_lrls_chol<float>(const FusedArgs<float>&, cudaStream_t);
-template ts_status launch_lrls_chol<double>(const FusedArgs<double>&, cudaStream_t);
+template ts_status launch_lrls_chol<float>(const FusedArgs<float>&, bool, cudaStream_t);
+template ts_status launch_lrls_chol<double>(const FusedArgs<double>&, bool, cudaStream_t);
 
 }  // namespace ts

@@ -966,7 +966,7 @@ ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, co
     c.core = core;
     c.map = map;
     c.flag = flag;
-    return launch_lrls_chol<T>(c, st);
+    return launch_lrls_chol<T>(c, fp64, st);
   }
   FusedArgs<T> a;
   size_t smem = 0;

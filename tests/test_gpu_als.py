@@ -151,23 +151,27 @@ def full_size_workload():
     return T, (ranks, m, sweeps, seed), f_o, r_final
 
 
-def test_full_size_fp32_workload_matches_oracle(ts, full_size_workload):
+@pytest.mark.parametrize("fp64", [False, True], ids=["fp32-solve", "fp64-qr-svd"])
+def test_full_size_fp32_workload_matches_oracle(ts, full_size_workload, fp64):
     T, (ranks, m, sweeps, seed), f_o, r_final = full_size_workload
     core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, sweeps,
-                                            seed=seed, rrf_k1=15)
+                                            seed=seed, rrf_k1=15, solve_fp64=fp64)
     assert abs(float(res[0]) - r_final) <= 1e-5 * r_final
     for n in range(3):
         assert np.abs(proj(fac[n].double().cpu().numpy()) - proj(f_o[n])).max() < 1e-4
 
 
-def test_full_size_bf16_workload_matches_oracle(ts, full_size_workload):
+@pytest.mark.parametrize("fp64", [False, True], ids=["fp32-solve", "fp64-qr-svd"])
+def test_full_size_bf16_workload_matches_oracle(ts, full_size_workload, fp64):
     # The precision form on the benchmark workload: every subproblem's Gram products in
-    # BF16 on the tensor cores (FP32 accumulation), against the FP64 oracle: BF16 stages
-    # are held to 1e-2 relative, the residual also to 1e-3 absolute (the equal-residual
-    # criterion), the factors' projectors to 1e-2.
+    # BF16 on the tensor cores (FP32 accumulation), the QR and SVD of the small system in
+    # FP32 or FP64, against the FP64 oracle: BF16 stages are held to 1e-2 relative, the
+    # residual also to 1e-3 absolute (the equal-residual criterion), the factors'
+    # projectors to 1e-2.
     T, (ranks, m, sweeps, seed), f_o, r_final = full_size_workload
     core, fac, res = ts.tucker_als_sketched(torch.from_numpy(T).cuda(), ranks, m, sweeps,
-                                            seed=seed, rrf_k1=15, gram_bf16=True)
+                                            seed=seed, rrf_k1=15, gram_bf16=True,
+                                            solve_fp64=fp64)
     r = float(res[0])
     assert abs(r - r_final) <= 1e-2 * r_final and abs(r - r_final) <= 1e-3
     for n in range(3):

@@ -248,8 +248,12 @@ def _solve_problem(seed, m, r, s, R, noise):
 @pytest.mark.parametrize("m,r,s,R", [(400, 25, 40, 5), (2000, 100, 400, 10), (97, 13, 31, 3),
                                      (3000, 125, 300, 12), (1500, 120, 200, 3),
                                      (1500, 105, 300, 6), (1500, 110, 300, 6)])
-@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_rsvd_lrls_matches_oracle(ts, m, r, s, R, dtype):
+@pytest.mark.parametrize("dtype,fp64", [(torch.float64, False), (torch.float32, False),
+                                        (torch.float32, True)],
+                         ids=["f64", "f32", "f32-fp64-qr-svd"])
+def test_rsvd_lrls_matches_oracle(ts, m, r, s, R, dtype, fp64):
+    # fp64: the precision form (FP32 data; the QR of C and the eigen-decomposition of the
+    # truncation's Gram in FP64)
     Z, Y = _solve_problem(3, m, r, s, R, 0.05)
     if dtype == torch.float32:
         Z = Z.astype(np.float32).astype(np.float64)
@@ -257,7 +261,8 @@ def test_rsvd_lrls_matches_oracle(ts, m, r, s, R, dtype):
     k = solve.rsvd_oversampled_rank(R, 5, r, s)
     Om = rng.gaussian(77, rng.make_tag(4, 2, 1, 0), s * k).reshape(s, k)
     Cw, Aw = solve.rsvd_lrls(Z, Y, R, Om)
-    Cg, Ag = ts.lrls_solve(dev(Z, dtype), dev(Y, dtype), R, ts.SOLVE_RSVD, seed=77, sweep=2, n=1)
+    Cg, Ag = ts.lrls_solve(dev(Z, dtype), dev(Y, dtype), R, ts.SOLVE_RSVD, seed=77, sweep=2, n=1,
+                           solve_fp64=fp64)
     Bw, Bg = Cw @ Aw.T, Cg.cpu().numpy() @ Ag.cpu().numpy().T
     tol = 1e-11 if dtype == torch.float64 else 1e-5
     assert np.linalg.norm(Bg - Bw) <= tol * np.linalg.norm(Bw)

@@ -21,7 +21,11 @@
 //   5. K = U Lambda U^T by cyclic Jacobi in ONE warp (round-robin pairs; rotations of a
 //      round applied as 2 x 2 block updates into a second buffer; no block barrier).
 //   6. C_(n)^T = Q U_R Sigma_R, A^(n) = D^T U_R Sigma_R^{-1}, canonical column signs, core.
+#include <cooperative_groups.h>
+
 #include "dense_la.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace ts {
 
@@ -33,6 +37,11 @@ constexpr int kCKs = 17;   // row stride of the k x k Jacobi buffers
 constexpr int kCX = 132;   // one cross: 128 columns + the pivot's reciprocal at kCX - 1
 constexpr int kCMax = 128; // r + k limit of the elimination tile
 constexpr unsigned kAll = 0xffffffffu;
+constexpr int kNC = 8;  // CTAs of the cluster that shares one subproblem (one per SM)
+// FP64 precision form: a scalar after the 16 x 17 Gram (S), and the size of the eigen
+// refinement's workspace (in doubles; K's FP64 copy follows it)
+constexpr int kP64Scal = 272;
+constexpr int kRefineWs = 656;
 }  // namespace
 
 // Rows per warp of the elimination (all 16 warps): FP32 8 (r <= 128), FP64 4 (r <= 64,
@@ -48,10 +57,11 @@ __device__ __forceinline__ void elim_sync(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
-// Shared-memory layout (byte offsets).  T = data type, U = QR type.
+// Shared-memory layout of one CTA (byte offsets).  T = data type, U = QR type; sw is the
+// widest column slice of H / D / A that a CTA owns.
 struct CholLayout {
-  int ldn;
-  size_t H, D, Am, N, dinv, Y, Q, E, buf, late, C, tau, K0, K1, V, F, CnT, total;
+  int ldn, sw;
+  size_t H, D, Am, N, dinv, Y, Q, E, buf, late, C, tau, K0, K1, V, F, CnT, X, total;
   bool h_smem, d_smem, a_smem;
 };
 
@@ -60,9 +70,11 @@ __host__ __device__ inline CholLayout chol_layout(int r, int s, int k, int R, si
                                                   bool a_smem) {
   CholLayout L{};
   L.ldn = (r + 3) & ~3;
+  L.sw = (s + kNC - 1) / kNC;
   L.h_smem = h_smem;
   L.d_smem = d_smem;
   L.a_smem = a_smem;
+  const size_t sw = L.sw;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     off = (off + 15) & ~(size_t)15;
@@ -70,31 +82,31 @@ __host__ __device__ inline CholLayout chol_layout(int r, int s, int k, int R, si
     off += bytes;
     return o;
   };
-  // H (r x s) when it is copied in; D (k x s) then overwrites its first k rows and A
-  // (s x R) follows them (row stride s for H and D)
+  // the own columns of H (r x sw) when they are copied in; D (k x sw) then overwrites
+  // their first k rows and A (sw x R) follows them (row stride sw for H and D)
   if (h_smem) {
-    L.H = take(tsz * (size_t)r * s);
+    L.H = take(tsz * (size_t)r * sw);
     L.D = L.H;
-    L.Am = L.H + tsz * (size_t)k * s;
+    L.Am = L.H + tsz * (size_t)k * sw;
   } else {
-    L.D = take(d_smem ? tsz * (size_t)k * s : 0);
-    L.Am = take(a_smem ? tsz * (size_t)s * R : 0);
+    L.D = take(d_smem ? tsz * (size_t)k * sw : 0);
+    L.Am = take(a_smem ? tsz * sw * R : 0);
   }
-  // N is dead after step 4: the FP64 eigen refinement's workspace (3 16 x 17 + 16
-  // doubles) reuses it; Y is dead during the QR: the FP64 Gram (16 x 17 + 16 doubles)
+  // N is dead after step 4: the FP64 eigen refinement's workspace and K's FP64 copy
+  // reuse it; Y is dead during the QR: the FP64 Gram, its scalars, D^{-1/2} and the own
+  // rows of C in FP64 (16 x 17 + 16 + 16 + 256 doubles)
   const size_t n_bytes = tsz * (size_t)r * L.ldn, y_bytes = tsz * (size_t)r * kCK;
-  L.N = take(n_bytes > 6656 ? n_bytes : 6656);
+  const size_t n64 = 8 * (size_t)(kRefineWs + 16 * 17), y64 = 8 * (size_t)(304 + 256);
+  L.N = take(n_bytes > n64 ? n_bytes : n64);
   L.dinv = take(tsz * (size_t)((r + 3) & ~3));
-  L.Y = take(y_bytes > 2304 ? y_bytes : 2304);
+  L.Y = take(y_bytes > y64 ? y_bytes : y64);
   L.Q = take(tsz * (size_t)r * kCK);
   L.E = take(tsz * (size_t)r * kCK);
-  L.buf = take(tsz * 2 * kCX);
+  L.buf = take(tsz * 2 * kCX > 66 * 8 ? tsz * 2 * kCX : 66 * 8);
   // the QR workspace, then (after Q is formed) the Jacobi buffers and C_(n)^T
   const size_t qr = ((usz * (size_t)r * 17 + 15) & ~(size_t)15) + usz * kCK;
   const size_t kb = ((tsz * kCK * kCKs + 15) & ~(size_t)15);
-  // C_(n)^T's buffer also holds a copy of K (16 x 17) in the precision form
-  const size_t cnt = tsz * (size_t)(r * R > kCK * kCKs ? r * R : kCK * kCKs);
-  const size_t lt = 3 * kb + ((tsz * kCK * kCK + 15) & ~(size_t)15) + cnt;
+  const size_t lt = 3 * kb + ((tsz * kCK * kCK + 15) & ~(size_t)15) + tsz * (size_t)r * R;
   L.late = take(qr > lt ? qr : lt);
   L.C = L.late;
   L.tau = L.late + ((usz * (size_t)r * 17 + 15) & ~(size_t)15);
@@ -103,6 +115,8 @@ __host__ __device__ inline CholLayout chol_layout(int r, int s, int k, int R, si
   L.V = L.K1 + kb;
   L.F = L.V + kb;
   L.CnT = L.F + ((tsz * kCK * kCK + 15) & ~(size_t)15);
+  // exchange with the peers: a 16 x 17 FP64 partial (Gram or K) and the sign candidates
+  L.X = take(8 * 16 * 17 + 3 * 16 * 8);
   L.total = off;
   return L;
 }
@@ -612,35 +626,107 @@ __device__ T* cj_jacobi_warp(T* K, T* K2, T* V, int max_sweeps) {
   return A;
 }
 
+// ---------------------------------------------------------------- cluster exchange
+
+// The CTAs of the cluster share one subproblem: every CTA repeats the short serial chains
+// (elimination, triangular products, Householder QR, Jacobi) on identical data, so they
+// hold identical results, and each owns a slice of the work that is wide rather than
+// deep: columns [j0, j1) of H, D and A, rows [i0, i1) of C for the FP64 products and two
+// rows of the 16 x 16 eigen refinement.  Partial results go to the peers through
+// distributed shared memory: written into a CTA's own buffer, a cluster barrier, read
+// from the peers' buffers (sums always in rank order, so every CTA gets the same bits).
+template <typename P>
+__device__ __forceinline__ P* cl_peer(P* p, int rank) {
+  return cg::this_cluster().map_shared_rank(p, rank);
+}
+__device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
+
 // ---------------------------------------------------------------- FP64 precision form
+//
+// On this part an FP64 warp instruction occupies its SM sub-partition's FP64 unit for
+// about 64 cycles (conversions to and from FP32 included), so the FP64 code keeps the
+// instruction count low: operands converted once, FP64 work split over the cluster and,
+// within a CTA, over warps on all four sub-partitions.
 
-// FP64 reciprocal: FP32 seed, two Newton steps (each doubles the correct digits).
+// FP64 reciprocal: the approximate FP64 reciprocal (a seed good to about FP32 precision)
+// refined by two Newton steps, y <- y + y (1 - x y) (each doubles the correct digits).
 __device__ __forceinline__ double p64_rcp(double x) {
-  double y = (double)__frcp_rn((float)x);
-  y = y * fma(-x, y, 2.0);
-  return y * fma(-x, y, 2.0);
-}
-// FP64 1/sqrt(x): FP32 seed, two Newton steps.
-__device__ __forceinline__ double p64_rsqrt(double x) {
-  double y = (double)rsqrtf((float)x);
-  y = y * fma(-0.5 * x * y, y, 1.5);
-  return y * fma(-0.5 * x * y, y, 1.5);
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
 }
 
-// One FP64 Cholesky-QR pass: C^T C + sigma I = N^{-1} D N^{-T} (LDL^T with L^{-1} = N
-// formed in place), Qout = C N^T D^{-1/2}.  With `shifted`, sigma = 11 (r k + k (k + 1))
-// u ||C||_F^2 keeps the Gram positive definite however small C's last singular values
-// (shifted Cholesky-QR, Fukaya et al. 2020); it moves only directions below its own
-// level.  Without it (sigma = 0), a pivot at or below 2^-40 ||C||_F^2 / k drops its
-// direction (a zero column of Qout: C has nothing there above the data type's rounding);
-// a NaN pivot propagates.  The Gram takes four threads per entry, the LDL^T one warp
-// (lane i owns row i), Qout a thread per row (so Qout may be C itself).  C: r x 16 in
-// the data type (its products are exact in FP64); S: 16 x 17 FP64 workspace; dsq: 16
-// FP64; columns >= k of Qout are zero.
+// x > thr for thr >= +0, compared on the bit patterns (integer unit): a negative x is
+// not above; neither is a NaN with its sign bit set (a NaN input reaches the outputs
+// through the other entries of its row and column anyway).
+__device__ __forceinline__ bool p64_above(double x, double thr) {
+  return __double_as_longlong(x) > __double_as_longlong(thr);
+}
+
+__device__ __forceinline__ void p64_sync() { asm volatile("bar.sync 2, 256;" ::: "memory"); }
+
+// LDL^T of a symmetric k x k FP64 matrix (k <= 16) held one entry per thread by threads
+// 0..255 (thread t: row t / 16, column t % 16; entries outside k x k are zero), with
+// L^{-1} = N formed in place.  On return v holds N(i, c) for c < i; the diagonal thread
+// returns D(i)^{-1} (0 for a pivot not above thr: the direction is dropped), the others
+// return 0.  Pivot j's row, column and reciprocal go out through a double-buffered shared
+// row (pub: 2 x 33 doubles); the owner of pivot j + 1 publishes its reciprocal as soon as
+// its own update is done: one barrier (256 threads) per pivot.  A warp with no row below
+// the pivot only waits, and each entry takes one FP64 multiply and one fused multiply-add
+// per pivot.
+__device__ double p64_ldl(double& v, int k, double thr, double* pub) {
+  const int t = threadIdx.x, i = t >> 4, c = t & 15, wp = t >> 5;
+  double dinv = 0.0;
+  if (i == 0) pub[c] = v;
+  if (c == 0) pub[16 + i] = v;
+  if (t == 0) pub[32] = p64_above(v, thr) ? p64_rcp(v) : 0.0;
+  p64_sync();
+  for (int j = 0; j < k; ++j) {
+    const double* cur = pub + (j & 1) * 33;
+    double* nxt = pub + ((j & 1) ^ 1) * 33;
+    if (i == j && c == j) dinv = cur[32];
+    if (2 * wp + 1 > j && 2 * wp < k && i > j && i < k) {
+      const double m = cur[16 + i] * cur[32];
+      const bool piv = c == j;  // column j of S becomes column j of N: -m
+      v = fma(-m, piv ? 1.0 : cur[c], piv ? 0.0 : v);  // c < j: N's row; c > j: Schur
+    }
+    const int jn = j + 1;
+    if (jn < k) {
+      if (i == jn) nxt[c] = v;
+      if (c == jn) nxt[16 + i] = v;
+      if (i == jn && c == jn) nxt[32] = p64_above(v, thr) ? p64_rcp(v) : 0.0;
+    }
+    p64_sync();
+  }
+  return dinv;
+}
+
+// One FP64 Cholesky-QR pass over the cluster: Qout = C N^T D^{-1/2} with
+// C^T C = N^{-1} D N^{-T}.  C (r x 16, type T, columns >= k ignored) is identical in every
+// CTA; this CTA owns rows [i0, i1).  A pivot not above 2^-40 ||C||_F^2 / k drops its
+// direction (a zero column of Qout): below that level the Gram's own rounding decides
+// the pivot, and C, computed from FP32 data, holds nothing there.  In the second pass
+// (`second`) of CholeskyQR2 the Gram is usually within 2^-20 of the identity (the first
+// pass leaves Q1 orthonormal to u kappa(C)^2 plus the data type's rounding); its factor
+// is then taken to first order, N = I - strictly_lower(S - I), D^{-1/2} = I - diag(S - I)
+// / 2, whose error is second order (below 2^-40); otherwise the full LDL^T runs again.
+// On return every CTA holds all of Qout (zero columns >= k; Qout may be C).  S: 16 x 17
+// FP64 and a scalar after it (kP64Scal); dsq: 16; Cd: 16 x 16 FP64 (own rows); Xg: 16 x 17
+// FP64, read by the peers; pub: 66 FP64.
 template <typename T>
-__device__ void p64_cholqr_pass(const T* C, int r, int k, bool shifted, double* S, double* dsq,
-                                T* Qout) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+__device__ void p64_cholqr_pass(const T* C, T* Qout, int r, int k, int i0, int i1, bool second,
+                                double* S, double* dsq, double* Cd, double* Xg, double* pub) {
+  const int tid = threadIdx.x, cr = (int)cg::this_cluster().block_rank();
+  const int nr = i1 - i0;
+  for (int e = tid; e < nr * kCK; e += kCT) {
+    const int ii = e >> 4, c = e & 15;
+    Cd[e] = c < k ? (double)C[(i0 + ii) * kCK + c] : 0.0;
+  }
+  __syncthreads();
+  // Gram of the own rows (4 threads per entry of the lower triangle), to the peers
   const int npair = k * (k + 1) / 2;
   for (int e = tid; e < 4 * ((npair + 127) / 128) * 128; e += kCT) {
     const int pr = e >> 2, part = e & 3;
@@ -653,143 +739,159 @@ __device__ void p64_cholqr_pass(const T* C, int r, int k, bool shifted, double* 
         ++a;
       }
       b = a + rem;
-      for (int i = part; i < r; i += 4)
-        acc = fma((double)C[i * kCK + a], (double)C[i * kCK + b], acc);
+      for (int ii = part; ii < nr; ii += 4) acc = fma(Cd[ii * kCK + a], Cd[ii * kCK + b], acc);
     }
     acc += __shfl_xor_sync(kAll, acc, 1);
     acc += __shfl_xor_sync(kAll, acc, 2);
-    if (pr < npair && part == 0) {
-      S[a * 17 + b] = acc;
-      S[b * 17 + a] = acc;
-    }
+    if (pr < npair && part == 0) Xg[b * 17 + a] = acc;
+  }
+  cl_sync();
+  const int i = tid >> 4, c = tid & 15;
+  const bool ent = tid < 256 && c <= i && i < k;
+  if (ent) {
+    double sum = 0;
+#pragma unroll
+    for (int q = 0; q < kNC; ++q) sum += cl_peer(Xg, q)[i * 17 + c];
+    S[i * 17 + c] = sum;
+    S[c * 17 + i] = sum;
   }
   __syncthreads();
-  if (warp == 0) {
-    double tr = lane < k ? S[lane * 17 + lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(kAll, tr, o);
-    const double shift =
-        shifted ? 11.0 * ((double)r * k + (double)k * (k + 1)) * 0x1.0p-53 * tr : 0.0;
-    const double thr = 0x1.0p-40 * tr / k;
-    double row[kCK];
-#pragma unroll
-    for (int c = 0; c < kCK; ++c) row[c] = (lane < k && c < k) ? S[lane * 17 + c] : 0.0;
-#pragma unroll
-    for (int c = 0; c < kCK; ++c)
-      if (c == lane) row[c] += shift;
-    double dinv_own = 1.0;
-    for (int j = 0; j < k; ++j) {
-      // pivot row j by shuffles: N(j, c < j), then the updated Gram row
-      double pj[kCK];
-#pragma unroll
-      for (int c = 0; c < kCK; ++c) pj[c] = __shfl_sync(kAll, row[c], j);
-      const double dj = pj[j];
-      const double di = !(dj <= thr) ? p64_rcp(dj) : 0.0;
-      if (lane == j) dinv_own = di;
-      if (lane > j && lane < k) {
-        double m = 0;
-#pragma unroll
-        for (int c = 0; c < kCK; ++c)
-          if (c == j) m = row[c] * di;
-#pragma unroll
-        for (int c = 0; c < kCK; ++c) {
-          if (c == j) row[c] = -m;
-          else row[c] = fma(-m, pj[c], row[c]);  // c < j: N's row; c > j: the Schur update
-        }
+  const bool near_identity =
+      second && !__syncthreads_or(ent && fabs(S[i * 17 + c] - (i == c ? 1.0 : 0.0)) > 0x1.0p-20);
+  if (near_identity) {
+    if (ent) {
+      const double v = S[i * 17 + c];
+      if (c < i) S[i * 17 + c] = -v;
+      if (c == i) {
+        dsq[i] = 1.0 - 0.5 * (v - 1.0);
+        S[i * 17 + i] = 1.0;
       }
     }
-    if (lane < k) {
-      dsq[lane] = sqrt(dinv_own);
+  } else {
+    if (tid < 32) {  // the drop threshold, once
+      double tr = tid < k ? S[tid * 17 + tid] : 0.0;
 #pragma unroll
-      for (int c = 0; c < kCK; ++c) S[lane * 17 + c] = c < lane ? row[c] : (c == lane ? 1.0 : 0.0);
+      for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(kAll, tr, o);
+      if (tid == 0) S[kP64Scal] = 0x1.0p-40 * tr / k;
     }
+    __syncthreads();
+    if (tid < 256) {
+      const double thr = S[kP64Scal];
+      double v = (i < k && c < k) ? S[i * 17 + c] : 0.0;
+      const double dinv = p64_ldl(v, k, thr, pub);
+      if (i < k && c < k) S[i * 17 + c] = c < i ? v : (c == i ? 1.0 : 0.0);
+      if (i < k && c == i) dsq[i] = dinv;
+    }
+    __syncthreads();
+    if (tid < k) dsq[tid] = sqrt(dsq[tid]);
   }
   __syncthreads();
-  // Qout(i, c) = dsq_c sum_{a <= c} C(i, a) N(c, a)
-  for (int i = tid; i < r; i += kCT) {
-    double ci[kCK];
-#pragma unroll
-    for (int a = 0; a < kCK; ++a) ci[a] = a < k ? (double)C[i * kCK + a] : 0.0;
-#pragma unroll
-    for (int c = 0; c < kCK; ++c) {
-      double acc = 0;
-#pragma unroll
-      for (int a = 0; a <= c; ++a) acc = fma(ci[a], S[c * 17 + a], acc);
-      Qout[i * kCK + c] = c < k ? (T)(acc * dsq[c]) : (T)0;
-    }
+  // own rows of Qout: Qout(i, c) = dsq_c sum_{a <= c} C(i, a) N(c, a)
+  for (int e = tid; e < nr * kCK; e += kCT) {
+    const int ii = e >> 4, cc = e & 15;
+    double acc = 0;
+    if (cc < k)
+      for (int a = 0; a <= cc; ++a) acc = fma(Cd[ii * kCK + a], S[cc * 17 + a], acc);
+    Qout[(i0 + ii) * kCK + cc] = cc < k ? (T)(acc * dsq[cc]) : (T)0;
+  }
+  cl_sync();
+  for (int q = 0; q < kNC; ++q) {  // the peers' rows
+    if (q == cr) continue;
+    const int b0 = r * q / kNC, b1 = r * (q + 1) / kNC;
+    const T* src = cl_peer(Qout, q);
+    for (int e = tid; e < (b1 - b0) * kCK; e += kCT) Qout[b0 * kCK + e] = src[b0 * kCK + e];
   }
   __syncthreads();
-}
-
-// Q = qr(C) in FP64: a shifted Cholesky-QR pass, then an unshifted pass on its (rounded)
-// result (shifted CholeskyQR2: the first pass leaves Q1 with condition number below
-// about u^{-1/2}, the second makes it orthonormal to the data type's rounding; a shift in
-// the second pass would move Q1's weakest directions by sigma / sigma_min(Q1)^2).  Q may
-// not be C.
-template <typename T>
-__device__ void p64_cholqr(const T* C, int r, int k, double* S, double* dsq, T* Q) {
-  p64_cholqr_pass<T>(C, r, k, true, S, dsq, Q);
-  p64_cholqr_pass<T>(Q, r, k, false, S, dsq, Q);
 }
 
 // One FP64 refinement of the eigen-decomposition K ~ X diag(lambda) X^T from the FP32
 // Jacobi (iterative refinement for symmetric eigenproblems, Ogita & Aishima 2018):
-// R = I - X^T X, S = X^T K X, lambda_i = S_ii / (1 - R_ii), and for i != j
-// E_ij = (S_ij + lambda_j R_ij) / (lambda_j - lambda_i) when the eigenvalues are apart
-// (|lambda_j - lambda_i| > delta), else R_ij / 2 (a cluster: only its subspace is
-// determined); E_ii = R_ii / 2; X <- X + X E.  K (16 x 17) and X (16 x 17) are T; the
-// results overwrite X and the diagonal of Kd (T).  W0..W2: 16 x 17 FP64 workspace.
+// R = I - X^T X, S = X^T K X, lambda_j = S_jj / (1 - R_jj), and for a != j
+// E_aj = (S_aj + mu_j R_aj) / (mu_j - mu_a) when the eigenvalues are apart
+// (|mu_j - mu_a| > 1e-5 max |mu|), else R_aj / 2 (a cluster: only its subspace is
+// determined); E_jj = R_jj / 2; X <- X + X E.  mu are the Jacobi's eigenvalues: they
+// enter E only through the gaps and through mu_j R_aj with R_aj itself of the order of the
+// Jacobi's error, so their error reaches X at second order.  This CTA computes columns
+// 2 cr, 2 cr + 1 of E and of X + X E (4 threads per entry) and lambda for them; one
+// cluster barrier, then every CTA gathers the other columns.  Kd: K in FP64 (16 x 17);
+// X (16 x 17, T, columns are eigenvectors) is overwritten, and so is the diagonal of Kf
+// (T; the Jacobi's eigenvalues on entry).  ws: kRefineWs FP64 (the last blocks are read
+// by the peers).
 template <typename T>
-__device__ void p64_eig_refine(const T* K, T* X, T* Kd, double* W0, double* W1, double* W2,
-                               double* lam) {
-  const int tid = threadIdx.x;
-  const int i = tid >> 4, j = tid & 15;  // 256 threads: one entry each
-  const bool act = tid < 256;
-  // W0 = K X, W1 = X^T X
-  if (act) {
-    double kx = 0, xx = 0;
+__device__ void p64_eig_refine(const double* Kd, T* X, T* Kf, double* ws) {
+  const int tid = threadIdx.x, cr = (int)cg::this_cluster().block_rank();
+  double* Xd = ws;        // X in FP64, 16 x 17
+  double* Yc = ws + 272;  // y_j = K x_j for the own j, 2 x 16
+  double* Ec = ws + 304;  // own columns of E, 16 x 2
+  double* mu = ws + 336;  // Jacobi eigenvalues (16) and max |mu| (at 16)
+  double* Xn = ws + 360;  // X + X E: own columns written here, read by the peers
+  double* lam = ws + 632; // refined lambda: own entries written here, read by the peers
+  if (tid < 256) Xd[(tid >> 4) * 17 + (tid & 15)] = (double)X[(tid >> 4) * kCKs + (tid & 15)];
+  if (tid >= 256 && tid < 288) {  // warp 8
+    const int l = tid & 15;
+    const double m = (double)Kf[l * kCKs + l];
+    double mx = fabs(m);
 #pragma unroll
-    for (int a = 0; a < kCK; ++a) {
-      kx = fma((double)K[i * kCKs + a], (double)X[a * kCKs + j], kx);
-      xx = fma((double)X[a * kCKs + i], (double)X[a * kCKs + j], xx);
+    for (int o = 8; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(kAll, mx, o));
+    if (tid < 272) mu[l] = m;
+    if (tid == 256) mu[16] = mx;
+  }
+  __syncthreads();
+  // thread: entry (a, j) of an own column j, quarter q of its 16-term sums
+  const int q = tid & 3, a = (tid >> 2) & 15, j = 2 * cr + ((tid >> 6) & 1);
+  const bool act = tid < 128;
+  if (act) {  // y_j(a) = sum_b K(a, b) X(b, j)
+    double acc = 0;
+#pragma unroll
+    for (int b = 4 * q; b < 4 * q + 4; ++b) acc = fma(Kd[a * 17 + b], Xd[b * 17 + j], acc);
+    acc += __shfl_xor_sync(kAll, acc, 1);
+    acc += __shfl_xor_sync(kAll, acc, 2);
+    if (q == 0) Yc[(j & 1) * 16 + a] = acc;
+  }
+  __syncthreads();
+  if (act) {  // S_aj = x_a . y_j, R_aj = delta_aj - x_a . x_j, then E_aj
+    double sv = 0, xv = 0;
+#pragma unroll
+    for (int b = 4 * q; b < 4 * q + 4; ++b) {
+      sv = fma(Xd[b * 17 + a], Yc[(j & 1) * 16 + b], sv);
+      xv = fma(Xd[b * 17 + a], Xd[b * 17 + j], xv);
     }
-    W0[i * 17 + j] = kx;
-    W1[i * 17 + j] = (i == j ? 1.0 : 0.0) - xx;  // R
-  }
-  __syncthreads();
-  if (act) {  // W2 = X^T (K X)
-    double sx = 0;
-#pragma unroll
-    for (int a = 0; a < kCK; ++a) sx = fma((double)X[a * kCKs + i], W0[a * 17 + j], sx);
-    W2[i * 17 + j] = sx;
-  }
-  __syncthreads();
-  if (tid < kCK) lam[tid] = W2[tid * 17 + tid] / (1.0 - W1[tid * 17 + tid]);
-  __syncthreads();
-  double lmax = 0;
-  for (int a = 0; a < kCK; ++a) lmax = fmax(lmax, fabs(lam[a]));
-  const double delta = 1e-5 * lmax;
-  if (act) {  // W0 = E
-    double e;
-    if (i == j) {
-      e = 0.5 * W1[i * 17 + i];
-    } else {
-      const double gap = lam[j] - lam[i];
-      e = fabs(gap) > delta ? (W2[i * 17 + j] + lam[j] * W1[i * 17 + j]) / gap
-                            : 0.5 * W1[i * 17 + j];
+    sv += __shfl_xor_sync(kAll, sv, 1);
+    sv += __shfl_xor_sync(kAll, sv, 2);
+    xv += __shfl_xor_sync(kAll, xv, 1);
+    xv += __shfl_xor_sync(kAll, xv, 2);
+    if (q == 0) {
+      const double rv = (a == j ? 1.0 : 0.0) - xv;
+      double e;
+      if (a == j) {
+        e = 0.5 * rv;
+        lam[j] = sv / (1.0 - rv);
+      } else {
+        const double gap = mu[j] - mu[a];
+        e = fabs(gap) > 1e-5 * mu[16] ? (sv + mu[j] * rv) / gap : 0.5 * rv;
+      }
+      Ec[a * 2 + (j & 1)] = e;
     }
-    W0[i * 17 + j] = e;
   }
   __syncthreads();
-  double xn = 0;
-  if (act) {  // X + X E
-    xn = (double)X[i * kCKs + j];
+  if (act) {  // own columns of X + X E
+    double acc = 0;
 #pragma unroll
-    for (int a = 0; a < kCK; ++a) xn = fma((double)X[i * kCKs + a], W0[a * 17 + j], xn);
+    for (int b = 4 * q; b < 4 * q + 4; ++b) acc = fma(Xd[a * 17 + b], Ec[b * 2 + (j & 1)], acc);
+    acc += __shfl_xor_sync(kAll, acc, 1);
+    acc += __shfl_xor_sync(kAll, acc, 2);
+    if (q == 0) Xn[a * 17 + j] = Xd[a * 17 + j] + acc;
   }
-  __syncthreads();
-  if (act) X[i * kCKs + j] = (T)xn;
-  if (tid < kCK) Kd[tid * kCKs + tid] = (T)lam[tid];
+  cl_sync();
+  if (tid < 256) {
+    const int ii = tid >> 4, jj = tid & 15, owner = jj >> 1;
+    const double v = owner == cr ? Xn[ii * 17 + jj] : cl_peer(Xn, owner)[ii * 17 + jj];
+    X[ii * kCKs + jj] = (T)v;
+  }
+  if (tid >= 256 && tid < 256 + kCK) {
+    const int l = tid - 256, owner = l >> 1;
+    Kf[l * kCKs + l] = (T)(owner == cr ? lam[l] : cl_peer(lam, owner)[l]);
+  }
   __syncthreads();
 }
 
@@ -804,8 +906,13 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
   constexpr int NWE = ElimShape<T>::NWE, RS = ElimShape<T>::RS;
   const int r = a.r, s = a.s, k = a.k, R = a.R;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int cr = (int)cg::this_cluster().block_rank();
   const CholLayout L =
       chol_layout(r, s, k, R, sizeof(T), sizeof(U), h_smem, a.m_smem, a.m_smem);
+  // this CTA's columns of H / D / A and rows of C
+  const int j0 = (int)((long)s * cr / kNC), w = (int)((long)s * (cr + 1) / kNC) - j0;
+  const int i0 = r * cr / kNC, i1 = r * (cr + 1) / kNC;
+  const int sw = L.sw;
   T* Hs = reinterpret_cast<T*>(smem_raw + L.H);
   T* Nm = reinterpret_cast<T*>(smem_raw + L.N);
   T* dinv = reinterpret_cast<T*>(smem_raw + L.dinv);
@@ -815,31 +922,35 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
   T* Q = reinterpret_cast<T*>(smem_raw + L.Q);
   T* E = reinterpret_cast<T*>(smem_raw + L.E);
   T* buf = reinterpret_cast<T*>(smem_raw + L.buf);
-  T* D = (h_smem || L.d_smem) ? reinterpret_cast<T*>(smem_raw + L.D) : a.Mbuf;
   T* K0 = reinterpret_cast<T*>(smem_raw + L.K0);
   T* K1 = reinterpret_cast<T*>(smem_raw + L.K1);
   T* V = reinterpret_cast<T*>(smem_raw + L.V);
   T* F = reinterpret_cast<T*>(smem_raw + L.F);
   T* CnTs = reinterpret_cast<T*>(smem_raw + L.CnT);
-  T* Am = (h_smem || L.a_smem) ? reinterpret_cast<T*>(smem_raw + L.Am) : a.A_out;
-  const T* Hsrc = h_smem ? Hs : a.H;
-  const long ldh = h_smem ? s : a.ldh;
+  double* Xg = reinterpret_cast<double*>(smem_raw + L.X);  // exchange: Gram / K partials
+  T* Xbest = reinterpret_cast<T*>(smem_raw + L.X + 17 * 16 * 8);
+  T* Xval = Xbest + kCK;
+  int* Xidx = reinterpret_cast<int*>(Xval + kCK);
+  // D (k x w) and A (w x R) of the own columns: in shared memory (row stride sw for D)
+  // or in the caller's buffers (row stride s for D; A's rows j0 .. j0 + w - 1)
+  const bool d_sm = h_smem || L.d_smem, a_sm = h_smem || L.a_smem;
+  T* D = d_sm ? reinterpret_cast<T*>(smem_raw + L.D) : a.Mbuf + j0;
+  const long ldd = d_sm ? sw : s;
+  T* Am = a_sm ? reinterpret_cast<T*>(smem_raw + L.Am) : a.A_out + (long)j0 * R;
+  const T* Hsrc = h_smem ? Hs : a.H + j0;
+  const long ldh = h_smem ? sw : a.ldh;
 
-  // 1. G = L D L^T with N = L^{-1} and N W, while H streams into shared memory by
-  //    asynchronous copies issued first (waited for before step 5)
+  // 1. G = L D L^T with N = L^{-1} and N W, while the own columns of H stream into
+  //    shared memory by asynchronous copies issued first (waited for before step 5)
   if (h_smem) {
-    for (int i = 0; i < r; ++i) {
-      const T* src = a.H + (long)i * a.ldh;
-      T* dst = Hs + (long)i * s;
-      for (int j = tid; j < s; j += kCT) {
-        const unsigned d = (unsigned)__cvta_generic_to_shared(dst + j);
-        if constexpr (sizeof(T) == 4)
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + j)
-                       : "memory");
-        else
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src + j)
-                       : "memory");
-      }
+    for (int e = tid; e < r * w; e += kCT) {
+      const int i = e / w, jj = e - i * w;
+      const T* src = a.H + (long)i * a.ldh + j0 + jj;
+      const unsigned d = (unsigned)__cvta_generic_to_shared(Hs + (long)i * sw + jj);
+      if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+      else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
     }
   }
   chol_eliminate<T, NWE, RS>(a.G, a.ldg, a.W, a.ldw, r, k, buf, Nm, L.ldn, dinv, Y, a.flag);
@@ -857,62 +968,92 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
     }
     __syncthreads();
   }
-  // 3. Q = qr(C): Householder in the data type, or Cholesky-QR in FP64 (precision form;
-  //    its Gram lives in Y, dead until step 4)
-  if constexpr (P64)
-    p64_cholqr<T>(E, r, k, reinterpret_cast<double*>(Y), reinterpret_cast<double*>(Y) + 16 * 17,
-                  Q);
-  else
+  // 3. Q = qr(C): Householder in the data type, or FP64 CholeskyQR2 over the cluster
+  //    (precision form; its buffers live in Y, dead until step 4)
+  if constexpr (P64) {
+    double* S = reinterpret_cast<double*>(Y);
+    double* pub = reinterpret_cast<double*>(buf);  // the elimination's cross is dead
+    p64_cholqr_pass<T>(E, Q, r, k, i0, i1, false, S, S + 288, S + 304, Xg, pub);
+    p64_cholqr_pass<T>(Q, Q, r, k, i0, i1, true, S, S + 288, S + 304, Xg, pub);
+  } else {
     chol_householder<U, T>(Cq, 17, r, k, tau, Q);
+  }
   // 4. E = N^T D^{-1} N Q
   tri_product<T, false>(Nm, L.ldn, r, nullptr, Q, dinv, Y);
   __syncthreads();
   tri_product<T, true>(Nm, L.ldn, r, nullptr, Y, nullptr, E);
   __syncthreads();
-  // 5. D = E^T H (k x s): a thread per column of H, k sums in registers (D may overwrite
-  //    H's first k rows in place: a thread writes only the column it has read)
+  // 5. D = E^T H over the own columns (k x w): a thread per (column, group of 4 rows of
+  //    D) runs down the r rows of H, four sums in registers (a compact loop: this phase
+  //    runs once per launch, so its code size, not its arithmetic, sets its time).  D may
+  //    overwrite H's first k rows in place: it is written after a barrier, and the four
+  //    threads of a column are always in the same round.
   if (h_smem) {
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
   }
-  for (int j = tid; j < s; j += kCT) {
-    T acc[kCK];
-#pragma unroll
-    for (int c = 0; c < kCK; ++c) acc[c] = (T)0;
+  for (int rd = 0; rd < (4 * w + kCT - 1) / kCT; ++rd) {
+    const int it = rd * kCT + tid, jj = it >> 2, cg = it & 3;
+    const bool act = jj < w && 4 * cg < k;
+    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+    if (act) {
+      const T* hp = Hsrc + jj;
+      const T* ep = E + 4 * cg;
 #pragma unroll 4
-    for (int i = 0; i < r; ++i) {
-      const T hv = Hsrc[(long)i * ldh + j];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
+      for (int i = 0; i < r; ++i) {
+        const T hv = hp[(long)i * ldh];
         T ev[4];
-        V4<T>::ld(E + i * kCK + 4 * q, ev);
+        V4<T>::ld(ep + i * kCK, ev);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[4 * q + e] = fma(ev[e], hv, acc[4 * q + e]);
+        for (int e = 0; e < 4; ++e) acc[e] = fma(ev[e], hv, acc[e]);
       }
     }
+    __syncthreads();
+    if (act) {
 #pragma unroll
-    for (int c = 0; c < kCK; ++c)
-      if (c < k) D[(long)c * s + j] = acc[c];
-  }
-  __syncthreads();
-  // K = D D^T (upper triangle by warps, mirrored; padded to 16 with zeros)
-  for (int pr = warp; pr < kCK * kCK; pr += kCW) {
-    const int i = pr >> 4, j = pr & 15;
-    if (j < i) continue;
-    T acc = 0;
-    if (i < k && j < k)
-      for (int t = lane; t < s; t += 32) acc = fma(D[(long)i * s + t], D[(long)j * s + t], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) {
-      K0[i * kCKs + j] = acc;
-      K0[j * kCKs + i] = acc;
+      for (int e = 0; e < 4; ++e)
+        if (4 * cg + e < k) D[(long)(4 * cg + e) * ldd + jj] = acc[e];
     }
   }
   __syncthreads();
-  // 6. eigen-decomposition of K in warp 0
-  if constexpr (P64) {  // keep K for the FP64 refinement (the Jacobi overwrites it)
-    for (int e = tid; e < kCK * kCKs; e += kCT) CnTs[e] = K0[e];
+  // K = D D^T: the own columns' part (4 threads per entry of the upper triangle), summed
+  // over the cluster in rank order
+  {
+    T* Kp = reinterpret_cast<T*>(Xg);
+    for (int e = tid; e < 4 * 136 + (kCT - (4 * 136) % kCT) % kCT; e += kCT) {
+      const int pr = e >> 2, part = e & 3;
+      T acc = 0;
+      int ia = 0, ib = 0;
+      if (pr < 136) {
+        int rem = pr;
+        while (rem >= kCK - ia) {
+          rem -= kCK - ia;
+          ++ia;
+        }
+        ib = ia + rem;
+        if (ib < k)
+          for (int t = part; t < w; t += 4) acc = fma(D[(long)ia * ldd + t], D[(long)ib * ldd + t], acc);
+      }
+      acc += __shfl_xor_sync(kAll, acc, 1);
+      acc += __shfl_xor_sync(kAll, acc, 2);
+      if (pr < 136 && part == 0) Kp[ia * kCKs + ib] = acc;
+    }
+    cl_sync();
+    if (tid < kCK * kCK) {
+      const int i = tid >> 4, j = tid & 15;
+      const int lo = min(i, j), hi = max(i, j);
+      T sum = 0;
+      for (int q = 0; q < kNC; ++q) sum += cl_peer(Kp, q)[lo * kCKs + hi];
+      K0[i * kCKs + j] = sum;
+    }
     __syncthreads();
+  }
+  // 6. eigen-decomposition of K in warp 0 (FP32 Jacobi; FP64 refinement in the precision
+  //    form, its workspace in N, dead after step 4)
+  double* w64 = reinterpret_cast<double*>(Nm);
+  double* Kd = w64 + kRefineWs;
+  if constexpr (P64) {
+    if (tid < 256) Kd[(tid >> 4) * 17 + (tid & 15)] = (double)K0[(tid >> 4) * kCKs + (tid & 15)];
   }
   if (warp == 0) {
     T* Kf = cj_jacobi_warp<T>(K0, K1, V, 20);
@@ -920,10 +1061,7 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
   }
   __syncthreads();
   T* Kf = Kfin;
-  if constexpr (P64) {  // FP64 refinement; its workspace reuses N (dead after step 4)
-    double* w64 = reinterpret_cast<double*>(Nm);
-    p64_eig_refine<T>(CnTs, V, Kf, w64, w64 + 16 * 17, w64 + 2 * 16 * 17, w64 + 3 * 16 * 17);
-  }
+  if constexpr (P64) p64_eig_refine<T>(Kd, V, Kf, w64);
   if (tid < kCK) order[tid] = tid;  // stays a valid index if a NaN breaks the ranking
   __syncthreads();
   // eigenvalues descending (rank by counting; ties keep index order); padded indices
@@ -952,42 +1090,42 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
     }
     F[i * kCK + c] = f;
   }
-  for (int e = tid; e < r * kCK; e += kCT) {
-    const int i = e >> 4, c = e & 15;
-    if (c >= R) continue;
-    const T l = Kf[order[c] * kCKs + order[c]];
-    const T sig = l > (T)0 ? sqrt(l) : (T)0;
-    T acc = 0;
-    for (int b = 0; b < k; ++b) acc = fma(Q[i * kCK + b], V[b * kCKs + order[c]], acc);
-    CnTs[i * R + c] = acc * sig;
+  if (cr == 0) {
+    for (int e = tid; e < r * kCK; e += kCT) {
+      const int i = e >> 4, c = e & 15;
+      if (c >= R) continue;
+      const T l = Kf[order[c] * kCKs + order[c]];
+      const T sig = l > (T)0 ? sqrt(l) : (T)0;
+      T acc = 0;
+      for (int b = 0; b < k; ++b) acc = fma(Q[i * kCK + b], V[b * kCKs + order[c]], acc);
+      CnTs[i * R + c] = acc * sig;
+    }
   }
   __syncthreads();
-  // 7. A = D^T F (unsigned)
-  for (int j = tid; j < s; j += kCT) {
-    T acc[kCK];
-#pragma unroll
-    for (int c = 0; c < kCK; ++c) acc[c] = (T)0;
+  // 7. A = D^T F over the own columns (unsigned): a thread per (column, group of 4
+  //    columns of A)
+  for (int it = tid; it < 4 * w; it += kCT) {
+    const int jj = it >> 2, cg = it & 3;
+    if (4 * cg >= R) continue;
+    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
     for (int b = 0; b < k; ++b) {
-      const T dv = D[(long)b * s + j];
+      const T dv = D[(long)b * ldd + jj];
+      T fv[4];
+      V4<T>::ld(F + b * kCK + 4 * cg, fv);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        T fv[4];
-        V4<T>::ld(F + b * kCK + 4 * q, fv);
-#pragma unroll
-        for (int e = 0; e < 4; ++e) acc[4 * q + e] = fma(dv, fv[e], acc[4 * q + e]);
-      }
+      for (int e = 0; e < 4; ++e) acc[e] = fma(dv, fv[e], acc[e]);
     }
 #pragma unroll
-    for (int c = 0; c < kCK; ++c)
-      if (c < R) Am[(long)j * R + c] = acc[c];
+    for (int e = 0; e < 4; ++e)
+      if (4 * cg + e < R) Am[(long)jj * R + 4 * cg + e] = acc[e];
   }
   __syncthreads();
   // 8. canonical signs (largest-|.| entry of each column of A positive, lowest index on
-  //    ties), then the signed outputs and the core
+  //    ties): each CTA's candidate over its columns, then the cluster's in rank order
   for (int c = warp; c < R; c += kCW) {
     T best = (T)-1;
     int bidx = 0x7fffffff;
-    for (int i = lane; i < s; i += 32) {
+    for (int i = lane; i < w; i += 32) {
       const T v = fabs(Am[(long)i * R + c]);
       if (v > best || (v == best && i < bidx)) {
         best = v;
@@ -1003,37 +1141,59 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
         bidx = oi;
       }
     }
-    if (lane == 0) sgn[c] = (bidx < s && Am[(long)bidx * R + c] < (T)0) ? (T)-1 : (T)1;
-  }
-  __syncthreads();
-  for (int e = tid; e < s * R; e += kCT) {
-    const int c = e % R;
-    a.A_out[e] = sgn[c] * Am[e];
-  }
-  for (int e = tid; e < r * R; e += kCT) {
-    const int rho = e / R, c = e - rho * R;
-    const T v = sgn[c] * CnTs[e];
-    if (a.CnT) a.CnT[e] = v;
-    if (a.core) {
-      long idx = 0, stride = 1, x = rho;
-      for (int kk = a.map.order - 1; kk >= 0; --kk) {
-        int digit;
-        if (kk == a.map.n) {
-          digit = c;
-        } else {
-          digit = (int)(x % a.map.ranks[kk]);
-          x /= a.map.ranks[kk];
-        }
-        idx += digit * stride;
-        stride *= a.map.ranks[kk];
-      }
-      a.core[idx] = v;
+    if (lane == 0) {
+      Xbest[c] = best;
+      Xval[c] = bidx < w ? Am[(long)bidx * R + c] : (T)0;
+      Xidx[c] = bidx < w ? j0 + bidx : 0x7fffffff;
     }
   }
+  cl_sync();
+  if (tid < R) {
+    T best = (T)-1, val = (T)0;
+    int bidx = 0x7fffffff;
+    for (int q = 0; q < kNC; ++q) {
+      const T b = cl_peer(Xbest, q)[tid];
+      const int ix = cl_peer(Xidx, q)[tid];
+      if (b > best || (b == best && ix < bidx)) {
+        best = b;
+        bidx = ix;
+        val = cl_peer(Xval, q)[tid];
+      }
+    }
+    sgn[tid] = val < (T)0 ? (T)-1 : (T)1;
+  }
+  __syncthreads();
+  for (int e = tid; e < w * R; e += kCT) {
+    const int c = e % R;
+    a.A_out[(long)j0 * R + e] = sgn[c] * Am[e];
+  }
+  if (cr == 0) {
+    for (int e = tid; e < r * R; e += kCT) {
+      const int rho = e / R, c = e - rho * R;
+      const T v = sgn[c] * CnTs[e];
+      if (a.CnT) a.CnT[e] = v;
+      if (a.core) {
+        long idx = 0, stride = 1, x = rho;
+        for (int kk = a.map.order - 1; kk >= 0; --kk) {
+          int digit;
+          if (kk == a.map.n) {
+            digit = c;
+          } else {
+            digit = (int)(x % a.map.ranks[kk]);
+            x /= a.map.ranks[kk];
+          }
+          idx += digit * stride;
+          stride *= a.map.ranks[kk];
+        }
+        a.core[idx] = v;
+      }
+    }
+  }
+  cl_sync();  // no CTA leaves while a peer may still read its shared memory
 }
 
 template <typename T, typename U, bool P64>
-__global__ void __launch_bounds__(kCT) k_lrls_chol(FusedArgs<T> a, bool h_smem) {
+__global__ void __cluster_dims__(kNC, 1, 1) __launch_bounds__(kCT) k_lrls_chol(FusedArgs<T> a, bool h_smem) {
   pdl_trigger();
   pdl_wait();
   lrls_chol_body<T, U, P64>(a, h_smem);
@@ -1042,12 +1202,15 @@ __global__ void __launch_bounds__(kCT) k_lrls_chol(FusedArgs<T> a, bool h_smem) 
 // ---------------------------------------------------------------- host side
 
 constexpr size_t kCholReserve = 1024;  // static shared memory of the kernel (~0.2 KB), with slack
+// At least this much dynamic shared memory per CTA, so that no two CTAs of the cluster
+// share an SM (their FP64 units and issue slots would be shared).
+constexpr size_t kCholSpread = 120 * 1024;
 
-// Layout of a subproblem: H copied in when it fits (FP32), else D and A in shared
-// memory when they fit, else in global memory.
+// Layout of a subproblem: the own columns of H copied in when they fit (and A fits in
+// H's rows below D), else D and A in shared memory when they fit, else in global memory.
 static CholLayout chol_pick(int r, int s, int k, int R, size_t tsz, size_t usz) {
   const size_t cap = kMaxSmem - kCholReserve;
-  if (tsz == 4 && R <= r - k) {
+  if (R <= r - k) {
     CholLayout L = chol_layout(r, s, k, R, tsz, usz, true, false, false);
     if (L.total <= cap) return L;
   }
@@ -1071,14 +1234,15 @@ ts_status launch_lrls_chol(const FusedArgs<T>& in, bool fp64, cudaStream_t st) {
   const CholLayout L = chol_pick(a.r, a.s, a.k, a.R, sizeof(T), sizeof(T));
   a.m_smem = L.d_smem;
   const bool h = L.h_smem;
+  const size_t bytes = L.total > kCholSpread ? L.total : kCholSpread;
   if constexpr (sizeof(T) == 4) {
     if (fp64) {  // the precision form: FP64 QR of C and FP64 refinement of K's eigenpairs
-      TS_TRY(ensure_dynamic_smem((const void*)k_lrls_chol<T, T, true>, L.total));
-      return launch_pdl(k_lrls_chol<T, T, true>, dim3(1), dim3(kCT), L.total, st, a, h);
+      TS_TRY(ensure_dynamic_smem((const void*)k_lrls_chol<T, T, true>, bytes));
+      return launch_pdl(k_lrls_chol<T, T, true>, dim3(kNC), dim3(kCT), bytes, st, a, h);
     }
   }
-  TS_TRY(ensure_dynamic_smem((const void*)k_lrls_chol<T, T, false>, L.total));
-  return launch_pdl(k_lrls_chol<T, T, false>, dim3(1), dim3(kCT), L.total, st, a, h);
+  TS_TRY(ensure_dynamic_smem((const void*)k_lrls_chol<T, T, false>, bytes));
+  return launch_pdl(k_lrls_chol<T, T, false>, dim3(kNC), dim3(kCT), bytes, st, a, h);
 }
 
 template ts_status launch_lrls_chol<float>(const FusedArgs<float>&, bool, cudaStream_t);

@@ -365,6 +365,21 @@ def _gram_condition(A):
     return worst
 
 
+def _noise_energy_bound(core_g, core_o, R_cp, T64, res_g, res_o):
+    """Relative residual difference that the noise directions allow.  With orthonormal
+    factors res^2 ||T||^2 = ||T||^2 - ||core||^2; both decompositions hold the signal
+    subspace, and the directions beyond the CP rank (noise) may capture any part of the
+    noise energy.  So |res_g^2 - res_o^2| ||T||^2 is at most the energy that the
+    trailing singular values (index >= R_cp) of each side's core unfoldings carry, and
+    |res_g - res_o| / res_o at most that divided by (res_g + res_o) res_o ||T||^2."""
+    e = 0.0
+    for c in (core_g, core_o):
+        for n in range(3):
+            sv = np.linalg.svd(tucker.unfold(c, n), compute_uv=False)
+            e += float(np.sum(sv[R_cp:] ** 2))
+    return e / ((res_g + res_o) * res_o * float(np.sum(T64 ** 2)))
+
+
 def _cp_stagewise(ts, T, R_cp, tranks, m, tsweeps, csweeps, seed):
     """cp_via_tucker (Alg. 6) on FP32 data, stage by stage against the FP64 oracle:
     (1) the sketched Tucker-ALS it starts from, (2) CP-ALS on the GPU's own Tucker core
@@ -381,6 +396,7 @@ def _cp_stagewise(ts, T, R_cp, tranks, m, tsweeps, csweeps, seed):
     Pg = _signal_projectors(core64, fac64, R_cp)
     Po = _signal_projectors(c_o, f_o, R_cp)
     out = {"tucker_res": abs(float(res[0]) - r_o) / r_o,
+           "tucker_res_bound": _noise_energy_bound(core64, c_o, R_cp, T64, float(res[0]), r_o),
            "tucker_signal_proj": max(np.abs(Pg[n] - Po[n]).max() for n in range(3))}
     A_g = [a.double().cpu().numpy() for a in ts.cp_als(core, R_cp, csweeps)]
     A_o = tucker.cp_als(core64, R_cp, csweeps, tucker.cp_init_hosvd(core64, R_cp))
@@ -433,10 +449,11 @@ def test_cp_via_tucker_fp32_collinear_workload(ts):
     # directions near 0.001.  FP32 rounding relative to the dominant direction is ~60x
     # larger relative to the signal, so: the noise directions' projectors may differ by
     # O(0.1); the signal subspace (10 leading directions, gap 0.014) is held to 1e-2;
-    # the residual, whose last digits the noise directions carry, to 5e-3 relative.
+    # the residual, whose last digits the noise directions carry, to the energy those
+    # directions hold (plus FP32 rounding).
     d = _cp_stagewise(ts, T, 10, tranks, m, 2, 25, seed=1)
     assert d["tucker_signal_proj"] <= 1e-2
-    assert d["tucker_res"] <= 5e-3
+    assert d["tucker_res"] <= d["tucker_res_bound"] + 1e-5
     # CP-ALS on factors of pairwise cosine 0.9: cond(Gamma) of the normal equations is
     # ~1e3 to 1e5 (measured), which turns FP32 rounding into trajectories that differ
     # pointwise (the arithmetic itself is pinned at 1e-5 on a well-conditioned core); the
@@ -454,7 +471,7 @@ def test_cp_via_tucker_collinear_workload_full_size(ts):
     # 5 noise directions per mode), held to the same bounds.
     d = _cp_stagewise(ts, T, 20, (25, 25, 25), 3000, 5, 25, seed=3)
     assert d["tucker_signal_proj"] <= 1e-2
-    assert d["tucker_res"] <= 5e-3
+    assert d["tucker_res"] <= d["tucker_res_bound"] + 1e-5
     # CP-ALS on factors of pairwise cosine 0.9: cond(Gamma) of the normal equations is
     # ~1e3 to 1e5 (measured), which turns FP32 rounding into trajectories that differ
     # pointwise (the arithmetic itself is pinned at 1e-5 on a well-conditioned core); the

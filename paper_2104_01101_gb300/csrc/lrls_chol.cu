@@ -115,8 +115,9 @@ __host__ __device__ inline CholLayout chol_layout(int r, int s, int k, int R, si
   L.V = L.K1 + kb;
   L.F = L.V + kb;
   L.CnT = L.F + ((tsz * kCK * kCK + 15) & ~(size_t)15);
-  // exchange with the peers: a 16 x 17 FP64 partial (Gram or K) and the sign candidates
-  L.X = take(8 * 16 * 17 + 3 * 16 * 8);
+  // exchange with the peers, one slot per CTA of the cluster: a 16 x 17 FP64 partial
+  // (Gram or K) and the sign candidates
+  L.X = take((size_t)kNC * 8 * (16 * 17 + 3 * 16));
   L.total = off;
   return L;
 }
@@ -632,9 +633,10 @@ __device__ T* cj_jacobi_warp(T* K, T* K2, T* V, int max_sweeps) {
 // (elimination, triangular products, Householder QR, Jacobi) on identical data, so they
 // hold identical results, and each owns a slice of the work that is wide rather than
 // deep: columns [j0, j1) of H, D and A, rows [i0, i1) of C for the FP64 products and two
-// rows of the 16 x 16 eigen refinement.  Partial results go to the peers through
-// distributed shared memory: written into a CTA's own buffer, a cluster barrier, read
-// from the peers' buffers (sums always in rank order, so every CTA gets the same bits).
+// columns of the 16 x 16 eigen refinement.  Partial results are pushed: a CTA stores its
+// part into its own slot (or rows) of every CTA's buffer through distributed shared
+// memory, a cluster barrier (release / acquire) makes the stores visible, and every read
+// is then local (sums always in rank order, so every CTA gets the same bits).
 template <typename P>
 __device__ __forceinline__ P* cl_peer(P* p, int rank) {
   return cg::this_cluster().map_shared_rank(p, rank);
@@ -714,8 +716,8 @@ __device__ double p64_ldl(double& v, int k, double thr, double* pub) {
 // is then taken to first order, N = I - strictly_lower(S - I), D^{-1/2} = I - diag(S - I)
 // / 2, whose error is second order (below 2^-40); otherwise the full LDL^T runs again.
 // On return every CTA holds all of Qout (zero columns >= k; Qout may be C).  S: 16 x 17
-// FP64 and a scalar after it (kP64Scal); dsq: 16; Cd: 16 x 16 FP64 (own rows); Xg: 16 x 17
-// FP64, read by the peers; pub: 66 FP64.
+// FP64 and a scalar after it (kP64Scal); dsq: 16; Cd: 16 x 16 FP64 (own rows); Xg: kNC
+// slots of 16 x 17 FP64 (the peers store theirs here); pub: 66 FP64.
 template <typename T>
 __device__ void p64_cholqr_pass(const T* C, T* Qout, int r, int k, int i0, int i1, bool second,
                                 double* S, double* dsq, double* Cd, double* Xg, double* pub) {
@@ -743,7 +745,10 @@ __device__ void p64_cholqr_pass(const T* C, T* Qout, int r, int k, int i0, int i
     }
     acc += __shfl_xor_sync(kAll, acc, 1);
     acc += __shfl_xor_sync(kAll, acc, 2);
-    if (pr < npair && part == 0) Xg[b * 17 + a] = acc;
+    if (pr < npair && part == 0) {
+#pragma unroll
+      for (int q = 0; q < kNC; ++q) cl_peer(Xg, q)[cr * 272 + b * 17 + a] = acc;
+    }
   }
   cl_sync();
   const int i = tid >> 4, c = tid & 15;
@@ -751,7 +756,7 @@ __device__ void p64_cholqr_pass(const T* C, T* Qout, int r, int k, int i0, int i
   if (ent) {
     double sum = 0;
 #pragma unroll
-    for (int q = 0; q < kNC; ++q) sum += cl_peer(Xg, q)[i * 17 + c];
+    for (int q = 0; q < kNC; ++q) sum += Xg[q * 272 + i * 17 + c];
     S[i * 17 + c] = sum;
     S[c * 17 + i] = sum;
   }
@@ -792,16 +797,11 @@ __device__ void p64_cholqr_pass(const T* C, T* Qout, int r, int k, int i0, int i
     double acc = 0;
     if (cc < k)
       for (int a = 0; a <= cc; ++a) acc = fma(Cd[ii * kCK + a], S[cc * 17 + a], acc);
-    Qout[(i0 + ii) * kCK + cc] = cc < k ? (T)(acc * dsq[cc]) : (T)0;
+    const T qv = cc < k ? (T)(acc * dsq[cc]) : (T)0;
+#pragma unroll
+    for (int q = 0; q < kNC; ++q) cl_peer(Qout, q)[(i0 + ii) * kCK + cc] = qv;
   }
   cl_sync();
-  for (int q = 0; q < kNC; ++q) {  // the peers' rows
-    if (q == cr) continue;
-    const int b0 = r * q / kNC, b1 = r * (q + 1) / kNC;
-    const T* src = cl_peer(Qout, q);
-    for (int e = tid; e < (b1 - b0) * kCK; e += kCT) Qout[b0 * kCK + e] = src[b0 * kCK + e];
-  }
-  __syncthreads();
 }
 
 // One FP64 refinement of the eigen-decomposition K ~ X diag(lambda) X^T from the FP32
@@ -812,11 +812,11 @@ __device__ void p64_cholqr_pass(const T* C, T* Qout, int r, int k, int i0, int i
 // determined); E_jj = R_jj / 2; X <- X + X E.  mu are the Jacobi's eigenvalues: they
 // enter E only through the gaps and through mu_j R_aj with R_aj itself of the order of the
 // Jacobi's error, so their error reaches X at second order.  This CTA computes columns
-// 2 cr, 2 cr + 1 of E and of X + X E (4 threads per entry) and lambda for them; one
-// cluster barrier, then every CTA gathers the other columns.  Kd: K in FP64 (16 x 17);
-// X (16 x 17, T, columns are eigenvectors) is overwritten, and so is the diagonal of Kf
-// (T; the Jacobi's eigenvalues on entry).  ws: kRefineWs FP64 (the last blocks are read
-// by the peers).
+// 2 cr, 2 cr + 1 of E and of X + X E (4 threads per entry) and lambda for them, stores
+// them into every CTA's Xn and lam, and after one cluster barrier converts the whole of
+// Xn and lam.  Kd: K in FP64 (16 x 17); X (16 x 17, T, columns are eigenvectors) is
+// overwritten, and so is the diagonal of Kf (T; the Jacobi's eigenvalues on entry).  ws:
+// kRefineWs FP64 (Xn and lam receive the peers' columns).
 template <typename T>
 __device__ void p64_eig_refine(const double* Kd, T* X, T* Kf, double* ws) {
   const int tid = threadIdx.x, cr = (int)cg::this_cluster().block_rank();
@@ -865,7 +865,9 @@ __device__ void p64_eig_refine(const double* Kd, T* X, T* Kf, double* ws) {
       double e;
       if (a == j) {
         e = 0.5 * rv;
-        lam[j] = sv / (1.0 - rv);
+        const double lj = sv / (1.0 - rv);
+#pragma unroll
+        for (int p = 0; p < kNC; ++p) cl_peer(lam, p)[j] = lj;
       } else {
         const double gap = mu[j] - mu[a];
         e = fabs(gap) > 1e-5 * mu[16] ? (sv + mu[j] * rv) / gap : 0.5 * rv;
@@ -880,18 +882,15 @@ __device__ void p64_eig_refine(const double* Kd, T* X, T* Kf, double* ws) {
     for (int b = 4 * q; b < 4 * q + 4; ++b) acc = fma(Xd[a * 17 + b], Ec[b * 2 + (j & 1)], acc);
     acc += __shfl_xor_sync(kAll, acc, 1);
     acc += __shfl_xor_sync(kAll, acc, 2);
-    if (q == 0) Xn[a * 17 + j] = Xd[a * 17 + j] + acc;
+    if (q == 0) {
+      const double xn = Xd[a * 17 + j] + acc;
+#pragma unroll
+      for (int p = 0; p < kNC; ++p) cl_peer(Xn, p)[a * 17 + j] = xn;
+    }
   }
   cl_sync();
-  if (tid < 256) {
-    const int ii = tid >> 4, jj = tid & 15, owner = jj >> 1;
-    const double v = owner == cr ? Xn[ii * 17 + jj] : cl_peer(Xn, owner)[ii * 17 + jj];
-    X[ii * kCKs + jj] = (T)v;
-  }
-  if (tid >= 256 && tid < 256 + kCK) {
-    const int l = tid - 256, owner = l >> 1;
-    Kf[l * kCKs + l] = (T)(owner == cr ? lam[l] : cl_peer(lam, owner)[l]);
-  }
+  if (tid < 256) X[(tid >> 4) * kCKs + (tid & 15)] = (T)Xn[(tid >> 4) * 17 + (tid & 15)];
+  if (tid >= 256 && tid < 256 + kCK) Kf[(tid - 256) * kCKs + (tid - 256)] = (T)lam[tid - 256];
   __syncthreads();
 }
 
@@ -927,10 +926,11 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
   T* V = reinterpret_cast<T*>(smem_raw + L.V);
   T* F = reinterpret_cast<T*>(smem_raw + L.F);
   T* CnTs = reinterpret_cast<T*>(smem_raw + L.CnT);
-  double* Xg = reinterpret_cast<double*>(smem_raw + L.X);  // exchange: Gram / K partials
-  T* Xbest = reinterpret_cast<T*>(smem_raw + L.X + 17 * 16 * 8);
-  T* Xval = Xbest + kCK;
-  int* Xidx = reinterpret_cast<int*>(Xval + kCK);
+  // exchange slots (one per CTA): Gram / K partials, then the sign candidates
+  double* Xg = reinterpret_cast<double*>(smem_raw + L.X);
+  T* Xbest = reinterpret_cast<T*>(smem_raw + L.X + (size_t)kNC * 16 * 17 * 8);
+  T* Xval = Xbest + kNC * kCK;
+  int* Xidx = reinterpret_cast<int*>(Xval + kNC * kCK);
   // D (k x w) and A (w x R) of the own columns: in shared memory (row stride sw for D)
   // or in the caller's buffers (row stride s for D; A's rows j0 .. j0 + w - 1)
   const bool d_sm = h_smem || L.d_smem, a_sm = h_smem || L.a_smem;
@@ -1036,14 +1036,17 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
       }
       acc += __shfl_xor_sync(kAll, acc, 1);
       acc += __shfl_xor_sync(kAll, acc, 2);
-      if (pr < 136 && part == 0) Kp[ia * kCKs + ib] = acc;
+      if (pr < 136 && part == 0) {
+#pragma unroll
+        for (int q = 0; q < kNC; ++q) cl_peer(Kp, q)[cr * 272 + ia * kCKs + ib] = acc;
+      }
     }
     cl_sync();
     if (tid < kCK * kCK) {
       const int i = tid >> 4, j = tid & 15;
       const int lo = min(i, j), hi = max(i, j);
       T sum = 0;
-      for (int q = 0; q < kNC; ++q) sum += cl_peer(Kp, q)[lo * kCKs + hi];
+      for (int q = 0; q < kNC; ++q) sum += Kp[q * 272 + lo * kCKs + hi];
       K0[i * kCKs + j] = sum;
     }
     __syncthreads();
@@ -1142,9 +1145,14 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
       }
     }
     if (lane == 0) {
-      Xbest[c] = best;
-      Xval[c] = bidx < w ? Am[(long)bidx * R + c] : (T)0;
-      Xidx[c] = bidx < w ? j0 + bidx : 0x7fffffff;
+      const T val = bidx < w ? Am[(long)bidx * R + c] : (T)0;
+      const int gidx = bidx < w ? j0 + bidx : 0x7fffffff;
+#pragma unroll
+      for (int q = 0; q < kNC; ++q) {
+        cl_peer(Xbest, q)[cr * kCK + c] = best;
+        cl_peer(Xval, q)[cr * kCK + c] = val;
+        cl_peer(Xidx, q)[cr * kCK + c] = gidx;
+      }
     }
   }
   cl_sync();
@@ -1152,12 +1160,12 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
     T best = (T)-1, val = (T)0;
     int bidx = 0x7fffffff;
     for (int q = 0; q < kNC; ++q) {
-      const T b = cl_peer(Xbest, q)[tid];
-      const int ix = cl_peer(Xidx, q)[tid];
+      const T b = Xbest[q * kCK + tid];
+      const int ix = Xidx[q * kCK + tid];
       if (b > best || (b == best && ix < bidx)) {
         best = b;
         bidx = ix;
-        val = cl_peer(Xval, q)[tid];
+        val = Xval[q * kCK + tid];
       }
     }
     sgn[tid] = val < (T)0 ? (T)-1 : (T)1;
@@ -1189,11 +1197,10 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
       }
     }
   }
-  cl_sync();  // no CTA leaves while a peer may still read its shared memory
 }
 
 template <typename T, typename U, bool P64>
-__global__ void __cluster_dims__(kNC, 1, 1) __launch_bounds__(kCT) k_lrls_chol(FusedArgs<T> a, bool h_smem) {
+__global__ void __cluster_dims__(kNC, 1, 1) __launch_bounds__(kCT, 1) k_lrls_chol(FusedArgs<T> a, bool h_smem) {
   pdl_trigger();
   pdl_wait();
   lrls_chol_body<T, U, P64>(a, h_smem);

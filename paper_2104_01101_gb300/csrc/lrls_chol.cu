@@ -1206,6 +1206,96 @@ __global__ void __cluster_dims__(kNC, 1, 1) __launch_bounds__(kCT, 1) k_lrls_cho
   lrls_chol_body<T, U, P64>(a, h_smem);
 }
 
+// ---------------------------------------------------------------- small eigensolver
+
+// K (n x n, n <= 16, symmetrised) = U Lambda U^T by the one-warp Jacobi above and, with
+// P64, one FP64 refinement over the cluster; eigenvalues descending (ties in index
+// order), sigma = sqrt(lambda).  Outputs as the general eigensolver's: Fm = U_R
+// Sigma_R^{-1} and Uout = U_R (n x R), CnT = Q U_R Sigma_R (r x R; Q null: U_R Sigma_R,
+// r = n); each may be null; CTA 0 writes them.  A non-finite eigenvalue sets *flag.
+template <typename T, bool P64>
+__global__ void __cluster_dims__(kNC, 1, 1) __launch_bounds__(kCT, 1)
+    k_eig16(int n, int R, const T* __restrict__ K, const T* __restrict__ Q, int r,
+            T* __restrict__ CnT, T* __restrict__ Fm, T* __restrict__ Uout, int* flag) {
+  pdl_trigger();
+  pdl_wait();
+  __shared__ __align__(16) T K0[kCK * kCKs], K1[kCK * kCKs], V[kCK * kCKs];
+  __shared__ __align__(16) double ws[P64 ? kRefineWs + kCK * 17 : 1];
+  __shared__ int order[kCK];
+  __shared__ T* Kfin;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid < kCK * kCK) {
+    const int i = tid >> 4, j = tid & 15;
+    const T v = (i < n && j < n) ? (T)0.5 * (K[i * n + j] + K[j * n + i]) : (T)0;
+    K0[i * kCKs + j] = v;
+    if constexpr (P64) ws[kRefineWs + i * 17 + j] = (double)v;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    T* Kf = cj_jacobi_warp<T>(K0, K1, V, 20);
+    if (lane == 0) Kfin = Kf;
+  }
+  __syncthreads();
+  T* Kf = Kfin;
+  if constexpr (P64) p64_eig_refine<T>(ws + kRefineWs, V, Kf, ws);
+  if (tid < kCK) order[tid] = tid;  // stays a valid index if a NaN breaks the ranking
+  __syncthreads();
+  if (tid < kCK) {
+    const bool real = tid < n;
+    const T l = Kf[tid * kCKs + tid];
+    int rank = 0;
+    for (int j = 0; j < kCK; ++j) {
+      const T o = Kf[j * kCKs + j];
+      rank += (j < n) ? (!real || o > l || (o == l && j < tid)) : (!real && j < tid);
+    }
+    order[rank] = tid;
+    if (real && !isfinite(l) && flag) atomicExch(flag, 1);
+  }
+  __syncthreads();
+  if (cg::this_cluster().block_rank() != 0) return;
+  for (int e = tid; e < n * R; e += kCT) {
+    const int i = e / R, c = e - (e / R) * R;
+    const T l = Kf[order[c] * kCKs + order[c]];
+    const T sig = l > (T)0 ? sqrt(l) : (T)0;
+    const T u = V[i * kCKs + order[c]];
+    if (Fm) Fm[e] = sig > (T)0 ? u / sig : (T)0;
+    if (Uout) Uout[e] = u;
+  }
+  if (CnT)
+    for (int e = tid; e < r * R; e += kCT) {
+      const int i = e / R, c = e - (e / R) * R;
+      const T l = Kf[order[c] * kCKs + order[c]];
+      const T sig = l > (T)0 ? sqrt(l) : (T)0;
+      T acc;
+      if (Q) {
+        acc = 0;
+        for (int a = 0; a < n; ++a) acc = fma(Q[(long)i * n + a], V[a * kCKs + order[c]], acc);
+      } else {
+        acc = V[i * kCKs + order[c]];
+      }
+      CnT[e] = acc * sig;
+    }
+}
+
+template <typename T>
+ts_status launch_eig16(int n, int R, const T* K, const T* Q, int r, T* CnT, T* Fm, T* Uout,
+                       bool fp64, int* flag, cudaStream_t st) {
+  if (n < 1 || n > kCK || R < 1 || R > n)
+    return fail(TS_ERR_SHAPE, "eigensolver: n=%d R=%d outside 1 <= R <= n <= %d", n, R, kCK);
+  if constexpr (sizeof(T) == 4) {
+    if (fp64)
+      return launch_pdl(k_eig16<T, true>, dim3(kNC), dim3(kCT), 0, st, n, R, K, Q, r, CnT, Fm,
+                        Uout, flag);
+  }
+  return launch_pdl(k_eig16<T, false>, dim3(kNC), dim3(kCT), 0, st, n, R, K, Q, r, CnT, Fm, Uout,
+                    flag);
+}
+
+template ts_status launch_eig16<float>(int, int, const float*, const float*, int, float*, float*,
+                                       float*, bool, int*, cudaStream_t);
+template ts_status launch_eig16<double>(int, int, const double*, const double*, int, double*,
+                                        double*, double*, bool, int*, cudaStream_t);
+
 // ---------------------------------------------------------------- host side
 
 constexpr size_t kCholReserve = 1024;  // static shared memory of the kernel (~0.2 KB), with slack

@@ -1,25 +1,30 @@
-// RSVD-LRLS (Alg. 5) of one sketched subproblem in ONE thread block, organised around
-// the short dependency chains of a single SM.  Inputs are the blocks of the augmented
-// product [G | W | H] = Z^T [Z | Y Omega | Y] (G = Z^T Z, r x r SPD; W, r x k; H, r x s).
+// RSVD-LRLS (Alg. 5) of one sketched subproblem on one cluster of 8 CTAs (one per SM),
+// organised around short dependency chains: every CTA runs steps 1-3 and 5 on identical
+// data, and the wide parts (D, K, A and the signs over column slices of H; the FP64
+// products of the precision form) are split over the cluster (see "cluster exchange"
+// below).  Inputs are the blocks of the augmented product [G | W | H] =
+// Z^T [Z | Y Omega | Y] (G = Z^T Z, r x r SPD; W, r x k; H, r x s).
 //
 //   1. Symmetric elimination (G = L D L^T, L unit lower) of the augmented block [G | W],
-//      one pivot per step, held in registers by NWE warps: warp w owns the RS consecutive
-//      rows RS w .. RS w + RS - 1, lane l the 4 consecutive columns 4 l .. 4 l + 3 of
-//      [G | W].  As column j of G is eliminated it is replaced in place by column j of
-//      N = L^{-1} (the in-place inverse), so after r steps the registers hold N (strictly
-//      lower), D (diagonal) and N W.  Step j reads the "cross" of pivot j (row j of N and
-//      W, column j of G, the pivot's reciprocal) from a double-buffered shared row that
-//      the owners of pivot j+1 fill during step j: one barrier per pivot.  The pivot loop
-//      runs over (row block, row slot) with the slot a compile-time index, so the slot
-//      of every row, the column slot of the pivot and which rows are still active are
-//      all known at compile time.  Meanwhile the other warps copy H into shared memory.
+//      held in registers by NWE warps: warp w owns the RS consecutive rows RS w ..
+//      RS w + RS - 1 (whole rows: both triangles of G), lane l the 4 consecutive columns
+//      4 l .. 4 l + 3 of [G | W].  As column j of G is eliminated it is replaced in place
+//      by column j of N = L^{-1} (the in-place inverse), so after r steps the registers
+//      hold N (strictly lower), D (diagonal) and N W.  Pivots go in groups of four, the
+//      rows of one warp: their owner eliminates them among themselves and publishes the
+//      four rows with their pivots' reciprocals through a double-buffered shared buffer;
+//      every warp then applies the four pivots to its rows below them, each row's
+//      multiplier being its own entry in the pivot's column.  One barrier per four pivots.
+//      Meanwhile asynchronous copies bring this CTA's columns of H into shared memory.
 //   2. B = G^{-1} = N^T D^{-1} N is never formed: C = B W = N^T (D^{-1} (N W)) and
 //      E = B Q = N^T (D^{-1} (N Q)) are triangular products with k <= 16 columns.
 //   3. Q = qr(C): Householder, warp c owning column c (one barrier per reflector), then
-//      warp c forms column c of Q.
-//   4. D = E^T H (k x s; E^T H = Q^T B Z^T Y of Alg. 5), K = D D^T.
+//      warp c forms column c of Q; in the precision form FP64 CholeskyQR2 instead.
+//   4. D = E^T H (k x s; E^T H = Q^T B Z^T Y of Alg. 5) over each CTA's columns, K = D D^T
+//      summed over the cluster.
 //   5. K = U Lambda U^T by cyclic Jacobi in ONE warp (round-robin pairs; rotations of a
-//      round applied as 2 x 2 block updates into a second buffer; no block barrier).
+//      round applied as 2 x 2 block updates into a second buffer; no block barrier); in
+//      the precision form one FP64 refinement of the eigenpairs follows.
 //   6. C_(n)^T = Q U_R Sigma_R, A^(n) = D^T U_R Sigma_R^{-1}, canonical column signs, core.
 #include <cooperative_groups.h>
 
@@ -34,7 +39,7 @@ constexpr int kCT = 512;  // threads of the block
 constexpr int kCW = kCT / 32;
 constexpr int kCK = 16;    // widest RSVD sketch (k) and Jacobi order
 constexpr int kCKs = 17;   // row stride of the k x k Jacobi buffers
-constexpr int kCX = 132;   // one cross: 128 columns + the pivot's reciprocal at kCX - 1
+constexpr int kCX = 132;   // one pivot row: 128 columns + the pivot's reciprocal at kCX - 1
 constexpr int kCMax = 128; // r + k limit of the elimination tile
 constexpr unsigned kAll = 0xffffffffu;
 constexpr int kNC = 8;  // CTAs of the cluster that shares one subproblem (one per SM)
@@ -102,7 +107,7 @@ __host__ __device__ inline CholLayout chol_layout(int r, int s, int k, int R, si
   L.Y = take(y_bytes > y64 ? y_bytes : y64);
   L.Q = take(tsz * (size_t)r * kCK);
   L.E = take(tsz * (size_t)r * kCK);
-  L.buf = take(tsz * 2 * kCX > 66 * 8 ? tsz * 2 * kCX : 66 * 8);
+  L.buf = take(tsz * 8 * kCX > 66 * 8 ? tsz * 8 * kCX : 66 * 8);
   // the QR workspace, then (after Q is formed) the Jacobi buffers and C_(n)^T
   const size_t qr = ((usz * (size_t)r * 17 + 15) & ~(size_t)15) + usz * kCK;
   const size_t kb = ((tsz * kCK * kCKs + 15) & ~(size_t)15);
@@ -163,119 +168,103 @@ __device__ __forceinline__ float elim_rcp(float v) {
 }
 __device__ __forceinline__ double elim_rcp(double v) { return 1.0 / v; }
 
-// Row j + 1's part of the next cross: its N part (c < jn), its W part and the reciprocal
-// of its pivot (the pivot itself goes out with its column).
-template <typename T>
-__device__ __forceinline__ void elim_row_publish(const T (&xr)[4], int jn, int r, int k, T* nxt,
-                                                 int* flag) {
+// ---- full rows, four pivots per barrier
+//
+// Each warp keeps its rows of [G | W] whole (both triangles of G), so the row of a pivot
+// is all in its owner warp: no column has to be gathered from the other warps.  The four
+// pivot rows of group g (pivots 4g .. 4g + 3, rows of one warp) are published together,
+// already eliminated among themselves by the owner; every warp then applies the four
+// pivots in turn to its rows below them, a row's multiplier being its own entry in the
+// pivot's column (lane g, slot b).  One barrier per four pivots.
+
+// The owner of group g publishes its rows (slots O .. O + 3 of x, every earlier pivot
+// applied), eliminated among themselves, to dst (4 x kCX; entry kCX - 1 of row b holds
+// the reciprocal of pivot 4g + b).  A non-positive or non-finite pivot sets *flag and is
+// replaced by 1.
+template <typename T, int RS, int O>
+__device__ __forceinline__ void elim_publish_group(const T (&x)[RS][4], int g, int r, T* dst,
+                                                   int* flag) {
   const int lane = threadIdx.x & 31;
+  T y[4][4];
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int c = 4 * lane + u;
-    const T v = xr[u];
-    if (c < jn || (c >= r && c - r < k)) nxt[c] = v;
-    if (c == jn) {
-      const bool bad = !(v > (T)0) || !isfinite(v);
-      if (bad && flag) atomicExch(flag, 1);
-      nxt[kCX - 1] = elim_rcp(bad ? (T)1 : v);
+  for (int b = 0; b < 4; ++b)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) y[b][u] = x[O + b][u];
+#pragma unroll
+  for (int b = 0; b < 4; ++b) {
+    if (4 * g + b >= r) break;
+    const T d = __shfl_sync(kAll, y[b][b], g);
+    const bool bad = !(d > (T)0) || !isfinite(d);
+    if (bad && lane == 0 && flag) atomicExch(flag, 1);
+    const T inv = elim_rcp(bad ? (T)1 : d);
+    V4<T>::st(dst + b * kCX + 4 * lane, y[b]);
+    if (lane == 0) dst[b * kCX + kCX - 1] = inv;
+#pragma unroll
+    for (int b2 = b + 1; b2 < 4; ++b2) {
+      const T mm = __shfl_sync(kAll, y[b2][b], g) * inv;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) y[b2][u] = fma(-mm, y[b][u], y[b2][u]);
+      if (lane == g) y[b2][b] = -mm;  // column 4g + b of the row becomes column of N
     }
   }
 }
 
-// Row `slot` of the tile by a select tree (no dynamic register index).
-template <typename T, int RS>
-__device__ __forceinline__ void elim_pick_row(const T (&x)[RS][4], int slot, T (&v)[4]) {
-  static_assert(RS == 4 || RS == 8, "select tree for 4 or 8 rows");
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const bool b0 = slot & 1, b1 = slot & 2;
-    const T a01 = b0 ? x[1][u] : x[0][u], a23 = b0 ? x[3][u] : x[2][u];
-    T lo = b1 ? a23 : a01;
-    if constexpr (RS == 8) {
-      const T a45 = b0 ? x[5][u] : x[4][u], a67 = b0 ? x[7][u] : x[6][u];
-      const T hi = b1 ? a67 : a45;
-      lo = (slot & 4) ? hi : lo;
-    }
-    v[u] = lo;
-  }
-}
-
-// Pivot j = 4 jb + U0 (U0 static: the pivot's column slot and the buffer parity).  Warps
-// whose rows are all above or at the pivot only wait at the barrier; the warp holding
-// the pivot row updates the rows below it under predicates (no branches, so its loads
-// are not serialised); the others update all their rows and publish column j + 1 with
-// vector stores.
-template <typename T, int NWE, int RS, int U0>
-__device__ __forceinline__ void elim_step(T (&x)[RS][4], int j, int r, int k, T* buf, int* flag) {
+// Group g's pivots applied to every row below them (GODD = g & 1: where the next group's
+// rows sit in their owner warp), then the next group's rows published.
+template <typename T, int NWE, int RS, int GODD>
+__device__ __forceinline__ void elim_group_step(T (&x)[RS][4], int g, int r, T* buf, int* flag) {
+  constexpr int ON = RS == 4 ? 0 : (GODD ? 0 : 4);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  constexpr int UJ = U0, UJN = (U0 + 1) & 3;
-  const int rb0 = RS * w;
-  if (rb0 + RS - 1 > j) {
-    const T* cur = buf + (U0 & 1) * kCX;  // j = 4 jb + U0 has the parity of U0
-    T* nxt = buf + ((U0 & 1) ^ 1) * kCX;
-    const T inv = cur[kCX - 1];
-    T colv[4];
-    V4<T>::ld(cur + 4 * lane, colv);
-    T mv[RS];
+  const int rb0 = RS * w, p0 = 4 * g;
+  const T* cur = buf + (g & 1) * 4 * kCX;
+  T* nxt = buf + ((g & 1) ^ 1) * 4 * kCX;
+  if (rb0 > p0 + 3) {  // every row of this warp is below the group: no predicates
 #pragma unroll
-    for (int q = 0; q < RS / 4; ++q) {
-      T t4[4];
-      V4<T>::ld(cur + rb0 + 4 * q, t4);
+    for (int b = 0; b < 4; ++b) {
+      if (p0 + b >= r) break;
+      const T inv = cur[b * kCX + kCX - 1];
+      T v[4];
+      V4<T>::ld(cur + b * kCX + 4 * lane, v);
+      const bool fix = lane == g;
 #pragma unroll
-      for (int e = 0; e < 4; ++e) mv[4 * q + e] = t4[e] * inv;
+      for (int t = 0; t < RS; ++t) {
+        const T mm = __shfl_sync(kAll, x[t][b], g) * inv;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) x[t][u] = fma(-mm, v[u], x[t][u]);
+        if (fix) x[t][b] = -mm;  // column p of G becomes column p of N
+      }
     }
-    const int jn = j + 1;
-    const bool fix = lane == (j >> 2);
-    const bool pub = lane == (jn >> 2) && jn < r;
-    if (rb0 > j) {  // every row of this warp is below the pivot
+  } else if (rb0 + RS - 1 > p0) {  // the warp that holds the group: rows below a pivot only
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int p = p0 + b;
+      if (p >= r) break;
+      const T inv = cur[b * kCX + kCX - 1];
+      T v[4];
+      V4<T>::ld(cur + b * kCX + 4 * lane, v);
 #pragma unroll
       for (int t = 0; t < RS; ++t) {
-#pragma unroll
-        for (int u = 0; u < 4; ++u) x[t][u] = fma(-mv[t], colv[u], x[t][u]);
-        if (fix) x[t][UJ] = -mv[t];  // column j of G becomes column j of N
-      }
-      if (pub) {  // column j + 1 on this warp's rows
-        if (rb0 + RS <= r) {
-#pragma unroll
-          for (int q = 0; q < RS / 4; ++q) {
-            T o[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) o[e] = x[4 * q + e][UJN];
-            V4<T>::st(nxt + rb0 + 4 * q, o);
-          }
-        } else {
-#pragma unroll
-          for (int t = 0; t < RS; ++t)
-            if (rb0 + t < r) nxt[rb0 + t] = x[t][UJN];
-        }
-      }
-    } else {  // the pivot row's warp: rows below the pivot
-#pragma unroll
-      for (int t = 0; t < RS; ++t) {
-        const bool act = rb0 + t > j;
+        const bool act = rb0 + t > p;
+        const T mm = __shfl_sync(kAll, x[t][b], g) * inv;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const T nv = fma(-mv[t], colv[u], x[t][u]);
+          const T nv = fma(-mm, v[u], x[t][u]);
           x[t][u] = act ? nv : x[t][u];
         }
-        if (act && fix) x[t][UJ] = -mv[t];
-        if (act && pub && rb0 + t < r) nxt[rb0 + t] = x[t][UJN];
+        if (act && lane == g) x[t][b] = -mm;
       }
     }
-    if (jn < r && w == jn / RS) {  // row j + 1 (updated above by this warp)
-      T v[4];
-      elim_pick_row<T, RS>(x, jn % RS, v);
-      elim_row_publish<T>(v, jn, r, k, nxt, flag);
-    }
   }
+  const int gn = g + 1;
+  if (4 * gn < r && w == (4 * gn) / RS) elim_publish_group<T, RS, ON>(x, gn, r, nxt, flag);
   elim_sync(NWE * 32);
 }
 
-// Symmetric elimination of [G | W] (r + k <= 128) by warps 0 .. NWE - 1; on exit N (unit
-// lower, r x ldn, zeros above), dinv = D^{-1} and Y = N W (r x 16, zero columns >= k)
-// are in shared memory (the caller synchronises the block).  A non-positive or
-// non-finite pivot sets *flag and is replaced by 1.  Tile slots above the diagonal and
-// beyond W take harmless garbage: they are never published and the dump masks them.
+// Symmetric elimination of [G | W] (r + k <= 128) by warps 0 .. NWE - 1 in groups of four
+// pivots (above); on exit N (unit lower, r x ldn, zeros above), dinv = D^{-1} and
+// Y = N W (r x 16, zero columns >= k) are in shared memory (the caller synchronises the
+// block).  A non-positive or non-finite pivot sets *flag and is replaced by 1.  Tile
+// slots beyond W take harmless garbage, and the dump masks the upper triangle.
 template <typename T, int NWE, int RS>
 __device__ void chol_eliminate(const T* __restrict__ G, long ldg, const T* __restrict__ W,
                                long ldw, int r, int k, T* buf, T* Nm, int ldn, T* dinv, T* Y,
@@ -291,7 +280,7 @@ __device__ void chol_eliminate(const T* __restrict__ G, long ldg, const T* __res
       T v = (T)0;
       if (i < r) {
         if (c < r) {
-          if (c <= i) v = G[(long)i * ldg + c];
+          v = G[(long)i * ldg + c];
         } else if (c - r < k) {
           v = W[(long)i * ldw + (c - r)];
         }
@@ -299,22 +288,12 @@ __device__ void chol_eliminate(const T* __restrict__ G, long ldg, const T* __res
       x[t][u] = v;
     }
   }
-  for (int e = tid; e < 2 * kCX; e += NWE * 32) buf[e] = (T)0;
+  // group 0's rows from warp 0, then one step per group of four pivots
+  if (w == 0) elim_publish_group<T, RS, 0>(x, 0, r, buf, flag);
   elim_sync(NWE * 32);
-  // cross of pivot 0: column 0 (every row; the pivot included) from lane 0, row 0's W
-  // part and the pivot's reciprocal from warp 0
-  if (lane == 0) {
-#pragma unroll
-    for (int t = 0; t < RS; ++t)
-      if (RS * w + t < r) buf[RS * w + t] = x[t][0];
-  }
-  if (w == 0) elim_row_publish<T>(x[0], 0, r, k, buf, flag);
-  elim_sync(NWE * 32);
-  for (int j = 0; j < r; j += 4) {
-    elim_step<T, NWE, RS, 0>(x, j, r, k, buf, flag);
-    if (j + 1 < r) elim_step<T, NWE, RS, 1>(x, j + 1, r, k, buf, flag);
-    if (j + 2 < r) elim_step<T, NWE, RS, 2>(x, j + 2, r, k, buf, flag);
-    if (j + 3 < r) elim_step<T, NWE, RS, 3>(x, j + 3, r, k, buf, flag);
+  for (int g = 0; 4 * g < r; g += 2) {
+    elim_group_step<T, NWE, RS, 0>(x, g, r, buf, flag);
+    if (4 * (g + 1) < r) elim_group_step<T, NWE, RS, 1>(x, g + 1, r, buf, flag);
   }
   // N (unit diagonal, zeros above), D^{-1}, N W
 #pragma unroll
@@ -972,7 +951,7 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
   //    (precision form; its buffers live in Y, dead until step 4)
   if constexpr (P64) {
     double* S = reinterpret_cast<double*>(Y);
-    double* pub = reinterpret_cast<double*>(buf);  // the elimination's cross is dead
+    double* pub = reinterpret_cast<double*>(buf);  // the pivot-row buffer is dead
     p64_cholqr_pass<T>(E, Q, r, k, i0, i1, false, S, S + 288, S + 304, Xg, pub);
     p64_cholqr_pass<T>(Q, Q, r, k, i0, i1, true, S, S + 288, S + 304, Xg, pub);
   } else {

@@ -265,10 +265,10 @@ __device__ __forceinline__ void elim_group_step(T (&x)[RS][4], int g, int r, T* 
 // Y = N W (r x 16, zero columns >= k) are in shared memory (the caller synchronises the
 // block).  A non-positive or non-finite pivot sets *flag and is replaced by 1.  Tile
 // slots beyond W take harmless garbage, and the dump masks the upper triangle.
-template <typename T, int NWE, int RS>
+template <typename T, int NWE, int RS, typename AfterLoad>
 __device__ void chol_eliminate(const T* __restrict__ G, long ldg, const T* __restrict__ W,
                                long ldw, int r, int k, T* buf, T* Nm, int ldn, T* dinv, T* Y,
-                               int* flag) {
+                               int* flag, AfterLoad after_load) {
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   T x[RS][4];
 #pragma unroll
@@ -288,6 +288,7 @@ __device__ void chol_eliminate(const T* __restrict__ G, long ldg, const T* __res
       x[t][u] = v;
     }
   }
+  after_load();  // issued behind the loads of the tile, which the first step waits for
   // group 0's rows from warp 0, then one step per group of four pivots
   if (w == 0) elim_publish_group<T, RS, 0>(x, 0, r, buf, flag);
   elim_sync(NWE * 32);
@@ -295,37 +296,37 @@ __device__ void chol_eliminate(const T* __restrict__ G, long ldg, const T* __res
     elim_group_step<T, NWE, RS, 0>(x, g, r, buf, flag);
     if (4 * (g + 1) < r) elim_group_step<T, NWE, RS, 1>(x, g + 1, r, buf, flag);
   }
-  // N (unit diagonal, zeros above), D^{-1}, N W
+  // N (unit diagonal, zeros above and in the padding columns r .. ldn - 1), D^{-1}, N W:
+  // a lane's four columns of N go out as one vector store
 #pragma unroll
   for (int t = 0; t < RS; ++t) {
     const int i = RS * w + t;
     if (i >= r) continue;
+    const int c0 = 4 * lane;
+    if (c0 < ldn) {
+      T o[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u;
+        o[u] = c < i ? x[t][u] : (c == i ? (T)1 : (T)0);
+      }
+      V4<T>::st(Nm + i * ldn + c0, o);
+      if (lane == (i >> 2)) {  // the diagonal: slot i & 3 = t & 3 (RS is a multiple of 4)
+        T d = x[t][t & 3];
+        if (!(d > (T)0) || !isfinite(d)) d = (T)1;  // flagged during elimination
+        dinv[i] = (T)1 / d;
+      }
+    }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int c = 4 * lane + u;
-      if (c < r) {
-        if (c == i) {
-          T d = x[t][u];
-          if (!(d > (T)0) || !isfinite(d)) d = (T)1;  // flagged during elimination
-          dinv[i] = (T)1 / d;
-          Nm[i * ldn + c] = (T)1;
-        } else {
-          Nm[i * ldn + c] = c < i ? x[t][u] : (T)0;
-        }
-      } else if (c - r < kCK) {
-        Y[i * kCK + (c - r)] = (c - r < k) ? x[t][u] : (T)0;
-      }
+      const int c = c0 + u;
+      if (c >= r && c - r < kCK) Y[i * kCK + (c - r)] = (c - r < k) ? x[t][u] : (T)0;
     }
   }
   // Y columns c with r + c >= 128 are outside the tile
   for (int e = tid; e < r * kCK; e += NWE * 32) {
     const int i = e >> 4, c = e & 15;
     if (r + c >= kCMax) Y[i * kCK + c] = (T)0;
-  }
-  // padding columns r .. ldn - 1 of N
-  for (int e = tid; e < r * 4; e += NWE * 32) {
-    const int i = e >> 2, c = r + (e & 3);
-    if (c < ldn) Nm[i * ldn + c] = (T)0;
   }
 }
 
@@ -920,8 +921,10 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
   const long ldh = h_smem ? sw : a.ldh;
 
   // 1. G = L D L^T with N = L^{-1} and N W, while the own columns of H stream into
-  //    shared memory by asynchronous copies issued first (waited for before step 5)
-  if (h_smem) {
+  //    shared memory by asynchronous copies issued once the tile's loads are out
+  //    (waited for before step 5)
+  auto copy_h = [&]() {
+    if (!h_smem) return;
     for (int e = tid; e < r * w; e += kCT) {
       const int i = e / w, jj = e - i * w;
       const T* src = a.H + (long)i * a.ldh + j0 + jj;
@@ -931,8 +934,9 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
       else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
     }
-  }
-  chol_eliminate<T, NWE, RS>(a.G, a.ldg, a.W, a.ldw, r, k, buf, Nm, L.ldn, dinv, Y, a.flag);
+  };
+  chol_eliminate<T, NWE, RS>(a.G, a.ldg, a.W, a.ldw, r, k, buf, Nm, L.ldn, dinv, Y, a.flag,
+                             copy_h);
   __syncthreads();
   // 2. C = N^T D^{-1} (N W)
   if constexpr (P64) {  // staged in E (free until step 4)

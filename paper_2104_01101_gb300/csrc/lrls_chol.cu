@@ -41,6 +41,8 @@ constexpr int kCK = 16;    // widest RSVD sketch (k) and Jacobi order
 constexpr int kCKs = 17;   // row stride of the k x k Jacobi buffers
 constexpr int kCX = 132;   // one pivot row: 128 columns + the pivot's reciprocal at kCX - 1
 constexpr int kCMax = 128; // r + k limit of the elimination tile
+constexpr int kQS = 20;    // row stride of Q and E (80 B: eight rows at one column
+                           // block fall in distinct shared-memory bank groups)
 constexpr unsigned kAll = 0xffffffffu;
 constexpr int kNC = 8;  // CTAs of the cluster that shares one subproblem (one per SM)
 // FP64 precision form: a scalar after the 16 x 17 Gram (S), and the size of the eigen
@@ -105,8 +107,8 @@ __host__ __device__ inline CholLayout chol_layout(int r, int s, int k, int R, si
   L.N = take(n_bytes > n64 ? n_bytes : n64);
   L.dinv = take(tsz * (size_t)((r + 3) & ~3));
   L.Y = take(y_bytes > y64 ? y_bytes : y64);
-  L.Q = take(tsz * (size_t)r * kCK);
-  L.E = take(tsz * (size_t)r * kCK);
+  L.Q = take(tsz * (size_t)r * kQS);
+  L.E = take(tsz * (size_t)r * kQS);
   L.buf = take(tsz * 8 * kCX > 66 * 8 ? tsz * 8 * kCX : 66 * 8);
   // the QR workspace, then (after Q is formed) the Jacobi buffers and C_(n)^T
   const size_t qr = ((usz * (size_t)r * 17 + 15) & ~(size_t)15) + usz * kCK;
@@ -335,11 +337,11 @@ __device__ void chol_eliminate(const T* __restrict__ G, long ldg, const T* __res
 // out(i, :) = post(i) * sum_a N~(i, a) * pre(a) * in(a, :) with N~ = N^T (UPPER: a >= i,
 // coefficient N(a, i)) or N (lower: a <= i, coefficient N(i, a)); N has a unit diagonal
 // and zeros above it, so the sums may run over whole 4-row blocks.  in/out are r x 16;
-// pre/post may be null (1).  A thread owns a 4 x 4 block of out and a quarter of the
+// pre/post may be null (1); ldi, ldo: their row strides.  A thread owns a 4 x 4 block of out and a quarter of the
 // sum (4-row blocks x 4 column blocks x 4 quarters = 512 threads for r <= 128).
 template <typename T, bool UPPER>
-__device__ void tri_product(const T* Nm, int ldn, int r, const T* pre, const T* in, const T* post,
-                            T* out) {
+__device__ void tri_product(const T* Nm, int ldn, int r, const T* pre, const T* in, int ldi,
+                            const T* post, T* out, int ldo) {
   const int tid = threadIdx.x, q = tid & 3, cb = (tid >> 2) & 3, ib = tid >> 4;
   const int i0 = 4 * ib;
   T acc[4][4];
@@ -359,7 +361,7 @@ __device__ void tri_product(const T* Nm, int ldn, int r, const T* pre, const T* 
 #pragma unroll
         for (int e = 0; e < 4; ++e) cf[e] = (i0 + e < r) ? Nm[(i0 + e) * ldn + a] : (T)0;
       }
-      V4<T>::ld(in + a * kCK + 4 * cb, v);
+      V4<T>::ld(in + a * ldi + 4 * cb, v);
       if (pre) {
         const T p = pre[a];
 #pragma unroll
@@ -387,7 +389,7 @@ __device__ void tri_product(const T* Nm, int ldn, int r, const T* pre, const T* 
         T o[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) o[b] = acc[e][b] * sc;
-        V4<T>::st(out + i * kCK + 4 * cb, o);
+        V4<T>::st(out + i * ldo + 4 * cb, o);
       }
     }
   }
@@ -398,7 +400,7 @@ __device__ void tri_product(const T* Nm, int ldn, int r, const T* pre, const T* 
 // Thin QR of A (r x k, row stride lda, type U) by Householder reflections, warp c owning
 // column c.  Warp j+1 applies reflector j to its column and then forms reflector j+1
 // without a barrier in between, so one block barrier per reflector.  On exit Qout
-// (r x 16, type T, zero columns >= k) holds the orthonormal factor.  A zero column gives
+// (r x 16, row stride kQS, type T, zero columns >= k) holds the orthonormal factor.  A zero column gives
 // tau = 0 (an identity reflector).
 template <typename U, typename T>
 __device__ void chol_householder(U* A, int lda, int r, int k, U* tau, T* Qout) {
@@ -464,10 +466,191 @@ __device__ void chol_householder(U* A, int lda, int r, int k, U* tau, T* Qout) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int i = lane + 32 * t;
-      if (i < r) Qout[i * kCK + c] = (T)q[t];
+      if (i < r) Qout[i * kQS + c] = (T)q[t];
     }
   }
   __syncthreads();
+}
+
+// ---------------------------------------------------------------- 3b. FP32 shifted CholeskyQR3
+
+// Q = qr(C) for FP32 data by shifted CholeskyQR3 (Fukaya, Kannan, Nakatsukasa, Yamamoto
+// and Yanagisawa, SIAM J. Sci. Comput. 42 (2020)): a Cholesky-QR pass on C^T C + s I with
+// s = 11 (r k + k (k + 1)) u ||C||_F^2 (u = 2^-24) leaves Q1 with a condition number the
+// unshifted passes can take, and two unshifted passes follow.  Each pass is one CTA on
+// its own data (no cluster exchange): the Gram by 10 warps (one 4 x 4 block of the lower
+// triangle each, rows over the lanes, then a butterfly reduce-scatter of the 16 sums),
+// the LDL^T in one warp's registers (no block barrier), the product by all threads.
+// Alg. 5 uses Q only as a basis of range(C), so the sign of each column (positive here,
+// the reflection's there) does not matter.
+
+__device__ __forceinline__ bool cq_above(float x, float thr) {
+  return __float_as_int(x) > __float_as_int(thr);  // thr >= +0: x > thr, x not a NaN
+}
+
+// S = C^T C (16 x 17, both triangles; columns >= k of C read as zero).  Warp w < 10 owns
+// block (bi, bc), bi >= bc; lane l sums rows l, l + 32, l + 64, l + 96.
+__device__ __forceinline__ void cq_gram(const float* C, int r, int k, float* S) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (w >= 10) return;
+  const int bi = w < 1 ? 0 : w < 3 ? 1 : w < 6 ? 2 : 3;  // w = bi (bi + 1) / 2 + bc
+  const int bc = w - bi * (bi + 1) / 2;
+  float acc[16];
+#pragma unroll
+  for (int u = 0; u < 16; ++u) acc[u] = 0.f;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int i = lane + 32 * t;
+    if (i < r) {
+      float a[4], b[4];
+      V4<float>::ld(C + i * kQS + 4 * bi, a);
+      V4<float>::ld(C + i * kQS + 4 * bc, b);
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        a[x] = 4 * bi + x < k ? a[x] : 0.f;
+        b[x] = 4 * bc + x < k ? b[x] : 0.f;
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[4 * x + y] = fmaf(a[x], b[y], acc[4 * x + y]);
+    }
+  }
+  // reduce-scatter: afterwards lanes 2v and 2v + 1 hold the warp's total of sum v
+#pragma unroll
+  for (int h = 8, o = 16; h >= 1; h >>= 1, o >>= 1) {
+    const bool up = lane & o;
+#pragma unroll
+    for (int u = 0; u < h; ++u) {
+      const float send = up ? acc[u] : acc[u + h];
+      const float keep = up ? acc[u + h] : acc[u];
+      acc[u] = keep + __shfl_xor_sync(kAll, send, o);
+    }
+  }
+  acc[0] += __shfl_xor_sync(kAll, acc[0], 1);
+  if ((lane & 1) == 0) {
+    const int x = lane >> 3, y = (lane >> 1) & 3;
+    S[(4 * bi + x) * kCKs + 4 * bc + y] = acc[0];
+    S[(4 * bc + y) * kCKs + 4 * bi + x] = acc[0];
+  }
+}
+
+// The factor of one pass in warp 0: S + shift I = N^{-1} D N^{-T}, written as Nt = N^T
+// (16 x 16: Nt[a][c] = N(c, a), unit diagonal, zeros below) and dsq = D^{-1/2} (a pivot
+// not above thr drops its direction: dsq = 0).  Lane l holds row l / 2, columns
+// 8 (l % 2) .. + 7; pivot j's row, the lane's own entry in column j and the pivot come
+// by shuffles.  The pivot loop is unrolled by 8 (the slot index a constant, one copy of
+// the code for both halves) and has no branch, so a step's trailing updates overlap the
+// next step's shuffles.  mode 0: shifted first pass; 1: full
+// LDL^T; 2: first order when S is within 2^-12 of I (N = I - strictly_lower(S - I),
+// D^{-1/2} = I - diag(S - I) / 2, error second order), else full.
+__device__ __forceinline__ void cq_factor(const float* S, int r, int k, int mode, float* Nt,
+                                          float* dsq) {
+  const int lane = threadIdx.x & 31, i = lane >> 1, h = lane & 1;
+  float v[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int c = 8 * h + u;
+    v[u] = (i < k && c < k) ? S[i * kCKs + c] : 0.f;
+  }
+  float tr = lane < k ? S[lane * kCKs + lane] : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) tr += __shfl_xor_sync(kAll, tr, o);
+  bool first_order = false;
+  if (mode == 2) {
+    bool off = false;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int c = 8 * h + u;
+      if (i < k && c < k) off |= !(fabsf(v[u] - (c == i ? 1.f : 0.f)) <= 0x1.0p-12f);
+    }
+    first_order = !__any_sync(kAll, off);
+  }
+  float dq = 0.f;
+  if (first_order) {
+    if (lane < k) dq = 1.5f - 0.5f * S[lane * kCKs + lane];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = 8 * h + u < i ? -v[u] : 0.f;
+  } else {
+    float thr = k > 0 ? 0x1.0p-40f * tr / (float)k : 0.f;
+    if (mode == 0) {  // the shift, on the diagonal
+      thr = 0.f;
+      const float sh = 11.f * (float)(r * k + k * (k + 1)) * 0x1.0p-24f * tr;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (8 * h + u == i && i < k) v[u] += sh;
+    }
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {  // pivots 8 q .. 8 q + 7: column 8 q + t is slot t of half q
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int j = 8 * q + t;
+        const float d = __shfl_sync(kAll, v[t], 17 * q + 2 * t);
+        const float sij = __shfl_sync(kAll, v[t], 2 * i + q);
+        float rowj[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) rowj[u] = __shfl_sync(kAll, v[u], 16 * q + 2 * t + h);
+        const float dinv = cq_above(d, thr) ? elim_rcp(d) : 0.f;
+        dq = lane == j ? dinv : dq;
+        const float m = i > j ? sij * dinv : 0.f;  // rows up to j: unchanged
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          v[u] = (u == t && h == q && i > j) ? -m : fmaf(-m, rowj[u], v[u]);
+      }
+    }
+    dq = sqrtf(dq);
+  }
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int c = 8 * h + u;
+    Nt[c * kCK + i] = c < i ? v[u] : (c == i ? 1.f : 0.f);
+  }
+  if (lane < kCK) dsq[lane] = lane < k ? dq : 0.f;
+}
+
+// One pass: Qout = C N^T D^{-1/2} (r x 16, zero columns >= k; both with row stride kQS);
+// Qout must not be C.  ws:
+// 16 x 17 + 16 x 16 + 16 floats, 16-byte aligned.
+__device__ __forceinline__ void cq_pass(const float* C, float* Qout, int r, int k, int mode,
+                                        float* ws) {
+  float* S = ws;
+  float* Nt = ws + kCK * kCKs;
+  float* dsq = Nt + kCK * kCK;
+  cq_gram(C, r, k, S);
+  __syncthreads();
+  if (threadIdx.x < 32) cq_factor(S, r, k, mode, Nt, dsq);
+  __syncthreads();
+  const int i = threadIdx.x >> 2, cg = threadIdx.x & 3;
+  if (i < r) {
+    float crow[4][4], acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      V4<float>::ld(C + i * kQS + 4 * b, crow[b]);
+#pragma unroll
+      for (int x = 0; x < 4; ++x) crow[b][x] = 4 * b + x < k ? crow[b][x] : 0.f;
+    }
+#pragma unroll
+    for (int a = 0; a < kCK; ++a) {
+      float nv[4];
+      V4<float>::ld(Nt + a * kCK + 4 * cg, nv);  // N(4 cg .. 4 cg + 3, a)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[e] = fmaf(crow[a >> 2][a & 3], nv[e], acc[e]);
+    }
+    float dv[4], o[4];
+    V4<float>::ld(dsq + 4 * cg, dv);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) o[e] = 4 * cg + e < k ? acc[e] * dv[e] : 0.f;
+    V4<float>::st(Qout + i * kQS + 4 * cg, o);
+  }
+  __syncthreads();
+}
+
+// Shifted CholeskyQR3: C (r x 16, FP32, row stride kQS) -> Q; B is scratch of the same shape
+// (C may be B).
+// The passes run as one loop, so their code is fetched once.
+__device__ void cq3_f32(const float* C, float* B, float* Q, int r, int k, float* ws) {
+#pragma unroll 1
+  for (int p = 0; p < 3; ++p) cq_pass(p == 0 ? C : (p == 1 ? Q : B), p == 1 ? B : Q, r, k, p, ws);
 }
 
 // ---------------------------------------------------------------- 5. one-warp Jacobi
@@ -687,7 +870,7 @@ __device__ double p64_ldl(double& v, int k, double thr, double* pub) {
 }
 
 // One FP64 Cholesky-QR pass over the cluster: Qout = C N^T D^{-1/2} with
-// C^T C = N^{-1} D N^{-T}.  C (r x 16, type T, columns >= k ignored) is identical in every
+// C^T C = N^{-1} D N^{-T}.  C (r x 16, row stride kQS, type T, columns >= k ignored) is identical in every
 // CTA; this CTA owns rows [i0, i1).  A pivot not above 2^-40 ||C||_F^2 / k drops its
 // direction (a zero column of Qout): below that level the Gram's own rounding decides
 // the pivot, and C, computed from FP32 data, holds nothing there.  In the second pass
@@ -705,7 +888,7 @@ __device__ void p64_cholqr_pass(const T* C, T* Qout, int r, int k, int i0, int i
   const int nr = i1 - i0;
   for (int e = tid; e < nr * kCK; e += kCT) {
     const int ii = e >> 4, c = e & 15;
-    Cd[e] = c < k ? (double)C[(i0 + ii) * kCK + c] : 0.0;
+    Cd[e] = c < k ? (double)C[(i0 + ii) * kQS + c] : 0.0;
   }
   __syncthreads();
   // Gram of the own rows (4 threads per entry of the lower triangle), to the peers
@@ -779,7 +962,7 @@ __device__ void p64_cholqr_pass(const T* C, T* Qout, int r, int k, int i0, int i
       for (int a = 0; a <= cc; ++a) acc = fma(Cd[ii * kCK + a], S[cc * 17 + a], acc);
     const T qv = cc < k ? (T)(acc * dsq[cc]) : (T)0;
 #pragma unroll
-    for (int q = 0; q < kNC; ++q) cl_peer(Qout, q)[(i0 + ii) * kCK + cc] = qv;
+    for (int q = 0; q < kNC; ++q) cl_peer(Qout, q)[(i0 + ii) * kQS + cc] = qv;
   }
   cl_sync();
 }
@@ -939,32 +1122,35 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
                              copy_h);
   __syncthreads();
   // 2. C = N^T D^{-1} (N W)
-  if constexpr (P64) {  // staged in E (free until step 4)
-    tri_product<T, true>(Nm, L.ldn, r, dinv, Y, nullptr, E);
+  if constexpr (P64 || sizeof(T) == 4) {  // staged in E (free until step 4)
+    tri_product<T, true>(Nm, L.ldn, r, dinv, Y, kCK, nullptr, E, kQS);
     __syncthreads();
   } else {  // staged in Q, then widened into the Householder buffer
-    tri_product<T, true>(Nm, L.ldn, r, dinv, Y, nullptr, Q);
+    tri_product<T, true>(Nm, L.ldn, r, dinv, Y, kCK, nullptr, Q, kQS);
     __syncthreads();
     for (int e = tid; e < r * kCK; e += kCT) {
       const int i = e >> 4, c = e & 15;
-      if (c < k) Cq[i * 17 + c] = (U)Q[e];
+      if (c < k) Cq[i * 17 + c] = (U)Q[i * kQS + c];
     }
     __syncthreads();
   }
-  // 3. Q = qr(C): Householder in the data type, or FP64 CholeskyQR2 over the cluster
-  //    (precision form; its buffers live in Y, dead until step 4)
+  // 3. Q = qr(C): FP64 CholeskyQR2 over the cluster (precision form), shifted
+  //    CholeskyQR3 in FP32, or Householder in FP64 (their buffers live in Y, dead until
+  //    step 4)
   if constexpr (P64) {
     double* S = reinterpret_cast<double*>(Y);
     double* pub = reinterpret_cast<double*>(buf);  // the pivot-row buffer is dead
     p64_cholqr_pass<T>(E, Q, r, k, i0, i1, false, S, S + 288, S + 304, Xg, pub);
     p64_cholqr_pass<T>(Q, Q, r, k, i0, i1, true, S, S + 288, S + 304, Xg, pub);
+  } else if constexpr (sizeof(T) == 4) {
+    cq3_f32(E, E, Q, r, k, reinterpret_cast<float*>(Y));
   } else {
     chol_householder<U, T>(Cq, 17, r, k, tau, Q);
   }
   // 4. E = N^T D^{-1} N Q
-  tri_product<T, false>(Nm, L.ldn, r, nullptr, Q, dinv, Y);
+  tri_product<T, false>(Nm, L.ldn, r, nullptr, Q, kQS, dinv, Y, kCK);
   __syncthreads();
-  tri_product<T, true>(Nm, L.ldn, r, nullptr, Y, nullptr, E);
+  tri_product<T, true>(Nm, L.ldn, r, nullptr, Y, kCK, nullptr, E, kQS);
   __syncthreads();
   // 5. D = E^T H over the own columns (k x w): a thread per (column, group of 4 rows of
   //    D) runs down the r rows of H, four sums in registers (a compact loop: this phase
@@ -986,7 +1172,7 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
       for (int i = 0; i < r; ++i) {
         const T hv = hp[(long)i * ldh];
         T ev[4];
-        V4<T>::ld(ep + i * kCK, ev);
+        V4<T>::ld(ep + i * kQS, ev);
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc[e] = fma(ev[e], hv, acc[e]);
       }
@@ -1083,7 +1269,7 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
       const T l = Kf[order[c] * kCKs + order[c]];
       const T sig = l > (T)0 ? sqrt(l) : (T)0;
       T acc = 0;
-      for (int b = 0; b < k; ++b) acc = fma(Q[i * kCK + b], V[b * kCKs + order[c]], acc);
+      for (int b = 0; b < k; ++b) acc = fma(Q[i * kQS + b], V[b * kCKs + order[c]], acc);
       CnTs[i * R + c] = acc * sig;
     }
   }

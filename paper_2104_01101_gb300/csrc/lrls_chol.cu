@@ -18,13 +18,14 @@
 //      Meanwhile asynchronous copies bring this CTA's columns of H into shared memory.
 //   2. B = G^{-1} = N^T D^{-1} N is never formed: C = B W = N^T (D^{-1} (N W)) and
 //      E = B Q = N^T (D^{-1} (N Q)) are triangular products with k <= 16 columns.
-//   3. Q = qr(C): Householder, warp c owning column c (one barrier per reflector), then
-//      warp c forms column c of Q; in the precision form FP64 CholeskyQR2 instead.
+//   3. Q = qr(C): shifted CholeskyQR3 in FP32 for FP32 data (one CTA: Gram by shuffles,
+//      LDL^T in one warp's registers), Householder for FP64 data, FP64 CholeskyQR2 over
+//      the cluster in the precision form.
 //   4. D = E^T H (k x s; E^T H = Q^T B Z^T Y of Alg. 5) over each CTA's columns, K = D D^T
 //      summed over the cluster.
-//   5. K = U Lambda U^T by cyclic Jacobi in ONE warp (round-robin pairs; rotations of a
-//      round applied as 2 x 2 block updates into a second buffer; no block barrier); in
-//      the precision form one FP64 refinement of the eigenpairs follows.
+//   5. K = U Lambda U^T by cyclic Jacobi on four warps (round-robin pairs; rotations of a
+//      round applied as 2 x 2 block updates into a second buffer; one 128-thread barrier
+//      per round); in the precision form one FP64 refinement of the eigenpairs follows.
 //   6. C_(n)^T = Q U_R Sigma_R, A^(n) = D^T U_R Sigma_R^{-1}, canonical column signs, core.
 #include <cooperative_groups.h>
 
@@ -653,7 +654,7 @@ __device__ void cq3_f32(const float* C, float* B, float* Q, int r, int k, float*
   for (int p = 0; p < 3; ++p) cq_pass(p == 0 ? C : (p == 1 ? Q : B), p == 1 ? B : Q, r, k, p, ws);
 }
 
-// ---------------------------------------------------------------- 5. one-warp Jacobi
+// ---------------------------------------------------------------- 5. Jacobi on four warps
 
 template <typename T>
 __host__ __device__ constexpr T cj_tol() {
@@ -690,9 +691,7 @@ __device__ __forceinline__ void cj_pair(int t, int a, int& p, int& q) {
 // t^2 + 2 theta t - 1 = 0 of smaller magnitude, theta = x / y).  Both reciprocal square
 // roots are refined to working precision, so c^2 + s^2 = 1 to rounding.
 template <typename T>
-__device__ __forceinline__ void cj_rotation(T app, T aqq, T apq, T tol2, T floor_abs, T& c,
-                                            T& s, bool& rot) {
-  rot = apq * apq > tol2 * fabs(app * aqq) && fabs(apq) > floor_abs;
+__device__ __forceinline__ void cj_rotation(T app, T aqq, T apq, bool rot, T& c, T& s) {
   const T x = aqq - app, y = 2 * apq;
   const T h = fma(x, x, y * y);
   const T ih = cj_rsqrt(rot ? h : (T)1);
@@ -702,20 +701,44 @@ __device__ __forceinline__ void cj_rotation(T app, T aqq, T apq, T tol2, T floor
   s = rot ? (x >= (T)0 ? y : -y) * ((T)0.5 * ih * rc) : (T)0;
 }
 
-// Symmetric eigen-decomposition of K (16 x 16, row stride kCKs, zero-padded beyond the
-// order) by cyclic Jacobi in the calling warp: K <- V^T K V, V (start: identity) holds
-// the eigenvectors.  A pair rotates when |a_pq| exceeds both tol sqrt(|a_pp a_qq|) and
-// floor max_i |a_ii|; a sweep whose largest |sin| is at most sqrt(tol) ends the loop
-// (quadratic convergence: the next sweep's angles would be ~tol).  Lane L works on pair
-// a = L & 7: every lane forms a's rotation itself, updates the 2 x 2 blocks (a, bj) for
-// the two column pairs bj = 2 (L >> 3) + {0, 1} (their rotations by shuffles from lanes
-// bj) and rows 4 (L >> 3) .. + 3 of V on a's columns.  Returns the buffer holding the
-// diagonalised matrix.
+// The same rotation for a small angle, |a_pq| <= g |x| (g = 2^-7 in FP32, 2^-14 in FP64):
+// t = tan(phi) = (a_pq / x) (1 - (a_pq / x)^2) (relative error O((a_pq / x)^4)),
+// c = 1 - t^2 / 2 and s = t c, for which c^2 + s^2 - 1 = -3 t^4 / 4 + O(t^6), below
+// 3 g^4 / 4 (2^-30 in FP32, 2^-58 in FP64): one reciprocal instead of two refined
+// reciprocal square roots.
 template <typename T>
-__device__ T* cj_jacobi_warp(T* K, T* K2, T* V, int max_sweeps) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int e = lane; e < kCK * kCK; e += 32) {
+__host__ __device__ constexpr T cj_small() {
+  return sizeof(T) == 4 ? (T)128 : (T)16384;  // 1 / g
+}
+template <typename T>
+__device__ __forceinline__ void cj_rotation_small(T app, T aqq, T apq, bool rot, T& c, T& s) {
+  const T u = apq * elim_rcp(rot ? aqq - app : (T)1);
+  const T t = u * fma(-u, u, (T)1);
+  c = rot ? fma((T)-0.5 * t, t, (T)1) : (T)1;
+  s = rot ? t * c : (T)0;
+}
+
+
+// Symmetric eigen-decomposition of K (16 x 16, row stride kCKs, zero-padded beyond the
+// order) by cyclic Jacobi on warps 0 .. kJW - 1 (the caller's other threads skip it):
+// K <- V^T K V, V (start: identity) holds the eigenvectors.  A pair rotates when |a_pq|
+// exceeds both tol sqrt(|a_pp a_qq|) and floor max_i |a_ii|; a sweep whose largest |sin|
+// is at most sqrt(tol) ends the loop (quadratic convergence: the next sweep's angles
+// would be ~tol).  Round t rotates the 8 disjoint pairs of the round-robin schedule.  In
+// every warp lane L forms the rotation of pair a = L & 7 (all warps the same values);
+// warps 0 and 1 update the 2 x 2 block (a, b) of A into B for the column pair
+// b = 2 (L >> 3) + w (its rotation by shuffle from lane b), warps 2 and 3 rotate
+// columns p, q of V in rows 4 (L >> 3) + 2 (w - 2) and the next.  Spreading the round
+// over four warps cuts each warp's instructions per round (the round is a latency chain
+// of loads, two refined reciprocal square roots, a shuffle and stores); one 128-thread
+// barrier per round.  Returns the buffer holding the diagonalised matrix.
+constexpr int kJW = 4;
+__device__ __forceinline__ void cj_sync() { asm volatile("bar.sync 3, 128;" ::: "memory"); }
+
+template <typename T>
+__device__ T* cj_jacobi(T* K, T* K2, T* V, int max_sweeps) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int e = tid; e < kCK * kCK; e += 32 * kJW) {
     const int i = e >> 4, j = e & 15;
     V[i * kCKs + j] = i == j ? (T)1 : (T)0;
   }
@@ -725,62 +748,70 @@ __device__ T* cj_jacobi_warp(T* K, T* K2, T* V, int max_sweeps) {
   for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(kAll, dmax, o));
   const T tol = cj_tol<T>(), tol2 = tol * tol, floor_abs = cj_floor<T>() * dmax;
   const float stop_s = sqrtf((float)tol);
-  __syncwarp();
+  cj_sync();
   T* A = K;
   T* B = K2;
   const int a = lane & 7, g = lane >> 3;
+  const bool blk = w < 2;
+  const int cb = 2 * g + (w & 1);   // the block's column pair (warps 0, 1)
+  const int vr = 4 * g + 2 * (w & 1);  // the first of the two V rows (warps 2, 3)
+  int p, q, pb, qb;  // this round's pairs; the next round's are formed during the round
+  cj_pair(0, a, p, q);
+  cj_pair(0, cb, pb, qb);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     bool any = false;
     float smax = 0.f;
     for (int t = 0; t < 15; ++t) {
-      int p, q;
-      cj_pair(t, a, p, q);
-      int pb[2], qb[2];
-      cj_pair(t, 2 * g, pb[0], qb[0]);
-      cj_pair(t, 2 * g + 1, pb[1], qb[1]);
-      // the blocks (a, bj) of the current matrix (independent of the rotations)
-      T blk[2][4];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        blk[h][0] = A[p * kCKs + pb[h]];
-        blk[h][1] = A[p * kCKs + qb[h]];
-        blk[h][2] = A[q * kCKs + pb[h]];
-        blk[h][3] = A[q * kCKs + qb[h]];
+      const T app = A[p * kCKs + p], aqq = A[q * kCKs + q], apq = A[p * kCKs + q];
+      T x0, x1, x2, x3;
+      if (blk) {
+        x0 = A[p * kCKs + pb];
+        x1 = A[p * kCKs + qb];
+        x2 = A[q * kCKs + pb];
+        x3 = A[q * kCKs + qb];
+      } else {
+        x0 = V[vr * kCKs + p];
+        x1 = V[vr * kCKs + q];
+        x2 = V[(vr + 1) * kCKs + p];
+        x3 = V[(vr + 1) * kCKs + q];
       }
-      T vp[4], vq[4];
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        vp[e] = V[(4 * g + e) * kCKs + p];
-        vq[e] = V[(4 * g + e) * kCKs + q];
-      }
+      int np, nq, npb, nqb;
+      cj_pair(t == 14 ? 0 : t + 1, a, np, nq);
+      cj_pair(t == 14 ? 0 : t + 1, cb, npb, nqb);
       T c, s;
-      bool rot;
-      cj_rotation<T>(A[p * kCKs + p], A[q * kCKs + q], A[p * kCKs + q], tol2, floor_abs, c, s,
-                     rot);
+      const bool rot = apq * apq > tol2 * fabs(app * aqq) && fabs(apq) > floor_abs;
+      // every rotating pair of the round at a small angle (the same in all warps): the
+      // one-reciprocal form
+      if (__all_sync(kAll, !rot || fabs(apq) * cj_small<T>() <= fabs(aqq - app)))
+        cj_rotation_small<T>(app, aqq, apq, rot, c, s);
+      else
+        cj_rotation<T>(app, aqq, apq, rot, c, s);
       if (rot && lane < 8) {
         any = true;
         smax = fmaxf(smax, (float)fabs(s));
       }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const T cj = __shfl_sync(kAll, c, 2 * g + h), sj = __shfl_sync(kAll, s, 2 * g + h);
-        // (J_a^T B J_bj)
-        const T t00 = c * blk[h][0] - s * blk[h][2], t01 = c * blk[h][1] - s * blk[h][3];
-        const T t10 = s * blk[h][0] + c * blk[h][2], t11 = s * blk[h][1] + c * blk[h][3];
-        B[p * kCKs + pb[h]] = cj * t00 - sj * t01;
-        B[p * kCKs + qb[h]] = sj * t00 + cj * t01;
-        B[q * kCKs + pb[h]] = cj * t10 - sj * t11;
-        B[q * kCKs + qb[h]] = sj * t10 + cj * t11;
+      const T cj = __shfl_sync(kAll, c, cb), sj = __shfl_sync(kAll, s, cb);
+      if (blk) {  // J_a^T X J_b
+        const T t00 = c * x0 - s * x2, t01 = c * x1 - s * x3;
+        const T t10 = s * x0 + c * x2, t11 = s * x1 + c * x3;
+        B[p * kCKs + pb] = cj * t00 - sj * t01;
+        B[p * kCKs + qb] = sj * t00 + cj * t01;
+        B[q * kCKs + pb] = cj * t10 - sj * t11;
+        B[q * kCKs + qb] = sj * t10 + cj * t11;
+      } else {  // V J_a
+        V[vr * kCKs + p] = c * x0 - s * x1;
+        V[vr * kCKs + q] = s * x0 + c * x1;
+        V[(vr + 1) * kCKs + p] = c * x2 - s * x3;
+        V[(vr + 1) * kCKs + q] = s * x2 + c * x3;
       }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        V[(4 * g + e) * kCKs + p] = c * vp[e] - s * vq[e];
-        V[(4 * g + e) * kCKs + q] = s * vp[e] + c * vq[e];
-      }
-      __syncwarp();
+      cj_sync();
       T* tmp = A;
       A = B;
       B = tmp;
+      p = np;
+      q = nq;
+      pb = npb;
+      qb = nqb;
     }
     any = __any_sync(kAll, any);
 #pragma unroll
@@ -813,15 +844,15 @@ __device__ __forceinline__ void cl_sync() { cg::this_cluster().sync(); }
 // instruction count low: operands converted once, FP64 work split over the cluster and,
 // within a CTA, over warps on all four sub-partitions.
 
-// FP64 reciprocal: the approximate FP64 reciprocal (a seed good to about FP32 precision)
-// refined by two Newton steps, y <- y + y (1 - x y) (each doubles the correct digits).
+// FP64 reciprocal: the approximate FP64 reciprocal y (relative error e = 1 - x y below
+// 2^-19; 2^-19.95 measured over 2^20 inputs on GB300) corrected by the series
+// 1 / x = y / (1 - e) = y (1 + e + e^2 + ...) to second order, y + y (e + e^2): the
+// truncation error is e^3 < 2^-57, one FP64 operation fewer than two Newton steps.
 __device__ __forceinline__ double p64_rcp(double x) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
+  const double e = fma(-x, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 
 // x > thr for thr >= +0, compared on the bit patterns (integer unit): a negative x is
@@ -891,10 +922,11 @@ __device__ void p64_cholqr_pass(const T* C, T* Qout, int r, int k, int i0, int i
     Cd[e] = c < k ? (double)C[(i0 + ii) * kQS + c] : 0.0;
   }
   __syncthreads();
-  // Gram of the own rows (4 threads per entry of the lower triangle), to the peers
+  // Gram of the own rows (2 threads per entry of the lower triangle: FP64 instructions
+  // occupy the pipe for ~64 cycles per warp, so fewer warps with longer sums), to the peers
   const int npair = k * (k + 1) / 2;
-  for (int e = tid; e < 4 * ((npair + 127) / 128) * 128; e += kCT) {
-    const int pr = e >> 2, part = e & 3;
+  for (int e = tid; e < 2 * ((npair + 255) / 256) * 256; e += kCT) {
+    const int pr = e >> 1, part = e & 1;
     double acc = 0;
     int a = 0, b = 0;
     if (pr < npair) {  // pair index -> (a, b), a <= b
@@ -904,10 +936,9 @@ __device__ void p64_cholqr_pass(const T* C, T* Qout, int r, int k, int i0, int i
         ++a;
       }
       b = a + rem;
-      for (int ii = part; ii < nr; ii += 4) acc = fma(Cd[ii * kCK + a], Cd[ii * kCK + b], acc);
+      for (int ii = part; ii < nr; ii += 2) acc = fma(Cd[ii * kCK + a], Cd[ii * kCK + b], acc);
     }
     acc += __shfl_xor_sync(kAll, acc, 1);
-    acc += __shfl_xor_sync(kAll, acc, 2);
     if (pr < npair && part == 0) {
 #pragma unroll
       for (int q = 0; q < kNC; ++q) cl_peer(Xg, q)[cr * 272 + b * 17 + a] = acc;
@@ -1185,6 +1216,10 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
     }
   }
   __syncthreads();
+  // FP64 workspace of the precision form's eigen refinement and K's FP64 copy, in N (dead
+  // after step 4)
+  double* w64 = reinterpret_cast<double*>(Nm);
+  double* Kd = w64 + kRefineWs;
   // K = D D^T: the own columns' part (4 threads per entry of the upper triangle), summed
   // over the cluster in rank order
   {
@@ -1217,19 +1252,15 @@ __device__ __forceinline__ void lrls_chol_body(const FusedArgs<T>& a, bool h_sme
       T sum = 0;
       for (int q = 0; q < kNC; ++q) sum += Kp[q * 272 + lo * kCKs + hi];
       K0[i * kCKs + j] = sum;
+      if constexpr (P64) Kd[i * 17 + j] = (double)sum;
     }
     __syncthreads();
   }
-  // 6. eigen-decomposition of K in warp 0 (FP32 Jacobi; FP64 refinement in the precision
-  //    form, its workspace in N, dead after step 4)
-  double* w64 = reinterpret_cast<double*>(Nm);
-  double* Kd = w64 + kRefineWs;
-  if constexpr (P64) {
-    if (tid < 256) Kd[(tid >> 4) * 17 + (tid & 15)] = (double)K0[(tid >> 4) * kCKs + (tid & 15)];
-  }
-  if (warp == 0) {
-    T* Kf = cj_jacobi_warp<T>(K0, K1, V, 20);
-    if (lane == 0) Kfin = Kf;
+  // 6. eigen-decomposition of K: FP32 Jacobi on warps 0 .. 3, then the FP64 refinement in
+  //    the precision form
+  if (warp < kJW) {
+    T* Kf = cj_jacobi<T>(K0, K1, V, 20);
+    if (tid == 0) Kfin = Kf;
   }
   __syncthreads();
   T* Kf = Kfin;
@@ -1377,7 +1408,7 @@ __global__ void __cluster_dims__(kNC, 1, 1) __launch_bounds__(kCT, 1) k_lrls_cho
 
 // ---------------------------------------------------------------- small eigensolver
 
-// K (n x n, n <= 16, symmetrised) = U Lambda U^T by the one-warp Jacobi above and, with
+// K (n x n, n <= 16, symmetrised) = U Lambda U^T by the four-warp Jacobi above and, with
 // P64, one FP64 refinement over the cluster; eigenvalues descending (ties in index
 // order), sigma = sqrt(lambda).  Outputs as the general eigensolver's: Fm = U_R
 // Sigma_R^{-1} and Uout = U_R (n x R), CnT = Q U_R Sigma_R (r x R; Q null: U_R Sigma_R,
@@ -1392,7 +1423,7 @@ __global__ void __cluster_dims__(kNC, 1, 1) __launch_bounds__(kCT, 1)
   __shared__ __align__(16) double ws[P64 ? kRefineWs + kCK * 17 : 1];
   __shared__ int order[kCK];
   __shared__ T* Kfin;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5;
   if (tid < kCK * kCK) {
     const int i = tid >> 4, j = tid & 15;
     const T v = (i < n && j < n) ? (T)0.5 * (K[i * n + j] + K[j * n + i]) : (T)0;
@@ -1400,9 +1431,9 @@ __global__ void __cluster_dims__(kNC, 1, 1) __launch_bounds__(kCT, 1)
     if constexpr (P64) ws[kRefineWs + i * 17 + j] = (double)v;
   }
   __syncthreads();
-  if (warp == 0) {
-    T* Kf = cj_jacobi_warp<T>(K0, K1, V, 20);
-    if (lane == 0) Kfin = Kf;
+  if (warp < kJW) {
+    T* Kf = cj_jacobi<T>(K0, K1, V, 20);
+    if (tid == 0) Kfin = Kf;
   }
   __syncthreads();
   T* Kf = Kfin;

@@ -103,9 +103,12 @@ typedef struct {
                                  form); the sketches and the solve stay FP32 */
   int32_t init_given;         /* 1: factors_inout already hold the initial A^(2..N) (no RRF) */
   int32_t track_fit;          /* 1: write the relative residual after every sweep */
-  int32_t solve_fp64;         /* FP32 data: 1 runs the QR of Alg. 5 and the last Jacobi
-                                 sweeps of the SVD in FP64 (slower on GB300); FP64 data
-                                 always solves in FP64 */
+  int32_t solve_fp64;         /* FP32 data: 1 runs the QR of Alg. 5 and the SVD's
+                                 eigenpairs in FP64 (slower on GB300): in the cluster solve
+                                 (r + k <= 128, k <= 16) FP64 CholeskyQR2 and one FP64
+                                 refinement of the FP32 Jacobi's eigenpairs, in the other
+                                 solves an FP64 Householder QR and an FP64 polish of the
+                                 eigenpairs; FP64 data always solves in FP64 */
   int32_t use_graph;          /* 1: capture the whole decomposition as a CUDA graph on first
                                  use (cached per argument set and device, up to 8 entries) and
                                  replay it on later calls with identical arguments.  The

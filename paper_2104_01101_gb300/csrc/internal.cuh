@@ -289,8 +289,8 @@ ts_status launch_lrls_fused(int r, int s, int k, int R, int solve, bool fp64, co
 bool lrls_chol_supported(int r, int s, int k, int R, int solve, size_t tsize, bool fp64);
 template <typename T>
 ts_status launch_lrls_chol(const FusedArgs<T>& a, bool fp64, cudaStream_t st);
-// lrls_chol.cu: the symmetric eigensolver for n <= 16 (one-warp Jacobi; fp64 with FP32
-// data: one FP64 refinement), with the outputs of launch_eig_small.
+// lrls_chol.cu: the symmetric eigensolver for n <= 16 (Jacobi on four warps; fp64 with
+// FP32 data: one FP64 refinement), with the outputs of launch_eig_small.
 template <typename T>
 ts_status launch_eig16(int n, int R, const T* K, const T* Q, int r, T* CnT, T* Fm, T* Uout,
                        bool fp64, int* flag, cudaStream_t st);

@@ -824,7 +824,7 @@ __device__ T* cj_jacobi(T* K, T* K2, T* V, int max_sweeps) {
 // ---------------------------------------------------------------- cluster exchange
 
 // The CTAs of the cluster share one subproblem: every CTA repeats the short serial chains
-// (elimination, triangular products, Householder QR, Jacobi) on identical data, so they
+// (elimination, triangular products, FP32 QR, Jacobi) on identical data, so they
 // hold identical results, and each owns a slice of the work that is wide rather than
 // deep: columns [j0, j1) of H, D and A, rows [i0, i1) of C for the FP64 products and two
 // columns of the 16 x 16 eigen refinement.  Partial results are pushed: a CTA stores its

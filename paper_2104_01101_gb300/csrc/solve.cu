@@ -733,7 +733,7 @@ ts_status launch_eig_small(int n, int R, const T* K, const T* Q, int r, T* CnT, 
                            bool polish64, int* flag, cudaStream_t st) {
   if (n > kMaxEig || n < 1)
     return fail(TS_ERR_SHAPE, "eigensolver: n=%d outside [1,%d]", n, kMaxEig);
-  if (n <= 16 && R <= n)  // one-warp Jacobi on an 8-CTA cluster (lrls_chol.cu)
+  if (n <= 16 && R <= n)  // four-warp Jacobi on an 8-CTA cluster (lrls_chol.cu)
     return launch_eig16<T>(n, R, K, Q, r, CnT, Fm, Uout, polish64, flag, st);
   JacobiShape js;
   js.n = n;

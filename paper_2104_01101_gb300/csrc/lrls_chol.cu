@@ -542,9 +542,9 @@ __device__ __forceinline__ void cq_gram(const float* C, int r, int k, float* S) 
 // 8 (l % 2) .. + 7; pivot j's row, the lane's own entry in column j and the pivot come
 // by shuffles.  The pivot loop is unrolled by 8 (the slot index a constant, one copy of
 // the code for both halves) and has no branch, so a step's trailing updates overlap the
-// next step's shuffles.  mode 0: shifted first pass; 1: full
-// LDL^T; 2: first order when S is within 2^-12 of I (N = I - strictly_lower(S - I),
-// D^{-1/2} = I - diag(S - I) / 2, error second order), else full.
+// next step's shuffles.  mode 0: shifted first pass; 1: full LDL^T; 2: first order when
+// S is within 2^-12 of I (N = I - strictly_lower(S - I), D^{-1/2} = I - diag(S - I) / 2,
+// error second order), else full.
 __device__ __forceinline__ void cq_factor(const float* S, int r, int k, int mode, float* Nt,
                                           float* dsq) {
   const int lane = threadIdx.x & 31, i = lane >> 1, h = lane & 1;
